@@ -1,0 +1,165 @@
+/*
+ * dspg.h -- C ABI of the batch-dynamic SpGEMM library for one GB300 GPU.
+ *
+ * The problem (van der Grinten et al., "Fast Dynamic Updates and Dynamic
+ * SpGEMM on MPI-Distributed Graphs", Section 5): A is n x k, B is k x m,
+ * C = A B over a semiring.  A batch of updates turns A, B into A', B'; the
+ * library then produces C' = A' B' by recomputing only the rows of C that
+ * the batch can change (general updates, Section 5: C' differs from C only
+ * where C* = A* B' + A B* (Eq. 1) has a non-zero), instead of the whole
+ * product.
+ *
+ * Semirings (Section 3): (+,.) on double, and (min,+) on int32 (the
+ * shortest-path semiring).  An entry is a non-zero iff it is stored
+ * ("structural" non-zero, Section 3), even when its value is 0; absent
+ * entries are the additive neutral element (infinity for (min,+)).
+ * (min,+) values must satisfy |v| < 2^30; sums use plain int32 addition.
+ *
+ * Updates (Section 4.1): INSERT and SET write a value at (i,j) (the paper's
+ * merge: overwrite, or add the entry when absent); DELETE removes (i,j)
+ * when present (the paper's mask) and is a no-op otherwise.  Within one
+ * batch, updates of the same (i,j) take effect in array order: the last
+ * one wins.
+ *
+ * Conventions for every call:
+ *  - Indices are int32 (rows, columns), offsets int64.
+ *  - Pointers marked "host or device" are device pointers when the
+ *    accompanying on_device flag is 1 and host pointers otherwise; they are
+ *    only read during the call (borrowed) and copied into library memory.
+ *  - The handle owns A', B', C' and all working memory on the device; no
+ *    pointer into library memory is ever returned.
+ *  - All work is enqueued on the given stream (0 = legacy default stream);
+ *    calls that return a status or sizes synchronise that stream.
+ *  - Errors are reported as dspg_status codes only; dspg_last_error gives a
+ *    message.  An invalid input returns DSPG_ERR_INVALID and leaves the
+ *    handle exactly as it was (validation precedes mutation).
+ *  - A handle is not thread-safe: one call at a time per handle.
+ */
+#ifndef DSPG_H
+#define DSPG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DSPG_PLUS_TIMES_F64 = 0, /* (+,.) with double values */
+    DSPG_MIN_PLUS_I32 = 1    /* (min,+) with int32 values, |v| < 2^30 */
+} dspg_semiring;
+
+typedef enum {
+    DSPG_OK = 0,
+    DSPG_ERR_INVALID = 1, /* bad argument or batch; the handle is unchanged */
+    DSPG_ERR_OOM = 2,     /* device memory exhausted; the handle is unchanged */
+    DSPG_ERR_CUDA = 3,    /* a CUDA runtime error; the handle should be destroyed */
+    DSPG_ERR_TIMEOUT = 4, /* a bounded device-side loop gave up */
+    DSPG_ERR_STATE = 5    /* call not valid in the handle's current state */
+} dspg_status;
+
+typedef enum { DSPG_OP_INSERT = 0, DSPG_OP_DELETE = 1, DSPG_OP_SET = 2 } dspg_op;
+
+/* A canonical CSR matrix: rowptr[nrows+1] (rowptr[0] = 0, non-decreasing),
+ * col[nnz] strictly ascending within each row and in [0, ncols), val[nnz]
+ * of the semiring's value type.  Host or device memory per on_device. */
+typedef struct {
+    int64_t nrows, ncols, nnz;
+    const int64_t *rowptr;
+    const int32_t *col;
+    const void *val;
+    int on_device;
+} dspg_csr;
+
+/* An update batch in arrival order (Section 4.1): n entries of
+ * (row, col, val, op); val is ignored for DELETE.  Host or device memory
+ * per on_device. */
+typedef struct {
+    int64_t n;
+    const int32_t *row;
+    const int32_t *col;
+    const void *val;
+    const uint8_t *op;
+    int on_device;
+} dspg_updates;
+
+/* Tuning knobs; pass NULL for the defaults given here. */
+typedef struct {
+    int32_t slack_min;      /* free slots reserved per row: max(slack_min, len/slack_div); default 4 */
+    int32_t slack_div;      /* default 4 */
+    double arena_headroom;  /* arena capacity / total row capacity at build; default 1.5 */
+    int32_t keep_transpose; /* 1: maintain A's transposed pattern (needed when B is A or B changes); -1: auto */
+} dspg_options;
+
+/* What one apply_batch did.  Counts of the unique, last-writer-wins batch
+ * entries of A and B together. */
+typedef struct {
+    int64_t n_updates;      /* entries received (A and B batches) */
+    int64_t n_unique;       /* distinct (matrix, row, col) keys */
+    int64_t n_insert;       /* writes of absent entries */
+    int64_t n_update;       /* writes of present entries */
+    int64_t n_delete;       /* deletes of present entries */
+    int64_t n_noop;         /* deletes of absent entries */
+    int64_t touched_rows;   /* rows of A and B rewritten by the merge */
+    int64_t affected_rows;  /* |R|: rows of C recomputed */
+    int64_t products;       /* semiring products formed in the recompute */
+    int64_t nnz_written;    /* entries of C written by the recompute */
+    int64_t relocations;    /* rows moved to the arena tail (A, B, transpose, C) */
+    int64_t compactions;    /* arena rebuilds (growth) during this batch */
+} dspg_batch_stats;
+
+typedef struct dspg_handle dspg_handle;
+
+/* Build a handle holding A, B and C = A B (Section 5's starting point; the
+ * product itself is Gustavson's row-wise algorithm, Section 6.1).
+ * B == NULL means B is A (C = A A): one batch then updates both operands.
+ * A->ncols must equal B->nrows.  On success *out receives the handle.
+ * Returns DSPG_ERR_INVALID for a non-canonical or out-of-range input. */
+dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, dspg_semiring sr,
+                       const dspg_options *opt, void *stream);
+
+/* Apply one batch to A (dA) and to B (dB; must be NULL or empty when B is
+ * A) and bring C up to date: C' = A' B' (Section 5, general updates).
+ * Rows of C outside the affected set R = rows(A*) u {i : A(i,k) != 0,
+ * k in rows(B*)} are left bit-for-bit as they were.  stats may be NULL.
+ * Synchronises the stream once to return the status. */
+dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
+                             dspg_batch_stats *stats, void *stream);
+
+/* Read C in canonical CSR (rows in order, columns ascending) into caller
+ * buffers: rowptr[nrows+1], col[nnz], val[nnz], host or device per
+ * on_device.  Two-call convention: with rowptr == NULL only *nnz_out is
+ * written. */
+dspg_status dspg_read_C(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32_t *col, void *val,
+                        int on_device, void *stream);
+
+/* Read A' (the updated left operand) in canonical CSR; same convention. */
+dspg_status dspg_read_A(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32_t *col, void *val,
+                        int on_device, void *stream);
+
+/* Read selected rows of C: rows[nrows] (host or device per on_device);
+ * rowptr[nrows+1], col, val as in dspg_read_C, in the order given. */
+dspg_status dspg_read_rows_C(dspg_handle *h, const int32_t *rows, int64_t nrows, int64_t *nnz_out,
+                             int64_t *rowptr, int32_t *col, void *val, int on_device, void *stream);
+
+/* The affected row set R of the last apply_batch, ascending, into rows
+ * (room for *count rows; with rows == NULL only *count is written). */
+dspg_status dspg_last_affected(dspg_handle *h, int64_t *count, int32_t *rows, int on_device, void *stream);
+
+/* Recompute every row of C from the current A', B' (the static product, used
+ * as the comparison point for the dynamic path). */
+dspg_status dspg_recompute_all(dspg_handle *h, void *stream);
+
+/* Shapes and sizes: nrows(A), ncols(A) = nrows(B), ncols(B), nnz(A'), nnz(C'). */
+dspg_status dspg_info(dspg_handle *h, int64_t *n, int64_t *k, int64_t *m, int64_t *nnz_a, int64_t *nnz_c);
+
+void dspg_destroy(dspg_handle *h);
+
+/* Message of the last error on h, or of the calling thread's last failed
+ * dspg_build when h == NULL.  Valid until the next call on h / the thread. */
+const char *dspg_last_error(const dspg_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSPG_H */

@@ -1,0 +1,192 @@
+// common.cuh -- types and device helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dspg.h"
+
+namespace dspg {
+
+constexpr int SR_PT = 0;  // (+,.) on double
+constexpr int SR_MP = 1;  // (min,+) on int32
+
+constexpr int32_t MP_INF = 0x7fffffff;     // (min,+) additive neutral element
+constexpr int32_t MP_LIMIT = 1 << 30;      // |value| bound for (min,+)
+
+// Device status bits (Ctl::status).  A kernel returns at entry when any bit
+// of the mask it depends on is set, so nothing is mutated after a failed
+// check.  Overflow bits are not errors: the host grows the buffer named by
+// the bit and re-runs the stage that set it.
+enum : unsigned {
+    ST_INVALID = 1u << 0,     // batch failed validation
+    ST_AB_STAGE = 1u << 1,    // A/B merge staging too small
+    ST_AB_ARENA = 1u << 2,    // A/B arena cannot take relocated rows
+    ST_AT_STAGE = 1u << 3,    // transposed-pattern staging too small
+    ST_AT_ARENA = 1u << 4,    // transposed-pattern arena exhausted
+    ST_C_STAGE = 1u << 5,     // C staging too small
+    ST_C_ARENA = 1u << 6,     // C arena exhausted
+    ST_C_SCRATCH = 1u << 7,   // accumulator scratch too small
+    ST_TIMEOUT = 1u << 8,     // a bounded probe loop gave up
+};
+constexpr unsigned M_AB = ST_INVALID | ST_AB_STAGE | ST_AB_ARENA | ST_TIMEOUT;
+constexpr unsigned M_AT = M_AB | ST_AT_STAGE | ST_AT_ARENA;
+constexpr unsigned M_C = M_AB | ST_C_STAGE | ST_C_ARENA | ST_C_SCRATCH;
+
+// Update operation codes as received, plus DEAD for an earlier duplicate of
+// a key (only the last write of a key in a batch takes effect).
+enum : uint8_t { OP_INSERT = 0, OP_DELETE = 1, OP_SET = 2, OP_DEAD = 3 };
+
+// Classification of a unique update against the row it targets.
+enum : uint8_t { K_NOP = 0, K_INS = 1, K_UPD = 2, K_DEL = 3 };
+
+// Counters of one matrix update (sort -> classify -> merge -> commit).
+struct UpdCtl {
+    long long n_seg;      // row segments of the sorted batch
+    long long n_merge;    // rows with at least one effective change
+    long long n_chunk;    // merge copy work items
+    long long stage_top;  // staging entries handed out
+    long long n_cchunk;   // commit copy work items
+    long long ins, upd, del, nop;
+    long long reloc;      // rows moved to the arena tail
+    long long pad[5];
+};
+
+constexpr int NBINS = 12;
+
+struct Ctl {
+    unsigned status;
+    unsigned pad0;
+    UpdCtl u[3];               // 0: A, 1: B, 2: transposed pattern of A
+    long long n_affected;      // |R|
+    long long c_stage_top;     // C staging entries handed out
+    long long c_chunk;         // C commit copy items
+    long long c_reloc;
+    long long products;
+    long long nnz_written;
+    long long scratch_top;     // accumulator scratch handed out
+    long long n_K;             // rows of B* (detection)
+    long long bin_count[NBINS];
+    long long ubc_total;       // sum over rows of min(product bound, columns)
+    long long pad[7];
+};
+
+// A row-slack CSR ("slack-CSR") on the device: row i occupies
+// col[off[i] .. off[i]+len[i]) with room for cap[i] entries; rows are kept
+// column-sorted.  Rows that outgrow their room move to the arena tail
+// (top), and the whole arena is rebuilt when the tail is exhausted.
+struct MatView {
+    int64_t nrows, ncols;
+    int64_t *off;
+    int32_t *len;
+    int32_t *cap;
+    int32_t *col;
+    void *val;            // double* or int32_t*, nullptr for a pattern
+    long long *top;       // arena high-water mark (device)
+    int64_t arena_cap;    // entries
+};
+
+__host__ __device__ inline int32_t slack_cap(int64_t len, int slack_min, int slack_div) {
+    int64_t extra = len / slack_div;
+    if (extra < slack_min) extra = slack_min;
+    int64_t c = len + extra;
+    c = (c + 3) & ~int64_t(3);  // 16-byte aligned rows for int32 columns
+    return (int32_t)c;
+}
+
+__host__ __device__ inline int bits_for(int64_t x) {  // bits to hold values in [0, x)
+    int b = 1;
+    while (b < 63 && (int64_t(1) << b) < x) b++;
+    return b;
+}
+
+#ifdef __CUDACC__
+
+__device__ __forceinline__ bool failed(const Ctl *ctl, unsigned mask) {
+    return (*(volatile const unsigned *)&ctl->status & mask) != 0u;
+}
+
+__device__ __forceinline__ void set_status(Ctl *ctl, unsigned bit) { atomicOr(&ctl->status, bit); }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// First index in [lo, hi) with a[idx] >= x (a ascending).
+template <typename T>
+__device__ __forceinline__ int64_t lower_bound_dev(const T *a, int64_t lo, int64_t hi, T x) {
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// First index in [lo, hi) with a[idx] > x.
+template <typename T>
+__device__ __forceinline__ int64_t upper_bound_dev(const T *a, int64_t lo, int64_t hi, T x) {
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+#endif  // __CUDACC__
+
+// ---------------------------------------------------------------- host side
+
+// Device scan: out[i] = sum_{j<i} in[j] for i <= n (out has n+1 entries).
+void scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
+void scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
+int64_t scan_tmp_entries(int64_t n);
+
+// Sort a batch of updates by (row, col), keep the last write of each key:
+// see sort.cu.
+struct SortOut {
+    int32_t *row, *col;
+    void *val;
+    uint8_t *op;
+};
+struct SortTmp {
+    uint64_t *k0, *k1;
+    uint32_t *i0, *i1;
+    uint32_t *counts;
+    int64_t *scan_tmp;
+    int64_t *scan_out;
+    int64_t cap;      // entries
+    int64_t cnt_cap;  // count entries
+};
+int64_t sort_small_max();
+void sort_tmp_sizes(int64_t n, int64_t *count_entries);
+// Validate + sort + dedupe n updates of a matrix with the given shape.
+// Sets ST_INVALID in ctl on a bad entry.
+// Kernels return at entry when a bit of skip_mask is set in ctl->status.
+void sort_updates(const int32_t *row, const int32_t *col, const void *val, const uint8_t *op, int64_t n,
+                  int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out, SortTmp tmp,
+                  Ctl *ctl, unsigned skip_mask, cudaStream_t s);
+// Stable sort of (key, value) pairs by the low `bits` bits of key (multi-CTA).
+void radix_sort_pairs(uint64_t *k, uint32_t *v, uint64_t *k_alt, uint32_t *v_alt, int64_t n, int bits,
+                      uint32_t *counts, int64_t *scan_tmp, int64_t *scan_out, cudaStream_t s, bool *result_in_alt);
+
+}  // namespace dspg

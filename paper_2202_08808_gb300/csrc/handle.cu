@@ -1,0 +1,951 @@
+// handle.cu -- the C ABI: handle lifecycle, build, apply_batch and reads.
+//
+// apply_batch enqueues the whole pipeline on the caller's stream without a
+// host round trip and synchronises once at the end to read the status:
+//
+//   S1 sort + de-duplicate the A (and B) batch        (sort.cu)
+//   S2 segment by row, classify against the old rows  (update.cu)
+//   S3 affected rows R from the classification and the transposed pattern
+//   S4 merge copy, S5 commit into A (and B)
+//   S6 forward structural changes to the transposed pattern of A, apply them
+//   S7 size and bin the rows of R, S8 recompute them  (spgemm.cu)
+//   S9 splice the recomputed rows into C
+//
+// Buffers whose need is only known on the device (staging, arena tails) are
+// checked there; an overflow sets a status bit, later kernels that depend on
+// it return at entry, and the host grows the buffer and re-runs the stages
+// from the failed one.  Nothing is mutated before the stage that overflowed
+// has succeeded, so the handle always stays consistent.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+
+#include "internal.h"
+
+using namespace dspg;
+
+namespace {
+
+struct Err : std::runtime_error {
+    dspg_status st;
+    Err(dspg_status s, const std::string &m) : std::runtime_error(m), st(s) {}
+};
+
+#define CK(x)                                                                                      \
+    do {                                                                                           \
+        cudaError_t e_ = (x);                                                                      \
+        if (e_ != cudaSuccess) throw Err(DSPG_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void *dmalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Err(DSPG_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    return p;
+}
+
+template <typename T>
+struct DBuf {
+    T *p = nullptr;
+    int64_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    // Ensure room for `need` elements; contents are discarded on growth.
+    void reserve(int64_t need) {
+        if (need <= n) return;
+        T *q = (T *)dmalloc(sizeof(T) * (size_t)need);
+        release();
+        p = q;
+        n = need;
+    }
+    void swap(DBuf &o) {
+        std::swap(p, o.p);
+        std::swap(n, o.n);
+    }
+};
+
+struct DevMat {
+    int64_t nrows = 0, ncols = 0;
+    int vsize = 0;  // 8, 4, or 0 for a pattern
+    DBuf<int64_t> off;
+    DBuf<int32_t> len, cap, col;
+    DBuf<char> val;
+    DBuf<long long> top;
+    int64_t arena_cap = 0;
+    MatView view() {
+        return MatView{nrows, ncols, off.p, len.p, cap.p, col.p, vsize ? (void *)val.p : nullptr, top.p, arena_cap};
+    }
+};
+
+// Work buffers of one matrix update (A, B, or the transposed pattern).
+struct UpdWs {
+    int which = 0;
+    int vsize = 0;
+    int64_t ncap = 0;
+    DBuf<int32_t> in_row, in_col;
+    DBuf<char> in_val;
+    DBuf<uint8_t> in_op;
+    DBuf<int32_t> row, col;
+    DBuf<char> val;
+    DBuf<uint8_t> op, kind;
+    DBuf<int32_t> pos, insx, delx, seg_lo, seg_hi, m_row, m_seg, m_len, m_nins, m_ndel, m_cap;
+    DBuf<int64_t> m_soff, m_dest;
+    DBuf<int32_t> ch_item, ch_part, cc_item, cc_part;
+    DBuf<int32_t> st_col;
+    DBuf<char> st_val;
+    int64_t st_cap = 0;
+    DBuf<uint64_t> k0, k1;
+    DBuf<uint32_t> i0, i1, counts;
+    DBuf<int64_t> scan_tmp, scan_out;
+
+    void ensure(int64_t n, int64_t arena_cap) {
+        if (n > ncap) {
+            int64_t c = std::max<int64_t>(n, std::max<int64_t>(2 * ncap, 1024));
+            in_row.reserve(c); in_col.reserve(c); in_val.reserve(c * std::max(vsize, 1)); in_op.reserve(c);
+            row.reserve(c); col.reserve(c); val.reserve(c * std::max(vsize, 1)); op.reserve(c); kind.reserve(c);
+            pos.reserve(c); insx.reserve(c); delx.reserve(c); seg_lo.reserve(c); seg_hi.reserve(c);
+            m_row.reserve(c); m_seg.reserve(c); m_len.reserve(c); m_nins.reserve(c); m_ndel.reserve(c);
+            m_cap.reserve(c); m_soff.reserve(c); m_dest.reserve(c);
+            k0.reserve(c); k1.reserve(c); i0.reserve(c); i1.reserve(c);
+            int64_t cnt;
+            sort_tmp_sizes(c, &cnt);
+            counts.reserve(cnt);
+            scan_out.reserve(cnt + 1);
+            scan_tmp.reserve(scan_tmp_entries(cnt) + 1);
+            ncap = c;
+        }
+        if (st_cap < 16 * n + 65536) grow_stage(16 * n + 65536);
+        ch_item.reserve(ncap + arena_cap / 256 + 64);
+        ch_part.reserve(ncap + arena_cap / 256 + 64);
+    }
+    void grow_stage(int64_t need) {
+        if (need <= st_cap) return;
+        int64_t c = std::max<int64_t>(need, st_cap + st_cap / 2);
+        st_col.reserve(c);
+        if (vsize) st_val.reserve(c * vsize);
+        st_cap = c;
+        cc_item.reserve(ncap * 2 + c / 256 + 64);
+        cc_part.reserve(ncap * 2 + c / 256 + 64);
+    }
+    SortOut sort_out() { return SortOut{row.p, col.p, vsize ? (void *)val.p : nullptr, op.p}; }
+    SortTmp sort_tmp() {
+        return SortTmp{k0.p, k1.p, i0.p, i1.p, counts.p, scan_tmp.p, scan_out.p, k0.n, counts.n};
+    }
+    UpdJob job(int64_t n) {
+        UpdJob J{};
+        J.which = which;
+        J.n = n;
+        J.row = row.p; J.col = col.p; J.val = vsize ? (void *)val.p : nullptr; J.op = op.p;
+        J.kind = kind.p; J.pos = pos.p; J.insx = insx.p; J.delx = delx.p;
+        J.seg_lo = seg_lo.p; J.seg_hi = seg_hi.p;
+        J.m_row = m_row.p; J.m_seg = m_seg.p; J.m_len = m_len.p; J.m_nins = m_nins.p; J.m_ndel = m_ndel.p;
+        J.m_soff = m_soff.p; J.m_dest = m_dest.p; J.m_cap = m_cap.p;
+        J.ch_item = ch_item.p; J.ch_part = ch_part.p; J.ch_cap = ch_item.n;
+        J.cc_item = cc_item.p; J.cc_part = cc_part.p; J.cc_cap = cc_item.n;
+        J.st_col = st_col.p; J.st_val = vsize ? (void *)st_val.p : nullptr; J.st_cap = st_cap;
+        return J;
+    }
+};
+
+// Work buffers of the recompute of C rows.
+struct CWs {
+    int64_t nrows = 0;
+    DBuf<int32_t> R, iota, slen, bins, ncap, cc_item, cc_part;
+    DBuf<int64_t> soff, dest;
+    DBuf<int32_t> st_col;
+    DBuf<char> st_val;
+    int64_t st_cap = 0;
+    DBuf<char> gd_acc;
+    DBuf<uint32_t> gd_mask;
+    int64_t gd_w = 0;
+    int gd_ctas = 0;
+    // detection
+    DBuf<uint32_t> bmR, bmK;
+    DBuf<int32_t> K;
+    int64_t nrows_b = 0;
+};
+
+struct BatchIn {
+    const int32_t *row = nullptr, *col = nullptr;
+    const void *val = nullptr;
+    const uint8_t *op = nullptr;
+    int64_t n = 0;
+};
+
+thread_local std::string g_err;
+
+}  // namespace
+
+struct dspg_handle {
+    int sr = 0, vsize = 8, num_sms = 148, dev = 0;
+    dspg_options opt{};
+    DevMat A, B, AT, C;
+    bool b_is_a = true;
+    bool has_at = false;
+    Ctl *ctl = nullptr;   // device
+    Ctl *hctl = nullptr;  // pinned host mirror
+    UpdWs wA, wB, wAT;
+    CWs wc;
+    BatchIn inA, inB;
+    int64_t last_nR = 0;
+    int64_t compactions = 0;
+    std::string err;
+
+    DevMat &Bm() { return b_is_a ? A : B; }
+};
+
+namespace {
+
+void set_defaults(dspg_options *o) {
+    o->slack_min = 4;
+    o->slack_div = 4;
+    o->arena_headroom = 1.5;
+    o->keep_transpose = -1;
+}
+
+void read_ctl(dspg_handle *h, cudaStream_t s) {
+    CK(cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+}
+
+int64_t read_i64(const int64_t *dptr, cudaStream_t s) {
+    int64_t v = 0;
+    CK(cudaMemcpyAsync(&v, dptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return v;
+}
+
+// Build a slack-CSR from rows given as (start, length) in a source arrays.
+void make_slack(dspg_handle *h, DevMat &M, int64_t nrows, int64_t ncols, int vsize, const int64_t *src_off,
+                const int32_t *len, const int32_t *src_col, const void *src_val, cudaStream_t s) {
+    DevMat N;
+    N.nrows = nrows;
+    N.ncols = ncols;
+    N.vsize = vsize;
+    N.len.reserve(nrows);
+    N.cap.reserve(nrows);
+    N.off.reserve(nrows + 1);
+    N.top.reserve(1);
+    if (nrows > 0) CK(cudaMemcpyAsync(N.len.p, len, sizeof(int32_t) * nrows, cudaMemcpyDeviceToDevice, s));
+    caps_from_lens(N.len.p, N.cap.p, nrows, h->opt.slack_min, h->opt.slack_div, s);
+    DBuf<int64_t> tmp;
+    tmp.reserve(scan_tmp_entries(nrows) + 1);
+    scan_i32_to_i64(N.cap.p, N.off.p, nrows, tmp.p, s);
+    const int64_t total = read_i64(N.off.p + nrows, s);
+    N.arena_cap = std::max<int64_t>((int64_t)(total * h->opt.arena_headroom), total + 4096);
+    N.col.reserve(N.arena_cap);
+    if (vsize) N.val.reserve(N.arena_cap * vsize);
+    copy_rows(nullptr, nrows, src_off, N.len.p, src_col, src_val, N.off.p, N.col.p, vsize ? (void *)N.val.p : nullptr,
+              vsize, s, h->num_sms);
+    long long t = total;
+    CK(cudaMemcpyAsync(N.top.p, &t, sizeof(long long), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    M.nrows = N.nrows; M.ncols = N.ncols; M.vsize = N.vsize; M.arena_cap = N.arena_cap;
+    M.off.swap(N.off); M.len.swap(N.len); M.cap.swap(N.cap); M.col.swap(N.col); M.val.swap(N.val);
+    M.top.swap(N.top);
+}
+
+// Rebuild M's arena with fresh slack for every row and at least twice the
+// room of the old arena (growth after the tail ran out).
+void regrow(dspg_handle *h, DevMat &M, cudaStream_t s) {
+    DBuf<int32_t> ncap;
+    DBuf<int64_t> noff, tmp;
+    ncap.reserve(M.nrows);
+    noff.reserve(M.nrows + 1);
+    tmp.reserve(scan_tmp_entries(M.nrows) + 1);
+    caps_from_lens(M.len.p, ncap.p, M.nrows, h->opt.slack_min, h->opt.slack_div, s);
+    scan_i32_to_i64(ncap.p, noff.p, M.nrows, tmp.p, s);
+    const int64_t total = read_i64(noff.p + M.nrows, s);
+    const int64_t cap = std::max<int64_t>(std::max<int64_t>((int64_t)(total * h->opt.arena_headroom), 2 * M.arena_cap),
+                                          total + 4096);
+    DBuf<int32_t> ncol;
+    DBuf<char> nval;
+    ncol.reserve(cap);
+    if (M.vsize) nval.reserve(cap * M.vsize);
+    copy_rows(nullptr, M.nrows, M.off.p, M.len.p, M.col.p, M.vsize ? (void *)M.val.p : nullptr, noff.p, ncol.p,
+              M.vsize ? (void *)nval.p : nullptr, M.vsize, s, h->num_sms);
+    long long t = total;
+    CK(cudaMemcpyAsync(M.top.p, &t, sizeof(long long), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    M.off.swap(noff);
+    M.cap.swap(ncap);
+    M.col.swap(ncol);
+    M.val.swap(nval);
+    M.arena_cap = cap;
+    h->compactions++;
+}
+
+// Canonical CSR copy of M's rows (all rows when rows == nullptr) into device
+// buffers; returns nnz.  rowptr_out has n+1 entries.
+int64_t mat_rowptr(dspg_handle *h, DevMat &M, const int32_t *rows, int64_t n, DBuf<int64_t> &rowptr,
+                   cudaStream_t s) {
+    DBuf<int32_t> lens;
+    const int32_t *lp = M.len.p;
+    if (rows) {
+        lens.reserve(n);
+        lens_of_rows(rows, n, M.len.p, lens.p, s);
+        lp = lens.p;
+    }
+    rowptr.reserve(n + 1);
+    DBuf<int64_t> tmp;
+    tmp.reserve(scan_tmp_entries(n) + 1);
+    scan_i32_to_i64(lp, rowptr.p, n, tmp.p, s);
+    return read_i64(rowptr.p + n, s);
+}
+
+void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
+    CWs &w = h->wc;
+    const int64_t n = h->A.nrows;
+    if (w.nrows == n && w.R.p) return;
+    w.nrows = n;
+    const int64_t nn = std::max<int64_t>(n, 1);
+    w.R.reserve(nn);
+    w.iota.reserve(nn);
+    fill_iota(w.iota.p, n, s);
+    w.slen.reserve(nn);
+    w.soff.reserve(nn);
+    w.bins.reserve((int64_t)NBINS * nn);
+    w.dest.reserve(nn);
+    w.ncap.reserve(nn);
+    w.bmR.reserve(nn / 32 + 2);
+    CK(cudaMemsetAsync(w.bmR.p, 0, sizeof(uint32_t) * w.bmR.n, s));
+    const int64_t nb = std::max<int64_t>(h->Bm().nrows, 1);
+    w.nrows_b = nb;
+    w.bmK.reserve(nb / 32 + 2);
+    CK(cudaMemsetAsync(w.bmK.p, 0, sizeof(uint32_t) * w.bmK.n, s));
+    w.K.reserve(nb);
+    const int64_t m = h->Bm().ncols;
+    if (m > DENSE_M_MAX) {
+        w.gd_w = (m + 31) / 32 * 32;
+        const double per = (double)w.gd_w * (h->vsize + 0.125);
+        int ctas = (int)std::min<double>(2.0 * h->num_sms, std::max(1.0, (1024.0 * 1024 * 1024) / per));
+        w.gd_ctas = std::max(1, ctas);
+        w.gd_acc.reserve(w.gd_w * w.gd_ctas * h->vsize);
+        w.gd_mask.reserve(w.gd_w / 32 * w.gd_ctas);
+        init_dense_scratch(h->sr, w.gd_acc.p, w.gd_mask.p, w.gd_w * w.gd_ctas, w.gd_w / 32 * w.gd_ctas, s);
+    }
+}
+
+void grow_c_stage(dspg_handle *h, int64_t need) {
+    CWs &w = h->wc;
+    if (need <= w.st_cap) return;
+    int64_t c = std::max<int64_t>(need, w.st_cap + w.st_cap / 2);
+    w.st_col.reserve(c);
+    w.st_val.reserve(c * h->vsize);
+    w.st_cap = c;
+    w.cc_item.reserve(2 * w.nrows + c / 256 + 64);
+    w.cc_part.reserve(2 * w.nrows + c / 256 + 64);
+}
+
+CJob c_job(dspg_handle *h, const int32_t *R) {
+    CWs &w = h->wc;
+    CJob J{};
+    J.R = R;
+    J.nR_max = w.nrows;
+    J.slen = w.slen.p;
+    J.soff = w.soff.p;
+    J.bins = w.bins.p;
+    J.bin_cap = std::max<int64_t>(w.nrows, 1);
+    J.st_col = w.st_col.p;
+    J.st_val = w.st_val.p;
+    J.st_cap = w.st_cap;
+    J.gd_acc = w.gd_acc.p;
+    J.gd_mask = w.gd_mask.p;
+    J.gd_w = w.gd_w;
+    J.gd_ctas = std::max(w.gd_ctas, 1);
+    J.m = h->Bm().ncols;
+    J.dense_mode = J.m <= DENSE_M_MAX ? 1 : 0;
+    return J;
+}
+
+CommitJob c_commit_job(dspg_handle *h, const int32_t *R) {
+    CWs &w = h->wc;
+    CommitJob J{};
+    J.rows = R;
+    J.lens = w.slen.p;
+    J.soff = w.soff.p;
+    J.count = &h->ctl->n_affected;
+    J.st_col = w.st_col.p;
+    J.st_val = w.st_val.p;
+    J.dest = w.dest.p;
+    J.ncap = w.ncap.p;
+    J.cc_item = w.cc_item.p;
+    J.cc_part = w.cc_part.p;
+    J.cc_count = &h->ctl->c_chunk;
+    J.cc_cap = w.cc_item.n;
+    J.reloc = &h->ctl->c_reloc;
+    J.arena_bit = ST_C_ARENA;
+    J.stage_bit = ST_C_STAGE;
+    return J;
+}
+
+CommitJob upd_commit_job(dspg_handle *h, UpdWs &w, unsigned arena_bit, unsigned stage_bit) {
+    CommitJob J{};
+    J.rows = w.m_row.p;
+    J.lens = w.m_len.p;
+    J.soff = w.m_soff.p;
+    J.count = &h->ctl->u[w.which].n_merge;
+    J.st_col = w.st_col.p;
+    J.st_val = w.vsize ? (const void *)w.st_val.p : nullptr;
+    J.dest = w.m_dest.p;
+    J.ncap = w.m_cap.p;
+    J.cc_item = w.cc_item.p;
+    J.cc_part = w.cc_part.p;
+    J.cc_count = &h->ctl->u[w.which].n_cchunk;
+    J.cc_cap = w.cc_item.n;
+    J.reloc = &h->ctl->u[w.which].reloc;
+    J.arena_bit = arena_bit;
+    J.stage_bit = stage_bit;
+    return J;
+}
+
+// Full recompute of C from A, B (the static product).  Replaces C.
+void static_recompute(dspg_handle *h, cudaStream_t s) {
+    ensure_c_ws(h, s);
+    const int64_t n = h->A.nrows;
+    CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+    long long nn = n;
+    CK(cudaMemcpyAsync(&h->ctl->n_affected, &nn, sizeof(long long), cudaMemcpyHostToDevice, s));
+    MatView Av = h->A.view(), Bv = h->Bm().view();
+    grow_c_stage(h, 1024);
+    run_size_bins(Av, Bv, c_job(h, h->wc.iota.p), n, h->ctl, M_C, s, h->num_sms);
+    read_ctl(h, s);
+    grow_c_stage(h, (int64_t)h->hctl->ubc_total + 1024);
+    run_numeric(h->sr, Av, Bv, c_job(h, h->wc.iota.p), h->ctl, M_C, s, h->num_sms);
+    read_ctl(h, s);
+    if (h->hctl->status & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, "accumulator probe limit reached");
+    if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "static recompute failed with status " + std::to_string(h->hctl->status));
+    const int64_t m = h->Bm().ncols;
+    make_slack(h, h->C, n, m, h->vsize, h->wc.soff.p, h->wc.slen.p, h->wc.st_col.p, h->wc.st_val.p, s);
+}
+
+// Transposed pattern of A (rows of A^T = columns of A), built from A's rows.
+void build_transpose(dspg_handle *h, cudaStream_t s) {
+    DevMat &A = h->A;
+    DBuf<int64_t> rowptr;
+    const int64_t nnz = mat_rowptr(h, A, nullptr, A.nrows, rowptr, s);
+    DBuf<int32_t> col;
+    col.reserve(nnz + 1);
+    gather_rows_out(nullptr, A.nrows, A.view(), rowptr.p, col.p, nullptr, 0, s, h->num_sms);
+    DBuf<uint64_t> k0, k1;
+    DBuf<uint32_t> v0, v1, counts;
+    DBuf<int64_t> scan_tmp, scan_out;
+    k0.reserve(nnz + 1); k1.reserve(nnz + 1); v0.reserve(nnz + 1); v1.reserve(nnz + 1);
+    int64_t cnt;
+    sort_tmp_sizes(nnz, &cnt);
+    counts.reserve(cnt);
+    scan_out.reserve(cnt + 1);
+    scan_tmp.reserve(scan_tmp_entries(cnt) + 1);
+    keys_from_cols(col.p, nnz, k0.p, s);
+    rows_of_entries(rowptr.p, A.nrows, v0.p, s, h->num_sms);
+    bool alt = false;
+    if (nnz > 0) radix_sort_pairs(k0.p, v0.p, k1.p, v1.p, nnz, bits_for(A.ncols), counts.p, scan_tmp.p, scan_out.p, s, &alt);
+    DBuf<int32_t> tlen;
+    tlen.reserve(std::max<int64_t>(A.ncols, 1));
+    CK(cudaMemsetAsync(tlen.p, 0, sizeof(int32_t) * tlen.n, s));
+    hist_cols(col.p, nnz, tlen.p, s);
+    DBuf<int64_t> toff, tmp;
+    toff.reserve(A.ncols + 1);
+    tmp.reserve(scan_tmp_entries(A.ncols) + 1);
+    scan_i32_to_i64(tlen.p, toff.p, A.ncols, tmp.p, s);
+    make_slack(h, h->AT, A.ncols, A.nrows, 0, toff.p, tlen.p, (const int32_t *)(alt ? v1.p : v0.p), nullptr, s);
+    h->has_at = true;
+}
+
+// ------------------------------------------------------------ pipeline
+
+void stage_sort_classify(dspg_handle *h, cudaStream_t s) {
+    Ctl *ctl = h->ctl;
+    if (h->inA.n > 0) {
+        sort_updates(h->inA.row, h->inA.col, h->inA.val, h->inA.op, h->inA.n, h->A.nrows, h->A.ncols, h->sr, true,
+                     h->wA.sort_out(), h->wA.sort_tmp(), ctl, 0u, s);
+    }
+    if (!h->b_is_a && h->inB.n > 0) {
+        sort_updates(h->inB.row, h->inB.col, h->inB.val, h->inB.op, h->inB.n, h->B.nrows, h->B.ncols, h->sr, true,
+                     h->wB.sort_out(), h->wB.sort_tmp(), ctl, 0u, s);
+    }
+    if (h->inA.n > 0) {
+        UpdJob J = h->wA.job(h->inA.n);
+        run_segments(J, h->A.nrows, ctl, M_AB, s);
+        run_classify(J, h->A.view(), h->vsize, ctl, M_AB, ST_AB_STAGE, s, h->num_sms);
+    }
+    if (!h->b_is_a && h->inB.n > 0) {
+        UpdJob J = h->wB.job(h->inB.n);
+        run_segments(J, h->B.nrows, ctl, M_AB, s);
+        run_classify(J, h->B.view(), h->vsize, ctl, M_AB, ST_AB_STAGE, s, h->num_sms);
+    }
+}
+
+void stage_detect(dspg_handle *h, cudaStream_t s) {
+    CWs &w = h->wc;
+    DetectBufs D{w.bmR.p, w.bmK.p, w.R.p, w.K.p, &h->ctl->n_K};
+    const bool use_at = h->has_at;
+    if (h->b_is_a) {
+        run_detect_entries(h->wA.row.p, h->wA.kind.p, h->inA.n, true, use_at, D, h->ctl, M_AB, s);
+    } else {
+        run_detect_entries(h->wA.row.p, h->wA.kind.p, h->inA.n, true, false, D, h->ctl, M_AB, s);
+        if (h->inB.n > 0) run_detect_entries(h->wB.row.p, h->wB.kind.p, h->inB.n, false, true, D, h->ctl, M_AB, s);
+    }
+    const bool any_cols = use_at && (h->b_is_a ? h->inA.n > 0 : h->inB.n > 0);
+    if (any_cols) run_detect_cols(h->AT.view(), D, h->ctl, M_AB, s, h->num_sms);
+    run_clear_marks(w.bmR.p, w.R.p, &h->ctl->n_affected, w.nrows, s);
+    if (any_cols) run_clear_marks(w.bmK.p, w.K.p, &h->ctl->n_K, w.nrows_b, s);
+}
+
+void stage_merge_commit_ab(dspg_handle *h, cudaStream_t s) {
+    if (h->inA.n > 0) {
+        UpdJob J = h->wA.job(h->inA.n);
+        run_merge_copy(J, h->A.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
+    }
+    if (!h->b_is_a && h->inB.n > 0) {
+        UpdJob J = h->wB.job(h->inB.n);
+        run_merge_copy(J, h->B.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
+    }
+    if (h->inA.n > 0)
+        run_commit(upd_commit_job(h, h->wA, ST_AB_ARENA, ST_AB_STAGE), h->A.view(), h->vsize, h->inA.n, h->ctl, M_AB,
+                   M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
+    if (!h->b_is_a && h->inB.n > 0)
+        run_commit(upd_commit_job(h, h->wB, ST_AB_ARENA, ST_AB_STAGE), h->B.view(), h->vsize, h->inB.n, h->ctl, M_AB,
+                   M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
+}
+
+void stage_transpose(dspg_handle *h, cudaStream_t s) {
+    if (!h->has_at || h->inA.n <= 0) return;
+    const int64_t n = h->inA.n;
+    UpdWs &w = h->wAT;
+    UpdJob JA = h->wA.job(n);
+    run_transpose_feed(JA, (int32_t)h->AT.nrows, w.in_row.p, w.in_col.p, w.in_op.p, h->ctl, M_AB, s);
+    sort_updates(w.in_row.p, w.in_col.p, nullptr, w.in_op.p, n, h->AT.nrows + 1, h->AT.ncols, h->sr, false,
+                 w.sort_out(), w.sort_tmp(), h->ctl, M_AT, s);
+    UpdJob J = w.job(n);
+    run_segments(J, h->AT.nrows, h->ctl, M_AT, s);
+    run_classify(J, h->AT.view(), 0, h->ctl, M_AT, ST_AT_STAGE, s, h->num_sms);
+    run_merge_copy(J, h->AT.view(), 0, h->ctl, M_AT, s, h->num_sms);
+    run_commit(upd_commit_job(h, w, ST_AT_ARENA, ST_AT_STAGE), h->AT.view(), 0, n, h->ctl, M_AT, M_AT,
+               h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
+}
+
+void stage_recompute(dspg_handle *h, cudaStream_t s) {
+    MatView Av = h->A.view(), Bv = h->Bm().view();
+    const int64_t maxR = h->A.nrows;
+    run_size_bins(Av, Bv, c_job(h, h->wc.R.p), maxR, h->ctl, M_C, s, h->num_sms);
+    run_numeric(h->sr, Av, Bv, c_job(h, h->wc.R.p), h->ctl, M_C, s, h->num_sms);
+    run_commit(c_commit_job(h, h->wc.R.p), h->C.view(), h->vsize, maxR, h->ctl, M_C, M_C, h->opt.slack_min,
+               h->opt.slack_div, s, h->num_sms);
+}
+
+void reset_range(dspg_handle *h, void *first, size_t bytes, cudaStream_t s) {
+    CK(cudaMemsetAsync(first, 0, bytes, s));
+}
+
+void reset_c_counters(dspg_handle *h, cudaStream_t s) {
+    Ctl *c = h->ctl;
+    char *from = (char *)&c->c_stage_top;
+    reset_range(h, from, sizeof(Ctl) - (size_t)(from - (char *)c), s);
+}
+
+void upload(dspg_handle *h, UpdWs &w, const dspg_updates *u, BatchIn &in, cudaStream_t s) {
+    in.n = u ? u->n : 0;
+    if (in.n <= 0) return;
+    if (u->on_device) {
+        in.row = u->row;
+        in.col = u->col;
+        in.val = u->val;
+        in.op = u->op;
+        return;
+    }
+    CK(cudaMemcpyAsync(w.in_row.p, u->row, sizeof(int32_t) * in.n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.in_col.p, u->col, sizeof(int32_t) * in.n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.in_val.p, u->val, (size_t)h->vsize * in.n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.in_op.p, u->op, sizeof(uint8_t) * in.n, cudaMemcpyHostToDevice, s));
+    in.row = w.in_row.p;
+    in.col = w.in_col.p;
+    in.val = w.in_val.p;
+    in.op = w.in_op.p;
+}
+
+dspg_status fail(dspg_handle *h, const Err &e) {
+    if (h) h->err = e.what();
+    else g_err = e.what();
+    return e.st;
+}
+
+void check_csr_arg(const dspg_csr *m, const char *name) {
+    if (!m) throw Err(DSPG_ERR_INVALID, std::string(name) + " is NULL");
+    if (m->nrows < 0 || m->ncols < 0 || m->nnz < 0) throw Err(DSPG_ERR_INVALID, std::string(name) + ": negative size");
+    if (m->nrows >= INT32_MAX || m->ncols >= INT32_MAX) throw Err(DSPG_ERR_INVALID, std::string(name) + ": too many rows or columns");
+    if (!m->rowptr || (m->nnz > 0 && (!m->col || !m->val))) throw Err(DSPG_ERR_INVALID, std::string(name) + ": NULL array");
+}
+
+// Device copy of an input CSR, validated.  Fills rowptr/col/val device buffers.
+void load_csr(dspg_handle *h, const dspg_csr *m, DBuf<int64_t> &rp, DBuf<int32_t> &col, DBuf<char> &val,
+              const int64_t **rp_d, const int32_t **col_d, const void **val_d, cudaStream_t s) {
+    if (m->on_device) {
+        *rp_d = m->rowptr;
+        *col_d = m->col;
+        *val_d = m->val;
+    } else {
+        rp.reserve(m->nrows + 1);
+        col.reserve(std::max<int64_t>(m->nnz, 1));
+        val.reserve(std::max<int64_t>(m->nnz, 1) * h->vsize);
+        CK(cudaMemcpyAsync(rp.p, m->rowptr, sizeof(int64_t) * (m->nrows + 1), cudaMemcpyHostToDevice, s));
+        if (m->nnz > 0) {
+            CK(cudaMemcpyAsync(col.p, m->col, sizeof(int32_t) * m->nnz, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(val.p, m->val, (size_t)h->vsize * m->nnz, cudaMemcpyHostToDevice, s));
+        }
+        *rp_d = rp.p;
+        *col_d = col.p;
+        *val_d = val.p;
+    }
+    DBuf<unsigned> bad;
+    bad.reserve(1);
+    CK(cudaMemsetAsync(bad.p, 0, sizeof(unsigned), s));
+    validate_rowptr(m->nrows, m->nnz, *rp_d, bad.p, s);
+    unsigned hb = 0;
+    CK(cudaMemcpyAsync(&hb, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hb) throw Err(DSPG_ERR_INVALID, "row pointers are not a valid CSR");
+    validate_csr_entries(m->nrows, m->ncols, *rp_d, *col_d, *val_d, h->sr, bad.p, s);
+    CK(cudaMemcpyAsync(&hb, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hb) throw Err(DSPG_ERR_INVALID, "columns out of range, not strictly ascending, or invalid values");
+}
+
+void init_slack_from_csr(dspg_handle *h, DevMat &M, const dspg_csr *m, cudaStream_t s) {
+    DBuf<int64_t> rp;
+    DBuf<int32_t> col;
+    DBuf<char> val;
+    const int64_t *rp_d;
+    const int32_t *col_d;
+    const void *val_d;
+    load_csr(h, m, rp, col, val, &rp_d, &col_d, &val_d, s);
+    DBuf<int32_t> len;
+    len.reserve(std::max<int64_t>(m->nrows, 1));
+    lens_from_rowptr(rp_d, len.p, m->nrows, s);
+    make_slack(h, M, m->nrows, m->ncols, h->vsize, rp_d, len.p, col_d, val_d, s);
+}
+
+int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, int64_t *rowptr, int32_t *col,
+                 void *val, int on_device, cudaStream_t s) {
+    DBuf<int32_t> rows_d;
+    const int32_t *rows = nullptr;
+    int64_t n = M.nrows;
+    if (rows_in) {
+        n = nr;
+        if (on_device) rows = rows_in;
+        else {
+            rows_d.reserve(std::max<int64_t>(n, 1));
+            if (n > 0) CK(cudaMemcpyAsync(rows_d.p, rows_in, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+            rows = rows_d.p;
+        }
+    }
+    DBuf<int64_t> rp;
+    const int64_t nnz = mat_rowptr(h, M, rows, n, rp, s);
+    if (!rowptr) return nnz;
+    if (on_device) {
+        CK(cudaMemcpyAsync(rowptr, rp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
+        gather_rows_out(rows, n, M.view(), rp.p, col, val, M.vsize, s, h->num_sms);
+        CK(cudaStreamSynchronize(s));
+    } else {
+        DBuf<int32_t> c;
+        DBuf<char> v;
+        c.reserve(std::max<int64_t>(nnz, 1));
+        v.reserve(std::max<int64_t>(nnz, 1) * std::max(M.vsize, 1));
+        gather_rows_out(rows, n, M.view(), rp.p, c.p, v.p, M.vsize, s, h->num_sms);
+        CK(cudaMemcpyAsync(rowptr, rp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+        if (nnz > 0) {
+            if (col) CK(cudaMemcpyAsync(col, c.p, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s));
+            if (val) CK(cudaMemcpyAsync(val, v.p, (size_t)M.vsize * nnz, cudaMemcpyDeviceToHost, s));
+        }
+        CK(cudaStreamSynchronize(s));
+    }
+    return nnz;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+
+extern "C" {
+
+dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, dspg_semiring sr,
+                       const dspg_options *opt, void *stream) {
+    dspg_handle *h = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        if (!out) throw Err(DSPG_ERR_INVALID, "out is NULL");
+        *out = nullptr;
+        if (sr != DSPG_PLUS_TIMES_F64 && sr != DSPG_MIN_PLUS_I32) throw Err(DSPG_ERR_INVALID, "unknown semiring");
+        check_csr_arg(A, "A");
+        if (B) {
+            check_csr_arg(B, "B");
+            if (A->ncols != B->nrows) throw Err(DSPG_ERR_INVALID, "A.ncols != B.nrows");
+        } else if (A->nrows != A->ncols) {
+            throw Err(DSPG_ERR_INVALID, "B == NULL (B is A) needs a square A");
+        }
+        h = new dspg_handle();
+        set_defaults(&h->opt);
+        if (opt) {
+            if (opt->slack_min >= 0) h->opt.slack_min = opt->slack_min;
+            if (opt->slack_div > 0) h->opt.slack_div = opt->slack_div;
+            if (opt->arena_headroom >= 1.0) h->opt.arena_headroom = opt->arena_headroom;
+            h->opt.keep_transpose = opt->keep_transpose;
+        }
+        h->sr = sr;
+        h->vsize = sr == DSPG_PLUS_TIMES_F64 ? 8 : 4;
+        CK(cudaGetDevice(&h->dev));
+        CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev));
+        CK(cudaMalloc((void **)&h->ctl, sizeof(Ctl)));
+        CK(cudaMallocHost((void **)&h->hctl, sizeof(Ctl)));
+        std::memset(h->hctl, 0, sizeof(Ctl));
+        h->wA.which = 0; h->wA.vsize = h->vsize;
+        h->wB.which = 1; h->wB.vsize = h->vsize;
+        h->wAT.which = 2; h->wAT.vsize = 0;
+        init_slack_from_csr(h, h->A, A, s);
+        h->b_is_a = (B == nullptr);
+        if (!h->b_is_a) init_slack_from_csr(h, h->B, B, s);
+        // C = A A needs the transposed pattern for every batch; otherwise it is built on the first B batch
+        const bool keep_t = h->b_is_a || h->opt.keep_transpose > 0;
+        if (keep_t) build_transpose(h, s);
+        static_recompute(h, s);
+        *out = h;
+        return DSPG_OK;
+    } catch (const Err &e) {
+        g_err = e.what();
+        delete h;
+        if (out) *out = nullptr;
+        return e.st;
+    }
+}
+
+dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
+                             dspg_batch_stats *stats, void *stream) {
+    if (!h) return DSPG_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        const int64_t nA = dA ? dA->n : 0, nB = dB ? dB->n : 0;
+        if (nA < 0 || nB < 0) throw Err(DSPG_ERR_INVALID, "negative batch size");
+        if (nA > INT32_MAX / 2 || nB > INT32_MAX / 2) throw Err(DSPG_ERR_INVALID, "batch too large");
+        if (nA > 0 && (!dA->row || !dA->col || !dA->val || !dA->op)) throw Err(DSPG_ERR_INVALID, "NULL array in dA");
+        if (nB > 0 && (!dB->row || !dB->col || !dB->val || !dB->op)) throw Err(DSPG_ERR_INVALID, "NULL array in dB");
+        if (h->b_is_a && nB > 0) throw Err(DSPG_ERR_INVALID, "B is A: pass the batch as dA only");
+        if (!h->b_is_a && nB > 0 && !h->has_at) build_transpose(h, s);
+        ensure_c_ws(h, s);
+        h->wA.ensure(nA, h->A.arena_cap);
+        if (!h->b_is_a) h->wB.ensure(nB, h->B.arena_cap);
+        if (h->has_at) h->wAT.ensure(nA, h->AT.arena_cap);
+        grow_c_stage(h, 65536);
+        upload(h, h->wA, dA, h->inA, s);
+        upload(h, h->wB, dB, h->inB, s);
+        if (h->b_is_a) h->inB = BatchIn{};
+        const int64_t compactions0 = h->compactions;
+
+        CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+        stage_sort_classify(h, s);
+        stage_detect(h, s);
+        stage_merge_commit_ab(h, s);
+        stage_transpose(h, s);
+        stage_recompute(h, s);
+        CK(cudaGetLastError());
+        read_ctl(h, s);
+
+        for (int iter = 0; iter < 8 && h->hctl->status; iter++) {
+            const unsigned st = h->hctl->status;
+            if (st & ST_INVALID) throw Err(DSPG_ERR_INVALID, "batch entry out of range or with an invalid value/op");
+            if (st & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, "accumulator probe limit reached");
+            if (st & ST_AB_STAGE) {
+                h->wA.grow_stage(h->hctl->u[0].stage_top + 1024);
+                h->wB.grow_stage(h->hctl->u[1].stage_top + 1024);
+                CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+                stage_sort_classify(h, s);
+                stage_detect(h, s);
+                stage_merge_commit_ab(h, s);
+                stage_transpose(h, s);
+                stage_recompute(h, s);
+                read_ctl(h, s);
+                continue;
+            }
+            if (st & ST_AB_ARENA) {
+                regrow(h, h->A, s);
+                if (!h->b_is_a && nB > 0) regrow(h, h->B, s);
+                for (int k = 0; k < 2; k++) {
+                    reset_range(h, &h->ctl->u[k].n_cchunk, sizeof(long long), s);
+                    reset_range(h, &h->ctl->u[k].reloc, sizeof(long long), s);
+                }
+                reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
+                reset_c_counters(h, s);
+                reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+                if (nA > 0)
+                    run_commit(upd_commit_job(h, h->wA, ST_AB_ARENA, ST_AB_STAGE), h->A.view(), h->vsize, nA, h->ctl,
+                               M_AB, M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
+                if (!h->b_is_a && nB > 0)
+                    run_commit(upd_commit_job(h, h->wB, ST_AB_ARENA, ST_AB_STAGE), h->B.view(), h->vsize, nB, h->ctl,
+                               M_AB, M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
+                stage_transpose(h, s);
+                stage_recompute(h, s);
+                read_ctl(h, s);
+                continue;
+            }
+            const bool at = st & (ST_AT_STAGE | ST_AT_ARENA);
+            const bool cc = st & (ST_C_STAGE | ST_C_ARENA | ST_C_SCRATCH);
+            if (st & ST_AT_STAGE) h->wAT.grow_stage(h->hctl->u[2].stage_top + 1024);
+            if (st & ST_AT_ARENA) regrow(h, h->AT, s);
+            if (st & ST_C_STAGE) grow_c_stage(h, h->hctl->c_stage_top + 1024);
+            if (st & ST_C_ARENA) regrow(h, h->C, s);
+            reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+            if (at) {
+                reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
+                stage_transpose(h, s);
+            }
+            if (cc) {
+                reset_c_counters(h, s);
+                stage_recompute(h, s);
+            }
+            read_ctl(h, s);
+        }
+        if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "apply_batch did not converge, status " + std::to_string(h->hctl->status));
+        h->last_nR = h->hctl->n_affected;
+        if (stats) {
+            const Ctl &c = *h->hctl;
+            std::memset(stats, 0, sizeof(*stats));
+            stats->n_updates = nA + nB;
+            for (int k = 0; k < 2; k++) {
+                stats->n_insert += c.u[k].ins;
+                stats->n_update += c.u[k].upd;
+                stats->n_delete += c.u[k].del;
+                stats->n_noop += c.u[k].nop;
+                stats->touched_rows += c.u[k].n_merge;
+                stats->relocations += c.u[k].reloc;
+            }
+            stats->n_unique = stats->n_insert + stats->n_update + stats->n_delete + stats->n_noop;
+            stats->relocations += c.u[2].reloc + c.c_reloc;
+            stats->affected_rows = c.n_affected;
+            stats->products = c.products;
+            stats->nnz_written = c.nnz_written;
+            stats->compactions = h->compactions - compactions0;
+        }
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_read_C(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32_t *col, void *val, int on_device,
+                        void *stream) {
+    if (!h || !nnz_out) return DSPG_ERR_INVALID;
+    try {
+        *nnz_out = read_mat(h, h->C, nullptr, 0, rowptr, col, val, on_device, (cudaStream_t)stream);
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_read_A(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32_t *col, void *val, int on_device,
+                        void *stream) {
+    if (!h || !nnz_out) return DSPG_ERR_INVALID;
+    try {
+        *nnz_out = read_mat(h, h->A, nullptr, 0, rowptr, col, val, on_device, (cudaStream_t)stream);
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_read_rows_C(dspg_handle *h, const int32_t *rows, int64_t nrows, int64_t *nnz_out, int64_t *rowptr,
+                             int32_t *col, void *val, int on_device, void *stream) {
+    if (!h || !nnz_out || nrows < 0 || (nrows > 0 && !rows)) return DSPG_ERR_INVALID;
+    try {
+        if (!on_device) {
+            for (int64_t i = 0; i < nrows; i++)
+                if (rows[i] < 0 || rows[i] >= h->C.nrows) throw Err(DSPG_ERR_INVALID, "row index out of range");
+        }
+        *nnz_out = read_mat(h, h->C, rows ? rows : (const int32_t *)h->wc.iota.p, nrows, rowptr, col, val, on_device,
+                            (cudaStream_t)stream);
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_last_affected(dspg_handle *h, int64_t *count, int32_t *rows, int on_device, void *stream) {
+    if (!h || !count) return DSPG_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        const int64_t n = h->last_nR;
+        if (!rows) {
+            *count = n;
+            return DSPG_OK;
+        }
+        if (*count < n) throw Err(DSPG_ERR_INVALID, "rows buffer too small");
+        *count = n;
+        if (n == 0) return DSPG_OK;
+        DBuf<int32_t> tmp;
+        tmp.reserve(n);
+        CK(cudaMemcpyAsync(tmp.p, h->wc.R.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        DBuf<uint64_t> k0, k1;
+        DBuf<uint32_t> i0, i1, counts;
+        DBuf<int64_t> st, so;
+        k0.reserve(n); k1.reserve(n); i0.reserve(n); i1.reserve(n);
+        int64_t cnt;
+        sort_tmp_sizes(n, &cnt);
+        counts.reserve(cnt);
+        so.reserve(cnt + 1);
+        st.reserve(scan_tmp_entries(cnt) + 1);
+        sort_i32_values(tmp.p, n, bits_for(h->A.nrows), k0.p, k1.p, i0.p, i1.p, counts.p, st.p, so.p, s);
+        CK(cudaMemcpyAsync(rows, tmp.p, sizeof(int32_t) * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_recompute_all(dspg_handle *h, void *stream) {
+    if (!h) return DSPG_ERR_INVALID;
+    try {
+        static_recompute(h, (cudaStream_t)stream);
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_info(dspg_handle *h, int64_t *n, int64_t *k, int64_t *m, int64_t *nnz_a, int64_t *nnz_c) {
+    if (!h) return DSPG_ERR_INVALID;
+    try {
+        if (n) *n = h->A.nrows;
+        if (k) *k = h->A.ncols;
+        if (m) *m = h->Bm().ncols;
+        if (nnz_a) *nnz_a = read_mat(h, h->A, nullptr, 0, nullptr, nullptr, nullptr, 0, 0);
+        if (nnz_c) *nnz_c = read_mat(h, h->C, nullptr, 0, nullptr, nullptr, nullptr, 0, 0);
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+void dspg_destroy(dspg_handle *h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    if (h->ctl) cudaFree(h->ctl);
+    if (h->hctl) cudaFreeHost(h->hctl);
+    delete h;
+}
+
+const char *dspg_last_error(const dspg_handle *h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

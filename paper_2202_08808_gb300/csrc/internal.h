@@ -1,0 +1,129 @@
+// internal.h -- job descriptors passed by value to the kernels, and the host
+// entry points of each translation unit.
+#pragma once
+
+#include "common.cuh"
+
+namespace dspg {
+
+// One sorted batch being applied to one slack-CSR (A, B, or A's transposed
+// pattern).  Per sorted entry arrays have n entries; per merge item arrays
+// have n entries too (at most one item per entry).
+struct UpdJob {
+    int which;  // index into Ctl::u
+    int64_t n;  // sorted entries
+    // sorted batch (output of sort_updates)
+    int32_t *row, *col;
+    void *val;  // nullptr for a pattern
+    uint8_t *op;
+    // classification
+    uint8_t *kind;
+    int32_t *pos, *insx, *delx;
+    // row segments [seg_lo, seg_hi) of the sorted batch
+    int32_t *seg_lo, *seg_hi;
+    // merge items: rows with an effective change
+    int32_t *m_row, *m_seg, *m_len, *m_nins, *m_ndel;
+    int64_t *m_soff;
+    // commit plan per item
+    int64_t *m_dest;
+    int32_t *m_cap;
+    // copy work items (item, part)
+    int32_t *ch_item, *ch_part;
+    int64_t ch_cap;
+    int32_t *cc_item, *cc_part;
+    int64_t cc_cap;
+    // staging for rebuilt rows
+    int32_t *st_col;
+    void *st_val;
+    int64_t st_cap;
+};
+
+// Staged rows -> slack-CSR.
+struct CommitJob {
+    const int32_t *rows;      // matrix row of each item
+    const int32_t *lens;      // new length of each item
+    const int64_t *soff;      // staging offset of each item
+    const long long *count;   // number of items (device)
+    const int32_t *st_col;
+    const void *st_val;
+    int64_t *dest;
+    int32_t *ncap;
+    int32_t *cc_item, *cc_part;
+    long long *cc_count;
+    int64_t cc_cap;
+    long long *reloc;
+    unsigned arena_bit, stage_bit;
+};
+
+struct DetectBufs {
+    uint32_t *bmR;   // bitmap over rows of A (rows of C)
+    uint32_t *bmK;   // bitmap over rows of B
+    int32_t *R;      // affected rows (unordered)
+    int32_t *K;      // rows of B*
+    long long *nK;
+};
+
+// The recompute of rows of C (static build: all rows).
+struct CJob {
+    const int32_t *R;         // rows to recompute
+    int64_t nR_max;           // capacity of the per-row arrays
+    int32_t *slen;            // output length per R index
+    int64_t *soff;            // staging offset per R index
+    int32_t *bins;            // NBINS lists of R indices, bin_cap each
+    int64_t bin_cap;
+    int32_t *st_col;
+    void *st_val;
+    int64_t st_cap;
+    void *gd_acc;             // per-CTA dense accumulators (global), gd_w entries each
+    uint32_t *gd_mask;        // per-CTA presence bits, gd_w / 32 words each
+    int64_t gd_w;
+    int gd_ctas;
+    int64_t m;                // columns of C
+    int dense_mode;           // 1: all rows use the dense small-m kernels
+};
+
+// update.cu
+void run_segments(const UpdJob &J, int64_t nrows, Ctl *ctl, unsigned mask, cudaStream_t s);
+void run_classify(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsigned mask, unsigned stage_bit,
+                  cudaStream_t s, int num_sms);
+void run_merge_copy(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsigned mask, cudaStream_t s,
+                    int num_sms);
+void run_commit(const CommitJob &J, const MatView &M, int vsize, int64_t max_items, Ctl *ctl, unsigned plan_mask,
+                unsigned copy_mask, int slack_min, int slack_div, cudaStream_t s, int num_sms);
+void run_detect_entries(const int32_t *srow, const uint8_t *kind, int64_t n, bool mark_rows, bool mark_cols,
+                        const DetectBufs &D, Ctl *ctl, unsigned mask, cudaStream_t s);
+void run_detect_cols(const MatView &AT, const DetectBufs &D, Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms);
+void run_clear_marks(uint32_t *bm, const int32_t *list, const long long *cnt, int64_t max_n, cudaStream_t s);
+void run_transpose_feed(const UpdJob &J, int32_t pad_row, int32_t *trow, int32_t *tcol, uint8_t *top, Ctl *ctl,
+                        unsigned mask, cudaStream_t s);
+
+// spgemm.cu
+constexpr int64_t DENSE_M_MAX = 1024;  // C columns up to this use dense accumulators
+void run_size_bins(const MatView &A, const MatView &B, const CJob &J, int64_t max_rows, Ctl *ctl, unsigned mask,
+                   cudaStream_t s, int num_sms);
+void run_numeric(int sr, const MatView &A, const MatView &B, const CJob &J, Ctl *ctl, unsigned mask, cudaStream_t s,
+                 int num_sms);
+void init_dense_scratch(int sr, void *acc, uint32_t *mask, int64_t entries, int64_t words, cudaStream_t s);
+
+// layout.cu: building and reading slack-CSRs
+void fill_iota(int32_t *a, int64_t n, cudaStream_t s);
+void caps_from_lens(const int32_t *len, int32_t *cap, int64_t n, int slack_min, int slack_div, cudaStream_t s);
+void lens_from_rowptr(const int64_t *rowptr, int32_t *len, int64_t n, cudaStream_t s);
+// Copy rows: dst row i gets src[src_off[i] .. +len[i]) at dst_off[i] (per index i < n, with an
+// optional row map rows[i]).
+void copy_rows(const int32_t *rows, int64_t n, const int64_t *src_off, const int32_t *len, const int32_t *src_col,
+               const void *src_val, const int64_t *dst_off, int32_t *dst_col, void *dst_val, int vsize,
+               cudaStream_t s, int num_sms);
+void gather_rows_out(const int32_t *rows, int64_t n, const MatView &M, const int64_t *out_rowptr, int32_t *out_col,
+                     void *out_val, int vsize, cudaStream_t s, int num_sms);
+void lens_of_rows(const int32_t *rows, int64_t n, const int32_t *len, int32_t *out, cudaStream_t s);
+void validate_rowptr(int64_t nrows, int64_t nnz, const int64_t *rowptr, unsigned *bad, cudaStream_t s);
+void validate_csr_entries(int64_t nrows, int64_t ncols, const int64_t *rowptr, const int32_t *col, const void *val,
+                          int sr, unsigned *bad, cudaStream_t s);
+void hist_cols(const int32_t *col, int64_t nnz, int32_t *counts, cudaStream_t s);
+void rows_of_entries(const int64_t *rowptr, int64_t nrows, uint32_t *rows_out, cudaStream_t s, int num_sms);
+void keys_from_cols(const int32_t *col, int64_t nnz, uint64_t *keys, cudaStream_t s);
+void sort_i32_values(int32_t *a, int64_t n, int bits, uint64_t *k0, uint64_t *k1, uint32_t *i0, uint32_t *i1,
+                     uint32_t *counts, int64_t *scan_tmp, int64_t *scan_out, cudaStream_t s);
+
+}  // namespace dspg

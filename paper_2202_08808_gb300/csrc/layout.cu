@@ -1,0 +1,193 @@
+// layout.cu -- building slack-CSRs from row-wise sources and reading them back.
+//
+// These kernels move whole rows between a CSR-like source (row start + row
+// length) and a destination layout, one warp per row; they carry no
+// semiring arithmetic.
+#include "internal.h"
+
+namespace dspg {
+
+static unsigned blocks_for(int64_t n, int nt, int64_t cap = 1 << 20) {
+    int64_t g = (n + nt - 1) / nt;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+__global__ void k_iota(int32_t *a, int64_t n) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        a[x] = (int32_t)x;
+}
+void fill_iota(int32_t *a, int64_t n, cudaStream_t s) {
+    if (n > 0) k_iota<<<blocks_for(n, 256, 8192), 256, 0, s>>>(a, n);
+}
+
+__global__ void k_caps(const int32_t *len, int32_t *cap, int64_t n, int smin, int sdiv) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        cap[x] = slack_cap(len[x], smin, sdiv);
+}
+void caps_from_lens(const int32_t *len, int32_t *cap, int64_t n, int smin, int sdiv, cudaStream_t s) {
+    if (n > 0) k_caps<<<blocks_for(n, 256, 8192), 256, 0, s>>>(len, cap, n, smin, sdiv);
+}
+
+__global__ void k_lens_rowptr(const int64_t *rowptr, int32_t *len, int64_t n) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        len[x] = (int32_t)(rowptr[x + 1] - rowptr[x]);
+}
+void lens_from_rowptr(const int64_t *rowptr, int32_t *len, int64_t n, cudaStream_t s) {
+    if (n > 0) k_lens_rowptr<<<blocks_for(n, 256, 8192), 256, 0, s>>>(rowptr, len, n);
+}
+
+__global__ void k_lens_of_rows(const int32_t *rows, int64_t n, const int32_t *len, int32_t *out) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        out[x] = len[rows[x]];
+}
+void lens_of_rows(const int32_t *rows, int64_t n, const int32_t *len, int32_t *out, cudaStream_t s) {
+    if (n > 0) k_lens_of_rows<<<blocks_for(n, 256, 8192), 256, 0, s>>>(rows, n, len, out);
+}
+
+template <typename T>
+__global__ void k_copy_rows(const int32_t *rows, int64_t n, const int64_t *src_off, const int32_t *len,
+                            const int32_t *src_col, const T *src_val, const int64_t *dst_off, int32_t *dst_col,
+                            T *dst_val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += nwarps) {
+        const int64_t r = rows ? rows[x] : x;
+        const int64_t so = src_off[r], d = dst_off[r];
+        const int L = len[r];
+        for (int e = lane; e < L; e += 32) {
+            dst_col[d + e] = src_col[so + e];
+            if (dst_val) dst_val[d + e] = src_val[so + e];
+        }
+    }
+}
+
+void copy_rows(const int32_t *rows, int64_t n, const int64_t *src_off, const int32_t *len, const int32_t *src_col,
+               const void *src_val, const int64_t *dst_off, int32_t *dst_col, void *dst_val, int vsize,
+               cudaStream_t s, int num_sms) {
+    if (n <= 0) return;
+    unsigned g = blocks_for(n * 32, 256, (int64_t)num_sms * 16);
+    if (vsize == 8)
+        k_copy_rows<double><<<g, 256, 0, s>>>(rows, n, src_off, len, src_col, (const double *)src_val, dst_off,
+                                              dst_col, (double *)dst_val);
+    else
+        k_copy_rows<int32_t><<<g, 256, 0, s>>>(rows, n, src_off, len, src_col, (const int32_t *)src_val, dst_off,
+                                               dst_col, (int32_t *)dst_val);
+}
+
+template <typename T>
+__global__ void k_gather_out(const int32_t *rows, int64_t n, MatView M, const int64_t *out_rowptr, int32_t *out_col,
+                             T *out_val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const T *mv = (const T *)M.val;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += nwarps) {
+        const int64_t r = rows ? rows[x] : x;
+        const int64_t so = M.off[r], d = out_rowptr[x];
+        const int L = M.len[r];
+        for (int e = lane; e < L; e += 32) {
+            out_col[d + e] = M.col[so + e];
+            if (out_val) out_val[d + e] = mv[so + e];
+        }
+    }
+}
+
+void gather_rows_out(const int32_t *rows, int64_t n, const MatView &M, const int64_t *out_rowptr, int32_t *out_col,
+                     void *out_val, int vsize, cudaStream_t s, int num_sms) {
+    if (n <= 0) return;
+    unsigned g = blocks_for(n * 32, 256, (int64_t)num_sms * 16);
+    if (vsize == 8) k_gather_out<double><<<g, 256, 0, s>>>(rows, n, M, out_rowptr, out_col, (double *)out_val);
+    else k_gather_out<int32_t><<<g, 256, 0, s>>>(rows, n, M, out_rowptr, out_col, (int32_t *)out_val);
+}
+
+// Canonical-CSR check: rowptr[0] = 0 and non-decreasing, rowptr[n] = nnz,
+// columns in range and strictly ascending per row, values valid for the
+// semiring.  Sets *bad = 1 on the first violation seen.
+__global__ void k_validate_rows(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t *rowptr, unsigned *bad) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= nrows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        if (r == 0 && rowptr[0] != 0) atomicOr(bad, 1u);
+        if (r == nrows && rowptr[nrows] != nnz) atomicOr(bad, 1u);
+        if (r < nrows && rowptr[r + 1] < rowptr[r]) atomicOr(bad, 1u);
+    }
+}
+
+__global__ void k_validate_entries(int64_t nrows, int64_t ncols, const int64_t *rowptr, const int32_t *col,
+                                   const void *val, int sr, unsigned *bad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nwarps) {
+        const int64_t lo = rowptr[r], hi = rowptr[r + 1];
+        if (hi < lo) continue;
+        for (int64_t p = lo + lane; p < hi; p += 32) {
+            const int32_t c = col[p];
+            bool ok = c >= 0 && (int64_t)c < ncols && (p == lo || col[p - 1] < c);
+            if (sr == SR_PT) ok = ok && isfinite(((const double *)val)[p]);
+            else {
+                const int32_t v = ((const int32_t *)val)[p];
+                ok = ok && v > -MP_LIMIT && v < MP_LIMIT;
+            }
+            if (!ok) atomicOr(bad, 1u);
+        }
+    }
+}
+
+// Entry check, run only after the row bounds have been verified on the host.
+void validate_csr_entries(int64_t nrows, int64_t ncols, const int64_t *rowptr, const int32_t *col, const void *val,
+                          int sr, unsigned *bad, cudaStream_t s) {
+    if (nrows > 0)
+        k_validate_entries<<<blocks_for(nrows * 32, 256, 8192), 256, 0, s>>>(nrows, ncols, rowptr, col, val, sr, bad);
+}
+
+void validate_rowptr(int64_t nrows, int64_t nnz, const int64_t *rowptr, unsigned *bad, cudaStream_t s) {
+    k_validate_rows<<<blocks_for(nrows + 1, 256, 4096), 256, 0, s>>>(nrows, 0, nnz, rowptr, bad);
+}
+
+__global__ void k_hist_cols(const int32_t *col, int64_t nnz, int32_t *counts) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nnz; x += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&counts[col[x]], 1);
+}
+void hist_cols(const int32_t *col, int64_t nnz, int32_t *counts, cudaStream_t s) {
+    if (nnz > 0) k_hist_cols<<<blocks_for(nnz, 256, 8192), 256, 0, s>>>(col, nnz, counts);
+}
+
+__global__ void k_rows_of_entries(const int64_t *rowptr, int64_t nrows, uint32_t *rows_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nwarps)
+        for (int64_t p = rowptr[r] + lane; p < rowptr[r + 1]; p += 32) rows_out[p] = (uint32_t)r;
+}
+void rows_of_entries(const int64_t *rowptr, int64_t nrows, uint32_t *rows_out, cudaStream_t s, int num_sms) {
+    if (nrows > 0)
+        k_rows_of_entries<<<blocks_for(nrows * 32, 256, (int64_t)num_sms * 16), 256, 0, s>>>(rowptr, nrows, rows_out);
+}
+
+__global__ void k_keys_from_cols(const int32_t *col, int64_t nnz, uint64_t *keys) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nnz; x += (int64_t)gridDim.x * blockDim.x)
+        keys[x] = (uint64_t)(uint32_t)col[x];
+}
+void keys_from_cols(const int32_t *col, int64_t nnz, uint64_t *keys, cudaStream_t s) {
+    if (nnz > 0) k_keys_from_cols<<<blocks_for(nnz, 256, 8192), 256, 0, s>>>(col, nnz, keys);
+}
+
+__global__ void k_keys_from_i32(const int32_t *a, int64_t n, uint64_t *keys, uint32_t *idx) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        keys[x] = (uint64_t)(uint32_t)a[x];
+        idx[x] = (uint32_t)x;
+    }
+}
+__global__ void k_keys_to_i32(const uint64_t *keys, int64_t n, int32_t *a) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        a[x] = (int32_t)keys[x];
+}
+void sort_i32_values(int32_t *a, int64_t n, int bits, uint64_t *k0, uint64_t *k1, uint32_t *i0, uint32_t *i1,
+                     uint32_t *counts, int64_t *scan_tmp, int64_t *scan_out, cudaStream_t s) {
+    if (n <= 1) return;
+    k_keys_from_i32<<<blocks_for(n, 256, 8192), 256, 0, s>>>(a, n, k0, i0);
+    bool alt = false;
+    radix_sort_pairs(k0, i0, k1, i1, n, bits, counts, scan_tmp, scan_out, s, &alt);
+    k_keys_to_i32<<<blocks_for(n, 256, 8192), 256, 0, s>>>(alt ? k1 : k0, n, a);
+}
+
+}  // namespace dspg

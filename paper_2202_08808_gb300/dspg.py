@@ -1,0 +1,293 @@
+"""Python binding of the C ABI in include/dspg.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``libdspg.so``; this module only
+turns numpy arrays (host memory) or torch tensors (device or host memory)
+into pointers and sizes, and status codes into exceptions. There is no CPU
+fallback: if the library cannot be loaded, ``load()`` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+PLUS_TIMES_F64 = 0
+MIN_PLUS_I32 = 1
+
+OP_INSERT = 0
+OP_DELETE = 1
+OP_SET = 2
+
+_STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT", 5: "ERR_STATE"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class DspgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Csr(C.Structure):
+    _fields_ = [("nrows", C.c_int64), ("ncols", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p), ("on_device", C.c_int)]
+
+
+class _Upd(C.Structure):
+    _fields_ = [("n", C.c_int64), ("row", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
+                ("op", C.c_void_p), ("on_device", C.c_int)]
+
+
+class _Opt(C.Structure):
+    _fields_ = [("slack_min", C.c_int32), ("slack_div", C.c_int32), ("arena_headroom", C.c_double),
+                ("keep_transpose", C.c_int32)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in (
+        "n_updates", "n_unique", "n_insert", "n_update", "n_delete", "n_noop", "touched_rows", "affected_rows",
+        "products", "nnz_written", "relocations", "compactions")]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libdspg.so (compiling it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        lib = C.CDLL(path)
+        p, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+        lib.dspg_build.restype = i32
+        lib.dspg_build.argtypes = [C.POINTER(p), C.POINTER(_Csr), C.POINTER(_Csr), i32, C.POINTER(_Opt), p]
+        lib.dspg_apply_batch.restype = i32
+        lib.dspg_apply_batch.argtypes = [p, C.POINTER(_Upd), C.POINTER(_Upd), C.POINTER(_Stats), p]
+        for name in ("dspg_read_C", "dspg_read_A"):
+            f = getattr(lib, name)
+            f.restype = i32
+            f.argtypes = [p, C.POINTER(i64), p, p, p, i32, p]
+        lib.dspg_read_rows_C.restype = i32
+        lib.dspg_read_rows_C.argtypes = [p, p, i64, C.POINTER(i64), p, p, p, i32, p]
+        lib.dspg_last_affected.restype = i32
+        lib.dspg_last_affected.argtypes = [p, C.POINTER(i64), p, i32, p]
+        lib.dspg_recompute_all.restype = i32
+        lib.dspg_recompute_all.argtypes = [p, p]
+        lib.dspg_info.restype = i32
+        lib.dspg_info.argtypes = [p] + [C.POINTER(i64)] * 5
+        lib.dspg_destroy.restype = None
+        lib.dspg_destroy.argtypes = [p]
+        lib.dspg_last_error.restype = C.c_char_p
+        lib.dspg_last_error.argtypes = [p]
+        _lib = lib
+        return lib
+
+
+EXPORTED = ["dspg_build", "dspg_apply_batch", "dspg_read_C", "dspg_read_A", "dspg_read_rows_C",
+            "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_destroy", "dspg_last_error"]
+
+
+def _vdtype(sr: int):
+    return np.float64 if sr == PLUS_TIMES_F64 else np.int32
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, keep: list):
+    """Pointer of a numpy array or torch tensor (contiguous); returns (ptr, on_device)."""
+    if x is None:
+        return None, 0
+    if _is_torch(x):
+        x = x.contiguous()
+        keep.append(x)
+        return x.data_ptr(), int(x.is_cuda)
+    a = np.ascontiguousarray(x)
+    keep.append(a)
+    return a.ctypes.data, 0
+
+
+def _stream(stream):
+    if stream is not None:
+        return getattr(stream, "cuda_stream", stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class DynamicSpGEMM:
+    """C = A B over a semiring, kept up to date under update batches.
+
+    ``A`` (and ``B``) are objects with ``nrows, ncols, rowptr, col, val``
+    (e.g. ``workloads.CSR``; arrays may be numpy or torch). ``B=None`` means
+    C = A A with one batch updating both operands."""
+
+    def __init__(self, A, B=None, semiring: int | None = None, slack_min: int = 4, slack_div: int = 4,
+                 arena_headroom: float = 1.5, keep_transpose: int = -1, stream=None):
+        self._lib = load()
+        self._h = C.c_void_p()
+        if semiring is None:
+            semiring = PLUS_TIMES_F64 if np.dtype(_dtype_of(A.val)) == np.float64 else MIN_PLUS_I32
+        self.sr = semiring
+        keep: list = []
+        ca = self._csr(A, keep)
+        cb = self._csr(B, keep) if B is not None else None
+        opt = _Opt(slack_min, slack_div, arena_headroom, keep_transpose)
+        st = self._lib.dspg_build(C.byref(self._h), C.byref(ca), C.byref(cb) if cb is not None else None,
+                                  semiring, C.byref(opt), _stream(stream))
+        if st != 0:
+            raise DspgError(st, self._lib.dspg_last_error(None).decode())
+        self.b_is_a = B is None
+
+    def _csr(self, M, keep) -> _Csr:
+        rp, dev = _ptr(_as_int(M.rowptr, np.int64), keep)
+        col, _ = _ptr(_as_int(M.col, np.int32), keep)
+        val, _ = _ptr(_as_val(M.val, self.sr), keep)
+        nnz = int(M.rowptr[-1])
+        return _Csr(M.nrows, M.ncols, nnz, rp, col, val, dev)
+
+    def _check(self, st):
+        if st != 0:
+            raise DspgError(st, self._lib.dspg_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.dspg_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _upd(self, b, keep) -> _Upd:
+        row, dev = _ptr(_as_int(b.row, np.int32), keep)
+        col, _ = _ptr(_as_int(b.col, np.int32), keep)
+        val, _ = _ptr(_as_val(b.val, self.sr), keep)
+        op, _ = _ptr(_as_int(b.op, np.uint8), keep)
+        return _Upd(len(b.row), row, col, val, op, dev)
+
+    def apply_batch(self, dA=None, dB=None, stream=None) -> dict:
+        keep: list = []
+        ua = self._upd(dA, keep) if dA is not None else None
+        ub = self._upd(dB, keep) if dB is not None else None
+        stats = _Stats()
+        st = self._lib.dspg_apply_batch(self._h, C.byref(ua) if ua is not None else None,
+                                        C.byref(ub) if ub is not None else None, C.byref(stats), _stream(stream))
+        self._check(st)
+        return {name: getattr(stats, name) for name, _ in _Stats._fields_}
+
+    def _read(self, fn, ncols: int, stream=None) -> "CsrArrays":
+        s = _stream(stream)
+        nnz = C.c_int64()
+        self._check(fn(self._h, C.byref(nnz), None, None, None, 0, s))
+        n = self.info()["n"]
+        rp = np.empty(n + 1, np.int64)
+        col = np.empty(nnz.value, np.int32)
+        val = np.empty(nnz.value, _vdtype(self.sr))
+        self._check(fn(self._h, C.byref(nnz), rp.ctypes.data, col.ctypes.data, val.ctypes.data, 0, s))
+        return CsrArrays(n, ncols, rp, col, val)
+
+    def read_C(self, stream=None) -> "CsrArrays":
+        """C' in canonical CSR (host numpy arrays)."""
+        return self._read(self._lib.dspg_read_C, self.info()["m"], stream)
+
+    def read_A(self, stream=None) -> "CsrArrays":
+        """A' in canonical CSR (host numpy arrays)."""
+        return self._read(self._lib.dspg_read_A, self.info()["k"], stream)
+
+    def read_C_device(self, stream=None):
+        """C as torch device tensors (rowptr, col, val)."""
+        import torch
+        nnz = C.c_int64()
+        s = _stream(stream)
+        self._check(self._lib.dspg_read_C(self._h, C.byref(nnz), None, None, None, 1, s))
+        n = self.info()["n"]
+        rp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device="cuda")
+        val = torch.empty(max(nnz.value, 1), dtype=torch.float64 if self.sr == PLUS_TIMES_F64 else torch.int32,
+                          device="cuda")
+        self._check(self._lib.dspg_read_C(self._h, C.byref(nnz), rp.data_ptr(), col.data_ptr(), val.data_ptr(), 1, s))
+        return rp, col[: nnz.value], val[: nnz.value]
+
+    def read_rows_C(self, rows, stream=None):
+        rows = np.ascontiguousarray(rows, np.int32)
+        nnz = C.c_int64()
+        s = _stream(stream)
+        self._check(self._lib.dspg_read_rows_C(self._h, rows.ctypes.data, rows.shape[0], C.byref(nnz), None, None,
+                                               None, 0, s))
+        rp = np.empty(rows.shape[0] + 1, np.int64)
+        col = np.empty(nnz.value, np.int32)
+        val = np.empty(nnz.value, _vdtype(self.sr))
+        self._check(self._lib.dspg_read_rows_C(self._h, rows.ctypes.data, rows.shape[0], C.byref(nnz),
+                                               rp.ctypes.data, col.ctypes.data, val.ctypes.data, 0, s))
+        return rp, col, val
+
+    def last_affected(self, stream=None) -> np.ndarray:
+        cnt = C.c_int64()
+        s = _stream(stream)
+        self._check(self._lib.dspg_last_affected(self._h, C.byref(cnt), None, 0, s))
+        out = np.empty(cnt.value, np.int32)
+        self._check(self._lib.dspg_last_affected(self._h, C.byref(cnt), out.ctypes.data, 0, s))
+        return out
+
+    def recompute_all(self, stream=None) -> None:
+        self._check(self._lib.dspg_recompute_all(self._h, _stream(stream)))
+
+    def info(self) -> dict:
+        v = [C.c_int64() for _ in range(5)]
+        self._check(self._lib.dspg_info(self._h, *[C.byref(x) for x in v]))
+        return dict(zip(("n", "k", "m", "nnz_a", "nnz_c"), [x.value for x in v]))
+
+
+class CsrArrays:
+    """A canonical CSR read back from the library (rowptr int64, col int32,
+    val float64 or int32)."""
+
+    def __init__(self, nrows, ncols, rowptr, col, val):
+        self.nrows, self.ncols, self.rowptr, self.col, self.val = nrows, ncols, rowptr, col, val
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def row_ids(self) -> np.ndarray:
+        return np.repeat(np.arange(self.nrows, dtype=np.int64), np.diff(self.rowptr))
+
+
+def _dtype_of(v):
+    if _is_torch(v):
+        import torch
+        return np.float64 if v.dtype == torch.float64 else np.int32
+    return np.asarray(v).dtype
+
+
+def _as_int(x, dt):
+    if _is_torch(x):
+        import torch
+        tdt = {np.int64: torch.int64, np.int32: torch.int32, np.uint8: torch.uint8}[dt]
+        return x.to(tdt)
+    return np.ascontiguousarray(x, dtype=dt)
+
+
+def _as_val(x, sr):
+    if _is_torch(x):
+        import torch
+        return x.to(torch.float64 if sr == PLUS_TIMES_F64 else torch.int32)
+    return np.ascontiguousarray(x, dtype=_vdtype(sr))

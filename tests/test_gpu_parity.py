@@ -1,0 +1,292 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every test builds a handle on the GPU, applies batches with the library, and
+compares C', A' and the affected row set R element by element with the
+oracle's results on the same seeded inputs: patterns and (min,+) values
+bit-exact, (+,.) values within 1e-12 * sum|ab| (see parity.py).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import OMat
+from parity import assert_matches, assert_same_pattern, oracle_product
+from workloads import (MIN_PLUS_I32, OP_DELETE, OP_SET, PLUS_TIMES_F64, Batch, bernoulli_sparse, er_batch,
+                       er_matrix, random_batch, random_csr, rmat_edge_batch, rmat_symmetric, stencil7,
+                       stencil_batch)
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_state(g, A_or, B_or, what, rel=False):
+    """C', A' (and R if given) of handle g against the oracle's A', B'."""
+    C_o, S_o = oracle_product(A_or, B_or if B_or is not None else A_or)
+    assert_matches(g.read_C(), C_o, S_o, what=f"{what} C", rel_check=rel)
+    Ag = g.read_A()
+    Ao = A_or.to_csr()
+    assert_same_pattern(Ag, Ao, what=f"{what} A")
+    assert np.array_equal(Ag.val, Ao.val), f"{what} A values"
+
+
+def _apply_both(g, A_or, C_or, b, B_or=None, bb=None):
+    st = g.apply_batch(b, bb)
+    R = oracle.row_dynamic(A_or, C_or, b, B_or, bb)
+    assert np.array_equal(g.last_affected(), R), "affected rows differ"
+    assert st["affected_rows"] == R.shape[0]
+    return st
+
+
+# ------------------------------------------------------------------ static
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_static_build_er_config1(dspg, sr):
+    A = er_matrix(4096, 8, seed=1, kind=sr)
+    g = dspg.DynamicSpGEMM(A)
+    Ao = OMat.from_csr(A)
+    _check_state(g, Ao, None, "build", rel=(sr == PLUS_TIMES_F64))
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_static_build_skewed_all_bins(dspg, sr):
+    """R-MAT rows give product bounds from 0 to tens of thousands, so every
+    hash / dense bin of the recompute runs (the square has hubs)."""
+    A, _ = rmat_symmetric(12, 16, (0.57, 0.19, 0.19, 0.05), seed=5, kind=sr)
+    g = dspg.DynamicSpGEMM(A)
+    _check_state(g, OMat.from_csr(A), None, "rmat12")
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_static_build_small_m_dense(dspg, sr):
+    """C with 256 columns: the dense shared-memory accumulators (warp and CTA)."""
+    A, _ = rmat_symmetric(12, 16, (0.57, 0.19, 0.19, 0.05), seed=6, kind=sr)
+    B = bernoulli_sparse(A.ncols, 256, 0.08, seed=7, kind=sr)
+    g = dspg.DynamicSpGEMM(A, B)
+    Ao, Bo = OMat.from_csr(A), OMat.from_csr(B)
+    C_o, S_o = oracle_product(Ao, Bo)
+    assert_matches(g.read_C(), C_o, S_o, what="dense C")
+
+
+def test_static_empty_and_ragged(dspg):
+    for seed in range(4):
+        A = random_csr(37, 53, 9, seed, PLUS_TIMES_F64, empty_frac=0.4)
+        B = random_csr(53, 29, 7, seed + 1, PLUS_TIMES_F64, empty_frac=0.4)
+        g = dspg.DynamicSpGEMM(A, B)
+        C_o, S_o = oracle_product(OMat.from_csr(A), OMat.from_csr(B))
+        assert_matches(g.read_C(), C_o, S_o, what=f"ragged {seed}")
+
+
+def test_build_rejects_noncanonical_input(dspg):
+    A = random_csr(10, 10, 4, 0, PLUS_TIMES_F64)
+    i = int(np.argmax(np.diff(A.rowptr) >= 2))
+    bad = A.col.copy()
+    s = A.rowptr[i]
+    bad[s], bad[s + 1] = bad[s + 1], bad[s]
+    from workloads import CSR
+    with pytest.raises(dspg.DspgError) as e:
+        dspg.DynamicSpGEMM(CSR(10, 10, A.rowptr, bad, A.val))
+    assert e.value.status == 1
+
+
+# ------------------------------------------------------------------ dynamic
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_config1_batch(dspg, sr):
+    """ER n=4096, 8 per row; one batch of 512 inserts, 256 deletes, 256 value
+    changes; C' against the oracle's A' A' and R against the oracle's R."""
+    A = er_matrix(4096, 8, seed=1, kind=sr)
+    b = er_batch(A, seed=2)
+    g = dspg.DynamicSpGEMM(A)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    st = _apply_both(g, Ao, Co, b)
+    assert st["n_insert"] == 512 and st["n_delete"] == 256 and st["n_update"] == 256 and st["n_noop"] == 0
+    _check_state(g, Ao, None, "config1", rel=(sr == PLUS_TIMES_F64))
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+@pytest.mark.parametrize("seed", range(6))
+def test_random_batches_sequence(dspg, sr, seed):
+    """Uneven rows, empty rows, duplicate keys in a batch, deletes of absent
+    entries, several batches in a row (state carries over)."""
+    n = 300
+    A = random_csr(n, n, 12, seed, sr, empty_frac=0.2)
+    g = dspg.DynamicSpGEMM(A)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    for k in range(4):
+        b = random_batch(n, n, [1, 17, 300, 2500][k], seed * 10 + k, sr, A=Ao.to_csr(), dup_frac=0.3)
+        _apply_both(g, Ao, Co, b)
+        _check_state(g, Ao, None, f"seed{seed} batch{k}")
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_separate_b_with_both_batches(dspg, sr):
+    A = random_csr(200, 150, 10, 3, sr)
+    B = random_csr(150, 180, 10, 4, sr)
+    g = dspg.DynamicSpGEMM(A, B)
+    Ao, Bo = OMat.from_csr(A), OMat.from_csr(B)
+    Co = Ao.multiply(Bo)
+    for k in range(3):
+        ba = random_batch(200, 150, 120, 40 + k, sr, A=Ao.to_csr())
+        bb = random_batch(150, 180, 90, 50 + k, sr, A=Bo.to_csr())
+        _apply_both(g, Ao, Co, ba, Bo, bb)
+        C_o, S_o = oracle_product(Ao, Bo)
+        assert_matches(g.read_C(), C_o, S_o, what=f"AB batch {k}")
+    # a batch on A only, after the transposed pattern exists
+    ba = random_batch(200, 150, 60, 77, sr, A=Ao.to_csr())
+    _apply_both(g, Ao, Co, ba, Bo, None)
+    C_o, S_o = oracle_product(Ao, Bo)
+    assert_matches(g.read_C(), C_o, S_o, what="A-only batch")
+
+
+def test_locality_rows_outside_R_unchanged_bitwise(dspg):
+    A = er_matrix(2048, 8, seed=11)
+    g = dspg.DynamicSpGEMM(A)
+    before = g.read_C()
+    b = er_batch(A, seed=12, n_insert=20, n_delete=10, n_set=10)
+    g.apply_batch(b)
+    R = g.last_affected()
+    after = g.read_C()
+    keep = np.setdiff1d(np.arange(A.nrows), R)
+    for i in keep[:: max(1, keep.shape[0] // 500)]:
+        s0, s1 = before.rowptr[i], before.rowptr[i + 1]
+        t0, t1 = after.rowptr[i], after.rowptr[i + 1]
+        assert np.array_equal(before.col[s0:s1], after.col[t0:t1])
+        assert np.array_equal(before.val[s0:s1].view(np.int64), after.val[t0:t1].view(np.int64))
+
+
+def test_edge_batches(dspg):
+    sr = PLUS_TIMES_F64
+    A = random_csr(120, 120, 8, 9, sr)
+    g = dspg.DynamicSpGEMM(A)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    # empty batch
+    empty = Batch(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0), np.zeros(0, np.uint8))
+    st = _apply_both(g, Ao, Co, empty)
+    assert st["affected_rows"] == 0
+    # only deletes of absent entries: nothing changes, R empty
+    present = set(zip(A.row_ids().tolist(), A.col.tolist()))
+    absent = [(i, j) for i in range(5) for j in range(120) if (i, j) not in present][:10]
+    b = Batch(np.array([p[0] for p in absent], np.int32), np.array([p[1] for p in absent], np.int32),
+              np.zeros(len(absent)), np.full(len(absent), OP_DELETE, np.uint8))
+    st = _apply_both(g, Ao, Co, b)
+    assert st["affected_rows"] == 0 and st["n_noop"] == len(absent)
+    # delete every entry of the longest row, and write the last row
+    r = int(np.argmax(np.diff(A.rowptr)))
+    cols = A.col[A.rowptr[r]:A.rowptr[r + 1]]
+    b = Batch(np.concatenate([np.full(cols.shape[0], r, np.int32), np.full(3, 119, np.int32)]),
+              np.concatenate([cols, np.array([0, 60, 119], np.int32)]),
+              np.concatenate([np.zeros(cols.shape[0]), np.array([1.5, -2.0, 0.0])]),
+              np.concatenate([np.full(cols.shape[0], OP_DELETE, np.uint8), np.full(3, OP_SET, np.uint8)]))
+    _apply_both(g, Ao, Co, b)
+    _check_state(g, Ao, None, "edge")
+
+
+def test_invalid_batch_leaves_state(dspg):
+    sr = MIN_PLUS_I32
+    A = random_csr(80, 80, 6, 21, sr)
+    g = dspg.DynamicSpGEMM(A)
+    C0, A0 = g.read_C(), g.read_A()
+    for bad in ("row", "op", "value"):
+        b = random_batch(80, 80, 40, 22, sr, A=A)
+        if bad == "row":
+            b.row[7] = 80
+        elif bad == "op":
+            b.op[3] = 9
+        else:
+            b.op[5] = OP_SET
+            b.val[5] = np.iinfo(np.int32).max
+        with pytest.raises(dspg.DspgError) as e:
+            g.apply_batch(b)
+        assert e.value.status == 1
+        C1, A1 = g.read_C(), g.read_A()
+        assert np.array_equal(C1.col, C0.col) and np.array_equal(C1.val, C0.val)
+        assert np.array_equal(A1.col, A0.col) and np.array_equal(A1.val, A0.val)
+
+
+def test_growth_paths_tight_arena(dspg):
+    """No slack and no arena headroom: every insert relocates its row, the
+    tails run out and the arenas are rebuilt mid-batch; results unchanged."""
+    sr = PLUS_TIMES_F64
+    A = random_csr(400, 400, 10, 31, sr)
+    g = dspg.DynamicSpGEMM(A, slack_min=0, slack_div=1 << 20, arena_headroom=1.0)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    total = 0
+    for k in range(3):
+        b = random_batch(400, 400, 3000, 60 + k, sr, A=Ao.to_csr(), hit_frac=0.1)
+        st = _apply_both(g, Ao, Co, b)
+        total += st["compactions"]
+        _check_state(g, Ao, None, f"tight {k}")
+    assert total > 0
+
+
+def test_large_batch_multi_cta_sort(dspg):
+    """Batches above the single-CTA sort size take the multi-pass radix sort."""
+    sr = MIN_PLUS_I32
+    A = er_matrix(20000, 6, seed=41, kind=sr)
+    g = dspg.DynamicSpGEMM(A)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    b = random_batch(20000, 20000, 30000, 42, sr, A=A, dup_frac=0.3)
+    _apply_both(g, Ao, Co, b)
+    _check_state(g, Ao, None, "big batch")
+
+
+# ------------------------------------------------------------ full configs
+
+
+def _sampled_rows(g, A_or, B_or, rows, what):
+    rp, col, val = g.read_rows_C(rows)
+    orp, ocol, oval = A_or.multiply_rows(B_or, rows)
+    assert np.array_equal(rp, orp), f"{what}: row lengths"
+    assert np.array_equal(col, ocol), f"{what}: columns"
+    if oval.dtype == np.float64:
+        _, _, sabs = A_or.multiply_rows(B_or, rows, absval=True)
+        assert np.all(np.abs(val - oval) <= 1e-12 * sabs), f"{what}: values"
+    else:
+        assert np.array_equal(val, oval), f"{what}: values"
+
+
+def test_config2_stencil_full_size(dspg):
+    """128^3 7-point stencil, C = A A (51,742,208 non-zeros), batches of
+    10^3 and 10^4 mixed updates within two grid hops: full C' compared."""
+    A = stencil7(128, 128, 128, seed=1)
+    g = dspg.DynamicSpGEMM(A)
+    assert g.info()["nnz_c"] == 51742208
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    for k, nb in enumerate([1000, 10000]):
+        b = stencil_batch(128, 128, 128, nb, seed=10 + k)
+        _apply_both(g, Ao, Co, b)
+    C_o = Co.to_csr()
+    Cg = g.read_C()
+    assert_same_pattern(Cg, C_o, "stencil C")
+    S_o = Ao.multiply(Ao, absval=True).to_csr()
+    err = np.abs(Cg.val - C_o.val)
+    assert np.all(err <= 1e-12 * S_o.val)
+
+
+def test_config3_rmat_minplus_full_size(dspg):
+    """R-MAT scale 20, edge factor 16, min-plus A B with B n x 256 at 1%;
+    edge batches of 10^2 and 10^4 (inserts of held-out edges, deletes of
+    present ones); C' bit-exact on all affected rows and a row sample."""
+    A, held = rmat_symmetric(20, 16, (0.57, 0.19, 0.19, 0.05), seed=3, kind=MIN_PLUS_I32, holdout=1 << 16)
+    B = bernoulli_sparse(A.ncols, 256, 0.01, seed=4, kind=MIN_PLUS_I32)
+    g = dspg.DynamicSpGEMM(A, B)
+    Ao, Bo = OMat.from_csr(A), OMat.from_csr(B)
+    rng = np.random.default_rng(0)
+    _sampled_rows(g, Ao, Bo, np.sort(rng.choice(A.nrows, 4000, replace=False)), "rmat build")
+    for k, ne in enumerate([100, 10000]):
+        b = rmat_edge_batch(Ao.to_csr() if k else A, held, ne, seed=30 + k)
+        g.apply_batch(b)
+        pre = None
+        Ao.apply(b)
+        R = g.last_affected()
+        assert np.array_equal(R, np.unique(b.row)), "R = rows of the A batch when B does not change"
+        _sampled_rows(g, Ao, Bo, R, f"rmat batch {k} R")
+        _sampled_rows(g, Ao, Bo, np.sort(rng.choice(A.nrows, 2000, replace=False)), f"rmat batch {k} sample")
