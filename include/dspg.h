@@ -106,7 +106,22 @@ typedef struct {
     int64_t nnz_written;    /* entries of C written by the recompute */
     int64_t relocations;    /* rows moved to the arena tail (A, B, transpose, C) */
     int64_t compactions;    /* arena rebuilds (growth) during this batch */
+    int64_t a_entries;      /* entries of A' rows read by the recompute */
 } dspg_batch_stats;
+
+/* Stages of apply_batch, in pipeline order, for dspg_stage_times. */
+enum {
+    DSPG_STAGE_SORT = 0,      /* radix sort + last-writer de-duplication (Section 4.2 grouping) */
+    DSPG_STAGE_CLASSIFY = 1,  /* row segments, insert/update/delete classification */
+    DSPG_STAGE_DETECT = 2,    /* affected rows R (Section 5, rows of C*) */
+    DSPG_STAGE_MERGE = 3,     /* rebuild changed rows of A (and B) in staging */
+    DSPG_STAGE_COMMIT = 4,    /* write them into the slack-CSR (Section 4.1 merge/mask) */
+    DSPG_STAGE_TRANSPOSE = 5, /* keep A's transposed pattern in step */
+    DSPG_STAGE_SIZE = 6,      /* product bounds and bins of the rows of R */
+    DSPG_STAGE_NUMERIC = 7,   /* Gustavson recompute of the rows of R (Section 6.1) */
+    DSPG_STAGE_SPLICE = 8,    /* write the new rows into C */
+    DSPG_NSTAGES = 9
+};
 
 typedef struct dspg_handle dspg_handle;
 
@@ -153,6 +168,19 @@ dspg_status dspg_recompute_all(dspg_handle *h, void *stream);
 /* Shapes and sizes: nrows(A), ncols(A) = nrows(B), ncols(B), nnz(A'), nnz(C'). */
 dspg_status dspg_info(dspg_handle *h, int64_t *n, int64_t *k, int64_t *m, int64_t *nnz_a, int64_t *nnz_c);
 
+/* Turn per-stage timing on (1) or off (0).  When on, apply_batch records a
+ * CUDA event between its stages on the caller's stream; dspg_stage_times
+ * then returns the device time of each stage of the last apply_batch in
+ * milliseconds (ms[DSPG_NSTAGES]; n = room in ms).  Re-runs after a buffer
+ * grew are not included. */
+dspg_status dspg_set_profiling(dspg_handle *h, int on);
+dspg_status dspg_stage_times(dspg_handle *h, float *ms, int n);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * handles), for auditing how many launches a call makes. */
+unsigned long long dspg_kernel_launches(void);
+
+/* Free the handle and all its device memory (synchronises the device). */
 void dspg_destroy(dspg_handle *h);
 
 /* Message of the last error on h, or of the calling thread's last failed

@@ -68,7 +68,8 @@ struct Ctl {
     long long n_K;             // rows of B* (detection)
     long long bin_count[NBINS];
     long long ubc_total;       // sum over rows of min(product bound, columns)
-    long long pad[7];
+    long long a_entries;       // A' entries read by the recompute
+    long long pad[6];
 };
 
 // A row-slack CSR ("slack-CSR") on the device: row i occupies
@@ -155,6 +156,18 @@ __device__ __forceinline__ int64_t upper_bound_dev(const T *a, int64_t lo, int64
 #endif  // __CUDACC__
 
 // ---------------------------------------------------------------- host side
+
+// Every kernel of the library is launched through launch_k, which counts
+// launches (process-wide) so that callers can audit the work of a call.
+unsigned long long &launch_counter();
+
+#ifdef __CUDACC__
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    kern<<<grid, block, smem, s>>>(args...);
+    __atomic_fetch_add(&launch_counter(), 1ull, __ATOMIC_RELAXED);
+}
+#endif
 
 // Device scan: out[i] = sum_{j<i} in[j] for i <= n (out has n+1 entries).
 void scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);

@@ -26,6 +26,11 @@
 
 using namespace dspg;
 
+unsigned long long &dspg::launch_counter() {
+    static unsigned long long count = 0;
+    return count;
+}
+
 namespace {
 
 struct Err : std::runtime_error {
@@ -201,6 +206,9 @@ struct dspg_handle {
     CWs wc;
     BatchIn inA, inB;
     int64_t last_nR = 0;
+    bool prof = false;
+    cudaEvent_t ev[DSPG_NSTAGES + 1] = {};
+    float stage_ms[DSPG_NSTAGES] = {};
     int64_t compactions = 0;
     std::string err;
 
@@ -467,25 +475,25 @@ void build_transpose(dspg_handle *h, cudaStream_t s) {
 
 // ------------------------------------------------------------ pipeline
 
-void stage_sort_classify(dspg_handle *h, cudaStream_t s) {
-    Ctl *ctl = h->ctl;
-    if (h->inA.n > 0) {
+void stage_sort(dspg_handle *h, cudaStream_t s) {
+    if (h->inA.n > 0)
         sort_updates(h->inA.row, h->inA.col, h->inA.val, h->inA.op, h->inA.n, h->A.nrows, h->A.ncols, h->sr, true,
-                     h->wA.sort_out(), h->wA.sort_tmp(), ctl, 0u, s);
-    }
-    if (!h->b_is_a && h->inB.n > 0) {
+                     h->wA.sort_out(), h->wA.sort_tmp(), h->ctl, 0u, s);
+    if (!h->b_is_a && h->inB.n > 0)
         sort_updates(h->inB.row, h->inB.col, h->inB.val, h->inB.op, h->inB.n, h->B.nrows, h->B.ncols, h->sr, true,
-                     h->wB.sort_out(), h->wB.sort_tmp(), ctl, 0u, s);
-    }
+                     h->wB.sort_out(), h->wB.sort_tmp(), h->ctl, 0u, s);
+}
+
+void stage_classify(dspg_handle *h, cudaStream_t s) {
     if (h->inA.n > 0) {
         UpdJob J = h->wA.job(h->inA.n);
-        run_segments(J, h->A.nrows, ctl, M_AB, s);
-        run_classify(J, h->A.view(), h->vsize, ctl, M_AB, ST_AB_STAGE, s, h->num_sms);
+        run_segments(J, h->A.nrows, h->ctl, M_AB, s);
+        run_classify(J, h->A.view(), h->vsize, h->ctl, M_AB, ST_AB_STAGE, s, h->num_sms);
     }
     if (!h->b_is_a && h->inB.n > 0) {
         UpdJob J = h->wB.job(h->inB.n);
-        run_segments(J, h->B.nrows, ctl, M_AB, s);
-        run_classify(J, h->B.view(), h->vsize, ctl, M_AB, ST_AB_STAGE, s, h->num_sms);
+        run_segments(J, h->B.nrows, h->ctl, M_AB, s);
+        run_classify(J, h->B.view(), h->vsize, h->ctl, M_AB, ST_AB_STAGE, s, h->num_sms);
     }
 }
 
@@ -505,15 +513,13 @@ void stage_detect(dspg_handle *h, cudaStream_t s) {
     if (any_cols) run_clear_marks(w.bmK.p, w.K.p, &h->ctl->n_K, w.nrows_b, s);
 }
 
-void stage_merge_commit_ab(dspg_handle *h, cudaStream_t s) {
-    if (h->inA.n > 0) {
-        UpdJob J = h->wA.job(h->inA.n);
-        run_merge_copy(J, h->A.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
-    }
-    if (!h->b_is_a && h->inB.n > 0) {
-        UpdJob J = h->wB.job(h->inB.n);
-        run_merge_copy(J, h->B.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
-    }
+void stage_merge(dspg_handle *h, cudaStream_t s) {
+    if (h->inA.n > 0) run_merge_copy(h->wA.job(h->inA.n), h->A.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
+    if (!h->b_is_a && h->inB.n > 0)
+        run_merge_copy(h->wB.job(h->inB.n), h->B.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
+}
+
+void stage_commit_ab(dspg_handle *h, cudaStream_t s) {
     if (h->inA.n > 0)
         run_commit(upd_commit_job(h, h->wA, ST_AB_ARENA, ST_AB_STAGE), h->A.view(), h->vsize, h->inA.n, h->ctl, M_AB,
                    M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
@@ -538,13 +544,30 @@ void stage_transpose(dspg_handle *h, cudaStream_t s) {
                h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
 }
 
-void stage_recompute(dspg_handle *h, cudaStream_t s) {
-    MatView Av = h->A.view(), Bv = h->Bm().view();
-    const int64_t maxR = h->A.nrows;
-    run_size_bins(Av, Bv, c_job(h, h->wc.R.p), maxR, h->ctl, M_C, s, h->num_sms);
-    run_numeric(h->sr, Av, Bv, c_job(h, h->wc.R.p), h->ctl, M_C, s, h->num_sms);
-    run_commit(c_commit_job(h, h->wc.R.p), h->C.view(), h->vsize, maxR, h->ctl, M_C, M_C, h->opt.slack_min,
+void stage_size(dspg_handle *h, cudaStream_t s) {
+    run_size_bins(h->A.view(), h->Bm().view(), c_job(h, h->wc.R.p), h->A.nrows, h->ctl, M_C, s, h->num_sms);
+}
+
+void stage_numeric(dspg_handle *h, cudaStream_t s) {
+    run_numeric(h->sr, h->A.view(), h->Bm().view(), c_job(h, h->wc.R.p), h->ctl, M_C, s, h->num_sms);
+}
+
+void stage_splice(dspg_handle *h, cudaStream_t s) {
+    run_commit(c_commit_job(h, h->wc.R.p), h->C.view(), h->vsize, h->A.nrows, h->ctl, M_C, M_C, h->opt.slack_min,
                h->opt.slack_div, s, h->num_sms);
+}
+
+typedef void (*StageFn)(dspg_handle *, cudaStream_t);
+const StageFn kStages[DSPG_NSTAGES] = {stage_sort,      stage_classify,  stage_detect,  stage_merge,  stage_commit_ab,
+                                       stage_transpose, stage_size,      stage_numeric, stage_splice};
+
+// Enqueue stages [from, to); with profiling on, an event brackets each.
+void run_stages(dspg_handle *h, int from, int to, cudaStream_t s, bool timed) {
+    for (int k = from; k < to; k++) {
+        if (timed) CK(cudaEventRecord(h->ev[k], s));
+        kStages[k](h, s);
+    }
+    if (timed) CK(cudaEventRecord(h->ev[to], s));
 }
 
 void reset_range(dspg_handle *h, void *first, size_t bytes, cudaStream_t s) {
@@ -754,13 +777,11 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
         const int64_t compactions0 = h->compactions;
 
         CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
-        stage_sort_classify(h, s);
-        stage_detect(h, s);
-        stage_merge_commit_ab(h, s);
-        stage_transpose(h, s);
-        stage_recompute(h, s);
+        run_stages(h, 0, DSPG_NSTAGES, s, h->prof);
         CK(cudaGetLastError());
         read_ctl(h, s);
+        if (h->prof)
+            for (int k = 0; k < DSPG_NSTAGES; k++) CK(cudaEventElapsedTime(&h->stage_ms[k], h->ev[k], h->ev[k + 1]));
 
         for (int iter = 0; iter < 8 && h->hctl->status; iter++) {
             const unsigned st = h->hctl->status;
@@ -770,11 +791,7 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
                 h->wA.grow_stage(h->hctl->u[0].stage_top + 1024);
                 h->wB.grow_stage(h->hctl->u[1].stage_top + 1024);
                 CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
-                stage_sort_classify(h, s);
-                stage_detect(h, s);
-                stage_merge_commit_ab(h, s);
-                stage_transpose(h, s);
-                stage_recompute(h, s);
+                run_stages(h, 0, DSPG_NSTAGES, s, false);
                 read_ctl(h, s);
                 continue;
             }
@@ -788,14 +805,7 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
                 reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
                 reset_c_counters(h, s);
                 reset_range(h, &h->ctl->status, sizeof(unsigned), s);
-                if (nA > 0)
-                    run_commit(upd_commit_job(h, h->wA, ST_AB_ARENA, ST_AB_STAGE), h->A.view(), h->vsize, nA, h->ctl,
-                               M_AB, M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
-                if (!h->b_is_a && nB > 0)
-                    run_commit(upd_commit_job(h, h->wB, ST_AB_ARENA, ST_AB_STAGE), h->B.view(), h->vsize, nB, h->ctl,
-                               M_AB, M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
-                stage_transpose(h, s);
-                stage_recompute(h, s);
+                run_stages(h, DSPG_STAGE_COMMIT, DSPG_NSTAGES, s, false);
                 read_ctl(h, s);
                 continue;
             }
@@ -808,11 +818,11 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
             reset_range(h, &h->ctl->status, sizeof(unsigned), s);
             if (at) {
                 reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
-                stage_transpose(h, s);
+                run_stages(h, DSPG_STAGE_TRANSPOSE, DSPG_STAGE_TRANSPOSE + 1, s, false);
             }
             if (cc) {
                 reset_c_counters(h, s);
-                stage_recompute(h, s);
+                run_stages(h, DSPG_STAGE_SIZE, DSPG_NSTAGES, s, false);
             }
             read_ctl(h, s);
         }
@@ -836,6 +846,7 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
             stats->products = c.products;
             stats->nnz_written = c.nnz_written;
             stats->compactions = h->compactions - compactions0;
+            stats->a_entries = c.a_entries;
         }
         return DSPG_OK;
     } catch (const Err &e) {
@@ -938,9 +949,31 @@ dspg_status dspg_info(dspg_handle *h, int64_t *n, int64_t *k, int64_t *m, int64_
     }
 }
 
+dspg_status dspg_set_profiling(dspg_handle *h, int on) {
+    if (!h) return DSPG_ERR_INVALID;
+    try {
+        if (on && !h->ev[0])
+            for (int k = 0; k <= DSPG_NSTAGES; k++) CK(cudaEventCreate(&h->ev[k]));
+        h->prof = on != 0;
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_stage_times(dspg_handle *h, float *ms, int n) {
+    if (!h || !ms || n < 0) return DSPG_ERR_INVALID;
+    for (int k = 0; k < n && k < DSPG_NSTAGES; k++) ms[k] = h->stage_ms[k];
+    return DSPG_OK;
+}
+
+unsigned long long dspg_kernel_launches(void) { return __atomic_load_n(&launch_counter(), __ATOMIC_RELAXED); }
+
 void dspg_destroy(dspg_handle *h) {
     if (!h) return;
     cudaDeviceSynchronize();
+    for (int k = 0; k <= DSPG_NSTAGES; k++)
+        if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     if (h->ctl) cudaFree(h->ctl);
     if (h->hctl) cudaFreeHost(h->hctl);
     delete h;

@@ -19,7 +19,7 @@ __global__ void k_iota(int32_t *a, int64_t n) {
         a[x] = (int32_t)x;
 }
 void fill_iota(int32_t *a, int64_t n, cudaStream_t s) {
-    if (n > 0) k_iota<<<blocks_for(n, 256, 8192), 256, 0, s>>>(a, n);
+    if (n > 0) launch_k(k_iota, blocks_for(n, 256, 8192), 256, 0, s, a, n);
 }
 
 __global__ void k_caps(const int32_t *len, int32_t *cap, int64_t n, int smin, int sdiv) {
@@ -27,7 +27,7 @@ __global__ void k_caps(const int32_t *len, int32_t *cap, int64_t n, int smin, in
         cap[x] = slack_cap(len[x], smin, sdiv);
 }
 void caps_from_lens(const int32_t *len, int32_t *cap, int64_t n, int smin, int sdiv, cudaStream_t s) {
-    if (n > 0) k_caps<<<blocks_for(n, 256, 8192), 256, 0, s>>>(len, cap, n, smin, sdiv);
+    if (n > 0) launch_k(k_caps, blocks_for(n, 256, 8192), 256, 0, s, len, cap, n, smin, sdiv);
 }
 
 __global__ void k_lens_rowptr(const int64_t *rowptr, int32_t *len, int64_t n) {
@@ -35,7 +35,7 @@ __global__ void k_lens_rowptr(const int64_t *rowptr, int32_t *len, int64_t n) {
         len[x] = (int32_t)(rowptr[x + 1] - rowptr[x]);
 }
 void lens_from_rowptr(const int64_t *rowptr, int32_t *len, int64_t n, cudaStream_t s) {
-    if (n > 0) k_lens_rowptr<<<blocks_for(n, 256, 8192), 256, 0, s>>>(rowptr, len, n);
+    if (n > 0) launch_k(k_lens_rowptr, blocks_for(n, 256, 8192), 256, 0, s, rowptr, len, n);
 }
 
 __global__ void k_lens_of_rows(const int32_t *rows, int64_t n, const int32_t *len, int32_t *out) {
@@ -43,7 +43,7 @@ __global__ void k_lens_of_rows(const int32_t *rows, int64_t n, const int32_t *le
         out[x] = len[rows[x]];
 }
 void lens_of_rows(const int32_t *rows, int64_t n, const int32_t *len, int32_t *out, cudaStream_t s) {
-    if (n > 0) k_lens_of_rows<<<blocks_for(n, 256, 8192), 256, 0, s>>>(rows, n, len, out);
+    if (n > 0) launch_k(k_lens_of_rows, blocks_for(n, 256, 8192), 256, 0, s, rows, n, len, out);
 }
 
 template <typename T>
@@ -69,10 +69,10 @@ void copy_rows(const int32_t *rows, int64_t n, const int64_t *src_off, const int
     if (n <= 0) return;
     unsigned g = blocks_for(n * 32, 256, (int64_t)num_sms * 16);
     if (vsize == 8)
-        k_copy_rows<double><<<g, 256, 0, s>>>(rows, n, src_off, len, src_col, (const double *)src_val, dst_off,
+        launch_k(k_copy_rows<double>, g, 256, 0, s, rows, n, src_off, len, src_col, (const double *)src_val, dst_off,
                                               dst_col, (double *)dst_val);
     else
-        k_copy_rows<int32_t><<<g, 256, 0, s>>>(rows, n, src_off, len, src_col, (const int32_t *)src_val, dst_off,
+        launch_k(k_copy_rows<int32_t>, g, 256, 0, s, rows, n, src_off, len, src_col, (const int32_t *)src_val, dst_off,
                                                dst_col, (int32_t *)dst_val);
 }
 
@@ -97,8 +97,8 @@ void gather_rows_out(const int32_t *rows, int64_t n, const MatView &M, const int
                      void *out_val, int vsize, cudaStream_t s, int num_sms) {
     if (n <= 0) return;
     unsigned g = blocks_for(n * 32, 256, (int64_t)num_sms * 16);
-    if (vsize == 8) k_gather_out<double><<<g, 256, 0, s>>>(rows, n, M, out_rowptr, out_col, (double *)out_val);
-    else k_gather_out<int32_t><<<g, 256, 0, s>>>(rows, n, M, out_rowptr, out_col, (int32_t *)out_val);
+    if (vsize == 8) launch_k(k_gather_out<double>, g, 256, 0, s, rows, n, M, out_rowptr, out_col, (double *)out_val);
+    else launch_k(k_gather_out<int32_t>, g, 256, 0, s, rows, n, M, out_rowptr, out_col, (int32_t *)out_val);
 }
 
 // Canonical-CSR check: rowptr[0] = 0 and non-decreasing, rowptr[n] = nnz,
@@ -137,11 +137,11 @@ __global__ void k_validate_entries(int64_t nrows, int64_t ncols, const int64_t *
 void validate_csr_entries(int64_t nrows, int64_t ncols, const int64_t *rowptr, const int32_t *col, const void *val,
                           int sr, unsigned *bad, cudaStream_t s) {
     if (nrows > 0)
-        k_validate_entries<<<blocks_for(nrows * 32, 256, 8192), 256, 0, s>>>(nrows, ncols, rowptr, col, val, sr, bad);
+        launch_k(k_validate_entries, blocks_for(nrows * 32, 256, 8192), 256, 0, s, nrows, ncols, rowptr, col, val, sr, bad);
 }
 
 void validate_rowptr(int64_t nrows, int64_t nnz, const int64_t *rowptr, unsigned *bad, cudaStream_t s) {
-    k_validate_rows<<<blocks_for(nrows + 1, 256, 4096), 256, 0, s>>>(nrows, 0, nnz, rowptr, bad);
+    launch_k(k_validate_rows, blocks_for(nrows + 1, 256, 4096), 256, 0, s, nrows, 0, nnz, rowptr, bad);
 }
 
 __global__ void k_hist_cols(const int32_t *col, int64_t nnz, int32_t *counts) {
@@ -149,7 +149,7 @@ __global__ void k_hist_cols(const int32_t *col, int64_t nnz, int32_t *counts) {
         atomicAdd(&counts[col[x]], 1);
 }
 void hist_cols(const int32_t *col, int64_t nnz, int32_t *counts, cudaStream_t s) {
-    if (nnz > 0) k_hist_cols<<<blocks_for(nnz, 256, 8192), 256, 0, s>>>(col, nnz, counts);
+    if (nnz > 0) launch_k(k_hist_cols, blocks_for(nnz, 256, 8192), 256, 0, s, col, nnz, counts);
 }
 
 __global__ void k_rows_of_entries(const int64_t *rowptr, int64_t nrows, uint32_t *rows_out) {
@@ -160,7 +160,7 @@ __global__ void k_rows_of_entries(const int64_t *rowptr, int64_t nrows, uint32_t
 }
 void rows_of_entries(const int64_t *rowptr, int64_t nrows, uint32_t *rows_out, cudaStream_t s, int num_sms) {
     if (nrows > 0)
-        k_rows_of_entries<<<blocks_for(nrows * 32, 256, (int64_t)num_sms * 16), 256, 0, s>>>(rowptr, nrows, rows_out);
+        launch_k(k_rows_of_entries, blocks_for(nrows * 32, 256, (int64_t)num_sms * 16), 256, 0, s, rowptr, nrows, rows_out);
 }
 
 __global__ void k_keys_from_cols(const int32_t *col, int64_t nnz, uint64_t *keys) {
@@ -168,7 +168,7 @@ __global__ void k_keys_from_cols(const int32_t *col, int64_t nnz, uint64_t *keys
         keys[x] = (uint64_t)(uint32_t)col[x];
 }
 void keys_from_cols(const int32_t *col, int64_t nnz, uint64_t *keys, cudaStream_t s) {
-    if (nnz > 0) k_keys_from_cols<<<blocks_for(nnz, 256, 8192), 256, 0, s>>>(col, nnz, keys);
+    if (nnz > 0) launch_k(k_keys_from_cols, blocks_for(nnz, 256, 8192), 256, 0, s, col, nnz, keys);
 }
 
 __global__ void k_keys_from_i32(const int32_t *a, int64_t n, uint64_t *keys, uint32_t *idx) {
@@ -184,10 +184,10 @@ __global__ void k_keys_to_i32(const uint64_t *keys, int64_t n, int32_t *a) {
 void sort_i32_values(int32_t *a, int64_t n, int bits, uint64_t *k0, uint64_t *k1, uint32_t *i0, uint32_t *i1,
                      uint32_t *counts, int64_t *scan_tmp, int64_t *scan_out, cudaStream_t s) {
     if (n <= 1) return;
-    k_keys_from_i32<<<blocks_for(n, 256, 8192), 256, 0, s>>>(a, n, k0, i0);
+    launch_k(k_keys_from_i32, blocks_for(n, 256, 8192), 256, 0, s, a, n, k0, i0);
     bool alt = false;
     radix_sort_pairs(k0, i0, k1, i1, n, bits, counts, scan_tmp, scan_out, s, &alt);
-    k_keys_to_i32<<<blocks_for(n, 256, 8192), 256, 0, s>>>(alt ? k1 : k0, n, a);
+    launch_k(k_keys_to_i32, blocks_for(n, 256, 8192), 256, 0, s, alt ? k1 : k0, n, a);
 }
 
 }  // namespace dspg

@@ -92,9 +92,9 @@ static void scan_impl(const T *in, int64_t *out, int64_t n, int64_t *tmp, cudaSt
         return;
     }
     int64_t nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
-    k_scan_reduce<T><<<(unsigned)nb, SCAN_NT, 0, s>>>(in, n, tmp);
-    k_scan_partials<<<1, SCAN_NT, 0, s>>>(tmp, nb);
-    k_scan_final<T><<<(unsigned)nb, SCAN_NT, 0, s>>>(in, n, tmp, out);
+    launch_k(k_scan_reduce<T>, (unsigned)nb, SCAN_NT, 0, s, in, n, tmp);
+    launch_k(k_scan_partials, 1, SCAN_NT, 0, s, tmp, nb);
+    launch_k(k_scan_final<T>, (unsigned)nb, SCAN_NT, 0, s, in, n, tmp, out);
 }
 
 void scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s) {

@@ -252,9 +252,9 @@ void radix_sort_pairs(uint64_t *k, uint32_t *v, uint64_t *k_alt, uint32_t *v_alt
         const uint32_t *vi = alt ? v_alt : v;
         uint64_t *ko = alt ? k : k_alt;
         uint32_t *vo = alt ? v : v_alt;
-        k_hist<<<(unsigned)nb, MS_NT, 0, s>>>(ki, n, shift, counts, nb);
+        launch_k(k_hist, (unsigned)nb, MS_NT, 0, s, ki, n, shift, counts, nb);
         scan_i32_to_i64((const int32_t *)counts, scan_out, 256 * nb, scan_tmp, s);
-        k_scatter<<<(unsigned)nb, MS_NT, 0, s>>>(ki, vi, n, shift, scan_out, nb, ko, vo);
+        launch_k(k_scatter, (unsigned)nb, MS_NT, 0, s, ki, vi, n, shift, scan_out, nb, ko, vo);
         alt = !alt;
     }
     *in_alt = alt;
@@ -272,16 +272,16 @@ void sort_updates(const int32_t *row, const int32_t *col, const void *val, const
             cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SS_SMEM);
             attr_set = true;
         }
-        k_sort_small<<<1, SS_NT, SS_SMEM, s>>>(row, col, val, op, (int)n, nrows, ncols, sr, check_values, out, ctl,
+        launch_k(k_sort_small, 1, SS_NT, SS_SMEM, s, row, col, val, op, (int)n, nrows, ncols, sr, check_values, out, ctl,
                                               skip_mask, cb, ib, kb);
         return;
     }
     unsigned nblk = (unsigned)((n + 255) / 256);
-    k_make_keys<<<nblk, 256, 0, s>>>(row, col, val, op, n, nrows, ncols, sr, check_values, ctl, skip_mask, cb, tmp.k0,
+    launch_k(k_make_keys, nblk, 256, 0, s, row, col, val, op, n, nrows, ncols, sr, check_values, ctl, skip_mask, cb, tmp.k0,
                                     tmp.i0);
     bool in_alt = false;
     radix_sort_pairs(tmp.k0, tmp.i0, tmp.k1, tmp.i1, n, kb, tmp.counts, tmp.scan_tmp, tmp.scan_out, s, &in_alt);
-    k_finalize<<<nblk, 256, 0, s>>>(in_alt ? tmp.k1 : tmp.k0, in_alt ? tmp.i1 : tmp.i0, n, cb, val, op, sr, out, ctl,
+    launch_k(k_finalize, nblk, 256, 0, s, in_alt ? tmp.k1 : tmp.k0, in_alt ? tmp.i1 : tmp.i0, n, cb, val, op, sr, out, ctl,
                                     skip_mask);
 }
 

@@ -78,7 +78,7 @@ __global__ void k_size_bins(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mas
     const long long nR = ctl->n_affected;
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    long long prod_acc = 0;
+    long long prod_acc = 0, ubc_acc = 0, a_acc = 0;
     for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nR; t += nwarps) {
         const int32_t i = J.R[t];
         const int64_t aoff = A.off[i];
@@ -87,19 +87,25 @@ __global__ void k_size_bins(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mas
         for (int a = lane; a < alen; a += 32) s += B.len[A.col[aoff + a]];
         s = warp_sum<long long>(s);
         if (lane == 0) {
+            const long long ubc = s < J.m ? s : J.m;
             prod_acc += s;
+            ubc_acc += ubc;
+            a_acc += alen;
             if (s == 0) {
                 J.slen[t] = 0;
                 J.soff[t] = 0;
             } else {
-                const long long ubc = s < J.m ? s : J.m;
                 const int b = pick_bin(ubc, J.dense_mode);
                 const long long x = atomic_add_ll2(&ctl->bin_count[b], 1);
                 J.bins[(int64_t)b * J.bin_cap + x] = (int32_t)t;
             }
         }
     }
-    if (lane == 0 && prod_acc) atomic_add_ll2(&ctl->products, prod_acc);
+    if (lane == 0 && prod_acc) {
+        atomic_add_ll2(&ctl->products, prod_acc);
+        atomic_add_ll2(&ctl->ubc_total, ubc_acc);
+    }
+    if (lane == 0 && a_acc) atomic_add_ll2(&ctl->a_entries, a_acc);
 }
 
 // --------------------------------------------------- product generators
@@ -635,8 +641,8 @@ __global__ void k_fill(T *p, int64_t n, T v) {
 
 void init_dense_scratch(int sr, void *acc, uint32_t *mask, int64_t entries, int64_t words, cudaStream_t s) {
     if (entries > 0) {
-        if (sr == SR_PT) k_fill<double><<<1024, 256, 0, s>>>((double *)acc, entries, 0.0);
-        else k_fill<int32_t><<<1024, 256, 0, s>>>((int32_t *)acc, entries, MP_INF);
+        if (sr == SR_PT) launch_k(k_fill<double>, 1024, 256, 0, s, (double *)acc, entries, 0.0);
+        else launch_k(k_fill<int32_t>, 1024, 256, 0, s, (int32_t *)acc, entries, MP_INF);
     }
     if (words > 0) cudaMemsetAsync(mask, 0, words * sizeof(uint32_t), s);
 }
@@ -647,7 +653,7 @@ void run_size_bins(const MatView &A, const MatView &B, const CJob &J, int64_t ma
     int64_t g = (max_rows * 32 + 255) / 256;
     if (g > num_sms * 16) g = num_sms * 16;
     if (g < 1) g = 1;
-    k_size_bins<<<(unsigned)g, 256, 0, s>>>(A, B, J, ctl, mask);
+    launch_k(k_size_bins, (unsigned)g, 256, 0, s, A, B, J, ctl, mask);
 }
 
 template <int SR, int LOG_TS, int NW>
@@ -664,7 +670,7 @@ static void launch_warp_hash(const MatView &A, const MatView &B, const CJob &J, 
     int per_sm = (int)((200 * 1024) / (smem + 1024));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2048 / (NW * 32)) per_sm = 2048 / (NW * 32);
-    k_num_warp_hash<SR, LOG_TS, NW><<<num_sms * per_sm, NW * 32, smem, s>>>(A, B, J, ctl, mask, bin);
+    launch_k(k_num_warp_hash<SR, LOG_TS, NW>, num_sms * per_sm, NW * 32, smem, s, A, B, J, ctl, mask, bin);
 }
 
 template <int SR, int LOG_TS>
@@ -681,7 +687,7 @@ static void launch_cta_hash(const MatView &A, const MatView &B, const CJob &J, C
     int per_sm = (int)((200 * 1024) / (smem + 8 * 1024));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 8) per_sm = 8;
-    k_num_cta_hash<SR, LOG_TS><<<num_sms * per_sm, 256, smem, s>>>(A, B, J, ctl, mask, bin);
+    launch_k(k_num_cta_hash<SR, LOG_TS>, num_sms * per_sm, 256, smem, s, A, B, J, ctl, mask, bin);
 }
 
 template <int SR>
@@ -697,9 +703,9 @@ static void run_numeric_t(const MatView &A, const MatView &B, const CJob &J, Ctl
             cudaFuncSetAttribute(k_num_warp_dense<SR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
             set_w = true;
         }
-        k_num_warp_dense<SR, NW><<<num_sms * 4, NW * 32, smem_w, s>>>(A, B, J, ctl, mask, BIN_WDENSE, mp);
+        launch_k(k_num_warp_dense<SR, NW>, num_sms * 4, NW * 32, smem_w, s, A, B, J, ctl, mask, BIN_WDENSE, mp);
         const size_t smem_c = (size_t)mp * sizeof(T) + 32 * sizeof(uint32_t);
-        k_num_cta_dense<SR><<<num_sms, 512, smem_c, s>>>(A, B, J, ctl, mask, BIN_CDENSE, mp);
+        launch_k(k_num_cta_dense<SR>, num_sms, 512, smem_c, s, A, B, J, ctl, mask, BIN_CDENSE, mp);
         return;
     }
     launch_warp_hash<SR, 6, 8>(A, B, J, ctl, mask, BIN_W64, s, num_sms);
@@ -710,7 +716,7 @@ static void run_numeric_t(const MatView &A, const MatView &B, const CJob &J, Ctl
     launch_cta_hash<SR, 11>(A, B, J, ctl, mask, BIN_C2048, s, num_sms);
     launch_cta_hash<SR, 12>(A, B, J, ctl, mask, BIN_C4096, s, num_sms);
     launch_cta_hash<SR, 13>(A, B, J, ctl, mask, BIN_C8192, s, num_sms);
-    k_num_gdense<SR><<<J.gd_ctas, 512, 0, s>>>(A, B, J, ctl, mask, BIN_GD);
+    launch_k(k_num_gdense<SR>, J.gd_ctas, 512, 0, s, A, B, J, ctl, mask, BIN_GD);
 }
 
 void run_numeric(int sr, const MatView &A, const MatView &B, const CJob &J, Ctl *ctl, unsigned mask, cudaStream_t s,

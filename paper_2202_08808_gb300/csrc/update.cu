@@ -318,7 +318,7 @@ static unsigned grid_for(int64_t n, int nt) {
 
 void run_segments(const UpdJob &J, int64_t nrows, Ctl *ctl, unsigned mask, cudaStream_t s) {
     if (J.n <= 0) return;
-    k_segments<<<(unsigned)((J.n + 255) / 256), 256, 0, s>>>(J.row, J.n, nrows, J.seg_lo, J.seg_hi,
+    launch_k(k_segments, (unsigned)((J.n + 255) / 256), 256, 0, s, J.row, J.n, nrows, J.seg_lo, J.seg_hi,
                                                             &ctl->u[J.which].n_seg, ctl, mask);
 }
 
@@ -327,16 +327,16 @@ void run_classify(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsign
     if (J.n <= 0) return;
     unsigned g = grid_for(J.n * 32, 256);
     if (g > (unsigned)num_sms * 8) g = num_sms * 8;
-    if (vsize == 8) k_classify<double><<<g, 256, 0, s>>>(J, M, ctl, mask, stage_bit);
-    else k_classify<int32_t><<<g, 256, 0, s>>>(J, M, ctl, mask, stage_bit);
+    if (vsize == 8) launch_k(k_classify<double>, g, 256, 0, s, J, M, ctl, mask, stage_bit);
+    else launch_k(k_classify<int32_t>, g, 256, 0, s, J, M, ctl, mask, stage_bit);
 }
 
 void run_merge_copy(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsigned mask, cudaStream_t s,
                     int num_sms) {
     if (J.n <= 0) return;
     unsigned g = num_sms * 8;
-    if (vsize == 8) k_merge_copy<double><<<g, 256, 0, s>>>(J, M, ctl, mask);
-    else k_merge_copy<int32_t><<<g, 256, 0, s>>>(J, M, ctl, mask);
+    if (vsize == 8) launch_k(k_merge_copy<double>, g, 256, 0, s, J, M, ctl, mask);
+    else launch_k(k_merge_copy<int32_t>, g, 256, 0, s, J, M, ctl, mask);
 }
 
 void run_commit(const CommitJob &J, const MatView &M, int vsize, int64_t max_items, Ctl *ctl, unsigned plan_mask,
@@ -344,31 +344,31 @@ void run_commit(const CommitJob &J, const MatView &M, int vsize, int64_t max_ite
     if (max_items <= 0) return;
     unsigned gp = grid_for(max_items, 256);
     if (gp > (unsigned)num_sms * 4) gp = num_sms * 4;
-    k_commit_plan<<<gp, 256, 0, s>>>(J, M, ctl, plan_mask, slack_min, slack_div);
+    launch_k(k_commit_plan, gp, 256, 0, s, J, M, ctl, plan_mask, slack_min, slack_div);
     unsigned g = num_sms * 8;
-    if (vsize == 8) k_commit_copy<double><<<g, 256, 0, s>>>(J, M, ctl, copy_mask);
-    else k_commit_copy<int32_t><<<g, 256, 0, s>>>(J, M, ctl, copy_mask);
+    if (vsize == 8) launch_k(k_commit_copy<double>, g, 256, 0, s, J, M, ctl, copy_mask);
+    else launch_k(k_commit_copy<int32_t>, g, 256, 0, s, J, M, ctl, copy_mask);
 }
 
 void run_detect_entries(const int32_t *srow, const uint8_t *kind, int64_t n, bool mark_rows, bool mark_cols,
                         const DetectBufs &D, Ctl *ctl, unsigned mask, cudaStream_t s) {
     if (n <= 0) return;
-    k_detect_entries<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(srow, kind, n, mark_rows, mark_cols, D, ctl, mask);
+    launch_k(k_detect_entries, (unsigned)((n + 255) / 256), 256, 0, s, srow, kind, n, mark_rows, mark_cols, D, ctl, mask);
 }
 
 void run_detect_cols(const MatView &AT, const DetectBufs &D, Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms) {
-    k_detect_cols<<<num_sms * 4, 256, 0, s>>>(AT, D, ctl, mask);
+    launch_k(k_detect_cols, num_sms * 4, 256, 0, s, AT, D, ctl, mask);
 }
 
 void run_clear_marks(uint32_t *bm, const int32_t *list, const long long *cnt, int64_t max_n, cudaStream_t s) {
     if (max_n <= 0) return;
-    k_clear_marks<<<grid_for(max_n, 256), 256, 0, s>>>(bm, list, cnt);
+    launch_k(k_clear_marks, grid_for(max_n, 256), 256, 0, s, bm, list, cnt);
 }
 
 void run_transpose_feed(const UpdJob &J, int32_t pad_row, int32_t *trow, int32_t *tcol, uint8_t *top, Ctl *ctl,
                         unsigned mask, cudaStream_t s) {
     if (J.n <= 0) return;
-    k_transpose_feed<<<(unsigned)((J.n + 255) / 256), 256, 0, s>>>(J.row, J.col, J.kind, J.n, pad_row, trow, tcol,
+    launch_k(k_transpose_feed, (unsigned)((J.n + 255) / 256), 256, 0, s, J.row, J.col, J.kind, J.n, pad_row, trow, tcol,
                                                                   top, ctl, mask);
 }
 

@@ -24,4 +24,5 @@ def cuda_available() -> bool:
 def dspg():
     """The CUDA library binding; a GPU test fails (not skips) if it is missing."""
     import paper_2202_08808_gb300 as pkg
-    return pkg.load()
+    pkg.load()
+    return pkg
