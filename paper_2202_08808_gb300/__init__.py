@@ -9,6 +9,7 @@ general updates).  All computation is in the CUDA library built from
 
 from .dspg import (  # noqa: F401
     EXPORTED,
+    STAGES,
     MIN_PLUS_I32,
     OP_DELETE,
     OP_INSERT,
@@ -17,6 +18,7 @@ from .dspg import (  # noqa: F401
     CsrArrays,
     DspgError,
     DynamicSpGEMM,
+    kernel_launches,
     library_path,
     load,
 )

@@ -53,7 +53,7 @@ class _Opt(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "n_updates", "n_unique", "n_insert", "n_update", "n_delete", "n_noop", "touched_rows", "affected_rows",
-        "products", "nnz_written", "relocations", "compactions")]
+        "products", "nnz_written", "relocations", "compactions", "a_entries")]
 
 
 def library_path() -> str:
@@ -85,6 +85,12 @@ def load():
         lib.dspg_recompute_all.argtypes = [p, p]
         lib.dspg_info.restype = i32
         lib.dspg_info.argtypes = [p] + [C.POINTER(i64)] * 5
+        lib.dspg_set_profiling.restype = i32
+        lib.dspg_set_profiling.argtypes = [p, i32]
+        lib.dspg_stage_times.restype = i32
+        lib.dspg_stage_times.argtypes = [p, C.POINTER(C.c_float), i32]
+        lib.dspg_kernel_launches.restype = C.c_ulonglong
+        lib.dspg_kernel_launches.argtypes = []
         lib.dspg_destroy.restype = None
         lib.dspg_destroy.argtypes = [p]
         lib.dspg_last_error.restype = C.c_char_p
@@ -94,7 +100,15 @@ def load():
 
 
 EXPORTED = ["dspg_build", "dspg_apply_batch", "dspg_read_C", "dspg_read_A", "dspg_read_rows_C",
-            "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_destroy", "dspg_last_error"]
+            "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_set_profiling", "dspg_stage_times",
+            "dspg_kernel_launches", "dspg_destroy", "dspg_last_error"]
+
+STAGES = ["sort", "classify", "detect", "merge", "commit", "transpose", "size", "numeric", "splice"]
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().dspg_kernel_launches())
 
 
 def _vdtype(sr: int):
@@ -246,6 +260,14 @@ class DynamicSpGEMM:
         out = np.empty(cnt.value, np.int32)
         self._check(self._lib.dspg_last_affected(self._h, C.byref(cnt), out.ctypes.data, 0, s))
         return out
+
+    def set_profiling(self, on: bool = True) -> None:
+        self._check(self._lib.dspg_set_profiling(self._h, int(on)))
+
+    def stage_times(self) -> dict:
+        ms = (C.c_float * len(STAGES))()
+        self._check(self._lib.dspg_stage_times(self._h, ms, len(STAGES)))
+        return dict(zip(STAGES, [float(x) for x in ms]))
 
     def recompute_all(self, stream=None) -> None:
         self._check(self._lib.dspg_recompute_all(self._h, _stream(stream)))

@@ -42,3 +42,28 @@ def test_last_error_without_handle_is_callable():
     import paper_2202_08808_gb300 as pkg
     lib = pkg.load()
     assert isinstance(lib.dspg_last_error(None), bytes)
+
+
+def _struct_fields(name):
+    with open(os.path.join(ROOT, "include", "dspg.h")) as f:
+        text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", text).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        names = decl.split(None, 1)[1] if not decl.startswith("const") else decl.split(None, 2)[2]
+        for n in names.split(","):
+            fields.append(n.strip().lstrip("*").strip())
+    return fields
+
+
+def test_binding_structs_mirror_the_header():
+    """ctypes mirrors must list the header's fields in order (a missing field
+    makes the library write past the Python-side struct)."""
+    from paper_2202_08808_gb300 import dspg as b
+    assert [f for f, _ in b._Stats._fields_] == _struct_fields("dspg_batch_stats")
+    assert [f for f, _ in b._Opt._fields_] == _struct_fields("dspg_options")
+    assert [f for f, _ in b._Csr._fields_] == _struct_fields("dspg_csr")
+    assert [f for f, _ in b._Upd._fields_] == _struct_fields("dspg_updates")
