@@ -1,0 +1,355 @@
+"""Benchmark: batch-dynamic SpGEMM on one GB300 (and N replicas).
+
+Workload (the stencil configuration): 7-point stencil matrix on a 128^3 grid
+(n = 2,097,152, nnz(A) = 14,581,760), C = A A in (+,.) on double
+(nnz(C) = 51,742,208); each step applies one batch of 10^4 mixed updates
+(inserts / deletes / value changes within two grid hops, 0.07% of nnz(A))
+through the C ABI and brings C up to date.  Inputs are resident in HBM when
+a timed step starts; L2 is flushed (256 MiB write) before every timed step.
+
+Printed JSON line (rank 0): value = batches/s over all ranks (each rank a
+replica on its own GPU: "replicas only", no data-path collective), the
+per-batch latency, the full static GPU recompute and the speedup over it,
+the recompute kernels' HBM roofline, an end-to-end number through the
+public API with host buffers, the oracle's CPU baseline, and clocks.
+
+--impl reference runs the CPU oracle (the deliberately slow reference) on
+the same workload and metric.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dynamic batch latency & speedup vs static GPU recompute; recompute HBM GB/s"
+GRID = 128
+BATCH = 10000
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def make_batches(count, seed0, nupd=BATCH):
+    from workloads import stencil_batch
+    return [stencil_batch(GRID, GRID, GRID, nupd, seed=seed0 + i) for i in range(count)]
+
+
+# --------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (median SM clock, reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ GPU arm
+
+def gpu_arm(args):
+    import torch
+    import paper_2202_08808_gb300 as pkg
+    from workloads import stencil7
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    A = stencil7(GRID, GRID, GRID, seed=1)
+    g = pkg.DynamicSpGEMM(A)
+    info = g.info()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    vsize, s_entry = 8, 12  # double values; column + value bytes per entry
+
+    # device-resident batches: warm-up + timed
+    nb = args.warmup + args.steps
+    host_batches = make_batches(nb, 1000 * (rank + 1))
+    dev_batches = []
+    for b in host_batches:
+        dev_batches.append(type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(),
+                                   torch.from_numpy(b.val).cuda(), torch.from_numpy(b.op).cuda()))
+    torch.cuda.synchronize()
+
+    g.set_profiling(True)
+    for k in range(args.warmup):
+        g.apply_batch(dev_batches[k])
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_acc = {s: 0.0 for s in pkg.STAGES}
+    stats_acc = []
+    launches0 = pkg.kernel_launches()
+    barrier()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        st = g.apply_batch(dev_batches[args.warmup + k])
+        ev1[k].record(stream)
+        stats_acc.append(st)
+        for s, v in g.stage_times().items():
+            stage_acc[s] += v
+    launches = pkg.kernel_launches() - launches0
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    lat = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = sum(lat)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    n_flush_launches = 0  # the L2 flush is torch's, not counted
+
+    # recompute roofline: algorithmic bytes of the numeric stage (gather model)
+    R = sum(s["affected_rows"] for s in stats_acc)
+    a_ent = sum(s["a_entries"] for s in stats_acc)
+    prods = sum(s["products"] for s in stats_acc)
+    nnzw = sum(s["nnz_written"] for s in stats_acc)
+    alg_bytes = 12 * R + (s_entry + 12) * a_ent + s_entry * prods + s_entry * nnzw
+    numeric_ms = stage_acc["numeric"]
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (numeric_ms * 1e-3) / 1e9 if numeric_ms > 0 else 0.0
+
+    # static comparator: full recompute of C from the same A', B' on the device
+    static_ms = []
+    for k in range(3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.recompute_all()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        static_ms.append(e0.elapsed_time(e1))
+    static_med = statistics.median(static_ms)
+
+    # end to end through the public API with pinned host buffers: upload of
+    # the batch, apply, read back the affected row set and its rows of C
+    e2e_ms, h2d, d2h = [], 0, 0
+    pinned = []
+    for b in make_batches(max(3, min(args.steps, 10)), 5000 * (rank + 1)):
+        pinned.append(type(b)(torch.from_numpy(b.row).pin_memory(), torch.from_numpy(b.col).pin_memory(),
+                              torch.from_numpy(b.val).pin_memory(), torch.from_numpy(b.op).pin_memory()))
+    for k, b in enumerate(pinned):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.apply_batch(b)
+        rows = g.last_affected()
+        rp, col, val = g.read_rows_C(rows)
+        t1 = time.perf_counter()
+        e2e_ms.append((t1 - t0) * 1e3)
+        h2d = len(b.row) * (4 + 4 + vsize + 1)
+        d2h = rows.nbytes + rp.nbytes + col.nbytes + val.nbytes + 13 * 8
+    e2e_mean = statistics.mean(e2e_ms)
+
+    # batch-size sweep (latency and speedup at 10^3 .. 10^6)
+    sweep = []
+    if not args.no_sweep:
+        for nupd in (1000, 10000, 100000, 1000000):
+            bs = make_batches(3, 9000 + nupd, nupd)
+            ts = []
+            for b in bs:
+                db = type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(),
+                             torch.from_numpy(b.val).cuda(), torch.from_numpy(b.op).cuda())
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = g.apply_batch(db)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            med = statistics.median(ts)
+            sweep.append({"batch": nupd, "frac_nnz_a": nupd / A.nnz, "latency_ms": round(med, 4),
+                          "speedup_vs_static": round(static_med / med, 2), "affected_rows": st["affected_rows"]})
+
+    out = None
+    if rank == 0:
+        cpu = None if args.no_cpu else cpu_baseline(args, budget_s=args.cpu_budget)
+        ms_per_step = total_ms / args.steps
+        out = {
+            "metric": METRIC,
+            "value": round(world * args.steps / (total_ms * 1e-3), 3),
+            "unit": "batches/s (10^4-update batches)",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "stencil 128^3 7-point, C = A A (+,.) f64, batches of 10^4 mixed updates",
+                       "n": info["n"], "nnz_a": info["nnz_a"], "nnz_c": info["nnz_c"], "batch": BATCH,
+                       "l2": "flushed before every timed step (256 MiB write)", "parallelism": f"replicas x{world}"},
+            "latency_ms": {"mean": round(statistics.mean(lat), 4), "p50": round(statistics.median(lat), 4),
+                           "p99": round(float(np.percentile(lat, 99)), 4)},
+            "static_recompute_ms": round(static_med, 3),
+            "speedup_vs_static": round(static_med / statistics.median(lat), 2),
+            "stages_ms": {s: round(v / args.steps, 4) for s, v in stage_acc.items()},
+            "roofline": {"bound": "hbm", "kernel": "numeric recompute (all bins) of the affected rows",
+                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                         "alg_bytes_per_step": int(alg_bytes / args.steps), "traffic": None},
+            "e2e": {"value": round(1e3 / e2e_mean, 3), "unit": "batches/s (10^4-update batches)",
+                    "latency_ms": round(e2e_mean, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "gpu_launches_per_step": round(launches / args.steps, 1),
+            "clocks": clk,
+            "wall_s_timed": round(wall, 3),
+            "batch_sweep": sweep,
+            "cpu_baseline": cpu,
+        }
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def cpu_baseline(args, budget_s=20.0, steps=None):
+    """The oracle's row-dynamic route (apply, affected rows, recompute of R)
+    on a bounded sample of the same workload: consecutive 10^4 batches until
+    the time budget is used; single-threaded C."""
+    import oracle
+    from oracle import OMat
+    from workloads import stencil7
+    A = stencil7(GRID, GRID, GRID, seed=1)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    times = []
+    k = 0
+    while True:
+        b = make_batches(1, 70000 + k)[0]
+        t0 = time.perf_counter()
+        oracle.row_dynamic(Ao, Co, b)
+        times.append(time.perf_counter() - t0)
+        k += 1
+        if steps is not None and k >= steps:
+            break
+        if steps is None and (sum(times) > budget_s or k >= 200):
+            break
+    mean = statistics.mean(times)
+    return {"value": round(1.0 / mean, 4), "unit": "batches/s (10^4-update batches)", "cores": 1,
+            "kind": "oracle", "latency_ms": round(mean * 1e3, 3),
+            "sample": f"{k} consecutive 10^4-update batches on the 128^3 stencil (apply + affected rows + row recompute)",
+            "times_ms": [round(t * 1e3, 2) for t in times[:20]]}
+
+
+def reference_arm(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    res = cpu_baseline(args, steps=args.steps)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": res["value"], "unit": res["unit"], "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["latency_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "stencil 128^3 7-point, C = A A (+,.) f64, batches of 10^4 mixed updates",
+                   "batch": BATCH},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": res["sample"], "value": res["value"]},
+        "e2e": {"value": res["value"], "unit": res["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()
