@@ -133,6 +133,20 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Warp-aggregated fetch-and-add on a device counter: all 32 lanes call it,
+// each with its own amount (0 allowed); lane l gets the counter value plus
+// the amounts of lanes < l.  One atomic per warp instead of one per lane, so
+// a counter shared by the whole grid does not serialise the kernel.
+__device__ __forceinline__ long long warp_fetch_add(long long *ctr, long long amount) {
+    const int lane = threadIdx.x & 31;
+    const long long incl = warp_incl_scan<long long>(amount);
+    const long long tot = __shfl_sync(0xffffffffu, incl, 31);
+    long long base = 0;
+    if (lane == 31 && tot != 0) base = (long long)atomicAdd((unsigned long long *)ctr, (unsigned long long)tot);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + incl - amount;
+}
+
 // First index in [lo, hi) with a[idx] >= x (a ascending).
 template <typename T>
 __device__ __forceinline__ int64_t lower_bound_dev(const T *a, int64_t lo, int64_t hi, T x) {

@@ -236,34 +236,36 @@ int64_t read_i64(const int64_t *dptr, cudaStream_t s) {
     return v;
 }
 
-// Build a slack-CSR from rows given as (start, length) in a source arrays.
+// Build a slack-CSR from rows given as (start, length) in source arrays
+// (which must not be M's own).  M's buffers are reused when large enough.
 void make_slack(dspg_handle *h, DevMat &M, int64_t nrows, int64_t ncols, int vsize, const int64_t *src_off,
                 const int32_t *len, const int32_t *src_col, const void *src_val, cudaStream_t s) {
-    DevMat N;
-    N.nrows = nrows;
-    N.ncols = ncols;
-    N.vsize = vsize;
-    N.len.reserve(nrows);
-    N.cap.reserve(nrows);
-    N.off.reserve(nrows + 1);
-    N.top.reserve(1);
-    if (nrows > 0) CK(cudaMemcpyAsync(N.len.p, len, sizeof(int32_t) * nrows, cudaMemcpyDeviceToDevice, s));
-    caps_from_lens(N.len.p, N.cap.p, nrows, h->opt.slack_min, h->opt.slack_div, s);
+    M.nrows = nrows;
+    M.ncols = ncols;
+    M.vsize = vsize;
+    M.len.reserve(std::max<int64_t>(nrows, 1));
+    M.cap.reserve(std::max<int64_t>(nrows, 1));
+    M.off.reserve(nrows + 1);
+    M.top.reserve(1);
+    if (nrows > 0) CK(cudaMemcpyAsync(M.len.p, len, sizeof(int32_t) * nrows, cudaMemcpyDeviceToDevice, s));
+    caps_from_lens(M.len.p, M.cap.p, nrows, h->opt.slack_min, h->opt.slack_div, s);
     DBuf<int64_t> tmp;
     tmp.reserve(scan_tmp_entries(nrows) + 1);
-    scan_i32_to_i64(N.cap.p, N.off.p, nrows, tmp.p, s);
-    const int64_t total = read_i64(N.off.p + nrows, s);
-    N.arena_cap = std::max<int64_t>((int64_t)(total * h->opt.arena_headroom), total + 4096);
-    N.col.reserve(N.arena_cap);
-    if (vsize) N.val.reserve(N.arena_cap * vsize);
-    copy_rows(nullptr, nrows, src_off, N.len.p, src_col, src_val, N.off.p, N.col.p, vsize ? (void *)N.val.p : nullptr,
+    scan_i32_to_i64(M.cap.p, M.off.p, nrows, tmp.p, s);
+    const int64_t total = read_i64(M.off.p + nrows, s);
+    const int64_t need = std::max<int64_t>((int64_t)(total * h->opt.arena_headroom), total + 4096);
+    if (M.col.n < need) {
+        M.col.release();
+        M.val.release();
+        M.col.reserve(need);
+    }
+    M.arena_cap = M.col.n;
+    if (vsize) M.val.reserve(M.arena_cap * vsize);
+    copy_rows(nullptr, nrows, src_off, M.len.p, src_col, src_val, M.off.p, M.col.p, vsize ? (void *)M.val.p : nullptr,
               vsize, s, h->num_sms);
     long long t = total;
-    CK(cudaMemcpyAsync(N.top.p, &t, sizeof(long long), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(M.top.p, &t, sizeof(long long), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
-    M.nrows = N.nrows; M.ncols = N.ncols; M.vsize = N.vsize; M.arena_cap = N.arena_cap;
-    M.off.swap(N.off); M.len.swap(N.len); M.cap.swap(N.cap); M.col.swap(N.col); M.val.swap(N.val);
-    M.top.swap(N.top);
 }
 
 // Rebuild M's arena with fresh slack for every row and at least twice the
@@ -420,18 +422,22 @@ CommitJob upd_commit_job(dspg_handle *h, UpdWs &w, unsigned arena_bit, unsigned 
     return J;
 }
 
-// Full recompute of C from A, B (the static product).  Replaces C.
+// Full recompute of C from A, B (the static product).  Replaces C, reusing
+// its arena when it is large enough.
 void static_recompute(dspg_handle *h, cudaStream_t s) {
     ensure_c_ws(h, s);
     const int64_t n = h->A.nrows;
-    CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
-    long long nn = n;
-    CK(cudaMemcpyAsync(&h->ctl->n_affected, &nn, sizeof(long long), cudaMemcpyHostToDevice, s));
     MatView Av = h->A.view(), Bv = h->Bm().view();
     grow_c_stage(h, 1024);
-    run_size_bins(Av, Bv, c_job(h, h->wc.iota.p), n, h->ctl, M_C, s, h->num_sms);
-    read_ctl(h, s);
-    grow_c_stage(h, (int64_t)h->hctl->ubc_total + 1024);
+    for (int attempt = 0; attempt < 3; attempt++) {
+        CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+        long long nn = n;
+        CK(cudaMemcpyAsync(&h->ctl->n_affected, &nn, sizeof(long long), cudaMemcpyHostToDevice, s));
+        run_size_bins(Av, Bv, c_job(h, h->wc.iota.p), n, h->ctl, M_C, s, h->num_sms);
+        read_ctl(h, s);
+        if (!(h->hctl->status & ST_C_STAGE)) break;
+        grow_c_stage(h, (int64_t)h->hctl->c_stage_top + 1024);
+    }
     run_numeric(h->sr, Av, Bv, c_job(h, h->wc.iota.p), h->ctl, M_C, s, h->num_sms);
     read_ctl(h, s);
     if (h->hctl->status & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, "accumulator probe limit reached");

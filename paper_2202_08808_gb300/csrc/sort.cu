@@ -51,54 +51,67 @@ __device__ __forceinline__ void write_sorted(SortOut out, int64_t s, uint64_t ke
     out.op[s] = dead ? OP_DEAD : op[idx];
 }
 
-// ------------------------------------------------------ single-CTA path
+// ---------------------------------------------------- tile-sort path
+//
+// Batches up to TS_TILE * TS_MAXT entries whose packed word
+// (key << ib | arrival index) fits 64 bits: each CTA sorts one tile of
+// TS_TILE words completely in shared memory (all digit passes), and one
+// merge kernel places every word at its global rank = its rank in its own
+// tile + the number of smaller words in each other tile (binary searches).
+// Words are distinct (they carry the index), so ranks are a permutation;
+// an entry is dead when a word with the same key and a later index exists.
+// A single tile finishes (de-duplicates and gathers) in the sort kernel.
 
-constexpr int SS_NT = 1024;
-constexpr int SS_NW = SS_NT / 32;
-constexpr int SS_MAX = 8192;
-constexpr int SS_ROUNDS = SS_MAX / SS_NT;  // 32-entry rounds per warp segment
-constexpr size_t SS_SMEM = 2 * SS_MAX * sizeof(uint64_t) + SS_NW * 256 * sizeof(uint32_t) + 256 * sizeof(uint32_t);
+constexpr int TS_NT = 1024;
+constexpr int TS_NW = TS_NT / 32;
+constexpr int TS_TILE = 4096;
+constexpr int TS_ROUNDS = TS_TILE / TS_NT;  // 32-entry rounds per warp segment
+constexpr int TS_MAXT = 8;
+constexpr size_t TS_SMEM = 2 * TS_TILE * sizeof(uint64_t) + TS_NW * 256 * sizeof(uint32_t) + 256 * sizeof(uint32_t);
 
-int64_t sort_small_max() { return SS_MAX; }
+int64_t sort_small_max() { return (int64_t)TS_TILE * TS_MAXT; }
 
-__global__ void __launch_bounds__(SS_NT, 1)
-k_sort_small(const int32_t *row, const int32_t *col, const void *val, const uint8_t *op, int n, int64_t nrows,
-             int64_t ncols, int sr, bool check_values, SortOut out, Ctl *ctl, unsigned skip_mask, int cb, int ib,
-             int kb) {
+__global__ void __launch_bounds__(TS_NT, 1)
+k_tile_sort(const int32_t *row, const int32_t *col, const void *val, const uint8_t *op, int n, int64_t nrows,
+            int64_t ncols, int sr, bool check_values, SortOut out, Ctl *ctl, unsigned skip_mask, int cb, int ib,
+            int kb, uint64_t *words_out) {
     extern __shared__ uint64_t sm[];
     if (failed(ctl, skip_mask)) return;
     uint64_t *b0 = sm;
-    uint64_t *b1 = sm + SS_MAX;
-    uint32_t *wc = (uint32_t *)(sm + 2 * SS_MAX);
-    uint32_t *dbase = wc + SS_NW * 256;
+    uint64_t *b1 = sm + TS_TILE;
+    uint32_t *wc = (uint32_t *)(sm + 2 * TS_TILE);
+    uint32_t *dbase = wc + TS_NW * 256;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int lo = blockIdx.x * TS_TILE;
+    const int cnt = min(TS_TILE, n - lo);
 
-    for (int i = tid; i < n; i += SS_NT) {
-        int32_t r = row[i], c = col[i];
-        uint8_t o = op[i];
-        bool ok = entry_ok(r, c, o, val, i, nrows, ncols, sr, check_values);
+    for (int i = tid; i < cnt; i += TS_NT) {
+        const int gi = lo + i;
+        const int32_t r = row[gi], c = col[gi];
+        const uint8_t o = op[gi];
+        const bool ok = entry_ok(r, c, o, val, gi, nrows, ncols, sr, check_values);
         if (!ok) set_status(ctl, ST_INVALID);
-        uint64_t key = ok ? (((uint64_t)(uint32_t)r << cb) | (uint32_t)c) : 0;
-        b0[i] = (key << ib) | (uint64_t)i;
+        const uint64_t key = ok ? (((uint64_t)(uint32_t)r << cb) | (uint32_t)c) : 0;
+        b0[i] = (key << ib) | (uint64_t)gi;
     }
     __syncthreads();
 
-    const int seg = (n + SS_NW - 1) / SS_NW;
+    const int seg = (cnt + TS_NW - 1) / TS_NW;
     const int seg_lo = w * seg;
-    const int seg_hi = min(n, seg_lo + seg);
+    const int seg_hi = min(cnt, seg_lo + seg);
     const int passes = (kb + 7) / 8;
     for (int p = 0; p < passes; p++) {
         const int shift = ib + 8 * p;
-        for (int j = tid; j < SS_NW * 256; j += SS_NT) wc[j] = 0;
+        for (int j = tid; j < TS_NW * 256; j += TS_NT) wc[j] = 0;
         __syncthreads();
-        uint32_t lr[SS_ROUNDS];
+        uint32_t lr[TS_ROUNDS];
 #pragma unroll
-        for (int r = 0; r < SS_ROUNDS; r++) {
-            int idx = seg_lo + r * 32 + lane;
-            bool valid = idx < seg_hi;
-            unsigned d = valid ? (unsigned)((b0[idx] >> shift) & 255) : 0xffffffffu;
-            unsigned peers = __match_any_sync(0xffffffffu, d);
-            uint32_t before = valid ? wc[w * 256 + d] : 0;
+        for (int r = 0; r < TS_ROUNDS; r++) {
+            const int idx = seg_lo + r * 32 + lane;
+            const bool valid = idx < seg_hi;
+            const unsigned d = valid ? (unsigned)((b0[idx] >> shift) & 255) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t before = valid ? wc[w * 256 + d] : 0;
             __syncwarp();
             lr[r] = before + __popc(peers & lanemask_lt());
             if (valid && lane == 31 - __clz(peers)) wc[w * 256 + d] = before + __popc(peers);
@@ -106,43 +119,95 @@ k_sort_small(const int32_t *row, const int32_t *col, const void *val, const uint
         }
         __syncthreads();
         if (tid < 256) {
-            uint32_t s = 0;
-            for (int ww = 0; ww < SS_NW; ww++) {
-                uint32_t c = wc[ww * 256 + tid];
-                wc[ww * 256 + tid] = s;
-                s += c;
+            uint32_t acc = 0;
+            for (int ww = 0; ww < TS_NW; ww++) {
+                const uint32_t c = wc[ww * 256 + tid];
+                wc[ww * 256 + tid] = acc;
+                acc += c;
             }
-            dbase[tid] = s;
+            dbase[tid] = acc;
         }
         __syncthreads();
         if (tid < 32) {  // exclusive scan of the 256 digit totals by one warp
-            uint32_t v[8], s = 0;
-            for (int j = 0; j < 8; j++) { v[j] = dbase[tid * 8 + j]; s += v[j]; }
-            uint32_t incl = warp_incl_scan<uint32_t>(s);
-            uint32_t e = incl - s;
-            for (int j = 0; j < 8; j++) { dbase[tid * 8 + j] = e; e += v[j]; }
+            uint32_t v[8], acc = 0;
+            for (int j = 0; j < 8; j++) {
+                v[j] = dbase[tid * 8 + j];
+                acc += v[j];
+            }
+            const uint32_t incl = warp_incl_scan<uint32_t>(acc);
+            uint32_t e = incl - acc;
+            for (int j = 0; j < 8; j++) {
+                dbase[tid * 8 + j] = e;
+                e += v[j];
+            }
         }
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < SS_ROUNDS; r++) {
-            int idx = seg_lo + r * 32 + lane;
+        for (int r = 0; r < TS_ROUNDS; r++) {
+            const int idx = seg_lo + r * 32 + lane;
             if (idx < seg_hi) {
-                uint64_t x = b0[idx];
-                unsigned d = (unsigned)((x >> shift) & 255);
+                const uint64_t x = b0[idx];
+                const unsigned d = (unsigned)((x >> shift) & 255);
                 b1[dbase[d] + wc[w * 256 + d] + lr[r]] = x;
             }
         }
         __syncthreads();
-        uint64_t *t = b0; b0 = b1; b1 = t;
+        uint64_t *t = b0;
+        b0 = b1;
+        b1 = t;
     }
 
-    const uint64_t imask = (uint64_t(1) << ib) - 1;
-    for (int s = tid; s < n; s += SS_NT) {
-        uint64_t x = b0[s];
-        uint64_t key = x >> ib;
-        bool dead = (s + 1 < n) && ((b0[s + 1] >> ib) == key);
-        write_sorted(out, s, key, x & imask, dead, cb, val, op, sr);
+    if (gridDim.x == 1) {
+        const uint64_t imask = (uint64_t(1) << ib) - 1;
+        for (int s = tid; s < cnt; s += TS_NT) {
+            const uint64_t x = b0[s];
+            const uint64_t key = x >> ib;
+            const bool dead = (s + 1 < cnt) && ((b0[s + 1] >> ib) == key);
+            write_sorted(out, s, key, x & imask, dead, cb, val, op, sr);
+        }
+    } else {
+        for (int s = tid; s < cnt; s += TS_NT) words_out[lo + s] = b0[s];
     }
+}
+
+__device__ __forceinline__ int count_less(const uint64_t *a, int n, uint64_t x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int count_le(const uint64_t *a, int n, uint64_t x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_tile_merge(const uint64_t *words, int n, int ib, int cb, const void *val, const uint8_t *op, int sr,
+                             SortOut out, const Ctl *ctl, unsigned skip_mask) {
+    if (failed(ctl, skip_mask)) return;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int t = e / TS_TILE;
+    const int ntiles = (n + TS_TILE - 1) / TS_TILE;
+    const uint64_t imask = (uint64_t(1) << ib) - 1;
+    const uint64_t w = words[e];
+    const uint64_t key = w >> ib;
+    int rank = e - t * TS_TILE;
+    int le = 0;  // words with a key <= key
+    for (int u = 0; u < ntiles; u++) {
+        const int ulo = u * TS_TILE;
+        const int ucnt = min(TS_TILE, n - ulo);
+        if (u != t) rank += count_less(words + ulo, ucnt, w);
+        le += count_le(words + ulo, ucnt, w | imask);
+    }
+    const bool dead = rank != le - 1;
+    write_sorted(out, rank, key, w & imask, dead, cb, val, op, sr);
 }
 
 // ------------------------------------------------------- multi-CTA path
@@ -266,14 +331,18 @@ void sort_updates(const int32_t *row, const int32_t *col, const void *val, const
     if (n <= 0) return;
     const int cb = bits_for(ncols), rb = bits_for(nrows), ib = bits_for(n);
     const int kb = cb + rb;
-    if (n <= SS_MAX && kb + ib <= 64) {
+    if (n <= (int64_t)TS_TILE * TS_MAXT && kb + ib <= 64) {
         static bool attr_set = false;
         if (!attr_set) {
-            cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SS_SMEM);
+            cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS_SMEM);
             attr_set = true;
         }
-        launch_k(k_sort_small, 1, SS_NT, SS_SMEM, s, row, col, val, op, (int)n, nrows, ncols, sr, check_values, out, ctl,
-                                              skip_mask, cb, ib, kb);
+        const int tiles = (int)((n + TS_TILE - 1) / TS_TILE);
+        launch_k(k_tile_sort, tiles, TS_NT, TS_SMEM, s, row, col, val, op, (int)n, nrows, ncols, sr, check_values, out,
+                 ctl, skip_mask, cb, ib, kb, tmp.k0);
+        if (tiles > 1)
+            launch_k(k_tile_merge, (unsigned)((n + 255) / 256), 256, 0, s, (const uint64_t *)tmp.k0, (int)n, ib, cb, val,
+                     op, sr, out, (const Ctl *)ctl, skip_mask);
         return;
     }
     unsigned nblk = (unsigned)((n + 255) / 256);

@@ -73,39 +73,53 @@ __device__ __forceinline__ int pick_bin(long long ubc, int dense_mode) {
     return BIN_GD;
 }
 
+// A warp sizes 32 rows of R at a time (all lanes on one row, lane r keeping
+// row r's bound ub), then hands out staging room (ub entries per row, so the
+// numeric kernels need no allocation) and bin slots with one atomic per warp
+// and counter.
 __global__ void k_size_bins(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask) {
     if (failed(ctl, mask)) return;
     const long long nR = ctl->n_affected;
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    long long prod_acc = 0, ubc_acc = 0, a_acc = 0;
-    for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nR; t += nwarps) {
-        const int32_t i = J.R[t];
-        const int64_t aoff = A.off[i];
-        const int alen = A.len[i];
-        long long s = 0;
-        for (int a = lane; a < alen; a += 32) s += B.len[A.col[aoff + a]];
-        s = warp_sum<long long>(s);
-        if (lane == 0) {
-            const long long ubc = s < J.m ? s : J.m;
-            prod_acc += s;
-            ubc_acc += ubc;
-            a_acc += alen;
-            if (s == 0) {
-                J.slen[t] = 0;
-                J.soff[t] = 0;
-            } else {
-                const int b = pick_bin(ubc, J.dense_mode);
-                const long long x = atomic_add_ll2(&ctl->bin_count[b], 1);
-                J.bins[(int64_t)b * J.bin_cap + x] = (int32_t)t;
-            }
+    long long prod_acc = 0, a_acc = 0;
+    for (long long t0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; t0 < nR; t0 += nwarps * 32) {
+        const long long my_t = t0 + lane;
+        const bool valid = my_t < nR;
+        const int32_t my_i = valid ? J.R[my_t] : 0;
+        const int64_t my_aoff = valid ? A.off[my_i] : 0;
+        const int my_alen = valid ? A.len[my_i] : 0;
+        long long my_s = 0;
+        const int cnt = (int)(nR - t0 < 32 ? nR - t0 : 32);
+        for (int rr = 0; rr < cnt; rr++) {
+            const int64_t aoff = __shfl_sync(0xffffffffu, my_aoff, rr);
+            const int alen = __shfl_sync(0xffffffffu, my_alen, rr);
+            long long s = 0;
+            for (int a = lane; a < alen; a += 32) s += B.len[A.col[aoff + a]];
+            s = warp_sum<long long>(s);
+            if (lane == rr) my_s = s;
         }
+        const long long ubc = my_s < J.m ? my_s : J.m;
+        const long long so = warp_fetch_add(&ctl->c_stage_top, ubc);
+        if (valid) {
+            J.soff[my_t] = so;
+            J.slen[my_t] = 0;
+            if (so + ubc > J.st_cap) set_status(ctl, ST_C_STAGE);
+        }
+        const int b = (valid && my_s > 0) ? pick_bin(ubc, J.dense_mode) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        long long bb = 0;
+        if (b >= 0 && lane == leader) bb = atomic_add_ll2(&ctl->bin_count[b], __popc(peers));
+        bb = __shfl_sync(0xffffffffu, bb, leader);
+        if (b >= 0) J.bins[(int64_t)b * J.bin_cap + bb + __popc(peers & lanemask_lt())] = (int32_t)my_t;
+        prod_acc += warp_sum<long long>(valid ? my_s : 0);
+        a_acc += warp_sum<long long>(my_alen);
     }
-    if (lane == 0 && prod_acc) {
-        atomic_add_ll2(&ctl->products, prod_acc);
-        atomic_add_ll2(&ctl->ubc_total, ubc_acc);
+    if (lane == 0) {
+        if (prod_acc) atomic_add_ll2(&ctl->products, prod_acc);
+        if (a_acc) atomic_add_ll2(&ctl->a_entries, a_acc);
     }
-    if (lane == 0 && a_acc) atomic_add_ll2(&ctl->a_entries, a_acc);
 }
 
 // --------------------------------------------------- product generators
@@ -266,6 +280,7 @@ k_num_warp_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) 
     int32_t *keys = (int32_t *)((T *)smem + (size_t)NW * (TS + HC)) + (size_t)w * TS;
     int32_t *ck = (int32_t *)((T *)smem + (size_t)NW * (TS + HC)) + (size_t)NW * TS + (size_t)w * HC;
     T *sv = (T *)J.st_val;
+    long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = (long long)blockIdx.x * NW + w; it < cnt; it += (long long)gridDim.x * NW) {
         const int t = J.bins[(int64_t)bin * J.bin_cap + it];
@@ -296,15 +311,10 @@ k_num_warp_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) 
         }
         if (n > HC) n = HC;  // unreachable when ub <= HC
         __syncwarp();
-        long long so = 0;
-        if (lane == 0) {
-            so = atomic_add_ll2(&ctl->c_stage_top, n);
-            if (so + n > J.st_cap) set_status(ctl, ST_C_STAGE);
-            J.slen[t] = n;
-            J.soff[t] = so;
-        }
-        so = __shfl_sync(0xffffffffu, so, 0);
-        const bool fits = so + n <= J.st_cap;
+        const long long so = J.soff[t];  // room for the row's product bound, from the sizing pass
+        if (lane == 0) J.slen[t] = n;
+        nnz_acc += n;
+        const bool fits = true;
         if (n <= 32) {
             // rank of each entry among distinct column keys
             const int32_t myk = lane < n ? ck[lane] : 0x7fffffff;
@@ -335,9 +345,9 @@ k_num_warp_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) 
                     sv[so + s] = cv[s];
                 }
         }
-        if (lane == 0) atomic_add_ll2(&ctl->nnz_written, n);
         __syncwarp();
     }
+    if (lane == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
 }
 
 // ------------------------------------------------------- CTA hash kernel
@@ -363,6 +373,7 @@ k_num_cta_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
     int32_t *ck = keys + TS;
     T *sv = (T *)J.st_val;
     BlockProdSmem<T> ps{p_boff, p_av, p_incl, p_blen, p_wsum};
+    long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
         const int t = J.bins[(int64_t)bin * J.bin_cap + it];
@@ -404,12 +415,9 @@ k_num_cta_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
         while (N < n) N <<= 1;
         for (int s = n + tid; s < N; s += 256) ck[s] = 0x7fffffff;
         if (tid == 0) {
-            const long long so = atomic_add_ll2(&ctl->c_stage_top, n);
-            if (so + n > J.st_cap) set_status(ctl, ST_C_STAGE);
             J.slen[t] = n;
-            J.soff[t] = so;
-            s_so = so;
-            atomic_add_ll2(&ctl->nnz_written, n);
+            s_so = J.soff[t];
+            nnz_acc += n;
         }
         __syncthreads();
         for (int size = 2; size <= N; size <<= 1) {
@@ -422,13 +430,13 @@ k_num_cta_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
             }
         }
         const long long so = s_so;
-        if (so + n <= J.st_cap)
-            for (int s = tid; s < n; s += 256) {
-                J.st_col[so + s] = ck[s];
-                sv[so + s] = cv[s];
-            }
+        for (int s = tid; s < n; s += 256) {
+            J.st_col[so + s] = ck[s];
+            sv[so + s] = cv[s];
+        }
         __syncthreads();
     }
+    if (tid == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
 }
 
 // ------------------------------------------------- global dense kernel
@@ -441,7 +449,6 @@ k_num_gdense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
     __shared__ T p_av[512];
     __shared__ int p_incl[512], p_blen[512], p_wsum[32];
     __shared__ int s_lo, s_hi;
-    __shared__ long long s_so;
     __shared__ int s_n;
     if (failed(ctl, mask)) return;
     const int tid = threadIdx.x;
@@ -449,6 +456,7 @@ k_num_gdense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
     uint32_t *msk = J.gd_mask + (int64_t)blockIdx.x * (J.gd_w / 32);
     T *sv = (T *)J.st_val;
     BlockProdSmem<T> ps{p_boff, p_av, p_incl, p_blen, p_wsum};
+    long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
         const int t = J.bins[(int64_t)bin * J.bin_cap + it];
@@ -477,16 +485,11 @@ k_num_gdense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
         __syncthreads();
         const int n = s_n;
         if (tid == 0) {
-            const long long so = atomic_add_ll2(&ctl->c_stage_top, n);
-            if (so + n > J.st_cap) set_status(ctl, ST_C_STAGE);
             J.slen[t] = n;
-            J.soff[t] = so;
-            s_so = so;
-            atomic_add_ll2(&ctl->nnz_written, n);
+            nnz_acc += n;
         }
-        __syncthreads();
-        const long long so = s_so;
-        const bool fits = so + n <= J.st_cap;
+        const long long so = J.soff[t];
+        const bool fits = true;
         int run = 0;  // entries written by earlier chunks
         for (int x0 = w0; x0 <= w1; x0 += 512) {
             const int x = x0 + tid;
@@ -511,6 +514,7 @@ k_num_gdense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
             __syncthreads();
         }
     }
+    if (tid == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
 }
 
 // ----------------------------------------------------- dense small-m kernels
@@ -529,6 +533,7 @@ k_num_warp_dense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin,
     for (int s = lane; s < mp; s += 32) acc[s] = Sr<SR>::zero();
     msk[lane] = 0u;
     __syncwarp();
+    long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = (long long)blockIdx.x * NW + w; it < cnt; it += (long long)gridDim.x * NW) {
         const int t = J.bins[(int64_t)bin * J.bin_cap + it];
@@ -542,32 +547,24 @@ k_num_warp_dense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin,
         const int pc = __popc(word);
         const int incl = warp_incl_scan<int>(pc);
         const int n = __shfl_sync(0xffffffffu, incl, 31);
-        long long so = 0;
-        if (lane == 0) {
-            so = atomic_add_ll2(&ctl->c_stage_top, n);
-            if (so + n > J.st_cap) set_status(ctl, ST_C_STAGE);
-            J.slen[t] = n;
-            J.soff[t] = so;
-            atomic_add_ll2(&ctl->nnz_written, n);
-        }
-        so = __shfl_sync(0xffffffffu, so, 0);
-        const bool fits = so + n <= J.st_cap;
+        const long long so = J.soff[t];
+        if (lane == 0) J.slen[t] = n;
+        nnz_acc += n;
         int o = incl - pc;
         uint32_t bits = word;
         while (bits) {
             const int b = __ffs(bits) - 1;
             bits &= bits - 1;
             const int j = (lane << 5) + b;
-            if (fits) {
-                J.st_col[so + o] = j;
-                sv[so + o] = acc[j];
-            }
+            J.st_col[so + o] = j;
+            sv[so + o] = acc[j];
             acc[j] = Sr<SR>::zero();
             o++;
         }
         msk[lane] = 0u;
         __syncwarp();
     }
+    if (lane == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
 }
 
 template <int SR>
@@ -588,6 +585,7 @@ k_num_cta_dense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin, 
     if (tid < 32) msk[tid] = 0u;
     __syncthreads();
     BlockProdSmem<T> ps{p_boff, p_av, p_incl, p_blen, p_wsum};
+    long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
         const int t = J.bins[(int64_t)bin * J.bin_cap + it];
@@ -602,26 +600,19 @@ k_num_cta_dense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin, 
             const int pc = __popc(word);
             const int incl = warp_incl_scan<int>(pc);
             const int n = __shfl_sync(0xffffffffu, incl, 31);
-            long long so = 0;
+            const long long so = J.soff[t];
             if (lane == 0) {
-                so = atomic_add_ll2(&ctl->c_stage_top, n);
-                if (so + n > J.st_cap) set_status(ctl, ST_C_STAGE);
                 J.slen[t] = n;
-                J.soff[t] = so;
-                atomic_add_ll2(&ctl->nnz_written, n);
+                nnz_acc += n;
             }
-            so = __shfl_sync(0xffffffffu, so, 0);
-            const bool fits = so + n <= J.st_cap;
             int o = incl - pc;
             uint32_t bits = word;
             while (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
                 const int j = (lane << 5) + b;
-                if (fits) {
-                    J.st_col[so + o] = j;
-                    sv[so + o] = acc[j];
-                }
+                J.st_col[so + o] = j;
+                sv[so + o] = acc[j];
                 acc[j] = Sr<SR>::zero();
                 o++;
             }
@@ -629,6 +620,7 @@ k_num_cta_dense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin, 
         }
         __syncthreads();
     }
+    if (tid == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
 }
 
 // -------------------------------------------------------------- host

@@ -37,19 +37,29 @@ __device__ __forceinline__ long long atomic_add_ll(long long *p, long long v) {
 __global__ void k_segments(const int32_t *srow, int64_t n, int64_t nrows, int32_t *seg_lo, int32_t *seg_hi,
                            long long *n_seg, const Ctl *ctl, unsigned mask) {
     if (failed(ctl, mask)) return;
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    int32_t r = srow[s];
-    if ((int64_t)r >= nrows) return;  // padding entries of a forwarded batch
-    if (s > 0 && srow[s - 1] == r) return;
-    int64_t hi = upper_bound_dev<int32_t>(srow, s, n, r);
-    long long t = atomic_add_ll(n_seg, 1);
-    seg_lo[t] = (int32_t)s;
-    seg_hi[t] = (int32_t)hi;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = base + threadIdx.x;
+        int32_t r = 0;
+        bool head = false;
+        if (s < n) {
+            r = srow[s];
+            // padding entries of a forwarded batch sit in a row past the end
+            head = (int64_t)r < nrows && (s == 0 || srow[s - 1] != r);
+        }
+        const long long t = warp_fetch_add(n_seg, head ? 1 : 0);
+        if (head) {
+            seg_lo[t] = (int32_t)s;
+            seg_hi[t] = (int32_t)upper_bound_dev<int32_t>(srow, s, n, r);
+        }
+    }
 }
 
 // ------------------------------------------------------------- classify
 
+// A warp takes 32 segments at a time: it classifies them one after the
+// other (all lanes on one segment), lane r keeping segment r's totals; then
+// it allocates merge items, staging and copy items for the 32 segments with
+// one atomic per counter, and finally writes the INS/UPD entries.
 template <typename T>
 __global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigned stage_bit) {
     if (failed(ctl, mask)) return;
@@ -59,86 +69,105 @@ __global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigne
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const T *bval = (const T *)J.val;
     T *sval = (T *)J.st_val;
-    for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nseg; t += nwarps) {
-        const int lo = J.seg_lo[t], hi = J.seg_hi[t];
-        const int32_t r = J.row[lo];
-        const int64_t base = M.off[r];
-        const int L = M.len[r];
-        const int32_t *rc = M.col + base;
-        int cins = 0, cdel = 0, cupd = 0, cnop = 0;
-        for (int u0 = lo; u0 < hi; u0 += 32) {
-            const int x = u0 + lane;
-            int ins = 0, del = 0;
-            if (x < hi) {
-                const int32_t c = J.col[x];
-                const uint8_t op = J.op[x];
-                const int p = (int)lower_bound_dev<int32_t>(rc, 0, L, c);
-                const bool present = p < L && rc[p] == c;
-                uint8_t k;
-                if (op == OP_DEAD) k = K_NOP;
-                else if (op == OP_DELETE) k = present ? K_DEL : K_NOP;
-                else k = present ? K_UPD : K_INS;
-                J.kind[x] = k;
-                J.pos[x] = p;
-                ins = k == K_INS;
-                del = k == K_DEL;
-                cupd += k == K_UPD;
-                cnop += (k == K_NOP && op == OP_DELETE);
+    long long s_ins = 0, s_del = 0, s_upd = 0, s_nop = 0;
+    for (long long t0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; t0 < nseg; t0 += nwarps * 32) {
+        int my_L = 0, my_ins = 0, my_del = 0, my_changed = 0;
+        int32_t my_row = 0;
+        for (int rr = 0; rr < 32; rr++) {
+            const long long t = t0 + rr;
+            if (t >= nseg) break;
+            const int lo = J.seg_lo[t], hi = J.seg_hi[t];
+            const int32_t r = J.row[lo];
+            const int64_t base = M.off[r];
+            const int L = M.len[r];
+            const int32_t *rc = M.col + base;
+            int cins = 0, cdel = 0, cupd = 0, cnop = 0;
+            for (int u0 = lo; u0 < hi; u0 += 32) {
+                const int x = u0 + lane;
+                int ins = 0, del = 0;
+                if (x < hi) {
+                    const int32_t c = J.col[x];
+                    const uint8_t op = J.op[x];
+                    const int p = (int)lower_bound_dev<int32_t>(rc, 0, L, c);
+                    const bool present = p < L && rc[p] == c;
+                    uint8_t k;
+                    if (op == OP_DEAD) k = K_NOP;
+                    else if (op == OP_DELETE) k = present ? K_DEL : K_NOP;
+                    else k = present ? K_UPD : K_INS;
+                    J.kind[x] = k;
+                    J.pos[x] = p;
+                    ins = k == K_INS;
+                    del = k == K_DEL;
+                    cupd += k == K_UPD;
+                    cnop += (k == K_NOP && op == OP_DELETE);
+                }
+                const int ii = warp_incl_scan<int>(ins), di = warp_incl_scan<int>(del);
+                if (x < hi) {
+                    J.insx[x] = cins + ii - ins;
+                    J.delx[x] = cdel + di - del;
+                }
+                cins += __shfl_sync(0xffffffffu, ii, 31);
+                cdel += __shfl_sync(0xffffffffu, di, 31);
             }
-            const int ii = warp_incl_scan<int>(ins), di = warp_incl_scan<int>(del);
-            if (x < hi) {
-                J.insx[x] = cins + ii - ins;
-                J.delx[x] = cdel + di - del;
+            cupd = warp_sum<int>(cupd);
+            cnop = warp_sum<int>(cnop);
+            s_ins += cins;
+            s_del += cdel;
+            s_upd += cupd;
+            s_nop += cnop;
+            if (lane == rr) {
+                my_L = L;
+                my_ins = cins;
+                my_del = cdel;
+                my_changed = (cins + cdel + cupd) > 0;
+                my_row = r;
             }
-            cins += __shfl_sync(0xffffffffu, ii, 31);
-            cdel += __shfl_sync(0xffffffffu, di, 31);
         }
-        cupd = warp_sum<int>(cupd);
-        cnop = warp_sum<int>(cnop);
-        if (lane == 0) {
-            if (cins) atomic_add_ll(&u->ins, cins);
-            if (cdel) atomic_add_ll(&u->del, cdel);
-            if (cupd) atomic_add_ll(&u->upd, cupd);
-            if (cnop) atomic_add_ll(&u->nop, cnop);
-        }
-        if (cins + cdel + cupd == 0) continue;  // row unchanged
-        const int nl = L + cins - cdel;
-        const int nch = (L + CH - 1) / CH;
-        long long m = 0, soff = 0, cb = 0;
+        const int my_nl = my_L + my_ins - my_del;
+        const int my_nch = my_changed ? (my_L + CH - 1) / CH : 0;
+        const long long m = warp_fetch_add(&u->n_merge, my_changed);
+        const long long soff = warp_fetch_add(&u->stage_top, my_changed ? my_nl : 0);
+        const long long cb = warp_fetch_add(&u->n_chunk, my_nch);
         int ok = 1;
-        if (lane == 0) {
-            m = atomic_add_ll(&u->n_merge, 1);
-            soff = atomic_add_ll(&u->stage_top, nl);
-            cb = nch ? atomic_add_ll(&u->n_chunk, nch) : 0;
-            ok = (soff + nl <= J.st_cap) && (cb + nch <= J.ch_cap);
+        if (my_changed) {
+            ok = (soff + my_nl <= J.st_cap) && (cb + my_nch <= J.ch_cap);
             if (!ok) set_status(ctl, stage_bit);
             else {
-                J.m_row[m] = r;
-                J.m_seg[m] = (int32_t)t;
-                J.m_len[m] = nl;
+                J.m_row[m] = my_row;
+                J.m_seg[m] = (int32_t)(t0 + lane);
+                J.m_len[m] = my_nl;
                 J.m_soff[m] = soff;
-                J.m_nins[m] = cins;
-                J.m_ndel[m] = cdel;
+                J.m_nins[m] = my_ins;
+                J.m_ndel[m] = my_del;
+                for (int c = 0; c < my_nch; c++) {
+                    J.ch_item[cb + c] = (int32_t)m;
+                    J.ch_part[cb + c] = c;
+                }
             }
-        }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) continue;
-        m = __shfl_sync(0xffffffffu, m, 0);
-        soff = __shfl_sync(0xffffffffu, soff, 0);
-        cb = __shfl_sync(0xffffffffu, cb, 0);
-        for (int c = lane; c < nch; c += 32) {
-            J.ch_item[cb + c] = (int32_t)m;
-            J.ch_part[cb + c] = c;
         }
         __syncwarp();
-        for (int x = lo + lane; x < hi; x += 32) {
-            const uint8_t k = J.kind[x];
-            if (k == K_INS || k == K_UPD) {
-                const int o = J.pos[x] - J.delx[x] + J.insx[x];
-                J.st_col[soff + o] = J.col[x];
-                if (sval) sval[soff + o] = bval[x];
+        for (int rr = 0; rr < 32; rr++) {
+            const long long t = t0 + rr;
+            if (t >= nseg) break;
+            const int write = __shfl_sync(0xffffffffu, my_changed && ok, rr);
+            const long long so = __shfl_sync(0xffffffffu, soff, rr);
+            if (!write) continue;
+            const int lo = J.seg_lo[t], hi = J.seg_hi[t];
+            for (int x = lo + lane; x < hi; x += 32) {
+                const uint8_t k = J.kind[x];
+                if (k == K_INS || k == K_UPD) {
+                    const int o = J.pos[x] - J.delx[x] + J.insx[x];
+                    J.st_col[so + o] = J.col[x];
+                    if (sval) sval[so + o] = bval[x];
+                }
             }
         }
+    }
+    if (lane == 0) {
+        if (s_ins) atomic_add_ll(&u->ins, s_ins);
+        if (s_del) atomic_add_ll(&u->del, s_del);
+        if (s_upd) atomic_add_ll(&u->upd, s_upd);
+        if (s_nop) atomic_add_ll(&u->nop, s_nop);
     }
 }
 
@@ -181,25 +210,30 @@ __global__ void k_merge_copy(UpdJob J, MatView M, const Ctl *ctl, unsigned mask)
 __global__ void k_commit_plan(CommitJob J, MatView M, Ctl *ctl, unsigned mask, int slack_min, int slack_div) {
     if (failed(ctl, mask)) return;
     const long long n = *J.count;
-    for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < n;
-         m += (long long)gridDim.x * blockDim.x) {
-        const int32_t r = J.rows[m];
-        const int32_t nl = J.lens[m];
-        int64_t d;
-        int32_t c;
-        if (nl <= M.cap[r]) {
-            d = M.off[r];
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+        const long long m = base + threadIdx.x;
+        const bool valid = m < n;
+        int32_t r = 0, nl = 0, c = 0;
+        bool reloc = false;
+        if (valid) {
+            r = J.rows[m];
+            nl = J.lens[m];
             c = M.cap[r];
-        } else {
-            c = slack_cap(nl, slack_min, slack_div);
-            d = atomic_add_ll(M.top, c);
-            if (d + c > M.arena_cap) set_status(ctl, J.arena_bit);
-            atomic_add_ll(J.reloc, 1);
+            if (nl > c) {
+                reloc = true;
+                c = slack_cap(nl, slack_min, slack_div);
+            }
         }
+        const long long dr = warp_fetch_add(M.top, reloc ? c : 0);
+        const unsigned nrel = __popc(__ballot_sync(0xffffffffu, reloc));
+        if ((threadIdx.x & 31) == 0 && nrel) atomic_add_ll(J.reloc, nrel);
+        const int nch = valid ? (nl > 0 ? (nl + CH - 1) / CH : 1) : 0;
+        const long long cb = warp_fetch_add(J.cc_count, nch);
+        if (!valid) continue;
+        int64_t d = reloc ? (int64_t)dr : M.off[r];
+        if (reloc && d + c > M.arena_cap) set_status(ctl, J.arena_bit);
         J.dest[m] = d;
         J.ncap[m] = c;
-        const int nch = nl > 0 ? (nl + CH - 1) / CH : 1;
-        const long long cb = atomic_add_ll(J.cc_count, nch);
         if (cb + nch > J.cc_cap) {
             set_status(ctl, J.stage_bit);
             continue;
@@ -245,25 +279,28 @@ __global__ void k_commit_copy(CommitJob J, MatView M, const Ctl *ctl, unsigned m
 // change their matrix (kind INS, UPD or DEL).  The second set is read from
 // the transposed pattern of A *before* this batch; it equals the set taken
 // over A' because a pattern difference at (i,k) already puts i in rows(A*).
-__device__ __forceinline__ void mark(uint32_t *bm, int32_t i, int32_t *list, long long *cnt) {
-    const uint32_t bit = 1u << (i & 31);
-    if (((volatile uint32_t *)bm)[i >> 5] & bit) return;
-    const uint32_t old = atomicOr(&bm[i >> 5], bit);
-    if (!(old & bit)) {
-        long long t = atomic_add_ll(cnt, 1);
-        list[t] = i;
+// Sets bit i of bm; the lanes that set a fresh bit append i to list with one
+// atomic per warp.  All 32 lanes must call it (want = false to abstain).
+__device__ __forceinline__ void mark_warp(uint32_t *bm, bool want, int32_t i, int32_t *list, long long *cnt) {
+    bool fresh = false;
+    if (want) {
+        const uint32_t bit = 1u << (i & 31);
+        if (!(((volatile uint32_t *)bm)[i >> 5] & bit)) fresh = !(atomicOr(&bm[i >> 5], bit) & bit);
     }
+    const long long t = warp_fetch_add(cnt, fresh ? 1 : 0);
+    if (fresh) list[t] = i;
 }
 
 __global__ void k_detect_entries(const int32_t *srow, const uint8_t *kind, int64_t n, int mark_rows, int mark_cols,
                                  DetectBufs D, Ctl *ctl, unsigned mask) {
     if (failed(ctl, mask)) return;
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    if (kind[s] == K_NOP) return;
-    const int32_t r = srow[s];
-    if (mark_rows) mark(D.bmR, r, D.R, &ctl->n_affected);
-    if (mark_cols) mark(D.bmK, r, D.K, D.nK);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = base + threadIdx.x;
+        const bool ch = s < n && kind[s] != K_NOP;
+        const int32_t r = ch ? srow[s] : 0;
+        if (mark_rows) mark_warp(D.bmR, ch, r, D.R, &ctl->n_affected);
+        if (mark_cols) mark_warp(D.bmK, ch, r, D.K, D.nK);
+    }
 }
 
 __global__ void k_detect_cols(MatView AT, DetectBufs D, Ctl *ctl, unsigned mask) {
@@ -275,7 +312,10 @@ __global__ void k_detect_cols(MatView AT, DetectBufs D, Ctl *ctl, unsigned mask)
         const int32_t k = D.K[x];
         const int64_t base = AT.off[k];
         const int L = AT.len[k];
-        for (int p = lane; p < L; p += 32) mark(D.bmR, AT.col[base + p], D.R, &ctl->n_affected);
+        for (int p0 = 0; p0 < L; p0 += 32) {
+            const int p = p0 + lane;
+            mark_warp(D.bmR, p < L, p < L ? AT.col[base + p] : 0, D.R, &ctl->n_affected);
+        }
     }
 }
 
