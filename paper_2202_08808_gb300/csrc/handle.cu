@@ -433,7 +433,7 @@ void static_recompute(dspg_handle *h, cudaStream_t s) {
         CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
         long long nn = n;
         CK(cudaMemcpyAsync(&h->ctl->n_affected, &nn, sizeof(long long), cudaMemcpyHostToDevice, s));
-        run_size_bins(Av, Bv, c_job(h, h->wc.iota.p), n, h->ctl, M_C, s, h->num_sms);
+        run_size_bins(Av, Bv, c_job(h, h->wc.iota.p), n, h->ctl, M_AB, s, h->num_sms);
         read_ctl(h, s);
         if (!(h->hctl->status & ST_C_STAGE)) break;
         grow_c_stage(h, (int64_t)h->hctl->c_stage_top + 1024);
@@ -441,7 +441,10 @@ void static_recompute(dspg_handle *h, cudaStream_t s) {
     run_numeric(h->sr, Av, Bv, c_job(h, h->wc.iota.p), h->ctl, M_C, s, h->num_sms);
     read_ctl(h, s);
     if (h->hctl->status & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, "accumulator probe limit reached");
-    if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "static recompute failed with status " + std::to_string(h->hctl->status));
+    if (h->hctl->status)
+        throw Err(DSPG_ERR_CUDA, "static recompute failed with status " + std::to_string(h->hctl->status) +
+                                     " (staging need " + std::to_string(h->hctl->c_stage_top) + ", capacity " +
+                                     std::to_string(h->wc.st_cap) + ")");
     const int64_t m = h->Bm().ncols;
     make_slack(h, h->C, n, m, h->vsize, h->wc.soff.p, h->wc.slen.p, h->wc.st_col.p, h->wc.st_val.p, s);
 }
@@ -494,12 +497,12 @@ void stage_classify(dspg_handle *h, cudaStream_t s) {
     if (h->inA.n > 0) {
         UpdJob J = h->wA.job(h->inA.n);
         run_segments(J, h->A.nrows, h->ctl, M_AB, s);
-        run_classify(J, h->A.view(), h->vsize, h->ctl, M_AB, ST_AB_STAGE, s, h->num_sms);
+        run_classify(J, h->A.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, s, h->num_sms);
     }
     if (!h->b_is_a && h->inB.n > 0) {
         UpdJob J = h->wB.job(h->inB.n);
         run_segments(J, h->B.nrows, h->ctl, M_AB, s);
-        run_classify(J, h->B.view(), h->vsize, h->ctl, M_AB, ST_AB_STAGE, s, h->num_sms);
+        run_classify(J, h->B.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, s, h->num_sms);
     }
 }
 
@@ -527,11 +530,11 @@ void stage_merge(dspg_handle *h, cudaStream_t s) {
 
 void stage_commit_ab(dspg_handle *h, cudaStream_t s) {
     if (h->inA.n > 0)
-        run_commit(upd_commit_job(h, h->wA, ST_AB_ARENA, ST_AB_STAGE), h->A.view(), h->vsize, h->inA.n, h->ctl, M_AB,
-                   M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
+        run_commit(upd_commit_job(h, h->wA, ST_AB_ARENA, ST_AB_STAGE), h->A.view(), h->vsize, h->inA.n, h->ctl,
+                   M_AB & ~ST_AB_ARENA, M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
     if (!h->b_is_a && h->inB.n > 0)
-        run_commit(upd_commit_job(h, h->wB, ST_AB_ARENA, ST_AB_STAGE), h->B.view(), h->vsize, h->inB.n, h->ctl, M_AB,
-                   M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
+        run_commit(upd_commit_job(h, h->wB, ST_AB_ARENA, ST_AB_STAGE), h->B.view(), h->vsize, h->inB.n, h->ctl,
+                   M_AB & ~ST_AB_ARENA, M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
 }
 
 void stage_transpose(dspg_handle *h, cudaStream_t s) {
@@ -544,14 +547,14 @@ void stage_transpose(dspg_handle *h, cudaStream_t s) {
                  w.sort_out(), w.sort_tmp(), h->ctl, M_AT, s);
     UpdJob J = w.job(n);
     run_segments(J, h->AT.nrows, h->ctl, M_AT, s);
-    run_classify(J, h->AT.view(), 0, h->ctl, M_AT, ST_AT_STAGE, s, h->num_sms);
+    run_classify(J, h->AT.view(), 0, h->ctl, M_AT & ~ST_AT_STAGE, ST_AT_STAGE, s, h->num_sms);
     run_merge_copy(J, h->AT.view(), 0, h->ctl, M_AT, s, h->num_sms);
-    run_commit(upd_commit_job(h, w, ST_AT_ARENA, ST_AT_STAGE), h->AT.view(), 0, n, h->ctl, M_AT, M_AT,
+    run_commit(upd_commit_job(h, w, ST_AT_ARENA, ST_AT_STAGE), h->AT.view(), 0, n, h->ctl, M_AT & ~ST_AT_ARENA, M_AT,
                h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
 }
 
 void stage_size(dspg_handle *h, cudaStream_t s) {
-    run_size_bins(h->A.view(), h->Bm().view(), c_job(h, h->wc.R.p), h->A.nrows, h->ctl, M_C, s, h->num_sms);
+    run_size_bins(h->A.view(), h->Bm().view(), c_job(h, h->wc.R.p), h->A.nrows, h->ctl, M_AB, s, h->num_sms);
 }
 
 void stage_numeric(dspg_handle *h, cudaStream_t s) {
@@ -559,7 +562,7 @@ void stage_numeric(dspg_handle *h, cudaStream_t s) {
 }
 
 void stage_splice(dspg_handle *h, cudaStream_t s) {
-    run_commit(c_commit_job(h, h->wc.R.p), h->C.view(), h->vsize, h->A.nrows, h->ctl, M_C, M_C, h->opt.slack_min,
+    run_commit(c_commit_job(h, h->wc.R.p), h->C.view(), h->vsize, h->A.nrows, h->ctl, M_C & ~ST_C_ARENA, M_C, h->opt.slack_min,
                h->opt.slack_div, s, h->num_sms);
 }
 
