@@ -118,9 +118,8 @@ enum {
     DSPG_STAGE_COMMIT = 4,    /* write them into the slack-CSR (Section 4.1 merge/mask) */
     DSPG_STAGE_TRANSPOSE = 5, /* keep A's transposed pattern in step */
     DSPG_STAGE_SIZE = 6,      /* product bounds and bins of the rows of R */
-    DSPG_STAGE_NUMERIC = 7,   /* Gustavson recompute of the rows of R (Section 6.1) */
-    DSPG_STAGE_SPLICE = 8,    /* write the new rows into C */
-    DSPG_NSTAGES = 9
+    DSPG_STAGE_NUMERIC = 7,   /* Gustavson recompute of the rows of R (Section 6.1), written into C */
+    DSPG_NSTAGES = 8
 };
 
 typedef struct dspg_handle dspg_handle;

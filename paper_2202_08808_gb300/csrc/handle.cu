@@ -106,7 +106,7 @@ struct UpdWs {
     DBuf<int32_t> row, col;
     DBuf<char> val;
     DBuf<uint8_t> op, kind;
-    DBuf<int32_t> pos, insx, delx, seg_lo, seg_hi, m_row, m_seg, m_len, m_nins, m_ndel, m_cap;
+    DBuf<int32_t> pos, insx, delx, m_lo, m_hi, m_row, m_len, m_nins, m_ndel, m_cap;
     DBuf<int64_t> m_soff, m_dest;
     DBuf<int32_t> ch_item, ch_part, cc_item, cc_part;
     DBuf<int32_t> st_col;
@@ -121,8 +121,8 @@ struct UpdWs {
             int64_t c = std::max<int64_t>(n, std::max<int64_t>(2 * ncap, 1024));
             in_row.reserve(c); in_col.reserve(c); in_val.reserve(c * std::max(vsize, 1)); in_op.reserve(c);
             row.reserve(c); col.reserve(c); val.reserve(c * std::max(vsize, 1)); op.reserve(c); kind.reserve(c);
-            pos.reserve(c); insx.reserve(c); delx.reserve(c); seg_lo.reserve(c); seg_hi.reserve(c);
-            m_row.reserve(c); m_seg.reserve(c); m_len.reserve(c); m_nins.reserve(c); m_ndel.reserve(c);
+            pos.reserve(c); insx.reserve(c); delx.reserve(c); m_lo.reserve(c); m_hi.reserve(c);
+            m_row.reserve(c); m_len.reserve(c); m_nins.reserve(c); m_ndel.reserve(c);
             m_cap.reserve(c); m_soff.reserve(c); m_dest.reserve(c);
             k0.reserve(c); k1.reserve(c); i0.reserve(c); i1.reserve(c);
             int64_t cnt;
@@ -155,8 +155,7 @@ struct UpdWs {
         J.n = n;
         J.row = row.p; J.col = col.p; J.val = vsize ? (void *)val.p : nullptr; J.op = op.p;
         J.kind = kind.p; J.pos = pos.p; J.insx = insx.p; J.delx = delx.p;
-        J.seg_lo = seg_lo.p; J.seg_hi = seg_hi.p;
-        J.m_row = m_row.p; J.m_seg = m_seg.p; J.m_len = m_len.p; J.m_nins = m_nins.p; J.m_ndel = m_ndel.p;
+        J.m_row = m_row.p; J.m_lo = m_lo.p; J.m_hi = m_hi.p; J.m_len = m_len.p; J.m_nins = m_nins.p; J.m_ndel = m_ndel.p;
         J.m_soff = m_soff.p; J.m_dest = m_dest.p; J.m_cap = m_cap.p;
         J.ch_item = ch_item.p; J.ch_part = ch_part.p; J.ch_cap = ch_item.n;
         J.cc_item = cc_item.p; J.cc_part = cc_part.p; J.cc_cap = cc_item.n;
@@ -168,11 +167,7 @@ struct UpdWs {
 // Work buffers of the recompute of C rows.
 struct CWs {
     int64_t nrows = 0;
-    DBuf<int32_t> R, iota, slen, bins, ncap, cc_item, cc_part;
-    DBuf<int64_t> soff, dest;
-    DBuf<int32_t> st_col;
-    DBuf<char> st_val;
-    int64_t st_cap = 0;
+    DBuf<int32_t> R, iota, bins;
     DBuf<char> gd_acc;
     DBuf<uint32_t> gd_mask;
     int64_t gd_w = 0;
@@ -325,11 +320,7 @@ void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
     w.R.reserve(nn);
     w.iota.reserve(nn);
     fill_iota(w.iota.p, n, s);
-    w.slen.reserve(nn);
-    w.soff.reserve(nn);
     w.bins.reserve((int64_t)NBINS * nn);
-    w.dest.reserve(nn);
-    w.ncap.reserve(nn);
     w.bmR.reserve(nn / 32 + 2);
     CK(cudaMemsetAsync(w.bmR.p, 0, sizeof(uint32_t) * w.bmR.n, s));
     const int64_t nb = std::max<int64_t>(h->Bm().nrows, 1);
@@ -349,56 +340,21 @@ void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
     }
 }
 
-void grow_c_stage(dspg_handle *h, int64_t need) {
-    CWs &w = h->wc;
-    if (need <= w.st_cap) return;
-    int64_t c = std::max<int64_t>(need, w.st_cap + w.st_cap / 2);
-    w.st_col.reserve(c);
-    w.st_val.reserve(c * h->vsize);
-    w.st_cap = c;
-    w.cc_item.reserve(2 * w.nrows + c / 256 + 64);
-    w.cc_part.reserve(2 * w.nrows + c / 256 + 64);
-}
-
-CJob c_job(dspg_handle *h, const int32_t *R) {
+CJob c_job(dspg_handle *h, const int32_t *R, bool static_mode) {
     CWs &w = h->wc;
     CJob J{};
     J.R = R;
-    J.nR_max = w.nrows;
-    J.slen = w.slen.p;
-    J.soff = w.soff.p;
     J.bins = w.bins.p;
     J.bin_cap = std::max<int64_t>(w.nrows, 1);
-    J.st_col = w.st_col.p;
-    J.st_val = w.st_val.p;
-    J.st_cap = w.st_cap;
     J.gd_acc = w.gd_acc.p;
     J.gd_mask = w.gd_mask.p;
     J.gd_w = w.gd_w;
     J.gd_ctas = std::max(w.gd_ctas, 1);
     J.m = h->Bm().ncols;
     J.dense_mode = J.m <= DENSE_M_MAX ? 1 : 0;
-    return J;
-}
-
-CommitJob c_commit_job(dspg_handle *h, const int32_t *R) {
-    CWs &w = h->wc;
-    CommitJob J{};
-    J.rows = R;
-    J.lens = w.slen.p;
-    J.soff = w.soff.p;
-    J.count = &h->ctl->n_affected;
-    J.st_col = w.st_col.p;
-    J.st_val = w.st_val.p;
-    J.dest = w.dest.p;
-    J.ncap = w.ncap.p;
-    J.cc_item = w.cc_item.p;
-    J.cc_part = w.cc_part.p;
-    J.cc_count = &h->ctl->c_chunk;
-    J.cc_cap = w.cc_item.n;
-    J.reloc = &h->ctl->c_reloc;
-    J.arena_bit = ST_C_ARENA;
-    J.stage_bit = ST_C_STAGE;
+    J.static_mode = static_mode ? 1 : 0;
+    J.slack_min = h->opt.slack_min;
+    J.slack_div = h->opt.slack_div;
     return J;
 }
 
@@ -422,31 +378,44 @@ CommitJob upd_commit_job(dspg_handle *h, UpdWs &w, unsigned arena_bit, unsigned 
     return J;
 }
 
-// Full recompute of C from A, B (the static product).  Replaces C, reusing
-// its arena when it is large enough.
+// Full recompute of C from A, B (the static product).  The sizing pass lays
+// C out afresh (room for each row's product bound), reusing the arena when
+// it is large enough; the numeric kernels then write every row in place.
 void static_recompute(dspg_handle *h, cudaStream_t s) {
     ensure_c_ws(h, s);
+    DevMat &C = h->C;
     const int64_t n = h->A.nrows;
+    C.nrows = n;
+    C.ncols = h->Bm().ncols;
+    C.vsize = h->vsize;
+    C.len.reserve(std::max<int64_t>(n, 1));
+    C.cap.reserve(std::max<int64_t>(n, 1));
+    C.off.reserve(n + 1);
+    C.top.reserve(1);
     MatView Av = h->A.view(), Bv = h->Bm().view();
-    grow_c_stage(h, 1024);
     for (int attempt = 0; attempt < 3; attempt++) {
         CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+        CK(cudaMemsetAsync(C.top.p, 0, sizeof(long long), s));
         long long nn = n;
         CK(cudaMemcpyAsync(&h->ctl->n_affected, &nn, sizeof(long long), cudaMemcpyHostToDevice, s));
-        run_size_bins(Av, Bv, c_job(h, h->wc.iota.p), n, h->ctl, M_AB, s, h->num_sms);
+        run_size_bins(Av, Bv, C.view(), c_job(h, h->wc.iota.p, true), n, h->ctl, M_AB, s, h->num_sms);
         read_ctl(h, s);
-        if (!(h->hctl->status & ST_C_STAGE)) break;
-        grow_c_stage(h, (int64_t)h->hctl->c_stage_top + 1024);
+        if (!(h->hctl->status & ST_C_ARENA)) break;
+        long long need = 0;
+        CK(cudaMemcpyAsync(&need, C.top.p, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const int64_t cap = std::max<int64_t>((int64_t)(need * h->opt.arena_headroom), need + 4096);
+        C.col.release();
+        C.val.release();
+        C.col.reserve(cap);
+        C.val.reserve(cap * h->vsize);
+        C.arena_cap = cap;
     }
-    run_numeric(h->sr, Av, Bv, c_job(h, h->wc.iota.p), h->ctl, M_C, s, h->num_sms);
+    if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "static sizing failed with status " + std::to_string(h->hctl->status));
+    run_numeric(h->sr, Av, Bv, C.view(), c_job(h, h->wc.iota.p, true), h->ctl, M_C, s, h->num_sms);
     read_ctl(h, s);
     if (h->hctl->status & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, "accumulator probe limit reached");
-    if (h->hctl->status)
-        throw Err(DSPG_ERR_CUDA, "static recompute failed with status " + std::to_string(h->hctl->status) +
-                                     " (staging need " + std::to_string(h->hctl->c_stage_top) + ", capacity " +
-                                     std::to_string(h->wc.st_cap) + ")");
-    const int64_t m = h->Bm().ncols;
-    make_slack(h, h->C, n, m, h->vsize, h->wc.soff.p, h->wc.slen.p, h->wc.st_col.p, h->wc.st_val.p, s);
+    if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "static recompute failed with status " + std::to_string(h->hctl->status));
 }
 
 // Transposed pattern of A (rows of A^T = columns of A), built from A's rows.
@@ -496,12 +465,10 @@ void stage_sort(dspg_handle *h, cudaStream_t s) {
 void stage_classify(dspg_handle *h, cudaStream_t s) {
     if (h->inA.n > 0) {
         UpdJob J = h->wA.job(h->inA.n);
-        run_segments(J, h->A.nrows, h->ctl, M_AB, s);
         run_classify(J, h->A.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, s, h->num_sms);
     }
     if (!h->b_is_a && h->inB.n > 0) {
         UpdJob J = h->wB.job(h->inB.n);
-        run_segments(J, h->B.nrows, h->ctl, M_AB, s);
         run_classify(J, h->B.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, s, h->num_sms);
     }
 }
@@ -546,7 +513,6 @@ void stage_transpose(dspg_handle *h, cudaStream_t s) {
     sort_updates(w.in_row.p, w.in_col.p, nullptr, w.in_op.p, n, h->AT.nrows + 1, h->AT.ncols, h->sr, false,
                  w.sort_out(), w.sort_tmp(), h->ctl, M_AT, s);
     UpdJob J = w.job(n);
-    run_segments(J, h->AT.nrows, h->ctl, M_AT, s);
     run_classify(J, h->AT.view(), 0, h->ctl, M_AT & ~ST_AT_STAGE, ST_AT_STAGE, s, h->num_sms);
     run_merge_copy(J, h->AT.view(), 0, h->ctl, M_AT, s, h->num_sms);
     run_commit(upd_commit_job(h, w, ST_AT_ARENA, ST_AT_STAGE), h->AT.view(), 0, n, h->ctl, M_AT & ~ST_AT_ARENA, M_AT,
@@ -554,21 +520,18 @@ void stage_transpose(dspg_handle *h, cudaStream_t s) {
 }
 
 void stage_size(dspg_handle *h, cudaStream_t s) {
-    run_size_bins(h->A.view(), h->Bm().view(), c_job(h, h->wc.R.p), h->A.nrows, h->ctl, M_AB, s, h->num_sms);
+    run_size_bins(h->A.view(), h->Bm().view(), h->C.view(), c_job(h, h->wc.R.p, false), h->A.nrows, h->ctl, M_AB, s,
+                  h->num_sms);
 }
 
 void stage_numeric(dspg_handle *h, cudaStream_t s) {
-    run_numeric(h->sr, h->A.view(), h->Bm().view(), c_job(h, h->wc.R.p), h->ctl, M_C, s, h->num_sms);
-}
-
-void stage_splice(dspg_handle *h, cudaStream_t s) {
-    run_commit(c_commit_job(h, h->wc.R.p), h->C.view(), h->vsize, h->A.nrows, h->ctl, M_C & ~ST_C_ARENA, M_C, h->opt.slack_min,
-               h->opt.slack_div, s, h->num_sms);
+    run_numeric(h->sr, h->A.view(), h->Bm().view(), h->C.view(), c_job(h, h->wc.R.p, false), h->ctl, M_C, s,
+                h->num_sms);
 }
 
 typedef void (*StageFn)(dspg_handle *, cudaStream_t);
-const StageFn kStages[DSPG_NSTAGES] = {stage_sort,      stage_classify,  stage_detect,  stage_merge,  stage_commit_ab,
-                                       stage_transpose, stage_size,      stage_numeric, stage_splice};
+const StageFn kStages[DSPG_NSTAGES] = {stage_sort,      stage_classify, stage_detect,  stage_merge,
+                                       stage_commit_ab, stage_transpose, stage_size, stage_numeric};
 
 // Enqueue stages [from, to); with profiling on, an event brackets each.
 void run_stages(dspg_handle *h, int from, int to, cudaStream_t s, bool timed) {
@@ -779,7 +742,6 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
         h->wA.ensure(nA, h->A.arena_cap);
         if (!h->b_is_a) h->wB.ensure(nB, h->B.arena_cap);
         if (h->has_at) h->wAT.ensure(nA, h->AT.arena_cap);
-        grow_c_stage(h, 65536);
         upload(h, h->wA, dA, h->inA, s);
         upload(h, h->wB, dB, h->inB, s);
         if (h->b_is_a) h->inB = BatchIn{};
@@ -819,10 +781,9 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
                 continue;
             }
             const bool at = st & (ST_AT_STAGE | ST_AT_ARENA);
-            const bool cc = st & (ST_C_STAGE | ST_C_ARENA | ST_C_SCRATCH);
+            const bool cc = st & ST_C_ARENA;
             if (st & ST_AT_STAGE) h->wAT.grow_stage(h->hctl->u[2].stage_top + 1024);
             if (st & ST_AT_ARENA) regrow(h, h->AT, s);
-            if (st & ST_C_STAGE) grow_c_stage(h, h->hctl->c_stage_top + 1024);
             if (st & ST_C_ARENA) regrow(h, h->C, s);
             reset_range(h, &h->ctl->status, sizeof(unsigned), s);
             if (at) {

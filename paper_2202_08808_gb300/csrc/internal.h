@@ -19,10 +19,9 @@ struct UpdJob {
     // classification
     uint8_t *kind;
     int32_t *pos, *insx, *delx;
-    // row segments [seg_lo, seg_hi) of the sorted batch
-    int32_t *seg_lo, *seg_hi;
-    // merge items: rows with an effective change
-    int32_t *m_row, *m_seg, *m_len, *m_nins, *m_ndel;
+    // merge items: rows with an effective change; their updates are the
+    // sorted entries [m_lo, m_hi)
+    int32_t *m_row, *m_lo, *m_hi, *m_len, *m_nins, *m_ndel;
     int64_t *m_soff;
     // commit plan per item
     int64_t *m_dest;
@@ -66,24 +65,19 @@ struct DetectBufs {
 // The recompute of rows of C (static build: all rows).
 struct CJob {
     const int32_t *R;         // rows to recompute
-    int64_t nR_max;           // capacity of the per-row arrays
-    int32_t *slen;            // output length per R index
-    int64_t *soff;            // staging offset per R index
     int32_t *bins;            // NBINS lists of R indices, bin_cap each
     int64_t bin_cap;
-    int32_t *st_col;
-    void *st_val;
-    int64_t st_cap;
     void *gd_acc;             // per-CTA dense accumulators (global), gd_w entries each
     uint32_t *gd_mask;        // per-CTA presence bits, gd_w / 32 words each
     int64_t gd_w;
     int gd_ctas;
     int64_t m;                // columns of C
     int dense_mode;           // 1: all rows use the dense small-m kernels
+    int static_mode;          // 1: C is laid out afresh by the sizing pass
+    int slack_min, slack_div;
 };
 
 // update.cu
-void run_segments(const UpdJob &J, int64_t nrows, Ctl *ctl, unsigned mask, cudaStream_t s);
 void run_classify(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsigned mask, unsigned stage_bit,
                   cudaStream_t s, int num_sms);
 void run_merge_copy(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsigned mask, cudaStream_t s,
@@ -99,10 +93,10 @@ void run_transpose_feed(const UpdJob &J, int32_t pad_row, int32_t *trow, int32_t
 
 // spgemm.cu
 constexpr int64_t DENSE_M_MAX = 1024;  // C columns up to this use dense accumulators
-void run_size_bins(const MatView &A, const MatView &B, const CJob &J, int64_t max_rows, Ctl *ctl, unsigned mask,
-                   cudaStream_t s, int num_sms);
-void run_numeric(int sr, const MatView &A, const MatView &B, const CJob &J, Ctl *ctl, unsigned mask, cudaStream_t s,
-                 int num_sms);
+void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const CJob &J, int64_t max_rows, Ctl *ctl,
+                   unsigned mask, cudaStream_t s, int num_sms);
+void run_numeric(int sr, const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,
+                 cudaStream_t s, int num_sms);
 void init_dense_scratch(int sr, void *acc, uint32_t *mask, int64_t entries, int64_t words, cudaStream_t s);
 
 // layout.cu: building and reading slack-CSRs

@@ -3,27 +3,29 @@
 // Section 6.1: the local product is Gustavson's row-wise algorithm; each row
 // C(i,:) = (+)_k A(i,k) (x) B(k,:) is formed in a sparse accumulator.  An
 // output column is a non-zero iff some product reaches it (structural
-// semantics, Section 3).  Here every affected row is first sized by the
-// product bound ub_i = sum_k len(B_k) (capped at the column count), binned
-// by that bound, and recomputed by the kernel of its bin:
+// semantics, Section 3).  Every row of R is first sized by its product bound
+// ub_i = sum_k len(B_k) (capped at the column count), binned by that bound,
+// and recomputed by the kernel of its bin:
 //
-//   bins 0-4   warp per row, open-addressing hash in shared memory
-//              (64 .. 1024 slots, load <= 1/2);
-//   bins 5-7   CTA per row, hash of 2048 .. 8192 slots in shared memory;
-//   bin  8     CTA per row, dense accumulator over all columns in global
+//   bins 0-1   8 / 16 lanes per row, open-addressing hash in shared memory
+//              (64 / 128 slots, load <= 1/2), several rows per warp in flight;
+//   bins 2-4   a warp per row, hash of 256 .. 1024 slots;
+//   bins 5-7   a CTA per row, hash of 2048 .. 8192 slots;
+//   bin  8     a CTA per row, dense accumulator over all columns in global
 //              memory (L2) with a presence bitmap, for the longest rows;
 //   bins 9-10  when C has at most 1024 columns: dense accumulators in shared
 //              memory (warp per row, or CTA per row for long rows).
 //
 // Products of a row are flattened over its A entries: a scan of the B-row
-// lengths of up to 32 (warp) or blockDim (CTA) A entries assigns product p
-// to A entry s by a binary search in the scan, so all lanes stay busy even
-// when B rows are short.  Each row's output is compacted, sorted by column
-// (hash bins) or read out in column order (dense bins), and written to a
-// staging buffer at an offset taken from a device counter; the splice then
-// moves it into C.  (+,.) accumulates with double atomics (the summation
-// order varies; the library's tolerance covers any order), (min,+) with
-// atomicMin (order-free, bit-exact).
+// lengths of the A entries held by the lanes assigns product p to A entry s
+// by a binary search in the scan, so lanes stay busy even when B rows are
+// short.  Each row's output is sorted by column (hash bins) or read out in
+// column order (dense bins) and written straight into C: in place when it
+// fits the row's capacity, otherwise at the arena tail.  For the static
+// product the sizing pass lays C out afresh with room for the bound.
+// (+,.) accumulates with double atomics (the summation order varies; the
+// library's tolerance covers any order), (min,+) with atomicMin
+// (order-free, bit-exact).
 #include "internal.h"
 
 namespace dspg {
@@ -46,7 +48,7 @@ struct Sr<SR_MP> {
 };
 
 enum {
-    BIN_W64 = 0, BIN_W128, BIN_W256, BIN_W512, BIN_W1024,
+    BIN_G8 = 0, BIN_G16, BIN_W256, BIN_W512, BIN_W1024,
     BIN_C2048, BIN_C4096, BIN_C8192,
     BIN_GD,
     BIN_WDENSE, BIN_CDENSE,
@@ -62,8 +64,8 @@ __device__ __forceinline__ long long atomic_add_ll2(long long *p, long long v) {
 
 __device__ __forceinline__ int pick_bin(long long ubc, int dense_mode) {
     if (dense_mode) return ubc <= 4096 ? BIN_WDENSE : BIN_CDENSE;
-    if (ubc <= 32) return BIN_W64;
-    if (ubc <= 64) return BIN_W128;
+    if (ubc <= 32) return BIN_G8;
+    if (ubc <= 64) return BIN_G16;
     if (ubc <= 128) return BIN_W256;
     if (ubc <= 256) return BIN_W512;
     if (ubc <= 512) return BIN_W1024;
@@ -73,69 +75,105 @@ __device__ __forceinline__ int pick_bin(long long ubc, int dense_mode) {
     return BIN_GD;
 }
 
-// A warp sizes 32 rows of R at a time (all lanes on one row, lane r keeping
-// row r's bound ub), then hands out staging room (ub entries per row, so the
-// numeric kernels need no allocation) and bin slots with one atomic per warp
-// and counter.
-__global__ void k_size_bins(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask) {
+constexpr int SIZE_SHORT = 64;  // A rows up to this length are sized by one thread
+
+// One thread per row of R sums the B-row lengths of its A entries (rows
+// longer than SIZE_SHORT are summed by the whole warp afterwards); then the
+// warp hands out bin slots (and, for the static product, the row's place in
+// a fresh C) with one atomic per counter.
+__global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask) {
     if (failed(ctl, mask)) return;
     const long long nR = ctl->n_affected;
     const int lane = threadIdx.x & 31;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     long long prod_acc = 0, a_acc = 0;
-    for (long long t0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; t0 < nR; t0 += nwarps * 32) {
-        const long long my_t = t0 + lane;
-        const bool valid = my_t < nR;
-        const int32_t my_i = valid ? J.R[my_t] : 0;
-        const int64_t my_aoff = valid ? A.off[my_i] : 0;
-        const int my_alen = valid ? A.len[my_i] : 0;
-        long long my_s = 0;
-        const int cnt = (int)(nR - t0 < 32 ? nR - t0 : 32);
-        for (int rr = 0; rr < cnt; rr++) {
-            const int64_t aoff = __shfl_sync(0xffffffffu, my_aoff, rr);
-            const int alen = __shfl_sync(0xffffffffu, my_alen, rr);
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < nR; base += (long long)gridDim.x * blockDim.x) {
+        const long long t = base + threadIdx.x;
+        const bool valid = t < nR;
+        const int32_t i = valid ? J.R[t] : 0;
+        const int64_t aoff = valid ? A.off[i] : 0;
+        const int alen = valid ? A.len[i] : 0;
+        const bool lng = alen > SIZE_SHORT;
+        long long ub = 0;
+        if (valid && !lng)
+            for (int a = 0; a < alen; a++) ub += B.len[A.col[aoff + a]];
+        unsigned lm = __ballot_sync(0xffffffffu, valid && lng);
+        while (lm) {
+            const int src = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const int64_t o = __shfl_sync(0xffffffffu, aoff, src);
+            const int l = __shfl_sync(0xffffffffu, alen, src);
             long long s = 0;
-            for (int a = lane; a < alen; a += 32) s += B.len[A.col[aoff + a]];
+            for (int a = lane; a < l; a += 32) s += B.len[A.col[o + a]];
             s = warp_sum<long long>(s);
-            if (lane == rr) my_s = s;
+            if (lane == src) ub = s;
         }
-        const long long ubc = my_s < J.m ? my_s : J.m;
-        const long long so = warp_fetch_add(&ctl->c_stage_top, ubc);
-        if (valid) {
-            J.soff[my_t] = so;
-            J.slen[my_t] = 0;
-            if (so + ubc > J.st_cap) set_status(ctl, ST_C_STAGE);
+        const long long ubc = ub < J.m ? ub : J.m;
+        if (J.static_mode) {
+            const int32_t c = valid ? slack_cap(ubc, J.slack_min, J.slack_div) : 0;
+            const long long d = warp_fetch_add(C.top, c);
+            if (valid) {
+                C.off[i] = d;
+                C.cap[i] = c;
+                C.len[i] = 0;
+                if (d + c > C.arena_cap) set_status(ctl, ST_C_ARENA);
+            }
+        } else if (valid && ub == 0) {
+            C.len[i] = 0;  // no products: the row becomes empty
         }
-        const int b = (valid && my_s > 0) ? pick_bin(ubc, J.dense_mode) : -1;
+        const int b = (valid && ub > 0) ? pick_bin(ubc, J.dense_mode) : -1;
         const unsigned peers = __match_any_sync(0xffffffffu, b);
         const int leader = __ffs(peers) - 1;
         long long bb = 0;
         if (b >= 0 && lane == leader) bb = atomic_add_ll2(&ctl->bin_count[b], __popc(peers));
         bb = __shfl_sync(0xffffffffu, bb, leader);
-        if (b >= 0) J.bins[(int64_t)b * J.bin_cap + bb + __popc(peers & lanemask_lt())] = (int32_t)my_t;
-        prod_acc += warp_sum<long long>(valid ? my_s : 0);
-        a_acc += warp_sum<long long>(my_alen);
+        if (b >= 0) J.bins[(int64_t)b * J.bin_cap + bb + __popc(peers & lanemask_lt())] = (int32_t)t;
+        prod_acc += ub;
+        a_acc += alen;
     }
+    prod_acc = warp_sum<long long>(prod_acc);
+    a_acc = warp_sum<long long>(a_acc);
     if (lane == 0) {
         if (prod_acc) atomic_add_ll2(&ctl->products, prod_acc);
         if (a_acc) atomic_add_ll2(&ctl->a_entries, a_acc);
     }
 }
 
+// ------------------------------------------------------------ output
+
+// Where row i of C goes when it has n entries: its own place when n fits
+// its capacity (always in the static layout), else a fresh place at the
+// arena tail.  Returns -1 when the tail is exhausted: the status bit makes
+// the host rebuild C with more room and recompute R again.
+__device__ __forceinline__ int64_t c_row_dest(const MatView &C, const CJob &J, Ctl *ctl, int32_t i, int n) {
+    const int32_t cap = C.cap[i];
+    if (J.static_mode || n <= cap) return C.off[i];
+    const int32_t c = slack_cap(n, J.slack_min, J.slack_div);
+    const long long d = atomic_add_ll2(C.top, c);
+    if (d + c > C.arena_cap) {
+        set_status(ctl, ST_C_ARENA);
+        return -1;
+    }
+    C.off[i] = d;
+    C.cap[i] = c;
+    atomic_add_ll2(&ctl->c_reloc, 1);
+    return d;
+}
+
 // --------------------------------------------------- product generators
 
-// Calls emit(j, a (x) b) for every product of row i, lanes of one warp
-// sharing the work.
-template <int SR, class F>
-__device__ __forceinline__ void warp_products(const MatView &A, const MatView &B, int32_t i, F emit) {
+// Calls emit(j, a (x) b) for every product of row i; the G lanes of one
+// group (G = 8, 16 or 32 consecutive lanes, mask gmask) share the work.
+template <int SR, int G, class F>
+__device__ __forceinline__ void group_products(const MatView &A, const MatView &B, int32_t i, unsigned gmask,
+                                               F emit) {
     using T = typename Sr<SR>::T;
-    const int lane = threadIdx.x & 31;
+    const int gl = threadIdx.x & (G - 1);
     const int64_t aoff = A.off[i];
     const int alen = A.len[i];
     const T *Av = (const T *)A.val;
     const T *Bv = (const T *)B.val;
-    for (int a0 = 0; a0 < alen; a0 += 32) {
-        const int ai = a0 + lane;
+    for (int a0 = 0; a0 < alen; a0 += G) {
+        const int ai = a0 + gl;
         int blen = 0;
         int64_t boff = 0;
         T av = T(0);
@@ -145,19 +183,24 @@ __device__ __forceinline__ void warp_products(const MatView &A, const MatView &B
             boff = B.off[k];
             blen = B.len[k];
         }
-        const int incl = warp_incl_scan<int>(blen);
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        for (int base = 0; base < total; base += 32) {
-            const int p = base + lane;
+        int incl = blen;
+#pragma unroll
+        for (int d = 1; d < G; d <<= 1) {
+            const int o = __shfl_up_sync(gmask, incl, d, G);
+            if (gl >= d) incl += o;
+        }
+        const int total = __shfl_sync(gmask, incl, G - 1, G);
+        for (int base = 0; base < total; base += G) {
+            const int p = base + gl;
             int s = 0;
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int v = __shfl_sync(0xffffffffu, incl, s + step - 1);
+            for (int step = G / 2; step > 0; step >>= 1) {
+                const int v = __shfl_sync(gmask, incl, s + step - 1, G);
                 if (v <= p) s += step;
             }
-            const int64_t bo = __shfl_sync(0xffffffffu, boff, s);
-            const T a = __shfl_sync(0xffffffffu, av, s);
-            const int excl = __shfl_sync(0xffffffffu, incl, s) - __shfl_sync(0xffffffffu, blen, s);
+            const int64_t bo = __shfl_sync(gmask, boff, s, G);
+            const T a = __shfl_sync(gmask, av, s, G);
+            const int excl = __shfl_sync(gmask, incl, s, G) - __shfl_sync(gmask, blen, s, G);
             if (p < total) {
                 const int64_t q = bo + (p - excl);
                 emit(B.col[q], Sr<SR>::mul(a, Bv[q]));
@@ -264,44 +307,50 @@ __device__ __forceinline__ void bitonic_step(int32_t *k, T *v, int i, int l, boo
     }
 }
 
-// ------------------------------------------------------ warp hash kernel
+// ---------------------------------------------------- group hash kernel
 
-template <int SR, int LOG_TS, int NW>
+// G lanes per row (32 / G rows per warp), TS hash slots per row.
+template <int SR, int LOG_TS, int G, int NW>
 __global__ void __launch_bounds__(NW * 32)
-k_num_warp_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
+k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
     constexpr int HC = TS / 2;  // compacted list capacity
+    constexpr int GPW = 32 / G;
+    constexpr int NG = NW * GPW;  // groups per block
     extern __shared__ __align__(16) unsigned char smem[];
     if (failed(ctl, mask)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    T *vals = (T *)smem + (size_t)w * TS;
-    T *cv = (T *)smem + (size_t)NW * TS + (size_t)w * HC;
-    int32_t *keys = (int32_t *)((T *)smem + (size_t)NW * (TS + HC)) + (size_t)w * TS;
-    int32_t *ck = (int32_t *)((T *)smem + (size_t)NW * (TS + HC)) + (size_t)NW * TS + (size_t)w * HC;
-    T *sv = (T *)J.st_val;
+    const int gl = lane & (G - 1), gw = lane / G;
+    const int g = w * GPW + gw;  // group in block
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (gw * G));
+    T *vals = (T *)smem + (size_t)g * TS;
+    T *cv = (T *)smem + (size_t)NG * TS + (size_t)g * HC;
+    int32_t *keys = (int32_t *)((T *)smem + (size_t)NG * (TS + HC)) + (size_t)g * TS;
+    int32_t *ck = (int32_t *)((T *)smem + (size_t)NG * (TS + HC)) + (size_t)NG * TS + (size_t)g * HC;
+    T *Cv = (T *)C.val;
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
-    for (long long it = (long long)blockIdx.x * NW + w; it < cnt; it += (long long)gridDim.x * NW) {
+    for (long long it = (long long)blockIdx.x * NG + g; it < cnt; it += (long long)gridDim.x * NG) {
         const int t = J.bins[(int64_t)bin * J.bin_cap + it];
         const int32_t i = J.R[t];
-        for (int s = lane; s < TS; s += 32) {
+        for (int s = gl; s < TS; s += G) {
             keys[s] = -1;
             vals[s] = Sr<SR>::zero();
         }
-        __syncwarp();
+        __syncwarp(gmask);
         bool ok = true;
-        warp_products<SR>(A, B, i, [&](int32_t j, T v) { ok &= hash_acc<LOG_TS, T, SR>(keys, vals, j, v); });
-        if (!__all_sync(0xffffffffu, ok) && lane == 0) set_status(ctl, ST_TIMEOUT);
-        __syncwarp();
+        group_products<SR, G>(A, B, i, gmask, [&](int32_t j, T v) { ok &= hash_acc<LOG_TS, T, SR>(keys, vals, j, v); });
+        if (!ok) set_status(ctl, ST_TIMEOUT);
+        __syncwarp(gmask);
         int n = 0;
-        for (int s0 = 0; s0 < TS; s0 += 32) {
-            const int s = s0 + lane;
+        for (int s0 = 0; s0 < TS; s0 += G) {
+            const int s = s0 + gl;
             const int32_t k = keys[s];
             const bool occ = k >= 0;
-            const unsigned bal = __ballot_sync(0xffffffffu, occ);
+            const unsigned bal = (__ballot_sync(gmask, occ) & gmask) >> (gw * G);
             if (occ) {
-                const int x = n + __popc(bal & lanemask_lt());
+                const int x = n + __popc(bal & ((1u << gl) - 1u));
                 if (x < HC) {
                     ck[x] = k;
                     cv[x] = vals[s];
@@ -310,51 +359,53 @@ k_num_warp_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) 
             n += __popc(bal);
         }
         if (n > HC) n = HC;  // unreachable when ub <= HC
-        __syncwarp();
-        const long long so = J.soff[t];  // room for the row's product bound, from the sizing pass
-        if (lane == 0) J.slen[t] = n;
-        nnz_acc += n;
-        const bool fits = true;
-        if (n <= 32) {
-            // rank of each entry among distinct column keys
-            const int32_t myk = lane < n ? ck[lane] : 0x7fffffff;
-            const T myv = lane < n ? cv[lane] : Sr<SR>::zero();
-            int rank = 0;
-            for (int s = 0; s < n; s++) rank += __shfl_sync(0xffffffffu, myk, s) < myk;
-            if (lane < n && fits) {
-                J.st_col[so + rank] = myk;
-                sv[so + rank] = myv;
+        __syncwarp(gmask);
+        int64_t dest = 0;
+        if (gl == 0) dest = c_row_dest(C, J, ctl, i, n);
+        dest = __shfl_sync(gmask, dest, 0, G);
+        if (n <= 64) {
+            // rank of each entry among the row's distinct columns
+            for (int e = gl; e < n; e += G) {
+                const int32_t key = ck[e];
+                int rank = 0;
+                for (int x = 0; x < n; x++) rank += ck[x] < key;
+                if (dest >= 0) {
+                    C.col[dest + rank] = key;
+                    Cv[dest + rank] = cv[e];
+                }
             }
         } else {
-            int N = 64;
+            int N = 128;
             while (N < n) N <<= 1;
-            for (int s = n + lane; s < N; s += 32) ck[s] = 0x7fffffff;
-            __syncwarp();
+            for (int s = n + gl; s < N; s += G) ck[s] = 0x7fffffff;
+            __syncwarp(gmask);
             for (int size = 2; size <= N; size <<= 1) {
                 for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    for (int x = lane; x < N / 2; x += 32) {
+                    for (int x = gl; x < N / 2; x += G) {
                         const int a = 2 * x - (x & (stride - 1));
                         bitonic_step<T>(ck, cv, a, a + stride, (a & size) == 0);
                     }
-                    __syncwarp();
+                    __syncwarp(gmask);
                 }
             }
-            if (fits)
-                for (int s = lane; s < n; s += 32) {
-                    J.st_col[so + s] = ck[s];
-                    sv[so + s] = cv[s];
+            if (dest >= 0)
+                for (int s = gl; s < n; s += G) {
+                    C.col[dest + s] = ck[s];
+                    Cv[dest + s] = cv[s];
                 }
         }
-        __syncwarp();
+        if (gl == 0 && dest >= 0) C.len[i] = n;
+        nnz_acc += n;
+        __syncwarp(gmask);
     }
-    if (lane == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
+    if (gl == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
 }
 
 // ------------------------------------------------------- CTA hash kernel
 
 template <int SR, int LOG_TS>
 __global__ void __launch_bounds__(256)
-k_num_cta_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
+k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
     constexpr int HC = TS / 2;
@@ -363,7 +414,7 @@ k_num_cta_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
     __shared__ T p_av[256];
     __shared__ int p_incl[256], p_blen[256], p_wsum[32];
     __shared__ int s_n;
-    __shared__ long long s_so;
+    __shared__ long long s_dest;
     __shared__ int s_ok;
     if (failed(ctl, mask)) return;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -371,7 +422,7 @@ k_num_cta_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
     T *cv = vals + TS;
     int32_t *keys = (int32_t *)(cv + HC);
     int32_t *ck = keys + TS;
-    T *sv = (T *)J.st_val;
+    T *Cv = (T *)C.val;
     BlockProdSmem<T> ps{p_boff, p_av, p_incl, p_blen, p_wsum};
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
@@ -392,7 +443,6 @@ k_num_cta_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
         if (!ok) s_ok = 0;
         __syncthreads();
         if (!s_ok && tid == 0) set_status(ctl, ST_TIMEOUT);
-        // compact (unordered) through a shared counter per warp chunk
         for (int s0 = w * 32; s0 < TS; s0 += 256) {
             const int s = s0 + lane;
             const int32_t k = keys[s];
@@ -410,13 +460,12 @@ k_num_cta_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
             }
         }
         __syncthreads();
-        int n = s_n < HC ? s_n : HC;
+        const int n = s_n < HC ? s_n : HC;
         int N = 2;
         while (N < n) N <<= 1;
         for (int s = n + tid; s < N; s += 256) ck[s] = 0x7fffffff;
         if (tid == 0) {
-            J.slen[t] = n;
-            s_so = J.soff[t];
+            s_dest = c_row_dest(C, J, ctl, i, n);
             nnz_acc += n;
         }
         __syncthreads();
@@ -429,10 +478,13 @@ k_num_cta_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
                 __syncthreads();
             }
         }
-        const long long so = s_so;
-        for (int s = tid; s < n; s += 256) {
-            J.st_col[so + s] = ck[s];
-            sv[so + s] = cv[s];
+        const long long dest = s_dest;
+        if (dest >= 0) {
+            for (int s = tid; s < n; s += 256) {
+                C.col[dest + s] = ck[s];
+                Cv[dest + s] = cv[s];
+            }
+            if (tid == 0) C.len[i] = n;
         }
         __syncthreads();
     }
@@ -443,18 +495,19 @@ k_num_cta_hash(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
 
 template <int SR>
 __global__ void __launch_bounds__(512)
-k_num_gdense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
+k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
     using T = typename Sr<SR>::T;
     __shared__ int64_t p_boff[512];
     __shared__ T p_av[512];
     __shared__ int p_incl[512], p_blen[512], p_wsum[32];
     __shared__ int s_lo, s_hi;
     __shared__ int s_n;
+    __shared__ long long s_dest;
     if (failed(ctl, mask)) return;
     const int tid = threadIdx.x;
     T *acc = (T *)J.gd_acc + (int64_t)blockIdx.x * J.gd_w;
     uint32_t *msk = J.gd_mask + (int64_t)blockIdx.x * (J.gd_w / 32);
-    T *sv = (T *)J.st_val;
+    T *Cv = (T *)C.val;
     BlockProdSmem<T> ps{p_boff, p_av, p_incl, p_blen, p_wsum};
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
@@ -485,11 +538,11 @@ k_num_gdense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
         __syncthreads();
         const int n = s_n;
         if (tid == 0) {
-            J.slen[t] = n;
+            s_dest = c_row_dest(C, J, ctl, i, n);
             nnz_acc += n;
         }
-        const long long so = J.soff[t];
-        const bool fits = true;
+        __syncthreads();
+        const long long dest = s_dest;
         int run = 0;  // entries written by earlier chunks
         for (int x0 = w0; x0 <= w1; x0 += 512) {
             const int x = x0 + tid;
@@ -502,9 +555,9 @@ k_num_gdense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
                 const int j = (x << 5) + b;
-                if (fits) {
-                    J.st_col[so + o] = j;
-                    sv[so + o] = acc[j];
+                if (dest >= 0) {
+                    C.col[dest + o] = j;
+                    Cv[dest + o] = acc[j];
                 }
                 acc[j] = Sr<SR>::zero();
                 o++;
@@ -513,6 +566,7 @@ k_num_gdense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
             run += incl;
             __syncthreads();
         }
+        if (tid == 0 && dest >= 0) C.len[i] = n;
     }
     if (tid == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
 }
@@ -521,7 +575,7 @@ k_num_gdense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin) {
 
 template <int SR, int NW>
 __global__ void __launch_bounds__(NW * 32)
-k_num_warp_dense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin, int mp) {
+k_num_warp_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin, int mp) {
     using T = typename Sr<SR>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     if (failed(ctl, mask)) return;
@@ -529,7 +583,7 @@ k_num_warp_dense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin,
     const int nw = mp >> 5;  // presence words (<= 32)
     T *acc = (T *)smem + (size_t)w * mp;
     uint32_t *msk = (uint32_t *)((T *)smem + (size_t)NW * mp) + (size_t)w * 32;
-    T *sv = (T *)J.st_val;
+    T *Cv = (T *)C.val;
     for (int s = lane; s < mp; s += 32) acc[s] = Sr<SR>::zero();
     msk[lane] = 0u;
     __syncwarp();
@@ -538,7 +592,7 @@ k_num_warp_dense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin,
     for (long long it = (long long)blockIdx.x * NW + w; it < cnt; it += (long long)gridDim.x * NW) {
         const int t = J.bins[(int64_t)bin * J.bin_cap + it];
         const int32_t i = J.R[t];
-        warp_products<SR>(A, B, i, [&](int32_t j, T v) {
+        group_products<SR, 32>(A, B, i, 0xffffffffu, [&](int32_t j, T v) {
             atomicOr(&msk[j >> 5], 1u << (j & 31));
             Sr<SR>::acc(&acc[j], v);
         });
@@ -547,21 +601,25 @@ k_num_warp_dense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin,
         const int pc = __popc(word);
         const int incl = warp_incl_scan<int>(pc);
         const int n = __shfl_sync(0xffffffffu, incl, 31);
-        const long long so = J.soff[t];
-        if (lane == 0) J.slen[t] = n;
-        nnz_acc += n;
+        int64_t dest = 0;
+        if (lane == 0) dest = c_row_dest(C, J, ctl, i, n);
+        dest = __shfl_sync(0xffffffffu, dest, 0);
         int o = incl - pc;
         uint32_t bits = word;
         while (bits) {
             const int b = __ffs(bits) - 1;
             bits &= bits - 1;
             const int j = (lane << 5) + b;
-            J.st_col[so + o] = j;
-            sv[so + o] = acc[j];
+            if (dest >= 0) {
+                C.col[dest + o] = j;
+                Cv[dest + o] = acc[j];
+            }
             acc[j] = Sr<SR>::zero();
             o++;
         }
         msk[lane] = 0u;
+        if (lane == 0 && dest >= 0) C.len[i] = n;
+        nnz_acc += n;
         __syncwarp();
     }
     if (lane == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
@@ -569,7 +627,7 @@ k_num_warp_dense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin,
 
 template <int SR>
 __global__ void __launch_bounds__(512)
-k_num_cta_dense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin, int mp) {
+k_num_cta_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin, int mp) {
     using T = typename Sr<SR>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t p_boff[512];
@@ -580,7 +638,7 @@ k_num_cta_dense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin, 
     const int nw = mp >> 5;
     T *acc = (T *)smem;
     uint32_t *msk = (uint32_t *)(acc + mp);
-    T *sv = (T *)J.st_val;
+    T *Cv = (T *)C.val;
     for (int s = tid; s < mp; s += 512) acc[s] = Sr<SR>::zero();
     if (tid < 32) msk[tid] = 0u;
     __syncthreads();
@@ -600,23 +658,27 @@ k_num_cta_dense(MatView A, MatView B, CJob J, Ctl *ctl, unsigned mask, int bin, 
             const int pc = __popc(word);
             const int incl = warp_incl_scan<int>(pc);
             const int n = __shfl_sync(0xffffffffu, incl, 31);
-            const long long so = J.soff[t];
-            if (lane == 0) {
-                J.slen[t] = n;
-                nnz_acc += n;
-            }
+            int64_t dest = 0;
+            if (lane == 0) dest = c_row_dest(C, J, ctl, i, n);
+            dest = __shfl_sync(0xffffffffu, dest, 0);
             int o = incl - pc;
             uint32_t bits = word;
             while (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
                 const int j = (lane << 5) + b;
-                J.st_col[so + o] = j;
-                sv[so + o] = acc[j];
+                if (dest >= 0) {
+                    C.col[dest + o] = j;
+                    Cv[dest + o] = acc[j];
+                }
                 acc[j] = Sr<SR>::zero();
                 o++;
             }
             msk[lane] = 0u;
+            if (lane == 0) {
+                if (dest >= 0) C.len[i] = n;
+                nnz_acc += n;
+            }
         }
         __syncthreads();
     }
@@ -639,35 +701,37 @@ void init_dense_scratch(int sr, void *acc, uint32_t *mask, int64_t entries, int6
     if (words > 0) cudaMemsetAsync(mask, 0, words * sizeof(uint32_t), s);
 }
 
-void run_size_bins(const MatView &A, const MatView &B, const CJob &J, int64_t max_rows, Ctl *ctl, unsigned mask,
-                   cudaStream_t s, int num_sms) {
+void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const CJob &J, int64_t max_rows, Ctl *ctl,
+                   unsigned mask, cudaStream_t s, int num_sms) {
     if (max_rows <= 0) return;
-    int64_t g = (max_rows * 32 + 255) / 256;
-    if (g > num_sms * 16) g = num_sms * 16;
+    int64_t g = (max_rows + 255) / 256;
+    if (g > num_sms * 8) g = num_sms * 8;
     if (g < 1) g = 1;
-    launch_k(k_size_bins, (unsigned)g, 256, 0, s, A, B, J, ctl, mask);
+    launch_k(k_size_bins, (unsigned)g, 256, 0, s, A, B, C, J, ctl, mask);
 }
 
-template <int SR, int LOG_TS, int NW>
-static void launch_warp_hash(const MatView &A, const MatView &B, const CJob &J, Ctl *ctl, unsigned mask, int bin,
-                             cudaStream_t s, int num_sms) {
+template <int SR, int LOG_TS, int G, int NW>
+static void launch_group_hash(const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl,
+                              unsigned mask, int bin, cudaStream_t s, int num_sms) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
-    const size_t smem = (size_t)NW * (TS + TS / 2) * (sizeof(T) + sizeof(int32_t));
+    constexpr int NG = NW * (32 / G);
+    const size_t smem = (size_t)NG * (TS + TS / 2) * (sizeof(T) + sizeof(int32_t));
     static bool set = false;
     if (!set) {
-        cudaFuncSetAttribute(k_num_warp_hash<SR, LOG_TS, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_num_group_hash<SR, LOG_TS, G, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
         set = true;
     }
     int per_sm = (int)((200 * 1024) / (smem + 1024));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2048 / (NW * 32)) per_sm = 2048 / (NW * 32);
-    launch_k(k_num_warp_hash<SR, LOG_TS, NW>, num_sms * per_sm, NW * 32, smem, s, A, B, J, ctl, mask, bin);
+    launch_k(k_num_group_hash<SR, LOG_TS, G, NW>, num_sms * per_sm, NW * 32, smem, s, A, B, C, J, ctl, mask, bin);
 }
 
 template <int SR, int LOG_TS>
-static void launch_cta_hash(const MatView &A, const MatView &B, const CJob &J, Ctl *ctl, unsigned mask, int bin,
-                            cudaStream_t s, int num_sms) {
+static void launch_cta_hash(const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl,
+                            unsigned mask, int bin, cudaStream_t s, int num_sms) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
     const size_t smem = (size_t)(TS + TS / 2) * (sizeof(T) + sizeof(int32_t));
@@ -679,12 +743,12 @@ static void launch_cta_hash(const MatView &A, const MatView &B, const CJob &J, C
     int per_sm = (int)((200 * 1024) / (smem + 8 * 1024));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 8) per_sm = 8;
-    launch_k(k_num_cta_hash<SR, LOG_TS>, num_sms * per_sm, 256, smem, s, A, B, J, ctl, mask, bin);
+    launch_k(k_num_cta_hash<SR, LOG_TS>, num_sms * per_sm, 256, smem, s, A, B, C, J, ctl, mask, bin);
 }
 
 template <int SR>
-static void run_numeric_t(const MatView &A, const MatView &B, const CJob &J, Ctl *ctl, unsigned mask, cudaStream_t s,
-                          int num_sms) {
+static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,
+                          cudaStream_t s, int num_sms) {
     using T = typename Sr<SR>::T;
     if (J.dense_mode) {
         const int mp = (int)((J.m + 31) / 32 * 32);
@@ -695,26 +759,26 @@ static void run_numeric_t(const MatView &A, const MatView &B, const CJob &J, Ctl
             cudaFuncSetAttribute(k_num_warp_dense<SR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
             set_w = true;
         }
-        launch_k(k_num_warp_dense<SR, NW>, num_sms * 4, NW * 32, smem_w, s, A, B, J, ctl, mask, BIN_WDENSE, mp);
+        launch_k(k_num_warp_dense<SR, NW>, num_sms * 4, NW * 32, smem_w, s, A, B, C, J, ctl, mask, (int)BIN_WDENSE, mp);
         const size_t smem_c = (size_t)mp * sizeof(T) + 32 * sizeof(uint32_t);
-        launch_k(k_num_cta_dense<SR>, num_sms, 512, smem_c, s, A, B, J, ctl, mask, BIN_CDENSE, mp);
+        launch_k(k_num_cta_dense<SR>, num_sms, 512, smem_c, s, A, B, C, J, ctl, mask, (int)BIN_CDENSE, mp);
         return;
     }
-    launch_warp_hash<SR, 6, 8>(A, B, J, ctl, mask, BIN_W64, s, num_sms);
-    launch_warp_hash<SR, 7, 8>(A, B, J, ctl, mask, BIN_W128, s, num_sms);
-    launch_warp_hash<SR, 8, 8>(A, B, J, ctl, mask, BIN_W256, s, num_sms);
-    launch_warp_hash<SR, 9, 4>(A, B, J, ctl, mask, BIN_W512, s, num_sms);
-    launch_warp_hash<SR, 10, 4>(A, B, J, ctl, mask, BIN_W1024, s, num_sms);
-    launch_cta_hash<SR, 11>(A, B, J, ctl, mask, BIN_C2048, s, num_sms);
-    launch_cta_hash<SR, 12>(A, B, J, ctl, mask, BIN_C4096, s, num_sms);
-    launch_cta_hash<SR, 13>(A, B, J, ctl, mask, BIN_C8192, s, num_sms);
-    launch_k(k_num_gdense<SR>, J.gd_ctas, 512, 0, s, A, B, J, ctl, mask, BIN_GD);
+    launch_group_hash<SR, 6, 8, 8>(A, B, C, J, ctl, mask, BIN_G8, s, num_sms);
+    launch_group_hash<SR, 7, 16, 8>(A, B, C, J, ctl, mask, BIN_G16, s, num_sms);
+    launch_group_hash<SR, 8, 32, 8>(A, B, C, J, ctl, mask, BIN_W256, s, num_sms);
+    launch_group_hash<SR, 9, 32, 4>(A, B, C, J, ctl, mask, BIN_W512, s, num_sms);
+    launch_group_hash<SR, 10, 32, 4>(A, B, C, J, ctl, mask, BIN_W1024, s, num_sms);
+    launch_cta_hash<SR, 11>(A, B, C, J, ctl, mask, BIN_C2048, s, num_sms);
+    launch_cta_hash<SR, 12>(A, B, C, J, ctl, mask, BIN_C4096, s, num_sms);
+    launch_cta_hash<SR, 13>(A, B, C, J, ctl, mask, BIN_C8192, s, num_sms);
+    launch_k(k_num_gdense<SR>, J.gd_ctas, 512, 0, s, A, B, C, J, ctl, mask, (int)BIN_GD);
 }
 
-void run_numeric(int sr, const MatView &A, const MatView &B, const CJob &J, Ctl *ctl, unsigned mask, cudaStream_t s,
-                 int num_sms) {
-    if (sr == SR_PT) run_numeric_t<SR_PT>(A, B, J, ctl, mask, s, num_sms);
-    else run_numeric_t<SR_MP>(A, B, J, ctl, mask, s, num_sms);
+void run_numeric(int sr, const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,
+                 cudaStream_t s, int num_sms) {
+    if (sr == SR_PT) run_numeric_t<SR_PT>(A, B, C, J, ctl, mask, s, num_sms);
+    else run_numeric_t<SR_MP>(A, B, C, J, ctl, mask, s, num_sms);
 }
 
 }  // namespace dspg

@@ -32,137 +32,188 @@ __device__ __forceinline__ long long atomic_add_ll(long long *p, long long v) {
     return (long long)atomicAdd((unsigned long long *)p, (unsigned long long)v);
 }
 
-// ------------------------------------------------------------- segments
-
-__global__ void k_segments(const int32_t *srow, int64_t n, int64_t nrows, int32_t *seg_lo, int32_t *seg_hi,
-                           long long *n_seg, const Ctl *ctl, unsigned mask) {
-    if (failed(ctl, mask)) return;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = base + threadIdx.x;
-        int32_t r = 0;
-        bool head = false;
-        if (s < n) {
-            r = srow[s];
-            // padding entries of a forwarded batch sit in a row past the end
-            head = (int64_t)r < nrows && (s == 0 || srow[s - 1] != r);
-        }
-        const long long t = warp_fetch_add(n_seg, head ? 1 : 0);
-        if (head) {
-            seg_lo[t] = (int32_t)s;
-            seg_hi[t] = (int32_t)upper_bound_dev<int32_t>(srow, s, n, r);
-        }
-    }
-}
-
 // ------------------------------------------------------------- classify
 
-// A warp takes 32 segments at a time: it classifies them one after the
-// other (all lanes on one segment), lane r keeping segment r's totals; then
-// it allocates merge items, staging and copy items for the 32 segments with
-// one atomic per counter, and finally writes the INS/UPD entries.
+constexpr int SEG_SHORT = 16;  // row segments up to this many updates are classified by one thread
+
+__device__ __forceinline__ uint8_t kind_of(uint8_t op, bool present) {
+    if (op == OP_DEAD) return K_NOP;
+    if (op == OP_DELETE) return present ? K_DEL : K_NOP;
+    return present ? K_UPD : K_INS;
+}
+
+// The thread at the first entry of each row segment of the sorted batch
+// owns the segment: it classifies the segment's updates against the old row
+// (binary search), keeps running INS/DEL counts, and writes the INS/UPD
+// entries of a changed row to their final staging slots; merge items,
+// staging and copy items are handed out with one atomic per warp.
+// Segments with more than SEG_SHORT updates are classified by the whole warp
+// afterwards, one at a time.
 template <typename T>
 __global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigned stage_bit) {
     if (failed(ctl, mask)) return;
     UpdCtl *u = &ctl->u[J.which];
-    const long long nseg = u->n_seg;
+    const int64_t n = J.n;
     const int lane = threadIdx.x & 31;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const T *bval = (const T *)J.val;
     T *sval = (T *)J.st_val;
     long long s_ins = 0, s_del = 0, s_upd = 0, s_nop = 0;
-    for (long long t0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; t0 < nseg; t0 += nwarps * 32) {
-        int my_L = 0, my_ins = 0, my_del = 0, my_changed = 0;
-        int32_t my_row = 0;
-        for (int rr = 0; rr < 32; rr++) {
-            const long long t = t0 + rr;
-            if (t >= nseg) break;
-            const int lo = J.seg_lo[t], hi = J.seg_hi[t];
-            const int32_t r = J.row[lo];
-            const int64_t base = M.off[r];
-            const int L = M.len[r];
-            const int32_t *rc = M.col + base;
-            int cins = 0, cdel = 0, cupd = 0, cnop = 0;
-            for (int u0 = lo; u0 < hi; u0 += 32) {
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = base + threadIdx.x;
+        int32_t r = 0;
+        bool head = false;
+        int hi = 0;
+        if (s < n) {
+            r = J.row[s];
+            // padding entries of a forwarded batch sit in a row past the end
+            head = (int64_t)r < M.nrows && (s == 0 || J.row[s - 1] != r);
+        }
+        if (head) hi = (int)upper_bound_dev<int32_t>(J.row, s, n, r);
+        const bool lng = head && (hi - s > SEG_SHORT);
+        const bool mine = head && !lng;
+        int L = 0, cins = 0, cdel = 0, cupd = 0, cnop = 0;
+        if (mine) {
+            const int64_t mb = M.off[r];
+            L = M.len[r];
+            const int32_t *rc = M.col + mb;
+            for (int x = (int)s; x < hi; x++) {
+                const int32_t c = J.col[x];
+                const uint8_t op = J.op[x];
+                const int p = (int)lower_bound_dev<int32_t>(rc, 0, L, c);
+                const uint8_t k = kind_of(op, p < L && rc[p] == c);
+                J.kind[x] = k;
+                J.pos[x] = p;
+                J.insx[x] = cins;
+                J.delx[x] = cdel;
+                cins += k == K_INS;
+                cdel += k == K_DEL;
+                cupd += k == K_UPD;
+                cnop += (k == K_NOP && op == OP_DELETE);
+            }
+        }
+        s_ins += cins;
+        s_del += cdel;
+        s_upd += cupd;
+        s_nop += cnop;
+        const bool changed = mine && (cins + cdel + cupd) > 0;
+        const int nl = L + cins - cdel;
+        const int nch = changed ? (L + CH - 1) / CH : 0;
+        const long long m = warp_fetch_add(&u->n_merge, changed ? 1 : 0);
+        const long long soff = warp_fetch_add(&u->stage_top, changed ? nl : 0);
+        const long long cb = warp_fetch_add(&u->n_chunk, nch);
+        if (changed) {
+            if (soff + nl > J.st_cap || cb + nch > J.ch_cap) {
+                set_status(ctl, stage_bit);
+            } else {
+                J.m_row[m] = r;
+                J.m_lo[m] = (int32_t)s;
+                J.m_hi[m] = hi;
+                J.m_len[m] = nl;
+                J.m_soff[m] = soff;
+                J.m_nins[m] = cins;
+                J.m_ndel[m] = cdel;
+                for (int c = 0; c < nch; c++) {
+                    J.ch_item[cb + c] = (int32_t)m;
+                    J.ch_part[cb + c] = c;
+                }
+                for (int x = (int)s; x < hi; x++) {
+                    const uint8_t k = J.kind[x];
+                    if (k == K_INS || k == K_UPD) {
+                        const int o = J.pos[x] - J.delx[x] + J.insx[x];
+                        J.st_col[soff + o] = J.col[x];
+                        if (sval) sval[soff + o] = bval[x];
+                    }
+                }
+            }
+        }
+        // long segments of this warp: all lanes on one segment at a time
+        unsigned lm = __ballot_sync(0xffffffffu, lng);
+        while (lm) {
+            const int src = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const int lo = (int)__shfl_sync(0xffffffffu, (long long)s, src);
+            const int hi2 = __shfl_sync(0xffffffffu, hi, src);
+            const int32_t r2 = __shfl_sync(0xffffffffu, r, src);
+            const int64_t mb = M.off[r2];
+            const int L2 = M.len[r2];
+            const int32_t *rc = M.col + mb;
+            int ti = 0, td = 0, tu = 0, tn = 0;
+            for (int u0 = lo; u0 < hi2; u0 += 32) {
                 const int x = u0 + lane;
                 int ins = 0, del = 0;
-                if (x < hi) {
+                if (x < hi2) {
                     const int32_t c = J.col[x];
                     const uint8_t op = J.op[x];
-                    const int p = (int)lower_bound_dev<int32_t>(rc, 0, L, c);
-                    const bool present = p < L && rc[p] == c;
-                    uint8_t k;
-                    if (op == OP_DEAD) k = K_NOP;
-                    else if (op == OP_DELETE) k = present ? K_DEL : K_NOP;
-                    else k = present ? K_UPD : K_INS;
+                    const int p = (int)lower_bound_dev<int32_t>(rc, 0, L2, c);
+                    const uint8_t k = kind_of(op, p < L2 && rc[p] == c);
                     J.kind[x] = k;
                     J.pos[x] = p;
                     ins = k == K_INS;
                     del = k == K_DEL;
-                    cupd += k == K_UPD;
-                    cnop += (k == K_NOP && op == OP_DELETE);
+                    tu += k == K_UPD;
+                    tn += (k == K_NOP && op == OP_DELETE);
                 }
                 const int ii = warp_incl_scan<int>(ins), di = warp_incl_scan<int>(del);
-                if (x < hi) {
-                    J.insx[x] = cins + ii - ins;
-                    J.delx[x] = cdel + di - del;
+                if (x < hi2) {
+                    J.insx[x] = ti + ii - ins;
+                    J.delx[x] = td + di - del;
                 }
-                cins += __shfl_sync(0xffffffffu, ii, 31);
-                cdel += __shfl_sync(0xffffffffu, di, 31);
+                ti += __shfl_sync(0xffffffffu, ii, 31);
+                td += __shfl_sync(0xffffffffu, di, 31);
             }
-            cupd = warp_sum<int>(cupd);
-            cnop = warp_sum<int>(cnop);
-            s_ins += cins;
-            s_del += cdel;
-            s_upd += cupd;
-            s_nop += cnop;
-            if (lane == rr) {
-                my_L = L;
-                my_ins = cins;
-                my_del = cdel;
-                my_changed = (cins + cdel + cupd) > 0;
-                my_row = r;
+            tu = warp_sum<int>(tu);
+            tn = warp_sum<int>(tn);
+            if (lane == 0) {
+                s_ins += ti;
+                s_del += td;
+                s_upd += tu;
+                s_nop += tn;
             }
-        }
-        const int my_nl = my_L + my_ins - my_del;
-        const int my_nch = my_changed ? (my_L + CH - 1) / CH : 0;
-        const long long m = warp_fetch_add(&u->n_merge, my_changed);
-        const long long soff = warp_fetch_add(&u->stage_top, my_changed ? my_nl : 0);
-        const long long cb = warp_fetch_add(&u->n_chunk, my_nch);
-        int ok = 1;
-        if (my_changed) {
-            ok = (soff + my_nl <= J.st_cap) && (cb + my_nch <= J.ch_cap);
-            if (!ok) set_status(ctl, stage_bit);
-            else {
-                J.m_row[m] = my_row;
-                J.m_seg[m] = (int32_t)(t0 + lane);
-                J.m_len[m] = my_nl;
-                J.m_soff[m] = soff;
-                J.m_nins[m] = my_ins;
-                J.m_ndel[m] = my_del;
-                for (int c = 0; c < my_nch; c++) {
-                    J.ch_item[cb + c] = (int32_t)m;
-                    J.ch_part[cb + c] = c;
+            if (ti + td + tu == 0) continue;
+            const int nl2 = L2 + ti - td;
+            const int nch2 = (L2 + CH - 1) / CH;
+            long long m2 = 0, so2 = 0, cb2 = 0;
+            int ok = 1;
+            if (lane == 0) {
+                m2 = atomic_add_ll(&u->n_merge, 1);
+                so2 = atomic_add_ll(&u->stage_top, nl2);
+                cb2 = atomic_add_ll(&u->n_chunk, nch2);
+                ok = (so2 + nl2 <= J.st_cap) && (cb2 + nch2 <= J.ch_cap);
+                if (!ok) set_status(ctl, stage_bit);
+                else {
+                    J.m_row[m2] = r2;
+                    J.m_lo[m2] = lo;
+                    J.m_hi[m2] = hi2;
+                    J.m_len[m2] = nl2;
+                    J.m_soff[m2] = so2;
+                    J.m_nins[m2] = ti;
+                    J.m_ndel[m2] = td;
                 }
             }
-        }
-        __syncwarp();
-        for (int rr = 0; rr < 32; rr++) {
-            const long long t = t0 + rr;
-            if (t >= nseg) break;
-            const int write = __shfl_sync(0xffffffffu, my_changed && ok, rr);
-            const long long so = __shfl_sync(0xffffffffu, soff, rr);
-            if (!write) continue;
-            const int lo = J.seg_lo[t], hi = J.seg_hi[t];
-            for (int x = lo + lane; x < hi; x += 32) {
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) continue;
+            m2 = __shfl_sync(0xffffffffu, m2, 0);
+            so2 = __shfl_sync(0xffffffffu, so2, 0);
+            cb2 = __shfl_sync(0xffffffffu, cb2, 0);
+            for (int c = lane; c < nch2; c += 32) {
+                J.ch_item[cb2 + c] = (int32_t)m2;
+                J.ch_part[cb2 + c] = c;
+            }
+            __syncwarp();
+            for (int x = lo + lane; x < hi2; x += 32) {
                 const uint8_t k = J.kind[x];
                 if (k == K_INS || k == K_UPD) {
                     const int o = J.pos[x] - J.delx[x] + J.insx[x];
-                    J.st_col[so + o] = J.col[x];
-                    if (sval) sval[so + o] = bval[x];
+                    J.st_col[so2 + o] = J.col[x];
+                    if (sval) sval[so2 + o] = bval[x];
                 }
             }
         }
     }
+    s_ins = warp_sum<long long>(s_ins);
+    s_del = warp_sum<long long>(s_del);
+    s_upd = warp_sum<long long>(s_upd);
+    s_nop = warp_sum<long long>(s_nop);
     if (lane == 0) {
         if (s_ins) atomic_add_ll(&u->ins, s_ins);
         if (s_del) atomic_add_ll(&u->del, s_del);
@@ -184,8 +235,7 @@ __global__ void k_merge_copy(UpdJob J, MatView M, const Ctl *ctl, unsigned mask)
     for (long long x = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < nch; x += nwarps) {
         const int m = J.ch_item[x], part = J.ch_part[x];
         const int32_t r = J.m_row[m];
-        const int t = J.m_seg[m];
-        const int lo = J.seg_lo[t], hi = J.seg_hi[t];
+        const int lo = J.m_lo[m], hi = J.m_hi[m];
         const int64_t base = M.off[r];
         const int L = M.len[r];
         const int64_t soff = J.m_soff[m];
@@ -356,16 +406,10 @@ static unsigned grid_for(int64_t n, int nt) {
     return (unsigned)g;
 }
 
-void run_segments(const UpdJob &J, int64_t nrows, Ctl *ctl, unsigned mask, cudaStream_t s) {
-    if (J.n <= 0) return;
-    launch_k(k_segments, (unsigned)((J.n + 255) / 256), 256, 0, s, J.row, J.n, nrows, J.seg_lo, J.seg_hi,
-                                                            &ctl->u[J.which].n_seg, ctl, mask);
-}
-
 void run_classify(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsigned mask, unsigned stage_bit,
                   cudaStream_t s, int num_sms) {
     if (J.n <= 0) return;
-    unsigned g = grid_for(J.n * 32, 256);
+    unsigned g = grid_for(J.n, 256);
     if (g > (unsigned)num_sms * 8) g = num_sms * 8;
     if (vsize == 8) launch_k(k_classify<double>, g, 256, 0, s, J, M, ctl, mask, stage_bit);
     else launch_k(k_classify<int32_t>, g, 256, 0, s, J, M, ctl, mask, stage_bit);

@@ -103,7 +103,7 @@ EXPORTED = ["dspg_build", "dspg_apply_batch", "dspg_read_C", "dspg_read_A", "dsp
             "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_set_profiling", "dspg_stage_times",
             "dspg_kernel_launches", "dspg_destroy", "dspg_last_error"]
 
-STAGES = ["sort", "classify", "detect", "merge", "commit", "transpose", "size", "numeric", "splice"]
+STAGES = ["sort", "classify", "detect", "merge", "commit", "transpose", "size", "numeric"]
 
 
 def kernel_launches() -> int:
