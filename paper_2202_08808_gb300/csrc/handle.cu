@@ -18,9 +18,11 @@
 // has succeeded, so the handle always stays consistent.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <stdexcept>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -69,12 +71,14 @@ struct DBuf {
         n = 0;
     }
     // Ensure room for `need` elements; contents are discarded on growth.
-    void reserve(int64_t need) {
-        if (need <= n) return;
+    // Returns true when the buffer moved.
+    bool reserve(int64_t need) {
+        if (need <= n) return false;
         T *q = (T *)dmalloc(sizeof(T) * (size_t)need);
         release();
         p = q;
         n = need;
+        return true;
     }
     void swap(DBuf &o) {
         std::swap(p, o.p);
@@ -116,8 +120,10 @@ struct UpdWs {
     DBuf<uint32_t> i0, i1, counts;
     DBuf<int64_t> scan_tmp, scan_out;
 
-    void ensure(int64_t n, int64_t arena_cap) {
+    bool ensure(int64_t n, int64_t arena_cap) {
+        bool moved = false;
         if (n > ncap) {
+            moved = true;
             int64_t c = std::max<int64_t>(n, std::max<int64_t>(2 * ncap, 1024));
             in_row.reserve(c); in_col.reserve(c); in_val.reserve(c * std::max(vsize, 1)); in_op.reserve(c);
             row.reserve(c); col.reserve(c); val.reserve(c * std::max(vsize, 1)); op.reserve(c); kind.reserve(c);
@@ -132,18 +138,20 @@ struct UpdWs {
             scan_tmp.reserve(scan_tmp_entries(cnt) + 1);
             ncap = c;
         }
-        if (st_cap < 16 * n + 65536) grow_stage(16 * n + 65536);
-        ch_item.reserve(ncap + arena_cap / 256 + 64);
-        ch_part.reserve(ncap + arena_cap / 256 + 64);
+        if (st_cap < 16 * n + 65536) moved |= grow_stage(16 * n + 65536);
+        moved |= ch_item.reserve(ncap + arena_cap / 256 + 64);
+        moved |= ch_part.reserve(ncap + arena_cap / 256 + 64);
+        return moved;
     }
-    void grow_stage(int64_t need) {
-        if (need <= st_cap) return;
+    bool grow_stage(int64_t need) {
+        if (need <= st_cap) return false;
         int64_t c = std::max<int64_t>(need, st_cap + st_cap / 2);
         st_col.reserve(c);
         if (vsize) st_val.reserve(c * vsize);
         st_cap = c;
         cc_item.reserve(ncap * 2 + c / 256 + 64);
         cc_part.reserve(ncap * 2 + c / 256 + 64);
+        return true;
     }
     SortOut sort_out() { return SortOut{row.p, col.p, vsize ? (void *)val.p : nullptr, op.p}; }
     SortTmp sort_tmp() {
@@ -202,8 +210,25 @@ struct dspg_handle {
     BatchIn inA, inB;
     int64_t last_nR = 0;
     bool prof = false;
-    cudaEvent_t ev[DSPG_NSTAGES + 1] = {};
+    cudaEvent_t pev[10] = {};  // stage boundaries (profiling)
     float stage_ms[DSPG_NSTAGES] = {};
+    // streams and events of the pipeline's branches
+    cudaStream_t gs = nullptr;       // graphs run here
+    cudaStream_t side = nullptr;     // transposed-pattern branch
+    cudaStream_t nstr[3] = {};       // numeric bin branches
+    cudaEvent_t evIn = nullptr, evFork = nullptr, evDetect = nullptr, evSide = nullptr, evSize = nullptr;
+    cudaEvent_t evNum[3] = {};
+    // captured pipelines, keyed by batch sizes and the buffer epoch
+    struct Graph {
+        int64_t nA, nB;
+        uint64_t epoch;
+        bool prof;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
+    std::vector<Graph> seen;  // keys run once eagerly (exec unused)
+    uint64_t epoch = 1;       // bumped whenever a persistent buffer moves
+    bool use_graphs = true;
     int64_t compactions = 0;
     std::string err;
 
@@ -261,6 +286,7 @@ void make_slack(dspg_handle *h, DevMat &M, int64_t nrows, int64_t ncols, int vsi
     long long t = total;
     CK(cudaMemcpyAsync(M.top.p, &t, sizeof(long long), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
+    h->epoch++;
 }
 
 // Rebuild M's arena with fresh slack for every row and at least twice the
@@ -291,6 +317,7 @@ void regrow(dspg_handle *h, DevMat &M, cudaStream_t s) {
     M.val.swap(nval);
     M.arena_cap = cap;
     h->compactions++;
+    h->epoch++;
 }
 
 // Canonical CSR copy of M's rows (all rows when rows == nullptr) into device
@@ -315,6 +342,7 @@ void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
     CWs &w = h->wc;
     const int64_t n = h->A.nrows;
     if (w.nrows == n && w.R.p) return;
+    h->epoch++;
     w.nrows = n;
     const int64_t nn = std::max<int64_t>(n, 1);
     w.R.reserve(nn);
@@ -378,6 +406,18 @@ CommitJob upd_commit_job(dspg_handle *h, UpdWs &w, unsigned arena_bit, unsigned 
     return J;
 }
 
+// The bin kernels of the recompute run on four branches that join s again.
+void numeric_branches(dspg_handle *h, cudaStream_t s, const CJob &J) {
+    CK(cudaEventRecord(h->evSize, s));
+    for (int k = 0; k < 3; k++) CK(cudaStreamWaitEvent(h->nstr[k], h->evSize, 0));
+    const cudaStream_t ss[4] = {s, h->nstr[0], h->nstr[1], h->nstr[2]};
+    run_numeric(h->sr, h->A.view(), h->Bm().view(), h->C.view(), J, h->ctl, M_C, ss, 4, h->num_sms);
+    for (int k = 0; k < 3; k++) {
+        CK(cudaEventRecord(h->evNum[k], h->nstr[k]));
+        CK(cudaStreamWaitEvent(s, h->evNum[k], 0));
+    }
+}
+
 // Full recompute of C from A, B (the static product).  The sizing pass lays
 // C out afresh (room for each row's product bound), reusing the arena when
 // it is large enough; the numeric kernels then write every row in place.
@@ -412,10 +452,11 @@ void static_recompute(dspg_handle *h, cudaStream_t s) {
         C.arena_cap = cap;
     }
     if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "static sizing failed with status " + std::to_string(h->hctl->status));
-    run_numeric(h->sr, Av, Bv, C.view(), c_job(h, h->wc.iota.p, true), h->ctl, M_C, s, h->num_sms);
+    numeric_branches(h, s, c_job(h, h->wc.iota.p, true));
     read_ctl(h, s);
     if (h->hctl->status & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, "accumulator probe limit reached");
     if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "static recompute failed with status " + std::to_string(h->hctl->status));
+    h->epoch++;
 }
 
 // Transposed pattern of A (rows of A^T = columns of A), built from A's rows.
@@ -449,6 +490,7 @@ void build_transpose(dspg_handle *h, cudaStream_t s) {
     scan_i32_to_i64(tlen.p, toff.p, A.ncols, tmp.p, s);
     make_slack(h, h->AT, A.ncols, A.nrows, 0, toff.p, tlen.p, (const int32_t *)(alt ? v1.p : v0.p), nullptr, s);
     h->has_at = true;
+    h->epoch++;
 }
 
 // ------------------------------------------------------------ pipeline
@@ -504,19 +546,25 @@ void stage_commit_ab(dspg_handle *h, cudaStream_t s) {
                    M_AB & ~ST_AB_ARENA, M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
 }
 
-void stage_transpose(dspg_handle *h, cudaStream_t s) {
-    if (!h->has_at || h->inA.n <= 0) return;
+// Transposed pattern of A, first part: forward the structural changes of
+// the A batch, sort them by (column, row) and rebuild the changed rows in
+// staging.  These only read the transposed pattern.
+void transpose_front(dspg_handle *h, cudaStream_t s) {
     const int64_t n = h->inA.n;
     UpdWs &w = h->wAT;
-    UpdJob JA = h->wA.job(n);
-    run_transpose_feed(JA, (int32_t)h->AT.nrows, w.in_row.p, w.in_col.p, w.in_op.p, h->ctl, M_AB, s);
+    run_transpose_feed(h->wA.job(n), (int32_t)h->AT.nrows, w.in_row.p, w.in_col.p, w.in_op.p, h->ctl, M_AB, s);
     sort_updates(w.in_row.p, w.in_col.p, nullptr, w.in_op.p, n, h->AT.nrows + 1, h->AT.ncols, h->sr, false,
                  w.sort_out(), w.sort_tmp(), h->ctl, M_AT, s);
     UpdJob J = w.job(n);
     run_classify(J, h->AT.view(), 0, h->ctl, M_AT & ~ST_AT_STAGE, ST_AT_STAGE, s, h->num_sms);
     run_merge_copy(J, h->AT.view(), 0, h->ctl, M_AT, s, h->num_sms);
-    run_commit(upd_commit_job(h, w, ST_AT_ARENA, ST_AT_STAGE), h->AT.view(), 0, n, h->ctl, M_AT & ~ST_AT_ARENA, M_AT,
-               h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
+}
+
+// Second part: write the rebuilt rows into the transposed pattern (only
+// after the affected-row detection has finished reading it).
+void transpose_commit(dspg_handle *h, cudaStream_t s) {
+    run_commit(upd_commit_job(h, h->wAT, ST_AT_ARENA, ST_AT_STAGE), h->AT.view(), 0, h->inA.n, h->ctl,
+               M_AT & ~ST_AT_ARENA, M_AT, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
 }
 
 void stage_size(dspg_handle *h, cudaStream_t s) {
@@ -524,22 +572,61 @@ void stage_size(dspg_handle *h, cudaStream_t s) {
                   h->num_sms);
 }
 
-void stage_numeric(dspg_handle *h, cudaStream_t s) {
-    run_numeric(h->sr, h->A.view(), h->Bm().view(), h->C.view(), c_job(h, h->wc.R.p, false), h->ctl, M_C, s,
-                h->num_sms);
+void stage_numeric(dspg_handle *h, cudaStream_t s) { numeric_branches(h, s, c_job(h, h->wc.R.p, false)); }
+
+void rec_event(cudaEvent_t e, cudaStream_t st, bool capturing) {
+    if (capturing) CK(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal));
+    else CK(cudaEventRecord(e, st));
 }
 
-typedef void (*StageFn)(dspg_handle *, cudaStream_t);
-const StageFn kStages[DSPG_NSTAGES] = {stage_sort,      stage_classify, stage_detect,  stage_merge,
-                                       stage_commit_ab, stage_transpose, stage_size, stage_numeric};
-
-// Enqueue stages [from, to); with profiling on, an event brackets each.
-void run_stages(dspg_handle *h, int from, int to, cudaStream_t s, bool timed) {
-    for (int k = from; k < to; k++) {
-        if (timed) CK(cudaEventRecord(h->ev[k], s));
-        kStages[k](h, s);
+// The whole batch on stream s.  The transposed-pattern update runs on a side
+// branch (its commit waits for the detection, which reads the old pattern);
+// s waits for it at the end.  With `timed`, events mark the stage bounds.
+void pipeline(dspg_handle *h, cudaStream_t s, bool timed, bool capturing) {
+    auto mark = [&](int k, cudaStream_t st) {
+        if (timed) rec_event(h->pev[k], st, capturing);
+    };
+    mark(0, s);
+    stage_sort(h, s);
+    mark(1, s);
+    stage_classify(h, s);
+    const bool side_on = h->has_at && h->inA.n > 0;
+    if (side_on) {
+        CK(cudaEventRecord(h->evFork, s));
+        CK(cudaStreamWaitEvent(h->side, h->evFork, 0));
+        mark(8, h->side);
+        transpose_front(h, h->side);
     }
-    if (timed) CK(cudaEventRecord(h->ev[to], s));
+    mark(2, s);
+    stage_detect(h, s);
+    if (side_on) {
+        CK(cudaEventRecord(h->evDetect, s));
+        CK(cudaStreamWaitEvent(h->side, h->evDetect, 0));
+        transpose_commit(h, h->side);
+        mark(9, h->side);
+        CK(cudaEventRecord(h->evSide, h->side));
+    }
+    mark(3, s);
+    stage_merge(h, s);
+    mark(4, s);
+    stage_commit_ab(h, s);
+    mark(5, s);
+    stage_size(h, s);
+    mark(6, s);
+    stage_numeric(h, s);
+    mark(7, s);
+    if (side_on) CK(cudaStreamWaitEvent(s, h->evSide, 0));
+}
+
+void stage_times_from_events(dspg_handle *h) {
+    const int a[DSPG_NSTAGES] = {0, 1, 2, 3, 4, 8, 5, 6};
+    const int b[DSPG_NSTAGES] = {1, 2, 3, 4, 5, 9, 6, 7};
+    const bool side_on = h->has_at && h->inA.n > 0;
+    for (int k = 0; k < DSPG_NSTAGES; k++) {
+        h->stage_ms[k] = 0.f;
+        if (k == DSPG_STAGE_TRANSPOSE && !side_on) continue;
+        CK(cudaEventElapsedTime(&h->stage_ms[k], h->pev[a[k]], h->pev[b[k]]));
+    }
 }
 
 void reset_range(dspg_handle *h, void *first, size_t bytes, cudaStream_t s) {
@@ -555,21 +642,70 @@ void reset_c_counters(dspg_handle *h, cudaStream_t s) {
 void upload(dspg_handle *h, UpdWs &w, const dspg_updates *u, BatchIn &in, cudaStream_t s) {
     in.n = u ? u->n : 0;
     if (in.n <= 0) return;
-    if (u->on_device) {
-        in.row = u->row;
-        in.col = u->col;
-        in.val = u->val;
-        in.op = u->op;
-        return;
-    }
-    CK(cudaMemcpyAsync(w.in_row.p, u->row, sizeof(int32_t) * in.n, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(w.in_col.p, u->col, sizeof(int32_t) * in.n, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(w.in_val.p, u->val, (size_t)h->vsize * in.n, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(w.in_op.p, u->op, sizeof(uint8_t) * in.n, cudaMemcpyHostToDevice, s));
+    // the batch is always copied into library buffers, so that captured
+    // pipelines keep stable pointers
+    const cudaMemcpyKind kind = u->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(w.in_row.p, u->row, sizeof(int32_t) * in.n, kind, s));
+    CK(cudaMemcpyAsync(w.in_col.p, u->col, sizeof(int32_t) * in.n, kind, s));
+    CK(cudaMemcpyAsync(w.in_val.p, u->val, (size_t)h->vsize * in.n, kind, s));
+    CK(cudaMemcpyAsync(w.in_op.p, u->op, sizeof(uint8_t) * in.n, kind, s));
     in.row = w.in_row.p;
     in.col = w.in_col.p;
     in.val = w.in_val.p;
     in.op = w.in_op.p;
+}
+
+// Runs the pipeline once and reads the status.  A batch shape (sizes of the
+// A and B batches) seen before with unchanged buffers runs as a captured
+// CUDA graph on the handle's own stream (ordered after s); the first time a
+// shape is seen it runs eagerly on s, the second time it is captured.
+void run_first(dspg_handle *h, cudaStream_t s) {
+    const int64_t nA = h->inA.n, nB = h->inB.n;
+    if (h->use_graphs) {
+        for (auto &g : h->graphs) {
+            if (g.nA == nA && g.nB == nB && g.epoch == h->epoch && g.prof == h->prof) {
+                CK(cudaEventRecord(h->evIn, s));
+                CK(cudaStreamWaitEvent(h->gs, h->evIn, 0));
+                CK(cudaGraphLaunch(g.exec, h->gs));
+                CK(cudaEventRecord(h->evIn, h->gs));
+                CK(cudaStreamWaitEvent(s, h->evIn, 0));
+                CK(cudaStreamSynchronize(h->gs));
+                return;
+            }
+        }
+        bool seen = false;
+        for (auto &g : h->seen) seen |= (g.nA == nA && g.nB == nB && g.epoch == h->epoch && g.prof == h->prof);
+        if (seen) {
+            cudaGraph_t graph = nullptr;
+            CK(cudaEventRecord(h->evIn, s));
+            CK(cudaStreamWaitEvent(h->gs, h->evIn, 0));
+            CK(cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeThreadLocal));
+            cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->gs);
+            pipeline(h, h->gs, h->prof, true);
+            cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->gs);
+            CK(cudaStreamEndCapture(h->gs, &graph));
+            cudaGraphExec_t exec = nullptr;
+            const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(e);
+            if (h->graphs.size() >= 4) {
+                cudaGraphExecDestroy(h->graphs.front().exec);
+                h->graphs.erase(h->graphs.begin());
+            }
+            h->graphs.push_back(dspg_handle::Graph{nA, nB, h->epoch, h->prof, exec});
+            CK(cudaGraphLaunch(exec, h->gs));
+            CK(cudaEventRecord(h->evIn, h->gs));
+            CK(cudaStreamWaitEvent(s, h->evIn, 0));
+            CK(cudaStreamSynchronize(h->gs));
+            return;
+        }
+        if (h->seen.size() >= 16) h->seen.erase(h->seen.begin());
+        h->seen.push_back(dspg_handle::Graph{nA, nB, h->epoch, h->prof, nullptr});
+    }
+    CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+    pipeline(h, s, h->prof, false);
+    CK(cudaGetLastError());
+    read_ctl(h, s);
 }
 
 dspg_status fail(dspg_handle *h, const Err &e) {
@@ -704,6 +840,13 @@ dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, 
         CK(cudaGetDevice(&h->dev));
         CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev));
         CK(cudaMalloc((void **)&h->ctl, sizeof(Ctl)));
+        CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        for (int k = 0; k < 3; k++) CK(cudaStreamCreateWithFlags(&h->nstr[k], cudaStreamNonBlocking));
+        for (cudaEvent_t *e : {&h->evIn, &h->evFork, &h->evDetect, &h->evSide, &h->evSize, &h->evNum[0], &h->evNum[1],
+                               &h->evNum[2]})
+            CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        if (const char *env = getenv("DSPG_NO_GRAPHS")) h->use_graphs = env[0] == '0';
         CK(cudaMallocHost((void **)&h->hctl, sizeof(Ctl)));
         std::memset(h->hctl, 0, sizeof(Ctl));
         h->wA.which = 0; h->wA.vsize = h->vsize;
@@ -739,33 +882,30 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
         if (h->b_is_a && nB > 0) throw Err(DSPG_ERR_INVALID, "B is A: pass the batch as dA only");
         if (!h->b_is_a && nB > 0 && !h->has_at) build_transpose(h, s);
         ensure_c_ws(h, s);
-        h->wA.ensure(nA, h->A.arena_cap);
-        if (!h->b_is_a) h->wB.ensure(nB, h->B.arena_cap);
-        if (h->has_at) h->wAT.ensure(nA, h->AT.arena_cap);
+        if (h->wA.ensure(nA, h->A.arena_cap)) h->epoch++;
+        if (!h->b_is_a && h->wB.ensure(nB, h->B.arena_cap)) h->epoch++;
+        if (h->has_at && h->wAT.ensure(nA, h->AT.arena_cap)) h->epoch++;
         upload(h, h->wA, dA, h->inA, s);
         upload(h, h->wB, dB, h->inB, s);
         if (h->b_is_a) h->inB = BatchIn{};
         const int64_t compactions0 = h->compactions;
 
-        CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
-        run_stages(h, 0, DSPG_NSTAGES, s, h->prof);
-        CK(cudaGetLastError());
-        read_ctl(h, s);
-        if (h->prof)
-            for (int k = 0; k < DSPG_NSTAGES; k++) CK(cudaEventElapsedTime(&h->stage_ms[k], h->ev[k], h->ev[k + 1]));
+        run_first(h, s);
+        if (h->prof) stage_times_from_events(h);
 
         for (int iter = 0; iter < 8 && h->hctl->status; iter++) {
             const unsigned st = h->hctl->status;
             if (st & ST_INVALID) throw Err(DSPG_ERR_INVALID, "batch entry out of range or with an invalid value/op");
             if (st & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, "accumulator probe limit reached");
             if (st & ST_AB_STAGE) {
-                h->wA.grow_stage(h->hctl->u[0].stage_top + 1024);
-                h->wB.grow_stage(h->hctl->u[1].stage_top + 1024);
+                if (h->wA.grow_stage(h->hctl->u[0].stage_top + 1024)) h->epoch++;
+                if (h->wB.grow_stage(h->hctl->u[1].stage_top + 1024)) h->epoch++;
                 CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
-                run_stages(h, 0, DSPG_NSTAGES, s, false);
+                pipeline(h, s, false, false);
                 read_ctl(h, s);
                 continue;
             }
+            const bool side_on = h->has_at && nA > 0;
             if (st & ST_AB_ARENA) {
                 regrow(h, h->A, s);
                 if (!h->b_is_a && nB > 0) regrow(h, h->B, s);
@@ -776,23 +916,31 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
                 reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
                 reset_c_counters(h, s);
                 reset_range(h, &h->ctl->status, sizeof(unsigned), s);
-                run_stages(h, DSPG_STAGE_COMMIT, DSPG_NSTAGES, s, false);
+                stage_commit_ab(h, s);
+                if (side_on) {
+                    transpose_front(h, s);
+                    transpose_commit(h, s);
+                }
+                stage_size(h, s);
+                stage_numeric(h, s);
                 read_ctl(h, s);
                 continue;
             }
-            const bool at = st & (ST_AT_STAGE | ST_AT_ARENA);
+            const bool at = side_on && (st & (ST_AT_STAGE | ST_AT_ARENA));
             const bool cc = st & ST_C_ARENA;
-            if (st & ST_AT_STAGE) h->wAT.grow_stage(h->hctl->u[2].stage_top + 1024);
+            if ((st & ST_AT_STAGE) && h->wAT.grow_stage(h->hctl->u[2].stage_top + 1024)) h->epoch++;
             if (st & ST_AT_ARENA) regrow(h, h->AT, s);
             if (st & ST_C_ARENA) regrow(h, h->C, s);
             reset_range(h, &h->ctl->status, sizeof(unsigned), s);
             if (at) {
                 reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
-                run_stages(h, DSPG_STAGE_TRANSPOSE, DSPG_STAGE_TRANSPOSE + 1, s, false);
+                transpose_front(h, s);
+                transpose_commit(h, s);
             }
             if (cc) {
                 reset_c_counters(h, s);
-                run_stages(h, DSPG_STAGE_SIZE, DSPG_NSTAGES, s, false);
+                stage_size(h, s);
+                stage_numeric(h, s);
             }
             read_ctl(h, s);
         }
@@ -922,8 +1070,8 @@ dspg_status dspg_info(dspg_handle *h, int64_t *n, int64_t *k, int64_t *m, int64_
 dspg_status dspg_set_profiling(dspg_handle *h, int on) {
     if (!h) return DSPG_ERR_INVALID;
     try {
-        if (on && !h->ev[0])
-            for (int k = 0; k <= DSPG_NSTAGES; k++) CK(cudaEventCreate(&h->ev[k]));
+        if (on && !h->pev[0])
+            for (int k = 0; k < 10; k++) CK(cudaEventCreate(&h->pev[k]));
         h->prof = on != 0;
         return DSPG_OK;
     } catch (const Err &e) {
@@ -942,8 +1090,13 @@ unsigned long long dspg_kernel_launches(void) { return __atomic_load_n(&launch_c
 void dspg_destroy(dspg_handle *h) {
     if (!h) return;
     cudaDeviceSynchronize();
-    for (int k = 0; k <= DSPG_NSTAGES; k++)
-        if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    for (int k = 0; k < 10; k++)
+        if (h->pev[k]) cudaEventDestroy(h->pev[k]);
+    for (cudaEvent_t e : {h->evIn, h->evFork, h->evDetect, h->evSide, h->evSize, h->evNum[0], h->evNum[1], h->evNum[2]})
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t st : {h->gs, h->side, h->nstr[0], h->nstr[1], h->nstr[2]})
+        if (st) cudaStreamDestroy(st);
     if (h->ctl) cudaFree(h->ctl);
     if (h->hctl) cudaFreeHost(h->hctl);
     delete h;

@@ -96,7 +96,7 @@ constexpr int64_t DENSE_M_MAX = 1024;  // C columns up to this use dense accumul
 void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const CJob &J, int64_t max_rows, Ctl *ctl,
                    unsigned mask, cudaStream_t s, int num_sms);
 void run_numeric(int sr, const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,
-                 cudaStream_t s, int num_sms);
+                 const cudaStream_t *ss, int ns, int num_sms);
 void init_dense_scratch(int sr, void *acc, uint32_t *mask, int64_t entries, int64_t words, cudaStream_t s);
 
 // layout.cu: building and reading slack-CSRs

@@ -62,16 +62,16 @@ __device__ __forceinline__ void write_sorted(SortOut out, int64_t s, uint64_t ke
 // an entry is dead when a word with the same key and a later index exists.
 // A single tile finishes (de-duplicates and gathers) in the sort kernel.
 
-constexpr int TS_NT = 1024;
+constexpr int TS_NT = 512;
 constexpr int TS_NW = TS_NT / 32;
-constexpr int TS_TILE = 4096;
+constexpr int TS_TILE = 2048;
 constexpr int TS_ROUNDS = TS_TILE / TS_NT;  // 32-entry rounds per warp segment
-constexpr int TS_MAXT = 8;
+constexpr int TS_MAXT = 16;
 constexpr size_t TS_SMEM = 2 * TS_TILE * sizeof(uint64_t) + TS_NW * 256 * sizeof(uint32_t) + 256 * sizeof(uint32_t);
 
 int64_t sort_small_max() { return (int64_t)TS_TILE * TS_MAXT; }
 
-__global__ void __launch_bounds__(TS_NT, 1)
+__global__ void __launch_bounds__(TS_NT)
 k_tile_sort(const int32_t *row, const int32_t *col, const void *val, const uint8_t *op, int n, int64_t nrows,
             int64_t ncols, int sr, bool check_values, SortOut out, Ctl *ctl, unsigned skip_mask, int cb, int ib,
             int kb, uint64_t *words_out) {
@@ -118,14 +118,14 @@ k_tile_sort(const int32_t *row, const int32_t *col, const void *val, const uint8
             __syncwarp();
         }
         __syncthreads();
-        if (tid < 256) {
+        for (int d = tid; d < 256; d += TS_NT) {
             uint32_t acc = 0;
             for (int ww = 0; ww < TS_NW; ww++) {
-                const uint32_t c = wc[ww * 256 + tid];
-                wc[ww * 256 + tid] = acc;
+                const uint32_t c = wc[ww * 256 + d];
+                wc[ww * 256 + d] = acc;
                 acc += c;
             }
-            dbase[tid] = acc;
+            dbase[d] = acc;
         }
         __syncthreads();
         if (tid < 32) {  // exclusive scan of the 256 digit totals by one warp

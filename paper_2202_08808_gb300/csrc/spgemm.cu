@@ -746,10 +746,15 @@ static void launch_cta_hash(const MatView &A, const MatView &B, const MatView &C
     launch_k(k_num_cta_hash<SR, LOG_TS>, num_sms * per_sm, 256, smem, s, A, B, C, J, ctl, mask, bin);
 }
 
+// The bin kernels are independent; they are spread over the given streams
+// (which the caller has ordered after the sizing pass) so that empty bins
+// cost no time on the critical path.
 template <int SR>
 static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,
-                          cudaStream_t s, int num_sms) {
+                          const cudaStream_t *ss, int ns, int num_sms) {
     using T = typename Sr<SR>::T;
+    int k = 0;
+    auto next = [&]() { return ss[(k++) % ns]; };
     if (J.dense_mode) {
         const int mp = (int)((J.m + 31) / 32 * 32);
         constexpr int NW = 8;
@@ -759,26 +764,27 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
             cudaFuncSetAttribute(k_num_warp_dense<SR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
             set_w = true;
         }
-        launch_k(k_num_warp_dense<SR, NW>, num_sms * 4, NW * 32, smem_w, s, A, B, C, J, ctl, mask, (int)BIN_WDENSE, mp);
+        launch_k(k_num_warp_dense<SR, NW>, num_sms * 4, NW * 32, smem_w, next(), A, B, C, J, ctl, mask,
+                 (int)BIN_WDENSE, mp);
         const size_t smem_c = (size_t)mp * sizeof(T) + 32 * sizeof(uint32_t);
-        launch_k(k_num_cta_dense<SR>, num_sms, 512, smem_c, s, A, B, C, J, ctl, mask, (int)BIN_CDENSE, mp);
+        launch_k(k_num_cta_dense<SR>, num_sms, 512, smem_c, next(), A, B, C, J, ctl, mask, (int)BIN_CDENSE, mp);
         return;
     }
-    launch_group_hash<SR, 6, 8, 8>(A, B, C, J, ctl, mask, BIN_G8, s, num_sms);
-    launch_group_hash<SR, 7, 16, 8>(A, B, C, J, ctl, mask, BIN_G16, s, num_sms);
-    launch_group_hash<SR, 8, 32, 8>(A, B, C, J, ctl, mask, BIN_W256, s, num_sms);
-    launch_group_hash<SR, 9, 32, 4>(A, B, C, J, ctl, mask, BIN_W512, s, num_sms);
-    launch_group_hash<SR, 10, 32, 4>(A, B, C, J, ctl, mask, BIN_W1024, s, num_sms);
-    launch_cta_hash<SR, 11>(A, B, C, J, ctl, mask, BIN_C2048, s, num_sms);
-    launch_cta_hash<SR, 12>(A, B, C, J, ctl, mask, BIN_C4096, s, num_sms);
-    launch_cta_hash<SR, 13>(A, B, C, J, ctl, mask, BIN_C8192, s, num_sms);
-    launch_k(k_num_gdense<SR>, J.gd_ctas, 512, 0, s, A, B, C, J, ctl, mask, (int)BIN_GD);
+    launch_group_hash<SR, 7, 16, 8>(A, B, C, J, ctl, mask, BIN_G16, next(), num_sms);
+    launch_group_hash<SR, 6, 8, 8>(A, B, C, J, ctl, mask, BIN_G8, next(), num_sms);
+    launch_group_hash<SR, 8, 32, 8>(A, B, C, J, ctl, mask, BIN_W256, next(), num_sms);
+    launch_group_hash<SR, 9, 32, 4>(A, B, C, J, ctl, mask, BIN_W512, next(), num_sms);
+    launch_group_hash<SR, 10, 32, 4>(A, B, C, J, ctl, mask, BIN_W1024, next(), num_sms);
+    launch_cta_hash<SR, 11>(A, B, C, J, ctl, mask, BIN_C2048, next(), num_sms);
+    launch_cta_hash<SR, 12>(A, B, C, J, ctl, mask, BIN_C4096, next(), num_sms);
+    launch_cta_hash<SR, 13>(A, B, C, J, ctl, mask, BIN_C8192, next(), num_sms);
+    launch_k(k_num_gdense<SR>, J.gd_ctas, 512, 0, next(), A, B, C, J, ctl, mask, (int)BIN_GD);
 }
 
 void run_numeric(int sr, const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,
-                 cudaStream_t s, int num_sms) {
-    if (sr == SR_PT) run_numeric_t<SR_PT>(A, B, C, J, ctl, mask, s, num_sms);
-    else run_numeric_t<SR_MP>(A, B, C, J, ctl, mask, s, num_sms);
+                 const cudaStream_t *ss, int ns, int num_sms) {
+    if (sr == SR_PT) run_numeric_t<SR_PT>(A, B, C, J, ctl, mask, ss, ns, num_sms);
+    else run_numeric_t<SR_MP>(A, B, C, J, ctl, mask, ss, ns, num_sms);
 }
 
 }  // namespace dspg

@@ -290,3 +290,36 @@ def test_config3_rmat_minplus_full_size(dspg):
         assert np.array_equal(R, np.unique(b.row)), "R = rows of the A batch when B does not change"
         _sampled_rows(g, Ao, Bo, R, f"rmat batch {k} R")
         _sampled_rows(g, Ao, Bo, np.sort(rng.choice(A.nrows, 2000, replace=False)), f"rmat batch {k} sample")
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_repeated_shape_captured_pipeline(dspg, sr):
+    """Equal-size batches: the first runs eagerly, the second is captured as a
+    CUDA graph, later ones replay it; every result must match the oracle."""
+    n = 2000
+    A = random_csr(n, n, 10, 77, sr)
+    g = dspg.DynamicSpGEMM(A)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    for k in range(5):
+        b = random_batch(n, n, 700, 500 + k, sr, A=Ao.to_csr(), dup_frac=0.2)
+        _apply_both(g, Ao, Co, b)
+        _check_state(g, Ao, None, f"replay {k}")
+
+
+def test_graph_and_eager_agree_minplus(dspg):
+    """Same batches through captured graphs and through the eager path
+    (profiling on) give bit-identical (min,+) results."""
+    n = 1500
+    A = random_csr(n, n, 9, 88, MIN_PLUS_I32)
+    g1 = dspg.DynamicSpGEMM(A)
+    g2 = dspg.DynamicSpGEMM(A)
+    g2.set_profiling(True)
+    for k in range(4):
+        b = random_batch(n, n, 400, 900 + k, MIN_PLUS_I32, A=A)
+        g1.apply_batch(b)
+        g2.apply_batch(b)
+        assert g2.stage_times()["numeric"] >= 0.0
+    c1, c2 = g1.read_C(), g2.read_C()
+    assert np.array_equal(c1.rowptr, c2.rowptr) and np.array_equal(c1.col, c2.col)
+    assert np.array_equal(c1.val, c2.val)
