@@ -52,7 +52,7 @@ struct UpdCtl {
     long long pad[5];
 };
 
-constexpr int NBINS = 12;
+constexpr int NBINS = 16;
 
 struct Ctl {
     unsigned status;

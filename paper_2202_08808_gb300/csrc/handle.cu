@@ -224,6 +224,7 @@ struct dspg_handle {
         uint64_t epoch;
         bool prof;
         cudaGraphExec_t exec;
+        unsigned long long kernels;  // kernel nodes, added to the launch counter per replay
     };
     std::vector<Graph> graphs;
     std::vector<Graph> seen;  // keys run once eagerly (exec unused)
@@ -383,6 +384,7 @@ CJob c_job(dspg_handle *h, const int32_t *R, bool static_mode) {
     J.static_mode = static_mode ? 1 : 0;
     J.slack_min = h->opt.slack_min;
     J.slack_div = h->opt.slack_div;
+    J.bmR = w.bmR.p;
     return J;
 }
 
@@ -527,8 +529,6 @@ void stage_detect(dspg_handle *h, cudaStream_t s) {
     }
     const bool any_cols = use_at && (h->b_is_a ? h->inA.n > 0 : h->inB.n > 0);
     if (any_cols) run_detect_cols(h->AT.view(), D, h->ctl, M_AB, s, h->num_sms);
-    run_clear_marks(w.bmR.p, w.R.p, &h->ctl->n_affected, w.nrows, s);
-    if (any_cols) run_clear_marks(w.bmK.p, w.K.p, &h->ctl->n_K, w.nrows_b, s);
 }
 
 void stage_merge(dspg_handle *h, cudaStream_t s) {
@@ -667,6 +667,7 @@ void run_first(dspg_handle *h, cudaStream_t s) {
                 CK(cudaEventRecord(h->evIn, s));
                 CK(cudaStreamWaitEvent(h->gs, h->evIn, 0));
                 CK(cudaGraphLaunch(g.exec, h->gs));
+                __atomic_fetch_add(&launch_counter(), g.kernels, __ATOMIC_RELAXED);
                 CK(cudaEventRecord(h->evIn, h->gs));
                 CK(cudaStreamWaitEvent(s, h->evIn, 0));
                 CK(cudaStreamSynchronize(h->gs));
@@ -679,6 +680,7 @@ void run_first(dspg_handle *h, cudaStream_t s) {
             cudaGraph_t graph = nullptr;
             CK(cudaEventRecord(h->evIn, s));
             CK(cudaStreamWaitEvent(h->gs, h->evIn, 0));
+            const unsigned long long k0 = launch_counter();
             CK(cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeThreadLocal));
             cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->gs);
             pipeline(h, h->gs, h->prof, true);
@@ -692,7 +694,8 @@ void run_first(dspg_handle *h, cudaStream_t s) {
                 cudaGraphExecDestroy(h->graphs.front().exec);
                 h->graphs.erase(h->graphs.begin());
             }
-            h->graphs.push_back(dspg_handle::Graph{nA, nB, h->epoch, h->prof, exec});
+            const unsigned long long nk = launch_counter() - k0;
+            h->graphs.push_back(dspg_handle::Graph{nA, nB, h->epoch, h->prof, exec, nk});
             CK(cudaGraphLaunch(exec, h->gs));
             CK(cudaEventRecord(h->evIn, h->gs));
             CK(cudaStreamWaitEvent(s, h->evIn, 0));
@@ -700,7 +703,7 @@ void run_first(dspg_handle *h, cudaStream_t s) {
             return;
         }
         if (h->seen.size() >= 16) h->seen.erase(h->seen.begin());
-        h->seen.push_back(dspg_handle::Graph{nA, nB, h->epoch, h->prof, nullptr});
+        h->seen.push_back(dspg_handle::Graph{nA, nB, h->epoch, h->prof, nullptr, 0});
     }
     CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
     pipeline(h, s, h->prof, false);

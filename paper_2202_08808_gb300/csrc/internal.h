@@ -75,6 +75,7 @@ struct CJob {
     int dense_mode;           // 1: all rows use the dense small-m kernels
     int static_mode;          // 1: C is laid out afresh by the sizing pass
     int slack_min, slack_div;
+    uint32_t *bmR;            // affected-row bitmap, cleared by the sizing pass (dynamic mode)
 };
 
 // update.cu
@@ -87,7 +88,6 @@ void run_commit(const CommitJob &J, const MatView &M, int vsize, int64_t max_ite
 void run_detect_entries(const int32_t *srow, const uint8_t *kind, int64_t n, bool mark_rows, bool mark_cols,
                         const DetectBufs &D, Ctl *ctl, unsigned mask, cudaStream_t s);
 void run_detect_cols(const MatView &AT, const DetectBufs &D, Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms);
-void run_clear_marks(uint32_t *bm, const int32_t *list, const long long *cnt, int64_t max_n, cudaStream_t s);
 void run_transpose_feed(const UpdJob &J, int32_t pad_row, int32_t *trow, int32_t *tcol, uint8_t *top, Ctl *ctl,
                         unsigned mask, cudaStream_t s);
 

@@ -55,118 +55,71 @@ __device__ __forceinline__ void write_sorted(SortOut out, int64_t s, uint64_t ke
 //
 // Batches up to TS_TILE * TS_MAXT entries whose packed word
 // (key << ib | arrival index) fits 64 bits: each CTA sorts one tile of
-// TS_TILE words completely in shared memory (all digit passes), and one
-// merge kernel places every word at its global rank = its rank in its own
-// tile + the number of smaller words in each other tile (binary searches).
-// Words are distinct (they carry the index), so ranks are a permutation;
-// an entry is dead when a word with the same key and a later index exists.
-// A single tile finishes (de-duplicates and gathers) in the sort kernel.
+// TS_TILE words in shared memory with a bitonic network (the words are
+// distinct, so no stability is needed), and one merge kernel places every
+// word at its global rank = its rank in its own tile + the number of smaller
+// words in each other tile (binary searches in a shared-memory copy of all
+// tiles).  An entry is dead when a word with the same key and a later index
+// exists.  A single tile finishes (de-duplicates and gathers) in the sort
+// kernel itself.
 
-constexpr int TS_NT = 512;
-constexpr int TS_NW = TS_NT / 32;
-constexpr int TS_TILE = 2048;
-constexpr int TS_ROUNDS = TS_TILE / TS_NT;  // 32-entry rounds per warp segment
-constexpr int TS_MAXT = 16;
-constexpr size_t TS_SMEM = 2 * TS_TILE * sizeof(uint64_t) + TS_NW * 256 * sizeof(uint32_t) + 256 * sizeof(uint32_t);
+constexpr int TS_NT = 1024;
+constexpr int TS_TILE = 4096;
+constexpr int TS_MAXT = 4;
+constexpr size_t TS_SMEM = TS_TILE * sizeof(uint64_t);
+constexpr size_t TM_SMEM = (size_t)TS_TILE * TS_MAXT * sizeof(uint64_t);
 
 int64_t sort_small_max() { return (int64_t)TS_TILE * TS_MAXT; }
 
 __global__ void __launch_bounds__(TS_NT)
 k_tile_sort(const int32_t *row, const int32_t *col, const void *val, const uint8_t *op, int n, int64_t nrows,
             int64_t ncols, int sr, bool check_values, SortOut out, Ctl *ctl, unsigned skip_mask, int cb, int ib,
-            int kb, uint64_t *words_out) {
+            uint64_t *words_out) {
     extern __shared__ uint64_t sm[];
     if (failed(ctl, skip_mask)) return;
-    uint64_t *b0 = sm;
-    uint64_t *b1 = sm + TS_TILE;
-    uint32_t *wc = (uint32_t *)(sm + 2 * TS_TILE);
-    uint32_t *dbase = wc + TS_NW * 256;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int tid = threadIdx.x;
     const int lo = blockIdx.x * TS_TILE;
     const int cnt = min(TS_TILE, n - lo);
-
-    for (int i = tid; i < cnt; i += TS_NT) {
-        const int gi = lo + i;
-        const int32_t r = row[gi], c = col[gi];
-        const uint8_t o = op[gi];
-        const bool ok = entry_ok(r, c, o, val, gi, nrows, ncols, sr, check_values);
-        if (!ok) set_status(ctl, ST_INVALID);
-        const uint64_t key = ok ? (((uint64_t)(uint32_t)r << cb) | (uint32_t)c) : 0;
-        b0[i] = (key << ib) | (uint64_t)gi;
+    int N = 64;
+    while (N < cnt) N <<= 1;
+    for (int i = tid; i < N; i += TS_NT) {
+        uint64_t w = ~uint64_t(0);  // padding sorts last
+        if (i < cnt) {
+            const int gi = lo + i;
+            const int32_t r = row[gi], c = col[gi];
+            const uint8_t o = op[gi];
+            const bool ok = entry_ok(r, c, o, val, gi, nrows, ncols, sr, check_values);
+            if (!ok) set_status(ctl, ST_INVALID);
+            const uint64_t key = ok ? (((uint64_t)(uint32_t)r << cb) | (uint32_t)c) : 0;
+            w = (key << ib) | (uint64_t)gi;
+        }
+        sm[i] = w;
     }
     __syncthreads();
-
-    const int seg = (cnt + TS_NW - 1) / TS_NW;
-    const int seg_lo = w * seg;
-    const int seg_hi = min(cnt, seg_lo + seg);
-    const int passes = (kb + 7) / 8;
-    for (int p = 0; p < passes; p++) {
-        const int shift = ib + 8 * p;
-        for (int j = tid; j < TS_NW * 256; j += TS_NT) wc[j] = 0;
-        __syncthreads();
-        uint32_t lr[TS_ROUNDS];
-#pragma unroll
-        for (int r = 0; r < TS_ROUNDS; r++) {
-            const int idx = seg_lo + r * 32 + lane;
-            const bool valid = idx < seg_hi;
-            const unsigned d = valid ? (unsigned)((b0[idx] >> shift) & 255) : 0xffffffffu;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t before = valid ? wc[w * 256 + d] : 0;
-            __syncwarp();
-            lr[r] = before + __popc(peers & lanemask_lt());
-            if (valid && lane == 31 - __clz(peers)) wc[w * 256 + d] = before + __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        for (int d = tid; d < 256; d += TS_NT) {
-            uint32_t acc = 0;
-            for (int ww = 0; ww < TS_NW; ww++) {
-                const uint32_t c = wc[ww * 256 + d];
-                wc[ww * 256 + d] = acc;
-                acc += c;
+    for (int size = 2; size <= N; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int x = tid; x < N / 2; x += TS_NT) {
+                const int a = 2 * x - (x & (stride - 1));
+                const int b = a + stride;
+                const uint64_t wa = sm[a], wb = sm[b];
+                if ((wa > wb) == ((a & size) == 0)) {
+                    sm[a] = wb;
+                    sm[b] = wa;
+                }
             }
-            dbase[d] = acc;
+            __syncthreads();
         }
-        __syncthreads();
-        if (tid < 32) {  // exclusive scan of the 256 digit totals by one warp
-            uint32_t v[8], acc = 0;
-            for (int j = 0; j < 8; j++) {
-                v[j] = dbase[tid * 8 + j];
-                acc += v[j];
-            }
-            const uint32_t incl = warp_incl_scan<uint32_t>(acc);
-            uint32_t e = incl - acc;
-            for (int j = 0; j < 8; j++) {
-                dbase[tid * 8 + j] = e;
-                e += v[j];
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < TS_ROUNDS; r++) {
-            const int idx = seg_lo + r * 32 + lane;
-            if (idx < seg_hi) {
-                const uint64_t x = b0[idx];
-                const unsigned d = (unsigned)((x >> shift) & 255);
-                b1[dbase[d] + wc[w * 256 + d] + lr[r]] = x;
-            }
-        }
-        __syncthreads();
-        uint64_t *t = b0;
-        b0 = b1;
-        b1 = t;
     }
-
     if (gridDim.x == 1) {
         const uint64_t imask = (uint64_t(1) << ib) - 1;
         for (int s = tid; s < cnt; s += TS_NT) {
-            const uint64_t x = b0[s];
+            const uint64_t x = sm[s];
             const uint64_t key = x >> ib;
-            const bool dead = (s + 1 < cnt) && ((b0[s + 1] >> ib) == key);
+            const bool dead = (s + 1 < cnt) && ((sm[s + 1] >> ib) == key);
             write_sorted(out, s, key, x & imask, dead, cb, val, op, sr);
         }
     } else {
-        for (int s = tid; s < cnt; s += TS_NT) words_out[lo + s] = b0[s];
+        for (int s = tid; s < cnt; s += TS_NT) words_out[lo + s] = sm[s];
     }
 }
 
@@ -188,26 +141,30 @@ __device__ __forceinline__ int count_le(const uint64_t *a, int n, uint64_t x) {
     return lo;
 }
 
-__global__ void k_tile_merge(const uint64_t *words, int n, int ib, int cb, const void *val, const uint8_t *op, int sr,
-                             SortOut out, const Ctl *ctl, unsigned skip_mask) {
+__global__ void __launch_bounds__(1024)
+k_tile_merge(const uint64_t *words, int n, int ib, int cb, const void *val, const uint8_t *op, int sr, SortOut out,
+             const Ctl *ctl, unsigned skip_mask) {
+    extern __shared__ uint64_t sw[];
     if (failed(ctl, skip_mask)) return;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const int t = e / TS_TILE;
+    for (int x = threadIdx.x; x < n; x += blockDim.x) sw[x] = words[x];
+    __syncthreads();
     const int ntiles = (n + TS_TILE - 1) / TS_TILE;
     const uint64_t imask = (uint64_t(1) << ib) - 1;
-    const uint64_t w = words[e];
-    const uint64_t key = w >> ib;
-    int rank = e - t * TS_TILE;
-    int le = 0;  // words with a key <= key
-    for (int u = 0; u < ntiles; u++) {
-        const int ulo = u * TS_TILE;
-        const int ucnt = min(TS_TILE, n - ulo);
-        if (u != t) rank += count_less(words + ulo, ucnt, w);
-        le += count_le(words + ulo, ucnt, w | imask);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int t = e / TS_TILE;
+        const uint64_t w = sw[e];
+        const uint64_t key = w >> ib;
+        int rank = e - t * TS_TILE;
+        int le = 0;  // words with a key <= key
+        for (int u = 0; u < ntiles; u++) {
+            const int ulo = u * TS_TILE;
+            const int ucnt = min(TS_TILE, n - ulo);
+            if (u != t) rank += count_less(sw + ulo, ucnt, w);
+            le += count_le(sw + ulo, ucnt, w | imask);
+        }
+        const bool dead = rank != le - 1;
+        write_sorted(out, rank, key, w & imask, dead, cb, val, op, sr);
     }
-    const bool dead = rank != le - 1;
-    write_sorted(out, rank, key, w & imask, dead, cb, val, op, sr);
 }
 
 // ------------------------------------------------------- multi-CTA path
@@ -335,14 +292,15 @@ void sort_updates(const int32_t *row, const int32_t *col, const void *val, const
         static bool attr_set = false;
         if (!attr_set) {
             cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS_SMEM);
+            cudaFuncSetAttribute(k_tile_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TM_SMEM);
             attr_set = true;
         }
         const int tiles = (int)((n + TS_TILE - 1) / TS_TILE);
         launch_k(k_tile_sort, tiles, TS_NT, TS_SMEM, s, row, col, val, op, (int)n, nrows, ncols, sr, check_values, out,
-                 ctl, skip_mask, cb, ib, kb, tmp.k0);
+                 ctl, skip_mask, cb, ib, tmp.k0);
         if (tiles > 1)
-            launch_k(k_tile_merge, (unsigned)((n + 255) / 256), 256, 0, s, (const uint64_t *)tmp.k0, (int)n, ib, cb, val,
-                     op, sr, out, (const Ctl *)ctl, skip_mask);
+            launch_k(k_tile_merge, (unsigned)((n + 1023) / 1024), 1024, (size_t)n * sizeof(uint64_t), s,
+                     (const uint64_t *)tmp.k0, (int)n, ib, cb, val, op, sr, out, (const Ctl *)ctl, skip_mask);
         return;
     }
     unsigned nblk = (unsigned)((n + 255) / 256);

@@ -48,7 +48,7 @@ struct Sr<SR_MP> {
 };
 
 enum {
-    BIN_G8 = 0, BIN_G16, BIN_W256, BIN_W512, BIN_W1024,
+    BIN_G8 = 0, BIN_G16, BIN_W128, BIN_W256, BIN_W512, BIN_W1024,
     BIN_C2048, BIN_C4096, BIN_C8192,
     BIN_GD,
     BIN_WDENSE, BIN_CDENSE,
@@ -64,14 +64,17 @@ __device__ __forceinline__ long long atomic_add_ll2(long long *p, long long v) {
 
 __device__ __forceinline__ int pick_bin(long long ubc, int dense_mode) {
     if (dense_mode) return ubc <= 4096 ? BIN_WDENSE : BIN_CDENSE;
+    // a row's distinct columns never exceed its bound, so a table of the
+    // next power of two at or above the bound cannot overflow
     if (ubc <= 32) return BIN_G8;
     if (ubc <= 64) return BIN_G16;
-    if (ubc <= 128) return BIN_W256;
-    if (ubc <= 256) return BIN_W512;
-    if (ubc <= 512) return BIN_W1024;
-    if (ubc <= 1024) return BIN_C2048;
-    if (ubc <= 2048) return BIN_C4096;
-    if (ubc <= 4096) return BIN_C8192;
+    if (ubc <= 128) return BIN_W128;
+    if (ubc <= 256) return BIN_W256;
+    if (ubc <= 512) return BIN_W512;
+    if (ubc <= 1024) return BIN_W1024;
+    if (ubc <= 2048) return BIN_C2048;
+    if (ubc <= 4096) return BIN_C4096;
+    if (ubc <= 8192) return BIN_C8192;
     return BIN_GD;
 }
 
@@ -117,8 +120,9 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
                 C.len[i] = 0;
                 if (d + c > C.arena_cap) set_status(ctl, ST_C_ARENA);
             }
-        } else if (valid && ub == 0) {
-            C.len[i] = 0;  // no products: the row becomes empty
+        } else if (valid) {
+            J.bmR[i >> 5] = 0u;  // the detection marks are not needed any more
+            if (ub == 0) C.len[i] = 0;  // no products: the row becomes empty
         }
         const int b = (valid && ub > 0) ? pick_bin(ubc, J.dense_mode) : -1;
         const unsigned peers = __match_any_sync(0xffffffffu, b);
@@ -315,7 +319,7 @@ __global__ void __launch_bounds__(NW * 32)
 k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
-    constexpr int HC = TS / 2;  // compacted list capacity
+    constexpr int HC = TS;  // compacted list capacity
     constexpr int GPW = 32 / G;
     constexpr int NG = NW * GPW;  // groups per block
     extern __shared__ __align__(16) unsigned char smem[];
@@ -358,7 +362,7 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
             }
             n += __popc(bal);
         }
-        if (n > HC) n = HC;  // unreachable when ub <= HC
+        if (n > HC) n = HC;  // unreachable: distinct columns <= ub <= TS
         __syncwarp(gmask);
         int64_t dest = 0;
         if (gl == 0) dest = c_row_dest(C, J, ctl, i, n);
@@ -375,7 +379,7 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
                 }
             }
         } else {
-            int N = 128;
+            int N = 128;  // n > 64 here
             while (N < n) N <<= 1;
             for (int s = n + gl; s < N; s += G) ck[s] = 0x7fffffff;
             __syncwarp(gmask);
@@ -408,7 +412,7 @@ __global__ void __launch_bounds__(256)
 k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
-    constexpr int HC = TS / 2;
+    constexpr int HC = TS;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t p_boff[256];
     __shared__ T p_av[256];
@@ -716,7 +720,7 @@ static void launch_group_hash(const MatView &A, const MatView &B, const MatView 
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
     constexpr int NG = NW * (32 / G);
-    const size_t smem = (size_t)NG * (TS + TS / 2) * (sizeof(T) + sizeof(int32_t));
+    const size_t smem = (size_t)NG * (2 * TS) * (sizeof(T) + sizeof(int32_t));
     static bool set = false;
     if (!set) {
         cudaFuncSetAttribute(k_num_group_hash<SR, LOG_TS, G, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -734,7 +738,7 @@ static void launch_cta_hash(const MatView &A, const MatView &B, const MatView &C
                             unsigned mask, int bin, cudaStream_t s, int num_sms) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
-    const size_t smem = (size_t)(TS + TS / 2) * (sizeof(T) + sizeof(int32_t));
+    const size_t smem = (size_t)(2 * TS) * (sizeof(T) + sizeof(int32_t));
     static bool set = false;
     if (!set) {
         cudaFuncSetAttribute(k_num_cta_hash<SR, LOG_TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -770,8 +774,9 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
         launch_k(k_num_cta_dense<SR>, num_sms, 512, smem_c, next(), A, B, C, J, ctl, mask, (int)BIN_CDENSE, mp);
         return;
     }
-    launch_group_hash<SR, 7, 16, 8>(A, B, C, J, ctl, mask, BIN_G16, next(), num_sms);
-    launch_group_hash<SR, 6, 8, 8>(A, B, C, J, ctl, mask, BIN_G8, next(), num_sms);
+    launch_group_hash<SR, 6, 16, 8>(A, B, C, J, ctl, mask, BIN_G16, next(), num_sms);
+    launch_group_hash<SR, 5, 8, 8>(A, B, C, J, ctl, mask, BIN_G8, next(), num_sms);
+    launch_group_hash<SR, 7, 32, 8>(A, B, C, J, ctl, mask, BIN_W128, next(), num_sms);
     launch_group_hash<SR, 8, 32, 8>(A, B, C, J, ctl, mask, BIN_W256, next(), num_sms);
     launch_group_hash<SR, 9, 32, 4>(A, B, C, J, ctl, mask, BIN_W512, next(), num_sms);
     launch_group_hash<SR, 10, 32, 4>(A, B, C, J, ctl, mask, BIN_W1024, next(), num_sms);

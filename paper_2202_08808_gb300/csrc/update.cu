@@ -360,6 +360,7 @@ __global__ void k_detect_cols(MatView AT, DetectBufs D, Ctl *ctl, unsigned mask)
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long x = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < nk; x += nwarps) {
         const int32_t k = D.K[x];
+        if (lane == 0) D.bmK[k >> 5] = 0u;  // marks of B* rows are not needed any more
         const int64_t base = AT.off[k];
         const int L = AT.len[k];
         for (int p0 = 0; p0 < L; p0 += 32) {
@@ -367,12 +368,6 @@ __global__ void k_detect_cols(MatView AT, DetectBufs D, Ctl *ctl, unsigned mask)
             mark_warp(D.bmR, p < L, p < L ? AT.col[base + p] : 0, D.R, &ctl->n_affected);
         }
     }
-}
-
-__global__ void k_clear_marks(uint32_t *bm, const int32_t *list, const long long *cnt) {
-    const long long n = *cnt;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-        bm[list[t] >> 5] = 0u;
 }
 
 // Structural changes of A, forwarded to its transposed pattern: INS (i,k)
@@ -442,11 +437,6 @@ void run_detect_entries(const int32_t *srow, const uint8_t *kind, int64_t n, boo
 
 void run_detect_cols(const MatView &AT, const DetectBufs &D, Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms) {
     launch_k(k_detect_cols, num_sms * 4, 256, 0, s, AT, D, ctl, mask);
-}
-
-void run_clear_marks(uint32_t *bm, const int32_t *list, const long long *cnt, int64_t max_n, cudaStream_t s) {
-    if (max_n <= 0) return;
-    launch_k(k_clear_marks, grid_for(max_n, 256), 256, 0, s, bm, list, cnt);
 }
 
 void run_transpose_feed(const UpdJob &J, int32_t pad_row, int32_t *trow, int32_t *tcol, uint8_t *top, Ctl *ctl,
