@@ -32,11 +32,14 @@ namespace dspg {
 
 template <int SR>
 struct Sr;
+// mul and add round each operation separately (no fused multiply-add), so a
+// row folded in ascending k gives exactly the textbook result.
 template <>
 struct Sr<SR_PT> {
     using T = double;
     __device__ static T zero() { return 0.0; }
-    __device__ static T mul(T a, T b) { return a * b; }
+    __device__ static T mul(T a, T b) { return __dmul_rn(a, b); }
+    __device__ static T add(T a, T b) { return __dadd_rn(a, b); }
     __device__ static void acc(T *p, T v) { atomicAdd(p, v); }
 };
 template <>
@@ -44,11 +47,12 @@ struct Sr<SR_MP> {
     using T = int32_t;
     __device__ static T zero() { return MP_INF; }
     __device__ static T mul(T a, T b) { return a + b; }
+    __device__ static T add(T a, T b) { return a < b ? a : b; }
     __device__ static void acc(T *p, T v) { atomicMin(p, v); }
 };
 
 enum {
-    BIN_G8 = 0, BIN_G16, BIN_W128, BIN_W256, BIN_W512, BIN_W1024,
+    BIN_T8 = 0, BIN_G8, BIN_G16, BIN_W128, BIN_W256, BIN_W512, BIN_W1024,
     BIN_C2048, BIN_C4096, BIN_C8192,
     BIN_GD,
     BIN_WDENSE, BIN_CDENSE,
@@ -62,7 +66,11 @@ __device__ __forceinline__ long long atomic_add_ll2(long long *p, long long v) {
 
 // ------------------------------------------------------------- sizing
 
-__device__ __forceinline__ int pick_bin(long long ubc, int dense_mode) {
+constexpr int MERGE_K = 8;      // A rows up to this length can be merged by one thread
+constexpr int MERGE_UB = 128;   // ... when their product bound is at most this
+
+__device__ __forceinline__ int pick_bin(long long ubc, int alen, int dense_mode) {
+    if (alen <= MERGE_K && ubc <= MERGE_UB) return BIN_T8;
     if (dense_mode) return ubc <= 4096 ? BIN_WDENSE : BIN_CDENSE;
     // a row's distinct columns never exceed its bound, so a table of the
     // next power of two at or above the bound cannot overflow
@@ -124,7 +132,7 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
             J.bmR[i >> 5] = 0u;  // the detection marks are not needed any more
             if (ub == 0) C.len[i] = 0;  // no products: the row becomes empty
         }
-        const int b = (valid && ub > 0) ? pick_bin(ubc, J.dense_mode) : -1;
+        const int b = (valid && ub > 0) ? pick_bin(ubc, alen, J.dense_mode) : -1;
         const unsigned peers = __match_any_sync(0xffffffffu, b);
         const int leader = __ffs(peers) - 1;
         long long bb = 0;
@@ -309,6 +317,102 @@ __device__ __forceinline__ void bitonic_step(int32_t *k, T *v, int i, int l, boo
         v[i] = v[l];
         v[l] = t;
     }
+}
+
+// ---------------------------------------------------- thread merge kernel
+
+// One thread per row with at most K A entries: the K sorted B rows are
+// merged like sorted lists (a cursor each); every output column comes out in
+// ascending order with its products folded in ascending k, so no table and
+// no sort are needed.  Writes go to the row's place while they fit its
+// capacity; a row that outgrows it is counted to the end, moved to the
+// arena tail and merged again (rare).
+template <int SR, int K>
+__device__ __forceinline__ int merge_row(const MatView &B, const typename Sr<SR>::T *av, const int32_t *ak, int alen,
+                                         int32_t *out_col, typename Sr<SR>::T *out_val, int limit) {
+    using T = typename Sr<SR>::T;
+    const T *Bv = (const T *)B.val;
+    int64_t pos[K], end[K];
+    int32_t head[K];
+#pragma unroll
+    for (int s = 0; s < K; s++) {
+        pos[s] = 0;
+        end[s] = 0;
+        head[s] = 0x7fffffff;
+        if (s < alen) {
+            const int32_t k = ak[s];
+            pos[s] = B.off[k];
+            end[s] = pos[s] + B.len[k];
+            if (pos[s] < end[s]) head[s] = B.col[pos[s]];
+        }
+    }
+    int n = 0;
+    while (true) {
+        int32_t j = head[0];
+#pragma unroll
+        for (int s = 1; s < K; s++) j = min(j, head[s]);
+        if (j == 0x7fffffff) break;
+        T acc = Sr<SR>::zero();
+        bool first = true;
+#pragma unroll
+        for (int s = 0; s < K; s++) {
+            if (head[s] == j) {
+                const T v = Sr<SR>::mul(av[s], Bv[pos[s]]);
+                acc = first ? v : Sr<SR>::add(acc, v);
+                first = false;
+                pos[s]++;
+                head[s] = pos[s] < end[s] ? B.col[pos[s]] : 0x7fffffff;
+            }
+        }
+        if (n < limit) {
+            out_col[n] = j;
+            out_val[n] = acc;
+        }
+        n++;
+    }
+    return n;
+}
+
+template <int SR, int K>
+__global__ void __launch_bounds__(256)
+k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
+    using T = typename Sr<SR>::T;
+    if (failed(ctl, mask)) return;
+    const T *Av = (const T *)A.val;
+    T *Cv = (T *)C.val;
+    long long nnz_acc = 0;
+    const long long cnt = ctl->bin_count[bin];
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < cnt;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int t = J.bins[(int64_t)bin * J.bin_cap + it];
+        const int32_t i = J.R[t];
+        const int64_t aoff = A.off[i];
+        const int alen = A.len[i];
+        T av[K];
+        int32_t ak[K];
+#pragma unroll
+        for (int s = 0; s < K; s++) {
+            av[s] = T(0);
+            ak[s] = 0;
+            if (s < alen) {
+                av[s] = Av[aoff + s];
+                ak[s] = A.col[aoff + s];
+            }
+        }
+        const int64_t off = C.off[i];
+        const int cap = J.static_mode ? 0x7fffffff : C.cap[i];
+        int n = merge_row<SR, K>(B, av, ak, alen, C.col + off, Cv + off, cap);
+        bool ok = true;
+        if (n > cap) {
+            const int64_t d = c_row_dest(C, J, ctl, i, n);
+            if (d >= 0) merge_row<SR, K>(B, av, ak, alen, C.col + d, Cv + d, n);
+            else ok = false;
+        }
+        if (ok) C.len[i] = n;
+        nnz_acc += n;
+    }
+    nnz_acc = warp_sum<long long>(nnz_acc);
+    if ((threadIdx.x & 31) == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
 }
 
 // ---------------------------------------------------- group hash kernel
@@ -759,6 +863,7 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
     using T = typename Sr<SR>::T;
     int k = 0;
     auto next = [&]() { return ss[(k++) % ns]; };
+    launch_k(k_num_thread_merge<SR, MERGE_K>, num_sms * 8, 256, 0, next(), A, B, C, J, ctl, mask, (int)BIN_T8);
     if (J.dense_mode) {
         const int mp = (int)((J.m + 31) / 32 * 32);
         constexpr int NW = 8;
