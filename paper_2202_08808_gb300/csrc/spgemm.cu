@@ -26,6 +26,8 @@
 // (+,.) accumulates with double atomics (the summation order varies; the
 // library's tolerance covers any order), (min,+) with atomicMin
 // (order-free, bit-exact).
+#include <algorithm>
+
 #include "internal.h"
 
 namespace dspg {
@@ -67,7 +69,7 @@ __device__ __forceinline__ long long atomic_add_ll2(long long *p, long long v) {
 // ------------------------------------------------------------- sizing
 
 constexpr int MERGE_K = 8;      // A rows up to this length can be merged by one thread
-constexpr int MERGE_UB = 128;   // ... when their product bound is at most this
+constexpr int MERGE_UB = 64;    // ... when their product bound is at most this
 
 __device__ __forceinline__ int pick_bin(long long ubc, int alen, int dense_mode) {
     if (alen <= MERGE_K && ubc <= MERGE_UB) return BIN_T8;
@@ -321,30 +323,29 @@ __device__ __forceinline__ void bitonic_step(int32_t *k, T *v, int i, int l, boo
 
 // ---------------------------------------------------- thread merge kernel
 
-// One thread per row with at most K A entries: the K sorted B rows are
-// merged like sorted lists (a cursor each); every output column comes out in
-// ascending order with its products folded in ascending k, so no table and
-// no sort are needed.  Writes go to the row's place while they fit its
-// capacity; a row that outgrows it is counted to the end, moved to the
-// arena tail and merged again (rare).
+// One thread per row with at most MERGE_K A entries and at most MERGE_UB
+// products: the row's B entries are first copied to shared memory with
+// independent loads (all in flight together), then the MERGE_K sorted B rows
+// are merged like sorted lists, a cursor each; every output column comes out
+// in ascending order with its products folded in ascending k, so no table
+// and no sort are needed.  Shared memory is laid out [entry][thread], so the
+// lanes of a warp never share a bank.  Writes go to the row's place while
+// they fit its capacity; a row that outgrows it is counted to the end, moved
+// to the arena tail and merged again (rare).
+constexpr int TM_NT = 128;  // threads per block of the merge kernel
+
 template <int SR, int K>
-__device__ __forceinline__ int merge_row(const MatView &B, const typename Sr<SR>::T *av, const int32_t *ak, int alen,
-                                         int32_t *out_col, typename Sr<SR>::T *out_val, int limit) {
+__device__ __forceinline__ int merge_rows_smem(const int32_t *scol, const typename Sr<SR>::T *sval,
+                                               const typename Sr<SR>::T *av, const int *start, const int *blen,
+                                               int alen, int32_t *out_col, typename Sr<SR>::T *out_val, int limit) {
     using T = typename Sr<SR>::T;
-    const T *Bv = (const T *)B.val;
-    int64_t pos[K], end[K];
+    int pos[K], end[K];
     int32_t head[K];
 #pragma unroll
     for (int s = 0; s < K; s++) {
-        pos[s] = 0;
-        end[s] = 0;
-        head[s] = 0x7fffffff;
-        if (s < alen) {
-            const int32_t k = ak[s];
-            pos[s] = B.off[k];
-            end[s] = pos[s] + B.len[k];
-            if (pos[s] < end[s]) head[s] = B.col[pos[s]];
-        }
+        pos[s] = start[s];
+        end[s] = start[s] + (s < alen ? blen[s] : 0);
+        head[s] = pos[s] < end[s] ? scol[pos[s] * TM_NT] : 0x7fffffff;
     }
     int n = 0;
     while (true) {
@@ -357,11 +358,11 @@ __device__ __forceinline__ int merge_row(const MatView &B, const typename Sr<SR>
 #pragma unroll
         for (int s = 0; s < K; s++) {
             if (head[s] == j) {
-                const T v = Sr<SR>::mul(av[s], Bv[pos[s]]);
+                const T v = Sr<SR>::mul(av[s], sval[pos[s] * TM_NT]);
                 acc = first ? v : Sr<SR>::add(acc, v);
                 first = false;
                 pos[s]++;
-                head[s] = pos[s] < end[s] ? B.col[pos[s]] : 0x7fffffff;
+                head[s] = pos[s] < end[s] ? scol[pos[s] * TM_NT] : 0x7fffffff;
             }
         }
         if (n < limit) {
@@ -373,39 +374,62 @@ __device__ __forceinline__ int merge_row(const MatView &B, const typename Sr<SR>
     return n;
 }
 
-template <int SR, int K>
-__global__ void __launch_bounds__(256)
+template <int SR, int K, int UB>
+__global__ void __launch_bounds__(TM_NT)
 k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
     using T = typename Sr<SR>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
     if (failed(ctl, mask)) return;
+    T *svals = (T *)smem + threadIdx.x;
+    int32_t *scols = (int32_t *)((T *)smem + (size_t)UB * TM_NT) + threadIdx.x;
     const T *Av = (const T *)A.val;
+    const T *Bv = (const T *)B.val;
     T *Cv = (T *)C.val;
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < cnt;
-         it += (long long)gridDim.x * blockDim.x) {
+    for (long long it = (long long)blockIdx.x * TM_NT + threadIdx.x; it < cnt; it += (long long)gridDim.x * TM_NT) {
         const int t = J.bins[(int64_t)bin * J.bin_cap + it];
         const int32_t i = J.R[t];
         const int64_t aoff = A.off[i];
         const int alen = A.len[i];
         T av[K];
-        int32_t ak[K];
+        int64_t boff[K];
+        int blen[K], start[K];
 #pragma unroll
         for (int s = 0; s < K; s++) {
             av[s] = T(0);
-            ak[s] = 0;
+            boff[s] = 0;
+            blen[s] = 0;
             if (s < alen) {
+                const int32_t k = A.col[aoff + s];
                 av[s] = Av[aoff + s];
-                ak[s] = A.col[aoff + s];
+                boff[s] = B.off[k];
+                blen[s] = B.len[k];
             }
         }
+        int tot = 0;
+#pragma unroll
+        for (int s = 0; s < K; s++) {
+            start[s] = tot;
+            tot += blen[s];
+        }
+        if (tot > UB) {  // the sizing pass guarantees tot <= UB; guard the buffer anyway
+            set_status(ctl, ST_TIMEOUT);
+            continue;
+        }
+#pragma unroll
+        for (int s = 0; s < K; s++)
+            for (int q = 0; q < blen[s]; q++) {
+                scols[(start[s] + q) * TM_NT] = B.col[boff[s] + q];
+                svals[(start[s] + q) * TM_NT] = Bv[boff[s] + q];
+            }
         const int64_t off = C.off[i];
         const int cap = J.static_mode ? 0x7fffffff : C.cap[i];
-        int n = merge_row<SR, K>(B, av, ak, alen, C.col + off, Cv + off, cap);
+        const int n = merge_rows_smem<SR, K>(scols, svals, av, start, blen, alen, C.col + off, Cv + off, cap);
         bool ok = true;
         if (n > cap) {
             const int64_t d = c_row_dest(C, J, ctl, i, n);
-            if (d >= 0) merge_row<SR, K>(B, av, ak, alen, C.col + d, Cv + d, n);
+            if (d >= 0) merge_rows_smem<SR, K>(scols, svals, av, start, blen, alen, C.col + d, Cv + d, n);
             else ok = false;
         }
         if (ok) C.len[i] = n;
@@ -863,7 +887,18 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
     using T = typename Sr<SR>::T;
     int k = 0;
     auto next = [&]() { return ss[(k++) % ns]; };
-    launch_k(k_num_thread_merge<SR, MERGE_K>, num_sms * 8, 256, 0, next(), A, B, C, J, ctl, mask, (int)BIN_T8);
+    {
+        const size_t smem_m = (size_t)MERGE_UB * TM_NT * (sizeof(T) + sizeof(int32_t));
+        static bool set_m = false;
+        if (!set_m) {
+            cudaFuncSetAttribute(k_num_thread_merge<SR, MERGE_K, MERGE_UB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_m);
+            set_m = true;
+        }
+        const int per_sm = (int)std::max<size_t>(1, (200 * 1024) / (smem_m + 1024));
+        launch_k(k_num_thread_merge<SR, MERGE_K, MERGE_UB>, num_sms * per_sm, TM_NT, smem_m, next(), A, B, C, J, ctl,
+                 mask, (int)BIN_T8);
+    }
     if (J.dense_mode) {
         const int mp = (int)((J.m + 31) / 32 * 32);
         constexpr int NW = 8;
