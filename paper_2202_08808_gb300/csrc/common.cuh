@@ -188,6 +188,15 @@ void scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, c
 void scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
 int64_t scan_tmp_entries(int64_t n);
 
+// Where a batch's arrays are: a small device-side block the pipeline reads,
+// so that a captured pipeline can take new input pointers on every launch.
+struct InArgs {
+    const int32_t *row;
+    const int32_t *col;
+    const void *val;
+    const uint8_t *op;
+};
+
 // Sort a batch of updates by (row, col), keep the last write of each key:
 // see sort.cu.
 struct SortOut {
@@ -209,9 +218,8 @@ void sort_tmp_sizes(int64_t n, int64_t *count_entries);
 // Validate + sort + dedupe n updates of a matrix with the given shape.
 // Sets ST_INVALID in ctl on a bad entry.
 // Kernels return at entry when a bit of skip_mask is set in ctl->status.
-void sort_updates(const int32_t *row, const int32_t *col, const void *val, const uint8_t *op, int64_t n,
-                  int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out, SortTmp tmp,
-                  Ctl *ctl, unsigned skip_mask, cudaStream_t s);
+void sort_updates(const InArgs *in, int64_t n, int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out,
+                  SortTmp tmp, Ctl *ctl, unsigned skip_mask, cudaStream_t s);
 // Stable sort of (key, value) pairs by the low `bits` bits of key (multi-CTA).
 void radix_sort_pairs(uint64_t *k, uint32_t *v, uint64_t *k_alt, uint32_t *v_alt, int64_t n, int bits,
                       uint32_t *counts, int64_t *scan_tmp, int64_t *scan_out, cudaStream_t s, bool *result_in_alt);

@@ -208,6 +208,8 @@ struct dspg_handle {
     UpdWs wA, wB, wAT;
     CWs wc;
     BatchIn inA, inB;
+    InArgs *d_args = nullptr;  // device: where the A, B and forwarded batches are (read by the sorts)
+    InArgs *h_args = nullptr;  // pinned host mirror, copied in by the pipeline's first step
     int64_t last_nR = 0;
     bool prof = false;
     cudaEvent_t pev[10] = {};  // stage boundaries (profiling)
@@ -498,12 +500,13 @@ void build_transpose(dspg_handle *h, cudaStream_t s) {
 // ------------------------------------------------------------ pipeline
 
 void stage_sort(dspg_handle *h, cudaStream_t s) {
+    CK(cudaMemcpyAsync(h->d_args, h->h_args, 3 * sizeof(InArgs), cudaMemcpyHostToDevice, s));
     if (h->inA.n > 0)
-        sort_updates(h->inA.row, h->inA.col, h->inA.val, h->inA.op, h->inA.n, h->A.nrows, h->A.ncols, h->sr, true,
-                     h->wA.sort_out(), h->wA.sort_tmp(), h->ctl, 0u, s);
+        sort_updates(h->d_args + 0, h->inA.n, h->A.nrows, h->A.ncols, h->sr, true, h->wA.sort_out(), h->wA.sort_tmp(),
+                     h->ctl, 0u, s);
     if (!h->b_is_a && h->inB.n > 0)
-        sort_updates(h->inB.row, h->inB.col, h->inB.val, h->inB.op, h->inB.n, h->B.nrows, h->B.ncols, h->sr, true,
-                     h->wB.sort_out(), h->wB.sort_tmp(), h->ctl, 0u, s);
+        sort_updates(h->d_args + 1, h->inB.n, h->B.nrows, h->B.ncols, h->sr, true, h->wB.sort_out(), h->wB.sort_tmp(),
+                     h->ctl, 0u, s);
 }
 
 void stage_classify(dspg_handle *h, cudaStream_t s) {
@@ -553,8 +556,8 @@ void transpose_front(dspg_handle *h, cudaStream_t s) {
     const int64_t n = h->inA.n;
     UpdWs &w = h->wAT;
     run_transpose_feed(h->wA.job(n), (int32_t)h->AT.nrows, w.in_row.p, w.in_col.p, w.in_op.p, h->ctl, M_AB, s);
-    sort_updates(w.in_row.p, w.in_col.p, nullptr, w.in_op.p, n, h->AT.nrows + 1, h->AT.ncols, h->sr, false,
-                 w.sort_out(), w.sort_tmp(), h->ctl, M_AT, s);
+    sort_updates(h->d_args + 2, n, h->AT.nrows + 1, h->AT.ncols, h->sr, false, w.sort_out(), w.sort_tmp(), h->ctl, M_AT,
+                 s);
     UpdJob J = w.job(n);
     run_classify(J, h->AT.view(), 0, h->ctl, M_AT & ~ST_AT_STAGE, ST_AT_STAGE, s, h->num_sms);
     run_merge_copy(J, h->AT.view(), 0, h->ctl, M_AT, s, h->num_sms);
@@ -639,20 +642,28 @@ void reset_c_counters(dspg_handle *h, cudaStream_t s) {
     reset_range(h, from, sizeof(Ctl) - (size_t)(from - (char *)c), s);
 }
 
-void upload(dspg_handle *h, UpdWs &w, const dspg_updates *u, BatchIn &in, cudaStream_t s) {
+// Host batches are copied to the device; device batches are read where
+// they are.  Either way the pointers go to the argument block slot k.
+void upload(dspg_handle *h, UpdWs &w, const dspg_updates *u, BatchIn &in, int k, cudaStream_t s) {
     in.n = u ? u->n : 0;
+    h->h_args[k] = InArgs{nullptr, nullptr, nullptr, nullptr};
     if (in.n <= 0) return;
-    // the batch is always copied into library buffers, so that captured
-    // pipelines keep stable pointers
-    const cudaMemcpyKind kind = u->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(w.in_row.p, u->row, sizeof(int32_t) * in.n, kind, s));
-    CK(cudaMemcpyAsync(w.in_col.p, u->col, sizeof(int32_t) * in.n, kind, s));
-    CK(cudaMemcpyAsync(w.in_val.p, u->val, (size_t)h->vsize * in.n, kind, s));
-    CK(cudaMemcpyAsync(w.in_op.p, u->op, sizeof(uint8_t) * in.n, kind, s));
-    in.row = w.in_row.p;
-    in.col = w.in_col.p;
-    in.val = w.in_val.p;
-    in.op = w.in_op.p;
+    if (u->on_device) {
+        in.row = u->row;
+        in.col = u->col;
+        in.val = u->val;
+        in.op = u->op;
+    } else {
+        CK(cudaMemcpyAsync(w.in_row.p, u->row, sizeof(int32_t) * in.n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w.in_col.p, u->col, sizeof(int32_t) * in.n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w.in_val.p, u->val, (size_t)h->vsize * in.n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w.in_op.p, u->op, sizeof(uint8_t) * in.n, cudaMemcpyHostToDevice, s));
+        in.row = w.in_row.p;
+        in.col = w.in_col.p;
+        in.val = w.in_val.p;
+        in.op = w.in_op.p;
+    }
+    h->h_args[k] = InArgs{in.row, in.col, in.val, in.op};
 }
 
 // Runs the pipeline once and reads the status.  A batch shape (sizes of the
@@ -851,6 +862,9 @@ dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, 
             CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         if (const char *env = getenv("DSPG_NO_GRAPHS")) h->use_graphs = env[0] == '0';
         CK(cudaMallocHost((void **)&h->hctl, sizeof(Ctl)));
+        CK(cudaMalloc((void **)&h->d_args, 3 * sizeof(InArgs)));
+        CK(cudaMallocHost((void **)&h->h_args, 3 * sizeof(InArgs)));
+        std::memset(h->h_args, 0, 3 * sizeof(InArgs));
         std::memset(h->hctl, 0, sizeof(Ctl));
         h->wA.which = 0; h->wA.vsize = h->vsize;
         h->wB.which = 1; h->wB.vsize = h->vsize;
@@ -888,9 +902,13 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
         if (h->wA.ensure(nA, h->A.arena_cap)) h->epoch++;
         if (!h->b_is_a && h->wB.ensure(nB, h->B.arena_cap)) h->epoch++;
         if (h->has_at && h->wAT.ensure(nA, h->AT.arena_cap)) h->epoch++;
-        upload(h, h->wA, dA, h->inA, s);
-        upload(h, h->wB, dB, h->inB, s);
-        if (h->b_is_a) h->inB = BatchIn{};
+        upload(h, h->wA, dA, h->inA, 0, s);
+        upload(h, h->wB, dB, h->inB, 1, s);
+        if (h->b_is_a) {
+            h->inB = BatchIn{};
+            h->h_args[1] = InArgs{nullptr, nullptr, nullptr, nullptr};
+        }
+        h->h_args[2] = InArgs{h->wAT.in_row.p, h->wAT.in_col.p, nullptr, h->wAT.in_op.p};
         const int64_t compactions0 = h->compactions;
 
         run_first(h, s);
@@ -1102,6 +1120,8 @@ void dspg_destroy(dspg_handle *h) {
         if (st) cudaStreamDestroy(st);
     if (h->ctl) cudaFree(h->ctl);
     if (h->hctl) cudaFreeHost(h->hctl);
+    if (h->d_args) cudaFree(h->d_args);
+    if (h->h_args) cudaFreeHost(h->h_args);
     delete h;
 }
 

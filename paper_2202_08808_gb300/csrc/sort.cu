@@ -63,20 +63,22 @@ __device__ __forceinline__ void write_sorted(SortOut out, int64_t s, uint64_t ke
 // exists.  A single tile finishes (de-duplicates and gathers) in the sort
 // kernel itself.
 
-constexpr int TS_NT = 1024;
-constexpr int TS_TILE = 4096;
-constexpr int TS_MAXT = 4;
+constexpr int TS_NT = 256;
+constexpr int TS_TILE = 1024;
+constexpr int TS_MAXT = 16;
 constexpr size_t TS_SMEM = TS_TILE * sizeof(uint64_t);
 constexpr size_t TM_SMEM = (size_t)TS_TILE * TS_MAXT * sizeof(uint64_t);
 
 int64_t sort_small_max() { return (int64_t)TS_TILE * TS_MAXT; }
 
 __global__ void __launch_bounds__(TS_NT)
-k_tile_sort(const int32_t *row, const int32_t *col, const void *val, const uint8_t *op, int n, int64_t nrows,
-            int64_t ncols, int sr, bool check_values, SortOut out, Ctl *ctl, unsigned skip_mask, int cb, int ib,
-            uint64_t *words_out) {
+k_tile_sort(const InArgs *in, int n, int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out, Ctl *ctl,
+            unsigned skip_mask, int cb, int ib, uint64_t *words_out) {
     extern __shared__ uint64_t sm[];
     if (failed(ctl, skip_mask)) return;
+    const int32_t *row = in->row, *col = in->col;
+    const void *val = in->val;
+    const uint8_t *op = in->op;
     const int tid = threadIdx.x;
     const int lo = blockIdx.x * TS_TILE;
     const int cnt = min(TS_TILE, n - lo);
@@ -142,10 +144,12 @@ __device__ __forceinline__ int count_le(const uint64_t *a, int n, uint64_t x) {
 }
 
 __global__ void __launch_bounds__(1024)
-k_tile_merge(const uint64_t *words, int n, int ib, int cb, const void *val, const uint8_t *op, int sr, SortOut out,
-             const Ctl *ctl, unsigned skip_mask) {
+k_tile_merge(const uint64_t *words, int n, int ib, int cb, const InArgs *in, int sr, SortOut out, const Ctl *ctl,
+             unsigned skip_mask) {
     extern __shared__ uint64_t sw[];
     if (failed(ctl, skip_mask)) return;
+    const void *val = in->val;
+    const uint8_t *op = in->op;
     for (int x = threadIdx.x; x < n; x += blockDim.x) sw[x] = words[x];
     __syncthreads();
     const int ntiles = (n + TS_TILE - 1) / TS_TILE;
@@ -180,10 +184,12 @@ void sort_tmp_sizes(int64_t n, int64_t *count_entries) {
     *count_entries = 256 * (nb > 0 ? nb : 1);
 }
 
-__global__ void k_make_keys(const int32_t *row, const int32_t *col, const void *val, const uint8_t *op, int64_t n,
-                            int64_t nrows, int64_t ncols, int sr, bool check_values, Ctl *ctl, unsigned skip_mask,
-                            int cb, uint64_t *k, uint32_t *v) {
+__global__ void k_make_keys(const InArgs *in, int64_t n, int64_t nrows, int64_t ncols, int sr, bool check_values,
+                            Ctl *ctl, unsigned skip_mask, int cb, uint64_t *k, uint32_t *v) {
     if (failed(ctl, skip_mask)) return;
+    const int32_t *row = in->row, *col = in->col;
+    const void *val = in->val;
+    const uint8_t *op = in->op;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t r = row[i], c = col[i];
@@ -255,9 +261,11 @@ k_scatter(const uint64_t *k, const uint32_t *v, int64_t n, int shift, const int6
     }
 }
 
-__global__ void k_finalize(const uint64_t *k, const uint32_t *v, int64_t n, int cb, const void *val,
-                           const uint8_t *op, int sr, SortOut out, const Ctl *ctl, unsigned skip_mask) {
+__global__ void k_finalize(const uint64_t *k, const uint32_t *v, int64_t n, int cb, const InArgs *in, int sr,
+                           SortOut out, const Ctl *ctl, unsigned skip_mask) {
     if (failed(ctl, skip_mask)) return;
+    const void *val = in->val;
+    const uint8_t *op = in->op;
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint64_t key = k[s];
@@ -282,9 +290,8 @@ void radix_sort_pairs(uint64_t *k, uint32_t *v, uint64_t *k_alt, uint32_t *v_alt
     *in_alt = alt;
 }
 
-void sort_updates(const int32_t *row, const int32_t *col, const void *val, const uint8_t *op, int64_t n,
-                  int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out, SortTmp tmp, Ctl *ctl,
-                  unsigned skip_mask, cudaStream_t s) {
+void sort_updates(const InArgs *in, int64_t n, int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out,
+                  SortTmp tmp, Ctl *ctl, unsigned skip_mask, cudaStream_t s) {
     if (n <= 0) return;
     const int cb = bits_for(ncols), rb = bits_for(nrows), ib = bits_for(n);
     const int kb = cb + rb;
@@ -296,19 +303,18 @@ void sort_updates(const int32_t *row, const int32_t *col, const void *val, const
             attr_set = true;
         }
         const int tiles = (int)((n + TS_TILE - 1) / TS_TILE);
-        launch_k(k_tile_sort, tiles, TS_NT, TS_SMEM, s, row, col, val, op, (int)n, nrows, ncols, sr, check_values, out,
-                 ctl, skip_mask, cb, ib, tmp.k0);
+        launch_k(k_tile_sort, tiles, TS_NT, TS_SMEM, s, in, (int)n, nrows, ncols, sr, check_values, out, ctl, skip_mask,
+                 cb, ib, tmp.k0);
         if (tiles > 1)
             launch_k(k_tile_merge, (unsigned)((n + 1023) / 1024), 1024, (size_t)n * sizeof(uint64_t), s,
-                     (const uint64_t *)tmp.k0, (int)n, ib, cb, val, op, sr, out, (const Ctl *)ctl, skip_mask);
+                     (const uint64_t *)tmp.k0, (int)n, ib, cb, in, sr, out, (const Ctl *)ctl, skip_mask);
         return;
     }
     unsigned nblk = (unsigned)((n + 255) / 256);
-    launch_k(k_make_keys, nblk, 256, 0, s, row, col, val, op, n, nrows, ncols, sr, check_values, ctl, skip_mask, cb, tmp.k0,
-                                    tmp.i0);
+    launch_k(k_make_keys, nblk, 256, 0, s, in, n, nrows, ncols, sr, check_values, ctl, skip_mask, cb, tmp.k0, tmp.i0);
     bool in_alt = false;
     radix_sort_pairs(tmp.k0, tmp.i0, tmp.k1, tmp.i1, n, kb, tmp.counts, tmp.scan_tmp, tmp.scan_out, s, &in_alt);
-    launch_k(k_finalize, nblk, 256, 0, s, in_alt ? tmp.k1 : tmp.k0, in_alt ? tmp.i1 : tmp.i0, n, cb, val, op, sr, out, ctl,
+    launch_k(k_finalize, nblk, 256, 0, s, in_alt ? tmp.k1 : tmp.k0, in_alt ? tmp.i1 : tmp.i0, n, cb, in, sr, out, ctl,
                                     skip_mask);
 }
 

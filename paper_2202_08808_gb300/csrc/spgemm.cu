@@ -324,8 +324,10 @@ __device__ __forceinline__ void bitonic_step(int32_t *k, T *v, int i, int l, boo
 // ---------------------------------------------------- thread merge kernel
 
 // One thread per row with at most MERGE_K A entries and at most MERGE_UB
-// products: the row's B entries are first copied to shared memory with
-// independent loads (all in flight together), then the MERGE_K sorted B rows
+// products: the column indices of the row's B entries are first copied to
+// shared memory with independent loads (all in flight together), and the
+// value at each list's head is loaded as soon as the head moves; the sorted
+// B rows
 // are merged like sorted lists, a cursor each; every output column comes out
 // in ascending order with its products folded in ascending k, so no table
 // and no sort are needed.  Shared memory is laid out [entry][thread], so the
@@ -335,17 +337,24 @@ __device__ __forceinline__ void bitonic_step(int32_t *k, T *v, int i, int l, boo
 constexpr int TM_NT = 128;  // threads per block of the merge kernel
 
 template <int SR, int K>
-__device__ __forceinline__ int merge_rows_smem(const int32_t *scol, const typename Sr<SR>::T *sval,
-                                               const typename Sr<SR>::T *av, const int *start, const int *blen,
-                                               int alen, int32_t *out_col, typename Sr<SR>::T *out_val, int limit) {
+__device__ __forceinline__ int merge_rows_smem(const int32_t *scol, const typename Sr<SR>::T *Bv,
+                                               const typename Sr<SR>::T *av, const int64_t *boff, const int *start,
+                                               const int *blen, int alen, int32_t *out_col,
+                                               typename Sr<SR>::T *out_val, int limit) {
     using T = typename Sr<SR>::T;
     int pos[K], end[K];
     int32_t head[K];
+    T hval[K];  // value at each list's head, loaded when the head moves
 #pragma unroll
     for (int s = 0; s < K; s++) {
         pos[s] = start[s];
         end[s] = start[s] + (s < alen ? blen[s] : 0);
-        head[s] = pos[s] < end[s] ? scol[pos[s] * TM_NT] : 0x7fffffff;
+        head[s] = 0x7fffffff;
+        hval[s] = T(0);
+        if (pos[s] < end[s]) {
+            head[s] = scol[pos[s] * TM_NT];
+            hval[s] = Bv[boff[s]];
+        }
     }
     int n = 0;
     while (true) {
@@ -358,11 +367,16 @@ __device__ __forceinline__ int merge_rows_smem(const int32_t *scol, const typena
 #pragma unroll
         for (int s = 0; s < K; s++) {
             if (head[s] == j) {
-                const T v = Sr<SR>::mul(av[s], sval[pos[s] * TM_NT]);
+                const T v = Sr<SR>::mul(av[s], hval[s]);
                 acc = first ? v : Sr<SR>::add(acc, v);
                 first = false;
                 pos[s]++;
-                head[s] = pos[s] < end[s] ? scol[pos[s] * TM_NT] : 0x7fffffff;
+                if (pos[s] < end[s]) {
+                    head[s] = scol[pos[s] * TM_NT];
+                    hval[s] = Bv[boff[s] + (pos[s] - start[s])];
+                } else {
+                    head[s] = 0x7fffffff;
+                }
             }
         }
         if (n < limit) {
@@ -380,8 +394,7 @@ k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned m
     using T = typename Sr<SR>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     if (failed(ctl, mask)) return;
-    T *svals = (T *)smem + threadIdx.x;
-    int32_t *scols = (int32_t *)((T *)smem + (size_t)UB * TM_NT) + threadIdx.x;
+    int32_t *scols = (int32_t *)smem + threadIdx.x;
     const T *Av = (const T *)A.val;
     const T *Bv = (const T *)B.val;
     T *Cv = (T *)C.val;
@@ -419,17 +432,14 @@ k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned m
         }
 #pragma unroll
         for (int s = 0; s < K; s++)
-            for (int q = 0; q < blen[s]; q++) {
-                scols[(start[s] + q) * TM_NT] = B.col[boff[s] + q];
-                svals[(start[s] + q) * TM_NT] = Bv[boff[s] + q];
-            }
+            for (int q = 0; q < blen[s]; q++) scols[(start[s] + q) * TM_NT] = B.col[boff[s] + q];
         const int64_t off = C.off[i];
         const int cap = J.static_mode ? 0x7fffffff : C.cap[i];
-        const int n = merge_rows_smem<SR, K>(scols, svals, av, start, blen, alen, C.col + off, Cv + off, cap);
+        const int n = merge_rows_smem<SR, K>(scols, Bv, av, boff, start, blen, alen, C.col + off, Cv + off, cap);
         bool ok = true;
         if (n > cap) {
             const int64_t d = c_row_dest(C, J, ctl, i, n);
-            if (d >= 0) merge_rows_smem<SR, K>(scols, svals, av, start, blen, alen, C.col + d, Cv + d, n);
+            if (d >= 0) merge_rows_smem<SR, K>(scols, Bv, av, boff, start, blen, alen, C.col + d, Cv + d, n);
             else ok = false;
         }
         if (ok) C.len[i] = n;
@@ -888,14 +898,14 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
     int k = 0;
     auto next = [&]() { return ss[(k++) % ns]; };
     {
-        const size_t smem_m = (size_t)MERGE_UB * TM_NT * (sizeof(T) + sizeof(int32_t));
+        const size_t smem_m = (size_t)MERGE_UB * TM_NT * sizeof(int32_t);
         static bool set_m = false;
         if (!set_m) {
             cudaFuncSetAttribute(k_num_thread_merge<SR, MERGE_K, MERGE_UB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_m);
             set_m = true;
         }
-        const int per_sm = (int)std::max<size_t>(1, (200 * 1024) / (smem_m + 1024));
+        const int per_sm = (int)std::min<size_t>(8, std::max<size_t>(1, (200 * 1024) / (smem_m + 1024)));
         launch_k(k_num_thread_merge<SR, MERGE_K, MERGE_UB>, num_sms * per_sm, TM_NT, smem_m, next(), A, B, C, J, ctl,
                  mask, (int)BIN_T8);
     }
