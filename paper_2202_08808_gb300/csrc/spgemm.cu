@@ -68,8 +68,8 @@ __device__ __forceinline__ long long atomic_add_ll2(long long *p, long long v) {
 
 // ------------------------------------------------------------- sizing
 
-constexpr int MERGE_K = 8;      // A rows up to this length are merged by a lane group
-constexpr int MERGE_UB = 256;   // ... when their product bound is at most this
+constexpr int MERGE_K = 8;      // A rows up to this length can be merged by one thread
+constexpr int MERGE_UB = 64;    // ... when their product bound is at most this
 
 __device__ __forceinline__ int pick_bin(long long ubc, int alen, int dense_mode) {
     if (alen <= MERGE_K && ubc <= MERGE_UB) return BIN_T8;
@@ -321,112 +321,132 @@ __device__ __forceinline__ void bitonic_step(int32_t *k, T *v, int i, int l, boo
     }
 }
 
-// ------------------------------------------------------ lane merge kernel
+// ---------------------------------------------------- thread merge kernel
 
-// Rows with at most LM_G A entries: a group of LM_G lanes per row (4 rows
-// per warp), lane s owning the sorted B row of A entry s, held LM_W entries
-// at a time in registers (loaded all at once, refilled when used up).  Each
-// step, a group-wide minimum (shuffles) gives the next output column j; the
-// lanes whose head is j contribute a (x) b, folded by a shuffle reduction,
-// and advance.  Output columns come out ascending; no table and no sort.
-// Writes go to the row's place while they fit its capacity; a row that
-// outgrows it is counted to the end, moved to the arena tail and merged
-// again (rare).
-constexpr int LM_G = 8;
-constexpr int LM_W = 8;
+// One thread per row with at most MERGE_K A entries and at most MERGE_UB
+// products: the column indices of the row's B entries are first copied to
+// shared memory with independent loads (all in flight together), and the
+// value at each list's head is loaded as soon as the head moves; the sorted
+// B rows
+// are merged like sorted lists, a cursor each; every output column comes out
+// in ascending order with its products folded in ascending k, so no table
+// and no sort are needed.  Shared memory is laid out [entry][thread], so the
+// lanes of a warp never share a bank.  Writes go to the row's place while
+// they fit its capacity; a row that outgrows it is counted to the end, moved
+// to the arena tail and merged again (rare).
+constexpr int TM_NT = 128;  // threads per block of the merge kernel
 
-template <int SR>
-__device__ __forceinline__ int lane_merge(const MatView &B, unsigned gmask, int gl, typename Sr<SR>::T a,
-                                          int64_t boff, int blen, int32_t *out_col, typename Sr<SR>::T *out_val,
-                                          int limit) {
+template <int SR, int K>
+__device__ __forceinline__ int merge_rows_smem(const int32_t *scol, const typename Sr<SR>::T *Bv,
+                                               const typename Sr<SR>::T *av, const int64_t *boff, const int *start,
+                                               const int *blen, int alen, int32_t *out_col,
+                                               typename Sr<SR>::T *out_val, int limit) {
     using T = typename Sr<SR>::T;
-    const T *Bv = (const T *)B.val;
-    int32_t wc[LM_W];
-    T wv[LM_W];
+    int pos[K], end[K];
+    int32_t head[K];
+    T hval[K];  // value at each list's head, loaded when the head moves
 #pragma unroll
-    for (int q = 0; q < LM_W; q++) {
-        wc[q] = q < blen ? B.col[boff + q] : 0x7fffffff;
-        wv[q] = q < blen ? Bv[boff + q] : T(0);
-    }
-    int p = 0, n = 0;
-    while (true) {
-        int32_t j = wc[0];
-#pragma unroll
-        for (int d = LM_G / 2; d > 0; d >>= 1) j = min(j, __shfl_xor_sync(gmask, j, d, LM_G));
-        if (j == 0x7fffffff) break;
-        const bool hit = wc[0] == j;
-        T v = hit ? Sr<SR>::mul(a, wv[0]) : Sr<SR>::zero();
-#pragma unroll
-        for (int d = LM_G / 2; d > 0; d >>= 1) v = Sr<SR>::add(v, __shfl_xor_sync(gmask, v, d, LM_G));
-        if (gl == 0 && n < limit) {
-            out_col[n] = j;
-            out_val[n] = v;
+    for (int s = 0; s < K; s++) {
+        pos[s] = start[s];
+        end[s] = start[s] + (s < alen ? blen[s] : 0);
+        head[s] = 0x7fffffff;
+        hval[s] = T(0);
+        if (pos[s] < end[s]) {
+            head[s] = scol[pos[s] * TM_NT];
+            hval[s] = Bv[boff[s]];
         }
-        n++;
-        if (hit) {
-            p++;
+    }
+    int n = 0;
+    while (true) {
+        int32_t j = head[0];
 #pragma unroll
-            for (int q = 0; q < LM_W - 1; q++) {
-                wc[q] = wc[q + 1];
-                wv[q] = wv[q + 1];
-            }
-            wc[LM_W - 1] = 0x7fffffff;
-            if (wc[0] == 0x7fffffff && p < blen) {
+        for (int s = 1; s < K; s++) j = min(j, head[s]);
+        if (j == 0x7fffffff) break;
+        T acc = Sr<SR>::zero();
+        bool first = true;
 #pragma unroll
-                for (int q = 0; q < LM_W; q++) {
-                    wc[q] = p + q < blen ? B.col[boff + p + q] : 0x7fffffff;
-                    wv[q] = p + q < blen ? Bv[boff + p + q] : T(0);
+        for (int s = 0; s < K; s++) {
+            if (head[s] == j) {
+                const T v = Sr<SR>::mul(av[s], hval[s]);
+                acc = first ? v : Sr<SR>::add(acc, v);
+                first = false;
+                pos[s]++;
+                if (pos[s] < end[s]) {
+                    head[s] = scol[pos[s] * TM_NT];
+                    hval[s] = Bv[boff[s] + (pos[s] - start[s])];
+                } else {
+                    head[s] = 0x7fffffff;
                 }
             }
         }
+        if (n < limit) {
+            out_col[n] = j;
+            out_val[n] = acc;
+        }
+        n++;
     }
     return n;
 }
 
-template <int SR>
-__global__ void __launch_bounds__(256)
-k_num_lane_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
+template <int SR, int K, int UB>
+__global__ void __launch_bounds__(TM_NT)
+k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
     using T = typename Sr<SR>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
     if (failed(ctl, mask)) return;
-    const int lane = threadIdx.x & 31, gl = lane & (LM_G - 1), gw = lane / LM_G;
-    const unsigned gmask = ((1u << LM_G) - 1u) << (gw * LM_G);
+    int32_t *scols = (int32_t *)smem + threadIdx.x;
     const T *Av = (const T *)A.val;
+    const T *Bv = (const T *)B.val;
     T *Cv = (T *)C.val;
-    const int gpb = blockDim.x / LM_G;
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
-    for (long long it = (long long)blockIdx.x * gpb + (threadIdx.x / LM_G); it < cnt; it += (long long)gridDim.x * gpb) {
+    for (long long it = (long long)blockIdx.x * TM_NT + threadIdx.x; it < cnt; it += (long long)gridDim.x * TM_NT) {
         const int t = J.bins[(int64_t)bin * J.bin_cap + it];
         const int32_t i = J.R[t];
         const int64_t aoff = A.off[i];
         const int alen = A.len[i];
-        T a = T(0);
-        int64_t boff = 0;
-        int blen = 0;
-        if (gl < alen) {
-            const int32_t k = A.col[aoff + gl];
-            a = Av[aoff + gl];
-            boff = B.off[k];
-            blen = B.len[k];
+        T av[K];
+        int64_t boff[K];
+        int blen[K], start[K];
+#pragma unroll
+        for (int s = 0; s < K; s++) {
+            av[s] = T(0);
+            boff[s] = 0;
+            blen[s] = 0;
+            if (s < alen) {
+                const int32_t k = A.col[aoff + s];
+                av[s] = Av[aoff + s];
+                boff[s] = B.off[k];
+                blen[s] = B.len[k];
+            }
         }
+        int tot = 0;
+#pragma unroll
+        for (int s = 0; s < K; s++) {
+            start[s] = tot;
+            tot += blen[s];
+        }
+        if (tot > UB) {  // the sizing pass guarantees tot <= UB; guard the buffer anyway
+            set_status(ctl, ST_TIMEOUT);
+            continue;
+        }
+#pragma unroll
+        for (int s = 0; s < K; s++)
+            for (int q = 0; q < blen[s]; q++) scols[(start[s] + q) * TM_NT] = B.col[boff[s] + q];
         const int64_t off = C.off[i];
         const int cap = J.static_mode ? 0x7fffffff : C.cap[i];
-        const int n = lane_merge<SR>(B, gmask, gl, a, boff, blen, C.col + off, Cv + off, cap);
+        const int n = merge_rows_smem<SR, K>(scols, Bv, av, boff, start, blen, alen, C.col + off, Cv + off, cap);
         bool ok = true;
         if (n > cap) {
-            int64_t d = 0;
-            if (gl == 0) d = c_row_dest(C, J, ctl, i, n);
-            d = __shfl_sync(gmask, d, 0, LM_G);
-            if (d >= 0) lane_merge<SR>(B, gmask, gl, a, boff, blen, C.col + d, Cv + d, n);
+            const int64_t d = c_row_dest(C, J, ctl, i, n);
+            if (d >= 0) merge_rows_smem<SR, K>(scols, Bv, av, boff, start, blen, alen, C.col + d, Cv + d, n);
             else ok = false;
         }
-        if (gl == 0) {
-            if (ok) C.len[i] = n;
-            nnz_acc += n;
-        }
+        if (ok) C.len[i] = n;
+        nnz_acc += n;
     }
     nnz_acc = warp_sum<long long>(nnz_acc);
-    if (lane == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
+    if ((threadIdx.x & 31) == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
 }
 
 // ---------------------------------------------------- group hash kernel
@@ -877,7 +897,18 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
     using T = typename Sr<SR>::T;
     int k = 0;
     auto next = [&]() { return ss[(k++) % ns]; };
-    launch_k(k_num_lane_merge<SR>, num_sms * 8, 256, 0, next(), A, B, C, J, ctl, mask, (int)BIN_T8);
+    {
+        const size_t smem_m = (size_t)MERGE_UB * TM_NT * sizeof(int32_t);
+        static bool set_m = false;
+        if (!set_m) {
+            cudaFuncSetAttribute(k_num_thread_merge<SR, MERGE_K, MERGE_UB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_m);
+            set_m = true;
+        }
+        const int per_sm = (int)std::min<size_t>(8, std::max<size_t>(1, (200 * 1024) / (smem_m + 1024)));
+        launch_k(k_num_thread_merge<SR, MERGE_K, MERGE_UB>, num_sms * per_sm, TM_NT, smem_m, next(), A, B, C, J, ctl,
+                 mask, (int)BIN_T8);
+    }
     if (J.dense_mode) {
         const int mp = (int)((J.m + 31) / 32 * 32);
         constexpr int NW = 8;
