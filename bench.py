@@ -333,6 +333,36 @@ def reference_arm(args):
     }), flush=True)
 
 
+def profile_arm(args):
+    """One warmed-up dynamic step (NVTX range "step") or one static recompute
+    (NVTX range "static"), for ncu captures filtered with --nvtx-include."""
+    import torch
+    import paper_2202_08808_gb300 as pkg
+    from workloads import stencil7
+    torch.cuda.set_device(0)
+    A = stencil7(GRID, GRID, GRID, seed=1)
+    g = pkg.DynamicSpGEMM(A)
+    if args.profile == "static":
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("static")
+        g.recompute_all()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print("static profiled")
+        return
+    bs = make_batches(4, 100, args.batch)
+    dev = [type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(), torch.from_numpy(b.val).cuda(),
+                   torch.from_numpy(b.op).cuda()) for b in bs]
+    for b in dev[:3]:
+        g.apply_batch(b)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("step")
+    st = g.apply_batch(dev[3])
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print("step profiled", st)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,7 +372,13 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--profile", choices=["step", "static"], default=None,
+                    help="run one NVTX-marked step or static recompute for ncu, then exit")
+    ap.add_argument("--batch", type=int, default=BATCH)
     args = ap.parse_args()
+    if args.profile:
+        profile_arm(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
