@@ -179,6 +179,33 @@ dspg_status dspg_stage_times(dspg_handle *h, float *ms, int n);
  * handles), for auditing how many launches a call makes. */
 unsigned long long dspg_kernel_launches(void);
 
+/* Rows of C = A B for callers that cannot let a library allocate device
+ * memory: their memory belongs to another allocator (a framework's caching
+ * pool, an arena fixed at start-up), or their latency budget cannot absorb
+ * cudaMalloc/cudaFree, which synchronise the device.  The paper has no
+ * counterpart of this call; it is a service of this library.
+ *
+ * A and B: canonical CSR in device memory (on_device = 1), A->ncols ==
+ * B->nrows, and B->ncols <= 65536 (larger B is rejected with
+ * DSPG_ERR_INVALID: the working memory is a fixed array).  rows[nrows]:
+ * device array of row indices of A (any order, repeats allowed).
+ * Outputs (device, caller-owned): rowptr[nrows+1], then col and val with
+ * room for `capacity` entries; row t of the result is row rows[t] of C with
+ * columns ascending.  Two-call convention: with col == NULL only rowptr and
+ * *nnz_out are written; a result larger than capacity returns
+ * DSPG_ERR_INVALID with *nnz_out set to the size needed.
+ *
+ * Allocation: none.  The working memory is a fixed array of about 4.2 MiB
+ * of device memory in this library image, held by every GPU that loads the
+ * library until the process exits.  The first call on each device looks up
+ * that array's device address (with the device current); make that first
+ * call before any stream capture.  All calls share the array: calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race and give wrong results.  The call synchronises the stream twice. */
+dspg_status dspg_multiply_rows_noalloc(const dspg_csr *A, const dspg_csr *B, dspg_semiring sr, const int32_t *rows,
+                                       int64_t nrows, int64_t *rowptr, int32_t *col, void *val, int64_t capacity,
+                                       int64_t *nnz_out, void *stream);
+
 /* Free the handle and all its device memory (synchronises the device). */
 void dspg_destroy(dspg_handle *h);
 

@@ -20,5 +20,6 @@ from .dspg import (  # noqa: F401
     DynamicSpGEMM,
     kernel_launches,
     library_path,
+    multiply_rows_noalloc,
     load,
 )

@@ -197,6 +197,11 @@ thread_local std::string g_err;
 
 }  // namespace
 
+namespace dspg {
+void set_thread_error(const char *msg);
+}
+void dspg::set_thread_error(const char *msg) { g_err = msg; }
+
 struct dspg_handle {
     int sr = 0, vsize = 8, num_sms = 148, dev = 0;
     dspg_options opt{};

@@ -91,6 +91,9 @@ def load():
         lib.dspg_stage_times.argtypes = [p, C.POINTER(C.c_float), i32]
         lib.dspg_kernel_launches.restype = C.c_ulonglong
         lib.dspg_kernel_launches.argtypes = []
+        lib.dspg_multiply_rows_noalloc.restype = i32
+        lib.dspg_multiply_rows_noalloc.argtypes = [C.POINTER(_Csr), C.POINTER(_Csr), i32, p, i64, p, p, p, i64,
+                                                   C.POINTER(i64), p]
         lib.dspg_destroy.restype = None
         lib.dspg_destroy.argtypes = [p]
         lib.dspg_last_error.restype = C.c_char_p
@@ -101,7 +104,7 @@ def load():
 
 EXPORTED = ["dspg_build", "dspg_apply_batch", "dspg_read_C", "dspg_read_A", "dspg_read_rows_C",
             "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_set_profiling", "dspg_stage_times",
-            "dspg_kernel_launches", "dspg_destroy", "dspg_last_error"]
+            "dspg_kernel_launches", "dspg_multiply_rows_noalloc", "dspg_destroy", "dspg_last_error"]
 
 STAGES = ["sort", "classify", "detect", "merge", "commit", "transpose", "size", "numeric"]
 
@@ -276,6 +279,48 @@ class DynamicSpGEMM:
         v = [C.c_int64() for _ in range(5)]
         self._check(self._lib.dspg_info(self._h, *[C.byref(x) for x in v]))
         return dict(zip(("n", "k", "m", "nnz_a", "nnz_c"), [x.value for x in v]))
+
+
+def multiply_rows_noalloc(A, B, rows, semiring: int | None = None, stream=None):
+    """Rows `rows` of C = A B through dspg_multiply_rows_noalloc, for callers
+    that cannot let the library allocate device memory (the call itself
+    allocates nothing: its working memory is a fixed array in the library).
+
+    A and B are objects with ``nrows, ncols, rowptr, col, val`` whose arrays
+    are CUDA tensors; rows is a CUDA int32 tensor.  The output tensors are
+    allocated here by torch, on the caller's side of the boundary.  Returns
+    (rowptr, col, val) as CUDA tensors."""
+    import torch
+    lib = load()
+    keep: list = []
+    if semiring is None:
+        semiring = PLUS_TIMES_F64 if A.val.dtype == torch.float64 else MIN_PLUS_I32
+
+    def csr(M):
+        rp = M.rowptr.to(torch.int64).contiguous()
+        col = M.col.to(torch.int32).contiguous()
+        val = M.val.contiguous()
+        keep.extend([rp, col, val])
+        return _Csr(M.nrows, M.ncols, int(rp[-1].item()), rp.data_ptr(), col.data_ptr(), val.data_ptr(), 1)
+
+    ca, cb = csr(A), csr(B)
+    rows = rows.to(torch.int32).contiguous()
+    n = rows.numel()
+    rp = torch.empty(n + 1, dtype=torch.int64, device=rows.device)
+    nnz = C.c_int64()
+    s = _stream(stream)
+    st = lib.dspg_multiply_rows_noalloc(C.byref(ca), C.byref(cb), semiring, rows.data_ptr(), n, rp.data_ptr(), None,
+                                        None, 0, C.byref(nnz), s)
+    if st != 0:
+        raise DspgError(st, lib.dspg_last_error(None).decode())
+    cap = max(nnz.value, 1)
+    col = torch.empty(cap, dtype=torch.int32, device=rows.device)
+    val = torch.empty(cap, dtype=torch.float64 if semiring == PLUS_TIMES_F64 else torch.int32, device=rows.device)
+    st = lib.dspg_multiply_rows_noalloc(C.byref(ca), C.byref(cb), semiring, rows.data_ptr(), n, rp.data_ptr(),
+                                        col.data_ptr(), val.data_ptr(), cap, C.byref(nnz), s)
+    if st != 0:
+        raise DspgError(st, lib.dspg_last_error(None).decode())
+    return rp, col[: nnz.value], val[: nnz.value]
 
 
 class CsrArrays:
