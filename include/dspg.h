@@ -89,6 +89,9 @@ typedef struct {
     int32_t slack_div;      /* default 4 */
     double arena_headroom;  /* arena capacity / total row capacity at build; default 1.5 */
     int32_t keep_transpose; /* 1: maintain A's transposed pattern (needed when B is A or B changes); -1: auto */
+    int32_t exact_static;   /* static product: 1 = count rows exactly before laying C out (two passes);
+                               0 = auto (exact only when the bound-sized layout would take over a quarter
+                               of the free device memory) */
 } dspg_options;
 
 /* What one apply_batch did.  Counts of the unique, last-writer-wins batch

@@ -250,6 +250,7 @@ void set_defaults(dspg_options *o) {
     o->slack_div = 4;
     o->arena_headroom = 1.5;
     o->keep_transpose = -1;
+    o->exact_static = 0;
 }
 
 void read_ctl(dspg_handle *h, cudaStream_t s) {
@@ -368,7 +369,7 @@ void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
     if (m > DENSE_M_MAX) {
         w.gd_w = (m + 31) / 32 * 32;
         const double per = (double)w.gd_w * (h->vsize + 0.125);
-        int ctas = (int)std::min<double>(2.0 * h->num_sms, std::max(1.0, (1024.0 * 1024 * 1024) / per));
+        int ctas = (int)std::min<double>(2.0 * h->num_sms, std::max(4.0, (256.0 * 1024 * 1024) / per));
         w.gd_ctas = std::max(1, ctas);
         w.gd_acc.reserve(w.gd_w * w.gd_ctas * h->vsize);
         w.gd_mask.reserve(w.gd_w / 32 * w.gd_ctas);
@@ -428,8 +429,12 @@ void numeric_branches(dspg_handle *h, cudaStream_t s, const CJob &J) {
 }
 
 // Full recompute of C from A, B (the static product).  The sizing pass lays
-// C out afresh (room for each row's product bound), reusing the arena when
-// it is large enough; the numeric kernels then write every row in place.
+// C out afresh with room for each row's product bound and the numeric
+// kernels write every row in place.  When that layout would take more than a
+// quarter of the free device memory (bounds far above the true row sizes,
+// as in squares of skewed graphs), an exact pass first counts every row and
+// C is laid out from the counts instead.  The arena is reused when large
+// enough.
 void static_recompute(dspg_handle *h, cudaStream_t s) {
     ensure_c_ws(h, s);
     DevMat &C = h->C;
@@ -441,26 +446,51 @@ void static_recompute(dspg_handle *h, cudaStream_t s) {
     C.cap.reserve(std::max<int64_t>(n, 1));
     C.off.reserve(n + 1);
     C.top.reserve(1);
+    h->epoch++;
     MatView Av = h->A.view(), Bv = h->Bm().view();
-    for (int attempt = 0; attempt < 3; attempt++) {
-        CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
-        CK(cudaMemsetAsync(C.top.p, 0, sizeof(long long), s));
-        long long nn = n;
-        CK(cudaMemcpyAsync(&h->ctl->n_affected, &nn, sizeof(long long), cudaMemcpyHostToDevice, s));
-        run_size_bins(Av, Bv, C.view(), c_job(h, h->wc.iota.p, true), n, h->ctl, M_AB, s, h->num_sms);
+    CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+    CK(cudaMemsetAsync(C.top.p, 0, sizeof(long long), s));
+    long long nn = n;
+    CK(cudaMemcpyAsync(&h->ctl->n_affected, &nn, sizeof(long long), cudaMemcpyHostToDevice, s));
+    run_size_bins(Av, Bv, C.view(), c_job(h, h->wc.iota.p, true), n, h->ctl, M_AB, s, h->num_sms);
+    read_ctl(h, s);
+    if (h->hctl->status & ~ST_C_ARENA)
+        throw Err(DSPG_ERR_CUDA, "static sizing failed with status " + std::to_string(h->hctl->status));
+    long long need = 0;
+    CK(cudaMemcpyAsync(&need, C.top.p, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const double entry_b = 4.0 + h->vsize;
+    const bool exact = h->opt.exact_static == 1 ||
+                       (double)need * entry_b * h->opt.arena_headroom > 0.25 * (double)(free_b + C.col.n * entry_b);
+    CK(cudaMemsetAsync(&h->ctl->status, 0, sizeof(unsigned), s));
+    if (exact) {
+        CJob Jc = c_job(h, h->wc.iota.p, true);
+        Jc.count_only = 1;
+        numeric_branches(h, s, Jc);
         read_ctl(h, s);
-        if (!(h->hctl->status & ST_C_ARENA)) break;
-        long long need = 0;
-        CK(cudaMemcpyAsync(&need, C.top.p, sizeof(long long), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        const int64_t cap = std::max<int64_t>((int64_t)(need * h->opt.arena_headroom), need + 4096);
+        if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "exact sizing failed with status " + std::to_string(h->hctl->status));
+        caps_from_lens(C.len.p, C.cap.p, n, h->opt.slack_min, h->opt.slack_div, s);
+        DBuf<int64_t> tmp;
+        tmp.reserve(scan_tmp_entries(n) + 1);
+        scan_i32_to_i64(C.cap.p, C.off.p, n, tmp.p, s);
+        need = read_i64(C.off.p + n, s);
+        CK(cudaMemcpyAsync(C.top.p, &need, sizeof(long long), cudaMemcpyHostToDevice, s));
+    }
+    const int64_t cap = std::max<int64_t>((int64_t)(need * h->opt.arena_headroom), need + 4096);
+    if (C.col.n < need + 1) {
         C.col.release();
         C.val.release();
         C.col.reserve(cap);
         C.val.reserve(cap * h->vsize);
-        C.arena_cap = cap;
     }
-    if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "static sizing failed with status " + std::to_string(h->hctl->status));
+    C.arena_cap = C.col.n;
+    C.val.reserve(C.arena_cap * h->vsize);
+    CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+    CK(cudaMemcpyAsync(&h->ctl->n_affected, &nn, sizeof(long long), cudaMemcpyHostToDevice, s));
+    // the bins of the sizing pass are still in place; restore their counts
+    CK(cudaMemcpyAsync(h->ctl->bin_count, h->hctl->bin_count, sizeof(h->hctl->bin_count), cudaMemcpyHostToDevice, s));
     numeric_branches(h, s, c_job(h, h->wc.iota.p, true));
     read_ctl(h, s);
     if (h->hctl->status & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, "accumulator probe limit reached");
@@ -825,6 +855,111 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
     return nnz;
 }
 
+// Checks one batch pair and gets the handle's buffers and inputs ready.
+void prepare_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, cudaStream_t s) {
+    const int64_t nA = dA ? dA->n : 0, nB = dB ? dB->n : 0;
+    if (nA < 0 || nB < 0) throw Err(DSPG_ERR_INVALID, "negative batch size");
+    if (nA > INT32_MAX / 2 || nB > INT32_MAX / 2) throw Err(DSPG_ERR_INVALID, "batch too large");
+    if (nA > 0 && (!dA->row || !dA->col || !dA->val || !dA->op)) throw Err(DSPG_ERR_INVALID, "NULL array in dA");
+    if (nB > 0 && (!dB->row || !dB->col || !dB->val || !dB->op)) throw Err(DSPG_ERR_INVALID, "NULL array in dB");
+    if (h->b_is_a && nB > 0) throw Err(DSPG_ERR_INVALID, "B is A: pass the batch as dA only");
+    if (!h->b_is_a && nB > 0 && !h->has_at) build_transpose(h, s);
+    ensure_c_ws(h, s);
+    if (h->wA.ensure(nA, h->A.arena_cap)) h->epoch++;
+    if (!h->b_is_a && h->wB.ensure(nB, h->B.arena_cap)) h->epoch++;
+    if (h->has_at && h->wAT.ensure(nA, h->AT.arena_cap)) h->epoch++;
+    upload(h, h->wA, dA, h->inA, 0, s);
+    upload(h, h->wB, dB, h->inB, 1, s);
+    if (h->b_is_a) {
+        h->inB = BatchIn{};
+        h->h_args[1] = InArgs{nullptr, nullptr, nullptr, nullptr};
+    }
+    h->h_args[2] = InArgs{h->wAT.in_row.p, h->wAT.in_col.p, nullptr, h->wAT.in_op.p};
+}
+
+// After a run: grow what overflowed and re-run the failed stages (eagerly,
+// on s) until the status is clean; errors become exceptions.
+void recover(dspg_handle *h, cudaStream_t s) {
+    const int64_t nA = h->inA.n, nB = h->inB.n;
+        for (int iter = 0; iter < 8 && h->hctl->status; iter++) {
+        const unsigned st = h->hctl->status;
+        if (st & ST_INVALID) throw Err(DSPG_ERR_INVALID, "batch entry out of range or with an invalid value/op");
+        if (st & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, "accumulator probe limit reached");
+        if (st & ST_AB_STAGE) {
+            if (h->wA.grow_stage(h->hctl->u[0].stage_top + 1024)) h->epoch++;
+            if (h->wB.grow_stage(h->hctl->u[1].stage_top + 1024)) h->epoch++;
+            CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+            pipeline(h, s, false, false);
+            read_ctl(h, s);
+            continue;
+        }
+        const bool side_on = h->has_at && nA > 0;
+        if (st & ST_AB_ARENA) {
+            regrow(h, h->A, s);
+            if (!h->b_is_a && nB > 0) regrow(h, h->B, s);
+            for (int k = 0; k < 2; k++) {
+                reset_range(h, &h->ctl->u[k].n_cchunk, sizeof(long long), s);
+                reset_range(h, &h->ctl->u[k].reloc, sizeof(long long), s);
+            }
+            reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
+            reset_c_counters(h, s);
+            reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+            stage_commit_ab(h, s);
+            if (side_on) {
+                transpose_front(h, s);
+                transpose_commit(h, s);
+            }
+            stage_size(h, s);
+            stage_numeric(h, s);
+            read_ctl(h, s);
+            continue;
+        }
+        const bool at = side_on && (st & (ST_AT_STAGE | ST_AT_ARENA));
+        const bool cc = st & ST_C_ARENA;
+        if ((st & ST_AT_STAGE) && h->wAT.grow_stage(h->hctl->u[2].stage_top + 1024)) h->epoch++;
+        if (st & ST_AT_ARENA) regrow(h, h->AT, s);
+        if (st & ST_C_ARENA) regrow(h, h->C, s);
+        reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+        if (at) {
+            reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
+            transpose_front(h, s);
+            transpose_commit(h, s);
+        }
+        if (cc) {
+            reset_c_counters(h, s);
+            stage_size(h, s);
+            stage_numeric(h, s);
+        }
+        read_ctl(h, s);
+    }
+    if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "apply_batch did not converge, status " + std::to_string(h->hctl->status));
+}
+
+void fill_stats(dspg_handle *h, dspg_batch_stats *stats, int64_t compactions0) {
+    const int64_t nA = h->inA.n, nB = h->inB.n;
+        h->last_nR = h->hctl->n_affected;
+    if (stats) {
+        const Ctl &c = *h->hctl;
+        std::memset(stats, 0, sizeof(*stats));
+        stats->n_updates = nA + nB;
+        for (int k = 0; k < 2; k++) {
+            stats->n_insert += c.u[k].ins;
+            stats->n_update += c.u[k].upd;
+            stats->n_delete += c.u[k].del;
+            stats->n_noop += c.u[k].nop;
+            stats->touched_rows += c.u[k].n_merge;
+            stats->relocations += c.u[k].reloc;
+        }
+        stats->n_unique = stats->n_insert + stats->n_update + stats->n_delete + stats->n_noop;
+        stats->relocations += c.u[2].reloc + c.c_reloc;
+        stats->affected_rows = c.n_affected;
+        stats->products = c.products;
+        stats->nnz_written = c.nnz_written;
+        stats->compactions = h->compactions - compactions0;
+        stats->a_entries = c.a_entries;
+    }
+}
+
 }  // namespace
 
 // ================================================================ C ABI
@@ -853,6 +988,7 @@ dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, 
             if (opt->slack_div > 0) h->opt.slack_div = opt->slack_div;
             if (opt->arena_headroom >= 1.0) h->opt.arena_headroom = opt->arena_headroom;
             h->opt.keep_transpose = opt->keep_transpose;
+            h->opt.exact_static = opt->exact_static;
         }
         h->sr = sr;
         h->vsize = sr == DSPG_PLUS_TIMES_F64 ? 8 : 4;
@@ -896,102 +1032,12 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
     if (!h) return DSPG_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     try {
-        const int64_t nA = dA ? dA->n : 0, nB = dB ? dB->n : 0;
-        if (nA < 0 || nB < 0) throw Err(DSPG_ERR_INVALID, "negative batch size");
-        if (nA > INT32_MAX / 2 || nB > INT32_MAX / 2) throw Err(DSPG_ERR_INVALID, "batch too large");
-        if (nA > 0 && (!dA->row || !dA->col || !dA->val || !dA->op)) throw Err(DSPG_ERR_INVALID, "NULL array in dA");
-        if (nB > 0 && (!dB->row || !dB->col || !dB->val || !dB->op)) throw Err(DSPG_ERR_INVALID, "NULL array in dB");
-        if (h->b_is_a && nB > 0) throw Err(DSPG_ERR_INVALID, "B is A: pass the batch as dA only");
-        if (!h->b_is_a && nB > 0 && !h->has_at) build_transpose(h, s);
-        ensure_c_ws(h, s);
-        if (h->wA.ensure(nA, h->A.arena_cap)) h->epoch++;
-        if (!h->b_is_a && h->wB.ensure(nB, h->B.arena_cap)) h->epoch++;
-        if (h->has_at && h->wAT.ensure(nA, h->AT.arena_cap)) h->epoch++;
-        upload(h, h->wA, dA, h->inA, 0, s);
-        upload(h, h->wB, dB, h->inB, 1, s);
-        if (h->b_is_a) {
-            h->inB = BatchIn{};
-            h->h_args[1] = InArgs{nullptr, nullptr, nullptr, nullptr};
-        }
-        h->h_args[2] = InArgs{h->wAT.in_row.p, h->wAT.in_col.p, nullptr, h->wAT.in_op.p};
+        prepare_batch(h, dA, dB, s);
         const int64_t compactions0 = h->compactions;
-
         run_first(h, s);
         if (h->prof) stage_times_from_events(h);
-
-        for (int iter = 0; iter < 8 && h->hctl->status; iter++) {
-            const unsigned st = h->hctl->status;
-            if (st & ST_INVALID) throw Err(DSPG_ERR_INVALID, "batch entry out of range or with an invalid value/op");
-            if (st & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, "accumulator probe limit reached");
-            if (st & ST_AB_STAGE) {
-                if (h->wA.grow_stage(h->hctl->u[0].stage_top + 1024)) h->epoch++;
-                if (h->wB.grow_stage(h->hctl->u[1].stage_top + 1024)) h->epoch++;
-                CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
-                pipeline(h, s, false, false);
-                read_ctl(h, s);
-                continue;
-            }
-            const bool side_on = h->has_at && nA > 0;
-            if (st & ST_AB_ARENA) {
-                regrow(h, h->A, s);
-                if (!h->b_is_a && nB > 0) regrow(h, h->B, s);
-                for (int k = 0; k < 2; k++) {
-                    reset_range(h, &h->ctl->u[k].n_cchunk, sizeof(long long), s);
-                    reset_range(h, &h->ctl->u[k].reloc, sizeof(long long), s);
-                }
-                reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
-                reset_c_counters(h, s);
-                reset_range(h, &h->ctl->status, sizeof(unsigned), s);
-                stage_commit_ab(h, s);
-                if (side_on) {
-                    transpose_front(h, s);
-                    transpose_commit(h, s);
-                }
-                stage_size(h, s);
-                stage_numeric(h, s);
-                read_ctl(h, s);
-                continue;
-            }
-            const bool at = side_on && (st & (ST_AT_STAGE | ST_AT_ARENA));
-            const bool cc = st & ST_C_ARENA;
-            if ((st & ST_AT_STAGE) && h->wAT.grow_stage(h->hctl->u[2].stage_top + 1024)) h->epoch++;
-            if (st & ST_AT_ARENA) regrow(h, h->AT, s);
-            if (st & ST_C_ARENA) regrow(h, h->C, s);
-            reset_range(h, &h->ctl->status, sizeof(unsigned), s);
-            if (at) {
-                reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
-                transpose_front(h, s);
-                transpose_commit(h, s);
-            }
-            if (cc) {
-                reset_c_counters(h, s);
-                stage_size(h, s);
-                stage_numeric(h, s);
-            }
-            read_ctl(h, s);
-        }
-        if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "apply_batch did not converge, status " + std::to_string(h->hctl->status));
-        h->last_nR = h->hctl->n_affected;
-        if (stats) {
-            const Ctl &c = *h->hctl;
-            std::memset(stats, 0, sizeof(*stats));
-            stats->n_updates = nA + nB;
-            for (int k = 0; k < 2; k++) {
-                stats->n_insert += c.u[k].ins;
-                stats->n_update += c.u[k].upd;
-                stats->n_delete += c.u[k].del;
-                stats->n_noop += c.u[k].nop;
-                stats->touched_rows += c.u[k].n_merge;
-                stats->relocations += c.u[k].reloc;
-            }
-            stats->n_unique = stats->n_insert + stats->n_update + stats->n_delete + stats->n_noop;
-            stats->relocations += c.u[2].reloc + c.c_reloc;
-            stats->affected_rows = c.n_affected;
-            stats->products = c.products;
-            stats->nnz_written = c.nnz_written;
-            stats->compactions = h->compactions - compactions0;
-            stats->a_entries = c.a_entries;
-        }
+        recover(h, s);
+        fill_stats(h, stats, compactions0);
         return DSPG_OK;
     } catch (const Err &e) {
         return fail(h, e);

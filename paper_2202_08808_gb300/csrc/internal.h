@@ -76,6 +76,7 @@ struct CJob {
     int static_mode;          // 1: C is laid out afresh by the sizing pass
     int slack_min, slack_div;
     uint32_t *bmR;            // affected-row bitmap, cleared by the sizing pass (dynamic mode)
+    int count_only;           // 1: only count each row's entries into C.len (exact sizing pass)
 };
 
 // update.cu

@@ -159,6 +159,10 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
 // arena tail.  Returns -1 when the tail is exhausted: the status bit makes
 // the host rebuild C with more room and recompute R again.
 __device__ __forceinline__ int64_t c_row_dest(const MatView &C, const CJob &J, Ctl *ctl, int32_t i, int n) {
+    if (J.count_only) {  // exact sizing pass: record the length, write nothing
+        C.len[i] = n;
+        return -1;
+    }
     const int32_t cap = C.cap[i];
     if (J.static_mode || n <= cap) return C.off[i];
     const int32_t c = slack_cap(n, J.slack_min, J.slack_div);
@@ -434,10 +438,13 @@ k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned m
         for (int s = 0; s < K; s++)
             for (int q = 0; q < blen[s]; q++) scols[(start[s] + q) * TM_NT] = B.col[boff[s] + q];
         const int64_t off = C.off[i];
-        const int cap = J.static_mode ? 0x7fffffff : C.cap[i];
+        const int cap = J.count_only ? 0 : (J.static_mode ? 0x7fffffff : C.cap[i]);
         const int n = merge_rows_smem<SR, K>(scols, Bv, av, boff, start, blen, alen, C.col + off, Cv + off, cap);
         bool ok = true;
-        if (n > cap) {
+        if (J.count_only) {
+            C.len[i] = n;
+            ok = false;
+        } else if (n > cap) {
             const int64_t d = c_row_dest(C, J, ctl, i, n);
             if (d >= 0) merge_rows_smem<SR, K>(scols, Bv, av, boff, start, blen, alen, C.col + d, Cv + d, n);
             else ok = false;
@@ -868,7 +875,8 @@ static void launch_group_hash(const MatView &A, const MatView &B, const MatView 
     int per_sm = (int)((200 * 1024) / (smem + 1024));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2048 / (NW * 32)) per_sm = 2048 / (NW * 32);
-    launch_k(k_num_group_hash<SR, LOG_TS, G, NW>, num_sms * per_sm, NW * 32, smem, s, A, B, C, J, ctl, mask, bin);
+    launch_k(k_num_group_hash<SR, LOG_TS, G, NW>, num_sms * per_sm, NW * 32, smem, s, A, B,
+             C, J, ctl, mask, bin);
 }
 
 template <int SR, int LOG_TS>
@@ -885,7 +893,8 @@ static void launch_cta_hash(const MatView &A, const MatView &B, const MatView &C
     int per_sm = (int)((200 * 1024) / (smem + 8 * 1024));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 8) per_sm = 8;
-    launch_k(k_num_cta_hash<SR, LOG_TS>, num_sms * per_sm, 256, smem, s, A, B, C, J, ctl, mask, bin);
+    launch_k(k_num_cta_hash<SR, LOG_TS>, num_sms * per_sm, 256, smem, s, A, B, C, J, ctl,
+             mask, bin);
 }
 
 // The bin kernels are independent; they are spread over the given streams
@@ -906,8 +915,8 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
             set_m = true;
         }
         const int per_sm = (int)std::min<size_t>(8, std::max<size_t>(1, (200 * 1024) / (smem_m + 1024)));
-        launch_k(k_num_thread_merge<SR, MERGE_K, MERGE_UB>, num_sms * per_sm, TM_NT, smem_m, next(), A, B, C, J, ctl,
-                 mask, (int)BIN_T8);
+        launch_k(k_num_thread_merge<SR, MERGE_K, MERGE_UB>, num_sms * per_sm, TM_NT,
+                 smem_m, next(), A, B, C, J, ctl, mask, (int)BIN_T8);
     }
     if (J.dense_mode) {
         const int mp = (int)((J.m + 31) / 32 * 32);
@@ -918,10 +927,11 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
             cudaFuncSetAttribute(k_num_warp_dense<SR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
             set_w = true;
         }
-        launch_k(k_num_warp_dense<SR, NW>, num_sms * 4, NW * 32, smem_w, next(), A, B, C, J, ctl, mask,
-                 (int)BIN_WDENSE, mp);
+        launch_k(k_num_warp_dense<SR, NW>, num_sms * 4, NW * 32, smem_w, next(), A, B, C, J,
+                 ctl, mask, (int)BIN_WDENSE, mp);
         const size_t smem_c = (size_t)mp * sizeof(T) + 32 * sizeof(uint32_t);
-        launch_k(k_num_cta_dense<SR>, num_sms, 512, smem_c, next(), A, B, C, J, ctl, mask, (int)BIN_CDENSE, mp);
+        launch_k(k_num_cta_dense<SR>, num_sms, 512, smem_c, next(), A, B, C, J, ctl, mask,
+                 (int)BIN_CDENSE, mp);
         return;
     }
     launch_group_hash<SR, 6, 16, 8>(A, B, C, J, ctl, mask, BIN_G16, next(), num_sms);

@@ -47,7 +47,7 @@ class _Upd(C.Structure):
 
 class _Opt(C.Structure):
     _fields_ = [("slack_min", C.c_int32), ("slack_div", C.c_int32), ("arena_headroom", C.c_double),
-                ("keep_transpose", C.c_int32)]
+                ("keep_transpose", C.c_int32), ("exact_static", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -155,7 +155,7 @@ class DynamicSpGEMM:
     C = A A with one batch updating both operands."""
 
     def __init__(self, A, B=None, semiring: int | None = None, slack_min: int = 4, slack_div: int = 4,
-                 arena_headroom: float = 1.5, keep_transpose: int = -1, stream=None):
+                 arena_headroom: float = 1.5, keep_transpose: int = -1, exact_static: int = 0, stream=None):
         self._lib = load()
         self._h = C.c_void_p()
         if semiring is None:
@@ -164,7 +164,7 @@ class DynamicSpGEMM:
         keep: list = []
         ca = self._csr(A, keep)
         cb = self._csr(B, keep) if B is not None else None
-        opt = _Opt(slack_min, slack_div, arena_headroom, keep_transpose)
+        opt = _Opt(slack_min, slack_div, arena_headroom, keep_transpose, exact_static)
         st = self._lib.dspg_build(C.byref(self._h), C.byref(ca), C.byref(cb) if cb is not None else None,
                                   semiring, C.byref(opt), _stream(stream))
         if st != 0:

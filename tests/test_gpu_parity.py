@@ -323,3 +323,19 @@ def test_graph_and_eager_agree_minplus(dspg):
     c1, c2 = g1.read_C(), g2.read_C()
     assert np.array_equal(c1.rowptr, c2.rowptr) and np.array_equal(c1.col, c2.col)
     assert np.array_equal(c1.val, c2.val)
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_exact_two_pass_static_layout(dspg, sr):
+    """The static product laid out from exact row counts (count pass, then
+    write pass) gives the same C, and later batches still match."""
+    A, _ = rmat_symmetric(11, 8, (0.57, 0.19, 0.19, 0.05), seed=9, kind=sr)
+    g = dspg.DynamicSpGEMM(A, exact_static=1)
+    Ao = OMat.from_csr(A)
+    _check_state(g, Ao, None, "exact static")
+    Co = Ao.multiply(Ao)
+    b = random_batch(A.nrows, A.ncols, 500, 19, sr, A=A)
+    _apply_both(g, Ao, Co, b)
+    _check_state(g, Ao, None, "exact static + batch")
+    g.recompute_all()
+    _check_state(g, Ao, None, "exact static recompute")
