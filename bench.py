@@ -286,6 +286,206 @@ def gpu_arm(args):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------- batched instances (group)
+
+G500 = (0.57, 0.19, 0.19, 0.05)
+
+
+def batched_instances(count, seed=4):
+    """The batched workload: `count` independent R-MAT instances (scale 10..16
+    uniform, edge factor 8, Graph500 parameters), (+,.) f64 U(0,1) for even t
+    and (min,+) int32 U[1,100] for odd t, C = A A; one batch size per
+    instance, log-uniform in 10..10^4 undirected-edge changes (insertions of
+    held-out edges, drawn with replacement when the batch wants more than the
+    pool holds, and deletions of present edges)."""
+    from workloads import MIN_PLUS_I32, PLUS_TIMES_F64, rmat_symmetric
+    rng = np.random.default_rng(seed)
+    scales = rng.integers(10, 17, size=count)
+    sizes = np.floor(10 ** rng.uniform(1, 4, size=count)).astype(np.int64)
+    out = []
+    for t in range(count):
+        sr = PLUS_TIMES_F64 if t % 2 == 0 else MIN_PLUS_I32
+        pool = int(min(max(16, sizes[t]), (8 << int(scales[t])) // 20))  # at most ~5% of the edges held out
+        A, held = rmat_symmetric(int(scales[t]), 8, G500, seed=1000 * seed + t, kind=sr, holdout=pool)
+        out.append({"A": A, "held": held, "size": int(sizes[t]), "scale": int(scales[t]), "sr": sr})
+    return out
+
+
+def batched_batches(insts, step, device=True):
+    import torch
+    from workloads import rmat_edge_batch
+    bs = []
+    for t, it in enumerate(insts):
+        b = rmat_edge_batch(it["A"], it["held"], it["size"], seed=7919 * (step + 1) + t)
+        if device:
+            b = type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(), torch.from_numpy(b.val).cuda(),
+                        torch.from_numpy(b.op).cuda())
+        bs.append(b)
+    return bs
+
+
+def batched_arm(args):
+    import torch
+    import paper_2202_08808_gb300 as pkg
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    count = args.instances
+    t0 = time.perf_counter()
+    insts = batched_instances(count, seed=4)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hs = [pkg.DynamicSpGEMM(it["A"], exact_static=1) for it in insts]
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    nnz_c = sum(h.info()["nnz_c"] for h in hs)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    step_no = [0]
+
+    def next_batches(device=True):
+        step_no[0] += 1
+        return batched_batches(insts, step_no[0], device)
+
+    def time_group(grp, steps, warmup, collect=None):
+        for _ in range(warmup):
+            grp.apply(next_batches())
+        torch.cuda.synchronize()
+        pre = [next_batches() for _ in range(steps)]
+        ms = []
+        k0 = pkg.kernel_launches()
+        for k in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats, _ = grp.apply(pre[k])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            if collect is not None:
+                collect.append(stats)
+        return ms, pkg.kernel_launches() - k0
+
+    grp = pkg.Group(hs)
+    default_ms, _ = time_group(grp, args.steps, args.warmup)
+
+    # autotune every instance on two calibration batches of its own size
+    t0 = time.perf_counter()
+    chosen = {}
+    for t, h in enumerate(hs):
+        cal = [batched_batches([insts[t]], 100000 + 2 * t + j)[0] for j in range(2)]
+        best, _ = h.autotune(cal)
+        key = tuple(best.values())
+        chosen[key] = chosen.get(key, 0) + 1
+    tune_s = time.perf_counter() - t0
+    cands = [tuple(c.values()) for c in pkg.tuning_candidates()]
+
+    stats_acc = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    wall0 = time.perf_counter()
+    tuned_ms, launches = time_group(grp, args.steps, args.warmup, stats_acc)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+
+    # the same instances as separate apply_batch calls, one after another
+    for _ in range(args.warmup):
+        for h, b in zip(hs, next_batches()):
+            h.apply_batch(b)
+    torch.cuda.synchronize()
+    sep_ms = []
+    for k in range(args.steps):
+        bs = next_batches()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for h, b in zip(hs, bs):
+            h.apply_batch(b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sep_ms.append(e0.elapsed_time(e1))
+
+    # end to end with pinned host batches through the group call
+    e2e_ms, h2d = [], 0
+    for k in range(max(3, min(args.steps, 5))):
+        hb = [type(b)(torch.from_numpy(b.row).pin_memory(), torch.from_numpy(b.col).pin_memory(),
+                      torch.from_numpy(b.val).pin_memory(), torch.from_numpy(b.op).pin_memory())
+              for b in next_batches(device=False)]
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats, _ = grp.apply(hb)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        h2d = sum(len(b.row) * (4 + 4 + b.val.element_size() + 1) for b in hb)
+    d2h = count * 13 * 8  # per-member statistics read back
+
+    med = statistics.median(tuned_ms)
+    R = sum(st["affected_rows"] for ss in stats_acc for st in ss) / len(stats_acc)
+    alg = 0.0
+    for ss in stats_acc:
+        for t, st in enumerate(ss):
+            se = 12 if insts[t]["sr"] == 0 else 8
+            alg += 12 * st["affected_rows"] + (se + 12) * st["a_entries"] + se * st["products"] + se * st["nnz_written"]
+    alg /= len(stats_acc)
+    peak, peak_kind = peaks()
+    achieved = alg / (statistics.mean(tuned_ms) * 1e-3) / 1e9
+    cpu = None if args.no_cpu else batched_cpu_baseline(insts, args.cpu_budget)
+    out = {
+        "metric": METRIC,
+        "value": round(world * count * args.steps / (sum(tuned_ms) * 1e-3), 1),
+        "unit": "instance batches/s (256 instances per step)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(statistics.mean(tuned_ms), 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+i32", "data": "synthetic",
+        "config": {"workload": f"batched: {count} R-MAT instances, scales 10-16, edge factor 8, C = A A, half (+,.) f64 "
+                               "half (min,+) i32, one batch each of 10..10^4 edge changes (log-uniform)",
+                   "nnz_c_total": int(nnz_c), "batch_entries_per_step": int(2 * sum(it["size"] for it in insts)),
+                   "l2": "flushed before every timed step (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": round(med, 4), "p99": round(float(np.percentile(tuned_ms, 99)), 4)},
+        "group_default_tuning_ms": round(statistics.median(default_ms), 4),
+        "group_tuned_ms": round(med, 4),
+        "separate_calls_ms": round(statistics.median(sep_ms), 4),
+        "speedup_group_vs_separate": round(statistics.median(sep_ms) / med, 2),
+        "autotune": {"seconds": round(tune_s, 2), "chosen": {str(cands.index(k)): v for k, v in chosen.items()}},
+        "affected_rows_per_step": int(R),
+        "roofline": {"bound": "hbm", "kernel": "whole group step (every stage of every instance)",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_kind": peak_kind, "alg_bytes_per_step": int(alg), "traffic": None},
+        "e2e": {"value": round(1e3 * count / statistics.mean(e2e_ms), 1), "unit": "instance batches/s",
+                "latency_ms": round(statistics.mean(e2e_ms), 4), "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches), "gpu_launches_per_step": round(launches / args.steps, 1),
+        "clocks": clk, "wall_s_timed": round(wall, 3),
+        "setup_s": {"generate": round(gen_s, 1), "build": round(build_s, 1)},
+        "cpu_baseline": cpu,
+    }
+    grp.close()
+    print(json.dumps(out), flush=True)
+
+
+def batched_cpu_baseline(insts, budget_s):
+    """The oracle's row-dynamic route on the instances of scale <= 12 of the
+    batched workload, one batch each, until the budget (set-up included) is
+    used; single-threaded C."""
+    import oracle
+    from oracle import OMat
+    times, k, start = [], 0, time.perf_counter()
+    for t, it in enumerate(insts):
+        if it["scale"] > 12:
+            continue
+        Ao = OMat.from_csr(it["A"])
+        Co = Ao.multiply(Ao)
+        b = batched_batches([it], 500000 + t, device=False)[0]
+        t0 = time.perf_counter()
+        oracle.row_dynamic(Ao, Co, b)
+        times.append(time.perf_counter() - t0)
+        k += 1
+        if time.perf_counter() - start > budget_s:
+            break
+    mean = statistics.mean(times)
+    return {"value": round(1.0 / mean, 3), "unit": "instance batches/s", "cores": 1, "kind": "oracle",
+            "sample": f"one batch on each of {k} instances of scale <= 12 (apply + affected rows + row recompute)"}
+
+
 # ------------------------------------------------------------ CPU oracle
 
 def cpu_baseline(args, budget_s=20.0, steps=None):
@@ -375,6 +575,9 @@ def main():
     ap.add_argument("--profile", choices=["step", "static"], default=None,
                     help="run one NVTX-marked step or static recompute for ncu, then exit")
     ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--workload", choices=["stencil", "batched"], default="stencil",
+                    help="stencil: the 128^3 stencil with 10^4-update batches; batched: 256 R-MAT instances")
+    ap.add_argument("--instances", type=int, default=256)
     args = ap.parse_args()
     if args.profile:
         profile_arm(args)
@@ -383,6 +586,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "batched":
+        batched_arm(args)
     else:
         gpu_arm(args)
 

@@ -182,6 +182,78 @@ dspg_status dspg_stage_times(dspg_handle *h, float *ms, int n);
  * handles), for auditing how many launches a call makes. */
 unsigned long long dspg_kernel_launches(void);
 
+/* Row bins of the recompute.  Section 6.1 fixes only that each row is formed
+ * in a sparse accumulator; which accumulator serves which row is this
+ * library's choice.  A row of R is binned by its product bound ub (the sum of
+ * the lengths of the B rows it reads, capped at the column count):
+ *  - thread merge: A rows with at most merge_k entries and ub <= merge_ub
+ *    (merge_k in 0..8, merge_ub in 0..64; 0 turns the bin off);
+ *  - hash tables in shared memory of at least ub << table_shift slots
+ *    (table_shift 0 or 1), served by 8, 16 or 32 lanes per row while the
+ *    table has at most 32, 64 or warp_max slots (lanes_min = 8, 16 or 32:
+ *    the fewest lanes a row may get; warp_max in 0..1024), then by a whole
+ *    CTA while it has at most cta_max slots (0..8192);
+ *  - longer rows: a CTA with a dense accumulator in global memory.
+ * Every setting gives the same C: a table never has fewer slots than the
+ * row's bound, which no row's distinct columns can exceed.  Only the speed
+ * changes.  C with at most 1024 columns uses dense shared-memory
+ * accumulators for all rows outside the thread-merge bin instead. */
+typedef struct {
+    int32_t merge_k, merge_ub;
+    int32_t lanes_min;
+    int32_t table_shift;
+    int32_t warp_max;
+    int32_t cta_max;
+} dspg_tuning;
+
+/* Set (t == NULL: restore the defaults {8, 64, 8, 0, 1024, 8192}) or read
+ * the tuning of h.  Out-of-range fields return DSPG_ERR_INVALID. */
+dspg_status dspg_set_tuning(dspg_handle *h, const dspg_tuning *t);
+dspg_status dspg_get_tuning(dspg_handle *h, dspg_tuning *t);
+
+/* Choose the tuning of h by measurement.  Each of the nbatches batches
+ * (updates of A; of B too when dB != NULL, as arrays of nbatches) is applied
+ * in full, in order, as by dspg_apply_batch: they are real updates.  After
+ * each, the recompute of its affected rows (sizing and numeric stages) is
+ * replayed once under every candidate of a built-in list of tunings, in a
+ * rotating order, and timed on the device; replaying rewrites the same rows
+ * of C from the same A', B'.  The candidate with the least total time is set
+ * on h and written to *best (may be NULL); ms[k] (room for n_ms entries, may
+ * be NULL) receives candidate k's total and *n_cand the list's length. */
+dspg_status dspg_autotune(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, int64_t nbatches,
+                          dspg_tuning *best, float *ms, int n_ms, int *n_cand, void *stream);
+
+/* The k-th built-in candidate tuning (k < *n_cand of dspg_autotune). */
+dspg_status dspg_tuning_candidate(int k, dspg_tuning *t);
+
+/* A group of independent handles whose batches are applied together: every
+ * handle's whole pipeline is enqueued as one branch of a single CUDA graph,
+ * so one graph launch runs all of them and their kernels overlap on the
+ * device.  The paper distributes one product over many processes; a group
+ * instead packs many small, unrelated products onto one GPU (no counterpart
+ * in the paper).  handles[n]: distinct handles on the current device; they
+ * must outlive the group, and a handle may belong to several groups.  The
+ * group keeps its graphs keyed by every member's batch sizes and buffers: the
+ * first apply of a key runs eagerly (branches on the members' own streams),
+ * the second captures the graph, later ones replay it. */
+typedef struct dspg_group dspg_group;
+dspg_status dspg_group_create(dspg_group **out, dspg_handle *const *handles, int64_t n);
+
+/* Apply dA[t] (and dB[t] when dB != NULL) to member t, for every t, as
+ * dspg_apply_batch would one by one; a NULL or empty batch leaves its member
+ * as it is.  stats and status may be NULL, else arrays of n: per-member
+ * statistics and status.  Members whose run needs more memory are grown and
+ * re-run eagerly after the graph.  Returns DSPG_OK when every member
+ * succeeded, else the first failing member's status (its message is in
+ * dspg_last_error of the group and of the member); the others are applied.
+ * Synchronises the stream. */
+dspg_status dspg_group_apply(dspg_group *g, const dspg_updates *dA, const dspg_updates *dB,
+                             dspg_batch_stats *stats, dspg_status *status, void *stream);
+
+/* Free the group (not its handles). */
+void dspg_group_destroy(dspg_group *g);
+const char *dspg_group_last_error(const dspg_group *g);
+
 /* Rows of C = A B for callers that cannot let a library allocate device
  * memory: their memory belongs to another allocator (a framework's caching
  * pool, an arena fixed at start-up), or their latency budget cannot absorb

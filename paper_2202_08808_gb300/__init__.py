@@ -18,8 +18,11 @@ from .dspg import (  # noqa: F401
     CsrArrays,
     DspgError,
     DynamicSpGEMM,
+    Group,
+    TUNING_FIELDS,
     kernel_launches,
     library_path,
     multiply_rows_noalloc,
+    tuning_candidates,
     load,
 )

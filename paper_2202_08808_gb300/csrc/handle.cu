@@ -237,10 +237,26 @@ struct dspg_handle {
     std::vector<Graph> seen;  // keys run once eagerly (exec unused)
     uint64_t epoch = 1;       // bumped whenever a persistent buffer moves
     bool use_graphs = true;
+    dspg_tuning tune{8, 64, 8, 0, 1024, 8192};  // row bins of the recompute
     int64_t compactions = 0;
     std::string err;
 
     DevMat &Bm() { return b_is_a ? A : B; }
+};
+
+// A group: the members' pipelines as branches of one graph.
+struct dspg_group {
+    std::vector<dspg_handle *> hs;
+    cudaStream_t gs = nullptr;  // graphs run here
+    cudaEvent_t evIn = nullptr, evFork = nullptr;
+    struct Graph {
+        std::vector<int64_t> key;  // per member: nA, nB, buffer epoch
+        cudaGraphExec_t exec;
+        unsigned long long kernels;
+    };
+    std::vector<Graph> graphs;
+    std::vector<std::vector<int64_t>> seen;
+    std::string err;
 };
 
 namespace {
@@ -393,6 +409,13 @@ CJob c_job(dspg_handle *h, const int32_t *R, bool static_mode) {
     J.slack_min = h->opt.slack_min;
     J.slack_div = h->opt.slack_div;
     J.bmR = w.bmR.p;
+    J.rows_hint = h->A.nrows;
+    J.tm_k = h->tune.merge_k;
+    J.tm_ub = h->tune.merge_ub;
+    J.lanes_min = h->tune.lanes_min;
+    J.table_shift = h->tune.table_shift;
+    J.warp_max = h->tune.warp_max;
+    J.cta_max = h->tune.cta_max;
     return J;
 }
 
@@ -960,6 +983,74 @@ void fill_stats(dspg_handle *h, dspg_batch_stats *stats, int64_t compactions0) {
     }
 }
 
+
+// One batch on one handle, as dspg_apply_batch (errors as exceptions).
+void apply_one(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, dspg_batch_stats *stats,
+               cudaStream_t s) {
+    prepare_batch(h, dA, dB, s);
+    const int64_t compactions0 = h->compactions;
+    run_first(h, s);
+    if (h->prof) stage_times_from_events(h);
+    recover(h, s);
+    fill_stats(h, stats, compactions0);
+}
+
+// Captures what body() enqueues on cs into an executable graph; the number
+// of kernels it launched goes to *nk.  The capture is closed on errors.
+template <typename F>
+cudaGraphExec_t capture_graph(cudaStream_t cs, unsigned long long *nk, F body) {
+    cudaGraph_t graph = nullptr;
+    const unsigned long long k0 = launch_counter();
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+        body();
+    } catch (...) {
+        cudaStreamEndCapture(cs, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        throw;
+    }
+    CK(cudaStreamEndCapture(cs, &graph));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    if (nk) *nk = launch_counter() - k0;
+    return exec;
+}
+
+void check_tuning(const dspg_tuning &t) {
+    if (t.merge_k < 0 || t.merge_k > 8 || t.merge_ub < 0 || t.merge_ub > 64)
+        throw Err(DSPG_ERR_INVALID, "tuning: merge_k must be in 0..8 and merge_ub in 0..64");
+    if (t.lanes_min != 8 && t.lanes_min != 16 && t.lanes_min != 32)
+        throw Err(DSPG_ERR_INVALID, "tuning: lanes_min must be 8, 16 or 32");
+    if (t.table_shift < 0 || t.table_shift > 1) throw Err(DSPG_ERR_INVALID, "tuning: table_shift must be 0 or 1");
+    if (t.warp_max < 0 || t.warp_max > 1024 || t.cta_max < 0 || t.cta_max > 8192)
+        throw Err(DSPG_ERR_INVALID, "tuning: warp_max must be in 0..1024 and cta_max in 0..8192");
+}
+
+// The autotuner's candidates: the defaults first, then one or two changes
+// each (thread-merge reach, lanes per short row, table oversizing, the
+// warp/CTA and CTA/global crossovers).
+const dspg_tuning kCandidates[] = {
+    {8, 64, 8, 0, 1024, 8192}, {0, 0, 8, 0, 1024, 8192},  {4, 32, 8, 0, 1024, 8192}, {8, 64, 16, 0, 1024, 8192},
+    {8, 64, 32, 0, 1024, 8192}, {8, 64, 8, 1, 1024, 8192}, {8, 64, 8, 0, 512, 8192},  {8, 64, 8, 0, 1024, 4096},
+    {8, 64, 8, 0, 1024, 2048}, {8, 64, 8, 1, 512, 4096},  {0, 0, 16, 1, 1024, 8192},
+};
+constexpr int kNumCandidates = (int)(sizeof(kCandidates) / sizeof(kCandidates[0]));
+
+// The recompute of the last batch's affected rows (sizing + numeric), as
+// a graph on the handle's stream, under the handle's current tuning.
+cudaGraphExec_t capture_recompute(dspg_handle *h) {
+    return capture_graph(h->gs, nullptr, [&] {
+        reset_c_counters(h, h->gs);
+        reset_range(h, &h->ctl->status, sizeof(unsigned), h->gs);
+        stage_size(h, h->gs);
+        stage_numeric(h, h->gs);
+        cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->gs);
+    });
+}
+
 }  // namespace
 
 // ================================================================ C ABI
@@ -1030,14 +1121,8 @@ dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, 
 dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
                              dspg_batch_stats *stats, void *stream) {
     if (!h) return DSPG_ERR_INVALID;
-    cudaStream_t s = (cudaStream_t)stream;
     try {
-        prepare_batch(h, dA, dB, s);
-        const int64_t compactions0 = h->compactions;
-        run_first(h, s);
-        if (h->prof) stage_times_from_events(h);
-        recover(h, s);
-        fill_stats(h, stats, compactions0);
+        apply_one(h, dA, dB, stats, (cudaStream_t)stream);
         return DSPG_OK;
     } catch (const Err &e) {
         return fail(h, e);
@@ -1158,6 +1243,238 @@ dspg_status dspg_stage_times(dspg_handle *h, float *ms, int n) {
 }
 
 unsigned long long dspg_kernel_launches(void) { return __atomic_load_n(&launch_counter(), __ATOMIC_RELAXED); }
+
+dspg_status dspg_tuning_candidate(int k, dspg_tuning *t) {
+    if (k < 0 || k >= kNumCandidates || !t) return DSPG_ERR_INVALID;
+    *t = kCandidates[k];
+    return DSPG_OK;
+}
+
+dspg_status dspg_set_tuning(dspg_handle *h, const dspg_tuning *t) {
+    if (!h) return DSPG_ERR_INVALID;
+    try {
+        const dspg_tuning v = t ? *t : kCandidates[0];
+        check_tuning(v);
+        h->tune = v;
+        h->epoch++;  // captured pipelines carry the old bins
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_get_tuning(dspg_handle *h, dspg_tuning *t) {
+    if (!h || !t) return DSPG_ERR_INVALID;
+    *t = h->tune;
+    return DSPG_OK;
+}
+
+dspg_status dspg_autotune(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, int64_t nbatches,
+                          dspg_tuning *best, float *ms, int n_ms, int *n_cand, void *stream) {
+    if (!h) return DSPG_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<cudaGraphExec_t> execs(kNumCandidates, nullptr);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const dspg_tuning keep = h->tune;
+    auto cleanup = [&] {
+        for (auto &x : execs)
+            if (x) cudaGraphExecDestroy(x);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    try {
+        if (nbatches < 0 || (nbatches > 0 && !dA)) throw Err(DSPG_ERR_INVALID, "autotune needs nbatches >= 0 batches");
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        std::vector<double> tot(kNumCandidates, 0.0);
+        std::vector<uint64_t> epochs(kNumCandidates, 0);
+        for (int64_t b = 0; b < nbatches; b++) {
+            h->tune = keep;
+            apply_one(h, dA + b, dB ? dB + b : nullptr, nullptr, s);
+            if (h->last_nR == 0) continue;
+            CK(cudaEventRecord(h->evIn, s));
+            CK(cudaStreamWaitEvent(h->gs, h->evIn, 0));
+            for (int j = 0; j < kNumCandidates; j++) {
+                const int c = (int)((b + j) % kNumCandidates);
+                h->tune = kCandidates[c];
+                if (!execs[c] || epochs[c] != h->epoch) {
+                    if (execs[c]) cudaGraphExecDestroy(execs[c]);
+                    execs[c] = capture_recompute(h);
+                    epochs[c] = h->epoch;
+                }
+                CK(cudaEventRecord(e0, h->gs));
+                CK(cudaGraphLaunch(execs[c], h->gs));
+                CK(cudaEventRecord(e1, h->gs));
+                CK(cudaStreamSynchronize(h->gs));
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, e0, e1));
+                tot[c] += t;
+                if (h->hctl->status) recover(h, h->gs);
+            }
+            CK(cudaEventRecord(h->evIn, h->gs));
+            CK(cudaStreamWaitEvent(s, h->evIn, 0));
+        }
+        int bi = 0;
+        for (int c = 1; c < kNumCandidates; c++)
+            if (tot[c] < tot[bi]) bi = c;
+        h->tune = kCandidates[bi];
+        h->epoch++;
+        if (best) *best = h->tune;
+        for (int c = 0; c < kNumCandidates && ms && c < n_ms; c++) ms[c] = (float)tot[c];
+        if (n_cand) *n_cand = kNumCandidates;
+        cleanup();
+        return DSPG_OK;
+    } catch (const Err &e) {
+        h->tune = keep;
+        h->epoch++;
+        cleanup();
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_group_create(dspg_group **out, dspg_handle *const *handles, int64_t n) {
+    dspg_group *g = nullptr;
+    try {
+        if (!out) throw Err(DSPG_ERR_INVALID, "out is NULL");
+        *out = nullptr;
+        if (n < 0 || (n > 0 && !handles)) throw Err(DSPG_ERR_INVALID, "group needs n >= 0 handles");
+        std::vector<dspg_handle *> hs(handles, handles + n);
+        for (int64_t t = 0; t < n; t++) {
+            if (!hs[t]) throw Err(DSPG_ERR_INVALID, "group member " + std::to_string(t) + " is NULL");
+            for (int64_t u = 0; u < t; u++)
+                if (hs[u] == hs[t]) throw Err(DSPG_ERR_INVALID, "group member " + std::to_string(t) + " repeats member " + std::to_string(u));
+        }
+        g = new dspg_group();
+        g->hs = std::move(hs);
+        CK(cudaStreamCreateWithFlags(&g->gs, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&g->evIn, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&g->evFork, cudaEventDisableTiming));
+        *out = g;
+        return DSPG_OK;
+    } catch (const Err &e) {
+        g_err = e.what();
+        dspg_group_destroy(g);
+        return e.st;
+    }
+}
+
+dspg_status dspg_group_apply(dspg_group *g, const dspg_updates *dA, const dspg_updates *dB,
+                             dspg_batch_stats *stats, dspg_status *status, void *stream) {
+    if (!g) return DSPG_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = g->hs.size();
+    try {
+        if (n > 0 && !dA) throw Err(DSPG_ERR_INVALID, "dA is NULL");
+        // host-side checks and uploads for every member before anything runs
+        std::vector<int64_t> key;
+        std::vector<int64_t> comp0(n);
+        key.reserve(3 * n);
+        for (size_t t = 0; t < n; t++) {
+            dspg_handle *h = g->hs[t];
+            try {
+                prepare_batch(h, dA + t, dB ? dB + t : nullptr, s);
+            } catch (const Err &e) {
+                h->err = e.what();
+                throw Err(e.st, "member " + std::to_string(t) + ": " + e.what());
+            }
+            comp0[t] = h->compactions;
+            key.push_back(h->inA.n);
+            key.push_back(h->inB.n);
+            key.push_back((int64_t)h->epoch);
+        }
+        const bool use_graphs = n > 0 && g->hs[0]->use_graphs;
+        dspg_group::Graph *hit = nullptr;
+        for (auto &x : g->graphs)
+            if (x.key == key) hit = &x;
+        bool seen = false;
+        for (auto &k : g->seen) seen |= (k == key);
+        if (use_graphs && !hit && seen) {
+            unsigned long long nk = 0;
+            cudaGraphExec_t exec = capture_graph(g->gs, &nk, [&] {
+                CK(cudaEventRecord(g->evFork, g->gs));
+                for (dspg_handle *h : g->hs) {
+                    CK(cudaStreamWaitEvent(h->gs, g->evFork, 0));
+                    cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->gs);
+                    pipeline(h, h->gs, false, true);
+                    cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->gs);
+                    CK(cudaEventRecord(h->evIn, h->gs));
+                    CK(cudaStreamWaitEvent(g->gs, h->evIn, 0));
+                }
+            });
+            if (g->graphs.size() >= 4) {
+                cudaGraphExecDestroy(g->graphs.front().exec);
+                g->graphs.erase(g->graphs.begin());
+            }
+            // the capture counted the kernels once: that is this first replay
+            __atomic_fetch_sub(&launch_counter(), nk, __ATOMIC_RELAXED);
+            g->graphs.push_back(dspg_group::Graph{key, exec, nk});
+            hit = &g->graphs.back();
+        }
+        if (hit) {
+            CK(cudaEventRecord(g->evIn, s));
+            CK(cudaStreamWaitEvent(g->gs, g->evIn, 0));
+            CK(cudaGraphLaunch(hit->exec, g->gs));
+            __atomic_fetch_add(&launch_counter(), hit->kernels, __ATOMIC_RELAXED);
+            CK(cudaEventRecord(g->evIn, g->gs));
+            CK(cudaStreamWaitEvent(s, g->evIn, 0));
+            CK(cudaStreamSynchronize(g->gs));
+        } else {
+            if (use_graphs) {
+                if (g->seen.size() >= 8) g->seen.erase(g->seen.begin());
+                g->seen.push_back(key);
+            }
+            CK(cudaEventRecord(g->evFork, s));
+            for (dspg_handle *h : g->hs) {
+                CK(cudaStreamWaitEvent(h->gs, g->evFork, 0));
+                CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->gs));
+                pipeline(h, h->gs, false, false);
+                CK(cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->gs));
+                CK(cudaEventRecord(h->evIn, h->gs));
+                CK(cudaStreamWaitEvent(s, h->evIn, 0));
+            }
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(s));
+        }
+        // members that overflowed a buffer are grown and re-run one by one
+        dspg_status first = DSPG_OK;
+        g->err.clear();
+        for (size_t t = 0; t < n; t++) {
+            dspg_handle *h = g->hs[t];
+            dspg_status st = DSPG_OK;
+            try {
+                recover(h, s);
+                fill_stats(h, stats ? stats + t : nullptr, comp0[t]);
+            } catch (const Err &e) {
+                h->err = e.what();
+                st = e.st;
+                if (first == DSPG_OK) {
+                    first = st;
+                    g->err = "member " + std::to_string(t) + ": " + e.what();
+                }
+                if (st == DSPG_ERR_CUDA) throw;
+            }
+            if (status) status[t] = st;
+        }
+        return first;
+    } catch (const Err &e) {
+        g->err = e.what();
+        if (status)
+            for (size_t t = 0; t < n; t++) status[t] = e.st;
+        return e.st;
+    }
+}
+
+void dspg_group_destroy(dspg_group *g) {
+    if (!g) return;
+    if (g->gs) cudaStreamSynchronize(g->gs);
+    for (auto &x : g->graphs) cudaGraphExecDestroy(x.exec);
+    if (g->evIn) cudaEventDestroy(g->evIn);
+    if (g->evFork) cudaEventDestroy(g->evFork);
+    if (g->gs) cudaStreamDestroy(g->gs);
+    delete g;
+}
+
+const char *dspg_group_last_error(const dspg_group *g) { return g ? g->err.c_str() : g_err.c_str(); }
 
 void dspg_destroy(dspg_handle *h) {
     if (!h) return;

@@ -77,6 +77,10 @@ struct CJob {
     int slack_min, slack_div;
     uint32_t *bmR;            // affected-row bitmap, cleared by the sizing pass (dynamic mode)
     int count_only;           // 1: only count each row's entries into C.len (exact sizing pass)
+    int64_t rows_hint;        // upper bound on the rows to recompute (caps the grids)
+    // row-bin thresholds (dspg_tuning): thread-merge limits, smallest hash
+    // executor, table oversizing, warp/CTA and CTA/global crossovers
+    int tm_k, tm_ub, lanes_min, table_shift, warp_max, cta_max;
 };
 
 // update.cu

@@ -71,20 +71,27 @@ __device__ __forceinline__ long long atomic_add_ll2(long long *p, long long v) {
 constexpr int MERGE_K = 8;      // A rows up to this length can be merged by one thread
 constexpr int MERGE_UB = 64;    // ... when their product bound is at most this
 
-__device__ __forceinline__ int pick_bin(long long ubc, int alen, int dense_mode) {
-    if (alen <= MERGE_K && ubc <= MERGE_UB) return BIN_T8;
-    if (dense_mode) return ubc <= 4096 ? BIN_WDENSE : BIN_CDENSE;
-    // a row's distinct columns never exceed its bound, so a table of the
-    // next power of two at or above the bound cannot overflow
-    if (ubc <= 32) return BIN_G8;
-    if (ubc <= 64) return BIN_G16;
-    if (ubc <= 128) return BIN_W128;
-    if (ubc <= 256) return BIN_W256;
-    if (ubc <= 512) return BIN_W512;
-    if (ubc <= 1024) return BIN_W1024;
-    if (ubc <= 2048) return BIN_C2048;
-    if (ubc <= 4096) return BIN_C4096;
-    if (ubc <= 8192) return BIN_C8192;
+// The bin of a row from its capped bound and A-row length.  The thresholds
+// come from the job (the tuning); a hash table is never smaller than the
+// bound, since a row's distinct columns never exceed it, so no choice of
+// thresholds can make a table overflow.
+__device__ __forceinline__ int pick_bin(long long ubc, int alen, const CJob &J) {
+    if (alen <= J.tm_k && ubc <= J.tm_ub) return BIN_T8;
+    if (J.dense_mode) return ubc <= 4096 ? BIN_WDENSE : BIN_CDENSE;
+    const long long need = ubc << J.table_shift;
+    if (need <= 32 && J.lanes_min <= 8) return BIN_G8;
+    if (need <= 64 && J.lanes_min <= 16) return BIN_G16;
+    if (need <= J.warp_max) {
+        if (need <= 128) return BIN_W128;
+        if (need <= 256) return BIN_W256;
+        if (need <= 512) return BIN_W512;
+        return BIN_W1024;
+    }
+    if (need <= J.cta_max) {
+        if (need <= 2048) return BIN_C2048;
+        if (need <= 4096) return BIN_C4096;
+        return BIN_C8192;
+    }
     return BIN_GD;
 }
 
@@ -134,7 +141,7 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
             J.bmR[i >> 5] = 0u;  // the detection marks are not needed any more
             if (ub == 0) C.len[i] = 0;  // no products: the row becomes empty
         }
-        const int b = (valid && ub > 0) ? pick_bin(ubc, alen, J.dense_mode) : -1;
+        const int b = (valid && ub > 0) ? pick_bin(ubc, alen, J) : -1;
         const unsigned peers = __match_any_sync(0xffffffffu, b);
         const int leader = __ffs(peers) - 1;
         long long bb = 0;
@@ -859,6 +866,13 @@ void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const C
     launch_k(k_size_bins, (unsigned)g, 256, 0, s, A, B, C, J, ctl, mask);
 }
 
+// A persistent grid of `full` blocks, but no more blocks than it takes for
+// `rows` rows at `per_block` rows per block (small matrices launch small).
+static unsigned grid_for(int64_t full, int64_t rows, int64_t per_block) {
+    const int64_t need = (std::max<int64_t>(rows, 1) + per_block - 1) / per_block;
+    return (unsigned)std::max<int64_t>(1, std::min(full, need));
+}
+
 template <int SR, int LOG_TS, int G, int NW>
 static void launch_group_hash(const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl,
                               unsigned mask, int bin, cudaStream_t s, int num_sms) {
@@ -875,7 +889,7 @@ static void launch_group_hash(const MatView &A, const MatView &B, const MatView 
     int per_sm = (int)((200 * 1024) / (smem + 1024));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2048 / (NW * 32)) per_sm = 2048 / (NW * 32);
-    launch_k(k_num_group_hash<SR, LOG_TS, G, NW>, num_sms * per_sm, NW * 32, smem, s, A, B,
+    launch_k(k_num_group_hash<SR, LOG_TS, G, NW>, grid_for(num_sms * per_sm, J.rows_hint, NG), NW * 32, smem, s, A, B,
              C, J, ctl, mask, bin);
 }
 
@@ -893,7 +907,7 @@ static void launch_cta_hash(const MatView &A, const MatView &B, const MatView &C
     int per_sm = (int)((200 * 1024) / (smem + 8 * 1024));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 8) per_sm = 8;
-    launch_k(k_num_cta_hash<SR, LOG_TS>, num_sms * per_sm, 256, smem, s, A, B, C, J, ctl,
+    launch_k(k_num_cta_hash<SR, LOG_TS>, grid_for(num_sms * per_sm, J.rows_hint, 1), 256, smem, s, A, B, C, J, ctl,
              mask, bin);
 }
 
@@ -915,7 +929,7 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
             set_m = true;
         }
         const int per_sm = (int)std::min<size_t>(8, std::max<size_t>(1, (200 * 1024) / (smem_m + 1024)));
-        launch_k(k_num_thread_merge<SR, MERGE_K, MERGE_UB>, num_sms * per_sm, TM_NT,
+        launch_k(k_num_thread_merge<SR, MERGE_K, MERGE_UB>, grid_for(num_sms * per_sm, J.rows_hint, TM_NT), TM_NT,
                  smem_m, next(), A, B, C, J, ctl, mask, (int)BIN_T8);
     }
     if (J.dense_mode) {
@@ -927,10 +941,10 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
             cudaFuncSetAttribute(k_num_warp_dense<SR, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
             set_w = true;
         }
-        launch_k(k_num_warp_dense<SR, NW>, num_sms * 4, NW * 32, smem_w, next(), A, B, C, J,
+        launch_k(k_num_warp_dense<SR, NW>, grid_for(num_sms * 4, J.rows_hint, NW), NW * 32, smem_w, next(), A, B, C, J,
                  ctl, mask, (int)BIN_WDENSE, mp);
         const size_t smem_c = (size_t)mp * sizeof(T) + 32 * sizeof(uint32_t);
-        launch_k(k_num_cta_dense<SR>, num_sms, 512, smem_c, next(), A, B, C, J, ctl, mask,
+        launch_k(k_num_cta_dense<SR>, grid_for(num_sms, J.rows_hint, 1), 512, smem_c, next(), A, B, C, J, ctl, mask,
                  (int)BIN_CDENSE, mp);
         return;
     }
@@ -943,7 +957,7 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
     launch_cta_hash<SR, 11>(A, B, C, J, ctl, mask, BIN_C2048, next(), num_sms);
     launch_cta_hash<SR, 12>(A, B, C, J, ctl, mask, BIN_C4096, next(), num_sms);
     launch_cta_hash<SR, 13>(A, B, C, J, ctl, mask, BIN_C8192, next(), num_sms);
-    launch_k(k_num_gdense<SR>, J.gd_ctas, 512, 0, next(), A, B, C, J, ctl, mask, (int)BIN_GD);
+    launch_k(k_num_gdense<SR>, grid_for(J.gd_ctas, J.rows_hint, 1), 512, 0, next(), A, B, C, J, ctl, mask, (int)BIN_GD);
 }
 
 void run_numeric(int sr, const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,

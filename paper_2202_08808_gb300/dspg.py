@@ -56,6 +56,10 @@ class _Stats(C.Structure):
         "products", "nnz_written", "relocations", "compactions", "a_entries")]
 
 
+class _Tuning(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("merge_k", "merge_ub", "lanes_min", "table_shift", "warp_max", "cta_max")]
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -94,6 +98,23 @@ def load():
         lib.dspg_multiply_rows_noalloc.restype = i32
         lib.dspg_multiply_rows_noalloc.argtypes = [C.POINTER(_Csr), C.POINTER(_Csr), i32, p, i64, p, p, p, i64,
                                                    C.POINTER(i64), p]
+        lib.dspg_set_tuning.restype = i32
+        lib.dspg_set_tuning.argtypes = [p, C.POINTER(_Tuning)]
+        lib.dspg_get_tuning.restype = i32
+        lib.dspg_get_tuning.argtypes = [p, C.POINTER(_Tuning)]
+        lib.dspg_tuning_candidate.restype = i32
+        lib.dspg_tuning_candidate.argtypes = [i32, C.POINTER(_Tuning)]
+        lib.dspg_autotune.restype = i32
+        lib.dspg_autotune.argtypes = [p, C.POINTER(_Upd), C.POINTER(_Upd), i64, C.POINTER(_Tuning),
+                                      C.POINTER(C.c_float), i32, C.POINTER(i32), p]
+        lib.dspg_group_create.restype = i32
+        lib.dspg_group_create.argtypes = [C.POINTER(p), C.POINTER(p), i64]
+        lib.dspg_group_apply.restype = i32
+        lib.dspg_group_apply.argtypes = [p, C.POINTER(_Upd), C.POINTER(_Upd), C.POINTER(_Stats), C.POINTER(i32), p]
+        lib.dspg_group_destroy.restype = None
+        lib.dspg_group_destroy.argtypes = [p]
+        lib.dspg_group_last_error.restype = C.c_char_p
+        lib.dspg_group_last_error.argtypes = [p]
         lib.dspg_destroy.restype = None
         lib.dspg_destroy.argtypes = [p]
         lib.dspg_last_error.restype = C.c_char_p
@@ -104,7 +125,26 @@ def load():
 
 EXPORTED = ["dspg_build", "dspg_apply_batch", "dspg_read_C", "dspg_read_A", "dspg_read_rows_C",
             "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_set_profiling", "dspg_stage_times",
-            "dspg_kernel_launches", "dspg_multiply_rows_noalloc", "dspg_destroy", "dspg_last_error"]
+            "dspg_kernel_launches", "dspg_multiply_rows_noalloc", "dspg_set_tuning", "dspg_get_tuning",
+            "dspg_tuning_candidate", "dspg_autotune", "dspg_group_create", "dspg_group_apply", "dspg_group_destroy",
+            "dspg_group_last_error", "dspg_destroy", "dspg_last_error"]
+
+TUNING_FIELDS = [n for n, _ in _Tuning._fields_]
+
+
+def _tuning_dict(t: _Tuning) -> dict:
+    return {n: int(getattr(t, n)) for n in TUNING_FIELDS}
+
+
+def tuning_candidates() -> list[dict]:
+    """The autotuner's built-in candidate tunings, in its order."""
+    lib, out, k = load(), [], 0
+    while True:
+        t = _Tuning()
+        if lib.dspg_tuning_candidate(k, C.byref(t)) != 0:
+            return out
+        out.append(_tuning_dict(t))
+        k += 1
 
 STAGES = ["sort", "classify", "detect", "merge", "commit", "transpose", "size", "numeric"]
 
@@ -272,6 +312,30 @@ class DynamicSpGEMM:
         self._check(self._lib.dspg_stage_times(self._h, ms, len(STAGES)))
         return dict(zip(STAGES, [float(x) for x in ms]))
 
+    def set_tuning(self, tuning: dict | None = None) -> None:
+        """Row-bin thresholds of the recompute (None: the defaults)."""
+        t = _Tuning(**tuning) if tuning is not None else None
+        self._check(self._lib.dspg_set_tuning(self._h, C.byref(t) if t is not None else None))
+
+    def get_tuning(self) -> dict:
+        t = _Tuning()
+        self._check(self._lib.dspg_get_tuning(self._h, C.byref(t)))
+        return _tuning_dict(t)
+
+    def autotune(self, batches, batches_b=None, stream=None) -> tuple[dict, list[float]]:
+        """Apply `batches` (real updates) while timing every candidate tuning
+        on each batch's affected rows; keeps and returns the fastest, with the
+        per-candidate total milliseconds."""
+        keep: list = []
+        ua = (_Upd * len(batches))(*[self._upd(b, keep) for b in batches])
+        ub = (_Upd * len(batches))(*[self._upd(b, keep) for b in batches_b]) if batches_b is not None else None
+        best = _Tuning()
+        ms = (C.c_float * 64)()
+        nc = C.c_int()
+        self._check(self._lib.dspg_autotune(self._h, ua, ub, len(batches), C.byref(best), ms, 64, C.byref(nc),
+                                            _stream(stream)))
+        return _tuning_dict(best), [float(ms[k]) for k in range(nc.value)]
+
     def recompute_all(self, stream=None) -> None:
         self._check(self._lib.dspg_recompute_all(self._h, _stream(stream)))
 
@@ -279,6 +343,50 @@ class DynamicSpGEMM:
         v = [C.c_int64() for _ in range(5)]
         self._check(self._lib.dspg_info(self._h, *[C.byref(x) for x in v]))
         return dict(zip(("n", "k", "m", "nnz_a", "nnz_c"), [x.value for x in v]))
+
+
+class Group:
+    """Several independent DynamicSpGEMM instances whose batches are applied
+    together, as branches of one CUDA graph (one graph launch per apply once
+    the batch sizes repeat)."""
+
+    def __init__(self, members):
+        self._lib = load()
+        self.members = list(members)
+        hs = (C.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        self._g = C.c_void_p()
+        st = self._lib.dspg_group_create(C.byref(self._g), hs, len(self.members))
+        if st != 0:
+            raise DspgError(st, self._lib.dspg_group_last_error(None).decode())
+
+    def apply(self, batches, batches_b=None, stream=None, raise_on_error: bool = True):
+        """batches[t] (or None) for member t; returns (stats list, status list)."""
+        n = len(self.members)
+        if len(batches) != n:
+            raise ValueError("one batch (or None) per member")
+        keep: list = []
+        empty = _Upd(0, None, None, None, None, 0)
+        ua = (_Upd * n)(*[m._upd(b, keep) if b is not None else empty for m, b in zip(self.members, batches)])
+        ub = None
+        if batches_b is not None:
+            ub = (_Upd * n)(*[m._upd(b, keep) if b is not None else empty for m, b in zip(self.members, batches_b)])
+        stats = (_Stats * n)()
+        status = (C.c_int * n)()
+        st = self._lib.dspg_group_apply(self._g, ua, ub, stats, status, _stream(stream))
+        if st != 0 and raise_on_error:
+            raise DspgError(st, self._lib.dspg_group_last_error(self._g).decode())
+        return ([{name: getattr(x, name) for name, _ in _Stats._fields_} for x in stats], [int(x) for x in status])
+
+    def close(self):
+        if getattr(self, "_g", None) is not None and self._g.value:
+            self._lib.dspg_group_destroy(self._g)
+            self._g = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def multiply_rows_noalloc(A, B, rows, semiring: int | None = None, stream=None):

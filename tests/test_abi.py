@@ -27,7 +27,7 @@ def test_library_loads_and_exports_all_declared_symbols():
     for name in declared_symbols():
         assert hasattr(lib, name), f"{name} declared in dspg.h but not exported"
     # the exported list of the binding covers the header too
-    assert set(declared_symbols()) <= set(pkg.EXPORTED) | set(declared_symbols())
+    assert set(declared_symbols()) == set(pkg.EXPORTED)
     raw = ctypes.CDLL(pkg.library_path())
     for name in declared_symbols():
         getattr(raw, name)
@@ -67,3 +67,19 @@ def test_binding_structs_mirror_the_header():
     assert [f for f, _ in b._Opt._fields_] == _struct_fields("dspg_options")
     assert [f for f, _ in b._Csr._fields_] == _struct_fields("dspg_csr")
     assert [f for f, _ in b._Upd._fields_] == _struct_fields("dspg_updates")
+    assert [f for f, _ in b._Tuning._fields_] == _struct_fields("dspg_tuning")
+
+
+def test_tuning_candidates_start_with_the_defaults_and_stay_in_range():
+    """The autotuner's list (host data, no GPU call): the first candidate is
+    the documented default, and every candidate keeps each hash table at or
+    above the bound (the ranges that make any tuning give the same C)."""
+    import paper_2202_08808_gb300 as pkg
+    cands = pkg.tuning_candidates()
+    assert len(cands) >= 8
+    assert cands[0] == dict(merge_k=8, merge_ub=64, lanes_min=8, table_shift=0, warp_max=1024, cta_max=8192)
+    for c in cands:
+        assert 0 <= c["merge_k"] <= 8 and 0 <= c["merge_ub"] <= 64
+        assert c["lanes_min"] in (8, 16, 32) and c["table_shift"] in (0, 1)
+        assert 0 <= c["warp_max"] <= 1024 and 0 <= c["cta_max"] <= 8192
+    assert len({tuple(sorted(c.items())) for c in cands}) == len(cands)

@@ -77,7 +77,7 @@ def _csr_from_unique_coo(nrows, ncols, r, c, v) -> CSR:
     """Canonical CSR from coordinates that are already free of duplicates."""
     r = np.asarray(r, dtype=np.int64)
     c = np.asarray(c, dtype=np.int64)
-    order = np.lexsort((c, r))
+    order = np.argsort(r * max(int(ncols), 1) + c, kind="stable")  # row-major order
     r, c, v = r[order], c[order], np.asarray(v)[order]
     counts = np.bincount(r, minlength=nrows).astype(np.int64)
     rowptr = np.zeros(nrows + 1, dtype=np.int64)
@@ -173,7 +173,8 @@ def rmat_symmetric(scale: int, edge_factor: int, abcd, seed: int, kind: int,
     keep = u != v
     lo = np.minimum(u[keep], v[keep])
     hi = np.maximum(u[keep], v[keep])
-    key = np.unique(lo * n + hi)
+    key = np.sort(lo * n + hi)
+    key = key[np.concatenate([[True], key[1:] != key[:-1]])] if key.shape[0] else key
     lo, hi = key // n, key % n
     w = _values(rng, key.shape[0], kind)
     if holdout > 0:
@@ -287,20 +288,22 @@ def rmat_edge_batch(A: CSR, held, n_edges: int, seed: int) -> Batch:
     without replacement from the held-out pool ``held`` = (u, v, w), half
     DELETEs of present undirected edges drawn uniformly. Each edge update is
     emitted as (u,v) and (v,u) with the same value, so the list has
-    2 * n_edges entries."""
+    2 * n_edges entries.  A pool (or edge set) smaller than its half of the
+    batch is drawn with replacement: repeated edges within the batch are
+    then written twice and the last write wins."""
     rng = np.random.default_rng(seed)
     kind = A.semiring
     n_ins = n_edges // 2
     n_del = n_edges - n_ins
     hu, hv, hw = held
-    if n_ins > hu.shape[0]:
-        raise ValueError("held-out pool too small")
-    pi = rng.choice(hu.shape[0], size=n_ins, replace=False)
+    if n_ins > 0 and hu.shape[0] == 0:
+        raise ValueError("empty held-out pool")
+    pi = rng.choice(hu.shape[0], size=n_ins, replace=n_ins > hu.shape[0])
     iu, iv, iw = hu[pi].astype(np.int64), hv[pi].astype(np.int64), hw[pi]
     r = A.row_ids()
     c = A.col.astype(np.int64)
     upper = np.nonzero(r < c)[0]
-    pd = rng.choice(upper.shape[0], size=n_del, replace=False)
+    pd = rng.choice(upper.shape[0], size=n_del, replace=n_del > upper.shape[0])
     du, dv = r[upper[pd]], c[upper[pd]]
     dw = np.zeros(n_del, dtype=hw.dtype)
     u = np.concatenate([iu, du])
