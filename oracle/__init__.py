@@ -10,6 +10,9 @@ Pinned by ``tests/test_oracle_pins.py`` against dense brute force, numpy's
 dense matmul, Floyd-Warshall and Dijkstra (scipy), a Python dictionary model
 of sequential updates, the paper's identities (Eq. 1 and the locality of
 general updates) and hand-worked fixtures in ``tests/golden/``.
+
+``mlp.py`` is the oracle of the learned row-size estimator (plain numpy,
+float64), pinned by ``tests/test_oracle_mlp.py``.
 """
 
 from .oracle import (  # noqa: F401
@@ -20,3 +23,4 @@ from .oracle import (  # noqa: F401
     oracle_lib,
     row_dynamic,
 )
+from . import mlp  # noqa: F401,E402
