@@ -110,6 +110,8 @@ typedef struct {
     int64_t relocations;    /* rows moved to the arena tail (A, B, transpose, C) */
     int64_t compactions;    /* arena rebuilds (growth) during this batch */
     int64_t a_entries;      /* entries of A' rows read by the recompute */
+    int64_t est_rows;       /* rows sized by the learned estimator */
+    int64_t est_overflows;  /* of those, rows whose table was too small (counted exactly, recomputed) */
 } dspg_batch_stats;
 
 /* Stages of apply_batch, in pipeline order, for dspg_stage_times. */
@@ -249,6 +251,72 @@ dspg_status dspg_group_create(dspg_group **out, dspg_handle *const *handles, int
  * Synchronises the stream. */
 dspg_status dspg_group_apply(dspg_group *g, const dspg_updates *dA, const dspg_updates *dB,
                              dspg_batch_stats *stats, dspg_status *status, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Sizing of the recompute's hash tables, and the learned row-size estimator.
+ *
+ * Each affected row is recomputed in a hash table in shared memory
+ * (Section 6.1's sparse accumulator) whose size the library must choose
+ * before the row is formed.  Three ways (the paper prescribes none):
+ *  DSPG_SIZE_BOUND    the product bound ub_i (never too small; default);
+ *  DSPG_SIZE_EXACT    a symbolic pass first counts nnz(C'_i) exactly, then
+ *                     the numeric pass uses tables of that size;
+ *  DSPG_SIZE_LEARNED  a small network (the estimator) predicts nnz(C'_i) from
+ *                     len(A_i) and the sum, maximum and mean of the lengths
+ *                     of the B rows it reads, for rows whose bound exceeds
+ *                     est_min; the table is the prediction times (1 + margin),
+ *                     clamped to [max_k len(B_k), ub_i].  A row whose table
+ *                     overflows is counted exactly and recomputed afterwards.
+ * The three give the same C (tables never decide the result); only the time
+ * differs.  The estimator has no counterpart in the paper. */
+enum { DSPG_SIZE_BOUND = 0, DSPG_SIZE_EXACT = 1, DSPG_SIZE_LEARNED = 2 };
+
+/* The estimator's network: x -> 64 ReLU -> 64 ReLU -> 1 with
+ * x = log2(1 + [len(A_i), sum_k len(B_k), max_k len(B_k), mean_k len(B_k)])
+ * and output o = log2(1 + nnz(C_i)).  Parameters: one float32 vector of
+ * DSPG_EST_PARAMS numbers, W1 (64 x 4, row-major), b1 (64), W2 (64 x 64,
+ * row-major), b2 (64), W3 (64), b3 (1).  Every forward pass uses the weights
+ * rounded to bfloat16 (nearest, ties to even) and accumulates in float32;
+ * training keeps a float32 master copy. */
+#define DSPG_EST_PARAMS 4545
+typedef struct dspg_estimator dspg_estimator;
+
+/* New estimator with the given initial parameters (host, float32). */
+dspg_status dspg_estimator_create(dspg_estimator **out, const float *params);
+
+/* Its float32 parameters into params (host, DSPG_EST_PARAMS). */
+dspg_status dspg_estimator_params(dspg_estimator *e, float *params, void *stream);
+
+/* Mean squared error L = mean_r (o_r - y_r)^2 over the n rows X (device,
+ * n x 4 float32, row-major) with targets y (device, n), and dL/dw at the
+ * bfloat16 weights into grad (host, DSPG_EST_PARAMS; may be NULL) and L into
+ * *loss (may be NULL).  The parameters do not change. */
+dspg_status dspg_estimator_grad(dspg_estimator *e, const float *X, const float *y, int64_t n, float *grad,
+                                double *loss, void *stream);
+
+/* `steps` SGD steps (w <- w - lr dL/dw) over consecutive mini-batches of
+ * `batch` rows of X, y (device; wrapping around); *loss (may be NULL)
+ * receives the loss over all n rows afterwards. */
+dspg_status dspg_estimator_train(dspg_estimator *e, const float *X, const float *y, int64_t n, int64_t batch,
+                                 int64_t steps, float lr, double *loss, void *stream);
+
+/* Outputs o for n rows X (device) into out (device, n float32). */
+dspg_status dspg_estimator_predict(dspg_estimator *e, const float *X, int64_t n, float *out, void *stream);
+
+const char *dspg_estimator_last_error(const dspg_estimator *e);
+void dspg_estimator_destroy(dspg_estimator *e);
+
+/* Training data from a handle: the features of rows rows[n] of C (device;
+ * rows == NULL: all rows, n = nrows(C)) into X (device, n x 4 float32) and,
+ * when y != NULL, log2(1 + nnz(C_i)) into y (device, n).  C's rows are exact
+ * after every build and batch, so these are exact symbolic counts. */
+dspg_status dspg_row_features(dspg_handle *h, const int32_t *rows, int64_t n, float *X, float *y, void *stream);
+
+/* Choose the sizing of h's dynamic recompute (the static product always uses
+ * the bound).  For DSPG_SIZE_LEARNED, e's current bfloat16 weights are
+ * copied into h (e may be destroyed afterwards), with est_min >= 0 and
+ * margin >= 0. */
+dspg_status dspg_set_sizing(dspg_handle *h, int mode, const dspg_estimator *e, int32_t est_min, float margin);
 
 /* Free the group (not its handles). */
 void dspg_group_destroy(dspg_group *g);

@@ -18,7 +18,12 @@ from .dspg import (  # noqa: F401
     CsrArrays,
     DspgError,
     DynamicSpGEMM,
+    EST_PARAMS,
+    Estimator,
     Group,
+    SIZE_BOUND,
+    SIZE_EXACT,
+    SIZE_LEARNED,
     TUNING_FIELDS,
     kernel_launches,
     library_path,

@@ -69,7 +69,9 @@ struct Ctl {
     long long bin_count[NBINS];
     long long ubc_total;       // sum over rows of min(product bound, columns)
     long long a_entries;       // A' entries read by the recompute
-    long long pad[6];
+    long long n_est;           // rows sized by the learned estimator
+    long long n_ovf;           // of those, rows whose table overflowed
+    long long pad[4];
 };
 
 // A row-slack CSR ("slack-CSR") on the device: row i occupies

@@ -24,6 +24,7 @@
 #include <string>
 #include <vector>
 
+#include "estimator.cuh"
 #include "internal.h"
 
 using namespace dspg;
@@ -184,6 +185,9 @@ struct CWs {
     DBuf<uint32_t> bmR, bmK;
     DBuf<int32_t> K;
     int64_t nrows_b = 0;
+    // learned sizing: rows waiting for an estimate, rows whose table overflowed
+    DBuf<int4> est;
+    DBuf<int32_t> ovf;
 };
 
 struct BatchIn {
@@ -197,9 +201,6 @@ thread_local std::string g_err;
 
 }  // namespace
 
-namespace dspg {
-void set_thread_error(const char *msg);
-}
 void dspg::set_thread_error(const char *msg) { g_err = msg; }
 
 struct dspg_handle {
@@ -238,6 +239,10 @@ struct dspg_handle {
     uint64_t epoch = 1;       // bumped whenever a persistent buffer moves
     bool use_graphs = true;
     dspg_tuning tune{8, 64, 8, 0, 1024, 8192};  // row bins of the recompute
+    int sizing = DSPG_SIZE_BOUND;               // how the recompute's tables are sized
+    int est_min = 128;
+    float est_margin = 0.25f;
+    DBuf<uint16_t> est_w;                       // estimator weights (bfloat16 bits)
     int64_t compactions = 0;
     std::string err;
 
@@ -376,6 +381,8 @@ void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
     w.bins.reserve((int64_t)NBINS * nn);
     w.bmR.reserve(nn / 32 + 2);
     CK(cudaMemsetAsync(w.bmR.p, 0, sizeof(uint32_t) * w.bmR.n, s));
+    w.est.reserve(nn);
+    w.ovf.reserve(nn);
     const int64_t nb = std::max<int64_t>(h->Bm().nrows, 1);
     w.nrows_b = nb;
     w.bmK.reserve(nb / 32 + 2);
@@ -416,6 +423,12 @@ CJob c_job(dspg_handle *h, const int32_t *R, bool static_mode) {
     J.table_shift = h->tune.table_shift;
     J.warp_max = h->tune.warp_max;
     J.cta_max = h->tune.cta_max;
+    J.sizing = (!static_mode && h->sizing == DSPG_SIZE_LEARNED) ? SIZE_LEARNED : SIZE_BOUND;
+    J.est_min = h->est_min;
+    J.est_margin = h->est_margin;
+    J.est_w = h->est_w.p;
+    J.est = w.est.p;
+    J.ovf = w.ovf.p;
     return J;
 }
 
@@ -628,7 +641,29 @@ void transpose_commit(dspg_handle *h, cudaStream_t s) {
                M_AT & ~ST_AT_ARENA, M_AT, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
 }
 
+// Exact sizing of rows R (count of `n_max` rows at most): bins by the bound,
+// a count_only pass writes each row's exact size into C.len, then the rows
+// are binned again by that count for the numeric pass (whose job is returned).
+CJob size_exact(dspg_handle *h, const int32_t *R, int64_t n_max, cudaStream_t s) {
+    CJob J = c_job(h, R, false);
+    J.sizing = SIZE_BOUND;
+    run_size_bins(h->A.view(), h->Bm().view(), h->C.view(), J, n_max, h->ctl, M_AB, s, h->num_sms);
+    CJob Jc = J;
+    Jc.count_only = 1;
+    numeric_branches(h, s, Jc);
+    CK(cudaMemsetAsync(h->ctl->bin_count, 0, sizeof(h->ctl->bin_count), s));
+    CK(cudaMemsetAsync(&h->ctl->nnz_written, 0, sizeof(long long), s));
+    CJob J2 = J;
+    J2.sizing = SIZE_COUNT;
+    run_size_bins(h->A.view(), h->Bm().view(), h->C.view(), J2, n_max, h->ctl, M_AB, s, h->num_sms);
+    return J2;
+}
+
 void stage_size(dspg_handle *h, cudaStream_t s) {
+    if (h->sizing == DSPG_SIZE_EXACT) {
+        size_exact(h, h->wc.R.p, h->A.nrows, s);
+        return;
+    }
     run_size_bins(h->A.view(), h->Bm().view(), h->C.view(), c_job(h, h->wc.R.p, false), h->A.nrows, h->ctl, M_AB, s,
                   h->num_sms);
 }
@@ -980,9 +1015,38 @@ void fill_stats(dspg_handle *h, dspg_batch_stats *stats, int64_t compactions0) {
         stats->nnz_written = c.nnz_written;
         stats->compactions = h->compactions - compactions0;
         stats->a_entries = c.a_entries;
+        stats->est_rows = c.n_est;
+        stats->est_overflows = c.n_ovf;
     }
 }
 
+
+// Rows whose learned table overflowed were left as they were; they are
+// counted exactly and recomputed here (eagerly; only when there are any).
+// The statistics of the main pass are kept.
+void est_fallback(dspg_handle *h, cudaStream_t s) {
+    const long long n_ovf = h->hctl->n_ovf;
+    if (n_ovf <= 0) return;
+    const Ctl main = *h->hctl;
+    for (int iter = 0;; iter++) {
+        CK(cudaMemsetAsync(&h->ctl->status, 0, sizeof(unsigned), s));
+        reset_c_counters(h, s);
+        CK(cudaMemcpyAsync(&h->ctl->n_affected, &main.n_ovf, sizeof(long long), cudaMemcpyHostToDevice, s));
+        numeric_branches(h, s, size_exact(h, h->wc.ovf.p, n_ovf, s));
+        read_ctl(h, s);
+        if ((h->hctl->status & ST_C_ARENA) && iter < 4) {
+            regrow(h, h->C, s);
+            continue;
+        }
+        if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "overflow recompute failed, status " + std::to_string(h->hctl->status));
+        break;
+    }
+    CK(cudaMemcpyAsync(&h->ctl->n_affected, &main.n_affected, sizeof(long long), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    const long long reloc = h->hctl->c_reloc;
+    *h->hctl = main;
+    h->hctl->c_reloc += reloc;
+}
 
 // One batch on one handle, as dspg_apply_batch (errors as exceptions).
 void apply_one(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, dspg_batch_stats *stats,
@@ -992,6 +1056,7 @@ void apply_one(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, d
     run_first(h, s);
     if (h->prof) stage_times_from_events(h);
     recover(h, s);
+    est_fallback(h, s);
     fill_stats(h, stats, compactions0);
 }
 
@@ -1332,6 +1397,48 @@ dspg_status dspg_autotune(dspg_handle *h, const dspg_updates *dA, const dspg_upd
     }
 }
 
+dspg_status dspg_set_sizing(dspg_handle *h, int mode, const dspg_estimator *e, int32_t est_min, float margin) {
+    if (!h) return DSPG_ERR_INVALID;
+    try {
+        if (mode != DSPG_SIZE_BOUND && mode != DSPG_SIZE_EXACT && mode != DSPG_SIZE_LEARNED)
+            throw Err(DSPG_ERR_INVALID, "unknown sizing mode");
+        if (mode == DSPG_SIZE_LEARNED) {
+            if (!e) throw Err(DSPG_ERR_INVALID, "learned sizing needs an estimator");
+            if (est_min < 0 || !(margin >= 0.0f) || margin > 1e6f) throw Err(DSPG_ERR_INVALID, "est_min and margin must be >= 0");
+            h->est_w.reserve(EST_PARAMS);
+            CK(cudaMemcpy(h->est_w.p, e->w, sizeof(uint16_t) * EST_PARAMS, cudaMemcpyDeviceToDevice));
+            h->est_min = est_min;
+            h->est_margin = margin;
+        }
+        h->sizing = mode;
+        h->epoch++;  // captured pipelines carry the old sizing
+        return DSPG_OK;
+    } catch (const Err &x) {
+        return fail(h, x);
+    }
+}
+
+dspg_status dspg_row_features(dspg_handle *h, const int32_t *rows, int64_t n, float *X, float *y, void *stream) {
+    if (!h) return DSPG_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        if (!X || n < 0) throw Err(DSPG_ERR_INVALID, "X is NULL or n < 0");
+        if (!rows && n != h->A.nrows) throw Err(DSPG_ERR_INVALID, "rows == NULL needs n = nrows");
+        DBuf<unsigned> bad;
+        bad.reserve(1);
+        CK(cudaMemsetAsync(bad.p, 0, sizeof(unsigned), s));
+        row_features(h->A.view(), h->Bm().view(), h->C.view(), rows, n, X, y, bad.p, s);
+        CK(cudaGetLastError());
+        unsigned hb = 0;
+        CK(cudaMemcpyAsync(&hb, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hb) throw Err(DSPG_ERR_INVALID, "row index out of range");
+        return DSPG_OK;
+    } catch (const Err &x) {
+        return fail(h, x);
+    }
+}
+
 dspg_status dspg_group_create(dspg_group **out, dspg_handle *const *handles, int64_t n) {
     dspg_group *g = nullptr;
     try {
@@ -1443,6 +1550,7 @@ dspg_status dspg_group_apply(dspg_group *g, const dspg_updates *dA, const dspg_u
             dspg_status st = DSPG_OK;
             try {
                 recover(h, s);
+                est_fallback(h, s);
                 fill_stats(h, stats ? stats + t : nullptr, comp0[t]);
             } catch (const Err &e) {
                 h->err = e.what();

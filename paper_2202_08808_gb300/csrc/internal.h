@@ -2,6 +2,8 @@
 // entry points of each translation unit.
 #pragma once
 
+#include <string>
+
 #include "common.cuh"
 
 namespace dspg {
@@ -81,7 +83,18 @@ struct CJob {
     // row-bin thresholds (dspg_tuning): thread-merge limits, smallest hash
     // executor, table oversizing, warp/CTA and CTA/global crossovers
     int tm_k, tm_ub, lanes_min, table_shift, warp_max, cta_max;
+    // sizing of the hash tables: SIZE_BOUND by the product bound; SIZE_COUNT
+    // by C.len (an exact count written by a count_only pass); SIZE_LEARNED by
+    // the estimator for rows with bound above est_min (tables may then
+    // overflow: the row goes to the overflow list instead of C)
+    int sizing;
+    int est_min;
+    float est_margin;
+    const uint16_t *est_w;    // estimator weights, bfloat16 bits (EST_PARAMS)
+    int4 *est;                // rows waiting for an estimate: {t, len(A_i), max len(B_k), bound}
+    int32_t *ovf;             // rows (of C) whose learned table overflowed
 };
+enum { SIZE_BOUND = 0, SIZE_COUNT = 1, SIZE_LEARNED = 2 };
 
 // update.cu
 void run_classify(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsigned mask, unsigned stage_bit,
@@ -103,6 +116,13 @@ void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const C
 void run_numeric(int sr, const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,
                  const cudaStream_t *ss, int ns, int num_sms);
 void init_dense_scratch(int sr, void *acc, uint32_t *mask, int64_t entries, int64_t words, cudaStream_t s);
+
+// Message for dspg_last_error(NULL) on the calling thread (handle.cu).
+void set_thread_error(const char *msg);
+
+// estimator.cu: features of rows of C for the estimator
+void row_features(const MatView &A, const MatView &B, const MatView &C, const int32_t *rows, int64_t n, float *X,
+                  float *y, unsigned *bad, cudaStream_t s);
 
 // layout.cu: building and reading slack-CSRs
 void fill_iota(int32_t *a, int64_t n, cudaStream_t s);
@@ -126,3 +146,15 @@ void sort_i32_values(int32_t *a, int64_t n, int bits, uint64_t *k0, uint64_t *k1
                      uint32_t *counts, int64_t *scan_tmp, int64_t *scan_out, cudaStream_t s);
 
 }  // namespace dspg
+
+// The learned row-size estimator (estimator.cu): float32 master weights, their
+// bfloat16 copy used by every forward pass, and training buffers.
+struct dspg_estimator {
+    float *master = nullptr;   // float32 parameters (device)
+    float *grad = nullptr;     // last gradient (device)
+    uint16_t *w = nullptr;     // bfloat16 bits of master (device)
+    float *H1 = nullptr, *H2 = nullptr, *D = nullptr, *DZ1 = nullptr, *DZ2 = nullptr, *O = nullptr;
+    int64_t cap = 0;           // rows the activation buffers hold
+    double *loss_d = nullptr;  // device accumulator
+    std::string err;
+};

@@ -26,8 +26,6 @@
 
 namespace dspg {
 
-void set_thread_error(const char *msg);
-
 namespace {
 
 constexpr int64_t NA_MAX_COLS = 1 << 16;  // widest C the entry point accepts

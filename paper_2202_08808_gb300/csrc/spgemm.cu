@@ -28,6 +28,7 @@
 // (order-free, bit-exact).
 #include <algorithm>
 
+#include "estimator.cuh"
 #include "internal.h"
 
 namespace dspg {
@@ -71,14 +72,10 @@ __device__ __forceinline__ long long atomic_add_ll2(long long *p, long long v) {
 constexpr int MERGE_K = 8;      // A rows up to this length can be merged by one thread
 constexpr int MERGE_UB = 64;    // ... when their product bound is at most this
 
-// The bin of a row from its capped bound and A-row length.  The thresholds
-// come from the job (the tuning); a hash table is never smaller than the
-// bound, since a row's distinct columns never exceed it, so no choice of
-// thresholds can make a table overflow.
-__device__ __forceinline__ int pick_bin(long long ubc, int alen, const CJob &J) {
-    if (alen <= J.tm_k && ubc <= J.tm_ub) return BIN_T8;
-    if (J.dense_mode) return ubc <= 4096 ? BIN_WDENSE : BIN_CDENSE;
-    const long long need = ubc << J.table_shift;
+// The hash (or global dense) bin for a table of at least `need` slots under
+// the job's thresholds.
+__device__ __forceinline__ int pick_table_bin(long long need, const CJob &J) {
+    need <<= J.table_shift;
     if (need <= 32 && J.lanes_min <= 8) return BIN_G8;
     if (need <= 64 && J.lanes_min <= 16) return BIN_G16;
     if (need <= J.warp_max) {
@@ -95,17 +92,41 @@ __device__ __forceinline__ int pick_bin(long long ubc, int alen, const CJob &J) 
     return BIN_GD;
 }
 
+// The bin of a row from its capped bound and A-row length (and, when the
+// tables are sized by an exact count, that count).  A table is never smaller
+// than the size it is given, so with the bound or an exact count no choice
+// of thresholds can make a table overflow.
+__device__ __forceinline__ int pick_bin(long long ubc, int alen, const CJob &J, long long table_need) {
+    if (alen <= J.tm_k && ubc <= J.tm_ub) return BIN_T8;
+    if (J.dense_mode) return ubc <= 4096 ? BIN_WDENSE : BIN_CDENSE;
+    return pick_table_bin(table_need, J);
+}
+
+// Append the calling lanes' rows t to their bins b (b < 0: none), one atomic
+// per distinct bin in the warp.
+__device__ __forceinline__ void append_bins(const CJob &J, Ctl *ctl, int b, long long t) {
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(peers) - 1;
+    long long bb = 0;
+    if (b >= 0 && lane == leader) bb = atomic_add_ll2(&ctl->bin_count[b], __popc(peers));
+    bb = __shfl_sync(0xffffffffu, bb, leader);
+    if (b >= 0) J.bins[(int64_t)b * J.bin_cap + bb + __popc(peers & lanemask_lt())] = (int32_t)t;
+}
+
 constexpr int SIZE_SHORT = 64;  // A rows up to this length are sized by one thread
 
 // One thread per row of R sums the B-row lengths of its A entries (rows
 // longer than SIZE_SHORT are summed by the whole warp afterwards); then the
 // warp hands out bin slots (and, for the static product, the row's place in
-// a fresh C) with one atomic per counter.
+// a fresh C) with one atomic per counter.  With SIZE_COUNT the tables are
+// sized by C.len (an exact count from a count_only pass); with SIZE_LEARNED
+// rows whose bound exceeds est_min go to the estimate list instead of a bin.
 __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask) {
     if (failed(ctl, mask)) return;
     const long long nR = ctl->n_affected;
     const int lane = threadIdx.x & 31;
-    long long prod_acc = 0, a_acc = 0;
+    long long prod_acc = 0, a_acc = 0, est_acc = 0;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < nR; base += (long long)gridDim.x * blockDim.x) {
         const long long t = base + threadIdx.x;
         const bool valid = t < nR;
@@ -113,19 +134,35 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
         const int64_t aoff = valid ? A.off[i] : 0;
         const int alen = valid ? A.len[i] : 0;
         const bool lng = alen > SIZE_SHORT;
-        long long ub = 0;
+        long long ub = 0, bmax = 0;
         if (valid && !lng)
-            for (int a = 0; a < alen; a++) ub += B.len[A.col[aoff + a]];
+            for (int a = 0; a < alen; a++) {
+                const long long l = B.len[A.col[aoff + a]];
+                ub += l;
+                bmax = l > bmax ? l : bmax;
+            }
         unsigned lm = __ballot_sync(0xffffffffu, valid && lng);
         while (lm) {
             const int src = __ffs(lm) - 1;
             lm &= lm - 1;
             const int64_t o = __shfl_sync(0xffffffffu, aoff, src);
             const int l = __shfl_sync(0xffffffffu, alen, src);
-            long long s = 0;
-            for (int a = lane; a < l; a += 32) s += B.len[A.col[o + a]];
+            long long s = 0, mx = 0;
+            for (int a = lane; a < l; a += 32) {
+                const long long x = B.len[A.col[o + a]];
+                s += x;
+                mx = x > mx ? x : mx;
+            }
             s = warp_sum<long long>(s);
-            if (lane == src) ub = s;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                const long long y = __shfl_xor_sync(0xffffffffu, mx, d);
+                mx = y > mx ? y : mx;
+            }
+            if (lane == src) {
+                ub = s;
+                bmax = mx;
+            }
         }
         const long long ubc = ub < J.m ? ub : J.m;
         if (J.static_mode) {
@@ -137,25 +174,63 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
                 C.len[i] = 0;
                 if (d + c > C.arena_cap) set_status(ctl, ST_C_ARENA);
             }
-        } else if (valid) {
+        } else if (valid && J.sizing != SIZE_COUNT) {
             J.bmR[i >> 5] = 0u;  // the detection marks are not needed any more
             if (ub == 0) C.len[i] = 0;  // no products: the row becomes empty
         }
-        const int b = (valid && ub > 0) ? pick_bin(ubc, alen, J) : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        const int leader = __ffs(peers) - 1;
-        long long bb = 0;
-        if (b >= 0 && lane == leader) bb = atomic_add_ll2(&ctl->bin_count[b], __popc(peers));
-        bb = __shfl_sync(0xffffffffu, bb, leader);
-        if (b >= 0) J.bins[(int64_t)b * J.bin_cap + bb + __popc(peers & lanemask_lt())] = (int32_t)t;
-        prod_acc += ub;
-        a_acc += alen;
+        const bool t8 = alen <= J.tm_k && ubc <= J.tm_ub;
+        const bool to_est = valid && ub > 0 && J.sizing == SIZE_LEARNED && !t8 && !J.dense_mode && ubc > J.est_min;
+        long long need = ubc;
+        if (J.sizing == SIZE_COUNT && valid) need = C.len[i];
+        const int b = (valid && ub > 0 && !to_est) ? pick_bin(ubc, alen, J, need) : -1;
+        append_bins(J, ctl, b, t);
+        if (to_est) {
+            const int4 e = make_int4((int)t, alen, (int)bmax, (int)(ub < 0x7fffffffLL ? ub : 0x7fffffffLL));
+            const long long at = atomic_add_ll2(&ctl->n_est, 1);
+            J.est[at] = e;
+            est_acc++;
+        }
+        if (J.sizing != SIZE_COUNT) {
+            prod_acc += ub;
+            a_acc += alen;
+        }
     }
     prod_acc = warp_sum<long long>(prod_acc);
     a_acc = warp_sum<long long>(a_acc);
     if (lane == 0) {
         if (prod_acc) atomic_add_ll2(&ctl->products, prod_acc);
         if (a_acc) atomic_add_ll2(&ctl->a_entries, a_acc);
+    }
+}
+
+// The learned sizing: one thread per row of the estimate list evaluates the
+// network (weights as floats in shared memory), sizes the row's table by the
+// prediction times (1 + margin), clamped to [max len(B_k), bound], and bins it.
+__global__ void __launch_bounds__(128) k_est_bins(CJob J, Ctl *ctl, unsigned mask) {
+    extern __shared__ __align__(16) float W[];
+    if (failed(ctl, mask)) return;
+    for (int k = threadIdx.x; k < EST_PARAMS; k += blockDim.x) W[k] = bf16_bits_to_float(J.est_w[k]);
+    __syncthreads();
+    const long long cnt = ctl->n_est;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += (long long)gridDim.x * blockDim.x) {
+        const long long q = base + threadIdx.x;
+        int b = -1;
+        long long t = 0;
+        if (q < cnt) {
+            const int4 e = J.est[q];
+            t = e.x;
+            float x[EST_IN];
+            est_features(x, e.y, e.w, e.z);
+            const float o = est_forward(W, x);
+            const float pred = exp2f(fminf(o, 40.0f)) - 1.0f;
+            long long need = (long long)ceilf(pred * (1.0f + J.est_margin));
+            const long long ubc = e.w < J.m ? e.w : J.m;
+            if (need > ubc) need = ubc;
+            if (need < e.z) need = e.z;
+            if (need < 1) need = 1;
+            b = pick_table_bin(need, J);
+        }
+        append_bins(J, ctl, b, t);
     }
 }
 
@@ -497,7 +572,18 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
         __syncwarp(gmask);
         bool ok = true;
         group_products<SR, G>(A, B, i, gmask, [&](int32_t j, T v) { ok &= hash_acc<LOG_TS, T, SR>(keys, vals, j, v); });
-        if (!ok) set_status(ctl, ST_TIMEOUT);
+        const bool full = (__ballot_sync(gmask, !ok) & gmask) != 0u;
+        if (full) {
+            // a learned table too small: the row goes to the overflow list and
+            // is counted and recomputed later; with a bound or exact size a
+            // full table cannot happen, so it is reported as an error
+            if (gl == 0) {
+                if (J.sizing == SIZE_LEARNED) J.ovf[atomic_add_ll2(&ctl->n_ovf, 1)] = i;
+                else set_status(ctl, ST_TIMEOUT);
+            }
+            __syncwarp(gmask);
+            continue;
+        }
         __syncwarp(gmask);
         int n = 0;
         for (int s0 = 0; s0 < TS; s0 += G) {
@@ -598,7 +684,14 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
         block_products<SR>(A, B, i, ps, [&](int32_t j, T v) { ok &= hash_acc<LOG_TS, T, SR>(keys, vals, j, v); });
         if (!ok) s_ok = 0;
         __syncthreads();
-        if (!s_ok && tid == 0) set_status(ctl, ST_TIMEOUT);
+        if (!s_ok) {  // table too small: see the group kernel
+            if (tid == 0) {
+                if (J.sizing == SIZE_LEARNED) J.ovf[atomic_add_ll2(&ctl->n_ovf, 1)] = i;
+                else set_status(ctl, ST_TIMEOUT);
+            }
+            __syncthreads();
+            continue;
+        }
         for (int s0 = w * 32; s0 < TS; s0 += 256) {
             const int s = s0 + lane;
             const int32_t k = keys[s];
@@ -864,6 +957,18 @@ void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const C
     if (g > num_sms * 8) g = num_sms * 8;
     if (g < 1) g = 1;
     launch_k(k_size_bins, (unsigned)g, 256, 0, s, A, B, C, J, ctl, mask);
+    if (J.sizing == SIZE_LEARNED) {
+        constexpr size_t smem = EST_PARAMS * sizeof(float) + 16;
+        static bool set = false;
+        if (!set) {
+            cudaFuncSetAttribute(k_est_bins, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            set = true;
+        }
+        int64_t ge = (max_rows + 127) / 128;
+        if (ge > num_sms * 4) ge = num_sms * 4;
+        if (ge < 1) ge = 1;
+        launch_k(k_est_bins, (unsigned)ge, 128, smem, s, J, ctl, mask);
+    }
 }
 
 // A persistent grid of `full` blocks, but no more blocks than it takes for

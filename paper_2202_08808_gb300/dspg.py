@@ -19,6 +19,11 @@ from . import _build
 PLUS_TIMES_F64 = 0
 MIN_PLUS_I32 = 1
 
+SIZE_BOUND = 0
+SIZE_EXACT = 1
+SIZE_LEARNED = 2
+EST_PARAMS = 4545
+
 OP_INSERT = 0
 OP_DELETE = 1
 OP_SET = 2
@@ -53,7 +58,7 @@ class _Opt(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "n_updates", "n_unique", "n_insert", "n_update", "n_delete", "n_noop", "touched_rows", "affected_rows",
-        "products", "nnz_written", "relocations", "compactions", "a_entries")]
+        "products", "nnz_written", "relocations", "compactions", "a_entries", "est_rows", "est_overflows")]
 
 
 class _Tuning(C.Structure):
@@ -115,6 +120,24 @@ def load():
         lib.dspg_group_destroy.argtypes = [p]
         lib.dspg_group_last_error.restype = C.c_char_p
         lib.dspg_group_last_error.argtypes = [p]
+        lib.dspg_estimator_create.restype = i32
+        lib.dspg_estimator_create.argtypes = [C.POINTER(p), p]
+        lib.dspg_estimator_params.restype = i32
+        lib.dspg_estimator_params.argtypes = [p, p, p]
+        lib.dspg_estimator_grad.restype = i32
+        lib.dspg_estimator_grad.argtypes = [p, p, p, i64, p, C.POINTER(C.c_double), p]
+        lib.dspg_estimator_train.restype = i32
+        lib.dspg_estimator_train.argtypes = [p, p, p, i64, i64, i64, C.c_float, C.POINTER(C.c_double), p]
+        lib.dspg_estimator_predict.restype = i32
+        lib.dspg_estimator_predict.argtypes = [p, p, i64, p, p]
+        lib.dspg_estimator_last_error.restype = C.c_char_p
+        lib.dspg_estimator_last_error.argtypes = [p]
+        lib.dspg_estimator_destroy.restype = None
+        lib.dspg_estimator_destroy.argtypes = [p]
+        lib.dspg_row_features.restype = i32
+        lib.dspg_row_features.argtypes = [p, p, i64, p, p, p]
+        lib.dspg_set_sizing.restype = i32
+        lib.dspg_set_sizing.argtypes = [p, i32, p, i32, C.c_float]
         lib.dspg_destroy.restype = None
         lib.dspg_destroy.argtypes = [p]
         lib.dspg_last_error.restype = C.c_char_p
@@ -127,7 +150,9 @@ EXPORTED = ["dspg_build", "dspg_apply_batch", "dspg_read_C", "dspg_read_A", "dsp
             "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_set_profiling", "dspg_stage_times",
             "dspg_kernel_launches", "dspg_multiply_rows_noalloc", "dspg_set_tuning", "dspg_get_tuning",
             "dspg_tuning_candidate", "dspg_autotune", "dspg_group_create", "dspg_group_apply", "dspg_group_destroy",
-            "dspg_group_last_error", "dspg_destroy", "dspg_last_error"]
+            "dspg_group_last_error", "dspg_estimator_create", "dspg_estimator_params", "dspg_estimator_grad",
+            "dspg_estimator_train", "dspg_estimator_predict", "dspg_estimator_last_error", "dspg_estimator_destroy",
+            "dspg_row_features", "dspg_set_sizing", "dspg_destroy", "dspg_last_error"]
 
 TUNING_FIELDS = [n for n, _ in _Tuning._fields_]
 
@@ -336,6 +361,30 @@ class DynamicSpGEMM:
                                             _stream(stream)))
         return _tuning_dict(best), [float(ms[k]) for k in range(nc.value)]
 
+    def set_sizing(self, mode: int, estimator: "Estimator | None" = None, est_min: int = 128,
+                   margin: float = 0.25) -> None:
+        """How the recompute sizes its hash tables: SIZE_BOUND, SIZE_EXACT or
+        SIZE_LEARNED (with an Estimator, whose weights are copied)."""
+        e = estimator._e if estimator is not None else None
+        self._check(self._lib.dspg_set_sizing(self._h, mode, e, est_min, margin))
+
+    def row_features(self, rows=None, stream=None):
+        """(X, y) as torch tensors on the device: the estimator's features of
+        rows of C (all rows when rows is None) and log2(1 + nnz(C_i))."""
+        import torch
+        keep: list = []
+        if rows is None:
+            n = self.info()["n"]
+            rp = None
+        else:
+            rows = rows if _is_torch(rows) and rows.is_cuda else torch.as_tensor(np.asarray(rows, np.int32)).cuda()
+            n = int(rows.shape[0])
+            rp, _ = _ptr(rows, keep)
+        X = torch.empty((max(n, 1), 4), dtype=torch.float32, device="cuda")
+        y = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+        self._check(self._lib.dspg_row_features(self._h, rp, n, X.data_ptr(), y.data_ptr(), _stream(stream)))
+        return X[:n], y[:n]
+
     def recompute_all(self, stream=None) -> None:
         self._check(self._lib.dspg_recompute_all(self._h, _stream(stream)))
 
@@ -343,6 +392,71 @@ class DynamicSpGEMM:
         v = [C.c_int64() for _ in range(5)]
         self._check(self._lib.dspg_info(self._h, *[C.byref(x) for x in v]))
         return dict(zip(("n", "k", "m", "nnz_a", "nnz_c"), [x.value for x in v]))
+
+
+class Estimator:
+    """The learned row-size estimator (include/dspg.h): a 4-64-64-1 network
+    with bfloat16 weights, trained on the GPU by the library's kernels."""
+
+    def __init__(self, params):
+        self._lib = load()
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        if p.shape != (EST_PARAMS,):
+            raise ValueError(f"need {EST_PARAMS} parameters")
+        self._e = C.c_void_p()
+        st = self._lib.dspg_estimator_create(C.byref(self._e), p.ctypes.data)
+        if st != 0:
+            raise DspgError(st, self._lib.dspg_last_error(None).decode())
+
+    def _check(self, st):
+        if st != 0:
+            raise DspgError(st, self._lib.dspg_estimator_last_error(self._e).decode())
+
+    def params(self, stream=None) -> np.ndarray:
+        out = np.empty(EST_PARAMS, dtype=np.float32)
+        self._check(self._lib.dspg_estimator_params(self._e, out.ctypes.data, _stream(stream)))
+        return out
+
+    @staticmethod
+    def _dev(x, dt):
+        import torch
+        t = x if _is_torch(x) else torch.as_tensor(np.asarray(x, dtype=dt))
+        return t.to(device="cuda", dtype=torch.float32).contiguous()
+
+    def grad(self, X, y, stream=None):
+        """(loss, dL/dw) at the current weights; the weights do not change."""
+        X, y = self._dev(X, np.float32), self._dev(y, np.float32)
+        g = np.empty(EST_PARAMS, dtype=np.float32)
+        loss = C.c_double()
+        self._check(self._lib.dspg_estimator_grad(self._e, X.data_ptr(), y.data_ptr(), int(X.shape[0]), g.ctypes.data,
+                                                  C.byref(loss), _stream(stream)))
+        return loss.value, g
+
+    def train(self, X, y, batch: int = 4096, steps: int = 1000, lr: float = 1e-3, stream=None) -> float:
+        X, y = self._dev(X, np.float32), self._dev(y, np.float32)
+        loss = C.c_double()
+        self._check(self._lib.dspg_estimator_train(self._e, X.data_ptr(), y.data_ptr(), int(X.shape[0]), batch, steps,
+                                                   lr, C.byref(loss), _stream(stream)))
+        return loss.value
+
+    def predict(self, X, stream=None):
+        import torch
+        X = self._dev(X, np.float32)
+        out = torch.empty(max(int(X.shape[0]), 1), dtype=torch.float32, device="cuda")
+        self._check(self._lib.dspg_estimator_predict(self._e, X.data_ptr(), int(X.shape[0]), out.data_ptr(),
+                                                     _stream(stream)))
+        return out[:X.shape[0]]
+
+    def close(self):
+        if getattr(self, "_e", None) is not None and self._e.value:
+            self._lib.dspg_estimator_destroy(self._e)
+            self._e = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Group:
