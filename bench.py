@@ -486,6 +486,218 @@ def batched_cpu_baseline(insts, budget_s):
             "sample": f"one batch on each of {k} instances of scale <= 12 (apply + affected rows + row recompute)"}
 
 
+# ------------------------------------------- learned sizing + serving
+
+R21 = (0.45, 0.15, 0.15, 0.25)
+
+
+def _dev_batch(b):
+    import torch
+    return type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(), torch.from_numpy(b.val).cuda(),
+                   torch.from_numpy(b.op).cuda())
+
+
+def train_estimator(pkg, seeds, steps, log):
+    """Features and exact row sizes of R-MAT scale-18 instances (all rows
+    after the build, and the affected rows after two random batches), then
+    SGD on the GPU."""
+    import torch
+    from workloads import PLUS_TIMES_F64, EdgeStream, mlp_init_params, rmat_symmetric
+    Xs, ys = [], []
+    t0 = time.perf_counter()
+    for sd in seeds:
+        A, held = rmat_symmetric(18, 8, R21, seed=sd, kind=PLUS_TIMES_F64, holdout=20000)
+        g = pkg.DynamicSpGEMM(A)
+        X, y = g.row_features()
+        Xs.append(X)
+        ys.append(y)
+        es = EdgeStream(A, held, sd)
+        for ne in (300, 3000):
+            g.apply_batch(_dev_batch(es.batch(ne)))
+            X, y = g.row_features(torch.from_numpy(g.last_affected()).cuda())
+            Xs.append(X)
+            ys.append(y)
+        g.close()
+    X, y = torch.cat(Xs), torch.cat(ys)
+    perm = torch.randperm(X.shape[0], generator=torch.Generator().manual_seed(1)).cuda()
+    X, y = X[perm].contiguous(), y[perm].contiguous()
+    data_s = time.perf_counter() - t0
+    est = pkg.Estimator(mlp_init_params(seeds[0]))
+    loss0, _ = est.grad(X, y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss1 = est.train(X, y, batch=4096, steps=steps, lr=5e-4)
+    train_s = time.perf_counter() - t0
+    log(f"estimator: {X.shape[0]} rows, loss {loss0:.3f} -> {loss1:.4f} in {steps} steps ({train_s:.2f} s)")
+    return est, {"rows": int(X.shape[0]), "graphs": len(seeds), "loss_initial": round(loss0, 4),
+                 "loss_final": round(loss1, 5), "steps": steps, "batch": 4096, "train_s": round(train_s, 3),
+                 "data_s": round(data_s, 2)}
+
+
+def learned_arm(args):
+    import torch
+    import paper_2202_08808_gb300 as pkg
+    from paper_2202_08808_gb300.serving import Request, Server, latency_summary
+    from workloads import PLUS_TIMES_F64, EdgeStream, rmat_symmetric
+    torch.cuda.set_device(0)
+
+    def log(msg):
+        print(msg, file=sys.stderr, flush=True)
+
+    est, est_info = train_estimator(pkg, list(range(50, 50 + args.train_graphs)), args.train_steps, log)
+    t0 = time.perf_counter()
+    A, held = rmat_symmetric(args.scale, 8, R21, seed=5, kind=PLUS_TIMES_F64, holdout=400000)
+    gen_s = time.perf_counter() - t0
+    modes = {"bound": pkg.SIZE_BOUND, "exact": pkg.SIZE_EXACT, "learned": pkg.SIZE_LEARNED}
+    hs = {}
+    t0 = time.perf_counter()
+    for name, mode in modes.items():
+        hs[name] = pkg.DynamicSpGEMM(A)
+        hs[name].set_sizing(mode, est if mode == pkg.SIZE_LEARNED else None, est_min=args.est_min,
+                            margin=args.est_margin)
+    torch.cuda.synchronize()
+    build_s = (time.perf_counter() - t0) / len(modes)
+    info = hs["bound"].info()
+    log(f"scale {args.scale}: nnz(A) {info['nnz_a']}, nnz(C) {info['nnz_c']}, build {build_s:.2f} s per handle")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    # the same batches, in the same order, on the three handles
+    rng = np.random.default_rng(500)
+    es = EdgeStream(A, held, 501)
+    sizes = np.floor(10 ** rng.uniform(1, 5, size=args.compare_batches)).astype(int)
+    warm = [_dev_batch(es.batch(int(x))) for x in (100, 1000, 10000)]
+    for h in hs.values():
+        for b in warm:
+            h.apply_batch(b)
+    times = {k: [] for k in modes}
+    stats = {k: [] for k in modes}
+    worst_rel = 0.0
+    for x in sizes:
+        b = _dev_batch(es.batch(int(x)))
+        for name, h in hs.items():
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = h.apply_batch(b)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times[name].append(e0.elapsed_time(e1))
+            stats[name].append(st)
+        # identical outputs: same affected rows, same patterns, values equal to rounding
+        R = hs["bound"].last_affected()
+        samp = R if R.shape[0] <= 20000 else np.sort(np.random.default_rng(int(x)).choice(R, 20000, replace=False))
+        ref = hs["bound"].read_rows_C(samp)
+        for name in ("exact", "learned"):
+            assert np.array_equal(hs[name].last_affected(), R), f"{name}: affected rows differ"
+            got = hs[name].read_rows_C(samp)
+            assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), f"{name}: patterns differ"
+            nz = ref[2] != 0
+            if nz.any():
+                worst_rel = max(worst_rel, float(np.max(np.abs(got[2][nz] - ref[2][nz]) / np.abs(ref[2][nz]))))
+    assert worst_rel <= 2e-12, worst_rel
+    per_mode = {}
+    for name in modes:
+        t = np.array(times[name])
+        per_mode[name] = {"mean_ms": round(float(t.mean()), 4), "p50_ms": round(float(np.median(t)), 4),
+                          "p99_ms": round(float(np.percentile(t, 99)), 4),
+                          "batches_per_s": round(len(t) / (t.sum() * 1e-3), 2),
+                          "est_rows": int(sum(s["est_rows"] for s in stats[name])),
+                          "est_overflows": int(sum(s["est_overflows"] for s in stats[name]))}
+    by_decade = {}
+    for d in range(1, 5):
+        sel = [k for k, x in enumerate(sizes) if 10 ** d <= x < 10 ** (d + 1)]
+        if sel:
+            by_decade[f"1e{d}"] = {name: round(float(np.mean([times[name][k] for k in sel])), 4) for name in modes}
+    log(f"sizing: {per_mode}")
+
+    # serving on the learned handle: service rate with every request queued,
+    # then Poisson arrivals at 0.5x, 1x and 2x that rate
+    srv_h = hs["learned"]
+    for name in ("bound", "exact"):
+        hs[name].close()
+    qrng = np.random.default_rng(502)
+
+    def requests(count, rate):
+        out = []
+        t = 0.0
+        for k in range(count):
+            if rate is not None:
+                t += float(qrng.exponential(1.0 / rate))
+            out.append(Request(k, t, es.batch(int(10 ** qrng.uniform(1, 5)))))
+        return out
+
+    srv = Server(srv_h, max_wave=args.max_wave, read_results=False)
+    cal = requests(args.requests, None)
+    t0 = time.perf_counter()
+    res = srv.serve(cal)
+    wall = time.perf_counter() - t0
+    mu = len(res) / wall
+    serving = {"service_rate_req_s": round(mu, 2), "saturated": latency_summary(res, wall)}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for f in (0.5, 1.0, 2.0):
+        srv = Server(srv_h, max_wave=args.max_wave, read_results=False)
+        reqs = requests(args.requests, f * mu)
+        t0 = time.perf_counter()
+        res = srv.serve(reqs)
+        wall = time.perf_counter() - t0
+        serving[f"rate_{f}x"] = dict(latency_summary(res, wall), offered_req_s=round(f * mu, 2), waves=srv.waves,
+                                     conflicts=srv.conflicts)
+    clk = clocks.stop()
+    log(f"serving: {serving}")
+
+    cpu = None if args.no_cpu else learned_cpu_baseline(A, held, args.cpu_budget)
+    lm = per_mode["learned"]
+    out = {
+        "metric": METRIC,
+        "value": lm["batches_per_s"],
+        "unit": "batches/s (learned sizing, batches of 10..10^5 edge changes)",
+        "n_gpus": 1, "steps": int(len(sizes)), "warmup": 3, "ms_per_step": lm["mean_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"learned sizing + serving: R-MAT scale {args.scale}, edge factor 8, (0.45,0.15,0.15,0.25), "
+                               "symmetrised, C = A A (+,.) f64; estimator trained on scale-18 instances",
+                   "nnz_a": info["nnz_a"], "nnz_c": info["nnz_c"], "batch_sizes": [int(x) for x in sizes],
+                   "l2": "flushed before every timed batch (256 MiB write)"},
+        "sizing": per_mode,
+        "sizing_by_decade_ms": by_decade,
+        "speedup_learned_vs_exact": round(per_mode["exact"]["mean_ms"] / lm["mean_ms"], 3),
+        "speedup_learned_vs_bound": round(per_mode["bound"]["mean_ms"] / lm["mean_ms"], 3),
+        "max_rel_diff_between_sizings": worst_rel,
+        "estimator": est_info,
+        "serving": serving,
+        "clocks": clk,
+        "setup_s": {"generate": round(gen_s, 1), "build_per_handle": round(build_s, 2)},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def learned_cpu_baseline(A, held, budget_s):
+    """The oracle on a bounded sample of the same workload: apply a
+    100-edge batch, find its affected rows, recompute them (the row-dynamic
+    route without the write into a stored C); single-threaded C."""
+    from oracle import OMat, affected_rows
+    from workloads import EdgeStream
+    start = time.perf_counter()
+    Ao = OMat.from_csr(A)
+    es = EdgeStream(A, held, 503)
+    times, rows = [], 0
+    while time.perf_counter() - start < budget_s and len(times) < 20:
+        b = es.batch(100)
+        t0 = time.perf_counter()
+        pre = Ao.presence(b)
+        Ao.apply(b)
+        post = Ao.presence(b)
+        R = affected_rows(Ao, b, pre, post, b_nrows=A.nrows, b_is_a=True)
+        Ao.multiply_rows(Ao, R)
+        times.append(time.perf_counter() - t0)
+        rows += len(R)
+    mean = statistics.mean(times)
+    return {"value": round(1.0 / mean, 4), "unit": "batches/s (100-edge batches)", "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} batches of 100 edge changes on the same graph ({rows} affected rows recomputed)"}
+
+
 # ------------------------------------------------------------ CPU oracle
 
 def cpu_baseline(args, budget_s=20.0, steps=None):
@@ -575,9 +787,18 @@ def main():
     ap.add_argument("--profile", choices=["step", "static"], default=None,
                     help="run one NVTX-marked step or static recompute for ncu, then exit")
     ap.add_argument("--batch", type=int, default=BATCH)
-    ap.add_argument("--workload", choices=["stencil", "batched"], default="stencil",
-                    help="stencil: the 128^3 stencil with 10^4-update batches; batched: 256 R-MAT instances")
+    ap.add_argument("--workload", choices=["stencil", "batched", "learned"], default="stencil",
+                    help="stencil: the 128^3 stencil with 10^4-update batches; batched: 256 R-MAT instances; "
+                         "learned: learned vs exact vs bound sizing and the serving loop on R-MAT scale 21")
     ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--scale", type=int, default=21)
+    ap.add_argument("--train-graphs", type=int, default=4)
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--est-min", type=int, default=128)
+    ap.add_argument("--est-margin", type=float, default=0.25)
+    ap.add_argument("--compare-batches", type=int, default=16)
+    ap.add_argument("--requests", type=int, default=300)
+    ap.add_argument("--max-wave", type=int, default=32)
     args = ap.parse_args()
     if args.profile:
         profile_arm(args)
@@ -588,6 +809,8 @@ def main():
         reference_arm(args)
     elif args.workload == "batched":
         batched_arm(args)
+    elif args.workload == "learned":
+        learned_arm(args)
     else:
         gpu_arm(args)
 

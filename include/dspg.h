@@ -318,6 +318,29 @@ dspg_status dspg_row_features(dspg_handle *h, const int32_t *rows, int64_t n, fl
  * margin >= 0. */
 dspg_status dspg_set_sizing(dspg_handle *h, int mode, const dspg_estimator *e, int32_t est_min, float margin);
 
+/* ---------------------------------------------------------------------------
+ * Serving support: merging queued batches without changing any result.
+ * (No counterpart in the paper, which applies one batch at a time.)
+ *
+ * A server that receives many small batches for the same handle can apply
+ * several in one call, concatenated in arrival order, when no one of them
+ * can change a row of C that another reports: the result of each is then
+ * the same as if it had been applied alone, in order.  The footprint of a
+ * batch dA is the set of rows of C it can touch, plus the rows its entries
+ * could connect: its rows, and, when B is A, its columns and every row i
+ * with A(i,k) != 0 for a row k of the batch (the rows of C* = A* B' + A B*,
+ * Eq. 1, on the current pattern).  Two batches whose footprints are
+ * disjoint can share a call.  (With B distinct from A the footprint is the
+ * batch's rows; batches of B are not covered.) */
+
+/* OR the footprint of dA into bitmap (device, ceil(nrows/32) words, bit i
+ * of word i/32 for row i).  DSPG_ERR_INVALID for an entry out of range. */
+dspg_status dspg_footprint(dspg_handle *h, const dspg_updates *dA, uint32_t *bitmap, void *stream);
+
+/* If the bitmaps f and u (device, `words` words each) share no bit, OR f
+ * into u and set *admitted = 1; otherwise leave u and set *admitted = 0. */
+dspg_status dspg_bitmap_admit(const uint32_t *f, uint32_t *u, int64_t words, int *admitted, void *stream);
+
 /* Free the group (not its handles). */
 void dspg_group_destroy(dspg_group *g);
 const char *dspg_group_last_error(const dspg_group *g);

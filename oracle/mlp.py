@@ -50,19 +50,6 @@ def bf16_round(a) -> np.ndarray:
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def init_params(seed: int) -> np.ndarray:
-    """He-uniform initial weights (float32 values), zero biases."""
-    rng = np.random.default_rng(seed)
-    parts = []
-    for shape in SHAPES:
-        if len(shape) == 2:
-            bound = np.sqrt(6.0 / shape[1])
-            parts.append(rng.uniform(-bound, bound, size=shape).reshape(-1))
-        else:
-            parts.append(np.zeros(shape[0]))
-    return np.concatenate(parts).astype(np.float32).astype(np.float64)
-
-
 def unpack(p: np.ndarray):
     out, at = [], 0
     for shape in SHAPES:

@@ -391,8 +391,13 @@ void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
     const int64_t m = h->Bm().ncols;
     if (m > DENSE_M_MAX) {
         w.gd_w = (m + 31) / 32 * 32;
+        // per-CTA dense accumulators for the longest rows: up to two CTAs per
+        // SM, within a budget of 1/32 of the free memory (256 MiB .. 4 GiB)
         const double per = (double)w.gd_w * (h->vsize + 0.125);
-        int ctas = (int)std::min<double>(2.0 * h->num_sms, std::max(4.0, (256.0 * 1024 * 1024) / per));
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        const double budget = std::min(4.0 * (1 << 30), std::max(256.0 * (1 << 20), (double)free_b / 32.0));
+        int ctas = (int)std::min<double>(2.0 * h->num_sms, std::max(4.0, budget / per));
         w.gd_ctas = std::max(1, ctas);
         w.gd_acc.reserve(w.gd_w * w.gd_ctas * h->vsize);
         w.gd_mask.reserve(w.gd_w / 32 * w.gd_ctas);
@@ -893,9 +898,15 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
     DBuf<int64_t> rp;
     const int64_t nnz = mat_rowptr(h, M, rows, n, rp, s);
     if (!rowptr) return nnz;
+    DBuf<unsigned> bad;
+    bad.reserve(1);
+    CK(cudaMemsetAsync(bad.p, 0, sizeof(unsigned), s));
+    unsigned hb = 0;
     if (on_device) {
         CK(cudaMemcpyAsync(rowptr, rp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
         gather_rows_out(rows, n, M.view(), rp.p, col, val, M.vsize, s, h->num_sms);
+        sort_rows(rp.p, n, col, val, M.vsize, bad.p, s, h->num_sms);
+        CK(cudaMemcpyAsync(&hb, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
     } else {
         DBuf<int32_t> c;
@@ -903,6 +914,8 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
         c.reserve(std::max<int64_t>(nnz, 1));
         v.reserve(std::max<int64_t>(nnz, 1) * std::max(M.vsize, 1));
         gather_rows_out(rows, n, M.view(), rp.p, c.p, v.p, M.vsize, s, h->num_sms);
+        sort_rows(rp.p, n, c.p, M.vsize ? (void *)v.p : nullptr, M.vsize, bad.p, s, h->num_sms);
+        CK(cudaMemcpyAsync(&hb, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(rowptr, rp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
         if (nnz > 0) {
             if (col) CK(cudaMemcpyAsync(col, c.p, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s));
@@ -910,6 +923,7 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
         }
         CK(cudaStreamSynchronize(s));
     }
+    if (hb) throw Err(DSPG_ERR_CUDA, "a stored row longer than 8192 entries is out of column order");
     return nnz;
 }
 
@@ -1436,6 +1450,63 @@ dspg_status dspg_row_features(dspg_handle *h, const int32_t *rows, int64_t n, fl
         return DSPG_OK;
     } catch (const Err &x) {
         return fail(h, x);
+    }
+}
+
+dspg_status dspg_footprint(dspg_handle *h, const dspg_updates *dA, uint32_t *bitmap, void *stream) {
+    if (!h) return DSPG_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        if (!dA || !bitmap) throw Err(DSPG_ERR_INVALID, "dA and bitmap must not be NULL");
+        const int64_t n = dA->n;
+        if (n < 0 || (n > 0 && (!dA->row || !dA->col))) throw Err(DSPG_ERR_INVALID, "bad batch");
+        if (n == 0) return DSPG_OK;
+        DBuf<int32_t> r, c;
+        const int32_t *rp = dA->row, *cp = dA->col;
+        if (!dA->on_device) {
+            r.reserve(n);
+            c.reserve(n);
+            CK(cudaMemcpyAsync(r.p, dA->row, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(c.p, dA->col, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+            rp = r.p;
+            cp = c.p;
+        }
+        DBuf<unsigned> bad;
+        bad.reserve(1);
+        CK(cudaMemsetAsync(bad.p, 0, sizeof(unsigned), s));
+        run_footprint(rp, cp, n, h->A.nrows, h->A.ncols, h->b_is_a, h->AT.view(), bitmap, bad.p, s, h->num_sms);
+        unsigned hb = 0;
+        CK(cudaMemcpyAsync(&hb, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hb) throw Err(DSPG_ERR_INVALID, "batch entry out of range");
+        return DSPG_OK;
+    } catch (const Err &x) {
+        return fail(h, x);
+    }
+}
+
+dspg_status dspg_bitmap_admit(const uint32_t *f, uint32_t *u, int64_t words, int *admitted, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        if (!f || !u || !admitted || words < 0) throw Err(DSPG_ERR_INVALID, "bad bitmap arguments");
+        int dev = 0, sms = 1;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        DBuf<unsigned long long> hits;
+        hits.reserve(1);
+        CK(cudaMemsetAsync(hits.p, 0, sizeof(unsigned long long), s));
+        run_bitmap_overlap(f, u, words, hits.p, s, sms);
+        unsigned long long hh = 0;
+        CK(cudaMemcpyAsync(&hh, hits.p, sizeof(hh), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *admitted = hh == 0 ? 1 : 0;
+        if (hh == 0) {
+            run_bitmap_or(f, u, words, s, sms);
+            CK(cudaStreamSynchronize(s));
+        }
+        return DSPG_OK;
+    } catch (const Err &x) {
+        return fail(nullptr, x);
     }
 }
 

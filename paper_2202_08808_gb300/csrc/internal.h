@@ -108,6 +108,11 @@ void run_detect_entries(const int32_t *srow, const uint8_t *kind, int64_t n, boo
 void run_detect_cols(const MatView &AT, const DetectBufs &D, Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms);
 void run_transpose_feed(const UpdJob &J, int32_t pad_row, int32_t *trow, int32_t *tcol, uint8_t *top, Ctl *ctl,
                         unsigned mask, cudaStream_t s);
+void run_footprint(const int32_t *row, const int32_t *col, int64_t n, int64_t nrows, int64_t ncols, bool b_is_a,
+                   const MatView &AT, uint32_t *bm, unsigned *bad, cudaStream_t s, int num_sms);
+void run_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t words, unsigned long long *hits, cudaStream_t s,
+                        int num_sms);
+void run_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words, cudaStream_t s, int num_sms);
 
 // spgemm.cu
 constexpr int64_t DENSE_M_MAX = 1024;  // C columns up to this use dense accumulators
@@ -135,6 +140,10 @@ void copy_rows(const int32_t *rows, int64_t n, const int64_t *src_off, const int
                cudaStream_t s, int num_sms);
 void gather_rows_out(const int32_t *rows, int64_t n, const MatView &M, const int64_t *out_rowptr, int32_t *out_col,
                      void *out_val, int vsize, cudaStream_t s, int num_sms);
+// Sort each row of a gathered CSR (rowptr over n rows) by column, in place;
+// sets *bad if a row longer than 8192 entries is out of order.
+void sort_rows(const int64_t *rowptr, int64_t n, int32_t *col, void *val, int vsize, unsigned *bad, cudaStream_t s,
+               int num_sms);
 void lens_of_rows(const int32_t *rows, int64_t n, const int32_t *len, int32_t *out, cudaStream_t s);
 void validate_rowptr(int64_t nrows, int64_t nnz, const int64_t *rowptr, unsigned *bad, cudaStream_t s);
 void validate_csr_entries(int64_t nrows, int64_t ncols, const int64_t *rowptr, const int32_t *col, const void *val,

@@ -1,8 +1,10 @@
 // layout.cu -- building slack-CSRs from row-wise sources and reading them back.
 //
 // These kernels move whole rows between a CSR-like source (row start + row
-// length) and a destination layout, one warp per row; they carry no
-// semiring arithmetic.
+// length) and a destination layout, one warp per row, and sort read rows by
+// column; they carry no semiring arithmetic.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace dspg {
@@ -99,6 +101,121 @@ void gather_rows_out(const int32_t *rows, int64_t n, const MatView &M, const int
     unsigned g = blocks_for(n * 32, 256, (int64_t)num_sms * 16);
     if (vsize == 8) launch_k(k_gather_out<double>, g, 256, 0, s, rows, n, M, out_rowptr, out_col, (double *)out_val);
     else launch_k(k_gather_out<int32_t>, g, 256, 0, s, rows, n, M, out_rowptr, out_col, (int32_t *)out_val);
+}
+
+// ------------------------------------------------------- row sorting
+
+// C's rows are stored in any column order (the hash bins write long rows in
+// table order); every read returns canonical rows, so the gathered rows are
+// sorted by column here.  Rows already in order are left as they are.
+constexpr int SORT_SHORT = 64;     // rows up to this length: a warp each
+constexpr int SORT_MAX = 8192;     // longer rows are written in order by their kernels
+
+template <typename T>
+__global__ void k_sort_short_rows(const int64_t *rowptr, int64_t n, int32_t *col, T *val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += nwarps) {
+        const int64_t lo = rowptr[x];
+        const int len = (int)(rowptr[x + 1] - lo);
+        if (len < 2 || len > SORT_SHORT) continue;
+        const int32_t k0 = lane < len ? col[lo + lane] : INT32_MAX;
+        const int32_t k1 = lane + 32 < len ? col[lo + lane + 32] : INT32_MAX;
+        T v0 = T(0), v1 = T(0);
+        if (val) {
+            if (lane < len) v0 = val[lo + lane];
+            if (lane + 32 < len) v1 = val[lo + lane + 32];
+        }
+        // rank of each key among the row's (distinct) columns
+        int r0 = 0, r1 = 0;
+        for (int j = 0; j < 32; j++) {
+            const int32_t a = __shfl_sync(0xffffffffu, k0, j), b = __shfl_sync(0xffffffffu, k1, j);
+            r0 += (a < k0) + (b < k0);
+            r1 += (a < k1) + (b < k1);
+        }
+        __syncwarp();
+        if (lane < len) {
+            col[lo + r0] = k0;
+            if (val) val[lo + r0] = v0;
+        }
+        if (lane + 32 < len) {
+            col[lo + r1] = k1;
+            if (val) val[lo + r1] = v1;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_sort_long_rows(const int64_t *rowptr, int64_t n, int32_t *col, T *val,
+                                                        unsigned *bad) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *sv = (T *)smem;
+    int32_t *sk = (int32_t *)(sv + SORT_MAX);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int64_t x = blockIdx.x; x < n; x += gridDim.x) {
+        const int64_t lo = rowptr[x];
+        const int64_t len = rowptr[x + 1] - lo;
+        if (len <= SORT_SHORT) continue;
+        int unsorted = 0;
+        for (int64_t e = tid; e + 1 < len; e += nt) unsorted |= col[lo + e] > col[lo + e + 1];
+        if (!__syncthreads_or(unsorted)) continue;
+        if (len > SORT_MAX) {
+            if (tid == 0) atomicOr(bad, 1u);
+            continue;
+        }
+        int N = 128;
+        while (N < len) N <<= 1;
+        for (int e = tid; e < N; e += nt) {
+            sk[e] = e < len ? col[lo + e] : INT32_MAX;
+            if (val && e < len) sv[e] = val[lo + e];
+        }
+        __syncthreads();
+        for (int size = 2; size <= N; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int q = tid; q < N / 2; q += nt) {
+                    const int a = 2 * q - (q & (stride - 1)), b = a + stride;
+                    const bool up = (a & size) == 0;
+                    const int32_t ka = sk[a], kb = sk[b];
+                    if ((ka > kb) == up) {
+                        sk[a] = kb;
+                        sk[b] = ka;
+                        if (val) {
+                            const T t = sv[a];
+                            sv[a] = sv[b];
+                            sv[b] = t;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int e = tid; e < len; e += nt) {
+            col[lo + e] = sk[e];
+            if (val) val[lo + e] = sv[e];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+static void sort_rows_t(const int64_t *rowptr, int64_t n, int32_t *col, T *val, unsigned *bad, cudaStream_t s,
+                        int num_sms) {
+    launch_k(k_sort_short_rows<T>, blocks_for(n * 32, 256, (int64_t)num_sms * 16), 256, 0, s, rowptr, n, col, val);
+    const size_t smem = (size_t)SORT_MAX * (sizeof(T) + sizeof(int32_t));
+    static bool set = false;
+    if (!set) {
+        cudaFuncSetAttribute(k_sort_long_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        set = true;
+    }
+    const int64_t g = std::min<int64_t>(n, (int64_t)num_sms * 2);
+    launch_k(k_sort_long_rows<T>, (unsigned)std::max<int64_t>(g, 1), 512, smem, s, rowptr, n, col, val, bad);
+}
+
+void sort_rows(const int64_t *rowptr, int64_t n, int32_t *col, void *val, int vsize, unsigned *bad, cudaStream_t s,
+               int num_sms) {
+    if (n <= 0 || !col) return;
+    if (vsize == 8) sort_rows_t<double>(rowptr, n, col, (double *)val, bad, s, num_sms);
+    else sort_rows_t<int32_t>(rowptr, n, col, (int32_t *)val, bad, s, num_sms);
 }
 
 // Canonical-CSR check: rowptr[0] = 0 and non-decreasing, rowptr[n] = nnz,

@@ -19,9 +19,11 @@
 // Products of a row are flattened over its A entries: a scan of the B-row
 // lengths of the A entries held by the lanes assigns product p to A entry s
 // by a binary search in the scan, so lanes stay busy even when B rows are
-// short.  Each row's output is sorted by column (hash bins) or read out in
-// column order (dense bins) and written straight into C: in place when it
-// fits the row's capacity, otherwise at the arena tail.  For the static
+// short.  Each row is written straight into C (in place when it fits the
+// row's capacity, otherwise at the arena tail) in whatever column order its
+// kernel produces it: like the paper's local rows, C's rows carry no column
+// order (the thread-merge, dense and small hash rows happen to come out
+// sorted; longer hash rows come out in table order), and reads sort them.  For the static
 // product the sizing pass lays C out afresh with room for the bound.
 // (+,.) accumulates with double atomics (the summation order varies; the
 // library's tolerance covers any order), (min,+) with atomicMin
@@ -261,6 +263,8 @@ __device__ __forceinline__ int64_t c_row_dest(const MatView &C, const CJob &J, C
 
 // --------------------------------------------------- product generators
 
+constexpr int PU = 4;  // products per lane whose B loads are issued together
+
 // Calls emit(j, a (x) b) for every product of row i; the G lanes of one
 // group (G = 8, 16 or 32 consecutive lanes, mask gmask) share the work.
 template <int SR, int G, class F>
@@ -290,21 +294,36 @@ __device__ __forceinline__ void group_products(const MatView &A, const MatView &
             if (gl >= d) incl += o;
         }
         const int total = __shfl_sync(gmask, incl, G - 1, G);
-        for (int base = 0; base < total; base += G) {
-            const int p = base + gl;
-            int s = 0;
+        // PU products per lane per round: their B entries are all loaded
+        // before any is accumulated, so PU loads per lane are in flight
+        for (int base = 0; base < total; base += G * PU) {
+            int64_t q[PU];
+            T a[PU];
 #pragma unroll
-            for (int step = G / 2; step > 0; step >>= 1) {
-                const int v = __shfl_sync(gmask, incl, s + step - 1, G);
-                if (v <= p) s += step;
+            for (int u = 0; u < PU; u++) {
+                const int p = base + u * G + gl;
+                int s = 0;
+#pragma unroll
+                for (int step = G / 2; step > 0; step >>= 1) {
+                    const int v = __shfl_sync(gmask, incl, s + step - 1, G);
+                    if (v <= p) s += step;
+                }
+                const int64_t bo = __shfl_sync(gmask, boff, s, G);
+                a[u] = __shfl_sync(gmask, av, s, G);
+                const int excl = __shfl_sync(gmask, incl, s, G) - __shfl_sync(gmask, blen, s, G);
+                q[u] = p < total ? bo + (p - excl) : -1;
             }
-            const int64_t bo = __shfl_sync(gmask, boff, s, G);
-            const T a = __shfl_sync(gmask, av, s, G);
-            const int excl = __shfl_sync(gmask, incl, s, G) - __shfl_sync(gmask, blen, s, G);
-            if (p < total) {
-                const int64_t q = bo + (p - excl);
-                emit(B.col[q], Sr<SR>::mul(a, Bv[q]));
-            }
+            int32_t c[PU];
+            T b[PU];
+#pragma unroll
+            for (int u = 0; u < PU; u++)
+                if (q[u] >= 0) {
+                    c[u] = __ldg(B.col + q[u]);
+                    b[u] = __ldg(Bv + q[u]);
+                }
+#pragma unroll
+            for (int u = 0; u < PU; u++)
+                if (q[u] >= 0) emit(c[u], Sr<SR>::mul(a[u], b[u]));
         }
     }
 }
@@ -358,14 +377,31 @@ __device__ __forceinline__ void block_products(const MatView &A, const MatView &
         }
         sm.blen[tid] = blen;
         const int total = block_incl_scan(blen, sm.incl, sm.wsum);
-        for (int base = 0; base < total; base += nt) {
-            const int p = base + tid;
-            if (p < total) {
-                const int s = (int)upper_bound_dev<int>(sm.incl, 0, nt, p);
-                const int excl = sm.incl[s] - sm.blen[s];
-                const int64_t q = sm.boff[s] + (p - excl);
-                emit(B.col[q], Sr<SR>::mul(sm.av[s], Bv[q]));
+        for (int base = 0; base < total; base += nt * PU) {  // PU loads per thread in flight, as above
+            int64_t q[PU];
+            T a[PU];
+#pragma unroll
+            for (int u = 0; u < PU; u++) {
+                const int p = base + u * nt + tid;
+                q[u] = -1;
+                if (p < total) {
+                    const int s = (int)upper_bound_dev<int>(sm.incl, 0, nt, p);
+                    const int excl = sm.incl[s] - sm.blen[s];
+                    q[u] = sm.boff[s] + (p - excl);
+                    a[u] = sm.av[s];
+                }
             }
+            int32_t c[PU];
+            T b[PU];
+#pragma unroll
+            for (int u = 0; u < PU; u++)
+                if (q[u] >= 0) {
+                    c[u] = __ldg(B.col + q[u]);
+                    b[u] = __ldg(Bv + q[u]);
+                }
+#pragma unroll
+            for (int u = 0; u < PU; u++)
+                if (q[u] >= 0) emit(c[u], Sr<SR>::mul(a[u], b[u]));
         }
         __syncthreads();
     }
@@ -393,18 +429,6 @@ __device__ __forceinline__ bool hash_acc(int32_t *keys, T *vals, int32_t j, T v)
         h = (h + 1) & (TS - 1);
     }
     return false;  // table full: cannot happen when the bin bound holds
-}
-
-template <typename T>
-__device__ __forceinline__ void bitonic_step(int32_t *k, T *v, int i, int l, bool up) {
-    const int32_t ki = k[i], kl = k[l];
-    if ((ki > kl) == up) {
-        k[i] = kl;
-        k[l] = ki;
-        const T t = v[i];
-        v[i] = v[l];
-        v[l] = t;
-    }
 }
 
 // ---------------------------------------------------- thread merge kernel
@@ -616,25 +640,13 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
                     Cv[dest + rank] = cv[e];
                 }
             }
-        } else {
-            int N = 128;  // n > 64 here
-            while (N < n) N <<= 1;
-            for (int s = n + gl; s < N; s += G) ck[s] = 0x7fffffff;
-            __syncwarp(gmask);
-            for (int size = 2; size <= N; size <<= 1) {
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    for (int x = gl; x < N / 2; x += G) {
-                        const int a = 2 * x - (x & (stride - 1));
-                        bitonic_step<T>(ck, cv, a, a + stride, (a & size) == 0);
-                    }
-                    __syncwarp(gmask);
-                }
+        } else if (dest >= 0) {
+            // longer rows go out in table order: C's rows need no column
+            // order (the reads sort them)
+            for (int s = gl; s < n; s += G) {
+                C.col[dest + s] = ck[s];
+                Cv[dest + s] = cv[s];
             }
-            if (dest >= 0)
-                for (int s = gl; s < n; s += G) {
-                    C.col[dest + s] = ck[s];
-                    Cv[dest + s] = cv[s];
-                }
         }
         if (gl == 0 && dest >= 0) C.len[i] = n;
         nnz_acc += n;
@@ -710,23 +722,11 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
         }
         __syncthreads();
         const int n = s_n < HC ? s_n : HC;
-        int N = 2;
-        while (N < n) N <<= 1;
-        for (int s = n + tid; s < N; s += 256) ck[s] = 0x7fffffff;
         if (tid == 0) {
             s_dest = c_row_dest(C, J, ctl, i, n);
             nnz_acc += n;
         }
         __syncthreads();
-        for (int size = 2; size <= N; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int x = tid; x < N / 2; x += 256) {
-                    const int a = 2 * x - (x & (stride - 1));
-                    bitonic_step<T>(ck, cv, a, a + stride, (a & size) == 0);
-                }
-                __syncthreads();
-            }
-        }
         const long long dest = s_dest;
         if (dest >= 0) {
             for (int s = tid; s < n; s += 256) {

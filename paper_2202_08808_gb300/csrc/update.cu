@@ -446,4 +446,72 @@ void run_transpose_feed(const UpdJob &J, int32_t pad_row, int32_t *trow, int32_t
                                                                   top, ctl, mask);
 }
 
+// ------------------------------------------------------------ footprints
+
+// The rows of C a batch of A updates can touch, as bits over the rows of A:
+// its rows (and, when B is A, its columns and every row i with A(i,k) != 0
+// for a row k of the batch: the rows of A* B' + A B* of Eq. 1, on the
+// current pattern).  A warp per batch entry walks the transposed pattern.
+__global__ void k_footprint(const int32_t *row, const int32_t *col, int64_t n, int64_t nrows, int64_t ncols,
+                            int b_is_a, MatView AT, uint32_t *bm, unsigned *bad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = w0; e < n; e += nw) {
+        const int32_t r = row[e], c = col[e];
+        if (r < 0 || r >= nrows || c < 0 || c >= ncols) {
+            if (lane == 0) atomicOr(bad, 1u);
+            continue;
+        }
+        if (lane == 0) {
+            atomicOr(&bm[r >> 5], 1u << (r & 31));
+            if (b_is_a) atomicOr(&bm[c >> 5], 1u << (c & 31));
+        }
+        if (!b_is_a) continue;
+        const int64_t off = AT.off[r];
+        const int len = AT.len[r];
+        for (int x = lane; x < len; x += 32) {
+            const int32_t i = AT.col[off + x];
+            atomicOr(&bm[i >> 5], 1u << (i & 31));
+        }
+    }
+}
+
+// hits = number of words where f and u share a bit.
+__global__ void k_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t words, unsigned long long *hits) {
+    unsigned long long c = 0;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < words; x += (int64_t)gridDim.x * blockDim.x)
+        c += (f[x] & u[x]) != 0u;
+    c = warp_sum<unsigned long long>(c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(hits, c);
+}
+
+__global__ void k_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < words; x += (int64_t)gridDim.x * blockDim.x)
+        u[x] |= f[x];
+}
+
+void run_footprint(const int32_t *row, const int32_t *col, int64_t n, int64_t nrows, int64_t ncols, bool b_is_a,
+                   const MatView &AT, uint32_t *bm, unsigned *bad, cudaStream_t s, int num_sms) {
+    if (n <= 0) return;
+    int64_t g = (n * 32 + 255) / 256;
+    if (g > num_sms * 16) g = num_sms * 16;
+    launch_k(k_footprint, (unsigned)g, 256, 0, s, row, col, n, nrows, ncols, b_is_a ? 1 : 0, AT, bm, bad);
+}
+
+void run_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t words, unsigned long long *hits, cudaStream_t s,
+                        int num_sms) {
+    int64_t g = (words + 255) / 256;
+    if (g > num_sms * 8) g = num_sms * 8;
+    if (g < 1) g = 1;
+    launch_k(k_bitmap_overlap, (unsigned)g, 256, 0, s, f, u, words, hits);
+}
+
+void run_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words, cudaStream_t s, int num_sms) {
+    int64_t g = (words + 255) / 256;
+    if (g > num_sms * 8) g = num_sms * 8;
+    if (g < 1) g = 1;
+    launch_k(k_bitmap_or, (unsigned)g, 256, 0, s, f, u, words);
+}
+
 }  // namespace dspg

@@ -19,7 +19,7 @@ import pytest
 import oracle
 from oracle import OMat, mlp
 from parity import assert_matches, oracle_product
-from workloads import MIN_PLUS_I32, PLUS_TIMES_F64, random_batch, rmat_edge_batch, rmat_symmetric
+from workloads import MIN_PLUS_I32, PLUS_TIMES_F64, mlp_init_params, random_batch, rmat_edge_batch, rmat_symmetric
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,7 @@ def _training_set(seed, n=3000):
 
 def test_gradient_matches_oracle_backprop(dspg):
     X, y = _training_set(61)
-    p = mlp.init_params(62).astype(np.float32)
+    p = mlp_init_params(62).astype(np.float32)
     est = dspg.Estimator(p)
     loss_g, grad_g = est.grad(X, y)
     loss_o, grad_o = mlp.loss_and_grad(p.astype(np.float64), X.astype(np.float64), y.astype(np.float64))
@@ -63,7 +63,7 @@ def test_gradient_matches_oracle_backprop(dspg):
 
 def test_sgd_step_matches_oracle(dspg):
     X, y = _training_set(63, n=1024)
-    p = mlp.init_params(64).astype(np.float32)
+    p = mlp_init_params(64).astype(np.float32)
     est = dspg.Estimator(p)
     lr = 1e-3
     est.train(X, y, batch=1024, steps=1, lr=lr)
@@ -87,7 +87,7 @@ def _trained_estimator(dspg, seeds=(71, 72), scale=12):
     X, y = torch.cat(Xs), torch.cat(ys)
     perm = torch.randperm(X.shape[0], generator=torch.Generator().manual_seed(0)).cuda()
     X, y = X[perm].contiguous(), y[perm].contiguous()
-    est = dspg.Estimator(mlp.init_params(73).astype(np.float32))
+    est = dspg.Estimator(mlp_init_params(73).astype(np.float32))
     loss0, _ = est.grad(X, y)
     loss1 = est.train(X, y, batch=2048, steps=1500, lr=5e-4)
     return est, loss0, loss1

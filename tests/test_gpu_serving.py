@@ -1,0 +1,84 @@
+"""The serving loop (continuous batching over one handle) against the oracle.
+
+Every request's result (its affected rows of C right after it commits) must
+be the same whether it ran inside a wave of merged requests or alone in
+arrival order, and both must be the oracle's rows at that version: patterns
+and (min,+) values bit-exact, (+,.) values within 1e-12 * sum|ab|.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import OMat
+from parity import assert_rows_match
+from workloads import MIN_PLUS_I32, PLUS_TIMES_F64, er_matrix, random_batch, rmat_symmetric
+
+pytestmark = pytest.mark.gpu
+
+G500 = (0.57, 0.19, 0.19, 0.05)
+
+
+def _requests(A, count, seed):
+    """Small mixed batches (1..5 entries, half on present entries), all
+    queued at once, so that waves form and some footprints collide."""
+    from paper_2202_08808_gb300.serving import Request
+    rng = np.random.default_rng(seed)
+    return [Request(k, 0.0, random_batch(A.nrows, A.ncols, int(rng.integers(1, 6)), seed=seed * 1000 + k,
+                                         kind=A.semiring, A=A, dup_frac=0.0)) for k in range(count)]
+
+
+def _alone_and_oracle(dspg, A, reqs, results):
+    g = dspg.DynamicSpGEMM(A)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    by_id = {r.rid: r for r in results}
+    for req in reqs:
+        g.apply_batch(req.batch)
+        rows = g.last_affected()
+        rp, col, val = g.read_rows_C(rows)
+        R_o = oracle.row_dynamic(Ao, Co, req.batch)
+        assert np.array_equal(rows, R_o), f"request {req.rid}: alone R differs from the oracle"
+        mix = by_id[req.rid]
+        assert np.array_equal(mix.rows, rows), f"request {req.rid}: R in the mix differs from alone"
+        o_rp, o_col, o_val = Ao.multiply_rows(Ao, rows)
+        o_abs = Ao.multiply_rows(Ao, rows, absval=True)[2] if Ao.sr == PLUS_TIMES_F64 else None
+        assert_rows_match(rp, col, val, o_rp, o_col, o_val, o_abs, what=f"request {req.rid} alone")
+        assert_rows_match(mix.rowptr, mix.col, mix.val, o_rp, o_col, o_val, o_abs, what=f"request {req.rid} mix")
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_each_result_is_the_same_alone_and_in_the_mix(dspg, sr):
+    from paper_2202_08808_gb300.serving import Server
+    A = er_matrix(4096, 4, seed=121, kind=sr)
+    reqs = _requests(A, 80, 122)
+    srv = Server(dspg.DynamicSpGEMM(A), max_wave=16)
+    results = srv.serve(reqs)
+    assert len(results) == len(reqs)
+    assert srv.waves < len(reqs), "no two requests were merged"
+    assert srv.conflicts > 0, "no footprint conflict was exercised"
+    assert max(r.wave_size for r in results) > 1
+    _alone_and_oracle(dspg, A, reqs, results)
+
+
+def test_memory_admission_stops_a_wave(dspg):
+    """With no free memory to spare, every wave holds one request (the first
+    request of a wave is always admitted, so the stream still drains)."""
+    from paper_2202_08808_gb300.serving import Server
+    A = er_matrix(1024, 4, seed=131, kind=PLUS_TIMES_F64)
+    reqs = _requests(A, 12, 132)
+    srv = Server(dspg.DynamicSpGEMM(A), max_wave=8, hbm_reserve=0, hbm_free=lambda: 1)
+    results = srv.serve(reqs)
+    assert srv.waves == len(reqs) and srv.memory_stops > 0
+    _alone_and_oracle(dspg, A, reqs, results)
+
+
+def test_footprint_rejects_out_of_range_entries(dspg):
+    import torch
+    from workloads import Batch
+    A, _ = rmat_symmetric(8, 8, G500, seed=141, kind=PLUS_TIMES_F64)
+    g = dspg.DynamicSpGEMM(A)
+    f = torch.zeros((A.nrows + 31) // 32, dtype=torch.int32, device="cuda")
+    bad = Batch(np.array([3, A.nrows], np.int32), np.array([1, 2], np.int32), np.zeros(2), np.zeros(2, np.uint8))
+    with pytest.raises(dspg.DspgError):
+        g.footprint(bad, f)

@@ -24,4 +24,6 @@ from .gen import (  # noqa: F401
     random_batch,
     random_csr,
     concat_batches,
+    EdgeStream,
+    mlp_init_params,
 )

@@ -319,6 +319,51 @@ def rmat_edge_batch(A: CSR, held, n_edges: int, seed: int) -> Batch:
     return Batch(rows.astype(np.int32), cols.astype(np.int32), vals, ops)
 
 
+def mlp_init_params(seed: int, n_in: int = 4, n_hid: int = 64) -> np.ndarray:
+    """Seeded initial parameters of the row-size estimator's network
+    (x -> n_hid -> n_hid -> 1), flat in the order W1, b1, W2, b2, W3, b3:
+    He-uniform weights (bound sqrt(6 / fan_in)), zero biases, float32."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((n_hid, n_in), (n_hid, n_hid), (1, n_hid)):
+        bound = np.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-bound, bound, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
+class EdgeStream:
+    """A stream of undirected-edge batches for a symmetric A, as
+    ``rmat_edge_batch`` draws them (half INSERTs from the held-out pool,
+    half DELETEs of edges of A, both directions emitted), but with the edge
+    lists prepared once so that each batch costs O(its size)."""
+
+    def __init__(self, A: CSR, held, seed: int):
+        self.rng = np.random.default_rng(seed)
+        r = A.row_ids()
+        c = A.col.astype(np.int64)
+        upper = r < c
+        self.du, self.dv = r[upper], c[upper]
+        self.hu, self.hv, self.hw = (np.asarray(x) for x in held)
+        self.kind = A.semiring
+
+    def batch(self, n_edges: int) -> Batch:
+        rng = self.rng
+        n_ins = n_edges // 2
+        n_del = n_edges - n_ins
+        pi = rng.integers(0, self.hu.shape[0], size=n_ins)
+        pd = rng.integers(0, self.du.shape[0], size=n_del)
+        u = np.concatenate([self.hu[pi].astype(np.int64), self.du[pd]])
+        v = np.concatenate([self.hv[pi].astype(np.int64), self.dv[pd]])
+        w = np.concatenate([self.hw[pi], np.zeros(n_del, dtype=self.hw.dtype)])
+        op = np.concatenate([np.full(n_ins, OP_INSERT), np.full(n_del, OP_DELETE)]).astype(np.uint8)
+        perm = rng.permutation(u.shape[0])
+        u, v, w, op = u[perm], v[perm], w[perm], op[perm]
+        rows = np.stack([u, v], axis=1).reshape(-1)
+        cols = np.stack([v, u], axis=1).reshape(-1)
+        return Batch(rows.astype(np.int32), cols.astype(np.int32), np.repeat(w, 2), np.repeat(op, 2))
+
+
 def random_batch(nrows: int, ncols: int, nupd: int, seed: int, kind: int,
                  A: CSR | None = None, hit_frac: float = 0.5,
                  dup_frac: float = 0.2) -> Batch:
