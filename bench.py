@@ -51,9 +51,60 @@ def dist_env():
     return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def make_batches(count, seed0, nupd=BATCH):
-    from workloads import stencil_batch
-    return [stencil_batch(GRID, GRID, GRID, nupd, seed=seed0 + i) for i in range(count)]
+class StencilWorkload:
+    """128^3 7-point stencil, C = A A in (+,.) f64, mixed batches within two
+    grid hops (inserts / deletes / value changes, a third each)."""
+    name = "stencil"
+    batch = BATCH
+    sweep = (1000, 10000, 100000, 1000000)
+    vsize, dtype = 8, "f64"
+
+    def __init__(self):
+        self.describe = "stencil 128^3 7-point, C = A A (+,.) f64, batches of 10^4 mixed updates"
+        self.unit = "batches/s (10^4-update batches)"
+
+    def operands(self):
+        from workloads import stencil7
+        return stencil7(GRID, GRID, GRID, seed=1), None
+
+    def batches(self, count, seed0, nupd=None):
+        from workloads import stencil_batch
+        return [stencil_batch(GRID, GRID, GRID, nupd or self.batch, seed=seed0 + i) for i in range(count)]
+
+
+class Rmat20Workload:
+    """R-MAT scale 20, edge factor 16, Graph500 parameters, symmetrised,
+    int32 weights U[1,100]; B is n x 256 with 1% density, int32 U[1,100];
+    C = A B in (min,+) (multi-source path relaxation); batches of undirected
+    edge insertions (held-out edges) and deletions of A, half each."""
+    name = "rmat20"
+    batch = 1000
+    sweep = (100, 1000, 10000, 100000)
+    vsize, dtype = 4, "i32"
+
+    def __init__(self):
+        self.describe = ("R-MAT scale 20 ef 16 (0.57,0.19,0.19,0.05) symmetrised, C = A B (min,+) i32 with B n x 256 "
+                         "at 1%, batches of 10^3 undirected edge insertions/deletions of A")
+        self.unit = "batches/s (10^3-edge batches)"
+        self._A = self._held = None
+        self._streams = {}
+
+    def operands(self):
+        from workloads import MIN_PLUS_I32, bernoulli_sparse, rmat_symmetric
+        self._A, self._held = rmat_symmetric(20, 16, (0.57, 0.19, 0.19, 0.05), seed=3, kind=MIN_PLUS_I32,
+                                             holdout=400000)
+        B = bernoulli_sparse(1 << 20, 256, 0.01, seed=3, kind=MIN_PLUS_I32)
+        return self._A, B
+
+    def batches(self, count, seed0, nupd=None):
+        from workloads import EdgeStream
+        es = self._streams.get(seed0)
+        if es is None:
+            es = self._streams[seed0] = EdgeStream(self._A, self._held, seed0)
+        return [es.batch(nupd or self.batch) for _ in range(count)]
+
+
+WORKLOADS = {"stencil": StencilWorkload, "rmat20": Rmat20Workload}
 
 
 # --------------------------------------------------------------- clocks
@@ -111,7 +162,7 @@ class ClockSampler:
 def gpu_arm(args):
     import torch
     import paper_2202_08808_gb300 as pkg
-    from workloads import stencil7
+    W = WORKLOADS[args.workload]()
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -125,16 +176,17 @@ def gpu_arm(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    A = stencil7(GRID, GRID, GRID, seed=1)
-    g = pkg.DynamicSpGEMM(A)
+    A, B = W.operands()
+    g = pkg.DynamicSpGEMM(A, B)
     info = g.info()
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    vsize, s_entry = 8, 12  # double values; column + value bytes per entry
+    vsize = W.vsize
+    s_entry = 4 + vsize  # column + value bytes per entry
 
     # device-resident batches: warm-up + timed
     nb = args.warmup + args.steps
-    host_batches = make_batches(nb, 1000 * (rank + 1))
+    host_batches = W.batches(nb, 1000 * (rank + 1))
     dev_batches = []
     for b in host_batches:
         dev_batches.append(type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(),
@@ -144,6 +196,15 @@ def gpu_arm(args):
     g.set_profiling(True)
     for k in range(args.warmup):
         g.apply_batch(dev_batches[k])
+    tuned = None
+    if args.autotune > 0:
+        # bins chosen by measurement on calibration batches of the same workload
+        cal = [type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(), torch.from_numpy(b.val).cuda(),
+                       torch.from_numpy(b.op).cuda()) for b in W.batches(args.autotune, 3000 * (rank + 1))]
+        best, cand_ms = g.autotune(cal)
+        tuned = {"chosen": best, "candidate_ms": [round(x, 4) for x in cand_ms], "batches": args.autotune}
+        for k in range(2):
+            g.apply_batch(dev_batches[k])  # capture the pipeline with the chosen bins
     barrier()
 
     clocks = ClockSampler(local)
@@ -185,25 +246,33 @@ def gpu_arm(args):
     peak, peak_kind = peaks()
     achieved = alg_bytes / (numeric_ms * 1e-3) / 1e9 if numeric_ms > 0 else 0.0
 
-    # static comparator: full recompute of C from the same A', B' on the device
-    static_ms = []
-    for k in range(3):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        g.recompute_all()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        static_ms.append(e0.elapsed_time(e1))
-    static_med = statistics.median(static_ms)
+    # static comparator: full recompute of C from the same A', B' on the device,
+    # under the handle's bins and under the default bins; the faster counts
+    def time_static():
+        ts = []
+        for k in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.recompute_all()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+    static_runs = {"handle_bins": time_static()}
+    if tuned is not None:
+        g.set_tuning(None)
+        static_runs["default_bins"] = time_static()
+        g.set_tuning(tuned["chosen"])
+    static_med = min(static_runs.values())
 
     # end to end through the public API with pinned host buffers: upload of
     # the batch, apply, read back the affected row set and its rows of C
     e2e_ms, h2d, d2h = [], 0, 0
     pinned = []
-    for b in make_batches(max(3, min(args.steps, 10)), 5000 * (rank + 1)):
+    for b in W.batches(max(3, min(args.steps, 10)), 5000 * (rank + 1)):
         pinned.append(type(b)(torch.from_numpy(b.row).pin_memory(), torch.from_numpy(b.col).pin_memory(),
                               torch.from_numpy(b.val).pin_memory(), torch.from_numpy(b.op).pin_memory()))
     for k, b in enumerate(pinned):
@@ -222,8 +291,8 @@ def gpu_arm(args):
     # batch-size sweep (latency and speedup at 10^3 .. 10^6)
     sweep = []
     if not args.no_sweep:
-        for nupd in (1000, 10000, 100000, 1000000):
-            bs = make_batches(3, 9000 + nupd, nupd)
+        for nupd in W.sweep:
+            bs = W.batches(3, 9000 + nupd, nupd)
             ts = []
             for b in bs:
                 db = type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(),
@@ -238,17 +307,18 @@ def gpu_arm(args):
                 torch.cuda.synchronize()
                 ts.append(e0.elapsed_time(e1))
             med = statistics.median(ts)
-            sweep.append({"batch": nupd, "frac_nnz_a": nupd / A.nnz, "latency_ms": round(med, 4),
+            sweep.append({"batch": nupd, "entries": len(bs[0]), "frac_nnz_a": len(bs[0]) / A.nnz,
+                          "latency_ms": round(med, 4),
                           "speedup_vs_static": round(static_med / med, 2), "affected_rows": st["affected_rows"]})
 
     out = None
     if rank == 0:
-        cpu = None if args.no_cpu else cpu_baseline(args, budget_s=args.cpu_budget)
+        cpu = None if args.no_cpu else cpu_baseline(args, W, budget_s=args.cpu_budget)
         ms_per_step = total_ms / args.steps
         out = {
             "metric": METRIC,
             "value": round(world * args.steps / (total_ms * 1e-3), 3),
-            "unit": "batches/s (10^4-update batches)",
+            "unit": W.unit,
             "n_gpus": world,
             "steps": args.steps,
             "warmup": args.warmup,
@@ -256,21 +326,24 @@ def gpu_arm(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64",
+            "dtype": W.dtype,
             "data": "synthetic",
-            "config": {"workload": "stencil 128^3 7-point, C = A A (+,.) f64, batches of 10^4 mixed updates",
-                       "n": info["n"], "nnz_a": info["nnz_a"], "nnz_c": info["nnz_c"], "batch": BATCH,
+            "config": {"workload": W.describe,
+                       "n": info["n"], "nnz_a": info["nnz_a"], "nnz_c": info["nnz_c"], "batch": W.batch,
+                       "batch_entries": len(host_batches[0]),
                        "l2": "flushed before every timed step (256 MiB write)", "parallelism": f"replicas x{world}"},
             "latency_ms": {"mean": round(statistics.mean(lat), 4), "p50": round(statistics.median(lat), 4),
                            "p99": round(float(np.percentile(lat, 99)), 4)},
             "static_recompute_ms": round(static_med, 3),
+            "static_runs_ms": {k: round(v, 3) for k, v in static_runs.items()},
+            "tuning": tuned,
             "speedup_vs_static": round(static_med / statistics.median(lat), 2),
             "stages_ms": {s: round(v / args.steps, 4) for s, v in stage_acc.items()},
             "roofline": {"bound": "hbm", "kernel": "numeric recompute (all bins) of the affected rows",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                          "alg_bytes_per_step": int(alg_bytes / args.steps), "traffic": None},
-            "e2e": {"value": round(1e3 / e2e_mean, 3), "unit": "batches/s (10^4-update batches)",
+            "e2e": {"value": round(1e3 / e2e_mean, 3), "unit": W.unit,
                     "latency_ms": round(e2e_mean, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "gpu_launches_per_step": round(launches / args.steps, 1),
@@ -700,22 +773,22 @@ def learned_cpu_baseline(A, held, budget_s):
 
 # ------------------------------------------------------------ CPU oracle
 
-def cpu_baseline(args, budget_s=20.0, steps=None):
+def cpu_baseline(args, W, budget_s=20.0, steps=None):
     """The oracle's row-dynamic route (apply, affected rows, recompute of R)
-    on a bounded sample of the same workload: consecutive 10^4 batches until
-    the time budget is used; single-threaded C."""
+    on a bounded sample of the same workload: consecutive batches until the
+    time budget is used; single-threaded C."""
     import oracle
     from oracle import OMat
-    from workloads import stencil7
-    A = stencil7(GRID, GRID, GRID, seed=1)
+    A, B = W.operands()
     Ao = OMat.from_csr(A)
-    Co = Ao.multiply(Ao)
+    Bo = OMat.from_csr(B) if B is not None else None
+    Co = Ao.multiply(Bo if Bo is not None else Ao)
     times = []
     k = 0
     while True:
-        b = make_batches(1, 70000 + k)[0]
+        b = W.batches(1, 70000 + k)[0]
         t0 = time.perf_counter()
-        oracle.row_dynamic(Ao, Co, b)
+        oracle.row_dynamic(Ao, Co, b, Bo)
         times.append(time.perf_counter() - t0)
         k += 1
         if steps is not None and k >= steps:
@@ -723,9 +796,9 @@ def cpu_baseline(args, budget_s=20.0, steps=None):
         if steps is None and (sum(times) > budget_s or k >= 200):
             break
     mean = statistics.mean(times)
-    return {"value": round(1.0 / mean, 4), "unit": "batches/s (10^4-update batches)", "cores": 1,
+    return {"value": round(1.0 / mean, 4), "unit": W.unit, "cores": 1,
             "kind": "oracle", "latency_ms": round(mean * 1e3, 3),
-            "sample": f"{k} consecutive 10^4-update batches on the 128^3 stencil (apply + affected rows + row recompute)",
+            "sample": f"{k} consecutive batches of the workload ({W.describe}): apply + affected rows + row recompute",
             "times_ms": [round(t * 1e3, 2) for t in times[:20]]}
 
 
@@ -733,13 +806,13 @@ def reference_arm(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    res = cpu_baseline(args, steps=args.steps)
+    W = WORKLOADS[args.workload if args.workload in WORKLOADS else "stencil"]()
+    res = cpu_baseline(args, W, steps=args.steps)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": res["value"], "unit": res["unit"], "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["latency_ms"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "stencil 128^3 7-point, C = A A (+,.) f64, batches of 10^4 mixed updates",
-                   "batch": BATCH},
+        "scaling": "weak", "vs_baseline": None, "dtype": W.dtype, "data": "synthetic",
+        "config": {"workload": W.describe, "batch": W.batch},
         "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": res["sample"], "value": res["value"]},
         "e2e": {"value": res["value"], "unit": res["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -762,7 +835,7 @@ def profile_arm(args):
         torch.cuda.nvtx.range_pop()
         print("static profiled")
         return
-    bs = make_batches(4, 100, args.batch)
+    bs = StencilWorkload().batches(4, 100, args.batch)
     dev = [type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(), torch.from_numpy(b.val).cuda(),
                    torch.from_numpy(b.op).cuda()) for b in bs]
     for b in dev[:3]:
@@ -787,9 +860,12 @@ def main():
     ap.add_argument("--profile", choices=["step", "static"], default=None,
                     help="run one NVTX-marked step or static recompute for ncu, then exit")
     ap.add_argument("--batch", type=int, default=BATCH)
-    ap.add_argument("--workload", choices=["stencil", "batched", "learned"], default="stencil",
-                    help="stencil: the 128^3 stencil with 10^4-update batches; batched: 256 R-MAT instances; "
-                         "learned: learned vs exact vs bound sizing and the serving loop on R-MAT scale 21")
+    ap.add_argument("--workload", choices=["stencil", "rmat20", "batched", "learned"], default="stencil",
+                    help="stencil: the 128^3 stencil with 10^4-update batches; rmat20: R-MAT scale 20 (min,+) "
+                         "A B with 10^3-edge batches; batched: 256 R-MAT instances; learned: learned vs exact vs "
+                         "bound sizing and the serving loop on R-MAT scale 21")
+    ap.add_argument("--autotune", type=int, default=0,
+                    help="stencil/rmat20: choose the row bins on this many calibration batches before timing")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--scale", type=int, default=21)
     ap.add_argument("--train-graphs", type=int, default=4)

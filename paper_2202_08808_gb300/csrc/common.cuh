@@ -71,7 +71,8 @@ struct Ctl {
     long long a_entries;       // A' entries read by the recompute
     long long n_est;           // rows sized by the learned estimator
     long long n_ovf;           // of those, rows whose table overflowed
-    long long pad[4];
+    long long n_long;          // rows with long A rows, sized by a CTA each
+    long long pad[3];
 };
 
 // A row-slack CSR ("slack-CSR") on the device: row i occupies

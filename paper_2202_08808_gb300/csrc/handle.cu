@@ -188,6 +188,13 @@ struct CWs {
     // learned sizing: rows waiting for an estimate, rows whose table overflowed
     DBuf<int4> est;
     DBuf<int32_t> ovf;
+    DBuf<int32_t> longr;  // rows with long A rows (sizing)
+    // split rows (dense mode): global accumulators
+    int64_t sp_rows = 0;
+    DBuf<char> sp_acc;
+    DBuf<uint32_t> sp_mask;
+    DBuf<int> sp_done;
+    DBuf<int64_t> sp_pre;
 };
 
 struct BatchIn {
@@ -383,12 +390,23 @@ void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
     CK(cudaMemsetAsync(w.bmR.p, 0, sizeof(uint32_t) * w.bmR.n, s));
     w.est.reserve(nn);
     w.ovf.reserve(nn);
+    w.longr.reserve(nn);
     const int64_t nb = std::max<int64_t>(h->Bm().nrows, 1);
     w.nrows_b = nb;
     w.bmK.reserve(nb / 32 + 2);
     CK(cudaMemsetAsync(w.bmK.p, 0, sizeof(uint32_t) * w.bmK.n, s));
     w.K.reserve(nb);
     const int64_t m = h->Bm().ncols;
+    if (m <= DENSE_M_MAX) {  // split rows: as many as 256 MiB of accumulators hold, at most 65536
+        const int64_t mp = (m + 31) / 32 * 32;
+        w.sp_rows = std::min<int64_t>(65536, (256LL << 20) / (mp * h->vsize + mp / 8));
+        w.sp_pre.reserve(w.sp_rows + 1);
+        w.sp_acc.reserve(w.sp_rows * mp * h->vsize);
+        w.sp_mask.reserve(w.sp_rows * mp / 32);
+        w.sp_done.reserve(w.sp_rows);
+        init_dense_scratch(h->sr, w.sp_acc.p, w.sp_mask.p, w.sp_rows * mp, w.sp_rows * mp / 32, s);
+        CK(cudaMemsetAsync(w.sp_done.p, 0, sizeof(int) * w.sp_rows, s));
+    }
     if (m > DENSE_M_MAX) {
         w.gd_w = (m + 31) / 32 * 32;
         // per-CTA dense accumulators for the longest rows: up to two CTAs per
@@ -434,6 +452,12 @@ CJob c_job(dspg_handle *h, const int32_t *R, bool static_mode) {
     J.est_w = h->est_w.p;
     J.est = w.est.p;
     J.ovf = w.ovf.p;
+    J.longr = w.longr.p;
+    J.sp_rows = J.dense_mode ? w.sp_rows : 0;
+    J.sp_acc = w.sp_acc.p;
+    J.sp_mask = w.sp_mask.p;
+    J.sp_done = w.sp_done.p;
+    J.sp_pre = w.sp_pre.p;
     return J;
 }
 
@@ -658,6 +682,7 @@ CJob size_exact(dspg_handle *h, const int32_t *R, int64_t n_max, cudaStream_t s)
     numeric_branches(h, s, Jc);
     CK(cudaMemsetAsync(h->ctl->bin_count, 0, sizeof(h->ctl->bin_count), s));
     CK(cudaMemsetAsync(&h->ctl->nnz_written, 0, sizeof(long long), s));
+    CK(cudaMemsetAsync(&h->ctl->n_long, 0, sizeof(long long), s));  // the second pass lists long rows again
     CJob J2 = J;
     J2.sizing = SIZE_COUNT;
     run_size_bins(h->A.view(), h->Bm().view(), h->C.view(), J2, n_max, h->ctl, M_AB, s, h->num_sms);

@@ -93,6 +93,15 @@ struct CJob {
     const uint16_t *est_w;    // estimator weights, bfloat16 bits (EST_PARAMS)
     int4 *est;                // rows waiting for an estimate: {t, len(A_i), max len(B_k), bound}
     int32_t *ovf;             // rows (of C) whose learned table overflowed
+    int32_t *longr;           // rows of R (indices t) whose A row is long (sized by a CTA each)
+    // split rows (dense mode): rows with many A entries or products are cut
+    // into chunks recomputed by different CTAs and combined in global
+    // accumulators (sp_rows rows at a time)
+    int64_t sp_rows;
+    void *sp_acc;             // sp_rows x mp accumulators
+    uint32_t *sp_mask;        // sp_rows x mp/32 presence bits
+    int *sp_done;             // sp_rows counters of folded chunks
+    int64_t *sp_pre;          // sp_rows + 1: prefix of the split rows' chunk counts
 };
 enum { SIZE_BOUND = 0, SIZE_COUNT = 1, SIZE_LEARNED = 2 };
 

@@ -60,7 +60,7 @@ enum {
     BIN_T8 = 0, BIN_G8, BIN_G16, BIN_W128, BIN_W256, BIN_W512, BIN_W1024,
     BIN_C2048, BIN_C4096, BIN_C8192,
     BIN_GD,
-    BIN_WDENSE, BIN_CDENSE,
+    BIN_WDENSE, BIN_CDENSE, BIN_DSPLIT,
     BIN_COUNT
 };
 static_assert(BIN_COUNT <= NBINS, "bin counters");
@@ -98,9 +98,14 @@ __device__ __forceinline__ int pick_table_bin(long long need, const CJob &J) {
 // tables are sized by an exact count, that count).  A table is never smaller
 // than the size it is given, so with the bound or an exact count no choice
 // of thresholds can make a table overflow.
-__device__ __forceinline__ int pick_bin(long long ubc, int alen, const CJob &J, long long table_need) {
+// With dense accumulators (few columns) the work of a row is its A entries
+// (each gathers a B row) and its products, not the capped bound: a warp for
+// short rows, else a CTA (rows with very many products are split later).
+constexpr int DENSE_WARP_A = 64;
+__device__ __forceinline__ int pick_bin(long long ubc, int alen, const CJob &J, long long table_need,
+                                        long long ub) {
     if (alen <= J.tm_k && ubc <= J.tm_ub) return BIN_T8;
-    if (J.dense_mode) return ubc <= 4096 ? BIN_WDENSE : BIN_CDENSE;
+    if (J.dense_mode) return (alen <= DENSE_WARP_A && ub <= 4096) ? BIN_WDENSE : BIN_CDENSE;
     return pick_table_bin(table_need, J);
 }
 
@@ -116,25 +121,52 @@ __device__ __forceinline__ void append_bins(const CJob &J, Ctl *ctl, int b, long
     if (b >= 0) J.bins[(int64_t)b * J.bin_cap + bb + __popc(peers & lanemask_lt())] = (int32_t)t;
 }
 
-constexpr int SIZE_SHORT = 64;  // A rows up to this length are sized by one thread
+constexpr int SIZE_SHORT = 64;   // A rows up to this length are sized by one thread,
+constexpr int SIZE_LONG = 512;   // up to this by a warp, longer ones by a CTA (k_size_long)
+constexpr long long SPLIT_MIN = 8192;  // dense mode: rows with more products, or with more than
+constexpr int SPLIT_A = 256;           // SPLIT_A A entries, are split in chunks (k_num_dsplit)
+constexpr int SPLIT_CHUNK = 2048;      // A entries per work item of a split row
+
+// Dense mode: claim a split slot for a row with very many products; false
+// when all slots are taken (the row then goes to the CTA dense bin).
+__device__ __forceinline__ bool claim_split(const CJob &J, Ctl *ctl, long long t) {
+    const long long slot = atomic_add_ll2(&ctl->bin_count[BIN_DSPLIT], 1);
+    if (slot >= J.sp_rows) return false;
+    J.bins[(int64_t)BIN_DSPLIT * J.bin_cap + slot] = (int32_t)t;
+    return true;
+}
+
+__device__ __forceinline__ bool wants_est(const CJob &J, long long ub, long long ubc, bool t8) {
+    return ub > 0 && J.sizing == SIZE_LEARNED && !t8 && !J.dense_mode && ubc > J.est_min;
+}
+
+__device__ __forceinline__ void push_est(const CJob &J, Ctl *ctl, long long t, int alen, long long bmax, long long ub) {
+    const int4 e = make_int4((int)t, alen, (int)bmax, (int)(ub < 0x7fffffffLL ? ub : 0x7fffffffLL));
+    J.est[atomic_add_ll2(&ctl->n_est, 1)] = e;
+}
 
 // One thread per row of R sums the B-row lengths of its A entries (rows
-// longer than SIZE_SHORT are summed by the whole warp afterwards); then the
-// warp hands out bin slots (and, for the static product, the row's place in
-// a fresh C) with one atomic per counter.  With SIZE_COUNT the tables are
-// sized by C.len (an exact count from a count_only pass); with SIZE_LEARNED
-// rows whose bound exceeds est_min go to the estimate list instead of a bin.
+// longer than SIZE_SHORT are summed by the whole warp afterwards, rows
+// longer than SIZE_LONG by a CTA in k_size_long); then the warp hands out
+// bin slots (and, for the static product, the row's place in a fresh C)
+// with one atomic per counter.  With SIZE_COUNT the tables are sized by
+// C.len (an exact count from a count_only pass); with SIZE_LEARNED rows
+// whose bound exceeds est_min go to the estimate list instead of a bin.
 __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask) {
     if (failed(ctl, mask)) return;
     const long long nR = ctl->n_affected;
     const int lane = threadIdx.x & 31;
-    long long prod_acc = 0, a_acc = 0, est_acc = 0;
+    long long prod_acc = 0, a_acc = 0;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < nR; base += (long long)gridDim.x * blockDim.x) {
         const long long t = base + threadIdx.x;
-        const bool valid = t < nR;
+        bool valid = t < nR;
         const int32_t i = valid ? J.R[t] : 0;
         const int64_t aoff = valid ? A.off[i] : 0;
         const int alen = valid ? A.len[i] : 0;
+        if (valid && alen > SIZE_LONG) {  // a CTA sizes this row later
+            J.longr[atomic_add_ll2(&ctl->n_long, 1)] = (int32_t)t;
+            valid = false;
+        }
         const bool lng = alen > SIZE_SHORT;
         long long ub = 0, bmax = 0;
         if (valid && !lng)
@@ -181,18 +213,14 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
             if (ub == 0) C.len[i] = 0;  // no products: the row becomes empty
         }
         const bool t8 = alen <= J.tm_k && ubc <= J.tm_ub;
-        const bool to_est = valid && ub > 0 && J.sizing == SIZE_LEARNED && !t8 && !J.dense_mode && ubc > J.est_min;
+        const bool to_est = valid && wants_est(J, ub, ubc, t8);
         long long need = ubc;
         if (J.sizing == SIZE_COUNT && valid) need = C.len[i];
-        const int b = (valid && ub > 0 && !to_est) ? pick_bin(ubc, alen, J, need) : -1;
+        int b = (valid && ub > 0 && !to_est) ? pick_bin(ubc, alen, J, need, ub) : -1;
+        if (b == BIN_CDENSE && (ub > SPLIT_MIN || alen > SPLIT_A) && claim_split(J, ctl, t)) b = -1;
         append_bins(J, ctl, b, t);
-        if (to_est) {
-            const int4 e = make_int4((int)t, alen, (int)bmax, (int)(ub < 0x7fffffffLL ? ub : 0x7fffffffLL));
-            const long long at = atomic_add_ll2(&ctl->n_est, 1);
-            J.est[at] = e;
-            est_acc++;
-        }
-        if (J.sizing != SIZE_COUNT) {
+        if (to_est) push_est(J, ctl, t, alen, bmax, ub);
+        if (J.sizing != SIZE_COUNT && valid) {
             prod_acc += ub;
             a_acc += alen;
         }
@@ -202,6 +230,79 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
     if (lane == 0) {
         if (prod_acc) atomic_add_ll2(&ctl->products, prod_acc);
         if (a_acc) atomic_add_ll2(&ctl->a_entries, a_acc);
+    }
+}
+
+// Rows of R with more than SIZE_LONG A entries: a CTA each sums the B-row
+// lengths (several loads in flight per thread) and bins the row as above.
+__global__ void __launch_bounds__(256) k_size_long(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask) {
+    __shared__ long long s_sum[8], s_max[8];
+    if (failed(ctl, mask)) return;
+    const long long cnt = ctl->n_long;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
+        const long long t = J.longr[it];
+        const int32_t i = J.R[t];
+        const int64_t aoff = A.off[i];
+        const int alen = A.len[i];
+        long long s = 0, mx = 0;
+        for (int a0 = 0; a0 < alen; a0 += 256 * 4) {
+            long long l[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int a = a0 + u * 256 + tid;
+                l[u] = a < alen ? (long long)B.len[__ldg(A.col + aoff + a)] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                s += l[u];
+                mx = l[u] > mx ? l[u] : mx;
+            }
+        }
+        s = warp_sum<long long>(s);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const long long y = __shfl_xor_sync(0xffffffffu, mx, d);
+            mx = y > mx ? y : mx;
+        }
+        if (lane == 0) {
+            s_sum[w] = s;
+            s_max[w] = mx;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            long long ub = 0, bmax = 0;
+            for (int k = 0; k < 8; k++) {
+                ub += s_sum[k];
+                bmax = s_max[k] > bmax ? s_max[k] : bmax;
+            }
+            const long long ubc = ub < J.m ? ub : J.m;
+            if (J.static_mode) {
+                const int32_t c = slack_cap(ubc, J.slack_min, J.slack_div);
+                const long long d = atomic_add_ll2(C.top, c);
+                C.off[i] = d;
+                C.cap[i] = c;
+                C.len[i] = 0;
+                if (d + c > C.arena_cap) set_status(ctl, ST_C_ARENA);
+            } else if (J.sizing != SIZE_COUNT) {
+                J.bmR[i >> 5] = 0u;
+                if (ub == 0) C.len[i] = 0;
+            }
+            const bool t8 = alen <= J.tm_k && ubc <= J.tm_ub;
+            if (wants_est(J, ub, ubc, t8)) {
+                push_est(J, ctl, t, alen, bmax, ub);
+            } else if (ub > 0) {
+                const long long need = J.sizing == SIZE_COUNT ? (long long)C.len[i] : ubc;
+                const int b = pick_bin(ubc, alen, J, need, ub);
+                if (!(b == BIN_CDENSE && (ub > SPLIT_MIN || alen > SPLIT_A) && claim_split(J, ctl, t)))
+                    J.bins[(int64_t)b * J.bin_cap + atomic_add_ll2(&ctl->bin_count[b], 1)] = (int32_t)t;
+            }
+            if (J.sizing != SIZE_COUNT) {
+                atomic_add_ll2(&ctl->products, ub);
+                atomic_add_ll2(&ctl->a_entries, alen);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -267,16 +368,19 @@ constexpr int PU = 4;  // products per lane whose B loads are issued together
 
 // Calls emit(j, a (x) b) for every product of row i; the G lanes of one
 // group (G = 8, 16 or 32 consecutive lanes, mask gmask) share the work.
+// (Only the A entries a_begin, a_begin + a_step, ... below a_end, in groups
+// of G, when given: the warps of a CTA can share a row this way without
+// block-wide barriers.)
 template <int SR, int G, class F>
 __device__ __forceinline__ void group_products(const MatView &A, const MatView &B, int32_t i, unsigned gmask,
-                                               F emit) {
+                                               F emit, int a_begin = 0, int a_end = -1, int a_step = G) {
     using T = typename Sr<SR>::T;
     const int gl = threadIdx.x & (G - 1);
     const int64_t aoff = A.off[i];
-    const int alen = A.len[i];
+    const int alen = a_end >= 0 ? a_end : A.len[i];
     const T *Av = (const T *)A.val;
     const T *Bv = (const T *)B.val;
-    for (int a0 = 0; a0 < alen; a0 += G) {
+    for (int a0 = a_begin; a0 < alen; a0 += a_step) {
         const int ai = a0 + gl;
         int blen = 0;
         int64_t boff = 0;
@@ -879,9 +983,6 @@ __global__ void __launch_bounds__(512)
 k_num_cta_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin, int mp) {
     using T = typename Sr<SR>::T;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int64_t p_boff[512];
-    __shared__ T p_av[512];
-    __shared__ int p_incl[512], p_blen[512], p_wsum[32];
     if (failed(ctl, mask)) return;
     const int tid = threadIdx.x, lane = tid & 31;
     const int nw = mp >> 5;
@@ -891,16 +992,15 @@ k_num_cta_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask
     for (int s = tid; s < mp; s += 512) acc[s] = Sr<SR>::zero();
     if (tid < 32) msk[tid] = 0u;
     __syncthreads();
-    BlockProdSmem<T> ps{p_boff, p_av, p_incl, p_blen, p_wsum};
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
         const int t = J.bins[(int64_t)bin * J.bin_cap + it];
         const int32_t i = J.R[t];
-        block_products<SR>(A, B, i, ps, [&](int32_t j, T v) {
+        group_products<SR, 32>(A, B, i, 0xffffffffu, [&](int32_t j, T v) {
             atomicOr(&msk[j >> 5], 1u << (j & 31));
             Sr<SR>::acc(&acc[j], v);
-        });
+        }, (tid >> 5) * 32, -1, 512);
         __syncthreads();
         if (tid < 32) {
             const uint32_t word = lane < nw ? msk[lane] : 0u;
@@ -957,6 +1057,8 @@ void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const C
     if (g > num_sms * 8) g = num_sms * 8;
     if (g < 1) g = 1;
     launch_k(k_size_bins, (unsigned)g, 256, 0, s, A, B, C, J, ctl, mask);
+    launch_k(k_size_long, (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * 2, (max_rows + 1) / 2)),
+             256, 0, s, A, B, C, J, ctl, mask);
     if (J.sizing == SIZE_LEARNED) {
         constexpr size_t smem = EST_PARAMS * sizeof(float) + 16;
         static bool set = false;
@@ -969,6 +1071,146 @@ void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const C
         if (ge < 1) ge = 1;
         launch_k(k_est_bins, (unsigned)ge, 128, smem, s, J, ctl, mask);
     }
+}
+
+// ---------------------------------------------------- split dense rows
+
+// Dense mode, rows with many A entries or products (the hubs of skewed
+// graphs): each split row is cut into chunks of SPLIT_CHUNK A entries, and
+// the chunks of all split rows form one work list (k_split_prep writes its
+// prefix over the rows, sp_pre).  A CTA accumulates a chunk in shared memory
+// and folds it into the row's global accumulator with atomics; the CTA that
+// folds a row's last chunk (a per-row counter) writes the row into C in
+// column order and resets the accumulator for the next launch.
+__global__ void __launch_bounds__(1024) k_split_prep(MatView A, CJob J, Ctl *ctl, unsigned mask) {
+    __shared__ int incl[1024], wsum[32];
+    if (failed(ctl, mask)) return;
+    long long cnt = ctl->bin_count[BIN_DSPLIT];
+    if (cnt > J.sp_rows) cnt = J.sp_rows;
+    long long carry = 0;
+    for (long long b0 = 0; b0 < cnt; b0 += 1024) {
+        const long long slot = b0 + threadIdx.x;
+        int nch = 0;
+        if (slot < cnt) {
+            const int32_t i = J.R[J.bins[(int64_t)BIN_DSPLIT * J.bin_cap + slot]];
+            nch = (A.len[i] + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
+        }
+        const int tot = block_incl_scan(nch, incl, wsum);
+        if (slot < cnt) J.sp_pre[slot] = carry + incl[threadIdx.x] - nch;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) J.sp_pre[cnt] = carry;
+}
+
+template <int SR>
+__global__ void __launch_bounds__(512)
+k_num_dsplit(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int mp) {
+    using T = typename Sr<SR>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_last;
+    __shared__ long long s_dest;
+    __shared__ int s_n;
+    if (failed(ctl, mask)) return;
+    const int tid = threadIdx.x;
+    const int nw = mp >> 5;
+    T *acc = (T *)smem;
+    uint32_t *msk = (uint32_t *)(acc + mp);
+    T *Cv = (T *)C.val;
+    for (int s = tid; s < mp; s += 512) acc[s] = Sr<SR>::zero();
+    if (tid < 32) msk[tid] = 0u;
+    __syncthreads();
+    long long cnt = ctl->bin_count[BIN_DSPLIT];
+    if (cnt > J.sp_rows) cnt = J.sp_rows;
+    const long long total = cnt > 0 ? J.sp_pre[cnt] : 0;
+    long long nnz_acc = 0;
+    // each CTA takes a contiguous range of work items: one search for its
+    // first row, then forward; consecutive chunks of a row are accumulated
+    // together and folded once
+    const long long per = (total + gridDim.x - 1) / gridDim.x;
+    const long long w0 = (long long)blockIdx.x * per, w1 = w0 + per < total ? w0 + per : total;
+    long long slot = 0;
+    if (w0 < w1) {
+        long long lo = 0, hi = cnt;  // last slot with sp_pre[slot] <= w0
+        while (hi - lo > 1) {
+            const long long mid = (lo + hi) >> 1;
+            if (J.sp_pre[mid] <= w0) lo = mid; else hi = mid;
+        }
+        slot = lo;
+    }
+    int pending = 0;  // chunks accumulated in shared memory, not yet folded
+    for (long long w = w0; w < w1; w++) {
+        while (J.sp_pre[slot + 1] <= w) slot++;
+        const long long base = J.sp_pre[slot];
+        const int nch = (int)(J.sp_pre[slot + 1] - base);
+        const int c = (int)(w - base);
+        const int32_t i = J.R[J.bins[(int64_t)BIN_DSPLIT * J.bin_cap + slot]];
+        const int alen = A.len[i];
+        const int a_lo = c * SPLIT_CHUNK, a_hi = a_lo + SPLIT_CHUNK < alen ? a_lo + SPLIT_CHUNK : alen;
+        // each warp takes groups of 32 A entries of the chunk (no block barriers)
+        group_products<SR, 32>(A, B, i, 0xffffffffu, [&](int32_t j, T v) {
+            atomicOr(&msk[j >> 5], 1u << (j & 31));
+            Sr<SR>::acc(&acc[j], v);
+        }, a_lo + (tid >> 5) * 32, a_hi, 512);
+        pending++;
+        if (c + 1 < nch && w + 1 < w1) continue;  // the next item is this row's next chunk: keep accumulating
+        __syncthreads();
+        T *gacc = (T *)J.sp_acc + slot * mp;
+        uint32_t *gmsk = J.sp_mask + slot * nw;
+        for (int j = tid; j < mp; j += 512)
+            if (msk[j >> 5] & (1u << (j & 31))) {
+                Sr<SR>::acc(&gacc[j], acc[j]);
+                acc[j] = Sr<SR>::zero();
+            }
+        __syncthreads();
+        if (tid < nw && msk[tid]) atomicOr(&gmsk[tid], msk[tid]);
+        __syncthreads();
+        if (tid < 32) msk[tid] = 0u;
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_last = atomicAdd(&J.sp_done[slot], pending) == nch - pending;
+        pending = 0;
+        __syncthreads();
+        if (s_last) {  // every chunk of the row is folded: write the row
+            __threadfence();
+            if (tid < 32) {
+                const int lane = tid;
+                const uint32_t word = lane < nw ? __ldcg(gmsk + lane) : 0u;
+                const int pc = __popc(word);
+                const int incl = warp_incl_scan<int>(pc);
+                const int n = __shfl_sync(0xffffffffu, incl, 31);
+                int64_t dest = 0;
+                if (lane == 0) dest = c_row_dest(C, J, ctl, i, n);
+                dest = __shfl_sync(0xffffffffu, dest, 0);
+                int o = incl - pc;
+                uint32_t bits = word;
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int j = (lane << 5) + b;
+                    if (dest >= 0) {
+                        C.col[dest + o] = j;
+                        Cv[dest + o] = __ldcg(gacc + j);
+                    }
+                    o++;
+                }
+                if (lane == 0) {
+                    s_dest = dest;
+                    s_n = n;
+                }
+            }
+            __syncthreads();
+            for (int j = tid; j < mp; j += 512) gacc[j] = Sr<SR>::zero();
+            if (tid < nw) gmsk[tid] = 0u;
+            if (tid == 0) {
+                if (s_dest >= 0) C.len[i] = s_n;
+                nnz_acc += s_n;
+                J.sp_done[slot] = 0;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
 }
 
 // A persistent grid of `full` blocks, but no more blocks than it takes for
@@ -1049,8 +1291,17 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
         launch_k(k_num_warp_dense<SR, NW>, grid_for(num_sms * 4, J.rows_hint, NW), NW * 32, smem_w, next(), A, B, C, J,
                  ctl, mask, (int)BIN_WDENSE, mp);
         const size_t smem_c = (size_t)mp * sizeof(T) + 32 * sizeof(uint32_t);
-        launch_k(k_num_cta_dense<SR>, grid_for(num_sms, J.rows_hint, 1), 512, smem_c, next(), A, B, C, J, ctl, mask,
-                 (int)BIN_CDENSE, mp);
+        launch_k(k_num_cta_dense<SR>, grid_for((int64_t)num_sms * 2, J.rows_hint, 1), 512, smem_c, next(), A, B, C, J,
+                 ctl, mask, (int)BIN_CDENSE, mp);
+        // every CTA of the split kernel must run to the end (the last one to
+        // arrive at a row writes it), so it tests only the status bits of
+        // the stages before the recompute, which no sibling kernel can set
+        if (J.sp_rows > 0) {
+            const cudaStream_t ss = next();
+            const unsigned early = mask & (ST_INVALID | ST_AB_STAGE | ST_AB_ARENA);
+            launch_k(k_split_prep, 1, 1024, 0, ss, A, J, ctl, early);
+            launch_k(k_num_dsplit<SR>, (unsigned)(2 * num_sms), 512, smem_c, ss, A, B, C, J, ctl, early, mp);
+        }
         return;
     }
     launch_group_hash<SR, 6, 16, 8>(A, B, C, J, ctl, mask, BIN_G16, next(), num_sms);

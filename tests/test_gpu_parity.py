@@ -339,3 +339,73 @@ def test_exact_two_pass_static_layout(dspg, sr):
     _check_state(g, Ao, None, "exact static + batch")
     g.recompute_all()
     _check_state(g, Ao, None, "exact static recompute")
+
+
+def _with_hubs(n, k, hub_rows, hub_len, sr, seed, short_max=12):
+    """n x k matrix: rows of 0..short_max random columns, and the rows in
+    hub_rows with hub_len columns each (the hubs of skewed graphs)."""
+    from workloads import CSR
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    for i in range(n):
+        L = hub_len if i in hub_rows else int(rng.integers(0, short_max + 1))
+        c = rng.choice(k, size=min(L, k), replace=False)
+        rows.append(np.full(c.shape[0], i, np.int64))
+        cols.append(c.astype(np.int64))
+    r, c = np.concatenate(rows), np.concatenate(cols)
+    order = np.argsort(r * k + c, kind="stable")
+    r, c = r[order], c[order]
+    v = rng.random(r.shape[0]) if sr == PLUS_TIMES_F64 else rng.integers(1, 101, r.shape[0]).astype(np.int32)
+    rowptr = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(r, minlength=n), out=rowptr[1:])
+    return CSR(n, k, rowptr, c.astype(np.int32), v)
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_hub_rows_split_across_ctas_small_m(dspg, sr):
+    """C with 256 columns (dense accumulators): rows of A with 3000-5000
+    entries over B rows of ~25 entries have over 16384 products each, so the
+    split kernel recomputes them with every CTA (a chunk of the A row each);
+    their A rows are also longer than a warp sizes (a CTA sizes them).  Static
+    build and batches that touch the hubs, against the oracle."""
+    hubs = {3, 700, 701, 1999}
+    A = _with_hubs(2000, 6000, hubs, 4000, sr, 151)
+    B = bernoulli_sparse(6000, 256, 0.1, seed=152, kind=sr)
+    g = dspg.DynamicSpGEMM(A, B)
+    Ao, Bo = OMat.from_csr(A), OMat.from_csr(B)
+    _check_state(g, Ao, Bo, "hub build")
+    Co = Ao.multiply(Bo)
+    for k in range(3):
+        b = random_batch(A.nrows, A.ncols, 400, 153 + k, sr, A=A)
+        # a few more updates on the hub rows themselves
+        extra = random_batch(A.nrows, A.ncols, 60, 160 + k, sr, A=A)
+        extra.row[:] = np.array(sorted(hubs), np.int32)[np.arange(60) % len(hubs)]
+        from workloads import concat_batches
+        bb = concat_batches(b, extra)
+        st = g.apply_batch(bb)
+        R = oracle.row_dynamic(Ao, Co, bb, Bo)
+        assert np.array_equal(g.last_affected(), R)
+        _check_state(g, Ao, Bo, f"hub batch {k}")
+    g.recompute_all()
+    _check_state(g, Ao, Bo, "hub recompute")
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_long_rows_sized_by_a_cta_wide_m(dspg, sr):
+    """C with 5000 columns (hash and global dense bins): A rows longer than
+    512 entries are sized by a CTA each; static build and batches against
+    the oracle."""
+    hubs = {0, 10, 11, 1499}
+    A = _with_hubs(1500, 5000, hubs, 3000, sr, 171)
+    B = random_csr(5000, 5000, 6, 172, sr)
+    g = dspg.DynamicSpGEMM(A, B)
+    Ao, Bo = OMat.from_csr(A), OMat.from_csr(B)
+    _check_state(g, Ao, Bo, "long-row build")
+    Co = Ao.multiply(Bo)
+    for k in range(2):
+        b = random_batch(A.nrows, A.ncols, 300, 173 + k, sr, A=A)
+        b.row[:40] = np.array(sorted(hubs), np.int32)[np.arange(40) % len(hubs)]
+        g.apply_batch(b)
+        R = oracle.row_dynamic(Ao, Co, b, Bo)
+        assert np.array_equal(g.last_affected(), R)
+        _check_state(g, Ao, Bo, f"long-row batch {k}")
