@@ -820,13 +820,14 @@ def reference_arm(args):
 
 def profile_arm(args):
     """One warmed-up dynamic step (NVTX range "step") or one static recompute
-    (NVTX range "static"), for ncu captures filtered with --nvtx-include."""
+    (NVTX range "static") of the stencil or R-MAT scale-20 workload, for ncu
+    captures filtered with --nvtx-include."""
     import torch
     import paper_2202_08808_gb300 as pkg
-    from workloads import stencil7
     torch.cuda.set_device(0)
-    A = stencil7(GRID, GRID, GRID, seed=1)
-    g = pkg.DynamicSpGEMM(A)
+    W = WORKLOADS[args.workload if args.workload in WORKLOADS else "stencil"]()
+    A, B = W.operands()
+    g = pkg.DynamicSpGEMM(A, B)
     if args.profile == "static":
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("static")
@@ -835,7 +836,8 @@ def profile_arm(args):
         torch.cuda.nvtx.range_pop()
         print("static profiled")
         return
-    bs = StencilWorkload().batches(4, 100, args.batch)
+    nupd = args.batch if args.workload == "stencil" else W.batch
+    bs = W.batches(4, 100, nupd)
     dev = [type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(), torch.from_numpy(b.val).cuda(),
                    torch.from_numpy(b.op).cuda()) for b in bs]
     for b in dev[:3]:

@@ -170,6 +170,7 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
         const bool lng = alen > SIZE_SHORT;
         long long ub = 0, bmax = 0;
         if (valid && !lng)
+#pragma unroll 8
             for (int a = 0; a < alen; a++) {
                 const long long l = B.len[A.col[aoff + a]];
                 ub += l;
@@ -538,37 +539,39 @@ __device__ __forceinline__ bool hash_acc(int32_t *keys, T *vals, int32_t j, T v)
 // ---------------------------------------------------- thread merge kernel
 
 // One thread per row with at most MERGE_K A entries and at most MERGE_UB
-// products: the column indices of the row's B entries are first copied to
-// shared memory with independent loads (all in flight together), and the
-// value at each list's head is loaded as soon as the head moves; the sorted
-// B rows
-// are merged like sorted lists, a cursor each; every output column comes out
-// in ascending order with its products folded in ascending k, so no table
-// and no sort are needed.  Shared memory is laid out [entry][thread], so the
-// lanes of a warp never share a bank.  Writes go to the row's place while
-// they fit its capacity; a row that outgrows it is counted to the end, moved
-// to the arena tail and merged again (rare).
+// products.  The row's B entries (columns and values) are first copied into
+// shared memory with asynchronous copies (cp.async: every copy of the row in
+// flight at once, no registers held), then the ≤ MERGE_K sorted B rows are
+// merged like sorted lists, a cursor each, entirely in shared memory: every
+// output column comes out in ascending order with its products folded in
+// ascending k, so no table and no sort are needed.  Shared memory is laid
+// out [entry][thread], so the lanes of a warp never share a bank.  Writes go
+// to the row's place while they fit its capacity; a row that outgrows it is
+// counted to the end, moved to the arena tail and merged again (rare).
 constexpr int TM_NT = 128;  // threads per block of the merge kernel
 
+__device__ __forceinline__ void cp_async_4(void *dst_smem, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void *dst_smem, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <int SR, int K>
-__device__ __forceinline__ int merge_rows_smem(const int32_t *scol, const typename Sr<SR>::T *Bv,
-                                               const typename Sr<SR>::T *av, const int64_t *boff, const int *start,
-                                               const int *blen, int alen, int32_t *out_col,
-                                               typename Sr<SR>::T *out_val, int limit) {
+__device__ __forceinline__ int merge_rows_smem(const int32_t *scol, const typename Sr<SR>::T *sval,
+                                               const typename Sr<SR>::T *av, const int *start, const int *blen,
+                                               int alen, int32_t *out_col, typename Sr<SR>::T *out_val, int limit) {
     using T = typename Sr<SR>::T;
     int pos[K], end[K];
     int32_t head[K];
-    T hval[K];  // value at each list's head, loaded when the head moves
 #pragma unroll
     for (int s = 0; s < K; s++) {
         pos[s] = start[s];
         end[s] = start[s] + (s < alen ? blen[s] : 0);
-        head[s] = 0x7fffffff;
-        hval[s] = T(0);
-        if (pos[s] < end[s]) {
-            head[s] = scol[pos[s] * TM_NT];
-            hval[s] = Bv[boff[s]];
-        }
+        head[s] = pos[s] < end[s] ? scol[pos[s] * TM_NT] : 0x7fffffff;
     }
     int n = 0;
     while (true) {
@@ -581,16 +584,11 @@ __device__ __forceinline__ int merge_rows_smem(const int32_t *scol, const typena
 #pragma unroll
         for (int s = 0; s < K; s++) {
             if (head[s] == j) {
-                const T v = Sr<SR>::mul(av[s], hval[s]);
+                const T v = Sr<SR>::mul(av[s], sval[pos[s] * TM_NT]);
                 acc = first ? v : Sr<SR>::add(acc, v);
                 first = false;
                 pos[s]++;
-                if (pos[s] < end[s]) {
-                    head[s] = scol[pos[s] * TM_NT];
-                    hval[s] = Bv[boff[s] + (pos[s] - start[s])];
-                } else {
-                    head[s] = 0x7fffffff;
-                }
+                head[s] = pos[s] < end[s] ? scol[pos[s] * TM_NT] : 0x7fffffff;
             }
         }
         if (n < limit) {
@@ -608,7 +606,8 @@ k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned m
     using T = typename Sr<SR>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     if (failed(ctl, mask)) return;
-    int32_t *scols = (int32_t *)smem + threadIdx.x;
+    T *svals = (T *)smem + threadIdx.x;                              // [UB][TM_NT] values
+    int32_t *scols = (int32_t *)((T *)smem + UB * TM_NT) + threadIdx.x;  // [UB][TM_NT] columns
     const T *Av = (const T *)A.val;
     const T *Bv = (const T *)B.val;
     T *Cv = (T *)C.val;
@@ -646,17 +645,22 @@ k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned m
         }
 #pragma unroll
         for (int s = 0; s < K; s++)
-            for (int q = 0; q < blen[s]; q++) scols[(start[s] + q) * TM_NT] = B.col[boff[s] + q];
+            for (int q = 0; q < blen[s]; q++) {
+                cp_async_4(&scols[(start[s] + q) * TM_NT], B.col + boff[s] + q);
+                if (sizeof(T) == 8) cp_async_8(&svals[(start[s] + q) * TM_NT], Bv + boff[s] + q);
+                else cp_async_4(&svals[(start[s] + q) * TM_NT], Bv + boff[s] + q);
+            }
+        cp_async_wait_all();
         const int64_t off = C.off[i];
         const int cap = J.count_only ? 0 : (J.static_mode ? 0x7fffffff : C.cap[i]);
-        const int n = merge_rows_smem<SR, K>(scols, Bv, av, boff, start, blen, alen, C.col + off, Cv + off, cap);
+        const int n = merge_rows_smem<SR, K>(scols, svals, av, start, blen, alen, C.col + off, Cv + off, cap);
         bool ok = true;
         if (J.count_only) {
             C.len[i] = n;
             ok = false;
         } else if (n > cap) {
             const int64_t d = c_row_dest(C, J, ctl, i, n);
-            if (d >= 0) merge_rows_smem<SR, K>(scols, Bv, av, boff, start, blen, alen, C.col + d, Cv + d, n);
+            if (d >= 0) merge_rows_smem<SR, K>(scols, svals, av, start, blen, alen, C.col + d, Cv + d, n);
             else ok = false;
         }
         if (ok) C.len[i] = n;
@@ -1268,7 +1272,7 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
     int k = 0;
     auto next = [&]() { return ss[(k++) % ns]; };
     {
-        const size_t smem_m = (size_t)MERGE_UB * TM_NT * sizeof(int32_t);
+        const size_t smem_m = (size_t)MERGE_UB * TM_NT * (sizeof(int32_t) + sizeof(T));
         static bool set_m = false;
         if (!set_m) {
             cudaFuncSetAttribute(k_num_thread_merge<SR, MERGE_K, MERGE_UB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
