@@ -163,13 +163,17 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
         const int32_t i = valid ? J.R[t] : 0;
         const int64_t aoff = valid ? A.off[i] : 0;
         const int alen = valid ? A.len[i] : 0;
-        if (valid && alen > SIZE_LONG) {  // a CTA sizes this row later
+        // dense accumulators: a row with more than SPLIT_A A entries is split,
+        // whatever its product count, so it needs no sum (its products are
+        // counted by the split kernel); its bound for the static layout is m
+        const bool direct = valid && J.dense_mode && alen > SPLIT_A && claim_split(J, ctl, t);
+        if (valid && !direct && alen > SIZE_LONG) {  // a CTA sizes this row later
             J.longr[atomic_add_ll2(&ctl->n_long, 1)] = (int32_t)t;
             valid = false;
         }
-        const bool lng = alen > SIZE_SHORT;
-        long long ub = 0, bmax = 0;
-        if (valid && !lng)
+        const bool lng = alen > SIZE_SHORT && !direct;
+        long long ub = direct ? J.m : 0, bmax = 0;
+        if (valid && !lng && !direct)
 #pragma unroll 8
             for (int a = 0; a < alen; a++) {
                 const long long l = B.len[A.col[aoff + a]];
@@ -217,12 +221,12 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
         const bool to_est = valid && wants_est(J, ub, ubc, t8);
         long long need = ubc;
         if (J.sizing == SIZE_COUNT && valid) need = C.len[i];
-        int b = (valid && ub > 0 && !to_est) ? pick_bin(ubc, alen, J, need, ub) : -1;
+        int b = (valid && ub > 0 && !to_est && !direct) ? pick_bin(ubc, alen, J, need, ub) : -1;
         if (b == BIN_CDENSE && (ub > SPLIT_MIN || alen > SPLIT_A) && claim_split(J, ctl, t)) b = -1;
         append_bins(J, ctl, b, t);
         if (to_est) push_est(J, ctl, t, alen, bmax, ub);
         if (J.sizing != SIZE_COUNT && valid) {
-            prod_acc += ub;
+            if (!direct) prod_acc += ub;
             a_acc += alen;
         }
     }
@@ -1143,6 +1147,7 @@ k_num_dsplit(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
         slot = lo;
     }
     int pending = 0;  // chunks accumulated in shared memory, not yet folded
+    long long prods = 0;  // products formed (the sizing pass does not sum split rows)
     for (long long w = w0; w < w1; w++) {
         while (J.sp_pre[slot + 1] <= w) slot++;
         const long long base = J.sp_pre[slot];
@@ -1155,23 +1160,26 @@ k_num_dsplit(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
         group_products<SR, 32>(A, B, i, 0xffffffffu, [&](int32_t j, T v) {
             atomicOr(&msk[j >> 5], 1u << (j & 31));
             Sr<SR>::acc(&acc[j], v);
+            prods++;
         }, a_lo + (tid >> 5) * 32, a_hi, 512);
         pending++;
         if (c + 1 < nch && w + 1 < w1) continue;  // the next item is this row's next chunk: keep accumulating
         __syncthreads();
         T *gacc = (T *)J.sp_acc + slot * mp;
         uint32_t *gmsk = J.sp_mask + slot * nw;
-        for (int j = tid; j < mp; j += 512)
-            if (msk[j >> 5] & (1u << (j & 31))) {
+        // fold: each present column into the global row, each mask word once;
+        // then one barrier, the mask reset and the row's chunk counter
+        for (int j = tid; j < mp; j += 512) {
+            const uint32_t word = msk[j >> 5];
+            if ((j & 31) == 0 && word) atomicOr(&gmsk[j >> 5], word);
+            if (word & (1u << (j & 31))) {
                 Sr<SR>::acc(&gacc[j], acc[j]);
                 acc[j] = Sr<SR>::zero();
             }
-        __syncthreads();
-        if (tid < nw && msk[tid]) atomicOr(&gmsk[tid], msk[tid]);
-        __syncthreads();
-        if (tid < 32) msk[tid] = 0u;
+        }
         __threadfence();
         __syncthreads();
+        if (tid < 32) msk[tid] = 0u;
         if (tid == 0) s_last = atomicAdd(&J.sp_done[slot], pending) == nch - pending;
         pending = 0;
         __syncthreads();
@@ -1214,6 +1222,8 @@ k_num_dsplit(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
         }
         __syncthreads();
     }
+    prods = warp_sum<long long>(prods);
+    if ((tid & 31) == 0 && prods && !J.count_only) atomic_add_ll2(&ctl->products, prods);
     if (tid == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
 }
 
