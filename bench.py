@@ -759,6 +759,8 @@ def learned_arm(args):
                                      conflicts=srv.conflicts)
     clk = clocks.stop()
     log(f"serving: {serving}")
+    srv_h.close()
+    serving_stencil = serving_on_stencil(args, log)
 
     cpu = None if args.no_cpu else learned_cpu_baseline(A, held, args.cpu_budget)
     lm = per_mode["learned"]
@@ -779,11 +781,56 @@ def learned_arm(args):
         "max_rel_diff_between_sizings": worst_rel,
         "estimator": est_info,
         "serving": serving,
+        "serving_stencil": serving_stencil,
         "clocks": clk,
         "setup_s": {"generate": round(gen_s, 1), "build_per_handle": round(build_s, 2)},
         "cpu_baseline": cpu,
     }
     print(json.dumps(out), flush=True)
+
+
+def serving_on_stencil(args, log):
+    """Continuous batching where footprints are small: the 128^3 stencil with
+    requests of 10..10^3 updates (log-uniform).  The same queued stream is
+    served with waves of one request (a plain queue) and with waves of up to
+    max_wave requests, then Poisson streams at 0.5x, 1x and 2x the batched
+    service rate."""
+    import paper_2202_08808_gb300 as pkg
+    from paper_2202_08808_gb300.serving import Request, Server, latency_summary
+    from workloads import stencil7, stencil_batch
+    A = stencil7(GRID, GRID, GRID, seed=1)
+    g = pkg.DynamicSpGEMM(A)
+    rng = np.random.default_rng(504)
+
+    def requests(count, rate, seed0):
+        out, t = [], 0.0
+        for k in range(count):
+            if rate is not None:
+                t += float(rng.exponential(1.0 / rate))
+            out.append(Request(k, t, stencil_batch(GRID, GRID, GRID, int(10 ** rng.uniform(1, 3)), seed=seed0 + k)))
+        return out
+
+    res = {}
+    for name, mw in (("queue", 1), ("waves", args.max_wave)):
+        Server(g, max_wave=mw, read_results=True).serve(requests(20, None, 600000 + mw))  # warm graphs
+        srv = Server(g, max_wave=mw, read_results=True)
+        reqs = requests(args.requests, None, 700000 + 1000 * mw)
+        t0 = time.perf_counter()
+        out = srv.serve(reqs)
+        wall = time.perf_counter() - t0
+        res[f"saturated_{name}"] = dict(latency_summary(out, wall), waves=srv.waves, conflicts=srv.conflicts)
+    mu = res["saturated_waves"]["throughput_req_s"]
+    for f in (0.5, 1.0, 2.0):
+        srv = Server(g, max_wave=args.max_wave, read_results=True)
+        reqs = requests(args.requests, f * mu, 800000 + int(10 * f))
+        t0 = time.perf_counter()
+        out = srv.serve(reqs)
+        wall = time.perf_counter() - t0
+        res[f"rate_{f}x"] = dict(latency_summary(out, wall), offered_req_s=round(f * mu, 2), waves=srv.waves,
+                                 conflicts=srv.conflicts)
+    g.close()
+    log(f"serving on the stencil: {res}")
+    return res
 
 
 def learned_cpu_baseline(A, held, budget_s):
@@ -813,7 +860,7 @@ def learned_cpu_baseline(A, held, budget_s):
 
 # ------------------------------------------------------------ CPU oracle
 
-def cpu_baseline(args, W, budget_s=20.0, steps=None):
+def cpu_baseline(args, W, budget_s=20.0, steps=None, warmup=0):
     """The oracle's row-dynamic route (apply, affected rows, recompute of R)
     on a bounded sample of the same workload: consecutive batches until the
     time budget is used; single-threaded C."""
@@ -823,6 +870,8 @@ def cpu_baseline(args, W, budget_s=20.0, steps=None):
     Ao = OMat.from_csr(A)
     Bo = OMat.from_csr(B) if B is not None else None
     Co = Ao.multiply(Bo if Bo is not None else Ao)
+    for w in range(warmup):  # untimed
+        oracle.row_dynamic(Ao, Co, W.batches(1, 60000 + w)[0], Bo)
     times = []
     k = 0
     while True:
@@ -847,7 +896,7 @@ def reference_arm(args):
     if rank != 0:
         return
     W = WORKLOADS[args.workload if args.workload in WORKLOADS else "stencil"]()
-    res = cpu_baseline(args, W, steps=args.steps)
+    res = cpu_baseline(args, W, steps=args.steps, warmup=args.warmup)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": res["value"], "unit": res["unit"], "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["latency_ms"], "higher_is_better": True,

@@ -333,13 +333,16 @@ dspg_status dspg_set_sizing(dspg_handle *h, int mode, const dspg_estimator *e, i
  * disjoint can share a call.  (With B distinct from A the footprint is the
  * batch's rows; batches of B are not covered.) */
 
-/* OR the footprint of dA into bitmap (device, ceil(nrows/32) words, bit i
- * of word i/32 for row i).  DSPG_ERR_INVALID for an entry out of range. */
-dspg_status dspg_footprint(dspg_handle *h, const dspg_updates *dA, uint32_t *bitmap, void *stream);
-
-/* If the bitmaps f and u (device, `words` words each) share no bit, OR f
- * into u and set *admitted = 1; otherwise leave u and set *admitted = 0. */
-dspg_status dspg_bitmap_admit(const uint32_t *f, uint32_t *u, int64_t words, int *admitted, void *stream);
+/* Write the footprint of dA into f (device, ceil(nrows/32) words, bit i of
+ * word i/32 for row i; f is cleared first) and its number of rows into *rows
+ * (may be NULL).  When u != NULL (device, same size, the rows a wave already
+ * holds): if f and u share no bit, u |= f and *admitted = 1; otherwise
+ * *admitted = 0, and u |= f only when or_anyway != 0 (a server marks a
+ * request it passes over, so that no later request that conflicts with it
+ * overtakes it).  Working memory is the handle's (kept between calls); one
+ * synchronisation.  DSPG_ERR_INVALID for an entry out of range. */
+dspg_status dspg_footprint(dspg_handle *h, const dspg_updates *dA, uint32_t *f, uint32_t *u, int or_anyway,
+                           int *admitted, int64_t *rows, void *stream);
 
 /* Free the group (not its handles). */
 void dspg_group_destroy(dspg_group *g);

@@ -197,6 +197,31 @@ struct CWs {
     DBuf<int64_t> sp_pre;
 };
 
+// Working memory of dspg_footprint (kept, so a serving loop allocates nothing).
+struct FpWs {
+    DBuf<int32_t> row, col;
+    DBuf<unsigned long long> cnt;
+    struct Pinned {
+        unsigned long long *p = nullptr;
+        int64_t n = 0;
+        void reserve_host(int64_t need) {
+            if (need <= n) return;
+            if (p) cudaFreeHost(p);
+            p = nullptr;
+            n = 0;
+            if (cudaMallocHost((void **)&p, sizeof(unsigned long long) * need) != cudaSuccess) {
+                cudaGetLastError();
+                p = nullptr;
+                throw Err(DSPG_ERR_OOM, "pinned host allocation failed");
+            }
+            n = need;
+        }
+        ~Pinned() {
+            if (p) cudaFreeHost(p);
+        }
+    } hcnt;
+};
+
 struct BatchIn {
     const int32_t *row = nullptr, *col = nullptr;
     const void *val = nullptr;
@@ -250,6 +275,7 @@ struct dspg_handle {
     int est_min = 128;
     float est_margin = 0.25f;
     DBuf<uint16_t> est_w;                       // estimator weights (bfloat16 bits)
+    FpWs fp;                                    // footprints (serving)
     int64_t compactions = 0;
     std::string err;
 
@@ -1478,60 +1504,43 @@ dspg_status dspg_row_features(dspg_handle *h, const int32_t *rows, int64_t n, fl
     }
 }
 
-dspg_status dspg_footprint(dspg_handle *h, const dspg_updates *dA, uint32_t *bitmap, void *stream) {
+dspg_status dspg_footprint(dspg_handle *h, const dspg_updates *dA, uint32_t *f, uint32_t *u, int or_anyway,
+                           int *admitted, int64_t *rows, void *stream) {
     if (!h) return DSPG_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     try {
-        if (!dA || !bitmap) throw Err(DSPG_ERR_INVALID, "dA and bitmap must not be NULL");
+        if (!dA || !f) throw Err(DSPG_ERR_INVALID, "dA and f must not be NULL");
+        if (u && !admitted) throw Err(DSPG_ERR_INVALID, "admitted must not be NULL when u is given");
         const int64_t n = dA->n;
         if (n < 0 || (n > 0 && (!dA->row || !dA->col))) throw Err(DSPG_ERR_INVALID, "bad batch");
-        if (n == 0) return DSPG_OK;
-        DBuf<int32_t> r, c;
+        const int64_t words = (h->A.nrows + 31) / 32;
+        FpWs &w = h->fp;
+        w.cnt.reserve(4);  // out-of-range flag, overlapping words, rows of f
+        w.hcnt.reserve_host(4);
+        CK(cudaMemsetAsync(f, 0, sizeof(uint32_t) * words, s));
+        CK(cudaMemsetAsync(w.cnt.p, 0, 4 * sizeof(unsigned long long), s));
         const int32_t *rp = dA->row, *cp = dA->col;
-        if (!dA->on_device) {
-            r.reserve(n);
-            c.reserve(n);
-            CK(cudaMemcpyAsync(r.p, dA->row, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(c.p, dA->col, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-            rp = r.p;
-            cp = c.p;
+        if (n > 0 && !dA->on_device) {
+            w.row.reserve(n);
+            w.col.reserve(n);
+            CK(cudaMemcpyAsync(w.row.p, dA->row, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(w.col.p, dA->col, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+            rp = w.row.p;
+            cp = w.col.p;
         }
-        DBuf<unsigned> bad;
-        bad.reserve(1);
-        CK(cudaMemsetAsync(bad.p, 0, sizeof(unsigned), s));
-        run_footprint(rp, cp, n, h->A.nrows, h->A.ncols, h->b_is_a, h->AT.view(), bitmap, bad.p, s, h->num_sms);
-        unsigned hb = 0;
-        CK(cudaMemcpyAsync(&hb, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        if (n > 0)
+            run_footprint(rp, cp, n, h->A.nrows, h->A.ncols, h->b_is_a, h->AT.view(), f, (unsigned *)w.cnt.p, s,
+                          h->num_sms);
+        run_bitmap_overlap(f, u, words, w.cnt.p + 1, s, h->num_sms);
+        if (u) run_bitmap_or(f, u, words, w.cnt.p + 1, or_anyway, s, h->num_sms);
+        CK(cudaMemcpyAsync(w.hcnt.p, w.cnt.p, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (hb) throw Err(DSPG_ERR_INVALID, "batch entry out of range");
+        if ((unsigned)w.hcnt.p[0]) throw Err(DSPG_ERR_INVALID, "batch entry out of range");
+        if (u) *admitted = w.hcnt.p[1] == 0 ? 1 : 0;
+        if (rows) *rows = (int64_t)w.hcnt.p[2];
         return DSPG_OK;
     } catch (const Err &x) {
         return fail(h, x);
-    }
-}
-
-dspg_status dspg_bitmap_admit(const uint32_t *f, uint32_t *u, int64_t words, int *admitted, void *stream) {
-    cudaStream_t s = (cudaStream_t)stream;
-    try {
-        if (!f || !u || !admitted || words < 0) throw Err(DSPG_ERR_INVALID, "bad bitmap arguments");
-        int dev = 0, sms = 1;
-        CK(cudaGetDevice(&dev));
-        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        DBuf<unsigned long long> hits;
-        hits.reserve(1);
-        CK(cudaMemsetAsync(hits.p, 0, sizeof(unsigned long long), s));
-        run_bitmap_overlap(f, u, words, hits.p, s, sms);
-        unsigned long long hh = 0;
-        CK(cudaMemcpyAsync(&hh, hits.p, sizeof(hh), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        *admitted = hh == 0 ? 1 : 0;
-        if (hh == 0) {
-            run_bitmap_or(f, u, words, s, sms);
-            CK(cudaStreamSynchronize(s));
-        }
-        return DSPG_OK;
-    } catch (const Err &x) {
-        return fail(nullptr, x);
     }
 }
 

@@ -119,9 +119,10 @@ void run_transpose_feed(const UpdJob &J, int32_t pad_row, int32_t *trow, int32_t
                         unsigned mask, cudaStream_t s);
 void run_footprint(const int32_t *row, const int32_t *col, int64_t n, int64_t nrows, int64_t ncols, bool b_is_a,
                    const MatView &AT, uint32_t *bm, unsigned *bad, cudaStream_t s, int num_sms);
-void run_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t words, unsigned long long *hits, cudaStream_t s,
+void run_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t words, unsigned long long *cnt, cudaStream_t s,
                         int num_sms);
-void run_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words, cudaStream_t s, int num_sms);
+void run_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words, const unsigned long long *cnt, int or_anyway,
+                   cudaStream_t s, int num_sms);
 
 // spgemm.cu
 constexpr int64_t DENSE_M_MAX = 1024;  // C columns up to this use dense accumulators

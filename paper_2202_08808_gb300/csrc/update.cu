@@ -477,16 +477,27 @@ __global__ void k_footprint(const int32_t *row, const int32_t *col, int64_t n, i
     }
 }
 
-// hits = number of words where f and u share a bit.
-__global__ void k_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t words, unsigned long long *hits) {
-    unsigned long long c = 0;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < words; x += (int64_t)gridDim.x * blockDim.x)
-        c += (f[x] & u[x]) != 0u;
+// cnt[0] = number of words where f and u share a bit (u may be null),
+// cnt[1] = number of bits set in f.
+__global__ void k_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t words, unsigned long long *cnt) {
+    unsigned long long c = 0, b = 0;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < words; x += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = f[x];
+        b += __popc(w);
+        if (u) c += (w & u[x]) != 0u;
+    }
     c = warp_sum<unsigned long long>(c);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(hits, c);
+    b = warp_sum<unsigned long long>(b);
+    if ((threadIdx.x & 31) == 0) {
+        if (c) atomicAdd(&cnt[0], c);
+        if (b) atomicAdd(&cnt[1], b);
+    }
 }
 
-__global__ void k_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words) {
+// u |= f when nothing overlapped (cnt[0] == 0) or always (or_anyway).
+__global__ void k_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words, const unsigned long long *cnt,
+                            int or_anyway) {
+    if (!or_anyway && *(volatile const unsigned long long *)cnt != 0ull) return;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < words; x += (int64_t)gridDim.x * blockDim.x)
         u[x] |= f[x];
 }
@@ -499,19 +510,20 @@ void run_footprint(const int32_t *row, const int32_t *col, int64_t n, int64_t nr
     launch_k(k_footprint, (unsigned)g, 256, 0, s, row, col, n, nrows, ncols, b_is_a ? 1 : 0, AT, bm, bad);
 }
 
-void run_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t words, unsigned long long *hits, cudaStream_t s,
+void run_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t words, unsigned long long *cnt, cudaStream_t s,
                         int num_sms) {
     int64_t g = (words + 255) / 256;
     if (g > num_sms * 8) g = num_sms * 8;
     if (g < 1) g = 1;
-    launch_k(k_bitmap_overlap, (unsigned)g, 256, 0, s, f, u, words, hits);
+    launch_k(k_bitmap_overlap, (unsigned)g, 256, 0, s, f, u, words, cnt);
 }
 
-void run_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words, cudaStream_t s, int num_sms) {
+void run_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words, const unsigned long long *cnt, int or_anyway,
+                   cudaStream_t s, int num_sms) {
     int64_t g = (words + 255) / 256;
     if (g > num_sms * 8) g = num_sms * 8;
     if (g < 1) g = 1;
-    launch_k(k_bitmap_or, (unsigned)g, 256, 0, s, f, u, words);
+    launch_k(k_bitmap_or, (unsigned)g, 256, 0, s, f, u, words, cnt, or_anyway);
 }
 
 }  // namespace dspg

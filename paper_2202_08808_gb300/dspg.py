@@ -139,9 +139,7 @@ def load():
         lib.dspg_set_sizing.restype = i32
         lib.dspg_set_sizing.argtypes = [p, i32, p, i32, C.c_float]
         lib.dspg_footprint.restype = i32
-        lib.dspg_footprint.argtypes = [p, C.POINTER(_Upd), p, p]
-        lib.dspg_bitmap_admit.restype = i32
-        lib.dspg_bitmap_admit.argtypes = [p, p, i64, C.POINTER(i32), p]
+        lib.dspg_footprint.argtypes = [p, C.POINTER(_Upd), p, p, i32, C.POINTER(i32), C.POINTER(i64), p]
         lib.dspg_destroy.restype = None
         lib.dspg_destroy.argtypes = [p]
         lib.dspg_last_error.restype = C.c_char_p
@@ -156,7 +154,7 @@ EXPORTED = ["dspg_build", "dspg_apply_batch", "dspg_read_C", "dspg_read_A", "dsp
             "dspg_tuning_candidate", "dspg_autotune", "dspg_group_create", "dspg_group_apply", "dspg_group_destroy",
             "dspg_group_last_error", "dspg_estimator_create", "dspg_estimator_params", "dspg_estimator_grad",
             "dspg_estimator_train", "dspg_estimator_predict", "dspg_estimator_last_error", "dspg_estimator_destroy",
-            "dspg_row_features", "dspg_set_sizing", "dspg_footprint", "dspg_bitmap_admit", "dspg_destroy",
+            "dspg_row_features", "dspg_set_sizing", "dspg_footprint", "dspg_destroy",
             "dspg_last_error"]
 
 TUNING_FIELDS = [n for n, _ in _Tuning._fields_]
@@ -390,11 +388,18 @@ class DynamicSpGEMM:
         self._check(self._lib.dspg_row_features(self._h, rp, n, X.data_ptr(), y.data_ptr(), _stream(stream)))
         return X[:n], y[:n]
 
-    def footprint(self, batch, bitmap, stream=None) -> None:
-        """OR the footprint of an A batch into `bitmap` (torch uint32/int32 on the device)."""
+    def footprint(self, batch, f, u=None, or_anyway: bool = False, stream=None):
+        """Write the footprint of an A batch into the device bitmap f (torch
+        int32, ceil(n/32) words).  Returns (rows in f, admitted): with a wave
+        bitmap u, admitted tells whether f was disjoint from u (and u |= f
+        then, or always with or_anyway); without u, admitted is None."""
         keep: list = []
-        u = self._upd(batch, keep)
-        self._check(self._lib.dspg_footprint(self._h, C.byref(u), bitmap.data_ptr(), _stream(stream)))
+        ub = self._upd(batch, keep)
+        adm = C.c_int()
+        rows = C.c_int64()
+        self._check(self._lib.dspg_footprint(self._h, C.byref(ub), f.data_ptr(), u.data_ptr() if u is not None else None,
+                                             int(or_anyway), C.byref(adm), C.byref(rows), _stream(stream)))
+        return int(rows.value), (bool(adm.value) if u is not None else None)
 
     def recompute_all(self, stream=None) -> None:
         self._check(self._lib.dspg_recompute_all(self._h, _stream(stream)))
@@ -512,16 +517,6 @@ class Group:
             self.close()
         except Exception:
             pass
-
-
-def bitmap_admit(f, u, stream=None) -> bool:
-    """If device bitmaps f and u share no bit, u |= f and True; else False."""
-    lib = load()
-    adm = C.c_int()
-    st = lib.dspg_bitmap_admit(f.data_ptr(), u.data_ptr(), int(f.numel()), C.byref(adm), _stream(stream))
-    if st != 0:
-        raise DspgError(st, lib.dspg_last_error(None).decode())
-    return bool(adm.value)
 
 
 def multiply_rows_noalloc(A, B, rows, semiring: int | None = None, stream=None):

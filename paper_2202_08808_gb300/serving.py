@@ -9,8 +9,11 @@ exactly as if they ran one by one):
 
 - a request joins only if its footprint (``dspg_footprint``: the rows of C
   it can touch, and the rows its entries could connect) shares no row with
-  the footprints already in the wave; the first one that conflicts ends the
-  wave, so no request ever overtakes an earlier one;
+  the footprints already in the wave; by default the first request that
+  conflicts ends the wave.  With ``overtake`` a conflicting request is passed
+  over instead and its footprint still counts, so a later request joins only
+  if it meets none of the footprints examined before it: it overtakes only
+  requests it commutes with, and conflicting requests stay in arrival order;
 - at most ``max_wave`` requests and ``max_wave_entries`` update entries per
   wave (the slots);
 - and only while the wave's estimated device memory (its batch and working
@@ -20,8 +23,8 @@ exactly as if they ran one by one):
 Requests that arrive while a wave runs on the GPU wait for the next turn.
 The result of a request is its affected rows of C (the rows of the wave's
 affected set inside its footprint) right after its wave commits, which, by
-the disjointness, is the result it would have had alone: see
-``tests/test_gpu_serving.py``.  All computation is in the library's
+the disjointness, is the result it would have had alone in arrival order:
+see ``tests/test_gpu_serving.py``.  All computation is in the library's
 kernels; this module only schedules and moves data.
 """
 
@@ -81,10 +84,12 @@ class Server:
     updates of A; C = A A in the intended use)."""
 
     def __init__(self, g, max_wave: int = 32, max_wave_entries: int = 1 << 21, hbm_reserve: int = 4 << 30,
-                 read_results: bool = True, hbm_free=None):
+                 read_results: bool = True, hbm_free=None, overtake: bool = False, scan: int | None = None):
         import torch
         self.g = g
         self.max_wave = max_wave
+        self.overtake = overtake  # pass over a conflicting request instead of ending the wave
+        self.scan = scan if scan is not None else 4 * max_wave  # queued requests examined per wave
         self.max_wave_entries = max_wave_entries
         self.hbm_reserve = hbm_reserve
         self.read_results = read_results
@@ -95,9 +100,27 @@ class Server:
         self.words = (self.n + 31) // 32
         self._union = torch.zeros(self.words, dtype=torch.int32, device="cuda")
         self._fp = [torch.zeros(self.words, dtype=torch.int32, device="cuda") for _ in range(max_wave)]
+        self._pin = None
         self.waves = 0
         self.conflicts = 0
         self.memory_stops = 0
+
+    def _stage(self, b: UpdateBatch) -> UpdateBatch:
+        """The wave's batch in pinned host memory (buffers kept and grown), so
+        its upload is a plain asynchronous copy."""
+        import torch
+        n = len(b)
+        if self._pin is None or self._pin[0].shape[0] < n:
+            cap = max(n, 1024) * 2
+            self._pin = (torch.empty(cap, dtype=torch.int32).pin_memory(), torch.empty(cap, dtype=torch.int32).pin_memory(),
+                         torch.empty(cap, dtype=torch.from_numpy(b.val[:0]).dtype).pin_memory(),
+                         torch.empty(cap, dtype=torch.uint8).pin_memory())
+        r, c, v, o = self._pin
+        r[:n].numpy()[:] = b.row
+        c[:n].numpy()[:] = b.col
+        v[:n].numpy()[:] = b.val
+        o[:n].numpy()[:] = b.op
+        return UpdateBatch(r[:n], c[:n], v[:n], o[:n])
 
     def _wave_bytes(self, entries: int, fp_rows: int) -> float:
         # device copy of the batch + sort/merge buffers (~64 B per entry) and
@@ -106,8 +129,6 @@ class Server:
 
     def serve(self, requests: list[Request], clock=time.perf_counter) -> list[Result]:
         import torch
-
-        from .dspg import bitmap_admit
 
         order = sorted(requests, key=lambda r: (r.arrival, r.rid))
         results: list[Result] = []
@@ -122,37 +143,53 @@ class Server:
             if not queue:
                 time.sleep(max(0.0, min(order[nxt].arrival - now, 0.01)))
                 continue
-            # admit a wave
+            # admit a wave: scan the queue in arrival order; a request joins if
+            # its footprint is disjoint from everything scanned before it (the
+            # wave, and with overtake the requests passed over), so a request
+            # only ever overtakes earlier ones it commutes with
             self._union.zero_()
             wave, fps, fp_rows, entries = [], [], 0, 0
             budget = self._free() - self.hbm_reserve
-            for req in queue:
-                if len(wave) >= self.max_wave or (wave and entries + len(req.batch) > self.max_wave_entries):
+            taken = []  # queue positions admitted
+            for qi, req in enumerate(queue[: self.scan]):
+                if len(wave) >= self.max_wave:
+                    break
+                if self.max_wave == 1:  # a plain queue: one request per wave, no footprint needed
+                    wave.append(req)
+                    fps.append(None)
+                    taken.append(qi)
                     break
                 f = self._fp[len(wave)]
-                f.zero_()
-                self.g.footprint(req.batch, f)
-                fbits = f.cpu().numpy().view(np.uint32)
-                rows_f = _popcount(fbits)
-                if wave and self._wave_bytes(entries + len(req.batch), fp_rows + rows_f) > budget:
+                # the footprint and the admission test against the wave's rows
+                # in one call (a wave that closes below drops its bitmap anyway)
+                rows_f, disjoint = self.g.footprint(req.batch, f, self._union, or_anyway=self.overtake)
+                fits = not wave or (entries + len(req.batch) <= self.max_wave_entries and
+                                    self._wave_bytes(entries + len(req.batch), fp_rows + rows_f) <= budget)
+                if not fits:
                     self.memory_stops += 1
                     break
-                if not bitmap_admit(f, self._union):
+                if not disjoint:
                     self.conflicts += 1
+                    if self.overtake:
+                        continue
                     break
                 wave.append(req)
-                fps.append(fbits)
+                fps.append(f)
+                taken.append(qi)
                 fp_rows += rows_f
                 entries += len(req.batch)
-            queue = queue[len(wave):]
+            keep = set(taken)
+            queue = [r for qi, r in enumerate(queue) if qi not in keep]
             start = clock() - t0
-            cat = concat([r.batch for r in wave])
-            pinned = UpdateBatch(torch.from_numpy(cat.row).pin_memory(), torch.from_numpy(cat.col).pin_memory(),
-                                 torch.from_numpy(cat.val).pin_memory(), torch.from_numpy(cat.op).pin_memory())
-            self.g.apply_batch(pinned)
+            self.g.apply_batch(self._stage(concat([r.batch for r in wave])))
             R = self.g.last_affected()
+            if len(wave) > 1:  # each request's rows: the wave's affected rows inside its footprint
+                fps = [f.cpu().numpy().view(np.uint32) for f in fps]
             for req, fbits in zip(wave, fps):
-                rows = R[((fbits[R >> 5] >> (R & 31).astype(np.uint32)) & 1) != 0] if R.shape[0] else R
+                if fbits is None or len(wave) == 1:
+                    rows = R
+                else:
+                    rows = R[((fbits[R >> 5] >> (R & 31).astype(np.uint32)) & 1) != 0] if R.shape[0] else R
                 res = Result(req.rid, req.arrival, start, 0.0, self.waves, len(wave), rows)
                 if self.read_results:
                     res.rowptr, res.col, res.val = self.g.read_rows_C(rows)
@@ -160,12 +197,6 @@ class Server:
                 results.append(res)
             self.waves += 1
         return results
-
-
-def _popcount(words: np.ndarray) -> int:
-    if hasattr(np, "bitwise_count"):
-        return int(np.bitwise_count(words).sum())
-    return int(np.unpackbits(words.view(np.uint8)).sum())
 
 
 def latency_summary(results: list[Result], wall: float | None = None) -> dict:

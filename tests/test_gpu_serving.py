@@ -82,3 +82,55 @@ def test_footprint_rejects_out_of_range_entries(dspg):
     bad = Batch(np.array([3, A.nrows], np.int32), np.array([1, 2], np.int32), np.zeros(2), np.zeros(2, np.uint8))
     with pytest.raises(dspg.DspgError):
         g.footprint(bad, f)
+
+
+def test_overtaking_keeps_every_result(dspg):
+    """With overtake on, a request may run before earlier ones it does not
+    conflict with; every result must still be the one it has alone in
+    arrival order."""
+    from paper_2202_08808_gb300.serving import Server
+    A = er_matrix(4096, 4, seed=181, kind=MIN_PLUS_I32)
+    reqs = _requests(A, 60, 182)
+    srv = Server(dspg.DynamicSpGEMM(A), max_wave=8, overtake=True)
+    results = srv.serve(reqs)
+    assert len(results) == len(reqs) and srv.conflicts > 0
+    order = [r.rid for r in sorted(results, key=lambda r: (r.wave, r.rid))]
+    assert order != sorted(order), "no request overtook an earlier one"
+    _alone_and_oracle(dspg, A, reqs, results)
+
+
+def test_footprint_is_the_rows_a_batch_can_reach(dspg):
+    """For C = A A the footprint of a batch is its rows, its columns and every
+    row i with A(i,k) != 0 for a row k of the batch (on A's current pattern):
+    compared bit for bit with a brute-force set; the admission test against a
+    wave bitmap agrees with set intersection."""
+    import torch
+    A = er_matrix(2048, 5, seed=191, kind=PLUS_TIMES_F64)
+    g = dspg.DynamicSpGEMM(A)
+    words = (A.nrows + 31) // 32
+    rows_of = A.row_ids()
+    cols = A.col.astype(np.int64)
+
+    def brute(b):
+        s = set(b.row.tolist()) | set(b.col.tolist())
+        for k in set(b.row.tolist()):
+            s |= set(rows_of[cols == k].tolist())
+        return s
+
+    def bits(f):
+        w = f.cpu().numpy().view(np.uint32)
+        return set(np.nonzero(np.unpackbits(w.view(np.uint8), bitorder="little"))[0].tolist())
+
+    b1 = random_batch(A.nrows, A.ncols, 7, seed=192, kind=PLUS_TIMES_F64, A=A, dup_frac=0.0)
+    b2 = random_batch(A.nrows, A.ncols, 7, seed=193, kind=PLUS_TIMES_F64, A=A, dup_frac=0.0)
+    f1 = torch.zeros(words, dtype=torch.int32, device="cuda")
+    f2 = torch.zeros(words, dtype=torch.int32, device="cuda")
+    u = torch.zeros(words, dtype=torch.int32, device="cuda")
+    n1, adm1 = g.footprint(b1, f1, u)
+    assert bits(f1) == brute(b1) and n1 == len(brute(b1)) and adm1
+    assert bits(u) == brute(b1)
+    n2, adm2 = g.footprint(b2, f2, u)
+    assert bits(f2) == brute(b2)
+    assert adm2 == (not (brute(b1) & brute(b2)))
+    n3, adm3 = g.footprint(b1, f1)  # no wave bitmap: no admission
+    assert adm3 is None and n3 == n1
