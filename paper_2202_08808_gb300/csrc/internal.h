@@ -67,7 +67,7 @@ struct DetectBufs {
 // The recompute of rows of C (static build: all rows).
 struct CJob {
     const int32_t *R;         // rows to recompute
-    int32_t *bins;            // NBINS lists of R indices, bin_cap each
+    int32_t *bins;            // NBINS lists of rows of C, bin_cap each
     int64_t bin_cap;
     void *gd_acc;             // per-CTA dense accumulators (global), gd_w entries each
     uint32_t *gd_mask;        // per-CTA presence bits, gd_w / 32 words each
@@ -91,9 +91,9 @@ struct CJob {
     int est_min;
     float est_margin;
     const uint16_t *est_w;    // estimator weights, bfloat16 bits (EST_PARAMS)
-    int4 *est;                // rows waiting for an estimate: {t, len(A_i), max len(B_k), bound}
+    int4 *est;                // rows waiting for an estimate: {i, len(A_i), max len(B_k), bound}
     int32_t *ovf;             // rows (of C) whose learned table overflowed
-    int32_t *longr;           // rows of R (indices t) whose A row is long (sized by a CTA each)
+    int32_t *longr;           // indices t into R of rows whose A row is long (sized by a CTA each)
     // split rows (dense mode): rows with many A entries or products are cut
     // into chunks recomputed by different CTAs and combined in global
     // accumulators (sp_rows rows at a time)

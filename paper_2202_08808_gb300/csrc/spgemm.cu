@@ -109,16 +109,16 @@ __device__ __forceinline__ int pick_bin(long long ubc, int alen, const CJob &J, 
     return pick_table_bin(table_need, J);
 }
 
-// Append the calling lanes' rows t to their bins b (b < 0: none), one atomic
-// per distinct bin in the warp.
-__device__ __forceinline__ void append_bins(const CJob &J, Ctl *ctl, int b, long long t) {
+// Append the calling lanes' rows i (of C) to their bins b (b < 0: none), one
+// atomic per distinct bin in the warp.
+__device__ __forceinline__ void append_bins(const CJob &J, Ctl *ctl, int b, int32_t i) {
     const int lane = threadIdx.x & 31;
     const unsigned peers = __match_any_sync(0xffffffffu, b);
     const int leader = __ffs(peers) - 1;
     long long bb = 0;
     if (b >= 0 && lane == leader) bb = atomic_add_ll2(&ctl->bin_count[b], __popc(peers));
     bb = __shfl_sync(0xffffffffu, bb, leader);
-    if (b >= 0) J.bins[(int64_t)b * J.bin_cap + bb + __popc(peers & lanemask_lt())] = (int32_t)t;
+    if (b >= 0) J.bins[(int64_t)b * J.bin_cap + bb + __popc(peers & lanemask_lt())] = i;
 }
 
 constexpr int SIZE_SHORT = 64;   // A rows up to this length are sized by one thread,
@@ -129,10 +129,10 @@ constexpr int SPLIT_CHUNK = 2048;      // A entries per work item of a split row
 
 // Dense mode: claim a split slot for a row with very many products; false
 // when all slots are taken (the row then goes to the CTA dense bin).
-__device__ __forceinline__ bool claim_split(const CJob &J, Ctl *ctl, long long t) {
+__device__ __forceinline__ bool claim_split(const CJob &J, Ctl *ctl, int32_t i) {
     const long long slot = atomic_add_ll2(&ctl->bin_count[BIN_DSPLIT], 1);
     if (slot >= J.sp_rows) return false;
-    J.bins[(int64_t)BIN_DSPLIT * J.bin_cap + slot] = (int32_t)t;
+    J.bins[(int64_t)BIN_DSPLIT * J.bin_cap + slot] = i;
     return true;
 }
 
@@ -140,8 +140,8 @@ __device__ __forceinline__ bool wants_est(const CJob &J, long long ub, long long
     return ub > 0 && J.sizing == SIZE_LEARNED && !t8 && !J.dense_mode && ubc > J.est_min;
 }
 
-__device__ __forceinline__ void push_est(const CJob &J, Ctl *ctl, long long t, int alen, long long bmax, long long ub) {
-    const int4 e = make_int4((int)t, alen, (int)bmax, (int)(ub < 0x7fffffffLL ? ub : 0x7fffffffLL));
+__device__ __forceinline__ void push_est(const CJob &J, Ctl *ctl, int32_t i, int alen, long long bmax, long long ub) {
+    const int4 e = make_int4(i, alen, (int)bmax, (int)(ub < 0x7fffffffLL ? ub : 0x7fffffffLL));
     J.est[atomic_add_ll2(&ctl->n_est, 1)] = e;
 }
 
@@ -166,7 +166,7 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
         // dense accumulators: a row with more than SPLIT_A A entries is split,
         // whatever its product count, so it needs no sum (its products are
         // counted by the split kernel); its bound for the static layout is m
-        const bool direct = valid && J.dense_mode && alen > SPLIT_A && claim_split(J, ctl, t);
+        const bool direct = valid && J.dense_mode && alen > SPLIT_A && claim_split(J, ctl, i);
         if (valid && !direct && alen > SIZE_LONG) {  // a CTA sizes this row later
             J.longr[atomic_add_ll2(&ctl->n_long, 1)] = (int32_t)t;
             valid = false;
@@ -222,9 +222,9 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
         long long need = ubc;
         if (J.sizing == SIZE_COUNT && valid) need = C.len[i];
         int b = (valid && ub > 0 && !to_est && !direct) ? pick_bin(ubc, alen, J, need, ub) : -1;
-        if (b == BIN_CDENSE && (ub > SPLIT_MIN || alen > SPLIT_A) && claim_split(J, ctl, t)) b = -1;
-        append_bins(J, ctl, b, t);
-        if (to_est) push_est(J, ctl, t, alen, bmax, ub);
+        if (b == BIN_CDENSE && (ub > SPLIT_MIN || alen > SPLIT_A) && claim_split(J, ctl, i)) b = -1;
+        append_bins(J, ctl, b, i);
+        if (to_est) push_est(J, ctl, i, alen, bmax, ub);
         if (J.sizing != SIZE_COUNT && valid) {
             if (!direct) prod_acc += ub;
             a_acc += alen;
@@ -295,12 +295,12 @@ __global__ void __launch_bounds__(256) k_size_long(MatView A, MatView B, MatView
             }
             const bool t8 = alen <= J.tm_k && ubc <= J.tm_ub;
             if (wants_est(J, ub, ubc, t8)) {
-                push_est(J, ctl, t, alen, bmax, ub);
+                push_est(J, ctl, i, alen, bmax, ub);
             } else if (ub > 0) {
                 const long long need = J.sizing == SIZE_COUNT ? (long long)C.len[i] : ubc;
                 const int b = pick_bin(ubc, alen, J, need, ub);
-                if (!(b == BIN_CDENSE && (ub > SPLIT_MIN || alen > SPLIT_A) && claim_split(J, ctl, t)))
-                    J.bins[(int64_t)b * J.bin_cap + atomic_add_ll2(&ctl->bin_count[b], 1)] = (int32_t)t;
+                if (!(b == BIN_CDENSE && (ub > SPLIT_MIN || alen > SPLIT_A) && claim_split(J, ctl, i)))
+                    J.bins[(int64_t)b * J.bin_cap + atomic_add_ll2(&ctl->bin_count[b], 1)] = i;
             }
             if (J.sizing != SIZE_COUNT) {
                 atomic_add_ll2(&ctl->products, ub);
@@ -323,10 +323,10 @@ __global__ void __launch_bounds__(128) k_est_bins(CJob J, Ctl *ctl, unsigned mas
     for (long long base = (long long)blockIdx.x * blockDim.x; base < cnt; base += (long long)gridDim.x * blockDim.x) {
         const long long q = base + threadIdx.x;
         int b = -1;
-        long long t = 0;
+        int32_t i = 0;
         if (q < cnt) {
             const int4 e = J.est[q];
-            t = e.x;
+            i = e.x;
             float x[EST_IN];
             est_features(x, e.y, e.w, e.z);
             const float o = est_forward(W, x);
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(128) k_est_bins(CJob J, Ctl *ctl, unsigned mas
             if (need < 1) need = 1;
             b = pick_table_bin(need, J);
         }
-        append_bins(J, ctl, b, t);
+        append_bins(J, ctl, b, i);
     }
 }
 
@@ -618,10 +618,11 @@ k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned m
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = (long long)blockIdx.x * TM_NT + threadIdx.x; it < cnt; it += (long long)gridDim.x * TM_NT) {
-        const int t = J.bins[(int64_t)bin * J.bin_cap + it];
-        const int32_t i = J.R[t];
+        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
         const int64_t aoff = A.off[i];
         const int alen = A.len[i];
+        const int64_t off = C.off[i];  // independent of the A and B loads: issued with them
+        const int cap = J.count_only ? 0 : (J.static_mode ? 0x7fffffff : C.cap[i]);
         T av[K];
         int64_t boff[K];
         int blen[K], start[K];
@@ -655,8 +656,6 @@ k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned m
                 else cp_async_4(&svals[(start[s] + q) * TM_NT], Bv + boff[s] + q);
             }
         cp_async_wait_all();
-        const int64_t off = C.off[i];
-        const int cap = J.count_only ? 0 : (J.static_mode ? 0x7fffffff : C.cap[i]);
         const int n = merge_rows_smem<SR, K>(scols, svals, av, start, blen, alen, C.col + off, Cv + off, cap);
         bool ok = true;
         if (J.count_only) {
@@ -699,8 +698,7 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = (long long)blockIdx.x * NG + g; it < cnt; it += (long long)gridDim.x * NG) {
-        const int t = J.bins[(int64_t)bin * J.bin_cap + it];
-        const int32_t i = J.R[t];
+        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
         for (int s = gl; s < TS; s += G) {
             keys[s] = -1;
             vals[s] = Sr<SR>::zero();
@@ -793,8 +791,7 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
-        const int t = J.bins[(int64_t)bin * J.bin_cap + it];
-        const int32_t i = J.R[t];
+        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
         for (int s = tid; s < TS; s += 256) {
             keys[s] = -1;
             vals[s] = Sr<SR>::zero();
@@ -873,8 +870,7 @@ k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
-        const int t = J.bins[(int64_t)bin * J.bin_cap + it];
-        const int32_t i = J.R[t];
+        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
         if (tid == 0) {
             s_lo = 0x7fffffff;
             s_hi = -1;
@@ -951,8 +947,7 @@ k_num_warp_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = (long long)blockIdx.x * NW + w; it < cnt; it += (long long)gridDim.x * NW) {
-        const int t = J.bins[(int64_t)bin * J.bin_cap + it];
-        const int32_t i = J.R[t];
+        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
         group_products<SR, 32>(A, B, i, 0xffffffffu, [&](int32_t j, T v) {
             atomicOr(&msk[j >> 5], 1u << (j & 31));
             Sr<SR>::acc(&acc[j], v);
@@ -1003,8 +998,7 @@ k_num_cta_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
-        const int t = J.bins[(int64_t)bin * J.bin_cap + it];
-        const int32_t i = J.R[t];
+        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
         group_products<SR, 32>(A, B, i, 0xffffffffu, [&](int32_t j, T v) {
             atomicOr(&msk[j >> 5], 1u << (j & 31));
             Sr<SR>::acc(&acc[j], v);
@@ -1100,7 +1094,7 @@ __global__ void __launch_bounds__(1024) k_split_prep(MatView A, CJob J, Ctl *ctl
         const long long slot = b0 + threadIdx.x;
         int nch = 0;
         if (slot < cnt) {
-            const int32_t i = J.R[J.bins[(int64_t)BIN_DSPLIT * J.bin_cap + slot]];
+            const int32_t i = J.bins[(int64_t)BIN_DSPLIT * J.bin_cap + slot];
             nch = (A.len[i] + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
         }
         const int tot = block_incl_scan(nch, incl, wsum);
@@ -1153,7 +1147,7 @@ k_num_dsplit(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
         const long long base = J.sp_pre[slot];
         const int nch = (int)(J.sp_pre[slot + 1] - base);
         const int c = (int)(w - base);
-        const int32_t i = J.R[J.bins[(int64_t)BIN_DSPLIT * J.bin_cap + slot]];
+        const int32_t i = J.bins[(int64_t)BIN_DSPLIT * J.bin_cap + slot];
         const int alen = A.len[i];
         const int a_lo = c * SPLIT_CHUNK, a_hi = a_lo + SPLIT_CHUNK < alen ? a_lo + SPLIT_CHUNK : alen;
         // each warp takes groups of 32 A entries of the chunk (no block barriers)
