@@ -194,7 +194,7 @@ unsigned long long dspg_kernel_launches(void);
  *    (table_shift 0 or 1), served by 8, 16 or 32 lanes per row while the
  *    table has at most 32, 64 or warp_max slots (lanes_min = 8, 16 or 32:
  *    the fewest lanes a row may get; warp_max in 0..1024), then by a whole
- *    CTA while it has at most cta_max slots (0..8192);
+ *    CTA while it has at most cta_max slots (0..16384);
  *  - longer rows: a CTA with a dense accumulator in global memory.
  * Every setting gives the same C: a table never has fewer slots than the
  * row's bound, which no row's distinct columns can exceed.  Only the speed

@@ -1155,17 +1155,17 @@ void check_tuning(const dspg_tuning &t) {
     if (t.lanes_min != 8 && t.lanes_min != 16 && t.lanes_min != 32)
         throw Err(DSPG_ERR_INVALID, "tuning: lanes_min must be 8, 16 or 32");
     if (t.table_shift < 0 || t.table_shift > 1) throw Err(DSPG_ERR_INVALID, "tuning: table_shift must be 0 or 1");
-    if (t.warp_max < 0 || t.warp_max > 1024 || t.cta_max < 0 || t.cta_max > 8192)
-        throw Err(DSPG_ERR_INVALID, "tuning: warp_max must be in 0..1024 and cta_max in 0..8192");
+    if (t.warp_max < 0 || t.warp_max > 1024 || t.cta_max < 0 || t.cta_max > 16384)
+        throw Err(DSPG_ERR_INVALID, "tuning: warp_max must be in 0..1024 and cta_max in 0..16384");
 }
 
 // The autotuner's candidates: the defaults first, then one or two changes
 // each (thread-merge reach, lanes per short row, table oversizing, the
 // warp/CTA and CTA/global crossovers).
 const dspg_tuning kCandidates[] = {
-    {8, 64, 8, 0, 1024, 8192}, {0, 0, 8, 0, 1024, 8192},  {4, 32, 8, 0, 1024, 8192}, {8, 64, 16, 0, 1024, 8192},
-    {8, 64, 32, 0, 1024, 8192}, {8, 64, 8, 1, 1024, 8192}, {8, 64, 8, 0, 512, 8192},  {8, 64, 8, 0, 1024, 4096},
-    {8, 64, 8, 0, 1024, 2048}, {8, 64, 8, 1, 512, 4096},  {0, 0, 16, 1, 1024, 8192},
+    {8, 64, 8, 0, 1024, 8192},  {0, 0, 8, 0, 1024, 8192},  {4, 32, 8, 0, 1024, 8192},  {8, 64, 16, 0, 1024, 8192},
+    {8, 64, 32, 0, 1024, 8192}, {8, 64, 8, 1, 1024, 8192}, {8, 64, 8, 0, 512, 8192},   {8, 64, 8, 0, 1024, 4096},
+    {8, 64, 8, 0, 1024, 16384}, {8, 64, 8, 1, 1024, 16384}, {0, 0, 16, 1, 1024, 8192}, {8, 64, 32, 0, 1024, 16384},
 };
 constexpr int kNumCandidates = (int)(sizeof(kCandidates) / sizeof(kCandidates[0]));
 

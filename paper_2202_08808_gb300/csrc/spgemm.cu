@@ -58,7 +58,7 @@ struct Sr<SR_MP> {
 
 enum {
     BIN_T8 = 0, BIN_G8, BIN_G16, BIN_W128, BIN_W256, BIN_W512, BIN_W1024,
-    BIN_C2048, BIN_C4096, BIN_C8192,
+    BIN_C2048, BIN_C4096, BIN_C8192, BIN_C16384,
     BIN_GD,
     BIN_WDENSE, BIN_CDENSE, BIN_DSPLIT,
     BIN_COUNT
@@ -89,7 +89,8 @@ __device__ __forceinline__ int pick_table_bin(long long need, const CJob &J) {
     if (need <= J.cta_max) {
         if (need <= 2048) return BIN_C2048;
         if (need <= 4096) return BIN_C4096;
-        return BIN_C8192;
+        if (need <= 8192) return BIN_C8192;
+        return BIN_C16384;
     }
     return BIN_GD;
 }
@@ -681,7 +682,10 @@ __global__ void __launch_bounds__(NW * 32)
 k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
-    constexpr int HC = TS;  // compacted list capacity
+    // rows of tables up to 64 slots are compacted and ranked (column order,
+    // cheap at that size); larger tables are written straight to C
+    constexpr bool RANKED = TS <= 64;
+    constexpr int HC = RANKED ? TS : 0;  // compacted list capacity
     constexpr int GPW = 32 / G;
     constexpr int NG = NW * GPW;  // groups per block
     extern __shared__ __align__(16) unsigned char smem[];
@@ -694,6 +698,8 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
     T *cv = (T *)smem + (size_t)NG * TS + (size_t)g * HC;
     int32_t *keys = (int32_t *)((T *)smem + (size_t)NG * (TS + HC)) + (size_t)g * TS;
     int32_t *ck = (int32_t *)((T *)smem + (size_t)NG * (TS + HC)) + (size_t)NG * TS + (size_t)g * HC;
+    (void)cv;
+    (void)ck;
     T *Cv = (T *)C.val;
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
@@ -720,26 +726,28 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
         }
         __syncwarp(gmask);
         int n = 0;
-        for (int s0 = 0; s0 < TS; s0 += G) {
-            const int s = s0 + gl;
-            const int32_t k = keys[s];
-            const bool occ = k >= 0;
-            const unsigned bal = (__ballot_sync(gmask, occ) & gmask) >> (gw * G);
-            if (occ) {
-                const int x = n + __popc(bal & ((1u << gl) - 1u));
-                if (x < HC) {
+        if constexpr (RANKED) {
+            for (int s0 = 0; s0 < TS; s0 += G) {
+                const int s = s0 + gl;
+                const int32_t k = keys[s];
+                const bool occ = k >= 0;
+                const unsigned bal = (__ballot_sync(gmask, occ) & gmask) >> (gw * G);
+                if (occ) {
+                    const int x = n + __popc(bal & ((1u << gl) - 1u));
                     ck[x] = k;
                     cv[x] = vals[s];
                 }
+                n += __popc(bal);
             }
-            n += __popc(bal);
+            __syncwarp(gmask);
+        } else {
+            for (int s0 = 0; s0 < TS; s0 += G)
+                n += __popc((__ballot_sync(gmask, keys[s0 + gl] >= 0) & gmask) >> (gw * G));
         }
-        if (n > HC) n = HC;  // unreachable: distinct columns <= ub <= TS
-        __syncwarp(gmask);
         int64_t dest = 0;
         if (gl == 0) dest = c_row_dest(C, J, ctl, i, n);
         dest = __shfl_sync(gmask, dest, 0, G);
-        if (n <= 64) {
+        if constexpr (RANKED) {
             // rank of each entry among the row's distinct columns
             for (int e = gl; e < n; e += G) {
                 const int32_t key = ck[e];
@@ -751,11 +759,20 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
                 }
             }
         } else if (dest >= 0) {
-            // longer rows go out in table order: C's rows need no column
+            // straight from the table, in table order: C's rows need no column
             // order (the reads sort them)
-            for (int s = gl; s < n; s += G) {
-                C.col[dest + s] = ck[s];
-                Cv[dest + s] = cv[s];
+            int x0 = 0;
+            for (int s0 = 0; s0 < TS; s0 += G) {
+                const int s = s0 + gl;
+                const int32_t k = keys[s];
+                const bool occ = k >= 0;
+                const unsigned bal = (__ballot_sync(gmask, occ) & gmask) >> (gw * G);
+                if (occ) {
+                    const int x = x0 + __popc(bal & ((1u << gl) - 1u));
+                    C.col[dest + x] = k;
+                    Cv[dest + x] = vals[s];
+                }
+                x0 += __popc(bal);
             }
         }
         if (gl == 0 && dest >= 0) C.len[i] = n;
@@ -772,20 +789,17 @@ __global__ void __launch_bounds__(256)
 k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
-    constexpr int HC = TS;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t p_boff[256];
     __shared__ T p_av[256];
     __shared__ int p_incl[256], p_blen[256], p_wsum[32];
-    __shared__ int s_n;
+    __shared__ int s_n, s_pos;
     __shared__ long long s_dest;
     __shared__ int s_ok;
     if (failed(ctl, mask)) return;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     T *vals = (T *)smem;
-    T *cv = vals + TS;
-    int32_t *keys = (int32_t *)(cv + HC);
-    int32_t *ck = keys + TS;
+    int32_t *keys = (int32_t *)(vals + TS);
     T *Cv = (T *)C.val;
     BlockProdSmem<T> ps{p_boff, p_av, p_incl, p_blen, p_wsum};
     long long nnz_acc = 0;
@@ -798,6 +812,7 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
         }
         if (tid == 0) {
             s_n = 0;
+            s_pos = 0;
             s_ok = 1;
         }
         __syncthreads();
@@ -813,24 +828,14 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
             __syncthreads();
             continue;
         }
+        // two passes over the table: count, then write straight to C (in
+        // table order; C's rows need no column order)
         for (int s0 = w * 32; s0 < TS; s0 += 256) {
-            const int s = s0 + lane;
-            const int32_t k = keys[s];
-            const bool occ = k >= 0;
-            const unsigned bal = __ballot_sync(0xffffffffu, occ);
-            int base = 0;
-            if (lane == 0 && bal) base = atomicAdd(&s_n, __popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (occ) {
-                const int x = base + __popc(bal & lanemask_lt());
-                if (x < HC) {
-                    ck[x] = k;
-                    cv[x] = vals[s];
-                }
-            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keys[s0 + lane] >= 0);
+            if (lane == 0 && bal) atomicAdd(&s_n, __popc(bal));
         }
         __syncthreads();
-        const int n = s_n < HC ? s_n : HC;
+        const int n = s_n;
         if (tid == 0) {
             s_dest = c_row_dest(C, J, ctl, i, n);
             nnz_acc += n;
@@ -838,9 +843,19 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
         __syncthreads();
         const long long dest = s_dest;
         if (dest >= 0) {
-            for (int s = tid; s < n; s += 256) {
-                C.col[dest + s] = ck[s];
-                Cv[dest + s] = cv[s];
+            for (int s0 = w * 32; s0 < TS; s0 += 256) {
+                const int s = s0 + lane;
+                const int32_t k = keys[s];
+                const bool occ = k >= 0;
+                const unsigned bal = __ballot_sync(0xffffffffu, occ);
+                int base = 0;
+                if (lane == 0 && bal) base = atomicAdd(&s_pos, __popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (occ) {
+                    const int x = base + __popc(bal & lanemask_lt());
+                    C.col[dest + x] = k;
+                    Cv[dest + x] = vals[s];
+                }
             }
             if (tid == 0) C.len[i] = n;
         }
@@ -1234,7 +1249,7 @@ static void launch_group_hash(const MatView &A, const MatView &B, const MatView 
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
     constexpr int NG = NW * (32 / G);
-    const size_t smem = (size_t)NG * (2 * TS) * (sizeof(T) + sizeof(int32_t));
+    const size_t smem = (size_t)NG * ((TS <= 64 ? 2 : 1) * TS) * (sizeof(T) + sizeof(int32_t));
     static bool set = false;
     if (!set) {
         cudaFuncSetAttribute(k_num_group_hash<SR, LOG_TS, G, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1253,7 +1268,7 @@ static void launch_cta_hash(const MatView &A, const MatView &B, const MatView &C
                             unsigned mask, int bin, cudaStream_t s, int num_sms) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
-    const size_t smem = (size_t)(2 * TS) * (sizeof(T) + sizeof(int32_t));
+    const size_t smem = (size_t)TS * (sizeof(T) + sizeof(int32_t));
     static bool set = false;
     if (!set) {
         cudaFuncSetAttribute(k_num_cta_hash<SR, LOG_TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1321,6 +1336,7 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
     launch_cta_hash<SR, 11>(A, B, C, J, ctl, mask, BIN_C2048, next(), num_sms);
     launch_cta_hash<SR, 12>(A, B, C, J, ctl, mask, BIN_C4096, next(), num_sms);
     launch_cta_hash<SR, 13>(A, B, C, J, ctl, mask, BIN_C8192, next(), num_sms);
+    launch_cta_hash<SR, 14>(A, B, C, J, ctl, mask, BIN_C16384, next(), num_sms);
     launch_k(k_num_gdense<SR>, grid_for(J.gd_ctas, J.rows_hint, 1), 512, 0, next(), A, B, C, J, ctl, mask, (int)BIN_GD);
 }
 

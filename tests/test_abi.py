@@ -81,5 +81,5 @@ def test_tuning_candidates_start_with_the_defaults_and_stay_in_range():
     for c in cands:
         assert 0 <= c["merge_k"] <= 8 and 0 <= c["merge_ub"] <= 64
         assert c["lanes_min"] in (8, 16, 32) and c["table_shift"] in (0, 1)
-        assert 0 <= c["warp_max"] <= 1024 and 0 <= c["cta_max"] <= 8192
+        assert 0 <= c["warp_max"] <= 1024 and 0 <= c["cta_max"] <= 16384
     assert len({tuple(sorted(c.items())) for c in cands}) == len(cands)
