@@ -179,6 +179,7 @@ struct CWs {
     DBuf<int32_t> R, iota, bins;
     DBuf<char> gd_acc;
     DBuf<uint32_t> gd_mask;
+    DBuf<int32_t> gd_list;
     int64_t gd_w = 0;
     int gd_ctas = 0;
     // detection
@@ -437,7 +438,7 @@ void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
         w.gd_w = (m + 31) / 32 * 32;
         // per-CTA dense accumulators for the longest rows: up to two CTAs per
         // SM, within a budget of 1/32 of the free memory (256 MiB .. 4 GiB)
-        const double per = (double)w.gd_w * (h->vsize + 0.125);
+        const double per = (double)w.gd_w * (h->vsize + 0.25);
         size_t free_b = 0, total_b = 0;
         CK(cudaMemGetInfo(&free_b, &total_b));
         const double budget = std::min(4.0 * (1 << 30), std::max(256.0 * (1 << 20), (double)free_b / 32.0));
@@ -445,6 +446,7 @@ void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
         w.gd_ctas = std::max(1, ctas);
         w.gd_acc.reserve(w.gd_w * w.gd_ctas * h->vsize);
         w.gd_mask.reserve(w.gd_w / 32 * w.gd_ctas);
+        w.gd_list.reserve(w.gd_w / 32 * w.gd_ctas);
         init_dense_scratch(h->sr, w.gd_acc.p, w.gd_mask.p, w.gd_w * w.gd_ctas, w.gd_w / 32 * w.gd_ctas, s);
     }
 }
@@ -457,6 +459,7 @@ CJob c_job(dspg_handle *h, const int32_t *R, bool static_mode) {
     J.bin_cap = std::max<int64_t>(w.nrows, 1);
     J.gd_acc = w.gd_acc.p;
     J.gd_mask = w.gd_mask.p;
+    J.gd_list = w.gd_list.p;
     J.gd_w = w.gd_w;
     J.gd_ctas = std::max(w.gd_ctas, 1);
     J.m = h->Bm().ncols;

@@ -71,6 +71,7 @@ struct CJob {
     int64_t bin_cap;
     void *gd_acc;             // per-CTA dense accumulators (global), gd_w entries each
     uint32_t *gd_mask;        // per-CTA presence bits, gd_w / 32 words each
+    int32_t *gd_list;         // per-CTA list of the mask words a row touched, gd_w / 32 each
     int64_t gd_w;
     int gd_ctas;
     int64_t m;                // columns of C

@@ -873,13 +873,13 @@ k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
     __shared__ int64_t p_boff[512];
     __shared__ T p_av[512];
     __shared__ int p_incl[512], p_blen[512], p_wsum[32];
-    __shared__ int s_lo, s_hi;
-    __shared__ int s_n;
+    __shared__ int s_nw, s_n, s_pos;
     __shared__ long long s_dest;
     if (failed(ctl, mask)) return;
     const int tid = threadIdx.x;
     T *acc = (T *)J.gd_acc + (int64_t)blockIdx.x * J.gd_w;
     uint32_t *msk = J.gd_mask + (int64_t)blockIdx.x * (J.gd_w / 32);
+    int32_t *touched = J.gd_list + (int64_t)blockIdx.x * (J.gd_w / 32);  // mask words this row set
     T *Cv = (T *)C.val;
     BlockProdSmem<T> ps{p_boff, p_av, p_incl, p_blen, p_wsum};
     long long nnz_acc = 0;
@@ -887,24 +887,21 @@ k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
         const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
         if (tid == 0) {
-            s_lo = 0x7fffffff;
-            s_hi = -1;
+            s_nw = 0;
             s_n = 0;
+            s_pos = 0;
         }
         __syncthreads();
-        int lo = 0x7fffffff, hi = -1;
         block_products<SR>(A, B, i, ps, [&](int32_t j, T v) {
-            atomicOr(&msk[j >> 5], 1u << (j & 31));
+            // the product that sets the first bit of a mask word lists the word,
+            // so the read-out visits only the words this row touched
+            if (atomicOr(&msk[j >> 5], 1u << (j & 31)) == 0u) touched[atomicAdd(&s_nw, 1)] = j >> 5;
             Sr<SR>::acc(&acc[j], v);
-            lo = min(lo, j);
-            hi = max(hi, j);
         });
-        atomicMin(&s_lo, lo);
-        atomicMax(&s_hi, hi);
         __syncthreads();
-        const int w0 = s_lo >> 5, w1 = s_hi < 0 ? -1 : (s_hi >> 5);
+        const int nw = s_nw;
         int c = 0;
-        for (int x = w0 + tid; x <= w1; x += 512) c += __popc(msk[x]);
+        for (int x = tid; x < nw; x += 512) c += __popc(__ldcg(msk + touched[x]));
         c = warp_sum<int>(c);
         if ((tid & 31) == 0 && c) atomicAdd(&s_n, c);
         __syncthreads();
@@ -915,29 +912,25 @@ k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
         }
         __syncthreads();
         const long long dest = s_dest;
-        int run = 0;  // entries written by earlier chunks
-        for (int x0 = w0; x0 <= w1; x0 += 512) {
-            const int x = x0 + tid;
-            const uint32_t word = x <= w1 ? msk[x] : 0u;
-            const int pc = __popc(word);
-            const int incl = block_incl_scan(pc, p_incl, p_wsum);
-            int o = run + p_incl[tid] - pc;
-            uint32_t bits = word;
+        // write (in word-list order: C's rows need no column order) and reset
+        for (int x = tid; x < nw; x += 512) {
+            const int wd = touched[x];
+            uint32_t bits = __ldcg(msk + wd);
+            int o = atomicAdd(&s_pos, __popc(bits));
             while (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
-                const int j = (x << 5) + b;
+                const int j = (wd << 5) + b;
                 if (dest >= 0) {
                     C.col[dest + o] = j;
-                    Cv[dest + o] = acc[j];
+                    Cv[dest + o] = __ldcg(acc + j);
                 }
                 acc[j] = Sr<SR>::zero();
                 o++;
             }
-            if (x <= w1) msk[x] = 0u;
-            run += incl;
-            __syncthreads();
+            msk[wd] = 0u;
         }
+        __syncthreads();
         if (tid == 0 && dest >= 0) C.len[i] = n;
     }
     if (tid == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
