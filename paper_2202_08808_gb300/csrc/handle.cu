@@ -977,7 +977,7 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
         }
         CK(cudaStreamSynchronize(s));
     }
-    if (hb) throw Err(DSPG_ERR_CUDA, "a stored row longer than 8192 entries is out of column order");
+    if (hb) throw Err(DSPG_ERR_CUDA, "a stored row longer than 16384 entries is out of column order");
     return nnz;
 }
 

@@ -152,7 +152,7 @@ void copy_rows(const int32_t *rows, int64_t n, const int64_t *src_off, const int
 void gather_rows_out(const int32_t *rows, int64_t n, const MatView &M, const int64_t *out_rowptr, int32_t *out_col,
                      void *out_val, int vsize, cudaStream_t s, int num_sms);
 // Sort each row of a gathered CSR (rowptr over n rows) by column, in place;
-// sets *bad if a row longer than 8192 entries is out of order.
+// sets *bad if a row longer than 16384 entries is out of order.
 void sort_rows(const int64_t *rowptr, int64_t n, int32_t *col, void *val, int vsize, unsigned *bad, cudaStream_t s,
                int num_sms);
 void lens_of_rows(const int32_t *rows, int64_t n, const int32_t *len, int32_t *out, cudaStream_t s);

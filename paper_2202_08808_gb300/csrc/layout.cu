@@ -109,7 +109,7 @@ void gather_rows_out(const int32_t *rows, int64_t n, const MatView &M, const int
 // table order); every read returns canonical rows, so the gathered rows are
 // sorted by column here.  Rows already in order are left as they are.
 constexpr int SORT_SHORT = 64;     // rows up to this length: a warp each
-constexpr int SORT_MAX = 8192;     // longer rows are written in order by their kernels
+constexpr int SORT_MAX = 16384;    // longer rows are written in order by their kernels
 
 template <typename T>
 __global__ void k_sort_short_rows(const int64_t *rowptr, int64_t n, int32_t *col, T *val) {

@@ -866,14 +866,17 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
 
 // ------------------------------------------------- global dense kernel
 
+constexpr int GD_SORT = 8192;  // rows touching at most this many mask words sort the word list
+
 template <int SR>
 __global__ void __launch_bounds__(512)
 k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
     using T = typename Sr<SR>::T;
+    extern __shared__ __align__(16) int32_t sl[];  // GD_SORT word indices, sorted
     __shared__ int64_t p_boff[512];
     __shared__ T p_av[512];
     __shared__ int p_incl[512], p_blen[512], p_wsum[32];
-    __shared__ int s_nw, s_n, s_pos;
+    __shared__ int s_nw, s_n, s_lo, s_hi;
     __shared__ long long s_dest;
     if (failed(ctl, mask)) return;
     const int tid = threadIdx.x;
@@ -889,7 +892,8 @@ k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
         if (tid == 0) {
             s_nw = 0;
             s_n = 0;
-            s_pos = 0;
+            s_lo = 0x7fffffff;
+            s_hi = -1;
         }
         __syncthreads();
         block_products<SR>(A, B, i, ps, [&](int32_t j, T v) {
@@ -900,10 +904,19 @@ k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
         });
         __syncthreads();
         const int nw = s_nw;
-        int c = 0;
-        for (int x = tid; x < nw; x += 512) c += __popc(__ldcg(msk + touched[x]));
+        int c = 0, lo = 0x7fffffff, hi = -1;
+        for (int x = tid; x < nw; x += 512) {
+            const int wd = touched[x];
+            c += __popc(__ldcg(msk + wd));
+            lo = min(lo, wd);
+            hi = max(hi, wd);
+        }
         c = warp_sum<int>(c);
         if ((tid & 31) == 0 && c) atomicAdd(&s_n, c);
+        if (hi >= 0) {
+            atomicMin(&s_lo, lo);
+            atomicMax(&s_hi, hi);
+        }
         __syncthreads();
         const int n = s_n;
         if (tid == 0) {
@@ -912,15 +925,44 @@ k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
         }
         __syncthreads();
         const long long dest = s_dest;
-        // write (in word-list order: C's rows need no column order) and reset
-        for (int x = tid; x < nw; x += 512) {
-            const int wd = touched[x];
-            uint32_t bits = __ldcg(msk + wd);
-            int o = atomicAdd(&s_pos, __popc(bits));
+        // the row goes out in column order: the touched words sorted (few
+        // words), or the whole touched range scanned in order (many)
+        const bool listed = nw <= GD_SORT && (int64_t)nw * 8 < (int64_t)(s_hi - s_lo + 1);
+        int nx = 0;
+        if (listed) {
+            int N = 2;
+            while (N < nw) N <<= 1;
+            for (int x = tid; x < N; x += 512) sl[x] = x < nw ? touched[x] : 0x7fffffff;
+            __syncthreads();
+            for (int size = 2; size <= N; size <<= 1)
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int q = tid; q < N / 2; q += 512) {
+                        const int x = 2 * q - (q & (stride - 1)), y = x + stride;
+                        const int32_t kx = sl[x], ky = sl[y];
+                        if ((kx > ky) == ((x & size) == 0)) {
+                            sl[x] = ky;
+                            sl[y] = kx;
+                        }
+                    }
+                    __syncthreads();
+                }
+            nx = nw;
+        } else {
+            nx = s_hi >= 0 ? s_hi - s_lo + 1 : 0;
+        }
+        int run = 0;  // entries written by earlier chunks
+        for (int x0 = 0; x0 < nx; x0 += 512) {
+            const int x = x0 + tid;
+            const int wd = x < nx ? (listed ? sl[x] : s_lo + x) : -1;
+            const uint32_t word = wd >= 0 ? __ldcg(msk + wd) : 0u;
+            const int pc = __popc(word);
+            const int incl = block_incl_scan(pc, p_incl, p_wsum);
+            int o = run + p_incl[tid] - pc;
+            uint32_t bits = word;
             while (bits) {
-                const int b = __ffs(bits) - 1;
+                const int bt = __ffs(bits) - 1;
                 bits &= bits - 1;
-                const int j = (wd << 5) + b;
+                const int j = (wd << 5) + bt;
                 if (dest >= 0) {
                     C.col[dest + o] = j;
                     Cv[dest + o] = __ldcg(acc + j);
@@ -928,9 +970,10 @@ k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
                 acc[j] = Sr<SR>::zero();
                 o++;
             }
-            msk[wd] = 0u;
+            if (word) msk[wd] = 0u;
+            run += incl;
+            __syncthreads();
         }
-        __syncthreads();
         if (tid == 0 && dest >= 0) C.len[i] = n;
     }
     if (tid == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
@@ -1330,7 +1373,16 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
     launch_cta_hash<SR, 12>(A, B, C, J, ctl, mask, BIN_C4096, next(), num_sms);
     launch_cta_hash<SR, 13>(A, B, C, J, ctl, mask, BIN_C8192, next(), num_sms);
     launch_cta_hash<SR, 14>(A, B, C, J, ctl, mask, BIN_C16384, next(), num_sms);
-    launch_k(k_num_gdense<SR>, grid_for(J.gd_ctas, J.rows_hint, 1), 512, 0, next(), A, B, C, J, ctl, mask, (int)BIN_GD);
+    {
+        constexpr size_t smem_g = GD_SORT * sizeof(int32_t);
+        static bool set_g = false;
+        if (!set_g) {
+            cudaFuncSetAttribute(k_num_gdense<SR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
+            set_g = true;
+        }
+        launch_k(k_num_gdense<SR>, grid_for(J.gd_ctas, J.rows_hint, 1), 512, smem_g, next(), A, B, C, J, ctl, mask,
+                 (int)BIN_GD);
+    }
 }
 
 void run_numeric(int sr, const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,

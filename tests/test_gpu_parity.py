@@ -409,3 +409,33 @@ def test_long_rows_sized_by_a_cta_wide_m(dspg, sr):
         R = oracle.row_dynamic(Ao, Co, b, Bo)
         assert np.array_equal(g.last_affected(), R)
         _check_state(g, Ao, Bo, f"long-row batch {k}")
+
+
+@pytest.mark.parametrize("cta_max", [8192, 16384])
+def test_rows_longer_than_the_tables_are_read_in_order(dspg, cta_max):
+    """Rows of C with 9,000 to 30,000 entries (hub rows of A over 60,000
+    columns): beyond the shared-memory tables they go to the global dense
+    kernel (or, with cta_max 16384, partly to the 16384-slot CTA table), and
+    every read returns them in column order, equal to the oracle's."""
+    sr = PLUS_TIMES_F64
+    hubs = {2, 300, 599}
+    A = _with_hubs(600, 3000, hubs, 2900, sr, 201)
+    B = random_csr(3000, 60000, 20, 202, sr)
+    g = dspg.DynamicSpGEMM(A, B)
+    g.set_tuning(dict(dspg.tuning_candidates()[0], cta_max=cta_max))
+    g.recompute_all()
+    Ao, Bo = OMat.from_csr(A), OMat.from_csr(B)
+    _check_state(g, Ao, Bo, f"long rows (cta_max {cta_max})")
+    Co = Ao.multiply(Bo)
+    lens = np.diff(Co.to_csr().rowptr)
+    assert lens.max() > 16384, "no row beyond the largest table"
+    b = random_batch(A.nrows, A.ncols, 200, 203, sr, A=A)
+    b.row[:30] = np.array(sorted(hubs), np.int32)[np.arange(30) % len(hubs)]
+    g.apply_batch(b)
+    R = oracle.row_dynamic(Ao, Co, b, Bo)
+    assert np.array_equal(g.last_affected(), R)
+    _check_state(g, Ao, Bo, f"long rows after a batch (cta_max {cta_max})")
+    rows = np.array(sorted(hubs) + [0, 1], np.int32)
+    rp, col, val = g.read_rows_C(rows)
+    o_rp, o_col, o_val = Ao.multiply_rows(Bo, rows)
+    assert np.array_equal(rp, o_rp) and np.array_equal(col, o_col)
