@@ -188,8 +188,12 @@ unsigned long long dspg_kernel_launches(void);
  * in a sparse accumulator; which accumulator serves which row is this
  * library's choice.  A row of R is binned by its product bound ub (the sum of
  * the lengths of the B rows it reads, capped at the column count):
- *  - thread merge: A rows with at most merge_k entries and ub <= merge_ub
- *    (merge_k in 0..8, merge_ub in 0..64; 0 turns the bin off);
+ *  - thread merge: A rows with at most merge_k entries (0..8; 0 turns the
+ *    merge off) and an uncapped bound ub <= 64, in two kernels: ub <=
+ *    merge_ub (0..64) in one whose threads stage merge_ub entries in shared
+ *    memory, so that a lower bound lets more threads run at once (at 49,
+ *    three 128-thread blocks per SM for double, at the cost of L1 cache),
+ *    the rest in one staging 64;
  *  - hash tables in shared memory of at least ub << table_shift slots
  *    (table_shift 0 or 1), served by 8, 16 or 32 lanes per row while the
  *    table has at most 32, 64 or warp_max slots (lanes_min = 8, 16 or 32:

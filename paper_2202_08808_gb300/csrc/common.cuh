@@ -52,7 +52,7 @@ struct UpdCtl {
     long long pad[5];
 };
 
-constexpr int NBINS = 16;
+constexpr int NBINS = 24;
 
 struct Ctl {
     unsigned status;
@@ -71,8 +71,10 @@ struct Ctl {
     long long a_entries;       // A' entries read by the recompute
     long long n_est;           // rows sized by the learned estimator
     long long n_ovf;           // of those, rows whose table overflowed
-    long long n_long;          // rows with long A rows, sized by a CTA each
-    long long pad[3];
+    long long timeout_bin;     // 1 + the bin whose table or staging overflowed (ST_TIMEOUT)
+    long long timeout_row;     // a row it happened on
+    long long timeout_ub;      // that row's product bound, summed again when it happened
+    long long pad[1];
 };
 
 // A row-slack CSR ("slack-CSR") on the device: row i occupies
@@ -168,6 +170,21 @@ __device__ __forceinline__ int64_t upper_bound_dev(const T *a, int64_t lo, int64
         if (a[mid] <= x) lo = mid + 1; else hi = mid;
     }
     return lo;
+}
+
+// End of the run of x that starts at s in the sorted array a[0, n) (a[s] ==
+// x): the first index past it.  Galloping forward (1, 2, 4, ... entries)
+// before the binary search makes a short run cost a load or two instead of
+// a search over the whole array.
+template <typename T>
+__device__ __forceinline__ int64_t run_end_dev(const T *a, int64_t s, int64_t n, T x) {
+    int64_t lo = s, step = 1, hi = s + 1 < n ? s + 1 : n;
+    while (hi < n && a[hi] == x) {
+        lo = hi;
+        step <<= 1;
+        hi = lo + step < n ? lo + step : n;
+    }
+    return upper_bound_dev<T>(a, lo + 1, hi, x);
 }
 
 #endif  // __CUDACC__

@@ -179,7 +179,7 @@ struct CWs {
     DBuf<int32_t> R, iota, bins;
     DBuf<char> gd_acc;
     DBuf<uint32_t> gd_mask;
-    DBuf<int32_t> gd_list;
+    DBuf<uint32_t> gd_sum;
     int64_t gd_w = 0;
     int gd_ctas = 0;
     // detection
@@ -189,7 +189,6 @@ struct CWs {
     // learned sizing: rows waiting for an estimate, rows whose table overflowed
     DBuf<int4> est;
     DBuf<int32_t> ovf;
-    DBuf<int32_t> longr;  // rows with long A rows (sizing)
     // split rows (dense mode): global accumulators
     int64_t sp_rows = 0;
     DBuf<char> sp_acc;
@@ -236,6 +235,12 @@ thread_local std::string g_err;
 
 void dspg::set_thread_error(const char *msg) { g_err = msg; }
 
+// Side streams of the recompute: the bin kernels run as parallel branches
+// (the first, the thread-merge bin, alone on the handle's stream).  More
+// branches than the device's hardware queues (8 by default) made the
+// launches share queues and wait on each other: three side streams.
+constexpr int NUM_SIDE = 3;
+
 struct dspg_handle {
     int sr = 0, vsize = 8, num_sms = 148, dev = 0;
     dspg_options opt{};
@@ -243,12 +248,14 @@ struct dspg_handle {
     bool b_is_a = true;
     bool has_at = false;
     Ctl *ctl = nullptr;   // device
-    Ctl *hctl = nullptr;  // pinned host mirror
+    Ctl *hctl = nullptr;      // pinned, mapped host mirror
+    Ctl *hctl_dev = nullptr;  // its device address
     UpdWs wA, wB, wAT;
     CWs wc;
     BatchIn inA, inB;
     InArgs *d_args = nullptr;  // device: where the A, B and forwarded batches are (read by the sorts)
-    InArgs *h_args = nullptr;  // pinned host mirror, copied in by the pipeline's first step
+    InArgs *h_args = nullptr;  // pinned, mapped host mirror, fetched by the pipeline's first step
+    InArgs *h_args_dev = nullptr;
     int64_t last_nR = 0;
     bool prof = false;
     cudaEvent_t pev[10] = {};  // stage boundaries (profiling)
@@ -256,9 +263,9 @@ struct dspg_handle {
     // streams and events of the pipeline's branches
     cudaStream_t gs = nullptr;       // graphs run here
     cudaStream_t side = nullptr;     // transposed-pattern branch
-    cudaStream_t nstr[3] = {};       // numeric bin branches
+    cudaStream_t nstr[NUM_SIDE] = {};  // numeric bin branches
     cudaEvent_t evIn = nullptr, evFork = nullptr, evDetect = nullptr, evSide = nullptr, evSize = nullptr;
-    cudaEvent_t evNum[3] = {};
+    cudaEvent_t evNum[NUM_SIDE] = {};
     // captured pipelines, keyed by batch sizes and the buffer epoch
     struct Graph {
         int64_t nA, nB;
@@ -306,6 +313,11 @@ void set_defaults(dspg_options *o) {
     o->arena_headroom = 1.5;
     o->keep_transpose = -1;
     o->exact_static = 0;
+}
+
+std::string overflow_message(const Ctl *c) {
+    return "accumulator probe limit reached (bin " + std::to_string(c->timeout_bin - 1) + ", row " +
+           std::to_string(c->timeout_row) + ", product bound " + std::to_string(c->timeout_ub) + ")";
 }
 
 void read_ctl(dspg_handle *h, cudaStream_t s) {
@@ -417,7 +429,6 @@ void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
     CK(cudaMemsetAsync(w.bmR.p, 0, sizeof(uint32_t) * w.bmR.n, s));
     w.est.reserve(nn);
     w.ovf.reserve(nn);
-    w.longr.reserve(nn);
     const int64_t nb = std::max<int64_t>(h->Bm().nrows, 1);
     w.nrows_b = nb;
     w.bmK.reserve(nb / 32 + 2);
@@ -438,7 +449,7 @@ void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
         w.gd_w = (m + 31) / 32 * 32;
         // per-CTA dense accumulators for the longest rows: up to two CTAs per
         // SM, within a budget of 1/32 of the free memory (256 MiB .. 4 GiB)
-        const double per = (double)w.gd_w * (h->vsize + 0.25);
+        const double per = (double)w.gd_w * (h->vsize + 0.13);
         size_t free_b = 0, total_b = 0;
         CK(cudaMemGetInfo(&free_b, &total_b));
         const double budget = std::min(4.0 * (1 << 30), std::max(256.0 * (1 << 20), (double)free_b / 32.0));
@@ -446,7 +457,9 @@ void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
         w.gd_ctas = std::max(1, ctas);
         w.gd_acc.reserve(w.gd_w * w.gd_ctas * h->vsize);
         w.gd_mask.reserve(w.gd_w / 32 * w.gd_ctas);
-        w.gd_list.reserve(w.gd_w / 32 * w.gd_ctas);
+        const int64_t nsum = (w.gd_w / 32 + 31) / 32;
+        w.gd_sum.reserve(nsum * w.gd_ctas);
+        CK(cudaMemsetAsync(w.gd_sum.p, 0, sizeof(uint32_t) * nsum * w.gd_ctas, s));
         init_dense_scratch(h->sr, w.gd_acc.p, w.gd_mask.p, w.gd_w * w.gd_ctas, w.gd_w / 32 * w.gd_ctas, s);
     }
 }
@@ -459,7 +472,7 @@ CJob c_job(dspg_handle *h, const int32_t *R, bool static_mode) {
     J.bin_cap = std::max<int64_t>(w.nrows, 1);
     J.gd_acc = w.gd_acc.p;
     J.gd_mask = w.gd_mask.p;
-    J.gd_list = w.gd_list.p;
+    J.gd_sum = w.gd_sum.p;
     J.gd_w = w.gd_w;
     J.gd_ctas = std::max(w.gd_ctas, 1);
     J.m = h->Bm().ncols;
@@ -467,7 +480,6 @@ CJob c_job(dspg_handle *h, const int32_t *R, bool static_mode) {
     J.static_mode = static_mode ? 1 : 0;
     J.slack_min = h->opt.slack_min;
     J.slack_div = h->opt.slack_div;
-    J.bmR = w.bmR.p;
     J.rows_hint = h->A.nrows;
     J.tm_k = h->tune.merge_k;
     J.tm_ub = h->tune.merge_ub;
@@ -481,7 +493,6 @@ CJob c_job(dspg_handle *h, const int32_t *R, bool static_mode) {
     J.est_w = h->est_w.p;
     J.est = w.est.p;
     J.ovf = w.ovf.p;
-    J.longr = w.longr.p;
     J.sp_rows = J.dense_mode ? w.sp_rows : 0;
     J.sp_acc = w.sp_acc.p;
     J.sp_mask = w.sp_mask.p;
@@ -513,10 +524,11 @@ CommitJob upd_commit_job(dspg_handle *h, UpdWs &w, unsigned arena_bit, unsigned 
 // The bin kernels of the recompute run on four branches that join s again.
 void numeric_branches(dspg_handle *h, cudaStream_t s, const CJob &J) {
     CK(cudaEventRecord(h->evSize, s));
-    for (int k = 0; k < 3; k++) CK(cudaStreamWaitEvent(h->nstr[k], h->evSize, 0));
-    const cudaStream_t ss[4] = {s, h->nstr[0], h->nstr[1], h->nstr[2]};
-    run_numeric(h->sr, h->A.view(), h->Bm().view(), h->C.view(), J, h->ctl, M_C, ss, 4, h->num_sms);
-    for (int k = 0; k < 3; k++) {
+    for (int k = 0; k < NUM_SIDE; k++) CK(cudaStreamWaitEvent(h->nstr[k], h->evSize, 0));
+    cudaStream_t ss[NUM_SIDE + 1] = {s};
+    for (int k = 0; k < NUM_SIDE; k++) ss[k + 1] = h->nstr[k];
+    run_numeric(h->sr, h->A.view(), h->Bm().view(), h->C.view(), J, h->ctl, M_C, ss, NUM_SIDE + 1, h->num_sms);
+    for (int k = 0; k < NUM_SIDE; k++) {
         CK(cudaEventRecord(h->evNum[k], h->nstr[k]));
         CK(cudaStreamWaitEvent(s, h->evNum[k], 0));
     }
@@ -587,7 +599,7 @@ void static_recompute(dspg_handle *h, cudaStream_t s) {
     CK(cudaMemcpyAsync(h->ctl->bin_count, h->hctl->bin_count, sizeof(h->hctl->bin_count), cudaMemcpyHostToDevice, s));
     numeric_branches(h, s, c_job(h, h->wc.iota.p, true));
     read_ctl(h, s);
-    if (h->hctl->status & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, "accumulator probe limit reached");
+    if (h->hctl->status & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, overflow_message(h->hctl));
     if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "static recompute failed with status " + std::to_string(h->hctl->status));
     h->epoch++;
 }
@@ -629,7 +641,6 @@ void build_transpose(dspg_handle *h, cudaStream_t s) {
 // ------------------------------------------------------------ pipeline
 
 void stage_sort(dspg_handle *h, cudaStream_t s) {
-    CK(cudaMemcpyAsync(h->d_args, h->h_args, 3 * sizeof(InArgs), cudaMemcpyHostToDevice, s));
     if (h->inA.n > 0)
         sort_updates(h->d_args + 0, h->inA.n, h->A.nrows, h->A.ncols, h->sr, true, h->wA.sort_out(), h->wA.sort_tmp(),
                      h->ctl, 0u, s);
@@ -638,34 +649,51 @@ void stage_sort(dspg_handle *h, cudaStream_t s) {
                      h->ctl, 0u, s);
 }
 
+DetectBufs detect_bufs(dspg_handle *h) {
+    CWs &w = h->wc;
+    return DetectBufs{w.bmR.p, w.bmK.p, w.R.p, w.K.p, &h->ctl->n_K};
+}
+
+// Classification of the sorted batches against the stored rows; it also
+// marks the rows with an effective change, the first step of the
+// affected-row detection (rows of the A batch are rows of C; rows of the B
+// batch, or of the A batch when B is A, are rows of B* whose columns are
+// followed next).
 void stage_classify(dspg_handle *h, cudaStream_t s) {
+    const DetectBufs D = detect_bufs(h);
     if (h->inA.n > 0) {
         UpdJob J = h->wA.job(h->inA.n);
-        run_classify(J, h->A.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, s, h->num_sms);
+        run_classify(J, h->A.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, D, true,
+                     h->b_is_a && h->has_at, s, h->num_sms);
     }
     if (!h->b_is_a && h->inB.n > 0) {
         UpdJob J = h->wB.job(h->inB.n);
-        run_classify(J, h->B.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, s, h->num_sms);
+        run_classify(J, h->B.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, D, false, true, s,
+                     h->num_sms);
     }
 }
 
-void stage_detect(dspg_handle *h, cudaStream_t s) {
-    CWs &w = h->wc;
-    DetectBufs D{w.bmR.p, w.bmK.p, w.R.p, w.K.p, &h->ctl->n_K};
-    const bool use_at = h->has_at;
+// Second step of the detection: rows i with A(i,k) != 0 for the marked
+// rows k of B*, read from the transposed pattern of A.  It shares its launch
+// with the merge copy of the matrix whose batch marked B* (B, or A when B
+// is A); returns which (0: A, 1: B, -1: none).
+int stage_detect(dspg_handle *h, cudaStream_t s) {
+    const DetectBufs D = detect_bufs(h);
+    const bool any_cols = h->has_at && (h->b_is_a ? h->inA.n > 0 : h->inB.n > 0);
+    if (!any_cols) return -1;
     if (h->b_is_a) {
-        run_detect_entries(h->wA.row.p, h->wA.kind.p, h->inA.n, true, use_at, D, h->ctl, M_AB, s);
-    } else {
-        run_detect_entries(h->wA.row.p, h->wA.kind.p, h->inA.n, true, false, D, h->ctl, M_AB, s);
-        if (h->inB.n > 0) run_detect_entries(h->wB.row.p, h->wB.kind.p, h->inB.n, false, true, D, h->ctl, M_AB, s);
+        run_detect_merge(h->AT.view(), D, h->wA.job(h->inA.n), h->A.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
+        return 0;
     }
-    const bool any_cols = use_at && (h->b_is_a ? h->inA.n > 0 : h->inB.n > 0);
-    if (any_cols) run_detect_cols(h->AT.view(), D, h->ctl, M_AB, s, h->num_sms);
+    run_detect_merge(h->AT.view(), D, h->wB.job(h->inB.n), h->B.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
+    return 1;
 }
 
-void stage_merge(dspg_handle *h, cudaStream_t s) {
-    if (h->inA.n > 0) run_merge_copy(h->wA.job(h->inA.n), h->A.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
-    if (!h->b_is_a && h->inB.n > 0)
+// The merge copies not done with the detection.
+void stage_merge(dspg_handle *h, cudaStream_t s, int merged) {
+    if (h->inA.n > 0 && merged != 0)
+        run_merge_copy(h->wA.job(h->inA.n), h->A.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
+    if (!h->b_is_a && h->inB.n > 0 && merged != 1)
         run_merge_copy(h->wB.job(h->inB.n), h->B.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
 }
 
@@ -688,7 +716,8 @@ void transpose_front(dspg_handle *h, cudaStream_t s) {
     sort_updates(h->d_args + 2, n, h->AT.nrows + 1, h->AT.ncols, h->sr, false, w.sort_out(), w.sort_tmp(), h->ctl, M_AT,
                  s);
     UpdJob J = w.job(n);
-    run_classify(J, h->AT.view(), 0, h->ctl, M_AT & ~ST_AT_STAGE, ST_AT_STAGE, s, h->num_sms);
+    run_classify(J, h->AT.view(), 0, h->ctl, M_AT & ~ST_AT_STAGE, ST_AT_STAGE, DetectBufs{}, false, false, s,
+                 h->num_sms);
     run_merge_copy(J, h->AT.view(), 0, h->ctl, M_AT, s, h->num_sms);
 }
 
@@ -711,7 +740,6 @@ CJob size_exact(dspg_handle *h, const int32_t *R, int64_t n_max, cudaStream_t s)
     numeric_branches(h, s, Jc);
     CK(cudaMemsetAsync(h->ctl->bin_count, 0, sizeof(h->ctl->bin_count), s));
     CK(cudaMemsetAsync(&h->ctl->nnz_written, 0, sizeof(long long), s));
-    CK(cudaMemsetAsync(&h->ctl->n_long, 0, sizeof(long long), s));  // the second pass lists long rows again
     CJob J2 = J;
     J2.sizing = SIZE_COUNT;
     run_size_bins(h->A.view(), h->Bm().view(), h->C.view(), J2, n_max, h->ctl, M_AB, s, h->num_sms);
@@ -753,7 +781,7 @@ void pipeline(dspg_handle *h, cudaStream_t s, bool timed, bool capturing) {
         transpose_front(h, h->side);
     }
     mark(2, s);
-    stage_detect(h, s);
+    const int merged = stage_detect(h, s);
     if (side_on) {
         CK(cudaEventRecord(h->evDetect, s));
         CK(cudaStreamWaitEvent(h->side, h->evDetect, 0));
@@ -761,8 +789,10 @@ void pipeline(dspg_handle *h, cudaStream_t s, bool timed, bool capturing) {
         mark(9, h->side);
         CK(cudaEventRecord(h->evSide, h->side));
     }
+    // R from the detection's bitmap, in row order within each block's range
+    run_collect_rows(h->wc.bmR.p, (h->A.nrows + 31) / 32, h->wc.R.p, h->ctl, M_AB, s, h->num_sms);
     mark(3, s);
-    stage_merge(h, s);
+    stage_merge(h, s, merged);
     mark(4, s);
     stage_commit_ab(h, s);
     mark(5, s);
@@ -845,9 +875,9 @@ void run_first(dspg_handle *h, cudaStream_t s) {
             CK(cudaStreamWaitEvent(h->gs, h->evIn, 0));
             const unsigned long long k0 = launch_counter();
             CK(cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeThreadLocal));
-            cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->gs);
+            begin_batch(h->h_args_dev, h->d_args, h->ctl, h->gs);
             pipeline(h, h->gs, h->prof, true);
-            cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->gs);
+            end_batch(h->ctl, h->hctl_dev, h->gs);
             CK(cudaStreamEndCapture(h->gs, &graph));
             cudaGraphExec_t exec = nullptr;
             const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
@@ -868,7 +898,7 @@ void run_first(dspg_handle *h, cudaStream_t s) {
         if (h->seen.size() >= 16) h->seen.erase(h->seen.begin());
         h->seen.push_back(dspg_handle::Graph{nA, nB, h->epoch, h->prof, nullptr, 0});
     }
-    CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+    begin_batch(h->h_args_dev, h->d_args, h->ctl, s);
     pipeline(h, s, h->prof, false);
     CK(cudaGetLastError());
     read_ctl(h, s);
@@ -952,24 +982,74 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
     DBuf<int64_t> rp;
     const int64_t nnz = mat_rowptr(h, M, rows, n, rp, s);
     if (!rowptr) return nnz;
-    DBuf<unsigned> bad;
-    bad.reserve(1);
-    CK(cudaMemsetAsync(bad.p, 0, sizeof(unsigned), s));
-    unsigned hb = 0;
+    // rows too long to sort in shared memory are listed, then sorted together
+    const int64_t list_cap = nnz / 16385 + 1;
+    DBuf<unsigned> n_listed;
+    DBuf<int64_t> listed;
+    n_listed.reserve(1);
+    listed.reserve(list_cap);
+    CK(cudaMemsetAsync(n_listed.p, 0, sizeof(unsigned), s));
+    auto sort_out = [&](int32_t *oc, void *ov) {
+        sort_rows(rp.p, n, oc, ov, M.vsize, n_listed.p, listed.p, list_cap, s, h->num_sms);
+        unsigned nl = 0;
+        CK(cudaMemcpyAsync(&nl, n_listed.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (nl == 0) return;
+        if ((int64_t)nl > list_cap) throw Err(DSPG_ERR_CUDA, "more long rows than the read can hold");
+        std::vector<int64_t> lh(nl), lo(nl), hi(nl), rph(n + 1);
+        CK(cudaMemcpyAsync(lh.data(), listed.p, sizeof(int64_t) * nl, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(rph.data(), rp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (unsigned k = 0; k < nl; k++) {
+            lo[k] = rph[lh[k]];
+            hi[k] = rph[lh[k] + 1];
+        }
+        // groups of rows of at most 2^28 entries (the radix sort's indices are 32-bit)
+        const int cb = bits_for(std::max<int64_t>(M.ncols, 2));
+        unsigned k0 = 0;
+        while (k0 < nl) {
+            std::vector<int64_t> pre(1, 0);
+            unsigned k1 = k0;
+            while (k1 < nl && (k1 == k0 || pre.back() + (hi[k1] - lo[k1]) <= (int64_t(1) << 28))) {
+                pre.push_back(pre.back() + (hi[k1] - lo[k1]));
+                k1++;
+            }
+            const int nk = (int)(k1 - k0);
+            const int64_t total = pre.back();
+            DBuf<int64_t> d_pre, d_list, scan_tmp, scan_out;
+            DBuf<uint64_t> kk0, kk1;
+            DBuf<uint32_t> ii0, ii1, counts;
+            DBuf<int32_t> tcol;
+            DBuf<char> tval;
+            d_pre.reserve(nk + 1);
+            d_list.reserve(nk);
+            kk0.reserve(total); kk1.reserve(total); ii0.reserve(total); ii1.reserve(total);
+            int64_t cnt;
+            sort_tmp_sizes(total, &cnt);
+            counts.reserve(cnt);
+            scan_out.reserve(cnt + 1);
+            scan_tmp.reserve(scan_tmp_entries(cnt) + 1);
+            tcol.reserve(total);
+            tval.reserve(total * std::max(M.vsize, 1));
+            CK(cudaMemcpyAsync(d_pre.p, pre.data(), sizeof(int64_t) * (nk + 1), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(d_list.p, lh.data() + k0, sizeof(int64_t) * nk, cudaMemcpyHostToDevice, s));
+            SortScratch w{kk0.p, kk1.p, ii0.p, ii1.p, counts.p, scan_tmp.p, scan_out.p, tcol.p, (void *)tval.p};
+            sort_listed_rows(rp.p, d_list.p, d_pre.p, nk, total, cb, oc, ov, M.vsize, w, s, h->num_sms);
+            CK(cudaStreamSynchronize(s));
+            k0 = k1;
+        }
+    };
     if (on_device) {
         CK(cudaMemcpyAsync(rowptr, rp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
         gather_rows_out(rows, n, M.view(), rp.p, col, val, M.vsize, s, h->num_sms);
-        sort_rows(rp.p, n, col, val, M.vsize, bad.p, s, h->num_sms);
-        CK(cudaMemcpyAsync(&hb, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        sort_out(col, val);
     } else {
         DBuf<int32_t> c;
         DBuf<char> v;
         c.reserve(std::max<int64_t>(nnz, 1));
         v.reserve(std::max<int64_t>(nnz, 1) * std::max(M.vsize, 1));
         gather_rows_out(rows, n, M.view(), rp.p, c.p, v.p, M.vsize, s, h->num_sms);
-        sort_rows(rp.p, n, c.p, M.vsize ? (void *)v.p : nullptr, M.vsize, bad.p, s, h->num_sms);
-        CK(cudaMemcpyAsync(&hb, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        sort_out(c.p, M.vsize ? (void *)v.p : nullptr);
         CK(cudaMemcpyAsync(rowptr, rp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
         if (nnz > 0) {
             if (col) CK(cudaMemcpyAsync(col, c.p, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s));
@@ -977,7 +1057,6 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
         }
         CK(cudaStreamSynchronize(s));
     }
-    if (hb) throw Err(DSPG_ERR_CUDA, "a stored row longer than 16384 entries is out of column order");
     return nnz;
 }
 
@@ -1010,11 +1089,14 @@ void recover(dspg_handle *h, cudaStream_t s) {
         for (int iter = 0; iter < 8 && h->hctl->status; iter++) {
         const unsigned st = h->hctl->status;
         if (st & ST_INVALID) throw Err(DSPG_ERR_INVALID, "batch entry out of range or with an invalid value/op");
-        if (st & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, "accumulator probe limit reached");
+        if (st & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, overflow_message(h->hctl));
         if (st & ST_AB_STAGE) {
             if (h->wA.grow_stage(h->hctl->u[0].stage_top + 1024)) h->epoch++;
             if (h->wB.grow_stage(h->hctl->u[1].stage_top + 1024)) h->epoch++;
             CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+            // the failed classification marked rows for the detection
+            CK(cudaMemsetAsync(h->wc.bmR.p, 0, sizeof(uint32_t) * h->wc.bmR.n, s));
+            CK(cudaMemsetAsync(h->wc.bmK.p, 0, sizeof(uint32_t) * h->wc.bmK.n, s));
             pipeline(h, s, false, false);
             read_ctl(h, s);
             continue;
@@ -1166,9 +1248,10 @@ void check_tuning(const dspg_tuning &t) {
 // each (thread-merge reach, lanes per short row, table oversizing, the
 // warp/CTA and CTA/global crossovers).
 const dspg_tuning kCandidates[] = {
-    {8, 64, 8, 0, 1024, 8192},  {0, 0, 8, 0, 1024, 8192},  {4, 32, 8, 0, 1024, 8192},  {8, 64, 16, 0, 1024, 8192},
-    {8, 64, 32, 0, 1024, 8192}, {8, 64, 8, 1, 1024, 8192}, {8, 64, 8, 0, 512, 8192},   {8, 64, 8, 0, 1024, 4096},
-    {8, 64, 8, 0, 1024, 16384}, {8, 64, 8, 1, 1024, 16384}, {0, 0, 16, 1, 1024, 8192}, {8, 64, 32, 0, 1024, 16384},
+    {8, 64, 8, 0, 1024, 8192},  {0, 0, 8, 0, 1024, 8192},   {4, 32, 8, 0, 1024, 8192},  {8, 49, 8, 0, 1024, 8192},
+    {8, 64, 16, 0, 1024, 8192}, {8, 64, 32, 0, 1024, 8192}, {8, 64, 8, 1, 1024, 8192},  {8, 64, 8, 0, 512, 8192},
+    {8, 64, 8, 0, 1024, 4096},  {8, 64, 8, 0, 1024, 16384}, {8, 64, 8, 1, 1024, 16384}, {8, 64, 32, 0, 1024, 16384},
+    {0, 0, 16, 1, 1024, 8192},
 };
 constexpr int kNumCandidates = (int)(sizeof(kCandidates) / sizeof(kCandidates[0]));
 
@@ -1221,14 +1304,18 @@ dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, 
         CK(cudaMalloc((void **)&h->ctl, sizeof(Ctl)));
         CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-        for (int k = 0; k < 3; k++) CK(cudaStreamCreateWithFlags(&h->nstr[k], cudaStreamNonBlocking));
-        for (cudaEvent_t *e : {&h->evIn, &h->evFork, &h->evDetect, &h->evSide, &h->evSize, &h->evNum[0], &h->evNum[1],
-                               &h->evNum[2]})
+        for (int k = 0; k < NUM_SIDE; k++) {
+            CK(cudaStreamCreateWithFlags(&h->nstr[k], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&h->evNum[k], cudaEventDisableTiming));
+        }
+        for (cudaEvent_t *e : {&h->evIn, &h->evFork, &h->evDetect, &h->evSide, &h->evSize})
             CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         if (const char *env = getenv("DSPG_NO_GRAPHS")) h->use_graphs = env[0] == '0';
-        CK(cudaMallocHost((void **)&h->hctl, sizeof(Ctl)));
+        CK(cudaHostAlloc((void **)&h->hctl, sizeof(Ctl), cudaHostAllocMapped));
+        CK(cudaHostGetDevicePointer((void **)&h->hctl_dev, h->hctl, 0));
         CK(cudaMalloc((void **)&h->d_args, 3 * sizeof(InArgs)));
-        CK(cudaMallocHost((void **)&h->h_args, 3 * sizeof(InArgs)));
+        CK(cudaHostAlloc((void **)&h->h_args, 3 * sizeof(InArgs), cudaHostAllocMapped));
+        CK(cudaHostGetDevicePointer((void **)&h->h_args_dev, h->h_args, 0));
         std::memset(h->h_args, 0, 3 * sizeof(InArgs));
         std::memset(h->hctl, 0, sizeof(Ctl));
         h->wA.which = 0; h->wA.vsize = h->vsize;
@@ -1609,9 +1696,9 @@ dspg_status dspg_group_apply(dspg_group *g, const dspg_updates *dA, const dspg_u
                 CK(cudaEventRecord(g->evFork, g->gs));
                 for (dspg_handle *h : g->hs) {
                     CK(cudaStreamWaitEvent(h->gs, g->evFork, 0));
-                    cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->gs);
+                    begin_batch(h->h_args_dev, h->d_args, h->ctl, h->gs);
                     pipeline(h, h->gs, false, true);
-                    cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->gs);
+                    end_batch(h->ctl, h->hctl_dev, h->gs);
                     CK(cudaEventRecord(h->evIn, h->gs));
                     CK(cudaStreamWaitEvent(g->gs, h->evIn, 0));
                 }
@@ -1641,7 +1728,7 @@ dspg_status dspg_group_apply(dspg_group *g, const dspg_updates *dA, const dspg_u
             CK(cudaEventRecord(g->evFork, s));
             for (dspg_handle *h : g->hs) {
                 CK(cudaStreamWaitEvent(h->gs, g->evFork, 0));
-                CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->gs));
+                begin_batch(h->h_args_dev, h->d_args, h->ctl, h->gs);
                 pipeline(h, h->gs, false, false);
                 CK(cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->gs));
                 CK(cudaEventRecord(h->evIn, h->gs));
@@ -1698,9 +1785,13 @@ void dspg_destroy(dspg_handle *h) {
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     for (int k = 0; k < 10; k++)
         if (h->pev[k]) cudaEventDestroy(h->pev[k]);
-    for (cudaEvent_t e : {h->evIn, h->evFork, h->evDetect, h->evSide, h->evSize, h->evNum[0], h->evNum[1], h->evNum[2]})
+    for (cudaEvent_t e : {h->evIn, h->evFork, h->evDetect, h->evSide, h->evSize})
         if (e) cudaEventDestroy(e);
-    for (cudaStream_t st : {h->gs, h->side, h->nstr[0], h->nstr[1], h->nstr[2]})
+    for (int k = 0; k < NUM_SIDE; k++) {
+        if (h->evNum[k]) cudaEventDestroy(h->evNum[k]);
+        if (h->nstr[k]) cudaStreamDestroy(h->nstr[k]);
+    }
+    for (cudaStream_t st : {h->gs, h->side})
         if (st) cudaStreamDestroy(st);
     if (h->ctl) cudaFree(h->ctl);
     if (h->hctl) cudaFreeHost(h->hctl);

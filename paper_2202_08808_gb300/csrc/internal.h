@@ -71,14 +71,13 @@ struct CJob {
     int64_t bin_cap;
     void *gd_acc;             // per-CTA dense accumulators (global), gd_w entries each
     uint32_t *gd_mask;        // per-CTA presence bits, gd_w / 32 words each
-    int32_t *gd_list;         // per-CTA list of the mask words a row touched, gd_w / 32 each
+    uint32_t *gd_sum;         // per-CTA summary: bit w set when mask word w is touched, gd_w / 1024 words each
     int64_t gd_w;
     int gd_ctas;
     int64_t m;                // columns of C
     int dense_mode;           // 1: all rows use the dense small-m kernels
     int static_mode;          // 1: C is laid out afresh by the sizing pass
     int slack_min, slack_div;
-    uint32_t *bmR;            // affected-row bitmap, cleared by the sizing pass (dynamic mode)
     int count_only;           // 1: only count each row's entries into C.len (exact sizing pass)
     int64_t rows_hint;        // upper bound on the rows to recompute (caps the grids)
     // row-bin thresholds (dspg_tuning): thread-merge limits, smallest hash
@@ -94,7 +93,6 @@ struct CJob {
     const uint16_t *est_w;    // estimator weights, bfloat16 bits (EST_PARAMS)
     int4 *est;                // rows waiting for an estimate: {i, len(A_i), max len(B_k), bound}
     int32_t *ovf;             // rows (of C) whose learned table overflowed
-    int32_t *longr;           // indices t into R of rows whose A row is long (sized by a CTA each)
     // split rows (dense mode): rows with many A entries or products are cut
     // into chunks recomputed by different CTAs and combined in global
     // accumulators (sp_rows rows at a time)
@@ -108,14 +106,15 @@ enum { SIZE_BOUND = 0, SIZE_COUNT = 1, SIZE_LEARNED = 2 };
 
 // update.cu
 void run_classify(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsigned mask, unsigned stage_bit,
-                  cudaStream_t s, int num_sms);
+                  const DetectBufs &D, bool mark_rows, bool mark_cols, cudaStream_t s, int num_sms);
 void run_merge_copy(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsigned mask, cudaStream_t s,
                     int num_sms);
 void run_commit(const CommitJob &J, const MatView &M, int vsize, int64_t max_items, Ctl *ctl, unsigned plan_mask,
                 unsigned copy_mask, int slack_min, int slack_div, cudaStream_t s, int num_sms);
-void run_detect_entries(const int32_t *srow, const uint8_t *kind, int64_t n, bool mark_rows, bool mark_cols,
-                        const DetectBufs &D, Ctl *ctl, unsigned mask, cudaStream_t s);
 void run_detect_cols(const MatView &AT, const DetectBufs &D, Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms);
+void run_collect_rows(uint32_t *bm, int64_t words, int32_t *R, Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms);
+void run_detect_merge(const MatView &AT, const DetectBufs &D, const UpdJob &J, const MatView &M, int vsize, Ctl *ctl,
+                      unsigned mask, cudaStream_t s, int num_sms);
 void run_transpose_feed(const UpdJob &J, int32_t pad_row, int32_t *trow, int32_t *tcol, uint8_t *top, Ctl *ctl,
                         unsigned mask, cudaStream_t s);
 void run_footprint(const int32_t *row, const int32_t *col, int64_t n, int64_t nrows, int64_t ncols, bool b_is_a,
@@ -142,6 +141,8 @@ void row_features(const MatView &A, const MatView &B, const MatView &C, const in
 
 // layout.cu: building and reading slack-CSRs
 void fill_iota(int32_t *a, int64_t n, cudaStream_t s);
+void begin_batch(const InArgs *host_args, InArgs *dev_args, Ctl *ctl, cudaStream_t s);
+void end_batch(const Ctl *ctl, Ctl *host_ctl, cudaStream_t s);
 void caps_from_lens(const int32_t *len, int32_t *cap, int64_t n, int slack_min, int slack_div, cudaStream_t s);
 void lens_from_rowptr(const int64_t *rowptr, int32_t *len, int64_t n, cudaStream_t s);
 // Copy rows: dst row i gets src[src_off[i] .. +len[i]) at dst_off[i] (per index i < n, with an
@@ -152,9 +153,22 @@ void copy_rows(const int32_t *rows, int64_t n, const int64_t *src_off, const int
 void gather_rows_out(const int32_t *rows, int64_t n, const MatView &M, const int64_t *out_rowptr, int32_t *out_col,
                      void *out_val, int vsize, cudaStream_t s, int num_sms);
 // Sort each row of a gathered CSR (rowptr over n rows) by column, in place;
-// sets *bad if a row longer than 16384 entries is out of order.
-void sort_rows(const int64_t *rowptr, int64_t n, int32_t *col, void *val, int vsize, unsigned *bad, cudaStream_t s,
-               int num_sms);
+// rows longer than 16384 entries that are out of order are counted in
+// *n_listed and their indices written to listed[0, list_cap) instead, for
+// sort_listed_rows.
+void sort_rows(const int64_t *rowptr, int64_t n, int32_t *col, void *val, int vsize, unsigned *n_listed,
+               int64_t *listed, int64_t list_cap, cudaStream_t s, int num_sms);
+struct SortScratch {  // for `total` entries: keys, indices (two each), radix counts, scans, gather space
+    uint64_t *k0, *k1;
+    uint32_t *i0, *i1, *counts;
+    int64_t *scan_tmp, *scan_out;
+    int32_t *tcol;
+    void *tval;
+};
+// Sorts the listed rows (nl of them, `total` entries, pre[k] = entries before
+// listed row k, pre[nl] = total; all on the device) by column, in place.
+void sort_listed_rows(const int64_t *rowptr, const int64_t *listed, const int64_t *pre, int nl, int64_t total,
+                      int cb, int32_t *col, void *val, int vsize, const SortScratch &w, cudaStream_t s, int num_sms);
 void lens_of_rows(const int32_t *rows, int64_t n, const int32_t *len, int32_t *out, cudaStream_t s);
 void validate_rowptr(int64_t nrows, int64_t nnz, const int64_t *rowptr, unsigned *bad, cudaStream_t s);
 void validate_csr_entries(int64_t nrows, int64_t ncols, const int64_t *rowptr, const int32_t *col, const void *val,

@@ -20,6 +20,34 @@ __global__ void k_iota(int32_t *a, int64_t n) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
         a[x] = (int32_t)x;
 }
+// First and last steps of a batch.  The host keeps the batch pointers and
+// receives the control block in pinned, mapped memory; these two small
+// kernels move them (the pointers read uncached, as the host rewrites them
+// between batches), which costs less on the stream than a memset and two
+// copy-engine transfers.
+static_assert(sizeof(Ctl) % sizeof(unsigned long long) == 0, "control block in 8-byte words");
+constexpr int CTL_WORDS = (int)(sizeof(Ctl) / sizeof(unsigned long long));
+constexpr int ARG_WORDS = (int)(3 * sizeof(InArgs) / sizeof(unsigned long long));
+
+__global__ void k_begin_batch(const InArgs *host_args, InArgs *dev_args, Ctl *ctl) {
+    unsigned long long *c = (unsigned long long *)ctl;
+    for (int k = threadIdx.x; k < CTL_WORDS; k += blockDim.x) c[k] = 0ull;
+    if (threadIdx.x < ARG_WORDS)
+        ((unsigned long long *)dev_args)[threadIdx.x] = __ldcv((const unsigned long long *)host_args + threadIdx.x);
+}
+
+__global__ void k_end_batch(const Ctl *ctl, Ctl *host_ctl) {
+    const unsigned long long *c = (const unsigned long long *)ctl;
+    for (int k = threadIdx.x; k < CTL_WORDS; k += blockDim.x) ((unsigned long long *)host_ctl)[k] = c[k];
+    __threadfence_system();
+}
+
+void begin_batch(const InArgs *host_args, InArgs *dev_args, Ctl *ctl, cudaStream_t s) {
+    launch_k(k_begin_batch, 1, 128, 0, s, host_args, dev_args, ctl);
+}
+
+void end_batch(const Ctl *ctl, Ctl *host_ctl, cudaStream_t s) { launch_k(k_end_batch, 1, 128, 0, s, ctl, host_ctl); }
+
 void fill_iota(int32_t *a, int64_t n, cudaStream_t s) {
     if (n > 0) launch_k(k_iota, blocks_for(n, 256, 8192), 256, 0, s, a, n);
 }
@@ -109,7 +137,7 @@ void gather_rows_out(const int32_t *rows, int64_t n, const MatView &M, const int
 // table order); every read returns canonical rows, so the gathered rows are
 // sorted by column here.  Rows already in order are left as they are.
 constexpr int SORT_SHORT = 64;     // rows up to this length: a warp each
-constexpr int SORT_MAX = 16384;    // longer rows are written in order by their kernels
+constexpr int SORT_MAX = 16384;    // longer rows are listed and sorted together (sort_listed_rows)
 
 template <typename T>
 __global__ void k_sort_short_rows(const int64_t *rowptr, int64_t n, int32_t *col, T *val) {
@@ -147,7 +175,7 @@ __global__ void k_sort_short_rows(const int64_t *rowptr, int64_t n, int32_t *col
 
 template <typename T>
 __global__ void __launch_bounds__(512) k_sort_long_rows(const int64_t *rowptr, int64_t n, int32_t *col, T *val,
-                                                        unsigned *bad) {
+                                                        unsigned *n_listed, int64_t *listed, int64_t list_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     T *sv = (T *)smem;
     int32_t *sk = (int32_t *)(sv + SORT_MAX);
@@ -159,8 +187,11 @@ __global__ void __launch_bounds__(512) k_sort_long_rows(const int64_t *rowptr, i
         int unsorted = 0;
         for (int64_t e = tid; e + 1 < len; e += nt) unsorted |= col[lo + e] > col[lo + e + 1];
         if (!__syncthreads_or(unsorted)) continue;
-        if (len > SORT_MAX) {
-            if (tid == 0) atomicOr(bad, 1u);
+        if (len > SORT_MAX) {  // too long for shared memory: listed for sort_listed_rows
+            if (tid == 0) {
+                const unsigned k = atomicAdd(n_listed, 1u);
+                if (k < list_cap) listed[k] = x;
+            }
             continue;
         }
         int N = 128;
@@ -198,8 +229,8 @@ __global__ void __launch_bounds__(512) k_sort_long_rows(const int64_t *rowptr, i
 }
 
 template <typename T>
-static void sort_rows_t(const int64_t *rowptr, int64_t n, int32_t *col, T *val, unsigned *bad, cudaStream_t s,
-                        int num_sms) {
+static void sort_rows_t(const int64_t *rowptr, int64_t n, int32_t *col, T *val, unsigned *n_listed, int64_t *listed,
+                        int64_t list_cap, cudaStream_t s, int num_sms) {
     launch_k(k_sort_short_rows<T>, blocks_for(n * 32, 256, (int64_t)num_sms * 16), 256, 0, s, rowptr, n, col, val);
     const size_t smem = (size_t)SORT_MAX * (sizeof(T) + sizeof(int32_t));
     static bool set = false;
@@ -208,14 +239,86 @@ static void sort_rows_t(const int64_t *rowptr, int64_t n, int32_t *col, T *val, 
         set = true;
     }
     const int64_t g = std::min<int64_t>(n, (int64_t)num_sms * 2);
-    launch_k(k_sort_long_rows<T>, (unsigned)std::max<int64_t>(g, 1), 512, smem, s, rowptr, n, col, val, bad);
+    launch_k(k_sort_long_rows<T>, (unsigned)std::max<int64_t>(g, 1), 512, smem, s, rowptr, n, col, val, n_listed,
+             listed, list_cap);
 }
 
-void sort_rows(const int64_t *rowptr, int64_t n, int32_t *col, void *val, int vsize, unsigned *bad, cudaStream_t s,
-               int num_sms) {
+void sort_rows(const int64_t *rowptr, int64_t n, int32_t *col, void *val, int vsize, unsigned *n_listed,
+               int64_t *listed, int64_t list_cap, cudaStream_t s, int num_sms) {
     if (n <= 0 || !col) return;
-    if (vsize == 8) sort_rows_t<double>(rowptr, n, col, (double *)val, bad, s, num_sms);
-    else sort_rows_t<int32_t>(rowptr, n, col, (int32_t *)val, bad, s, num_sms);
+    if (vsize == 8) sort_rows_t<double>(rowptr, n, col, (double *)val, n_listed, listed, list_cap, s, num_sms);
+    else sort_rows_t<int32_t>(rowptr, n, col, (int32_t *)val, n_listed, listed, list_cap, s, num_sms);
+}
+
+// Rows too long for a CTA's shared memory, sorted all at once: the packed
+// key (list index << cb | column) of every entry of the listed rows goes
+// through the LSD radix sort with its place in the rows' concatenation,
+// then each entry is gathered into its sorted place and copied back.
+// pre[k] = entries of the listed rows before row k (pre[nl] = their total).
+__device__ __forceinline__ int list_of(const int64_t *pre, int nl, int64_t q) {
+    int lo = 0, hi = nl;  // the k with pre[k] <= q < pre[k + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= q) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_listed_keys(const int64_t *rowptr, const int64_t *listed, const int64_t *pre, int nl, int cb,
+                              const int32_t *col, uint64_t *keys, uint32_t *idx) {
+    const int64_t E = pre[nl];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E; q += (int64_t)gridDim.x * blockDim.x) {
+        const int k = list_of(pre, nl, q);
+        const int64_t p = rowptr[listed[k]] + (q - pre[k]);
+        keys[q] = ((uint64_t)k << cb) | (uint32_t)col[p];
+        idx[q] = (uint32_t)q;
+    }
+}
+
+template <typename T>
+__global__ void k_listed_gather(const int64_t *rowptr, const int64_t *listed, const int64_t *pre, int nl,
+                                const uint32_t *idx, const int32_t *col, const T *val, int32_t *tcol, T *tval) {
+    const int64_t E = pre[nl];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t src = idx[q];  // the same row as q: the keys sort by list index first
+        const int k = list_of(pre, nl, src);
+        const int64_t p = rowptr[listed[k]] + (src - pre[k]);
+        tcol[q] = col[p];
+        if (val) tval[q] = val[p];
+    }
+}
+
+template <typename T>
+__global__ void k_listed_back(const int64_t *rowptr, const int64_t *listed, const int64_t *pre, int nl,
+                              const int32_t *tcol, const T *tval, int32_t *col, T *val) {
+    const int64_t E = pre[nl];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E; q += (int64_t)gridDim.x * blockDim.x) {
+        const int k = list_of(pre, nl, q);
+        const int64_t p = rowptr[listed[k]] + (q - pre[k]);
+        col[p] = tcol[q];
+        if (val) val[p] = tval[q];
+    }
+}
+
+void sort_listed_rows(const int64_t *rowptr, const int64_t *listed, const int64_t *pre, int nl, int64_t total,
+                      int cb, int32_t *col, void *val, int vsize, const SortScratch &w, cudaStream_t s, int num_sms) {
+    if (nl <= 0 || total <= 0) return;
+    const unsigned g = blocks_for(total, 256, (int64_t)num_sms * 8);
+    launch_k(k_listed_keys, g, 256, 0, s, rowptr, listed, pre, nl, cb, col, w.k0, w.i0);
+    bool alt = false;
+    radix_sort_pairs(w.k0, w.i0, w.k1, w.i1, total, bits_for(nl) + cb, w.counts, w.scan_tmp, w.scan_out, s, &alt);
+    const uint32_t *idx = alt ? w.i1 : w.i0;
+    if (vsize == 8) {
+        launch_k(k_listed_gather<double>, g, 256, 0, s, rowptr, listed, pre, nl, idx, col, (const double *)val, w.tcol,
+                 (double *)w.tval);
+        launch_k(k_listed_back<double>, g, 256, 0, s, rowptr, listed, pre, nl, (const int32_t *)w.tcol,
+                 (const double *)w.tval, col, (double *)val);
+    } else {
+        launch_k(k_listed_gather<int32_t>, g, 256, 0, s, rowptr, listed, pre, nl, idx, col, (const int32_t *)val,
+                 w.tcol, (int32_t *)w.tval);
+        launch_k(k_listed_back<int32_t>, g, 256, 0, s, rowptr, listed, pre, nl, (const int32_t *)w.tcol,
+                 (const int32_t *)w.tval, col, (int32_t *)val);
+    }
 }
 
 // Canonical-CSR check: rowptr[0] = 0 and non-decreasing, rowptr[n] = nnz,

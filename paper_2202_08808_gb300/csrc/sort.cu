@@ -19,7 +19,11 @@
 // with equal digits, the rank inside the group is a popcount, and a per-warp
 // shared-memory counter per digit carries ranks across rounds.  Per-digit
 // prefixes over warps (in warp order) then give each entry its position.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace dspg {
 
@@ -51,124 +55,192 @@ __device__ __forceinline__ void write_sorted(SortOut out, int64_t s, uint64_t ke
     out.op[s] = dead ? OP_DEAD : op[idx];
 }
 
-// ---------------------------------------------------- tile-sort path
+// ---------------------------------------------------- cluster-sort path
 //
-// Batches up to TS_TILE * TS_MAXT entries whose packed word
-// (key << ib | arrival index) fits 64 bits: each CTA sorts one tile of
-// TS_TILE words in shared memory with a bitonic network (the words are
-// distinct, so no stability is needed), and one merge kernel places every
-// word at its global rank = its rank in its own tile + the number of smaller
-// words in each other tile (binary searches in a shared-memory copy of all
-// tiles).  An entry is dead when a word with the same key and a later index
-// exists.  A single tile finishes (de-duplicates and gathers) in the sort
-// kernel itself.
+// Batches up to CS_TILE * CS_MAXT entries whose packed word
+// (key << ib | arrival index) fits 64 bits are sorted by one launch: a
+// thread-block cluster with a CTA per tile of CS_TILE words.  Each CTA sorts
+// its tile with a bitonic network held in registers (CS_EPT consecutive
+// words per thread: strides below CS_EPT inside a thread, strides up to a
+// warp's span by shuffles, longer ones through shared memory; the words are
+// distinct, so no stability is needed).  The CTAs then copy each other's
+// sorted tiles through distributed shared memory, and every word's global
+// rank is its rank in its own tile plus the number of smaller words in each
+// other tile (a thread's words are consecutive, so each search starts where
+// the previous one ended).  A word is dead when a word with the same key and
+// a later index exists: the next word of its own tile or, in another tile,
+// the first word above it.
 
-constexpr int TS_NT = 256;
-constexpr int TS_TILE = 1024;
-constexpr int TS_MAXT = 16;
-constexpr size_t TS_SMEM = TS_TILE * sizeof(uint64_t);
-constexpr size_t TM_SMEM = (size_t)TS_TILE * TS_MAXT * sizeof(uint64_t);
+constexpr int CS_NT = 1024;
+constexpr int CS_EPT = 2;
+constexpr int CS_TILE = CS_NT * CS_EPT;
+constexpr int CS_MAXT = 8;  // the portable cluster size
 
-int64_t sort_small_max() { return (int64_t)TS_TILE * TS_MAXT; }
+int64_t sort_small_max() { return (int64_t)CS_TILE * CS_MAXT; }
 
-__global__ void __launch_bounds__(TS_NT)
-k_tile_sort(const InArgs *in, int n, int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out, Ctl *ctl,
-            unsigned skip_mask, int cb, int ib, uint64_t *words_out) {
-    extern __shared__ uint64_t sm[];
-    if (failed(ctl, skip_mask)) return;
-    const int32_t *row = in->row, *col = in->col;
-    const void *val = in->val;
-    const uint8_t *op = in->op;
-    const int tid = threadIdx.x;
-    const int lo = blockIdx.x * TS_TILE;
-    const int cnt = min(TS_TILE, n - lo);
-    int N = 64;
-    while (N < cnt) N <<= 1;
-    for (int i = tid; i < N; i += TS_NT) {
-        uint64_t w = ~uint64_t(0);  // padding sorts last
-        if (i < cnt) {
-            const int gi = lo + i;
-            const int32_t r = row[gi], c = col[gi];
-            const uint8_t o = op[gi];
-            const bool ok = entry_ok(r, c, o, val, gi, nrows, ncols, sr, check_values);
-            if (!ok) set_status(ctl, ST_INVALID);
-            const uint64_t key = ok ? (((uint64_t)(uint32_t)r << cb) | (uint32_t)c) : 0;
-            w = (key << ib) | (uint64_t)gi;
-        }
-        sm[i] = w;
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < b ? b : a; }
+
+// number of words of t[lo, hi) below x (t sorted)
+__device__ __forceinline__ int count_below(const uint64_t *t, int lo, int hi, uint64_t x) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (t[mid] < x) lo = mid + 1; else hi = mid;
     }
-    __syncthreads();
-    for (int size = 2; size <= N; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int x = tid; x < N / 2; x += TS_NT) {
-                const int a = 2 * x - (x & (stride - 1));
-                const int b = a + stride;
-                const uint64_t wa = sm[a], wb = sm[b];
-                if ((wa > wb) == ((a & size) == 0)) {
-                    sm[a] = wb;
-                    sm[b] = wa;
+    return lo;
+}
+
+// Compare-exchange of x (at position i) with its partner y at distance
+// stride in a bitonic merge of size `size`: the lower position keeps the
+// smaller word when the run ascends.
+__device__ __forceinline__ uint64_t bitonic_keep(uint64_t x, uint64_t y, int i, int stride, int size) {
+    const bool keep_min = ((i & stride) == 0) == ((i & size) == 0);
+    return keep_min ? umin64(x, y) : umax64(x, y);
+}
+
+// Steps of distance 4, 2, 1 of a merge of size >= 8: inside the thread, in
+// one direction (asc) for all of its words.
+__device__ __forceinline__ void bitonic_in_thread(uint64_t (&x)[CS_EPT], bool asc) {
+#pragma unroll
+    for (int stride = CS_EPT / 2; stride > 0; stride >>= 1)
+#pragma unroll
+        for (int e = 0; e < CS_EPT; e++)
+            if ((e & stride) == 0) {
+                const uint64_t a = x[e], b = x[e | stride];
+                x[e] = asc ? umin64(a, b) : umax64(a, b);
+                x[e | stride] = asc ? umax64(a, b) : umin64(a, b);
+            }
+}
+
+// Bitonic sort of the tile, word e of thread tid at position tid * CS_EPT + e.
+// Merges up to CS_EPT words run inside the thread (unrolled); the larger ones
+// are loops whose steps reach the partner by shuffle (within a warp's span)
+// or through shared memory, so the code stays small.
+__device__ __forceinline__ void bitonic_sort_tile(uint64_t (&x)[CS_EPT], uint64_t *own, int tid) {
+#pragma unroll
+    for (int size = 2; size <= CS_EPT; size <<= 1)
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1)
+#pragma unroll
+            for (int e = 0; e < CS_EPT; e++)
+                if ((e & stride) == 0) {
+                    const int i = tid * CS_EPT + e;
+                    const uint64_t a = x[e], b = x[e | stride];
+                    const bool asc = (i & size) == 0;
+                    x[e] = asc ? umin64(a, b) : umax64(a, b);
+                    x[e | stride] = asc ? umax64(a, b) : umin64(a, b);
+                }
+#pragma unroll 1
+    for (int size = 2 * CS_EPT; size <= CS_TILE; size <<= 1) {
+#pragma unroll 1
+        for (int stride = size >> 1; stride >= CS_EPT; stride >>= 1) {
+            if (stride >= CS_EPT * 32) {  // partner in another warp
+#pragma unroll
+                for (int e = 0; e < CS_EPT; e++) own[tid * CS_EPT + e] = x[e];
+                __syncthreads();
+#pragma unroll
+                for (int e = 0; e < CS_EPT; e++) {
+                    const int i = tid * CS_EPT + e;
+                    x[e] = bitonic_keep(x[e], own[i ^ stride], i, stride, size);
+                }
+                __syncthreads();
+            } else {  // partner in another lane
+                const int lm = stride / CS_EPT;
+#pragma unroll
+                for (int e = 0; e < CS_EPT; e++) {
+                    const uint64_t y = __shfl_xor_sync(0xffffffffu, (unsigned long long)x[e], lm);
+                    x[e] = bitonic_keep(x[e], y, tid * CS_EPT + e, stride, size);
                 }
             }
-            __syncthreads();
         }
+        bitonic_in_thread(x, ((tid * CS_EPT) & size) == 0);
     }
-    if (gridDim.x == 1) {
-        const uint64_t imask = (uint64_t(1) << ib) - 1;
-        for (int s = tid; s < cnt; s += TS_NT) {
-            const uint64_t x = sm[s];
-            const uint64_t key = x >> ib;
-            const bool dead = (s + 1 < cnt) && ((sm[s + 1] >> ib) == key);
-            write_sorted(out, s, key, x & imask, dead, cb, val, op, sr);
+}
+
+__global__ void __launch_bounds__(CS_NT)
+k_cluster_sort(const InArgs *in, int n, int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out,
+               Ctl *ctl, unsigned skip_mask, int cb, int ib) {
+    extern __shared__ uint64_t tiles[];  // slot u: the sorted tile of CTA u
+    cg::cluster_group cl = cg::this_cluster();
+    // no early return: every CTA of the cluster must reach both cluster barriers
+    const bool skip = failed(ctl, skip_mask);
+    const int tid = threadIdx.x;
+    const int me = blockIdx.x, nt = gridDim.x;
+    const int lo = me * CS_TILE;
+    const int cnt = min(CS_TILE, n - lo);
+    uint64_t *own = tiles + (size_t)me * CS_TILE;
+    uint64_t x[CS_EPT];
+    if (!skip) {
+        const int32_t *row = in->row, *col = in->col;
+        const void *val = in->val;
+        const uint8_t *op = in->op;
+#pragma unroll
+        for (int e = 0; e < CS_EPT; e++) {
+            const int i = tid * CS_EPT + e;
+            uint64_t w = ~uint64_t(0);  // padding sorts last
+            if (i < cnt) {
+                const int gi = lo + i;
+                const int32_t r = row[gi], c = col[gi];
+                const uint8_t o = op[gi];
+                const bool ok = entry_ok(r, c, o, val, gi, nrows, ncols, sr, check_values);
+                if (!ok) set_status(ctl, ST_INVALID);
+                const uint64_t key = ok ? (((uint64_t)(uint32_t)r << cb) | (uint32_t)c) : 0;
+                w = (key << ib) | (uint64_t)gi;
+            }
+            x[e] = w;
         }
     } else {
-        for (int s = tid; s < cnt; s += TS_NT) words_out[lo + s] = sm[s];
+#pragma unroll
+        for (int e = 0; e < CS_EPT; e++) x[e] = ~uint64_t(0);
     }
-}
-
-__device__ __forceinline__ int count_less(const uint64_t *a, int n, uint64_t x) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    // bitonic sort of the tile: position of x[e] is tid * CS_EPT + e
+    bitonic_sort_tile(x, own, tid);
+#pragma unroll
+    for (int e = 0; e < CS_EPT; e++) own[tid * CS_EPT + e] = x[e];
+    cl.sync();
+    // the other tiles into this CTA's shared memory (16-byte loads)
+    for (int u = 0; u < nt; u++) {
+        if (u == me) continue;
+        const uint4 *src = (const uint4 *)cl.map_shared_rank(tiles + (size_t)u * CS_TILE, u);
+        uint4 *dst = (uint4 *)(tiles + (size_t)u * CS_TILE);
+        for (int k = tid; k < CS_TILE / 2; k += CS_NT) dst[k] = src[k];
     }
-    return lo;
-}
-
-__device__ __forceinline__ int count_le(const uint64_t *a, int n, uint64_t x) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] <= x) lo = mid + 1; else hi = mid;
+    cl.sync();  // no CTA leaves while another still reads its tile
+    if (skip) return;
+    const uint64_t imask = (uint64_t(1) << ib) - 1;
+    int rank[CS_EPT];
+    bool dead[CS_EPT];
+    const int nv = max(0, min(CS_EPT, cnt - tid * CS_EPT));  // this thread's real words
+#pragma unroll
+    for (int e = 0; e < CS_EPT; e++) {
+        rank[e] = tid * CS_EPT + e;
+        const int nx = tid * CS_EPT + e + 1;
+        dead[e] = nx < cnt && ((own[nx] >> ib) == (x[e] >> ib));
     }
-    return lo;
-}
-
-__global__ void __launch_bounds__(1024)
-k_tile_merge(const uint64_t *words, int n, int ib, int cb, const InArgs *in, int sr, SortOut out, const Ctl *ctl,
-             unsigned skip_mask) {
-    extern __shared__ uint64_t sw[];
-    if (failed(ctl, skip_mask)) return;
+    if (nv > 0)
+        for (int u = 0; u < nt; u++) {
+            if (u == me) continue;
+            const uint64_t *t = tiles + (size_t)u * CS_TILE;
+            const int cu = min(CS_TILE, n - u * CS_TILE);
+            int p = count_below(t, 0, cu, x[0]);
+#pragma unroll
+            for (int e = 0; e < CS_EPT; e++) {
+                const uint64_t xe = x[e];  // padding words (e >= nv) leave p where it is
+                const bool real = e < nv;
+                // a few steps forward, then a search over the rest
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if (real && p < cu && t[p] < xe) p++;
+                if (real && p < cu && t[p] < xe) p = count_below(t, p, cu, xe);
+                rank[e] += p;
+                dead[e] |= real && p < cu && ((t[p] >> ib) == (xe >> ib));
+            }
+        }
     const void *val = in->val;
     const uint8_t *op = in->op;
-    for (int x = threadIdx.x; x < n; x += blockDim.x) sw[x] = words[x];
-    __syncthreads();
-    const int ntiles = (n + TS_TILE - 1) / TS_TILE;
-    const uint64_t imask = (uint64_t(1) << ib) - 1;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const int t = e / TS_TILE;
-        const uint64_t w = sw[e];
-        const uint64_t key = w >> ib;
-        int rank = e - t * TS_TILE;
-        int le = 0;  // words with a key <= key
-        for (int u = 0; u < ntiles; u++) {
-            const int ulo = u * TS_TILE;
-            const int ucnt = min(TS_TILE, n - ulo);
-            if (u != t) rank += count_less(sw + ulo, ucnt, w);
-            le += count_le(sw + ulo, ucnt, w | imask);
-        }
-        const bool dead = rank != le - 1;
-        write_sorted(out, rank, key, w & imask, dead, cb, val, op, sr);
-    }
+#pragma unroll
+    for (int e = 0; e < CS_EPT; e++)
+        if (e < nv) write_sorted(out, rank[e], x[e] >> ib, x[e] & imask, dead[e], cb, val, op, sr);
 }
 
 // ------------------------------------------------------- multi-CTA path
@@ -295,19 +367,30 @@ void sort_updates(const InArgs *in, int64_t n, int64_t nrows, int64_t ncols, int
     if (n <= 0) return;
     const int cb = bits_for(ncols), rb = bits_for(nrows), ib = bits_for(n);
     const int kb = cb + rb;
-    if (n <= (int64_t)TS_TILE * TS_MAXT && kb + ib <= 64) {
+    if (n <= (int64_t)CS_TILE * CS_MAXT && kb + ib <= 64) {
+        const int tiles = (int)((n + CS_TILE - 1) / CS_TILE);
+        const size_t smem = (size_t)tiles * CS_TILE * sizeof(uint64_t);
         static bool attr_set = false;
         if (!attr_set) {
-            cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS_SMEM);
-            cudaFuncSetAttribute(k_tile_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TM_SMEM);
+            cudaFuncSetAttribute(k_cluster_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)CS_MAXT * CS_TILE * sizeof(uint64_t)));
             attr_set = true;
         }
-        const int tiles = (int)((n + TS_TILE - 1) / TS_TILE);
-        launch_k(k_tile_sort, tiles, TS_NT, TS_SMEM, s, in, (int)n, nrows, ncols, sr, check_values, out, ctl, skip_mask,
-                 cb, ib, tmp.k0);
-        if (tiles > 1)
-            launch_k(k_tile_merge, (unsigned)((n + 1023) / 1024), 1024, (size_t)n * sizeof(uint64_t), s,
-                     (const uint64_t *)tmp.k0, (int)n, ib, cb, in, sr, out, (const Ctl *)ctl, skip_mask);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)tiles);
+        cfg.blockDim = dim3(CS_NT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)tiles;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        // a failed launch stays in the runtime's last error, which the caller checks
+        cudaLaunchKernelEx(&cfg, k_cluster_sort, in, (int)n, nrows, ncols, sr, check_values, out, ctl, skip_mask, cb, ib);
+        __atomic_fetch_add(&launch_counter(), 1ull, __ATOMIC_RELAXED);
         return;
     }
     unsigned nblk = (unsigned)((n + 255) / 256);

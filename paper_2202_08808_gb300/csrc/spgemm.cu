@@ -30,21 +30,28 @@
 // (order-free, bit-exact).
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "estimator.cuh"
 #include "internal.h"
 
 namespace dspg {
 
+namespace cg = cooperative_groups;
+
 template <int SR>
 struct Sr;
-// mul and add round each operation separately (no fused multiply-add), so a
-// row folded in ascending k gives exactly the textbook result.
+// mul and add round each operation separately; fma(a, b, c) = c (+) a (x) b
+// in one step, which for (+,.) is a fused multiply-add: one rounding instead
+// of two, and one instruction of the double-precision pipe (whose rate on
+// this GPU is 1/64 of single precision) instead of two.
 template <>
 struct Sr<SR_PT> {
     using T = double;
     __device__ static T zero() { return 0.0; }
     __device__ static T mul(T a, T b) { return __dmul_rn(a, b); }
     __device__ static T add(T a, T b) { return __dadd_rn(a, b); }
+    __device__ static T fma(T a, T b, T c) { return __fma_rn(a, b, c); }
     __device__ static void acc(T *p, T v) { atomicAdd(p, v); }
 };
 template <>
@@ -53,6 +60,7 @@ struct Sr<SR_MP> {
     __device__ static T zero() { return MP_INF; }
     __device__ static T mul(T a, T b) { return a + b; }
     __device__ static T add(T a, T b) { return a < b ? a : b; }
+    __device__ static T fma(T a, T b, T c) { return add(c, mul(a, b)); }
     __device__ static void acc(T *p, T v) { atomicMin(p, v); }
 };
 
@@ -61,6 +69,8 @@ enum {
     BIN_C2048, BIN_C4096, BIN_C8192, BIN_C16384,
     BIN_GD,
     BIN_WDENSE, BIN_CDENSE, BIN_DSPLIT,
+    BIN_T64,  // thread merge, rows whose bound is above the tuned staging bound (up to MERGE_UB)
+    BIN_K2, BIN_K4, BIN_K8, BIN_K8L,  // cluster tables: 2, 4, 8 CTAs x 8192 slots, 8 x 16384
     BIN_COUNT
 };
 static_assert(BIN_COUNT <= NBINS, "bin counters");
@@ -72,10 +82,22 @@ __device__ __forceinline__ long long atomic_add_ll2(long long *p, long long v) {
 // ------------------------------------------------------------- sizing
 
 constexpr int MERGE_K = 8;      // A rows up to this length can be merged by one thread
-constexpr int MERGE_UB = 64;    // ... when their product bound is at most this
+constexpr int MERGE_UB = 64;    // ... when their product bound is at most this (the tuning
+                                // may lower it: the kernel stages the tuned bound per thread)
 
 // The hash (or global dense) bin for a table of at least `need` slots under
 // the job's thresholds.
+// A table or staging area too small for a row although the sizing bound it:
+// reported as ST_TIMEOUT, with the bin and a row for the error message.
+__device__ __forceinline__ void report_overflow(Ctl *ctl, int bin, int32_t i, const MatView &A, const MatView &B) {
+    long long ub = 0;
+    for (int a = 0; a < A.len[i]; a++) ub += B.len[A.col[A.off[i] + a]];
+    ctl->timeout_bin = bin + 1;
+    ctl->timeout_row = i;
+    ctl->timeout_ub = ub;
+    set_status(ctl, ST_TIMEOUT);
+}
+
 __device__ __forceinline__ int pick_table_bin(long long need, const CJob &J) {
     need <<= J.table_shift;
     if (need <= 32 && J.lanes_min <= 8) return BIN_G8;
@@ -92,6 +114,10 @@ __device__ __forceinline__ int pick_table_bin(long long need, const CJob &J) {
         if (need <= 8192) return BIN_C8192;
         return BIN_C16384;
     }
+    if (need <= 2 * 8192) return BIN_K2;
+    if (need <= 4 * 8192) return BIN_K4;
+    if (need <= 8 * 8192) return BIN_K8;
+    if (need <= 8 * 16384) return BIN_K8L;
     return BIN_GD;
 }
 
@@ -103,9 +129,16 @@ __device__ __forceinline__ int pick_table_bin(long long need, const CJob &J) {
 // (each gathers a B row) and its products, not the capped bound: a warp for
 // short rows, else a CTA (rows with very many products are split later).
 constexpr int DENSE_WARP_A = 64;
+// Rows merged by one thread: at most tm_k A entries and at most MERGE_UB
+// products (the uncapped bound: it is what the thread stages), in the first
+// kernel while the bound is within the tuned staging size tm_ub.
+__device__ __forceinline__ bool merge_row(int alen, long long ub, const CJob &J) {
+    return alen <= J.tm_k && ub <= MERGE_UB;
+}
+
 __device__ __forceinline__ int pick_bin(long long ubc, int alen, const CJob &J, long long table_need,
                                         long long ub) {
-    if (alen <= J.tm_k && ubc <= J.tm_ub) return BIN_T8;
+    if (merge_row(alen, ub, J)) return ub <= J.tm_ub ? BIN_T8 : BIN_T64;
     if (J.dense_mode) return (alen <= DENSE_WARP_A && ub <= 4096) ? BIN_WDENSE : BIN_CDENSE;
     return pick_table_bin(table_need, J);
 }
@@ -123,7 +156,7 @@ __device__ __forceinline__ void append_bins(const CJob &J, Ctl *ctl, int b, int3
 }
 
 constexpr int SIZE_SHORT = 64;   // A rows up to this length are sized by one thread,
-constexpr int SIZE_LONG = 512;   // up to this by a warp, longer ones by a CTA (k_size_long)
+constexpr int SIZE_LONG = 512;   // up to this by a warp, longer ones by the whole block
 constexpr long long SPLIT_MIN = 8192;  // dense mode: rows with more products, or with more than
 constexpr int SPLIT_A = 256;           // SPLIT_A A entries, are split in chunks (k_num_dsplit)
 constexpr int SPLIT_CHUNK = 2048;      // A entries per work item of a split row
@@ -146,30 +179,106 @@ __device__ __forceinline__ void push_est(const CJob &J, Ctl *ctl, int32_t i, int
     J.est[atomic_add_ll2(&ctl->n_est, 1)] = e;
 }
 
+// A row of R with more than SIZE_LONG A entries, sized by the whole block:
+// the B-row lengths summed with several loads in flight per thread, then
+// the row is binned as in k_size_bins (by thread 0).  t indexes R.
+__device__ __forceinline__ void size_long_row(const MatView &A, const MatView &B, const MatView &C, const CJob &J,
+                                              Ctl *ctl, long long t, long long *s_sum, long long *s_max) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    const int32_t i = __ldcg(J.R + t);
+    const int64_t aoff = __ldcg(A.off + i);
+    const int alen = __ldcg(A.len + i);
+    long long sm = 0, mx = 0;
+    for (int a0 = 0; a0 < alen; a0 += (int)blockDim.x * 4) {
+        long long l[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int a = a0 + u * (int)blockDim.x + tid;
+            l[u] = a < alen ? (long long)__ldcg(B.len + __ldcg(A.col + aoff + a)) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            sm += l[u];
+            mx = l[u] > mx ? l[u] : mx;
+        }
+    }
+    sm = warp_sum<long long>(sm);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const long long y = __shfl_xor_sync(0xffffffffu, mx, d);
+        mx = y > mx ? y : mx;
+    }
+    if (lane == 0) {
+        s_sum[w] = sm;
+        s_max[w] = mx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long ub = 0, bmax = 0;
+        for (int k = 0; k < nw; k++) {
+            ub += s_sum[k];
+            bmax = s_max[k] > bmax ? s_max[k] : bmax;
+        }
+        const long long ubc = ub < J.m ? ub : J.m;
+        if (J.static_mode) {
+            const int32_t c = slack_cap(ubc, J.slack_min, J.slack_div);
+            const long long d = atomic_add_ll2(C.top, c);
+            C.off[i] = d;
+            C.cap[i] = c;
+            C.len[i] = 0;
+            if (d + c > C.arena_cap) set_status(ctl, ST_C_ARENA);
+        } else if (J.sizing != SIZE_COUNT) {
+            if (ub == 0) C.len[i] = 0;
+        }
+        const bool t8 = merge_row(alen, ub, J);
+        if (wants_est(J, ub, ubc, t8)) {
+            push_est(J, ctl, i, alen, bmax, ub);
+        } else if (ub > 0) {
+            const long long need = J.sizing == SIZE_COUNT ? (long long)C.len[i] : ubc;
+            const int b = pick_bin(ubc, alen, J, need, ub);
+            if (!(b == BIN_CDENSE && (ub > SPLIT_MIN || alen > SPLIT_A) && claim_split(J, ctl, i)))
+                J.bins[(int64_t)b * J.bin_cap + atomic_add_ll2(&ctl->bin_count[b], 1)] = i;
+        }
+        if (J.sizing != SIZE_COUNT) {
+            atomic_add_ll2(&ctl->products, ub);
+            atomic_add_ll2(&ctl->a_entries, alen);
+        }
+    }
+    __syncthreads();
+}
+
 // One thread per row of R sums the B-row lengths of its A entries (rows
 // longer than SIZE_SHORT are summed by the whole warp afterwards, rows
-// longer than SIZE_LONG by a CTA in k_size_long); then the warp hands out
+// longer than SIZE_LONG by the whole block at the end of its round); then the warp hands out
 // bin slots (and, for the static product, the row's place in a fresh C)
 // with one atomic per counter.  With SIZE_COUNT the tables are sized by
 // C.len (an exact count from a count_only pass); with SIZE_LEARNED rows
 // whose bound exceeds est_min go to the estimate list instead of a bin.
-__global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask) {
+__global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask) {
+    __shared__ long long s_long[256];  // this block's rows (indices into R) with long A rows
+    __shared__ long long s_sum[8], s_max[8];
+    __shared__ int s_nlong;
     if (failed(ctl, mask)) return;
     const long long nR = ctl->n_affected;
     const int lane = threadIdx.x & 31;
     long long prod_acc = 0, a_acc = 0;
+    if (threadIdx.x == 0) s_nlong = 0;
+    __syncthreads();
     for (long long base = (long long)blockIdx.x * blockDim.x; base < nR; base += (long long)gridDim.x * blockDim.x) {
         const long long t = base + threadIdx.x;
         bool valid = t < nR;
-        const int32_t i = valid ? J.R[t] : 0;
-        const int64_t aoff = valid ? A.off[i] : 0;
-        const int alen = valid ? A.len[i] : 0;
+        // the row structure was just rewritten by the commit: read through L2
+        // (ld.global.cg), not a possibly stale L1 line
+        const int32_t i = valid ? __ldcg(J.R + t) : 0;
+        const int64_t aoff = valid ? __ldcg(A.off + i) : 0;
+        const int alen = valid ? __ldcg(A.len + i) : 0;
         // dense accumulators: a row with more than SPLIT_A A entries is split,
         // whatever its product count, so it needs no sum (its products are
         // counted by the split kernel); its bound for the static layout is m
         const bool direct = valid && J.dense_mode && alen > SPLIT_A && claim_split(J, ctl, i);
-        if (valid && !direct && alen > SIZE_LONG) {  // a CTA sizes this row later
-            J.longr[atomic_add_ll2(&ctl->n_long, 1)] = (int32_t)t;
+        if (valid && !direct && alen > SIZE_LONG) {  // the whole block sizes this row below
+            s_long[atomicAdd(&s_nlong, 1)] = t;
             valid = false;
         }
         const bool lng = alen > SIZE_SHORT && !direct;
@@ -177,7 +286,7 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
         if (valid && !lng && !direct)
 #pragma unroll 8
             for (int a = 0; a < alen; a++) {
-                const long long l = B.len[A.col[aoff + a]];
+                const long long l = __ldcg(B.len + __ldcg(A.col + aoff + a));
                 ub += l;
                 bmax = l > bmax ? l : bmax;
             }
@@ -189,7 +298,7 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
             const int l = __shfl_sync(0xffffffffu, alen, src);
             long long s = 0, mx = 0;
             for (int a = lane; a < l; a += 32) {
-                const long long x = B.len[A.col[o + a]];
+                const long long x = __ldcg(B.len + __ldcg(A.col + o + a));
                 s += x;
                 mx = x > mx ? x : mx;
             }
@@ -215,10 +324,9 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
                 if (d + c > C.arena_cap) set_status(ctl, ST_C_ARENA);
             }
         } else if (valid && J.sizing != SIZE_COUNT) {
-            J.bmR[i >> 5] = 0u;  // the detection marks are not needed any more
             if (ub == 0) C.len[i] = 0;  // no products: the row becomes empty
         }
-        const bool t8 = alen <= J.tm_k && ubc <= J.tm_ub;
+        const bool t8 = merge_row(alen, ub, J);
         const bool to_est = valid && wants_est(J, ub, ubc, t8);
         long long need = ubc;
         if (J.sizing == SIZE_COUNT && valid) need = C.len[i];
@@ -230,85 +338,18 @@ __global__ void k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, u
             if (!direct) prod_acc += ub;
             a_acc += alen;
         }
+        __syncthreads();
+        const int nl = s_nlong;
+        for (int k = 0; k < nl; k++) size_long_row(A, B, C, J, ctl, s_long[k], s_sum, s_max);
+        __syncthreads();
+        if (threadIdx.x == 0) s_nlong = 0;
+        __syncthreads();
     }
     prod_acc = warp_sum<long long>(prod_acc);
     a_acc = warp_sum<long long>(a_acc);
     if (lane == 0) {
         if (prod_acc) atomic_add_ll2(&ctl->products, prod_acc);
         if (a_acc) atomic_add_ll2(&ctl->a_entries, a_acc);
-    }
-}
-
-// Rows of R with more than SIZE_LONG A entries: a CTA each sums the B-row
-// lengths (several loads in flight per thread) and bins the row as above.
-__global__ void __launch_bounds__(256) k_size_long(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask) {
-    __shared__ long long s_sum[8], s_max[8];
-    if (failed(ctl, mask)) return;
-    const long long cnt = ctl->n_long;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
-        const long long t = J.longr[it];
-        const int32_t i = J.R[t];
-        const int64_t aoff = A.off[i];
-        const int alen = A.len[i];
-        long long s = 0, mx = 0;
-        for (int a0 = 0; a0 < alen; a0 += 256 * 4) {
-            long long l[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int a = a0 + u * 256 + tid;
-                l[u] = a < alen ? (long long)B.len[__ldg(A.col + aoff + a)] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                s += l[u];
-                mx = l[u] > mx ? l[u] : mx;
-            }
-        }
-        s = warp_sum<long long>(s);
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            const long long y = __shfl_xor_sync(0xffffffffu, mx, d);
-            mx = y > mx ? y : mx;
-        }
-        if (lane == 0) {
-            s_sum[w] = s;
-            s_max[w] = mx;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            long long ub = 0, bmax = 0;
-            for (int k = 0; k < 8; k++) {
-                ub += s_sum[k];
-                bmax = s_max[k] > bmax ? s_max[k] : bmax;
-            }
-            const long long ubc = ub < J.m ? ub : J.m;
-            if (J.static_mode) {
-                const int32_t c = slack_cap(ubc, J.slack_min, J.slack_div);
-                const long long d = atomic_add_ll2(C.top, c);
-                C.off[i] = d;
-                C.cap[i] = c;
-                C.len[i] = 0;
-                if (d + c > C.arena_cap) set_status(ctl, ST_C_ARENA);
-            } else if (J.sizing != SIZE_COUNT) {
-                J.bmR[i >> 5] = 0u;
-                if (ub == 0) C.len[i] = 0;
-            }
-            const bool t8 = alen <= J.tm_k && ubc <= J.tm_ub;
-            if (wants_est(J, ub, ubc, t8)) {
-                push_est(J, ctl, i, alen, bmax, ub);
-            } else if (ub > 0) {
-                const long long need = J.sizing == SIZE_COUNT ? (long long)C.len[i] : ubc;
-                const int b = pick_bin(ubc, alen, J, need, ub);
-                if (!(b == BIN_CDENSE && (ub > SPLIT_MIN || alen > SPLIT_A) && claim_split(J, ctl, i)))
-                    J.bins[(int64_t)b * J.bin_cap + atomic_add_ll2(&ctl->bin_count[b], 1)] = i;
-            }
-            if (J.sizing != SIZE_COUNT) {
-                atomic_add_ll2(&ctl->products, ub);
-                atomic_add_ll2(&ctl->a_entries, alen);
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -326,7 +367,7 @@ __global__ void __launch_bounds__(128) k_est_bins(CJob J, Ctl *ctl, unsigned mas
         int b = -1;
         int32_t i = 0;
         if (q < cnt) {
-            const int4 e = J.est[q];
+            const int4 e = __ldcg(J.est + q);
             i = e.x;
             float x[EST_IN];
             est_features(x, e.y, e.w, e.z);
@@ -466,10 +507,14 @@ __device__ __forceinline__ int block_incl_scan(int v, int *incl, int *wsum) {
 }
 
 // Calls emit(j, a (x) b) for every product of row i, all threads of the
-// block sharing the work.  Must be called by the whole block.
-template <int SR, class F>
+// block sharing the work (with parts > 1: the share `part` of them, the
+// CTAs of a cluster taking one part each; with BATCH, emit(c[PU], v[PU],
+// valid[PU]) takes a round's products at once).  Must be called by the whole
+// block.
+template <int SR, bool BATCH = false, class F>
 __device__ __forceinline__ void block_products(const MatView &A, const MatView &B, int32_t i,
-                                               BlockProdSmem<typename Sr<SR>::T> sm, F emit) {
+                                               BlockProdSmem<typename Sr<SR>::T> sm, F emit, int part = 0,
+                                               int parts = 1) {
     using T = typename Sr<SR>::T;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t aoff = A.off[i];
@@ -487,7 +532,9 @@ __device__ __forceinline__ void block_products(const MatView &A, const MatView &
         }
         sm.blen[tid] = blen;
         const int total = block_incl_scan(blen, sm.incl, sm.wsum);
-        for (int base = 0; base < total; base += nt * PU) {  // PU loads per thread in flight, as above
+        // PU loads per thread in flight, as above; with parts > 1 the rounds
+        // of a chunk's products are dealt out to the parts in turn
+        for (int base = part * nt * PU; base < total; base += parts * nt * PU) {
             int64_t q[PU];
             T a[PU];
 #pragma unroll
@@ -509,9 +556,21 @@ __device__ __forceinline__ void block_products(const MatView &A, const MatView &
                     c[u] = __ldg(B.col + q[u]);
                     b[u] = __ldg(Bv + q[u]);
                 }
+            if constexpr (BATCH) {  // the round's PU products in one call (their atomics issued together)
+                T v[PU];
+                bool ok[PU];
 #pragma unroll
-            for (int u = 0; u < PU; u++)
-                if (q[u] >= 0) emit(c[u], Sr<SR>::mul(a[u], b[u]));
+                for (int u = 0; u < PU; u++) {
+                    ok[u] = q[u] >= 0;
+                    v[u] = ok[u] ? Sr<SR>::mul(a[u], b[u]) : Sr<SR>::zero();
+                    if (!ok[u]) c[u] = 0;
+                }
+                emit(c, v, ok);
+            } else {
+#pragma unroll
+                for (int u = 0; u < PU; u++)
+                    if (q[u] >= 0) emit(c[u], Sr<SR>::mul(a[u], b[u]));
+            }
         }
         __syncthreads();
     }
@@ -519,26 +578,47 @@ __device__ __forceinline__ void block_products(const MatView &A, const MatView &
 
 // ----------------------------------------------------------- hash table
 
-template <int LOG_TS, typename T, int SR>
-__device__ __forceinline__ bool hash_acc(int32_t *keys, T *vals, int32_t j, T v) {
+// Accumulates v into the slot of column j: 1 when this call claimed the
+// slot (a new column of the row), 0 when the column was there, -1 when the
+// table is full.  Probing is triangular (steps 1, 2, 3, ...), which visits
+// every slot of a power-of-two table and, unlike linear probing, does not
+// build long runs of occupied slots as the table fills.
+// With CAS_FIRST every probe is a compare-and-swap (one round trip per
+// probe instead of a load and then a swap: for tables in another CTA's
+// shared memory).  probe0 > 0 continues a probe sequence from that step.
+template <int LOG_TS, typename T, int SR, bool CAS_FIRST = false>
+__device__ __forceinline__ int hash_acc_from(int32_t *keys, T *vals, uint32_t h, int32_t j, T v, int probe0 = 0) {
     constexpr int TS = 1 << LOG_TS;
-    uint32_t h = ((uint32_t)j * 2654435761u) >> (32 - LOG_TS);
-    for (int probe = 0; probe < TS; probe++) {
-        const int32_t k = ((volatile int32_t *)keys)[h];
-        if (k == j) {
-            Sr<SR>::acc(&vals[h], v);
-            return true;
-        }
-        if (k == -1) {
+    h = (h + (uint32_t)(probe0 * (probe0 + 1) / 2)) & (TS - 1);
+    for (int probe = probe0; probe < TS; probe++) {
+        if constexpr (CAS_FIRST) {
             const int32_t old = atomicCAS(&keys[h], -1, j);
             if (old == -1 || old == j) {
                 Sr<SR>::acc(&vals[h], v);
-                return true;
+                return old == -1 ? 1 : 0;
+            }
+        } else {
+            const int32_t k = ((volatile int32_t *)keys)[h];
+            if (k == j) {
+                Sr<SR>::acc(&vals[h], v);
+                return 0;
+            }
+            if (k == -1) {
+                const int32_t old = atomicCAS(&keys[h], -1, j);
+                if (old == -1 || old == j) {
+                    Sr<SR>::acc(&vals[h], v);
+                    return old == -1 ? 1 : 0;
+                }
             }
         }
-        h = (h + 1) & (TS - 1);
+        h = (h + probe + 1) & (TS - 1);
     }
-    return false;  // table full: cannot happen when the bin bound holds
+    return -1;  // table full: cannot happen when the bin bound holds
+}
+
+template <int LOG_TS, typename T, int SR>
+__device__ __forceinline__ int hash_acc(int32_t *keys, T *vals, int32_t j, T v) {
+    return hash_acc_from<LOG_TS, T, SR>(keys, vals, ((uint32_t)j * 2654435761u) >> (32 - LOG_TS), j, v);
 }
 
 // ---------------------------------------------------- thread merge kernel
@@ -585,13 +665,10 @@ __device__ __forceinline__ int merge_rows_smem(const int32_t *scol, const typena
         for (int s = 1; s < K; s++) j = min(j, head[s]);
         if (j == 0x7fffffff) break;
         T acc = Sr<SR>::zero();
-        bool first = true;
 #pragma unroll
         for (int s = 0; s < K; s++) {
             if (head[s] == j) {
-                const T v = Sr<SR>::mul(av[s], sval[pos[s] * TM_NT]);
-                acc = first ? v : Sr<SR>::add(acc, v);
-                first = false;
+                acc = Sr<SR>::fma(av[s], sval[pos[s] * TM_NT], acc);
                 pos[s]++;
                 head[s] = pos[s] < end[s] ? scol[pos[s] * TM_NT] : 0x7fffffff;
             }
@@ -605,12 +682,13 @@ __device__ __forceinline__ int merge_rows_smem(const int32_t *scol, const typena
     return n;
 }
 
-template <int SR, int K, int UB>
+template <int SR, int K>
 __global__ void __launch_bounds__(TM_NT)
-k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
+k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin, int UB) {
     using T = typename Sr<SR>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     if (failed(ctl, mask)) return;
+    // UB: staged entries per thread (the bin's product bound)
     T *svals = (T *)smem + threadIdx.x;                              // [UB][TM_NT] values
     int32_t *scols = (int32_t *)((T *)smem + UB * TM_NT) + threadIdx.x;  // [UB][TM_NT] columns
     const T *Av = (const T *)A.val;
@@ -646,7 +724,7 @@ k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned m
             tot += blen[s];
         }
         if (tot > UB) {  // the sizing pass guarantees tot <= UB; guard the buffer anyway
-            set_status(ctl, ST_TIMEOUT);
+            report_overflow(ctl, bin, i, A, B);
             continue;
         }
 #pragma unroll
@@ -703,46 +781,58 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
     T *Cv = (T *)C.val;
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
+    // the table is cleared once here; each row's read-out clears the slots
+    // it used
+    for (int s = gl; s < TS; s += G) {
+        keys[s] = -1;
+        vals[s] = Sr<SR>::zero();
+    }
+    __syncwarp(gmask);
     for (long long it = (long long)blockIdx.x * NG + g; it < cnt; it += (long long)gridDim.x * NG) {
         const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
-        for (int s = gl; s < TS; s += G) {
-            keys[s] = -1;
-            vals[s] = Sr<SR>::zero();
-        }
-        __syncwarp(gmask);
         bool ok = true;
-        group_products<SR, G>(A, B, i, gmask, [&](int32_t j, T v) { ok &= hash_acc<LOG_TS, T, SR>(keys, vals, j, v); });
+        unsigned fresh = 0;  // slots this lane claimed: the row's length, summed over the group
+        group_products<SR, G>(A, B, i, gmask, [&](int32_t j, T v) {
+            const int r = hash_acc<LOG_TS, T, SR>(keys, vals, j, v);
+            ok &= r >= 0;
+            fresh += r > 0;
+        });
         const bool full = (__ballot_sync(gmask, !ok) & gmask) != 0u;
         if (full) {
             // a learned table too small: the row goes to the overflow list and
             // is counted and recomputed later; with a bound or exact size a
             // full table cannot happen, so it is reported as an error
+            __syncwarp(gmask);
+            for (int s = gl; s < TS; s += G) {
+                keys[s] = -1;
+                vals[s] = Sr<SR>::zero();
+            }
             if (gl == 0) {
                 if (J.sizing == SIZE_LEARNED) J.ovf[atomic_add_ll2(&ctl->n_ovf, 1)] = i;
-                else set_status(ctl, ST_TIMEOUT);
+                else report_overflow(ctl, bin, i, A, B);
             }
             __syncwarp(gmask);
             continue;
         }
         __syncwarp(gmask);
-        int n = 0;
+        const int n = (int)__reduce_add_sync(gmask, fresh);
         if constexpr (RANKED) {
+            int x0 = 0;
             for (int s0 = 0; s0 < TS; s0 += G) {
                 const int s = s0 + gl;
                 const int32_t k = keys[s];
                 const bool occ = k >= 0;
                 const unsigned bal = (__ballot_sync(gmask, occ) & gmask) >> (gw * G);
                 if (occ) {
-                    const int x = n + __popc(bal & ((1u << gl) - 1u));
+                    const int x = x0 + __popc(bal & ((1u << gl) - 1u));
                     ck[x] = k;
                     cv[x] = vals[s];
+                    keys[s] = -1;
+                    vals[s] = Sr<SR>::zero();
                 }
-                n += __popc(bal);
+                x0 += __popc(bal);
             }
             __syncwarp(gmask);
-        } else {
-            for (int s0 = 0; s0 < TS; s0 += G)
-                n += __popc((__ballot_sync(gmask, keys[s0 + gl] >= 0) & gmask) >> (gw * G));
         }
         int64_t dest = 0;
         if (gl == 0) dest = c_row_dest(C, J, ctl, i, n);
@@ -758,9 +848,9 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
                     Cv[dest + rank] = cv[e];
                 }
             }
-        } else if (dest >= 0) {
-            // straight from the table, in table order: C's rows need no column
-            // order (the reads sort them)
+        } else {
+            // straight from the table, in table order (C's rows need no column
+            // order: the reads sort them), clearing the used slots
             int x0 = 0;
             for (int s0 = 0; s0 < TS; s0 += G) {
                 const int s = s0 + gl;
@@ -768,9 +858,13 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
                 const bool occ = k >= 0;
                 const unsigned bal = (__ballot_sync(gmask, occ) & gmask) >> (gw * G);
                 if (occ) {
-                    const int x = x0 + __popc(bal & ((1u << gl) - 1u));
-                    C.col[dest + x] = k;
-                    Cv[dest + x] = vals[s];
+                    if (dest >= 0) {
+                        const int x = x0 + __popc(bal & ((1u << gl) - 1u));
+                        C.col[dest + x] = k;
+                        Cv[dest + x] = vals[s];
+                    }
+                    keys[s] = -1;
+                    vals[s] = Sr<SR>::zero();
                 }
                 x0 += __popc(bal);
             }
@@ -795,7 +889,6 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
     __shared__ int p_incl[256], p_blen[256], p_wsum[32];
     __shared__ int s_n, s_pos;
     __shared__ long long s_dest;
-    __shared__ int s_ok;
     if (failed(ctl, mask)) return;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     T *vals = (T *)smem;
@@ -804,119 +897,282 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
     BlockProdSmem<T> ps{p_boff, p_av, p_incl, p_blen, p_wsum};
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
+    // the table is cleared once here; each row's read-out clears the slots it used
+    for (int s = tid; s < TS; s += 256) {
+        keys[s] = -1;
+        vals[s] = Sr<SR>::zero();
+    }
+    if (tid == 0) s_n = 0;
+    __syncthreads();
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
         const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
-        for (int s = tid; s < TS; s += 256) {
-            keys[s] = -1;
-            vals[s] = Sr<SR>::zero();
-        }
-        if (tid == 0) {
-            s_n = 0;
-            s_pos = 0;
-            s_ok = 1;
-        }
-        __syncthreads();
         bool ok = true;
-        block_products<SR>(A, B, i, ps, [&](int32_t j, T v) { ok &= hash_acc<LOG_TS, T, SR>(keys, vals, j, v); });
-        if (!ok) s_ok = 0;
-        __syncthreads();
-        if (!s_ok) {  // table too small: see the group kernel
+        int fresh = 0;  // slots this thread claimed; their sum is the row's length
+        block_products<SR, true>(A, B, i, ps, [&](const int32_t (&c)[PU], const T (&v)[PU], const bool (&valid)[PU]) {
+            uint32_t h[PU];
+            int32_t old[PU];
+            // first probes of the round's products, all in flight at once
+#pragma unroll
+            for (int u = 0; u < PU; u++) {
+                h[u] = ((uint32_t)c[u] * 2654435761u) >> (32 - LOG_TS);
+                old[u] = valid[u] ? atomicCAS(keys + h[u], -1, c[u]) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < PU; u++) {
+                if (!valid[u]) continue;
+                if (old[u] == -1 || old[u] == c[u]) {
+                    Sr<SR>::acc(vals + h[u], v[u]);
+                    fresh += old[u] == -1;
+                    continue;
+                }
+                const int r = hash_acc_from<LOG_TS, T, SR>(keys, vals, h[u], c[u], v[u], 1);
+                ok &= r >= 0;
+                fresh += r > 0;
+            }
+        });
+        fresh = warp_sum<int>(fresh);
+        if (lane == 0 && fresh) atomicAdd(&s_n, fresh);
+        const bool full = __syncthreads_or(!ok);
+        const int n = s_n;
+        if (full) {  // table too small: see the group kernel
+            for (int s = tid; s < TS; s += 256) {
+                keys[s] = -1;
+                vals[s] = Sr<SR>::zero();
+            }
+            __syncthreads();  // every thread has read s_n
             if (tid == 0) {
+                s_n = 0;
                 if (J.sizing == SIZE_LEARNED) J.ovf[atomic_add_ll2(&ctl->n_ovf, 1)] = i;
-                else set_status(ctl, ST_TIMEOUT);
+                else report_overflow(ctl, bin, i, A, B);
             }
             __syncthreads();
             continue;
         }
-        // two passes over the table: count, then write straight to C (in
-        // table order; C's rows need no column order)
-        for (int s0 = w * 32; s0 < TS; s0 += 256) {
-            const unsigned bal = __ballot_sync(0xffffffffu, keys[s0 + lane] >= 0);
-            if (lane == 0 && bal) atomicAdd(&s_n, __popc(bal));
-        }
-        __syncthreads();
-        const int n = s_n;
         if (tid == 0) {
             s_dest = c_row_dest(C, J, ctl, i, n);
+            s_pos = 0;
             nnz_acc += n;
         }
         __syncthreads();
+        if (tid == 0) s_n = 0;  // every thread has read it
         const long long dest = s_dest;
-        if (dest >= 0) {
-            for (int s0 = w * 32; s0 < TS; s0 += 256) {
-                const int s = s0 + lane;
-                const int32_t k = keys[s];
-                const bool occ = k >= 0;
-                const unsigned bal = __ballot_sync(0xffffffffu, occ);
+        // one pass over the table: write straight to C (in table order; C's
+        // rows need no column order) and clear the used slots
+        for (int s0 = w * 32; s0 < TS; s0 += 256) {
+            const int s = s0 + lane;
+            const int32_t k = keys[s];
+            const bool occ = k >= 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, occ);
+            if (bal) {
                 int base = 0;
-                if (lane == 0 && bal) base = atomicAdd(&s_pos, __popc(bal));
+                if (lane == 0) base = atomicAdd(&s_pos, __popc(bal));
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (occ) {
-                    const int x = base + __popc(bal & lanemask_lt());
-                    C.col[dest + x] = k;
-                    Cv[dest + x] = vals[s];
+                    if (dest >= 0) {
+                        const int x = base + __popc(bal & lanemask_lt());
+                        C.col[dest + x] = k;
+                        Cv[dest + x] = vals[s];
+                    }
+                    keys[s] = -1;
+                    vals[s] = Sr<SR>::zero();
                 }
             }
-            if (tid == 0) C.len[i] = n;
+        }
+        if (tid == 0 && dest >= 0) C.len[i] = n;
+        __syncthreads();
+    }
+    if (tid == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
+}
+
+// --------------------------------------------------- cluster hash kernel
+//
+// Rows whose tables outgrow one CTA's shared memory: a thread-block cluster
+// of CL CTAs holds one table of CL * TS slots in their shared memories
+// together (distributed shared memory).  The CTAs share the row's products
+// (block_products parts); a product goes to the CTA that owns its column
+// (the top bits of the column's hash), to a slot there given by the next
+// LOG_TS bits (triangular probing; when that table is full, on to the next
+// CTA's), with atomics on that CTA's shared memory.  Then each CTA counts its slots, CTA 0 places the row (the sum)
+// and hands every CTA its offset, and each writes its entries straight to
+// C (in table order) and clears the slots it used.  Every CTA passes the
+// same cluster barriers: the row loop and the status test are uniform.
+template <int SR, int LOG_TS, int CL>
+__global__ void __launch_bounds__(256, 1)
+k_num_cluster_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned early_mask, int bin) {
+    using T = typename Sr<SR>::T;
+    constexpr int TS = 1 << LOG_TS;
+    constexpr int LOG_CL = CL == 2 ? 1 : (CL == 4 ? 2 : 3);
+    static_assert((1 << LOG_CL) == CL, "cluster size 2, 4 or 8");
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int64_t p_boff[256];
+    __shared__ T p_av[256];
+    __shared__ int p_incl[256], p_blen[256], p_wsum[32];
+    __shared__ int s_cnt, s_full, s_pos;
+    __shared__ long long s_dest;  // written by CTA 0: this row's place (-1: none)
+    __shared__ int s_off;         // written by CTA 0: this CTA's offset in the row
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    T *vals = (T *)smem;
+    int32_t *keys = (int32_t *)(vals + TS);
+    T *Cv = (T *)C.val;
+    BlockProdSmem<T> ps{p_boff, p_av, p_incl, p_blen, p_wsum};
+    // early_mask holds only bits of the stages before the recompute, which
+    // no sibling kernel sets meanwhile: every CTA reads the same answer
+    const bool skip = failed(ctl, early_mask);
+    for (int s = tid; s < TS; s += 256) {
+        keys[s] = -1;
+        vals[s] = Sr<SR>::zero();
+    }
+    if (tid == 0) {
+        s_cnt = 0;
+        s_full = 0;
+    }
+    cl.sync();
+    long long nnz_acc = 0;
+    const long long cnt = skip ? 0 : ctl->bin_count[bin];
+    const long long nclusters = gridDim.x / CL;
+    for (long long it = blockIdx.x / CL; it < cnt; it += nclusters) {
+        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        if (tid == 0) s_pos = 0;
+        bool ok = true;
+        block_products<SR, true>(A, B, i, ps, [&](const int32_t (&c)[PU], const T (&v)[PU], const bool (&valid)[PU]) {
+            int owner[PU];
+            uint32_t slot[PU];
+            int32_t old[PU];
+            // first probes of the round's products, all in flight at once
+#pragma unroll
+            for (int u = 0; u < PU; u++) {
+                const uint32_t h = (uint32_t)c[u] * 2654435761u;
+                owner[u] = (int)(h >> (32 - LOG_CL));
+                slot[u] = (h << LOG_CL) >> (32 - LOG_TS);
+                old[u] = valid[u] ? atomicCAS(cl.map_shared_rank(keys, owner[u]) + slot[u], -1, c[u]) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < PU; u++) {
+                if (!valid[u]) continue;
+                T *rv = cl.map_shared_rank(vals, owner[u]);
+                if (old[u] == -1 || old[u] == c[u]) {
+                    Sr<SR>::acc(rv + slot[u], v[u]);
+                    continue;
+                }
+                // the rest of the probe sequence; a full table passes the
+                // column on to the next CTA's, so the cluster's tables fill
+                // up together whatever the hash spread
+                int r = hash_acc_from<LOG_TS, T, SR, true>(cl.map_shared_rank(keys, owner[u]), rv, slot[u], c[u], v[u], 1);
+                for (int t = 1; t < CL && r < 0; t++) {
+                    const int o = (owner[u] + t) & (CL - 1);
+                    r = hash_acc_from<LOG_TS, T, SR, true>(cl.map_shared_rank(keys, o), cl.map_shared_rank(vals, o),
+                                                            slot[u], c[u], v[u]);
+                }
+                ok &= r >= 0;
+            }
+        }, rank, CL);
+        if (!ok) s_full = 1;
+        cl.sync();  // (1) every product of the row is in the tables
+        int c = 0;
+        for (int s0 = w * 32; s0 < TS; s0 += 256) c += __popc(__ballot_sync(0xffffffffu, keys[s0 + lane] >= 0));
+        if (lane == 0 && c) atomicAdd(&s_cnt, c);
+        cl.sync();  // (2) counts and overflow flags are final
+        if (rank == 0 && tid == 0) {
+            int full = 0, n = 0;
+            for (int r = 0; r < CL; r++) {
+                *cl.map_shared_rank(&s_off, r) = n;  // this CTA's entries follow those of the CTAs before it
+                n += *cl.map_shared_rank(&s_cnt, r);
+                full |= *cl.map_shared_rank(&s_full, r);
+            }
+            long long dest = -1;
+            if (full) {  // a learned table too small: see the group kernel
+                if (J.sizing == SIZE_LEARNED) J.ovf[atomic_add_ll2(&ctl->n_ovf, 1)] = i;
+                else report_overflow(ctl, bin, i, A, B);
+            } else {
+                dest = c_row_dest(C, J, ctl, i, n);
+                nnz_acc += n;
+                if (dest >= 0) C.len[i] = n;
+            }
+            for (int r = 0; r < CL; r++) *cl.map_shared_rank(&s_dest, r) = dest;
+        }
+        cl.sync();  // (3) every CTA knows the row's place and its offset
+        const long long dest = s_dest;
+        const int off = s_off;
+        for (int s0 = w * 32; s0 < TS; s0 += 256) {
+            const int s = s0 + lane;
+            const int32_t k = keys[s];
+            const bool occ = k >= 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, occ);
+            if (bal) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&s_pos, __popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (occ) {
+                    if (dest >= 0) {
+                        const int x = off + base + __popc(bal & lanemask_lt());
+                        C.col[dest + x] = k;
+                        Cv[dest + x] = vals[s];
+                    }
+                    keys[s] = -1;
+                    vals[s] = Sr<SR>::zero();
+                }
+            }
         }
         __syncthreads();
+        if (tid == 0) {
+            s_cnt = 0;
+            s_full = 0;
+        }
+        cl.sync();  // (4) the tables are clear before the next row's products arrive
     }
     if (tid == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
 }
 
 // ------------------------------------------------- global dense kernel
 
-constexpr int GD_SORT = 8192;  // rows touching at most this many mask words sort the word list
-
 template <int SR>
 __global__ void __launch_bounds__(512)
 k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
     using T = typename Sr<SR>::T;
-    extern __shared__ __align__(16) int32_t sl[];  // GD_SORT word indices, sorted
     __shared__ int64_t p_boff[512];
     __shared__ T p_av[512];
     __shared__ int p_incl[512], p_blen[512], p_wsum[32];
-    __shared__ int s_nw, s_n, s_lo, s_hi;
+    __shared__ int s_n;
     __shared__ long long s_dest;
     if (failed(ctl, mask)) return;
     const int tid = threadIdx.x;
+    const int nwords = (int)(J.gd_w / 32);
+    const int nsum = (nwords + 31) / 32;
     T *acc = (T *)J.gd_acc + (int64_t)blockIdx.x * J.gd_w;
-    uint32_t *msk = J.gd_mask + (int64_t)blockIdx.x * (J.gd_w / 32);
-    int32_t *touched = J.gd_list + (int64_t)blockIdx.x * (J.gd_w / 32);  // mask words this row set
+    uint32_t *msk = J.gd_mask + (int64_t)blockIdx.x * nwords;
+    uint32_t *sum = J.gd_sum + (int64_t)blockIdx.x * nsum;  // bit w: mask word w was touched
     T *Cv = (T *)C.val;
     BlockProdSmem<T> ps{p_boff, p_av, p_incl, p_blen, p_wsum};
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
         const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
-        if (tid == 0) {
-            s_nw = 0;
-            s_n = 0;
-            s_lo = 0x7fffffff;
-            s_hi = -1;
-        }
+        if (tid == 0) s_n = 0;
         __syncthreads();
         block_products<SR>(A, B, i, ps, [&](int32_t j, T v) {
-            // the product that sets the first bit of a mask word lists the word,
-            // so the read-out visits only the words this row touched
-            if (atomicOr(&msk[j >> 5], 1u << (j & 31)) == 0u) touched[atomicAdd(&s_nw, 1)] = j >> 5;
+            // the product that sets the first bit of a mask word marks the
+            // word in the summary, so the read-out skips untouched words
+            if (atomicOr(&msk[j >> 5], 1u << (j & 31)) == 0u) atomicOr(&sum[j >> 10], 1u << ((j >> 5) & 31));
             Sr<SR>::acc(&acc[j], v);
         });
         __syncthreads();
-        const int nw = s_nw;
-        int c = 0, lo = 0x7fffffff, hi = -1;
-        for (int x = tid; x < nw; x += 512) {
-            const int wd = touched[x];
-            c += __popc(__ldcg(msk + wd));
-            lo = min(lo, wd);
-            hi = max(hi, wd);
-        }
+        // entries under summary word x (its touched mask words)
+        auto entries_of = [&](int x) {
+            int c = 0;
+            uint32_t sw = x < nsum ? __ldcg(sum + x) : 0u;
+            while (sw) {
+                const int b = __ffs(sw) - 1;
+                sw &= sw - 1;
+                c += __popc(__ldcg(msk + x * 32 + b));
+            }
+            return c;
+        };
+        int c = 0;
+        for (int x = tid; x < nsum; x += 512) c += entries_of(x);
         c = warp_sum<int>(c);
         if ((tid & 31) == 0 && c) atomicAdd(&s_n, c);
-        if (hi >= 0) {
-            atomicMin(&s_lo, lo);
-            atomicMax(&s_hi, hi);
-        }
         __syncthreads();
         const int n = s_n;
         if (tid == 0) {
@@ -925,52 +1181,34 @@ k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
         }
         __syncthreads();
         const long long dest = s_dest;
-        // the row goes out in column order: the touched words sorted (few
-        // words), or the whole touched range scanned in order (many)
-        const bool listed = nw <= GD_SORT && (int64_t)nw * 8 < (int64_t)(s_hi - s_lo + 1);
-        int nx = 0;
-        if (listed) {
-            int N = 2;
-            while (N < nw) N <<= 1;
-            for (int x = tid; x < N; x += 512) sl[x] = x < nw ? touched[x] : 0x7fffffff;
-            __syncthreads();
-            for (int size = 2; size <= N; size <<= 1)
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    for (int q = tid; q < N / 2; q += 512) {
-                        const int x = 2 * q - (q & (stride - 1)), y = x + stride;
-                        const int32_t kx = sl[x], ky = sl[y];
-                        if ((kx > ky) == ((x & size) == 0)) {
-                            sl[x] = ky;
-                            sl[y] = kx;
-                        }
-                    }
-                    __syncthreads();
-                }
-            nx = nw;
-        } else {
-            nx = s_hi >= 0 ? s_hi - s_lo + 1 : 0;
-        }
-        int run = 0;  // entries written by earlier chunks
-        for (int x0 = 0; x0 < nx; x0 += 512) {
+        // the row in column order: summary words in order (a block scan gives
+        // each its offset), then each summary word's mask words and bits in order
+        int run = 0;
+        for (int x0 = 0; x0 < nsum; x0 += 512) {
             const int x = x0 + tid;
-            const int wd = x < nx ? (listed ? sl[x] : s_lo + x) : -1;
-            const uint32_t word = wd >= 0 ? __ldcg(msk + wd) : 0u;
-            const int pc = __popc(word);
-            const int incl = block_incl_scan(pc, p_incl, p_wsum);
-            int o = run + p_incl[tid] - pc;
-            uint32_t bits = word;
-            while (bits) {
-                const int bt = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const int j = (wd << 5) + bt;
-                if (dest >= 0) {
-                    C.col[dest + o] = j;
-                    Cv[dest + o] = __ldcg(acc + j);
+            const int e = entries_of(x);
+            const int incl = block_incl_scan(e, p_incl, p_wsum);
+            int o = run + p_incl[tid] - e;
+            uint32_t sw = x < nsum ? __ldcg(sum + x) : 0u;
+            while (sw) {
+                const int b = __ffs(sw) - 1;
+                sw &= sw - 1;
+                const int wd = x * 32 + b;
+                uint32_t bits = __ldcg(msk + wd);
+                while (bits) {
+                    const int bt = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int j = (wd << 5) + bt;
+                    if (dest >= 0) {
+                        C.col[dest + o] = j;
+                        Cv[dest + o] = __ldcg(acc + j);
+                    }
+                    acc[j] = Sr<SR>::zero();
+                    o++;
                 }
-                acc[j] = Sr<SR>::zero();
-                o++;
+                msk[wd] = 0u;
             }
-            if (word) msk[wd] = 0u;
+            if (x < nsum) sum[x] = 0u;
             run += incl;
             __syncthreads();
         }
@@ -1110,8 +1348,6 @@ void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const C
     if (g > num_sms * 8) g = num_sms * 8;
     if (g < 1) g = 1;
     launch_k(k_size_bins, (unsigned)g, 256, 0, s, A, B, C, J, ctl, mask);
-    launch_k(k_size_long, (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * 2, (max_rows + 1) / 2)),
-             256, 0, s, A, B, C, J, ctl, mask);
     if (J.sizing == SIZE_LEARNED) {
         constexpr size_t smem = EST_PARAMS * sizeof(float) + 16;
         static bool set = false;
@@ -1320,23 +1556,74 @@ static void launch_cta_hash(const MatView &A, const MatView &B, const MatView &C
 // The bin kernels are independent; they are spread over the given streams
 // (which the caller has ordered after the sizing pass) so that empty bins
 // cost no time on the critical path.
+template <int SR, int LOG_TS, int CL>
+static void launch_cluster_hash(const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl,
+                                unsigned mask, int bin, cudaStream_t s, int num_sms) {
+    using T = typename Sr<SR>::T;
+    constexpr int TS = 1 << LOG_TS;
+    const size_t smem = (size_t)TS * (sizeof(T) + sizeof(int32_t));
+    static bool set = false;
+    if (!set) {
+        cudaFuncSetAttribute(k_num_cluster_hash<SR, LOG_TS, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        set = true;
+    }
+    int per_sm = (int)((200 * 1024) / (smem + 8 * 1024));
+    if (per_sm < 1) per_sm = 1;
+    long long clusters = (long long)num_sms * per_sm / CL;
+    if (clusters > J.rows_hint) clusters = J.rows_hint;
+    if (clusters < 1) clusters = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(clusters * CL));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    // every CTA must reach the kernel's cluster barriers, so it tests only the
+    // status bits of the stages before the recompute (see the split kernel)
+    const unsigned early = mask & (ST_INVALID | ST_AB_STAGE | ST_AB_ARENA);
+    // a failed launch stays in the runtime's last error, which the caller checks
+    cudaLaunchKernelEx(&cfg, k_num_cluster_hash<SR, LOG_TS, CL>, A, B, C, J, ctl, early, bin);
+    __atomic_fetch_add(&launch_counter(), 1ull, __ATOMIC_RELAXED);
+}
+
 template <int SR>
 static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,
                           const cudaStream_t *ss, int ns, int num_sms) {
     using T = typename Sr<SR>::T;
+    // the first kernel (the thread-merge bin, the bulk of the rows of
+    // sparse products) has ss[0] to itself; the others take the remaining
+    // streams in turn, so that a small bin never waits behind a large one
+    // of a stream it shares unless there are more bins than streams
     int k = 0;
-    auto next = [&]() { return ss[(k++) % ns]; };
+    auto next = [&]() {
+        const int j = k++;
+        return (j == 0 || ns == 1) ? ss[0] : ss[1 + (j - 1) % (ns - 1)];
+    };
     {
-        const size_t smem_m = (size_t)MERGE_UB * TM_NT * (sizeof(int32_t) + sizeof(T));
+        // shared memory for the bin's bound only: at a bound of 49 three
+        // blocks of 128 threads fit an SM with double values (two at 64),
+        // leaving less of the SM's memory to the L1 cache that catches the
+        // B rows shared by neighbouring rows
         static bool set_m = false;
         if (!set_m) {
-            cudaFuncSetAttribute(k_num_thread_merge<SR, MERGE_K, MERGE_UB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_m);
+            cudaFuncSetAttribute(k_num_thread_merge<SR, MERGE_K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)MERGE_UB * TM_NT * (sizeof(int32_t) + sizeof(T))));
             set_m = true;
         }
-        const int per_sm = (int)std::min<size_t>(8, std::max<size_t>(1, (200 * 1024) / (smem_m + 1024)));
-        launch_k(k_num_thread_merge<SR, MERGE_K, MERGE_UB>, grid_for(num_sms * per_sm, J.rows_hint, TM_NT), TM_NT,
-                 smem_m, next(), A, B, C, J, ctl, mask, (int)BIN_T8);
+        auto launch_merge = [&](int bin, int ub) {
+            const size_t smem_m = (size_t)ub * TM_NT * (sizeof(int32_t) + sizeof(T));
+            const int per_sm = (int)std::min<size_t>(8, std::max<size_t>(1, (227 * 1024) / (smem_m + 1024)));
+            launch_k(k_num_thread_merge<SR, MERGE_K>, grid_for(num_sms * per_sm, J.rows_hint, TM_NT), TM_NT, smem_m,
+                     next(), A, B, C, J, ctl, mask, bin, ub);
+        };
+        launch_merge((int)BIN_T8, std::max(J.tm_ub, 1));
+        if (J.tm_k > 0 && J.tm_ub < MERGE_UB) launch_merge((int)BIN_T64, MERGE_UB);
     }
     if (J.dense_mode) {
         const int mp = (int)((J.m + 31) / 32 * 32);
@@ -1373,16 +1660,11 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
     launch_cta_hash<SR, 12>(A, B, C, J, ctl, mask, BIN_C4096, next(), num_sms);
     launch_cta_hash<SR, 13>(A, B, C, J, ctl, mask, BIN_C8192, next(), num_sms);
     launch_cta_hash<SR, 14>(A, B, C, J, ctl, mask, BIN_C16384, next(), num_sms);
-    {
-        constexpr size_t smem_g = GD_SORT * sizeof(int32_t);
-        static bool set_g = false;
-        if (!set_g) {
-            cudaFuncSetAttribute(k_num_gdense<SR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
-            set_g = true;
-        }
-        launch_k(k_num_gdense<SR>, grid_for(J.gd_ctas, J.rows_hint, 1), 512, smem_g, next(), A, B, C, J, ctl, mask,
-                 (int)BIN_GD);
-    }
+    launch_cluster_hash<SR, 13, 2>(A, B, C, J, ctl, mask, BIN_K2, next(), num_sms);
+    launch_cluster_hash<SR, 13, 4>(A, B, C, J, ctl, mask, BIN_K4, next(), num_sms);
+    launch_cluster_hash<SR, 13, 8>(A, B, C, J, ctl, mask, BIN_K8, next(), num_sms);
+    launch_cluster_hash<SR, 14, 8>(A, B, C, J, ctl, mask, BIN_K8L, next(), num_sms);
+    launch_k(k_num_gdense<SR>, grid_for(J.gd_ctas, J.rows_hint, 1), 512, 0, next(), A, B, C, J, ctl, mask, (int)BIN_GD);
 }
 
 void run_numeric(int sr, const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,

@@ -42,6 +42,28 @@ __device__ __forceinline__ uint8_t kind_of(uint8_t op, bool present) {
     return present ? K_UPD : K_INS;
 }
 
+// Rows of C* (Section 5, Eq. 1) at row granularity: R = rows(A*) u
+// {i : A(i,k) != 0, k in rows(B*)}.  A* and B* hold the batch entries that
+// change their matrix (kind INS, UPD or DEL).  The second set is read from
+// the transposed pattern of A *before* this batch; it equals the set taken
+// over A' because a pattern difference at (i,k) already puts i in rows(A*).
+// Sets bit i of bm; the lanes that set a fresh bit append i to list with one
+// atomic per warp.  All 32 lanes must call it (want = false to abstain).
+__device__ __forceinline__ void mark_bit(uint32_t *bm, int32_t i) {
+    const uint32_t bit = 1u << (i & 31);
+    if (!(((volatile uint32_t *)bm)[i >> 5] & bit)) atomicOr(&bm[i >> 5], bit);
+}
+
+__device__ __forceinline__ void mark_warp(uint32_t *bm, bool want, int32_t i, int32_t *list, long long *cnt) {
+    bool fresh = false;
+    if (want) {
+        const uint32_t bit = 1u << (i & 31);
+        if (!(((volatile uint32_t *)bm)[i >> 5] & bit)) fresh = !(atomicOr(&bm[i >> 5], bit) & bit);
+    }
+    const long long t = warp_fetch_add(cnt, fresh ? 1 : 0);
+    if (fresh) list[t] = i;
+}
+
 // The thread at the first entry of each row segment of the sorted batch
 // owns the segment: it classifies the segment's updates against the old row
 // (binary search), keeps running INS/DEL counts, and writes the INS/UPD
@@ -50,7 +72,8 @@ __device__ __forceinline__ uint8_t kind_of(uint8_t op, bool present) {
 // Segments with more than SEG_SHORT updates are classified by the whole warp
 // afterwards, one at a time.
 template <typename T>
-__global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigned stage_bit) {
+__global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigned stage_bit, DetectBufs D,
+                           int mark_rows, int mark_cols) {
     if (failed(ctl, mask)) return;
     UpdCtl *u = &ctl->u[J.which];
     const int64_t n = J.n;
@@ -68,7 +91,7 @@ __global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigne
             // padding entries of a forwarded batch sit in a row past the end
             head = (int64_t)r < M.nrows && (s == 0 || J.row[s - 1] != r);
         }
-        if (head) hi = (int)upper_bound_dev<int32_t>(J.row, s, n, r);
+        if (head) hi = (int)run_end_dev<int32_t>(J.row, s, n, r);
         const bool lng = head && (hi - s > SEG_SHORT);
         const bool mine = head && !lng;
         int L = 0, cins = 0, cdel = 0, cupd = 0, cnop = 0;
@@ -96,6 +119,10 @@ __global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigne
         s_upd += cupd;
         s_nop += cnop;
         const bool changed = mine && (cins + cdel + cupd) > 0;
+        // the first step of the affected-row detection: a row with an
+        // effective change is in rows(A*) (and, for C = A A, in rows(B*))
+        if (mark_rows && changed) mark_bit(D.bmR, r);
+        if (mark_cols) mark_warp(D.bmK, changed, r, D.K, D.nK);
         const int nl = L + cins - cdel;
         const int nch = changed ? (L + CH - 1) / CH : 0;
         const long long m = warp_fetch_add(&u->n_merge, changed ? 1 : 0);
@@ -170,6 +197,8 @@ __global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigne
                 s_nop += tn;
             }
             if (ti + td + tu == 0) continue;
+            if (mark_rows && lane == 0) mark_bit(D.bmR, r2);
+            if (mark_cols) mark_warp(D.bmK, lane == 0, r2, D.K, D.nK);
             const int nl2 = L2 + ti - td;
             const int nch2 = (L2 + CH - 1) / CH;
             long long m2 = 0, so2 = 0, cb2 = 0;
@@ -224,15 +253,17 @@ __global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigne
 
 // ------------------------------------------------------------ merge copy
 
+// The work of the merge copy for block `blk` of `nblk` (a kernel of its own,
+// or a share of the grid of k_detect_merge).
 template <typename T>
-__global__ void k_merge_copy(UpdJob J, MatView M, const Ctl *ctl, unsigned mask) {
-    if (failed(ctl, mask)) return;
+__device__ __forceinline__ void merge_copy_blocks(const UpdJob &J, const MatView &M, const Ctl *ctl, long long blk,
+                                                  long long nblk) {
     const long long nch = ctl->u[J.which].n_chunk;
     const int lane = threadIdx.x & 31;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long nwarps = (nblk * blockDim.x) >> 5;
     const T *mval = (const T *)M.val;
     T *sval = (T *)J.st_val;
-    for (long long x = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < nch; x += nwarps) {
+    for (long long x = (blk * blockDim.x + threadIdx.x) >> 5; x < nch; x += nwarps) {
         const int m = J.ch_item[x], part = J.ch_part[x];
         const int32_t r = J.m_row[m];
         const int lo = J.m_lo[m], hi = J.m_hi[m];
@@ -253,6 +284,12 @@ __global__ void k_merge_copy(UpdJob J, MatView M, const Ctl *ctl, unsigned mask)
             if (sval) sval[soff + o] = mval[base + p];
         }
     }
+}
+
+template <typename T>
+__global__ void k_merge_copy(UpdJob J, MatView M, const Ctl *ctl, unsigned mask) {
+    if (failed(ctl, mask)) return;
+    merge_copy_blocks<T>(J, M, ctl, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------- commit
@@ -324,50 +361,85 @@ __global__ void k_commit_copy(CommitJob J, MatView M, const Ctl *ctl, unsigned m
 
 // ---------------------------------------------------------- detection
 
-// Rows of C* (Section 5, Eq. 1) at row granularity: R = rows(A*) u
-// {i : A(i,k) != 0, k in rows(B*)}.  A* and B* hold the batch entries that
-// change their matrix (kind INS, UPD or DEL).  The second set is read from
-// the transposed pattern of A *before* this batch; it equals the set taken
-// over A' because a pattern difference at (i,k) already puts i in rows(A*).
-// Sets bit i of bm; the lanes that set a fresh bit append i to list with one
-// atomic per warp.  All 32 lanes must call it (want = false to abstain).
-__device__ __forceinline__ void mark_warp(uint32_t *bm, bool want, int32_t i, int32_t *list, long long *cnt) {
-    bool fresh = false;
-    if (want) {
-        const uint32_t bit = 1u << (i & 31);
-        if (!(((volatile uint32_t *)bm)[i >> 5] & bit)) fresh = !(atomicOr(&bm[i >> 5], bit) & bit);
-    }
-    const long long t = warp_fetch_add(cnt, fresh ? 1 : 0);
-    if (fresh) list[t] = i;
-}
-
-__global__ void k_detect_entries(const int32_t *srow, const uint8_t *kind, int64_t n, int mark_rows, int mark_cols,
-                                 DetectBufs D, Ctl *ctl, unsigned mask) {
-    if (failed(ctl, mask)) return;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = base + threadIdx.x;
-        const bool ch = s < n && kind[s] != K_NOP;
-        const int32_t r = ch ? srow[s] : 0;
-        if (mark_rows) mark_warp(D.bmR, ch, r, D.R, &ctl->n_affected);
-        if (mark_cols) mark_warp(D.bmK, ch, r, D.K, D.nK);
-    }
-}
-
-__global__ void k_detect_cols(MatView AT, DetectBufs D, Ctl *ctl, unsigned mask) {
-    if (failed(ctl, mask)) return;
+__device__ __forceinline__ void detect_cols_blocks(const MatView &AT, const DetectBufs &D, Ctl *ctl, long long blk,
+                                                   long long nblk) {
     const long long nk = *D.nK;
     const int lane = threadIdx.x & 31;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long x = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < nk; x += nwarps) {
+    const long long nwarps = (nblk * blockDim.x) >> 5;
+    for (long long x = (blk * blockDim.x + threadIdx.x) >> 5; x < nk; x += nwarps) {
         const int32_t k = D.K[x];
         if (lane == 0) D.bmK[k >> 5] = 0u;  // marks of B* rows are not needed any more
         const int64_t base = AT.off[k];
         const int L = AT.len[k];
         for (int p0 = 0; p0 < L; p0 += 32) {
             const int p = p0 + lane;
-            mark_warp(D.bmR, p < L, p < L ? AT.col[base + p] : 0, D.R, &ctl->n_affected);
+            if (p < L) mark_bit(D.bmR, AT.col[base + p]);
         }
     }
+}
+
+__global__ void k_detect_cols(MatView AT, DetectBufs D, Ctl *ctl, unsigned mask) {
+    if (failed(ctl, mask)) return;
+    detect_cols_blocks(AT, D, ctl, blockIdx.x, gridDim.x);
+}
+
+// The detection's second step and the merge copy of one matrix in one
+// launch (they read and write disjoint data): the first `detect_blocks`
+// blocks detect, the others copy.
+template <typename T>
+__global__ void k_detect_merge(MatView AT, DetectBufs D, long long detect_blocks, UpdJob J, MatView M, Ctl *ctl,
+                               unsigned mask) {
+    if (failed(ctl, mask)) return;
+    if (blockIdx.x < detect_blocks) detect_cols_blocks(AT, D, ctl, blockIdx.x, detect_blocks);
+    else merge_copy_blocks<T>(J, M, ctl, blockIdx.x - detect_blocks, gridDim.x - detect_blocks);
+}
+
+// The affected rows R from their bitmap: a thread per bitmap word, a block
+// per 256 words (8192 rows), one atomic per block for its place in R.  R
+// comes out in row order within each block's range, so the recompute's
+// neighbouring lanes work on neighbouring rows (shared B rows stay in L1).
+// The words are cleared for the next batch.
+__global__ void __launch_bounds__(256) k_collect_rows(uint32_t *bm, int64_t words, int32_t *R, Ctl *ctl,
+                                                      unsigned mask) {
+    __shared__ int s_wsum[8];
+    __shared__ long long s_base;
+    if (failed(ctl, mask)) return;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int64_t b0 = (int64_t)blockIdx.x * 256; b0 < words; b0 += (int64_t)gridDim.x * 256) {
+        const int64_t x = b0 + tid;
+        uint32_t bits = x < words ? bm[x] : 0u;
+        const int c = __popc(bits);
+        int incl = warp_incl_scan<int>(c);
+        if (lane == 31) s_wsum[w] = incl;
+        __syncthreads();
+        if (tid == 0) {
+            int t = 0;
+            for (int k = 0; k < 8; k++) {
+                const int v = s_wsum[k];
+                s_wsum[k] = t;
+                t += v;
+            }
+            s_base = t ? atomic_add_ll(&ctl->n_affected, t) : 0;
+        }
+        __syncthreads();
+        long long o = s_base + s_wsum[w] + incl - c;
+        if (bits) {
+            bm[x] = 0u;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                R[o++] = (int32_t)(x * 32 + b);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+void run_collect_rows(uint32_t *bm, int64_t words, int32_t *R, Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms) {
+    int64_t g = (words + 255) / 256;
+    if (g > (int64_t)num_sms * 8) g = (int64_t)num_sms * 8;
+    if (g < 1) g = 1;
+    launch_k(k_collect_rows, (unsigned)g, 256, 0, s, bm, words, R, ctl, mask);
 }
 
 // Structural changes of A, forwarded to its transposed pattern: INS (i,k)
@@ -402,12 +474,12 @@ static unsigned grid_for(int64_t n, int nt) {
 }
 
 void run_classify(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsigned mask, unsigned stage_bit,
-                  cudaStream_t s, int num_sms) {
+                  const DetectBufs &D, bool mark_rows, bool mark_cols, cudaStream_t s, int num_sms) {
     if (J.n <= 0) return;
     unsigned g = grid_for(J.n, 256);
     if (g > (unsigned)num_sms * 8) g = num_sms * 8;
-    if (vsize == 8) launch_k(k_classify<double>, g, 256, 0, s, J, M, ctl, mask, stage_bit);
-    else launch_k(k_classify<int32_t>, g, 256, 0, s, J, M, ctl, mask, stage_bit);
+    if (vsize == 8) launch_k(k_classify<double>, g, 256, 0, s, J, M, ctl, mask, stage_bit, D, (int)mark_rows, (int)mark_cols);
+    else launch_k(k_classify<int32_t>, g, 256, 0, s, J, M, ctl, mask, stage_bit, D, (int)mark_rows, (int)mark_cols);
 }
 
 void run_merge_copy(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsigned mask, cudaStream_t s,
@@ -429,10 +501,16 @@ void run_commit(const CommitJob &J, const MatView &M, int vsize, int64_t max_ite
     else launch_k(k_commit_copy<int32_t>, g, 256, 0, s, J, M, ctl, copy_mask);
 }
 
-void run_detect_entries(const int32_t *srow, const uint8_t *kind, int64_t n, bool mark_rows, bool mark_cols,
-                        const DetectBufs &D, Ctl *ctl, unsigned mask, cudaStream_t s) {
-    if (n <= 0) return;
-    launch_k(k_detect_entries, (unsigned)((n + 255) / 256), 256, 0, s, srow, kind, n, mark_rows, mark_cols, D, ctl, mask);
+void run_detect_merge(const MatView &AT, const DetectBufs &D, const UpdJob &J, const MatView &M, int vsize, Ctl *ctl,
+                      unsigned mask, cudaStream_t s, int num_sms) {
+    if (J.n <= 0) {
+        run_detect_cols(AT, D, ctl, mask, s, num_sms);
+        return;
+    }
+    const long long nd = (long long)num_sms * 4;
+    const unsigned g = (unsigned)(nd + (long long)num_sms * 8);
+    if (vsize == 8) launch_k(k_detect_merge<double>, g, 256, 0, s, AT, D, nd, J, M, ctl, mask);
+    else launch_k(k_detect_merge<int32_t>, g, 256, 0, s, AT, D, nd, J, M, ctl, mask);
 }
 
 void run_detect_cols(const MatView &AT, const DetectBufs &D, Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms) {

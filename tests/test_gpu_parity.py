@@ -142,6 +142,29 @@ def test_separate_b_with_both_batches(dspg, sr):
     assert_matches(g.read_C(), C_o, S_o, what="A-only batch")
 
 
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_short_rows_with_more_products_than_columns(dspg, sr):
+    """C with 20 columns, A rows of at most 8 entries reading B rows of up to
+    18: a row's product bound (up to 144) exceeds both the column count and
+    the thread-merge staging size, so the merge bins must be chosen by the
+    uncapped bound, every tuning candidate alike."""
+    A = random_csr(300, 30, 8, 5, sr, empty_frac=0.05)
+    B = random_csr(30, 20, 18, 6, sr, empty_frac=0.0)
+    Ao, Bo = OMat.from_csr(A), OMat.from_csr(B)
+    for cand in dspg.tuning_candidates():
+        g = dspg.DynamicSpGEMM(A, B)
+        g.set_tuning(cand)
+        Ao, Bo = OMat.from_csr(A), OMat.from_csr(B)
+        Co = Ao.multiply(Bo)
+        C_o, S_o = oracle_product(Ao, Bo)
+        assert_matches(g.read_C(), C_o, S_o, what=f"static {cand}")
+        ba = random_batch(300, 30, 200, 7, sr, A=A)
+        _apply_both(g, Ao, Co, ba, Bo, None)
+        C_o, S_o = oracle_product(Ao, Bo)
+        assert_matches(g.read_C(), C_o, S_o, what=f"batch {cand}")
+        g.close()
+
+
 def test_locality_rows_outside_R_unchanged_bitwise(dspg):
     A = er_matrix(2048, 8, seed=11)
     g = dspg.DynamicSpGEMM(A)
@@ -223,6 +246,23 @@ def test_growth_paths_tight_arena(dspg):
         total += st["compactions"]
         _check_state(g, Ao, None, f"tight {k}")
     assert total > 0
+
+
+@pytest.mark.parametrize("nupd", [2047, 2048, 2049, 6000, 16384, 16385])
+def test_batch_sizes_at_the_sort_tile_bounds(dspg, nupd):
+    """Batch sizes around the sort's tiles (2048 words per CTA, up to 8 CTAs
+    in one cluster; 16385 takes the radix path), half of the entries
+    repeating keys, so that a key's last write and its dead copies sit in
+    different tiles."""
+    sr = PLUS_TIMES_F64
+    A = er_matrix(3000, 6, seed=43, kind=sr)
+    g = dspg.DynamicSpGEMM(A)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    b = random_batch(3000, 3000, nupd, 44 + nupd, sr, A=A, dup_frac=0.5)
+    st = _apply_both(g, Ao, Co, b)
+    assert st["n_unique"] < nupd
+    _check_state(g, Ao, None, f"batch of {nupd}")
 
 
 def test_large_batch_multi_cta_sort(dspg):
@@ -436,6 +476,52 @@ def test_rows_longer_than_the_tables_are_read_in_order(dspg, cta_max):
     assert np.array_equal(g.last_affected(), R)
     _check_state(g, Ao, Bo, f"long rows after a batch (cta_max {cta_max})")
     rows = np.array(sorted(hubs) + [0, 1], np.int32)
+    rp, col, val = g.read_rows_C(rows)
+    o_rp, o_col, o_val = Ao.multiply_rows(Bo, rows)
+    assert np.array_equal(rp, o_rp) and np.array_equal(col, o_col)
+
+
+def _hub_lengths(n, k, hub_lens, sr, seed, short_max=6):
+    """n x k matrix whose rows 0..len(hub_lens)-1 have the given lengths and
+    the others 0..short_max random columns."""
+    from workloads import CSR
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    for i in range(n):
+        L = hub_lens[i] if i < len(hub_lens) else int(rng.integers(0, short_max + 1))
+        c = np.sort(rng.choice(k, size=min(L, k), replace=False))
+        rows.append(np.full(c.shape[0], i, np.int64))
+        cols.append(c.astype(np.int64))
+    r, c = np.concatenate(rows), np.concatenate(cols)
+    v = rng.random(r.shape[0]) if sr == PLUS_TIMES_F64 else rng.integers(1, 101, r.shape[0]).astype(np.int32)
+    rowptr = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(r, minlength=n), out=rowptr[1:])
+    return CSR(n, k, rowptr, c.astype(np.int32), v)
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_rows_in_cluster_tables_and_beyond(dspg, sr):
+    """Rows of C with about 20,000, 45,000, 100,000 and 150,000 products
+    over 400,000 columns (nearly all distinct): they go to the tables that
+    span 4 and 8 CTAs of a cluster (distributed shared memory), to the one of
+    8 CTAs x 16384 slots, and past it to the global dense kernel; C' equals
+    the oracle's, statically, after a batch on the hub rows, and in every
+    read (rows longer than a CTA can sort are sorted together)."""
+    A = _hub_lengths(64, 20000, [2000, 4500, 10000, 15000], sr, 211)
+    B = random_csr(20000, 400000, 20, 212, sr, empty_frac=0.0)
+    g = dspg.DynamicSpGEMM(A, B)
+    Ao, Bo = OMat.from_csr(A), OMat.from_csr(B)
+    Co = Ao.multiply(Bo)
+    blen = np.diff(B.rowptr)
+    prods = [int(blen[A.col[A.rowptr[i]:A.rowptr[i + 1]]].sum()) for i in range(4)]
+    assert 2 * 8192 < prods[0] <= 4 * 8192 < prods[1] <= 8 * 8192 < prods[2] <= 8 * 16384 < prods[3], prods
+    assert np.diff(Co.to_csr().rowptr)[:4].min() > 16384
+    _check_state(g, Ao, Bo, "cluster tables, static")
+    b = random_batch(A.nrows, A.ncols, 400, 213, sr, A=A)
+    b.row[:40] = np.arange(40, dtype=np.int32) % 4
+    _apply_both(g, Ao, Co, b, Bo, None)
+    _check_state(g, Ao, Bo, "cluster tables, after a batch")
+    rows = np.array([3, 0, 2, 1, 17], np.int32)
     rp, col, val = g.read_rows_C(rows)
     o_rp, o_col, o_val = Ao.multiply_rows(Bo, rows)
     assert np.array_equal(rp, o_rp) and np.array_equal(col, o_col)
