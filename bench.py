@@ -131,15 +131,17 @@ class Rmat21Workload(Rmat20Workload):
     sweep = (10, 100, 1000, 10000)
     vsize, dtype = 8, "f64"
 
-    def __init__(self):
+    def __init__(self, scale=21):
         super().__init__()
-        self.describe = ("R-MAT scale 21 ef 8 (0.45,0.15,0.15,0.25) symmetrised, C = A A (+,.) f64, "
+        self.scale = scale
+        self.describe = (f"R-MAT scale {scale} ef 8 (0.45,0.15,0.15,0.25) symmetrised, C = A A (+,.) f64, "
                          "batches of 10^3 undirected edge insertions/deletions")
         self.unit = "batches/s (10^3-edge batches)"
 
     def operands(self):
         from workloads import PLUS_TIMES_F64, rmat_symmetric
-        self._A, self._held = rmat_symmetric(21, 8, R21, seed=5, kind=PLUS_TIMES_F64, holdout=400000)
+        self._A, self._held = rmat_symmetric(self.scale, 8, R21, seed=5, kind=PLUS_TIMES_F64,
+                                             holdout=400000 >> max(0, 21 - self.scale))
         return self._A, None
 
 
@@ -940,12 +942,14 @@ def reference_arm(args):
 
 def profile_arm(args):
     """One warmed-up dynamic step (NVTX range "step") or one static recompute
-    (NVTX range "static") of the stencil or R-MAT scale-20 workload, for ncu
-    captures filtered with --nvtx-include."""
+    (NVTX range "static") of the stencil, R-MAT scale-20 or R-MAT A A
+    workload (scale --scale), for ncu captures filtered with --nvtx-include."""
     import torch
     import paper_2202_08808_gb300 as pkg
     torch.cuda.set_device(0)
-    W = WORKLOADS[args.workload if args.workload in WORKLOADS else "stencil"]()
+    name = args.workload if args.workload in WORKLOADS else "stencil"
+    # rmat21 at a smaller --scale: the same kernels on a case small enough for full ncu captures
+    W = WORKLOADS[name](args.scale) if name == "rmat21" else WORKLOADS[name]()
     A, B = W.operands()
     g = pkg.DynamicSpGEMM(A, B)
     if args.profile == "static":

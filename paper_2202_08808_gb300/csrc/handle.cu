@@ -781,7 +781,18 @@ void pipeline(dspg_handle *h, cudaStream_t s, bool timed, bool capturing) {
         transpose_front(h, h->side);
     }
     mark(2, s);
-    const int merged = stage_detect(h, s);
+    // when B is A: the detection's column step, A's merge copy and commit
+    // plan share one launch, the collection of R and the commit copy the
+    // next (the merge and commit stage times are then part of the detection's)
+    const bool fused = h->b_is_a && h->has_at && h->inA.n > 0;
+    const int64_t words = (h->A.nrows + 31) / 32;
+    const CommitJob cjA = upd_commit_job(h, h->wA, ST_AB_ARENA, ST_AB_STAGE);
+    int merged = -1;
+    if (fused)
+        run_detect_merge_plan(h->AT.view(), detect_bufs(h), h->wA.job(h->inA.n), h->A.view(), cjA, h->vsize, h->ctl,
+                              M_AB & ~ST_AB_ARENA, h->opt.slack_min, h->opt.slack_div, h->inA.n, s, h->num_sms);
+    else
+        merged = stage_detect(h, s);
     if (side_on) {
         CK(cudaEventRecord(h->evDetect, s));
         CK(cudaStreamWaitEvent(h->side, h->evDetect, 0));
@@ -789,12 +800,19 @@ void pipeline(dspg_handle *h, cudaStream_t s, bool timed, bool capturing) {
         mark(9, h->side);
         CK(cudaEventRecord(h->evSide, h->side));
     }
-    // R from the detection's bitmap, in row order within each block's range
-    run_collect_rows(h->wc.bmR.p, (h->A.nrows + 31) / 32, h->wc.R.p, h->ctl, M_AB, s, h->num_sms);
-    mark(3, s);
-    stage_merge(h, s, merged);
-    mark(4, s);
-    stage_commit_ab(h, s);
+    if (fused) {
+        // R from the detection's bitmap, in row order within each block's range
+        run_collect_copy(h->wc.bmR.p, words, h->wc.R.p, cjA, h->A.view(), h->vsize, h->ctl, M_AB & ~ST_AB_ARENA,
+                         M_AB, s, h->num_sms);
+        mark(3, s);
+        mark(4, s);
+    } else {
+        run_collect_rows(h->wc.bmR.p, words, h->wc.R.p, h->ctl, M_AB, s, h->num_sms);
+        mark(3, s);
+        stage_merge(h, s, merged);
+        mark(4, s);
+        stage_commit_ab(h, s);
+    }
     mark(5, s);
     stage_size(h, s);
     mark(6, s);

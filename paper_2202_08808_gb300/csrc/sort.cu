@@ -57,26 +57,26 @@ __device__ __forceinline__ void write_sorted(SortOut out, int64_t s, uint64_t ke
 
 // ---------------------------------------------------- cluster-sort path
 //
-// Batches up to CS_TILE * CS_MAXT entries whose packed word
-// (key << ib | arrival index) fits 64 bits are sorted by one launch: a
-// thread-block cluster with a CTA per tile of CS_TILE words.  Each CTA sorts
-// its tile with a bitonic network held in registers (CS_EPT consecutive
-// words per thread: strides below CS_EPT inside a thread, strides up to a
-// warp's span by shuffles, longer ones through shared memory; the words are
-// distinct, so no stability is needed).  The CTAs then copy each other's
-// sorted tiles through distributed shared memory, and every word's global
-// rank is its rank in its own tile plus the number of smaller words in each
-// other tile (a thread's words are consecutive, so each search starts where
-// the previous one ended).  A word is dead when a word with the same key and
-// a later index exists: the next word of its own tile or, in another tile,
-// the first word above it.
+// Batches up to 16384 entries whose packed word (key << ib | arrival index)
+// fits 64 bits are sorted by one launch: a thread-block cluster with a CTA
+// per tile of 1024 words (512 threads; up to 16 CTAs where the device allows
+// clusters that large, else tiles of 2048 words in up to 8 CTAs of 1024
+// threads).  Each CTA sorts its tile with a bitonic network held in
+// registers (CS_EPT consecutive words per thread: strides below CS_EPT
+// inside a thread, strides up to a warp's span by shuffles, longer ones
+// through shared memory; the words are distinct, so no stability is
+// needed).  The CTAs then copy each other's sorted tiles through
+// distributed shared memory, and every word's global rank is its rank in
+// its own tile plus the number of smaller words in each other tile (a
+// thread's words are consecutive, so each search starts where the previous
+// one ended).  A word is dead when a word with the same key and a later
+// index exists: the next word of its own tile or, in another tile, the
+// first word above it.
 
-constexpr int CS_NT = 1024;
-constexpr int CS_EPT = 2;
-constexpr int CS_TILE = CS_NT * CS_EPT;
+constexpr int CS_EPT = 2;   // words per thread
 constexpr int CS_MAXT = 8;  // the portable cluster size
 
-int64_t sort_small_max() { return (int64_t)CS_TILE * CS_MAXT; }
+int64_t sort_small_max() { return (int64_t)2048 * CS_MAXT; }
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < b ? b : a; }
@@ -116,6 +116,7 @@ __device__ __forceinline__ void bitonic_in_thread(uint64_t (&x)[CS_EPT], bool as
 // Merges up to CS_EPT words run inside the thread (unrolled); the larger ones
 // are loops whose steps reach the partner by shuffle (within a warp's span)
 // or through shared memory, so the code stays small.
+template <int TILE>
 __device__ __forceinline__ void bitonic_sort_tile(uint64_t (&x)[CS_EPT], uint64_t *own, int tid) {
 #pragma unroll
     for (int size = 2; size <= CS_EPT; size <<= 1)
@@ -131,7 +132,7 @@ __device__ __forceinline__ void bitonic_sort_tile(uint64_t (&x)[CS_EPT], uint64_
                     x[e | stride] = asc ? umax64(a, b) : umin64(a, b);
                 }
 #pragma unroll 1
-    for (int size = 2 * CS_EPT; size <= CS_TILE; size <<= 1) {
+    for (int size = 2 * CS_EPT; size <= TILE; size <<= 1) {
 #pragma unroll 1
         for (int stride = size >> 1; stride >= CS_EPT; stride >>= 1) {
             if (stride >= CS_EPT * 32) {  // partner in another warp
@@ -157,18 +158,20 @@ __device__ __forceinline__ void bitonic_sort_tile(uint64_t (&x)[CS_EPT], uint64_
     }
 }
 
-__global__ void __launch_bounds__(CS_NT)
+template <int NT>
+__global__ void __launch_bounds__(NT)
 k_cluster_sort(const InArgs *in, int n, int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out,
                Ctl *ctl, unsigned skip_mask, int cb, int ib) {
+    constexpr int TILE = NT * CS_EPT;
     extern __shared__ uint64_t tiles[];  // slot u: the sorted tile of CTA u
     cg::cluster_group cl = cg::this_cluster();
     // no early return: every CTA of the cluster must reach both cluster barriers
     const bool skip = failed(ctl, skip_mask);
     const int tid = threadIdx.x;
     const int me = blockIdx.x, nt = gridDim.x;
-    const int lo = me * CS_TILE;
-    const int cnt = min(CS_TILE, n - lo);
-    uint64_t *own = tiles + (size_t)me * CS_TILE;
+    const int lo = me * TILE;
+    const int cnt = min(TILE, n - lo);
+    uint64_t *own = tiles + (size_t)me * TILE;
     uint64_t x[CS_EPT];
     if (!skip) {
         const int32_t *row = in->row, *col = in->col;
@@ -194,16 +197,16 @@ k_cluster_sort(const InArgs *in, int n, int64_t nrows, int64_t ncols, int sr, bo
         for (int e = 0; e < CS_EPT; e++) x[e] = ~uint64_t(0);
     }
     // bitonic sort of the tile: position of x[e] is tid * CS_EPT + e
-    bitonic_sort_tile(x, own, tid);
+    bitonic_sort_tile<TILE>(x, own, tid);
 #pragma unroll
     for (int e = 0; e < CS_EPT; e++) own[tid * CS_EPT + e] = x[e];
     cl.sync();
     // the other tiles into this CTA's shared memory (16-byte loads)
     for (int u = 0; u < nt; u++) {
         if (u == me) continue;
-        const uint4 *src = (const uint4 *)cl.map_shared_rank(tiles + (size_t)u * CS_TILE, u);
-        uint4 *dst = (uint4 *)(tiles + (size_t)u * CS_TILE);
-        for (int k = tid; k < CS_TILE / 2; k += CS_NT) dst[k] = src[k];
+        const uint4 *src = (const uint4 *)cl.map_shared_rank(tiles + (size_t)u * TILE, u);
+        uint4 *dst = (uint4 *)(tiles + (size_t)u * TILE);
+        for (int k = tid; k < TILE / 2; k += NT) dst[k] = src[k];
     }
     cl.sync();  // no CTA leaves while another still reads its tile
     if (skip) return;
@@ -220,8 +223,8 @@ k_cluster_sort(const InArgs *in, int n, int64_t nrows, int64_t ncols, int sr, bo
     if (nv > 0)
         for (int u = 0; u < nt; u++) {
             if (u == me) continue;
-            const uint64_t *t = tiles + (size_t)u * CS_TILE;
-            const int cu = min(CS_TILE, n - u * CS_TILE);
+            const uint64_t *t = tiles + (size_t)u * TILE;
+            const int cu = min(TILE, n - u * TILE);
             int p = count_below(t, 0, cu, x[0]);
 #pragma unroll
             for (int e = 0; e < CS_EPT; e++) {
@@ -367,19 +370,36 @@ void sort_updates(const InArgs *in, int64_t n, int64_t nrows, int64_t ncols, int
     if (n <= 0) return;
     const int cb = bits_for(ncols), rb = bits_for(nrows), ib = bits_for(n);
     const int kb = cb + rb;
-    if (n <= (int64_t)CS_TILE * CS_MAXT && kb + ib <= 64) {
-        const int tiles = (int)((n + CS_TILE - 1) / CS_TILE);
-        const size_t smem = (size_t)tiles * CS_TILE * sizeof(uint64_t);
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_cluster_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((size_t)CS_MAXT * CS_TILE * sizeof(uint64_t)));
-            attr_set = true;
+    if (n <= sort_small_max() && kb + ib <= 64) {
+        // tiles of 1024 words (512 threads) where the cluster may hold as
+        // many CTAs as there are tiles (8 portably, 16 where the device
+        // allows it), else tiles of 2048 words (1024 threads)
+        static int small_tiles_max = 0;  // most 1024-word tiles per cluster
+        if (small_tiles_max == 0) {
+            const size_t smem16 = (size_t)16 * 1024 * sizeof(uint64_t);
+            cudaFuncSetAttribute(k_cluster_sort<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem16);
+            cudaFuncSetAttribute(k_cluster_sort<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)CS_MAXT * 2048 * sizeof(uint64_t)));
+            small_tiles_max = 8;
+            if (cudaFuncSetAttribute(k_cluster_sort<512>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess) {
+                cudaLaunchConfig_t q = {};
+                q.gridDim = dim3(16);
+                q.blockDim = dim3(512);
+                q.dynamicSmemBytes = smem16;
+                int cs = 0;
+                if (cudaOccupancyMaxPotentialClusterSize(&cs, k_cluster_sort<512>, &q) == cudaSuccess && cs >= 16)
+                    small_tiles_max = 16;
+            }
+            cudaGetLastError();  // the queries' errors are not the pipeline's
         }
+        const bool small = n <= (int64_t)1024 * small_tiles_max;
+        const int tile = small ? 1024 : 2048;
+        const int tiles = (int)((n + tile - 1) / tile);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)tiles);
-        cfg.blockDim = dim3(CS_NT);
-        cfg.dynamicSmemBytes = smem;
+        cfg.blockDim = dim3(small ? 512 : 1024);
+        cfg.dynamicSmemBytes = (size_t)tiles * tile * sizeof(uint64_t);
         cfg.stream = s;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -389,7 +409,12 @@ void sort_updates(const InArgs *in, int64_t n, int64_t nrows, int64_t ncols, int
         cfg.attrs = at;
         cfg.numAttrs = 1;
         // a failed launch stays in the runtime's last error, which the caller checks
-        cudaLaunchKernelEx(&cfg, k_cluster_sort, in, (int)n, nrows, ncols, sr, check_values, out, ctl, skip_mask, cb, ib);
+        if (small)
+            cudaLaunchKernelEx(&cfg, k_cluster_sort<512>, in, (int)n, nrows, ncols, sr, check_values, out, ctl, skip_mask,
+                               cb, ib);
+        else
+            cudaLaunchKernelEx(&cfg, k_cluster_sort<1024>, in, (int)n, nrows, ncols, sr, check_values, out, ctl,
+                               skip_mask, cb, ib);
         __atomic_fetch_add(&launch_counter(), 1ull, __ATOMIC_RELAXED);
         return;
     }

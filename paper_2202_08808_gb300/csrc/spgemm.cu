@@ -908,27 +908,10 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
         const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
         bool ok = true;
         int fresh = 0;  // slots this thread claimed; their sum is the row's length
-        block_products<SR, true>(A, B, i, ps, [&](const int32_t (&c)[PU], const T (&v)[PU], const bool (&valid)[PU]) {
-            uint32_t h[PU];
-            int32_t old[PU];
-            // first probes of the round's products, all in flight at once
-#pragma unroll
-            for (int u = 0; u < PU; u++) {
-                h[u] = ((uint32_t)c[u] * 2654435761u) >> (32 - LOG_TS);
-                old[u] = valid[u] ? atomicCAS(keys + h[u], -1, c[u]) : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < PU; u++) {
-                if (!valid[u]) continue;
-                if (old[u] == -1 || old[u] == c[u]) {
-                    Sr<SR>::acc(vals + h[u], v[u]);
-                    fresh += old[u] == -1;
-                    continue;
-                }
-                const int r = hash_acc_from<LOG_TS, T, SR>(keys, vals, h[u], c[u], v[u], 1);
-                ok &= r >= 0;
-                fresh += r > 0;
-            }
+        block_products<SR>(A, B, i, ps, [&](int32_t j, T v) {
+            const int r = hash_acc<LOG_TS, T, SR>(keys, vals, j, v);
+            ok &= r >= 0;
+            fresh += r > 0;
         });
         fresh = warp_sum<int>(fresh);
         if (lane == 0 && fresh) atomicAdd(&s_n, fresh);

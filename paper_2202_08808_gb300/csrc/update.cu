@@ -294,10 +294,10 @@ __global__ void k_merge_copy(UpdJob J, MatView M, const Ctl *ctl, unsigned mask)
 
 // ---------------------------------------------------------------- commit
 
-__global__ void k_commit_plan(CommitJob J, MatView M, Ctl *ctl, unsigned mask, int slack_min, int slack_div) {
-    if (failed(ctl, mask)) return;
+__device__ __forceinline__ void commit_plan_blocks(const CommitJob &J, const MatView &M, Ctl *ctl, int slack_min,
+                                                   int slack_div, long long blk, long long nblk) {
     const long long n = *J.count;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+    for (long long base = blk * blockDim.x; base < n; base += nblk * blockDim.x) {
         const long long m = base + threadIdx.x;
         const bool valid = m < n;
         int32_t r = 0, nl = 0, c = 0;
@@ -332,15 +332,20 @@ __global__ void k_commit_plan(CommitJob J, MatView M, Ctl *ctl, unsigned mask, i
     }
 }
 
-template <typename T>
-__global__ void k_commit_copy(CommitJob J, MatView M, const Ctl *ctl, unsigned mask) {
+__global__ void k_commit_plan(CommitJob J, MatView M, Ctl *ctl, unsigned mask, int slack_min, int slack_div) {
     if (failed(ctl, mask)) return;
+    commit_plan_blocks(J, M, ctl, slack_min, slack_div, blockIdx.x, gridDim.x);
+}
+
+template <typename T>
+__device__ __forceinline__ void commit_copy_blocks(const CommitJob &J, const MatView &M, long long blk,
+                                                   long long nblk) {
     const long long n = *J.cc_count;
     const int lane = threadIdx.x & 31;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long nwarps = (nblk * blockDim.x) >> 5;
     const T *sv = (const T *)J.st_val;
     T *mv = (T *)M.val;
-    for (long long x = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += nwarps) {
+    for (long long x = (blk * blockDim.x + threadIdx.x) >> 5; x < n; x += nwarps) {
         const int m = J.cc_item[x], part = J.cc_part[x];
         const int32_t r = J.rows[m];
         const int32_t nl = J.lens[m];
@@ -357,6 +362,12 @@ __global__ void k_commit_copy(CommitJob J, MatView M, const Ctl *ctl, unsigned m
             M.cap[r] = J.ncap[m];
         }
     }
+}
+
+template <typename T>
+__global__ void k_commit_copy(CommitJob J, MatView M, const Ctl *ctl, unsigned mask) {
+    if (failed(ctl, mask)) return;
+    commit_copy_blocks<T>(J, M, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------- detection
@@ -399,13 +410,12 @@ __global__ void k_detect_merge(MatView AT, DetectBufs D, long long detect_blocks
 // comes out in row order within each block's range, so the recompute's
 // neighbouring lanes work on neighbouring rows (shared B rows stay in L1).
 // The words are cleared for the next batch.
-__global__ void __launch_bounds__(256) k_collect_rows(uint32_t *bm, int64_t words, int32_t *R, Ctl *ctl,
-                                                      unsigned mask) {
+__device__ __forceinline__ void collect_blocks(uint32_t *bm, int64_t words, int32_t *R, Ctl *ctl, long long blk,
+                                               long long nblk) {
     __shared__ int s_wsum[8];
     __shared__ long long s_base;
-    if (failed(ctl, mask)) return;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int64_t b0 = (int64_t)blockIdx.x * 256; b0 < words; b0 += (int64_t)gridDim.x * 256) {
+    for (int64_t b0 = blk * 256; b0 < words; b0 += nblk * 256) {
         const int64_t x = b0 + tid;
         uint32_t bits = x < words ? bm[x] : 0u;
         const int c = __popc(bits);
@@ -433,6 +443,70 @@ __global__ void __launch_bounds__(256) k_collect_rows(uint32_t *bm, int64_t word
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(256) k_collect_rows(uint32_t *bm, int64_t words, int32_t *R, Ctl *ctl,
+                                                      unsigned mask) {
+    if (failed(ctl, mask)) return;
+    collect_blocks(bm, words, R, ctl, blockIdx.x, gridDim.x);
+}
+
+// When B is A the update needs two launches between the classification and
+// the sizing: the detection's column step, the merge copy and the commit
+// plan (disjoint data: the transposed pattern, A's old rows into staging,
+// A's row places) in one, then the collection of R and the commit copy in
+// the next.  The first launch's blocks are dealt out to the three jobs; the
+// plan may set the arena bit, which none of the others depends on.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_detect_merge_plan(MatView AT, DetectBufs D, long long nd, UpdJob J, MatView M, CommitJob CJ, long long nm, Ctl *ctl,
+                    unsigned mask, int slack_min, int slack_div) {
+    if (failed(ctl, mask)) return;
+    if (blockIdx.x < nd) detect_cols_blocks(AT, D, ctl, blockIdx.x, nd);
+    else if (blockIdx.x < nd + nm) merge_copy_blocks<T>(J, M, ctl, blockIdx.x - nd, nm);
+    else commit_plan_blocks(CJ, M, ctl, slack_min, slack_div, blockIdx.x - nd - nm, gridDim.x - nd - nm);
+}
+
+// R is collected whatever the plan decided (a recovery after an exhausted
+// arena re-runs the commit, not the detection); the copy waits for a plan
+// that did not fail.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_collect_copy(uint32_t *bm, int64_t words, int32_t *R, long long nc, CommitJob CJ, MatView M, Ctl *ctl,
+               unsigned collect_mask, unsigned copy_mask) {
+    if (blockIdx.x < nc) {
+        if (failed(ctl, collect_mask)) return;
+        collect_blocks(bm, words, R, ctl, blockIdx.x, nc);
+    } else {
+        if (failed(ctl, copy_mask)) return;
+        commit_copy_blocks<T>(CJ, M, blockIdx.x - nc, gridDim.x - nc);
+    }
+}
+
+void run_detect_merge_plan(const MatView &AT, const DetectBufs &D, const UpdJob &J, const MatView &M,
+                           const CommitJob &CJ, int vsize, Ctl *ctl, unsigned mask, int slack_min, int slack_div,
+                           int64_t max_items, cudaStream_t s, int num_sms) {
+    const long long nd = (long long)num_sms * 4, nm = (long long)num_sms * 8;
+    long long np = (max_items + 255) / 256;
+    if (np > (long long)num_sms * 4) np = (long long)num_sms * 4;
+    if (np < 1) np = 1;
+    const unsigned g = (unsigned)(nd + nm + np);
+    if (vsize == 8)
+        launch_k(k_detect_merge_plan<double>, g, 256, 0, s, AT, D, nd, J, M, CJ, nm, ctl, mask, slack_min, slack_div);
+    else
+        launch_k(k_detect_merge_plan<int32_t>, g, 256, 0, s, AT, D, nd, J, M, CJ, nm, ctl, mask, slack_min, slack_div);
+}
+
+void run_collect_copy(uint32_t *bm, int64_t words, int32_t *R, const CommitJob &CJ, const MatView &M, int vsize,
+                      Ctl *ctl, unsigned collect_mask, unsigned copy_mask, cudaStream_t s, int num_sms) {
+    long long nc = (words + 255) / 256;
+    if (nc > (long long)num_sms * 8) nc = (long long)num_sms * 8;
+    if (nc < 1) nc = 1;
+    const unsigned g = (unsigned)(nc + (long long)num_sms * 8);
+    if (vsize == 8)
+        launch_k(k_collect_copy<double>, g, 256, 0, s, bm, words, R, nc, CJ, M, ctl, collect_mask, copy_mask);
+    else
+        launch_k(k_collect_copy<int32_t>, g, 256, 0, s, bm, words, R, nc, CJ, M, ctl, collect_mask, copy_mask);
 }
 
 void run_collect_rows(uint32_t *bm, int64_t words, int32_t *R, Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms) {

@@ -248,12 +248,12 @@ def test_growth_paths_tight_arena(dspg):
     assert total > 0
 
 
-@pytest.mark.parametrize("nupd", [2047, 2048, 2049, 6000, 16384, 16385])
+@pytest.mark.parametrize("nupd", [1023, 1024, 1025, 2049, 6000, 8192, 8193, 10000, 16384, 16385])
 def test_batch_sizes_at_the_sort_tile_bounds(dspg, nupd):
-    """Batch sizes around the sort's tiles (2048 words per CTA, up to 8 CTAs
-    in one cluster; 16385 takes the radix path), half of the entries
-    repeating keys, so that a key's last write and its dead copies sit in
-    different tiles."""
+    """Batch sizes around the sort's tiles (1024 words per CTA, up to 16 CTAs
+    in one cluster where the device allows it, else 2048 words in up to 8;
+    16385 takes the radix path), half of the entries repeating keys, so that
+    a key's last write and its dead copies sit in different tiles."""
     sr = PLUS_TIMES_F64
     A = er_matrix(3000, 6, seed=43, kind=sr)
     g = dspg.DynamicSpGEMM(A)
