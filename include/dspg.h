@@ -212,7 +212,7 @@ typedef struct {
     int32_t cta_max;
 } dspg_tuning;
 
-/* Set (t == NULL: restore the defaults {8, 64, 8, 0, 1024, 8192}) or read
+/* Set (t == NULL: restore the defaults {8, 64, 8, 0, 1024, 16384}) or read
  * the tuning of h.  Out-of-range fields return DSPG_ERR_INVALID. */
 dspg_status dspg_set_tuning(dspg_handle *h, const dspg_tuning *t);
 dspg_status dspg_get_tuning(dspg_handle *h, dspg_tuning *t);

@@ -278,7 +278,7 @@ struct dspg_handle {
     std::vector<Graph> seen;  // keys run once eagerly (exec unused)
     uint64_t epoch = 1;       // bumped whenever a persistent buffer moves
     bool use_graphs = true;
-    dspg_tuning tune{8, 64, 8, 0, 1024, 8192};  // row bins of the recompute
+    dspg_tuning tune{8, 64, 8, 0, 1024, 16384};  // row bins of the recompute
     int sizing = DSPG_SIZE_BOUND;               // how the recompute's tables are sized
     int est_min = 128;
     float est_margin = 0.25f;
@@ -1266,10 +1266,10 @@ void check_tuning(const dspg_tuning &t) {
 // each (thread-merge reach, lanes per short row, table oversizing, the
 // warp/CTA and CTA/global crossovers).
 const dspg_tuning kCandidates[] = {
-    {8, 64, 8, 0, 1024, 8192},  {0, 0, 8, 0, 1024, 8192},   {4, 32, 8, 0, 1024, 8192},  {8, 49, 8, 0, 1024, 8192},
-    {8, 64, 16, 0, 1024, 8192}, {8, 64, 32, 0, 1024, 8192}, {8, 64, 8, 1, 1024, 8192},  {8, 64, 8, 0, 512, 8192},
-    {8, 64, 8, 0, 1024, 4096},  {8, 64, 8, 0, 1024, 16384}, {8, 64, 8, 1, 1024, 16384}, {8, 64, 32, 0, 1024, 16384},
-    {0, 0, 16, 1, 1024, 8192},
+    {8, 64, 8, 0, 1024, 16384}, {0, 0, 8, 0, 1024, 16384},   {4, 32, 8, 0, 1024, 16384}, {8, 49, 8, 0, 1024, 16384},
+    {8, 64, 16, 0, 1024, 16384}, {8, 64, 32, 0, 1024, 16384}, {8, 64, 8, 1, 1024, 16384}, {8, 64, 8, 0, 512, 16384},
+    {8, 64, 8, 0, 1024, 4096},  {8, 64, 8, 0, 1024, 8192},    {8, 64, 8, 1, 1024, 8192},  {8, 64, 32, 0, 1024, 8192},
+    {0, 0, 16, 1, 1024, 16384},
 };
 constexpr int kNumCandidates = (int)(sizeof(kCandidates) / sizeof(kCandidates[0]));
 

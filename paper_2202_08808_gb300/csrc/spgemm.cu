@@ -98,7 +98,14 @@ __device__ __forceinline__ void report_overflow(Ctl *ctl, int bin, int32_t i, co
     set_status(ctl, ST_TIMEOUT);
 }
 
-__device__ __forceinline__ int pick_table_bin(long long need, const CJob &J) {
+// ub: the row's uncapped product bound.  Rows beyond a CTA's table go to a
+// cluster's table only while their products are not far more than its
+// slots (ub <= 2 * need) and the row is sparse (need <= m / 8): a row whose
+// products collide many times over, or that fills much of C's width (as in
+// small squares of skewed graphs), is cheaper in the global dense
+// accumulator, which every CTA of a cluster would otherwise read the whole
+// row's products for.
+__device__ __forceinline__ int pick_table_bin(long long need, const CJob &J, long long ub) {
     need <<= J.table_shift;
     if (need <= 32 && J.lanes_min <= 8) return BIN_G8;
     if (need <= 64 && J.lanes_min <= 16) return BIN_G16;
@@ -114,6 +121,7 @@ __device__ __forceinline__ int pick_table_bin(long long need, const CJob &J) {
         if (need <= 8192) return BIN_C8192;
         return BIN_C16384;
     }
+    if (ub > 2 * need || need * 8 > J.m) return BIN_GD;
     if (need <= 2 * 8192) return BIN_K2;
     if (need <= 4 * 8192) return BIN_K4;
     if (need <= 8 * 8192) return BIN_K8;
@@ -140,7 +148,7 @@ __device__ __forceinline__ int pick_bin(long long ubc, int alen, const CJob &J, 
                                         long long ub) {
     if (merge_row(alen, ub, J)) return ub <= J.tm_ub ? BIN_T8 : BIN_T64;
     if (J.dense_mode) return (alen <= DENSE_WARP_A && ub <= 4096) ? BIN_WDENSE : BIN_CDENSE;
-    return pick_table_bin(table_need, J);
+    return pick_table_bin(table_need, J, ub);
 }
 
 // Append the calling lanes' rows i (of C) to their bins b (b < 0: none), one
@@ -378,7 +386,7 @@ __global__ void __launch_bounds__(128) k_est_bins(CJob J, Ctl *ctl, unsigned mas
             if (need > ubc) need = ubc;
             if (need < e.z) need = e.z;
             if (need < 1) need = 1;
-            b = pick_table_bin(need, J);
+            b = pick_table_bin(need, J, (long long)e.w);
         }
         append_bins(J, ctl, b, i);
     }
@@ -508,13 +516,17 @@ __device__ __forceinline__ int block_incl_scan(int v, int *incl, int *wsum) {
 
 // Calls emit(j, a (x) b) for every product of row i, all threads of the
 // block sharing the work (with parts > 1: the share `part` of them, the
-// CTAs of a cluster taking one part each; with BATCH, emit(c[PU], v[PU],
-// valid[PU]) takes a round's products at once).  Must be called by the whole
-// block.
-template <int SR, bool BATCH = false, class F>
+// CTAs of a cluster taking one part each), and of those only the ones whose
+// column passes keep (the others load no value).  Must be called by the
+// whole block.
+struct KeepAll {
+    __device__ bool operator()(int32_t) const { return true; }
+};
+
+template <int SR, class F, class K = KeepAll>
 __device__ __forceinline__ void block_products(const MatView &A, const MatView &B, int32_t i,
                                                BlockProdSmem<typename Sr<SR>::T> sm, F emit, int part = 0,
-                                               int parts = 1) {
+                                               int parts = 1, K keep = K()) {
     using T = typename Sr<SR>::T;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t aoff = A.off[i];
@@ -535,14 +547,18 @@ __device__ __forceinline__ void block_products(const MatView &A, const MatView &
         // PU loads per thread in flight, as above; with parts > 1 the rounds
         // of a chunk's products are dealt out to the parts in turn
         for (int base = part * nt * PU; base < total; base += parts * nt * PU) {
+            // each thread takes PU consecutive products: one search for the
+            // first, then a step to the next B row where the run crosses one
             int64_t q[PU];
             T a[PU];
+            const int p0 = base + tid * PU;
+            int s = p0 < total ? (int)upper_bound_dev<int>(sm.incl, 0, nt, p0) : 0;
 #pragma unroll
             for (int u = 0; u < PU; u++) {
-                const int p = base + u * nt + tid;
+                const int p = p0 + u;
                 q[u] = -1;
                 if (p < total) {
-                    const int s = (int)upper_bound_dev<int>(sm.incl, 0, nt, p);
+                    while (sm.incl[s] <= p) s++;  // past the B rows that end before p (empty ones too)
                     const int excl = sm.incl[s] - sm.blen[s];
                     q[u] = sm.boff[s] + (p - excl);
                     a[u] = sm.av[s];
@@ -552,25 +568,16 @@ __device__ __forceinline__ void block_products(const MatView &A, const MatView &
             T b[PU];
 #pragma unroll
             for (int u = 0; u < PU; u++)
+                if (q[u] >= 0) c[u] = __ldg(B.col + q[u]);
+#pragma unroll
+            for (int u = 0; u < PU; u++)
                 if (q[u] >= 0) {
-                    c[u] = __ldg(B.col + q[u]);
-                    b[u] = __ldg(Bv + q[u]);
+                    if (keep(c[u])) b[u] = __ldg(Bv + q[u]);
+                    else q[u] = -1;  // another CTA's column: no value load, no product
                 }
-            if constexpr (BATCH) {  // the round's PU products in one call (their atomics issued together)
-                T v[PU];
-                bool ok[PU];
 #pragma unroll
-                for (int u = 0; u < PU; u++) {
-                    ok[u] = q[u] >= 0;
-                    v[u] = ok[u] ? Sr<SR>::mul(a[u], b[u]) : Sr<SR>::zero();
-                    if (!ok[u]) c[u] = 0;
-                }
-                emit(c, v, ok);
-            } else {
-#pragma unroll
-                for (int u = 0; u < PU; u++)
-                    if (q[u] >= 0) emit(c[u], Sr<SR>::mul(a[u], b[u]));
-            }
+            for (int u = 0; u < PU; u++)
+                if (q[u] >= 0) emit(c[u], Sr<SR>::mul(a[u], b[u]));
         }
         __syncthreads();
     }
@@ -781,6 +788,7 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
     T *Cv = (T *)C.val;
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
+    if ((long long)blockIdx.x * NG >= cnt) return;  // no row for this block
     // the table is cleared once here; each row's read-out clears the slots
     // it used
     for (int s = gl; s < TS; s += G) {
@@ -878,15 +886,17 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
 
 // ------------------------------------------------------- CTA hash kernel
 
-template <int SR, int LOG_TS>
-__global__ void __launch_bounds__(256)
+// NT threads per CTA: more for the larger tables, whose shared memory leaves
+// room for fewer CTAs per SM, so that an SM keeps as many warps in flight.
+template <int SR, int LOG_TS, int NT>
+__global__ void __launch_bounds__(NT)
 k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int64_t p_boff[256];
-    __shared__ T p_av[256];
-    __shared__ int p_incl[256], p_blen[256], p_wsum[32];
+    __shared__ int64_t p_boff[NT];
+    __shared__ T p_av[NT];
+    __shared__ int p_incl[NT], p_blen[NT], p_wsum[32];
     __shared__ int s_n, s_pos;
     __shared__ long long s_dest;
     if (failed(ctl, mask)) return;
@@ -897,8 +907,9 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
     BlockProdSmem<T> ps{p_boff, p_av, p_incl, p_blen, p_wsum};
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
+    if (blockIdx.x >= cnt) return;  // no row for this CTA (an empty bin costs no table clear)
     // the table is cleared once here; each row's read-out clears the slots it used
-    for (int s = tid; s < TS; s += 256) {
+    for (int s = tid; s < TS; s += NT) {
         keys[s] = -1;
         vals[s] = Sr<SR>::zero();
     }
@@ -918,7 +929,7 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
         const bool full = __syncthreads_or(!ok);
         const int n = s_n;
         if (full) {  // table too small: see the group kernel
-            for (int s = tid; s < TS; s += 256) {
+            for (int s = tid; s < TS; s += NT) {
                 keys[s] = -1;
                 vals[s] = Sr<SR>::zero();
             }
@@ -941,7 +952,7 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
         const long long dest = s_dest;
         // one pass over the table: write straight to C (in table order; C's
         // rows need no column order) and clear the used slots
-        for (int s0 = w * 32; s0 < TS; s0 += 256) {
+        for (int s0 = w * 32; s0 < TS; s0 += NT) {
             const int s = s0 + lane;
             const int32_t k = keys[s];
             const bool occ = k >= 0;
@@ -971,25 +982,28 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
 //
 // Rows whose tables outgrow one CTA's shared memory: a thread-block cluster
 // of CL CTAs holds one table of CL * TS slots in their shared memories
-// together (distributed shared memory).  The CTAs share the row's products
-// (block_products parts); a product goes to the CTA that owns its column
-// (the top bits of the column's hash), to a slot there given by the next
-// LOG_TS bits (triangular probing; when that table is full, on to the next
-// CTA's), with atomics on that CTA's shared memory.  Then each CTA counts its slots, CTA 0 places the row (the sum)
-// and hands every CTA its offset, and each writes its entries straight to
-// C (in table order) and clears the slots it used.  Every CTA passes the
-// same cluster barriers: the row loop and the status test are uniform.
-template <int SR, int LOG_TS, int CL>
-__global__ void __launch_bounds__(256, 1)
+// together.  Each column belongs to one CTA (the top bits of its hash); every
+// CTA goes through all of the row's products, keeps those of its own
+// columns (loading no value for the others) and inserts them into its own
+// shared memory, at the slot given by the next LOG_TS bits (triangular
+// probing).  Only when a CTA's table is full does it pass a column on to the
+// next CTA's table, with atomics through distributed shared memory, so the
+// cluster's tables fill up together whatever the hash spread.  Then each CTA
+// counts its slots, CTA 0 places the row (the sum) and hands every CTA its
+// offset, and each writes its entries straight to C (in table order) and
+// clears the slots it used.  Every CTA passes the same cluster barriers: the
+// row loop and the status test are uniform.
+template <int SR, int LOG_TS, int CL, int NT>
+__global__ void __launch_bounds__(NT, 1)
 k_num_cluster_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned early_mask, int bin) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
     constexpr int LOG_CL = CL == 2 ? 1 : (CL == 4 ? 2 : 3);
     static_assert((1 << LOG_CL) == CL, "cluster size 2, 4 or 8");
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int64_t p_boff[256];
-    __shared__ T p_av[256];
-    __shared__ int p_incl[256], p_blen[256], p_wsum[32];
+    __shared__ int64_t p_boff[NT];
+    __shared__ T p_av[NT];
+    __shared__ int p_incl[NT], p_blen[NT], p_wsum[32];
     __shared__ int s_cnt, s_full, s_pos;
     __shared__ long long s_dest;  // written by CTA 0: this row's place (-1: none)
     __shared__ int s_off;         // written by CTA 0: this CTA's offset in the row
@@ -1003,7 +1017,12 @@ k_num_cluster_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned e
     // early_mask holds only bits of the stages before the recompute, which
     // no sibling kernel sets meanwhile: every CTA reads the same answer
     const bool skip = failed(ctl, early_mask);
-    for (int s = tid; s < TS; s += 256) {
+    const long long cnt = skip ? 0 : ctl->bin_count[bin];
+    const long long nclusters = gridDim.x / CL;
+    // a cluster without rows leaves before its first barrier: all of its CTAs
+    // see the same count and cluster index, so they all leave together
+    if ((long long)(blockIdx.x / CL) >= cnt) return;
+    for (int s = tid; s < TS; s += NT) {
         keys[s] = -1;
         vals[s] = Sr<SR>::zero();
     }
@@ -1013,48 +1032,28 @@ k_num_cluster_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned e
     }
     cl.sync();
     long long nnz_acc = 0;
-    const long long cnt = skip ? 0 : ctl->bin_count[bin];
-    const long long nclusters = gridDim.x / CL;
     for (long long it = blockIdx.x / CL; it < cnt; it += nclusters) {
         const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
         if (tid == 0) s_pos = 0;
         bool ok = true;
-        block_products<SR, true>(A, B, i, ps, [&](const int32_t (&c)[PU], const T (&v)[PU], const bool (&valid)[PU]) {
-            int owner[PU];
-            uint32_t slot[PU];
-            int32_t old[PU];
-            // first probes of the round's products, all in flight at once
-#pragma unroll
-            for (int u = 0; u < PU; u++) {
-                const uint32_t h = (uint32_t)c[u] * 2654435761u;
-                owner[u] = (int)(h >> (32 - LOG_CL));
-                slot[u] = (h << LOG_CL) >> (32 - LOG_TS);
-                old[u] = valid[u] ? atomicCAS(cl.map_shared_rank(keys, owner[u]) + slot[u], -1, c[u]) : 0;
+        // every CTA goes through all of the row's products and keeps those
+        // whose column it owns: inserts into its own shared memory, no remote
+        // atomics; only a full table passes a column on to the next CTA's
+        block_products<SR>(A, B, i, ps, [&](int32_t j, T v) {
+            const uint32_t h = (uint32_t)j * 2654435761u;
+            const uint32_t slot = (h << LOG_CL) >> (32 - LOG_TS);
+            int r = hash_acc_from<LOG_TS, T, SR>(keys, vals, slot, j, v);
+            for (int t = 1; t < CL && r < 0; t++) {
+                const int o = (rank + t) & (CL - 1);
+                r = hash_acc_from<LOG_TS, T, SR, true>(cl.map_shared_rank(keys, o), cl.map_shared_rank(vals, o), slot,
+                                                        j, v);
             }
-#pragma unroll
-            for (int u = 0; u < PU; u++) {
-                if (!valid[u]) continue;
-                T *rv = cl.map_shared_rank(vals, owner[u]);
-                if (old[u] == -1 || old[u] == c[u]) {
-                    Sr<SR>::acc(rv + slot[u], v[u]);
-                    continue;
-                }
-                // the rest of the probe sequence; a full table passes the
-                // column on to the next CTA's, so the cluster's tables fill
-                // up together whatever the hash spread
-                int r = hash_acc_from<LOG_TS, T, SR, true>(cl.map_shared_rank(keys, owner[u]), rv, slot[u], c[u], v[u], 1);
-                for (int t = 1; t < CL && r < 0; t++) {
-                    const int o = (owner[u] + t) & (CL - 1);
-                    r = hash_acc_from<LOG_TS, T, SR, true>(cl.map_shared_rank(keys, o), cl.map_shared_rank(vals, o),
-                                                            slot[u], c[u], v[u]);
-                }
-                ok &= r >= 0;
-            }
-        }, rank, CL);
+            ok &= r >= 0;
+        }, 0, 1, [&](int32_t j) { return (int)(((uint32_t)j * 2654435761u) >> (32 - LOG_CL)) == rank; });
         if (!ok) s_full = 1;
         cl.sync();  // (1) every product of the row is in the tables
         int c = 0;
-        for (int s0 = w * 32; s0 < TS; s0 += 256) c += __popc(__ballot_sync(0xffffffffu, keys[s0 + lane] >= 0));
+        for (int s0 = w * 32; s0 < TS; s0 += NT) c += __popc(__ballot_sync(0xffffffffu, keys[s0 + lane] >= 0));
         if (lane == 0 && c) atomicAdd(&s_cnt, c);
         cl.sync();  // (2) counts and overflow flags are final
         if (rank == 0 && tid == 0) {
@@ -1078,7 +1077,7 @@ k_num_cluster_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned e
         cl.sync();  // (3) every CTA knows the row's place and its offset
         const long long dest = s_dest;
         const int off = s_off;
-        for (int s0 = w * 32; s0 < TS; s0 += 256) {
+        for (int s0 = w * 32; s0 < TS; s0 += NT) {
             const int s = s0 + lane;
             const int32_t k = keys[s];
             const bool occ = k >= 0;
@@ -1110,6 +1109,10 @@ k_num_cluster_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned e
 
 // ------------------------------------------------- global dense kernel
 
+// Up to this many mask words (512K columns) the read-out takes a thread per
+// mask word; wider rows go through the summary of touched words.
+constexpr int GD_DIRECT = 16384;
+
 template <int SR>
 __global__ void __launch_bounds__(512)
 k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
@@ -1123,6 +1126,7 @@ k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
     const int tid = threadIdx.x;
     const int nwords = (int)(J.gd_w / 32);
     const int nsum = (nwords + 31) / 32;
+    const bool direct = nwords <= GD_DIRECT;
     T *acc = (T *)J.gd_acc + (int64_t)blockIdx.x * J.gd_w;
     uint32_t *msk = J.gd_mask + (int64_t)blockIdx.x * nwords;
     uint32_t *sum = J.gd_sum + (int64_t)blockIdx.x * nsum;  // bit w: mask word w was touched
@@ -1137,10 +1141,51 @@ k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
         block_products<SR>(A, B, i, ps, [&](int32_t j, T v) {
             // the product that sets the first bit of a mask word marks the
             // word in the summary, so the read-out skips untouched words
-            if (atomicOr(&msk[j >> 5], 1u << (j & 31)) == 0u) atomicOr(&sum[j >> 10], 1u << ((j >> 5) & 31));
+            if (atomicOr(&msk[j >> 5], 1u << (j & 31)) == 0u && !direct)
+                atomicOr(&sum[j >> 10], 1u << ((j >> 5) & 31));
             Sr<SR>::acc(&acc[j], v);
         });
         __syncthreads();
+        if (direct) {
+            // few columns: a thread per mask word, in order (a block scan per
+            // 512 words gives each its offset); no summary needed
+            int c = 0;
+            for (int wd = tid; wd < nwords; wd += 512) c += __popc(__ldcg(msk + wd));
+            c = warp_sum<int>(c);
+            if ((tid & 31) == 0 && c) atomicAdd(&s_n, c);
+            __syncthreads();
+            const int n = s_n;
+            if (tid == 0) {
+                s_dest = c_row_dest(C, J, ctl, i, n);
+                nnz_acc += n;
+            }
+            __syncthreads();
+            const long long dest = s_dest;
+            int run = 0;
+            for (int w0 = 0; w0 < nwords; w0 += 512) {
+                const int wd = w0 + tid;
+                uint32_t bits = wd < nwords ? __ldcg(msk + wd) : 0u;
+                const int e = __popc(bits);
+                const int incl = block_incl_scan(e, p_incl, p_wsum);
+                int o = run + p_incl[tid] - e;
+                if (bits) msk[wd] = 0u;
+                while (bits) {
+                    const int bt = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int j = (wd << 5) + bt;
+                    if (dest >= 0) {
+                        C.col[dest + o] = j;
+                        Cv[dest + o] = __ldcg(acc + j);
+                    }
+                    acc[j] = Sr<SR>::zero();
+                    o++;
+                }
+                run += incl;
+                __syncthreads();
+            }
+            if (tid == 0 && dest >= 0) C.len[i] = n;
+            continue;
+        }
         // entries under summary word x (its touched mask words)
         auto entries_of = [&](int x) {
             int c = 0;
@@ -1213,11 +1258,12 @@ k_num_warp_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
     T *acc = (T *)smem + (size_t)w * mp;
     uint32_t *msk = (uint32_t *)((T *)smem + (size_t)NW * mp) + (size_t)w * 32;
     T *Cv = (T *)C.val;
+    const long long cnt = ctl->bin_count[bin];
+    if ((long long)blockIdx.x * NW >= cnt) return;  // no row for this block
     for (int s = lane; s < mp; s += 32) acc[s] = Sr<SR>::zero();
     msk[lane] = 0u;
     __syncwarp();
     long long nnz_acc = 0;
-    const long long cnt = ctl->bin_count[bin];
     for (long long it = (long long)blockIdx.x * NW + w; it < cnt; it += (long long)gridDim.x * NW) {
         const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
         group_products<SR, 32>(A, B, i, 0xffffffffu, [&](int32_t j, T v) {
@@ -1264,11 +1310,12 @@ k_num_cta_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask
     T *acc = (T *)smem;
     uint32_t *msk = (uint32_t *)(acc + mp);
     T *Cv = (T *)C.val;
+    const long long cnt = ctl->bin_count[bin];
+    if (blockIdx.x >= cnt) return;  // no row for this block
     for (int s = tid; s < mp; s += 512) acc[s] = Sr<SR>::zero();
     if (tid < 32) msk[tid] = 0u;
     __syncthreads();
     long long nnz_acc = 0;
-    const long long cnt = ctl->bin_count[bin];
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
         const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
         group_products<SR, 32>(A, B, i, 0xffffffffu, [&](int32_t j, T v) {
@@ -1523,16 +1570,17 @@ static void launch_cta_hash(const MatView &A, const MatView &B, const MatView &C
                             unsigned mask, int bin, cudaStream_t s, int num_sms) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
+    constexpr int NT = LOG_TS <= 12 ? 256 : (LOG_TS == 13 ? 512 : 1024);
     const size_t smem = (size_t)TS * (sizeof(T) + sizeof(int32_t));
     static bool set = false;
     if (!set) {
-        cudaFuncSetAttribute(k_num_cta_hash<SR, LOG_TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_num_cta_hash<SR, LOG_TS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         set = true;
     }
     int per_sm = (int)((200 * 1024) / (smem + 8 * 1024));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 8) per_sm = 8;
-    launch_k(k_num_cta_hash<SR, LOG_TS>, grid_for(num_sms * per_sm, J.rows_hint, 1), 256, smem, s, A, B, C, J, ctl,
+    launch_k(k_num_cta_hash<SR, LOG_TS, NT>, grid_for(num_sms * per_sm, J.rows_hint, 1), NT, smem, s, A, B, C, J, ctl,
              mask, bin);
 }
 
@@ -1544,10 +1592,11 @@ static void launch_cluster_hash(const MatView &A, const MatView &B, const MatVie
                                 unsigned mask, int bin, cudaStream_t s, int num_sms) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
+    constexpr int NT = LOG_TS == 13 ? 512 : 1024;  // as the CTA kernels: warps per SM for the larger tables
     const size_t smem = (size_t)TS * (sizeof(T) + sizeof(int32_t));
     static bool set = false;
     if (!set) {
-        cudaFuncSetAttribute(k_num_cluster_hash<SR, LOG_TS, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_num_cluster_hash<SR, LOG_TS, CL, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         set = true;
     }
     int per_sm = (int)((200 * 1024) / (smem + 8 * 1024));
@@ -1557,7 +1606,7 @@ static void launch_cluster_hash(const MatView &A, const MatView &B, const MatVie
     if (clusters < 1) clusters = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(clusters * CL));
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(NT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -1571,7 +1620,7 @@ static void launch_cluster_hash(const MatView &A, const MatView &B, const MatVie
     // status bits of the stages before the recompute (see the split kernel)
     const unsigned early = mask & (ST_INVALID | ST_AB_STAGE | ST_AB_ARENA);
     // a failed launch stays in the runtime's last error, which the caller checks
-    cudaLaunchKernelEx(&cfg, k_num_cluster_hash<SR, LOG_TS, CL>, A, B, C, J, ctl, early, bin);
+    cudaLaunchKernelEx(&cfg, k_num_cluster_hash<SR, LOG_TS, CL, NT>, A, B, C, J, ctl, early, bin);
     __atomic_fetch_add(&launch_counter(), 1ull, __ATOMIC_RELAXED);
 }
 
