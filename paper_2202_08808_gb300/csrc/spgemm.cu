@@ -1545,6 +1545,21 @@ static unsigned grid_for(int64_t full, int64_t rows, int64_t per_block) {
     return (unsigned)std::max<int64_t>(1, std::min(full, need));
 }
 
+// Blocks of `kern` resident per SM at nt threads and smem dynamic bytes
+// (registers, shared memory and the thread limit all counted), with the
+// shared-memory carveout at its maximum: the hash tables live there.
+template <typename K>
+static int resident_per_sm(K kern, int nt, size_t smem) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nt, smem) != cudaSuccess || nb < 1) {
+        cudaGetLastError();  // the launch itself reports a kernel that cannot run
+        nb = 1;
+    }
+    return nb;
+}
+
 template <int SR, int LOG_TS, int G, int NW>
 static void launch_group_hash(const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl,
                               unsigned mask, int bin, cudaStream_t s, int num_sms) {
@@ -1552,15 +1567,7 @@ static void launch_group_hash(const MatView &A, const MatView &B, const MatView 
     constexpr int TS = 1 << LOG_TS;
     constexpr int NG = NW * (32 / G);
     const size_t smem = (size_t)NG * ((TS <= 64 ? 2 : 1) * TS) * (sizeof(T) + sizeof(int32_t));
-    static bool set = false;
-    if (!set) {
-        cudaFuncSetAttribute(k_num_group_hash<SR, LOG_TS, G, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        set = true;
-    }
-    int per_sm = (int)((200 * 1024) / (smem + 1024));
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 2048 / (NW * 32)) per_sm = 2048 / (NW * 32);
+    static const int per_sm = resident_per_sm(k_num_group_hash<SR, LOG_TS, G, NW>, NW * 32, smem);
     launch_k(k_num_group_hash<SR, LOG_TS, G, NW>, grid_for(num_sms * per_sm, J.rows_hint, NG), NW * 32, smem, s, A, B,
              C, J, ctl, mask, bin);
 }
@@ -1572,14 +1579,8 @@ static void launch_cta_hash(const MatView &A, const MatView &B, const MatView &C
     constexpr int TS = 1 << LOG_TS;
     constexpr int NT = LOG_TS <= 12 ? 256 : (LOG_TS == 13 ? 512 : 1024);
     const size_t smem = (size_t)TS * (sizeof(T) + sizeof(int32_t));
-    static bool set = false;
-    if (!set) {
-        cudaFuncSetAttribute(k_num_cta_hash<SR, LOG_TS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        set = true;
-    }
-    int per_sm = (int)((200 * 1024) / (smem + 8 * 1024));
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 8) per_sm = 8;
+    // one wave of resident CTAs: a second, partial wave would only lengthen the tail
+    static const int per_sm = std::min(8, resident_per_sm(k_num_cta_hash<SR, LOG_TS, NT>, NT, smem));
     launch_k(k_num_cta_hash<SR, LOG_TS, NT>, grid_for(num_sms * per_sm, J.rows_hint, 1), NT, smem, s, A, B, C, J, ctl,
              mask, bin);
 }
