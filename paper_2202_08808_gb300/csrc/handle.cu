@@ -252,6 +252,18 @@ struct dspg_handle {
     Ctl *hctl_dev = nullptr;  // its device address
     UpdWs wA, wB, wAT;
     CWs wc;
+    // grow-only scratch of the read calls (row list, lengths, row pointers,
+    // gathered rows, the affected-row sort), so that reading results between
+    // batches allocates nothing; a read larger than kReadKeep bytes per
+    // buffer allocates for the call instead of holding that memory
+    struct ReadWs {
+        DBuf<int32_t> rows, lens, c, r;
+        DBuf<int64_t> rp, scan, listed, st, so;
+        DBuf<unsigned> n_listed;
+        DBuf<char> v;
+        DBuf<uint64_t> k0, k1;
+        DBuf<uint32_t> i0, i1, counts;
+    } rd;
     BatchIn inA, inB;
     InArgs *d_args = nullptr;  // device: where the A, B and forwarded batches are (read by the sorts)
     InArgs *h_args = nullptr;  // pinned, mapped host mirror, fetched by the pipeline's first step
@@ -398,20 +410,35 @@ void regrow(dspg_handle *h, DevMat &M, cudaStream_t s) {
 
 // Canonical CSR copy of M's rows (all rows when rows == nullptr) into device
 // buffers; returns nnz.  rowptr_out has n+1 entries.
-int64_t mat_rowptr(dspg_handle *h, DevMat &M, const int32_t *rows, int64_t n, DBuf<int64_t> &rowptr,
-                   cudaStream_t s) {
-    DBuf<int32_t> lens;
+constexpr int64_t kReadKeep = int64_t(256) << 20;  // bytes per kept read buffer
+
+// Room for `need` elements: the handle's kept buffer while it stays within
+// kReadKeep bytes, else `local` (freed when the caller returns).
+template <typename T>
+T *read_scratch(DBuf<T> &keep, DBuf<T> &local, int64_t need) {
+    need = std::max<int64_t>(need, 1);
+    if ((int64_t)sizeof(T) * need <= kReadKeep) {
+        keep.reserve(need);
+        return keep.p;
+    }
+    local.reserve(need);
+    return local.p;
+}
+
+// Row pointers of rows[n] of M (every row when rows is NULL) into rowptr
+// (room for n + 1); returns their total length.
+int64_t mat_rowptr(dspg_handle *h, DevMat &M, const int32_t *rows, int64_t n, int64_t *rowptr, cudaStream_t s) {
+    DBuf<int32_t> lens_l;
+    DBuf<int64_t> tmp_l;
     const int32_t *lp = M.len.p;
     if (rows) {
-        lens.reserve(n);
-        lens_of_rows(rows, n, M.len.p, lens.p, s);
-        lp = lens.p;
+        int32_t *lens = read_scratch(h->rd.lens, lens_l, n);
+        lens_of_rows(rows, n, M.len.p, lens, s);
+        lp = lens;
     }
-    rowptr.reserve(n + 1);
-    DBuf<int64_t> tmp;
-    tmp.reserve(scan_tmp_entries(n) + 1);
-    scan_i32_to_i64(lp, rowptr.p, n, tmp.p, s);
-    return read_i64(rowptr.p + n, s);
+    int64_t *tmp = read_scratch(h->rd.scan, tmp_l, scan_tmp_entries(n) + 1);
+    scan_i32_to_i64(lp, rowptr, n, tmp, s);
+    return read_i64(rowptr + n, s);
 }
 
 void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
@@ -608,7 +635,8 @@ void static_recompute(dspg_handle *h, cudaStream_t s) {
 void build_transpose(dspg_handle *h, cudaStream_t s) {
     DevMat &A = h->A;
     DBuf<int64_t> rowptr;
-    const int64_t nnz = mat_rowptr(h, A, nullptr, A.nrows, rowptr, s);
+    rowptr.reserve(A.nrows + 1);
+    const int64_t nnz = mat_rowptr(h, A, nullptr, A.nrows, rowptr.p, s);
     DBuf<int32_t> col;
     col.reserve(nnz + 1);
     gather_rows_out(nullptr, A.nrows, A.view(), rowptr.p, col.p, nullptr, 0, s, h->num_sms);
@@ -985,38 +1013,39 @@ void init_slack_from_csr(dspg_handle *h, DevMat &M, const dspg_csr *m, cudaStrea
 
 int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, int64_t *rowptr, int32_t *col,
                  void *val, int on_device, cudaStream_t s) {
-    DBuf<int32_t> rows_d;
+    DBuf<int32_t> rows_l;
     const int32_t *rows = nullptr;
     int64_t n = M.nrows;
     if (rows_in) {
         n = nr;
         if (on_device) rows = rows_in;
         else {
-            rows_d.reserve(std::max<int64_t>(n, 1));
-            if (n > 0) CK(cudaMemcpyAsync(rows_d.p, rows_in, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-            rows = rows_d.p;
+            int32_t *rows_d = read_scratch(h->rd.rows, rows_l, n);
+            if (n > 0) CK(cudaMemcpyAsync(rows_d, rows_in, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+            rows = rows_d;
         }
     }
-    DBuf<int64_t> rp;
+    DBuf<int64_t> rp_l;
+    int64_t *rp = read_scratch(h->rd.rp, rp_l, n + 1);
     const int64_t nnz = mat_rowptr(h, M, rows, n, rp, s);
     if (!rowptr) return nnz;
     // rows too long to sort in shared memory are listed, then sorted together
     const int64_t list_cap = nnz / 16385 + 1;
-    DBuf<unsigned> n_listed;
-    DBuf<int64_t> listed;
-    n_listed.reserve(1);
-    listed.reserve(list_cap);
-    CK(cudaMemsetAsync(n_listed.p, 0, sizeof(unsigned), s));
+    DBuf<int64_t> listed_l;
+    h->rd.n_listed.reserve(1);
+    unsigned *n_listed = h->rd.n_listed.p;
+    int64_t *listed = read_scratch(h->rd.listed, listed_l, list_cap);
+    CK(cudaMemsetAsync(n_listed, 0, sizeof(unsigned), s));
     auto sort_out = [&](int32_t *oc, void *ov) {
-        sort_rows(rp.p, n, oc, ov, M.vsize, n_listed.p, listed.p, list_cap, s, h->num_sms);
+        sort_rows(rp, n, oc, ov, M.vsize, n_listed, listed, list_cap, s, h->num_sms);
         unsigned nl = 0;
-        CK(cudaMemcpyAsync(&nl, n_listed.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&nl, n_listed, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (nl == 0) return;
         if ((int64_t)nl > list_cap) throw Err(DSPG_ERR_CUDA, "more long rows than the read can hold");
         std::vector<int64_t> lh(nl), lo(nl), hi(nl), rph(n + 1);
-        CK(cudaMemcpyAsync(lh.data(), listed.p, sizeof(int64_t) * nl, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(rph.data(), rp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(lh.data(), listed, sizeof(int64_t) * nl, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(rph.data(), rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         for (unsigned k = 0; k < nl; k++) {
             lo[k] = rph[lh[k]];
@@ -1052,26 +1081,26 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
             CK(cudaMemcpyAsync(d_pre.p, pre.data(), sizeof(int64_t) * (nk + 1), cudaMemcpyHostToDevice, s));
             CK(cudaMemcpyAsync(d_list.p, lh.data() + k0, sizeof(int64_t) * nk, cudaMemcpyHostToDevice, s));
             SortScratch w{kk0.p, kk1.p, ii0.p, ii1.p, counts.p, scan_tmp.p, scan_out.p, tcol.p, (void *)tval.p};
-            sort_listed_rows(rp.p, d_list.p, d_pre.p, nk, total, cb, oc, ov, M.vsize, w, s, h->num_sms);
+            sort_listed_rows(rp, d_list.p, d_pre.p, nk, total, cb, oc, ov, M.vsize, w, s, h->num_sms);
             CK(cudaStreamSynchronize(s));
             k0 = k1;
         }
     };
     if (on_device) {
-        CK(cudaMemcpyAsync(rowptr, rp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
-        gather_rows_out(rows, n, M.view(), rp.p, col, val, M.vsize, s, h->num_sms);
+        CK(cudaMemcpyAsync(rowptr, rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
+        gather_rows_out(rows, n, M.view(), rp, col, val, M.vsize, s, h->num_sms);
         sort_out(col, val);
     } else {
-        DBuf<int32_t> c;
-        DBuf<char> v;
-        c.reserve(std::max<int64_t>(nnz, 1));
-        v.reserve(std::max<int64_t>(nnz, 1) * std::max(M.vsize, 1));
-        gather_rows_out(rows, n, M.view(), rp.p, c.p, v.p, M.vsize, s, h->num_sms);
-        sort_out(c.p, M.vsize ? (void *)v.p : nullptr);
-        CK(cudaMemcpyAsync(rowptr, rp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+        DBuf<int32_t> c_l;
+        DBuf<char> v_l;
+        int32_t *c = read_scratch(h->rd.c, c_l, nnz);
+        char *v = read_scratch(h->rd.v, v_l, nnz * std::max(M.vsize, 1));
+        gather_rows_out(rows, n, M.view(), rp, c, v, M.vsize, s, h->num_sms);
+        sort_out(c, M.vsize ? (void *)v : nullptr);
+        CK(cudaMemcpyAsync(rowptr, rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
         if (nnz > 0) {
-            if (col) CK(cudaMemcpyAsync(col, c.p, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s));
-            if (val) CK(cudaMemcpyAsync(val, v.p, (size_t)M.vsize * nnz, cudaMemcpyDeviceToHost, s));
+            if (col) CK(cudaMemcpyAsync(col, c, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s));
+            if (val) CK(cudaMemcpyAsync(val, v, (size_t)M.vsize * nnz, cudaMemcpyDeviceToHost, s));
         }
         CK(cudaStreamSynchronize(s));
     }
@@ -1417,20 +1446,18 @@ dspg_status dspg_last_affected(dspg_handle *h, int64_t *count, int32_t *rows, in
         if (*count < n) throw Err(DSPG_ERR_INVALID, "rows buffer too small");
         *count = n;
         if (n == 0) return DSPG_OK;
-        DBuf<int32_t> tmp;
-        tmp.reserve(n);
-        CK(cudaMemcpyAsync(tmp.p, h->wc.R.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-        DBuf<uint64_t> k0, k1;
-        DBuf<uint32_t> i0, i1, counts;
-        DBuf<int64_t> st, so;
-        k0.reserve(n); k1.reserve(n); i0.reserve(n); i1.reserve(n);
+        // R is at most one entry per row of A: its sort buffers are kept
+        dspg_handle::ReadWs &w = h->rd;
+        w.r.reserve(n);
+        CK(cudaMemcpyAsync(w.r.p, h->wc.R.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        w.k0.reserve(n); w.k1.reserve(n); w.i0.reserve(n); w.i1.reserve(n);
         int64_t cnt;
         sort_tmp_sizes(n, &cnt);
-        counts.reserve(cnt);
-        so.reserve(cnt + 1);
-        st.reserve(scan_tmp_entries(cnt) + 1);
-        sort_i32_values(tmp.p, n, bits_for(h->A.nrows), k0.p, k1.p, i0.p, i1.p, counts.p, st.p, so.p, s);
-        CK(cudaMemcpyAsync(rows, tmp.p, sizeof(int32_t) * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        w.counts.reserve(cnt);
+        w.so.reserve(cnt + 1);
+        w.st.reserve(scan_tmp_entries(cnt) + 1);
+        sort_i32_values(w.r.p, n, bits_for(h->A.nrows), w.k0.p, w.k1.p, w.i0.p, w.i1.p, w.counts.p, w.st.p, w.so.p, s);
+        CK(cudaMemcpyAsync(rows, w.r.p, sizeof(int32_t) * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         return DSPG_OK;
     } catch (const Err &e) {
