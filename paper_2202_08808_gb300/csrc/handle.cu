@@ -184,6 +184,9 @@ struct CWs {
     int gd_ctas = 0;
     // detection
     DBuf<uint32_t> bmR, bmK;
+    // per 256-word chunk of bmR: the offset in R of its rows and their count
+    // (R is ascending within a chunk), so R can be read back in order
+    DBuf<long long> rchunk;
     DBuf<int32_t> K;
     int64_t nrows_b = 0;
     // learned sizing: rows waiting for an estimate, rows whose table overflowed
@@ -454,6 +457,7 @@ void ensure_c_ws(dspg_handle *h, cudaStream_t s) {
     w.bins.reserve((int64_t)NBINS * nn);
     w.bmR.reserve(nn / 32 + 2);
     CK(cudaMemsetAsync(w.bmR.p, 0, sizeof(uint32_t) * w.bmR.n, s));
+    w.rchunk.reserve(2 * ((nn + 31) / 32 / 256 + 1));
     w.est.reserve(nn);
     w.ovf.reserve(nn);
     const int64_t nb = std::max<int64_t>(h->Bm().nrows, 1);
@@ -830,12 +834,12 @@ void pipeline(dspg_handle *h, cudaStream_t s, bool timed, bool capturing) {
     }
     if (fused) {
         // R from the detection's bitmap, in row order within each block's range
-        run_collect_copy(h->wc.bmR.p, words, h->wc.R.p, cjA, h->A.view(), h->vsize, h->ctl, M_AB & ~ST_AB_ARENA,
-                         M_AB, s, h->num_sms);
+        run_collect_copy(h->wc.bmR.p, words, h->wc.R.p, h->wc.rchunk.p, cjA, h->A.view(), h->vsize, h->ctl,
+                         M_AB & ~ST_AB_ARENA, M_AB, s, h->num_sms);
         mark(3, s);
         mark(4, s);
     } else {
-        run_collect_rows(h->wc.bmR.p, words, h->wc.R.p, h->ctl, M_AB, s, h->num_sms);
+        run_collect_rows(h->wc.bmR.p, words, h->wc.R.p, h->wc.rchunk.p, h->ctl, M_AB, s, h->num_sms);
         mark(3, s);
         stage_merge(h, s, merged);
         mark(4, s);
@@ -1446,6 +1450,31 @@ dspg_status dspg_last_affected(dspg_handle *h, int64_t *count, int32_t *rows, in
         if (*count < n) throw Err(DSPG_ERR_INVALID, "rows buffer too small");
         *count = n;
         if (n == 0) return DSPG_OK;
+        if (!on_device) {
+            // R is ascending within each 8192-row chunk of the bitmap it was
+            // collected from; the chunk table says where each chunk's rows
+            // went, so laying the chunks end to end in chunk order sorts R
+            const int64_t nch = (h->A.nrows + 31) / 32 / 256 + 1;
+            std::vector<int32_t> raw(n);
+            std::vector<long long> ch(2 * nch);
+            CK(cudaMemcpyAsync(raw.data(), h->wc.R.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(ch.data(), h->wc.rchunk.p, sizeof(long long) * 2 * nch, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            const int64_t used = ((h->A.nrows + 31) / 32 + 255) / 256;  // chunks the collection visited
+            int64_t o = 0;
+            bool ok = true;
+            for (int64_t c = 0; c < used && ok; c++) {
+                const long long b = ch[2 * c], k = ch[2 * c + 1];
+                ok = k >= 0 && b >= 0 && b + k <= n && o + k <= n;
+                if (ok && k > 0) {
+                    std::memcpy(rows + o, raw.data() + b, sizeof(int32_t) * (size_t)k);
+                    o += k;
+                }
+            }
+            for (int64_t x = 1; ok && x < o; x++) ok = rows[x - 1] < rows[x];
+            if (ok && o == n) return DSPG_OK;
+            // otherwise (R not from one collection): sort it on the device
+        }
         // R is at most one entry per row of A: its sort buffers are kept
         dspg_handle::ReadWs &w = h->rd;
         w.r.reserve(n);

@@ -112,12 +112,13 @@ void run_merge_copy(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsi
 void run_commit(const CommitJob &J, const MatView &M, int vsize, int64_t max_items, Ctl *ctl, unsigned plan_mask,
                 unsigned copy_mask, int slack_min, int slack_div, cudaStream_t s, int num_sms);
 void run_detect_cols(const MatView &AT, const DetectBufs &D, Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms);
-void run_collect_rows(uint32_t *bm, int64_t words, int32_t *R, Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms);
+void run_collect_rows(uint32_t *bm, int64_t words, int32_t *R, long long *chunk, Ctl *ctl, unsigned mask,
+                      cudaStream_t s, int num_sms);
 void run_detect_merge_plan(const MatView &AT, const DetectBufs &D, const UpdJob &J, const MatView &M,
                            const CommitJob &CJ, int vsize, Ctl *ctl, unsigned mask, int slack_min, int slack_div,
                            int64_t max_items, cudaStream_t s, int num_sms);
-void run_collect_copy(uint32_t *bm, int64_t words, int32_t *R, const CommitJob &CJ, const MatView &M, int vsize,
-                      Ctl *ctl, unsigned collect_mask, unsigned copy_mask, cudaStream_t s, int num_sms);
+void run_collect_copy(uint32_t *bm, int64_t words, int32_t *R, long long *chunk, const CommitJob &CJ, const MatView &M,
+                      int vsize, Ctl *ctl, unsigned collect_mask, unsigned copy_mask, cudaStream_t s, int num_sms);
 void run_detect_merge(const MatView &AT, const DetectBufs &D, const UpdJob &J, const MatView &M, int vsize, Ctl *ctl,
                       unsigned mask, cudaStream_t s, int num_sms);
 void run_transpose_feed(const UpdJob &J, int32_t pad_row, int32_t *trow, int32_t *tcol, uint8_t *top, Ctl *ctl,

@@ -410,8 +410,10 @@ __global__ void k_detect_merge(MatView AT, DetectBufs D, long long detect_blocks
 // comes out in row order within each block's range, so the recompute's
 // neighbouring lanes work on neighbouring rows (shared B rows stay in L1).
 // The words are cleared for the next batch.
+// chunk (may be NULL): per 256-word chunk of the bitmap, where its rows went
+// in R and how many (R is ascending within a chunk; chunks land in any order)
 __device__ __forceinline__ void collect_blocks(uint32_t *bm, int64_t words, int32_t *R, Ctl *ctl, long long blk,
-                                               long long nblk) {
+                                               long long nblk, long long *chunk) {
     __shared__ int s_wsum[8];
     __shared__ long long s_base;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -430,6 +432,10 @@ __device__ __forceinline__ void collect_blocks(uint32_t *bm, int64_t words, int3
                 t += v;
             }
             s_base = t ? atomic_add_ll(&ctl->n_affected, t) : 0;
+            if (chunk) {
+                chunk[2 * (b0 / 256)] = s_base;
+                chunk[2 * (b0 / 256) + 1] = t;
+            }
         }
         __syncthreads();
         long long o = s_base + s_wsum[w] + incl - c;
@@ -445,10 +451,10 @@ __device__ __forceinline__ void collect_blocks(uint32_t *bm, int64_t words, int3
     }
 }
 
-__global__ void __launch_bounds__(256) k_collect_rows(uint32_t *bm, int64_t words, int32_t *R, Ctl *ctl,
-                                                      unsigned mask) {
+__global__ void __launch_bounds__(256) k_collect_rows(uint32_t *bm, int64_t words, int32_t *R, long long *chunk,
+                                                      Ctl *ctl, unsigned mask) {
     if (failed(ctl, mask)) return;
-    collect_blocks(bm, words, R, ctl, blockIdx.x, gridDim.x);
+    collect_blocks(bm, words, R, ctl, blockIdx.x, gridDim.x, chunk);
 }
 
 // When B is A the update needs two launches between the classification and
@@ -472,11 +478,11 @@ k_detect_merge_plan(MatView AT, DetectBufs D, long long nd, UpdJob J, MatView M,
 // that did not fail.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_collect_copy(uint32_t *bm, int64_t words, int32_t *R, long long nc, CommitJob CJ, MatView M, Ctl *ctl,
-               unsigned collect_mask, unsigned copy_mask) {
+k_collect_copy(uint32_t *bm, int64_t words, int32_t *R, long long *chunk, long long nc, CommitJob CJ, MatView M,
+               Ctl *ctl, unsigned collect_mask, unsigned copy_mask) {
     if (blockIdx.x < nc) {
         if (failed(ctl, collect_mask)) return;
-        collect_blocks(bm, words, R, ctl, blockIdx.x, nc);
+        collect_blocks(bm, words, R, ctl, blockIdx.x, nc, chunk);
     } else {
         if (failed(ctl, copy_mask)) return;
         commit_copy_blocks<T>(CJ, M, blockIdx.x - nc, gridDim.x - nc);
@@ -497,23 +503,24 @@ void run_detect_merge_plan(const MatView &AT, const DetectBufs &D, const UpdJob 
         launch_k(k_detect_merge_plan<int32_t>, g, 256, 0, s, AT, D, nd, J, M, CJ, nm, ctl, mask, slack_min, slack_div);
 }
 
-void run_collect_copy(uint32_t *bm, int64_t words, int32_t *R, const CommitJob &CJ, const MatView &M, int vsize,
-                      Ctl *ctl, unsigned collect_mask, unsigned copy_mask, cudaStream_t s, int num_sms) {
+void run_collect_copy(uint32_t *bm, int64_t words, int32_t *R, long long *chunk, const CommitJob &CJ, const MatView &M,
+                      int vsize, Ctl *ctl, unsigned collect_mask, unsigned copy_mask, cudaStream_t s, int num_sms) {
     long long nc = (words + 255) / 256;
     if (nc > (long long)num_sms * 8) nc = (long long)num_sms * 8;
     if (nc < 1) nc = 1;
     const unsigned g = (unsigned)(nc + (long long)num_sms * 8);
     if (vsize == 8)
-        launch_k(k_collect_copy<double>, g, 256, 0, s, bm, words, R, nc, CJ, M, ctl, collect_mask, copy_mask);
+        launch_k(k_collect_copy<double>, g, 256, 0, s, bm, words, R, chunk, nc, CJ, M, ctl, collect_mask, copy_mask);
     else
-        launch_k(k_collect_copy<int32_t>, g, 256, 0, s, bm, words, R, nc, CJ, M, ctl, collect_mask, copy_mask);
+        launch_k(k_collect_copy<int32_t>, g, 256, 0, s, bm, words, R, chunk, nc, CJ, M, ctl, collect_mask, copy_mask);
 }
 
-void run_collect_rows(uint32_t *bm, int64_t words, int32_t *R, Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms) {
+void run_collect_rows(uint32_t *bm, int64_t words, int32_t *R, long long *chunk, Ctl *ctl, unsigned mask,
+                      cudaStream_t s, int num_sms) {
     int64_t g = (words + 255) / 256;
     if (g > (int64_t)num_sms * 8) g = (int64_t)num_sms * 8;
     if (g < 1) g = 1;
-    launch_k(k_collect_rows, (unsigned)g, 256, 0, s, bm, words, R, ctl, mask);
+    launch_k(k_collect_rows, (unsigned)g, 256, 0, s, bm, words, R, chunk, ctl, mask);
 }
 
 // Structural changes of A, forwarded to its transposed pattern: INS (i,k)
