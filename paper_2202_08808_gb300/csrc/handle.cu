@@ -266,7 +266,19 @@ struct dspg_handle {
         DBuf<char> v;
         DBuf<uint64_t> k0, k1;
         DBuf<uint32_t> i0, i1, counts;
+        std::vector<int32_t> h_r;     // R as collected (host)
+        std::vector<long long> h_ch;  // its chunk table (host)
     } rd;
+    // C's generation (bumped by every call that may change C) and the row
+    // list whose row pointers rd.rp holds, so the fill call of a two-call
+    // read of C's rows reuses what its count call computed
+    uint64_t c_serial = 0;
+    struct ReadKey {
+        bool valid = false;
+        uint64_t serial = 0;
+        int64_t nnz = 0;
+        std::vector<int32_t> rows;
+    } rd_key;
     BatchIn inA, inB;
     InArgs *d_args = nullptr;  // device: where the A, B and forwarded batches are (read by the sorts)
     InArgs *h_args = nullptr;  // pinned, mapped host mirror, fetched by the pipeline's first step
@@ -573,6 +585,7 @@ void numeric_branches(dspg_handle *h, cudaStream_t s, const CJob &J) {
 // C is laid out from the counts instead.  The arena is reused when large
 // enough.
 void static_recompute(dspg_handle *h, cudaStream_t s) {
+    h->c_serial++;
     ensure_c_ws(h, s);
     DevMat &C = h->C;
     const int64_t n = h->A.nrows;
@@ -1020,18 +1033,39 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
     DBuf<int32_t> rows_l;
     const int32_t *rows = nullptr;
     int64_t n = M.nrows;
-    if (rows_in) {
-        n = nr;
-        if (on_device) rows = rows_in;
-        else {
-            int32_t *rows_d = read_scratch(h->rd.rows, rows_l, n);
-            if (n > 0) CK(cudaMemcpyAsync(rows_d, rows_in, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-            rows = rows_d;
-        }
-    }
+    if (rows_in) n = nr;
+    // host rows of C that the last read of this generation of C listed too:
+    // their row pointers are still in the kept buffer
+    dspg_handle::ReadKey &key = h->rd_key;
+    const bool keyed = rows_in && !on_device && &M == &h->C;
+    const bool hit = keyed && key.valid && key.serial == h->c_serial && (int64_t)key.rows.size() == n &&
+                     (n == 0 || std::memcmp(key.rows.data(), rows_in, sizeof(int32_t) * (size_t)n) == 0);
+    key.valid = false;  // the kept row list and row pointers are rewritten below unless this is a hit
     DBuf<int64_t> rp_l;
-    int64_t *rp = read_scratch(h->rd.rp, rp_l, n + 1);
-    const int64_t nnz = mat_rowptr(h, M, rows, n, rp, s);
+    int64_t *rp;
+    int64_t nnz;
+    if (hit) {
+        rows = h->rd.rows.p;
+        rp = h->rd.rp.p;
+        nnz = key.nnz;
+    } else {
+        if (rows_in) {
+            if (on_device) rows = rows_in;
+            else {
+                int32_t *rows_d = read_scratch(h->rd.rows, rows_l, n);
+                if (n > 0) CK(cudaMemcpyAsync(rows_d, rows_in, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+                rows = rows_d;
+            }
+        }
+        rp = read_scratch(h->rd.rp, rp_l, n + 1);
+        nnz = mat_rowptr(h, M, rows, n, rp, s);
+    }
+    if (keyed && rows == h->rd.rows.p && rp == h->rd.rp.p) {
+        if (!hit) key.rows.assign(rows_in, rows_in + n);
+        key.serial = h->c_serial;
+        key.nnz = nnz;
+        key.valid = true;
+    }
     if (!rowptr) return nnz;
     // rows too long to sort in shared memory are listed, then sorted together
     const int64_t list_cap = nnz / 16385 + 1;
@@ -1113,6 +1147,7 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
 
 // Checks one batch pair and gets the handle's buffers and inputs ready.
 void prepare_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, cudaStream_t s) {
+    h->c_serial++;
     const int64_t nA = dA ? dA->n : 0, nB = dB ? dB->n : 0;
     if (nA < 0 || nB < 0) throw Err(DSPG_ERR_INVALID, "negative batch size");
     if (nA > INT32_MAX / 2 || nB > INT32_MAX / 2) throw Err(DSPG_ERR_INVALID, "batch too large");
@@ -1455,8 +1490,10 @@ dspg_status dspg_last_affected(dspg_handle *h, int64_t *count, int32_t *rows, in
             // collected from; the chunk table says where each chunk's rows
             // went, so laying the chunks end to end in chunk order sorts R
             const int64_t nch = (h->A.nrows + 31) / 32 / 256 + 1;
-            std::vector<int32_t> raw(n);
-            std::vector<long long> ch(2 * nch);
+            std::vector<int32_t> &raw = h->rd.h_r;
+            std::vector<long long> &ch = h->rd.h_ch;
+            if ((int64_t)raw.size() < n) raw.resize(n);
+            if ((int64_t)ch.size() < 2 * nch) ch.resize(2 * nch);
             CK(cudaMemcpyAsync(raw.data(), h->wc.R.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
             CK(cudaMemcpyAsync(ch.data(), h->wc.rchunk.p, sizeof(long long) * 2 * nch, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));

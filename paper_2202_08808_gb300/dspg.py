@@ -186,6 +186,29 @@ def _vdtype(sr: int):
     return np.float64 if sr == PLUS_TIMES_F64 else np.int32
 
 
+_PINNED = {}
+
+
+def _host_empty(n: int, dtype) -> np.ndarray:
+    """An uninitialised host array for results copied from the device: page-
+    locked memory from torch's caching host allocator when a GPU is there (the
+    copy runs at full speed and touches no fresh pages; freed arrays give their
+    blocks back for the next read), else plain numpy memory."""
+    if _PINNED.get("ok") is None:
+        try:
+            import torch
+            _PINNED["ok"] = bool(torch.cuda.is_available())
+            _PINNED["torch"] = torch
+        except ImportError:
+            _PINNED["ok"] = False
+    if not _PINNED["ok"]:
+        return np.empty(n, dtype)
+    torch = _PINNED["torch"]
+    tdt = {np.dtype(np.int64): torch.int64, np.dtype(np.int32): torch.int32,
+           np.dtype(np.float64): torch.float64}[np.dtype(dtype)]
+    return torch.empty(n, dtype=tdt, pin_memory=True).numpy()
+
+
 def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
@@ -283,9 +306,9 @@ class DynamicSpGEMM:
         nnz = C.c_int64()
         self._check(fn(self._h, C.byref(nnz), None, None, None, 0, s))
         n = self.info()["n"]
-        rp = np.empty(n + 1, np.int64)
-        col = np.empty(nnz.value, np.int32)
-        val = np.empty(nnz.value, _vdtype(self.sr))
+        rp = _host_empty(n + 1, np.int64)
+        col = _host_empty(nnz.value, np.int32)
+        val = _host_empty(nnz.value, _vdtype(self.sr))
         self._check(fn(self._h, C.byref(nnz), rp.ctypes.data, col.ctypes.data, val.ctypes.data, 0, s))
         return CsrArrays(n, ncols, rp, col, val)
 
@@ -317,9 +340,9 @@ class DynamicSpGEMM:
         s = _stream(stream)
         self._check(self._lib.dspg_read_rows_C(self._h, rows.ctypes.data, rows.shape[0], C.byref(nnz), None, None,
                                                None, 0, s))
-        rp = np.empty(rows.shape[0] + 1, np.int64)
-        col = np.empty(nnz.value, np.int32)
-        val = np.empty(nnz.value, _vdtype(self.sr))
+        rp = _host_empty(rows.shape[0] + 1, np.int64)
+        col = _host_empty(nnz.value, np.int32)
+        val = _host_empty(nnz.value, _vdtype(self.sr))
         self._check(self._lib.dspg_read_rows_C(self._h, rows.ctypes.data, rows.shape[0], C.byref(nnz),
                                                rp.ctypes.data, col.ctypes.data, val.ctypes.data, 0, s))
         return rp, col, val
@@ -328,7 +351,7 @@ class DynamicSpGEMM:
         cnt = C.c_int64()
         s = _stream(stream)
         self._check(self._lib.dspg_last_affected(self._h, C.byref(cnt), None, 0, s))
-        out = np.empty(cnt.value, np.int32)
+        out = _host_empty(cnt.value, np.int32)
         self._check(self._lib.dspg_last_affected(self._h, C.byref(cnt), out.ctypes.data, 0, s))
         return out
 

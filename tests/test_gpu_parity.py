@@ -525,3 +525,27 @@ def test_rows_in_cluster_tables_and_beyond(dspg, sr):
     rp, col, val = g.read_rows_C(rows)
     o_rp, o_col, o_val = Ao.multiply_rows(Bo, rows)
     assert np.array_equal(rp, o_rp) and np.array_equal(col, o_col)
+
+
+def test_row_reads_between_batches(dspg):
+    """A two-call read of C's rows (count, then fill) reuses the count's row
+    pointers only for the same rows of the same C: the affected rows read
+    twice, another list of the same length, a read of all of C in between,
+    and the next batches each give the oracle's rows."""
+    sr = PLUS_TIMES_F64
+    n = 4000
+    A = er_matrix(n, 6, seed=71, kind=sr)
+    g = dspg.DynamicSpGEMM(A)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    rng = np.random.default_rng(72)
+    for t in range(3):
+        _apply_both(g, Ao, Co, random_batch(n, n, 400, 73 + t, sr, A=A))
+        R = g.last_affected()
+        assert R.size > 0
+        _sampled_rows(g, Ao, Ao, R, f"batch {t}: R")
+        _sampled_rows(g, Ao, Ao, R, f"batch {t}: R again")
+        other = np.sort(rng.choice(n, size=R.size, replace=False)).astype(np.int32)
+        _sampled_rows(g, Ao, Ao, other, f"batch {t}: other rows")
+        g.read_C()
+        _sampled_rows(g, Ao, Ao, R, f"batch {t}: R after a read of C")
