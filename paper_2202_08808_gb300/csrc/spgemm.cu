@@ -994,7 +994,7 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
 // clears the slots it used.  Every CTA passes the same cluster barriers: the
 // row loop and the status test are uniform.
 template <int SR, int LOG_TS, int CL, int NT>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, LOG_TS == 13 ? 2 : 1)  // two 8192-slot tables fit an SM
 k_num_cluster_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned early_mask, int bin) {
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
@@ -1595,14 +1595,31 @@ static void launch_cluster_hash(const MatView &A, const MatView &B, const MatVie
     constexpr int TS = 1 << LOG_TS;
     constexpr int NT = LOG_TS == 13 ? 512 : 1024;  // as the CTA kernels: warps per SM for the larger tables
     const size_t smem = (size_t)TS * (sizeof(T) + sizeof(int32_t));
-    static bool set = false;
-    if (!set) {
+    // as many clusters as can be resident at once (the occupancy query for
+    // this cluster shape), so the grid is one wave
+    static long long max_clusters = 0;
+    if (!max_clusters) {
         cudaFuncSetAttribute(k_num_cluster_hash<SR, LOG_TS, CL, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        set = true;
+        cudaFuncSetAttribute(k_num_cluster_hash<SR, LOG_TS, CL, NT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaLaunchConfig_t q = {};
+        q.gridDim = dim3((unsigned)(CL * num_sms));
+        q.blockDim = dim3(NT);
+        q.dynamicSmemBytes = smem;
+        cudaLaunchAttribute qa[1];
+        qa[0].id = cudaLaunchAttributeClusterDimension;
+        qa[0].val.clusterDim.x = CL;
+        qa[0].val.clusterDim.y = 1;
+        qa[0].val.clusterDim.z = 1;
+        q.attrs = qa;
+        q.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, k_num_cluster_hash<SR, LOG_TS, CL, NT>, &q) != cudaSuccess || nc < 1) {
+            cudaGetLastError();  // the launch reports a shape that cannot run
+            nc = std::max(1, num_sms / CL);
+        }
+        max_clusters = nc;
     }
-    int per_sm = (int)((200 * 1024) / (smem + 8 * 1024));
-    if (per_sm < 1) per_sm = 1;
-    long long clusters = (long long)num_sms * per_sm / CL;
+    long long clusters = max_clusters;
     if (clusters > J.rows_hint) clusters = J.rows_hint;
     if (clusters < 1) clusters = 1;
     cudaLaunchConfig_t cfg = {};
