@@ -147,8 +147,11 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
 
 /* Read C in canonical CSR (rows in order, columns ascending) into caller
  * buffers: rowptr[nrows+1], col[nnz], val[nnz], host or device per
- * on_device.  Two-call convention: with rowptr == NULL only *nnz_out is
- * written. */
+ * on_device (host buffers may be pageable or page-locked; page-locked ones
+ * are copied to at full speed).  Two-call convention: with rowptr == NULL
+ * only *nnz_out is written.  The handle keeps the read's device scratch
+ * (up to 256 MiB per buffer) for later reads; a larger read allocates and
+ * frees its scratch within the call. */
 dspg_status dspg_read_C(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32_t *col, void *val,
                         int on_device, void *stream);
 
@@ -157,7 +160,9 @@ dspg_status dspg_read_A(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32
                         int on_device, void *stream);
 
 /* Read selected rows of C: rows[nrows] (host or device per on_device);
- * rowptr[nrows+1], col, val as in dspg_read_C, in the order given. */
+ * rowptr[nrows+1], col, val as in dspg_read_C, in the order given.  The
+ * fill call reuses the row pointers its count call computed when the host
+ * row list is the same (by content) and C has not changed in between. */
 dspg_status dspg_read_rows_C(dspg_handle *h, const int32_t *rows, int64_t nrows, int64_t *nnz_out,
                              int64_t *rowptr, int32_t *col, void *val, int on_device, void *stream);
 
