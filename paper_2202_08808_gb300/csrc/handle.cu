@@ -1172,7 +1172,7 @@ void prepare_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *d
 // on s) until the status is clean; errors become exceptions.
 void recover(dspg_handle *h, cudaStream_t s) {
     const int64_t nA = h->inA.n, nB = h->inB.n;
-        for (int iter = 0; iter < 8 && h->hctl->status; iter++) {
+    for (int iter = 0; iter < 8 && h->hctl->status; iter++) {
         const unsigned st = h->hctl->status;
         if (st & ST_INVALID) throw Err(DSPG_ERR_INVALID, "batch entry out of range or with an invalid value/op");
         if (st & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, overflow_message(h->hctl));
@@ -1231,7 +1231,7 @@ void recover(dspg_handle *h, cudaStream_t s) {
 
 void fill_stats(dspg_handle *h, dspg_batch_stats *stats, int64_t compactions0) {
     const int64_t nA = h->inA.n, nB = h->inB.n;
-        h->last_nR = h->hctl->n_affected;
+    h->last_nR = h->hctl->n_affected;
     if (stats) {
         const Ctl &c = *h->hctl;
         std::memset(stats, 0, sizeof(*stats));
