@@ -84,9 +84,14 @@ class Server:
     updates of A; C = A A in the intended use)."""
 
     def __init__(self, g, max_wave: int = 32, max_wave_entries: int = 1 << 21, hbm_reserve: int = 4 << 30,
-                 read_results: bool = True, hbm_free=None, overtake: bool = False, scan: int | None = None):
+                 read_results: bool = True, hbm_free=None, overtake: bool = False, scan: int | None = None,
+                 bitmap_device: str = "cuda"):
+        """bitmap_device: where the footprint bitmaps live.  The library
+        writes them on the GPU ("cuda"); "cpu" is for driving the scheduling
+        alone with a stand-in for the handle (the host-logic tests)."""
         import torch
         self.g = g
+        self.bitmap_device = bitmap_device
         self.max_wave = max_wave
         self.overtake = overtake  # pass over a conflicting request instead of ending the wave
         self.scan = scan if scan is not None else 4 * max_wave  # queued requests examined per wave
@@ -98,8 +103,8 @@ class Server:
         self.n = info["n"]
         self.c_row_bytes = (info["nnz_c"] / max(self.n, 1)) * (4 + (8 if g.sr == 0 else 4))
         self.words = (self.n + 31) // 32
-        self._union = torch.zeros(self.words, dtype=torch.int32, device="cuda")
-        self._fp = [torch.zeros(self.words, dtype=torch.int32, device="cuda") for _ in range(max_wave)]
+        self._union = torch.zeros(self.words, dtype=torch.int32, device=bitmap_device)
+        self._fp = [torch.zeros(self.words, dtype=torch.int32, device=bitmap_device) for _ in range(max_wave)]
         self._pin = None
         self.waves = 0
         self.conflicts = 0
@@ -112,9 +117,13 @@ class Server:
         n = len(b)
         if self._pin is None or self._pin[0].shape[0] < n:
             cap = max(n, 1024) * 2
-            self._pin = (torch.empty(cap, dtype=torch.int32).pin_memory(), torch.empty(cap, dtype=torch.int32).pin_memory(),
-                         torch.empty(cap, dtype=torch.from_numpy(b.val[:0]).dtype).pin_memory(),
-                         torch.empty(cap, dtype=torch.uint8).pin_memory())
+            pin = self.bitmap_device != "cpu"
+
+            def buf(dt):
+                t = torch.empty(cap, dtype=dt)
+                return t.pin_memory() if pin else t
+
+            self._pin = (buf(torch.int32), buf(torch.int32), buf(torch.from_numpy(b.val[:0]).dtype), buf(torch.uint8))
         r, c, v, o = self._pin
         r[:n].numpy()[:] = b.row
         c[:n].numpy()[:] = b.col
