@@ -179,9 +179,18 @@ class ClockSampler:
         time.sleep(0.3)
         self.proc.terminate()
         self.proc.wait()
+        with open(self.path) as f:
+            out = self.parse(f)
+        os.unlink(self.path)
+        return out
+
+    @staticmethod
+    def parse(lines):
+        """Samples in FIELDS order (csv, no header, no units): the median SM
+        clock, the maximum, and every throttle reason seen Active."""
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -193,7 +202,6 @@ class ClockSampler:
             for n, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
-        os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "samples": len(sm), "reasons": sorted(reasons)}
 

@@ -83,3 +83,14 @@ def test_tuning_candidates_start_with_the_defaults_and_stay_in_range():
         assert c["lanes_min"] in (8, 16, 32) and c["table_shift"] in (0, 1)
         assert 0 <= c["warp_max"] <= 1024 and 0 <= c["cta_max"] <= 16384
     assert len({tuple(sorted(c.items())) for c in cands}) == len(cands)
+
+
+def test_host_result_arrays():
+    """Arrays the binding reads results into: the asked length and dtype
+    (page-locked when a GPU is there, plain numpy memory otherwise)."""
+    import numpy as np
+    from paper_2202_08808_gb300 import dspg as b
+    for dt in (np.int64, np.int32, np.float64):
+        a = b._host_empty(7, dt)
+        assert a.shape == (7,) and a.dtype == np.dtype(dt)
+    assert b._host_empty(0, np.int32).shape == (0,)

@@ -39,3 +39,21 @@ def test_reference_arm_other_ranks_do_no_work():
     p = run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, "--steps", "1", "--warmup", "3")
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def test_clock_samples_are_parsed_for_the_median_and_the_reasons():
+    sys.path.insert(0, ROOT)
+    import bench
+    rows = [
+        "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",  # skipped
+        "short line",
+    ]
+    d = bench.ClockSampler.parse(rows)
+    assert d == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "samples": 3, "reasons": ["sw_power_cap"]}
+    d = bench.ClockSampler.parse([rows[0].replace("Not Active, Not Active, Not Active, Not Active",
+                                                  "Active, Not Active, Active, Not Active")])
+    assert d["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.ClockSampler.parse([])["sm_mhz"] is None
