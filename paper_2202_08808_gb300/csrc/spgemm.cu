@@ -1547,7 +1547,9 @@ static unsigned grid_for(int64_t full, int64_t rows, int64_t per_block) {
 
 // Blocks of `kern` resident per SM at nt threads and smem dynamic bytes
 // (registers, shared memory and the thread limit all counted), with the
-// shared-memory carveout at its maximum: the hash tables live there.
+// shared-memory carveout at its maximum: the hash tables live there.  The
+// launchers keep the answer per kernel for the process, whose handles all
+// run on one GPU model.
 template <typename K>
 static int resident_per_sm(K kern, int nt, size_t smem) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
