@@ -137,3 +137,16 @@ def test_param_count_and_layout():
     W1, b1, W2, b2, W3, b3 = mlp.unpack(p)
     assert W1[0, 1] == 1 and b1[0] == 256 and W2[0, 1] == 321 and b2[0] == 4416 and W3[0, 0] == 4480 and b3[0] == 4544
     assert np.array_equal(mlp.pack(mlp.unpack(p)), p)
+
+
+def test_predict_nnz_worked_value():
+    """The estimate is 2^o - 1 (the inverse of the target y = log2(1 + nnz)).
+    The one-path network of test_network_worked_by_hand gives o = 6 x0 + 1;
+    with x0 = 1 that is o = 7, an estimate of 2^7 - 1 = 127 entries, and
+    with x0 = 0 (an empty A row) o = 1 and the estimate is 1.  A network
+    whose output is the target itself recovers nnz exactly: log2(1 + 127) = 7."""
+    p = _single_path_params()
+    X = np.array([[1.0, 0.7, 0.2, 0.9], [0.0, 3.0, 1.0, 2.0]])
+    est = mlp.predict_nnz(p, X)
+    assert est.tolist() == [127.0, 1.0]
+    assert np.log2(1.0 + est[0]) == 7.0

@@ -434,3 +434,119 @@ def test_golden_hand_worked(name):
     assert R.tolist() == g["R"]
     assert csr_equal(Am.to_csr(), csr(g["A_after"]))
     assert csr_equal(C.to_csr(), csr(g["C_after"]))
+
+
+# ------------------------------------------- the bound and the B != A rows
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_absval_product_is_abs_matmul(seed):
+    """The (+,.) tolerance bound S = |A| |B| (Section 3's product on the
+    entrywise magnitudes): on integer-valued data of both signs every sum is
+    exact, so the oracle's absval product equals numpy's |A| @ |B| bit for
+    bit on the product's pattern, and that pattern is the plain product's.
+    An inflated bound (|a| + |b|, or a fold into a stale accumulator) fails."""
+    A = integer_valued(random_csr(40, 30, 5, seed, PLUS_TIMES_F64), seed, lo=-7, hi=8)
+    B = integer_valued(random_csr(30, 50, 4, seed + 11, PLUS_TIMES_F64), seed + 1, lo=-7, hi=8)
+    Am, Bm = OMat.from_csr(A), OMat.from_csr(B)
+    S = Am.multiply(Bm, absval=True).to_csr()
+    C = Am.multiply(Bm).to_csr()
+    PA, VA = to_dense(A)
+    PB, VB = to_dense(B)
+    want_p = (PA.astype(np.int64) @ PB.astype(np.int64)) > 0
+    want_v = np.abs(VA) @ np.abs(VB)
+    PS, VS = to_dense(S)
+    PC, _ = to_dense(C)
+    assert np.array_equal(PS, want_p) and np.array_equal(PC, want_p)
+    assert np.array_equal(VS[PS], want_v[PS])
+    # the rows-only route of the oracle gives the same bound
+    rows = np.array([0, 7, 13, 39], np.int32)
+    rp, col, val = Am.multiply_rows(Bm, rows, absval=True)
+    for t, i in enumerate(rows):
+        js = col[rp[t]:rp[t + 1]]
+        assert np.array_equal(js, np.nonzero(want_p[i])[0])
+        assert np.array_equal(val[rp[t]:rp[t + 1]], want_v[i, js])
+
+
+def _presence_model(M: CSR, batch: Batch):
+    """Presence of each batch key before and after applying the batch in
+    array order, from a set of (row, col) pairs (Section 4.1 semantics:
+    INSERT and SET store, DELETE removes)."""
+    present = set(zip(M.row_ids().tolist(), M.col.tolist()))
+    pre = np.array([(int(r), int(c)) in present for r, c in zip(batch.row, batch.col)], np.uint8)
+    for r, c, o in zip(batch.row.tolist(), batch.col.tolist(), batch.op.tolist()):
+        if o == OP_DELETE:
+            present.discard((r, c))
+        else:
+            present.add((r, c))
+    post = np.array([(int(r), int(c)) in present for r, c in zip(batch.row, batch.col)], np.uint8)
+    return pre, post, present
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_affected_rows_separate_b_brute_force(seed):
+    """R for C = A B with separate batches of A and B, against Eq. 1's row
+    set written out on dense patterns: R = rows(A*) u {i : A'(i,k) != 0,
+    k in rows(B*)}, where A* (B*) holds the batch keys present before or
+    after the batch.  R must also contain every row whose product changed
+    (the rows of C' - C), and nothing else may enter it: a B batch made
+    partly of deletes of absent entries (no change) and of rows whose column
+    in A' is empty checks that R is not over-inclusive."""
+    rng = np.random.default_rng(seed + 70)
+    n, k, m = 50, 40, 45
+    A = random_csr(n, k, 3, seed, PLUS_TIMES_F64)
+    B = random_csr(k, m, 3, seed + 20, PLUS_TIMES_F64)
+    ba = random_batch(n, k, 12, seed + 5, PLUS_TIMES_F64, A=A)
+    bb = random_batch(k, m, 10, seed + 6, PLUS_TIMES_F64, A=B)
+    # no-op deletes in B rows that A' reads: they change nothing
+    PB, _ = to_dense(B)
+    absent = np.argwhere(~PB)
+    pick = absent[rng.choice(absent.shape[0], size=6, replace=False)]
+    bb = Batch(np.concatenate([bb.row, pick[:, 0].astype(np.int32)]),
+               np.concatenate([bb.col, pick[:, 1].astype(np.int32)]),
+               np.concatenate([bb.val, np.zeros(6)]),
+               np.concatenate([bb.op, np.full(6, OP_DELETE, np.uint8)]))
+    pre_a, post_a, a_after = _presence_model(A, ba)
+    pre_b, post_b, _ = _presence_model(B, bb)
+    star_a = {int(r) for r, p, q in zip(ba.row, pre_a, post_a) if p or q}
+    star_b = {int(r) for r, p, q in zip(bb.row, pre_b, post_b) if p or q}
+    want = set(star_a)
+    for (i, kk) in a_after:
+        if kk in star_b:
+            want.add(i)
+    Am, Bm = OMat.from_csr(A), OMat.from_csr(B)
+    # the oracle's own presence agrees with the set model
+    assert np.array_equal(Am.presence(ba), pre_a) and np.array_equal(Bm.presence(bb), pre_b)
+    Cm = Am.multiply(Bm)
+    C0 = Cm.to_csr()
+    R = oracle.row_dynamic(Am, Cm, ba, Bm, bb)
+    assert R.tolist() == sorted(want)
+    P0, V0 = to_dense(C0)
+    P1, V1 = to_dense(Cm.to_csr())
+    changed = set(np.nonzero((P0 != P1).any(axis=1) | (V0 != V1).any(axis=1))[0].tolist())
+    assert changed <= set(R.tolist())
+
+
+def test_affected_rows_separate_b_worked_example():
+    """A 3 x 3 example by hand.  A has (0,1), (1,2), (2,0); B has (0,0),
+    (1,1), (2,2).  The A batch sets (2,0) (an existing entry: A* = {(2,0)});
+    the B batch inserts (1,0) and deletes the absent (0,2).  B* = {(1,0)},
+    rows(B*) = {1}, and the only row of A' with column 1 is row 0, so
+    R = {2} u {0} = {0, 2}: row 1, whose A row reads B row 2, is untouched,
+    and the no-op delete in B row 0 adds nothing (row 2 reads B row 0 but is
+    already in R for its own change)."""
+    A = CSR(3, 3, np.array([0, 1, 2, 3], np.int64), np.array([1, 2, 0], np.int32), np.array([1.0, 2.0, 3.0]))
+    B = CSR(3, 3, np.array([0, 1, 2, 3], np.int64), np.array([0, 1, 2], np.int32), np.array([4.0, 5.0, 6.0]))
+    ba = Batch(np.array([2], np.int32), np.array([0], np.int32), np.array([7.0]), np.array([OP_SET], np.uint8))
+    bb = Batch(np.array([1, 0], np.int32), np.array([0, 2], np.int32), np.array([8.0, 0.0]),
+               np.array([OP_INSERT, OP_DELETE], np.uint8))
+    Am, Bm = OMat.from_csr(A), OMat.from_csr(B)
+    Cm = Am.multiply(Bm)
+    R = oracle.row_dynamic(Am, Cm, ba, Bm, bb)
+    assert R.tolist() == [0, 2]
+    # C' by hand: row 0 = 1 * B'(1,:) = {0: 8, 1: 5}; row 1 = 2 * B(2,:) = {2: 12};
+    # row 2 = 7 * B(0,:) = {0: 28}
+    Cn = Cm.to_csr()
+    assert Cn.rowptr.tolist() == [0, 2, 3, 4]
+    assert Cn.col.tolist() == [0, 1, 2, 0]
+    assert Cn.val.tolist() == [8.0, 5.0, 12.0, 28.0]
