@@ -373,13 +373,21 @@ const char *dspg_group_last_error(const dspg_group *g);
  * *nnz_out are written; a result larger than capacity returns
  * DSPG_ERR_INVALID with *nnz_out set to the size needed.
  *
- * Allocation: none.  The working memory is a fixed array of about 4.2 MiB
- * of device memory in this library image, held by every GPU that loads the
- * library until the process exits.  The first call on each device looks up
- * that array's device address (with the device current); make that first
- * call before any stream capture.  All calls share the array: calls whose
+ * Allocation: none.  The working memory is a fixed array of about 4.1 MiB
+ * (4,260,096 bytes) of device memory in this library image, held by every
+ * GPU that loads the library until the process exits.  The first call on
+ * each device looks up that array's device address (with the device
+ * current); make that first call before any stream capture begins.  The
+ * stream must belong to the current device (another device's stream is
+ * rejected with DSPG_ERR_INVALID).  All calls share the array: calls whose
  * work overlaps on the GPU (different streams, or different host threads)
- * race and give wrong results.  The call synchronises the stream twice. */
+ * race and give wrong results.  Each call synchronises the stream before it
+ * returns (twice when it writes the rows).
+ *
+ * Errors: a row index outside [0, A->nrows), or a column index of A or B
+ * outside its matrix, makes the call return DSPG_ERR_INVALID ("row or
+ * column index out of range") without writing col/val (the kernel skips
+ * the bad index instead of reading through it). */
 dspg_status dspg_multiply_rows_noalloc(const dspg_csr *A, const dspg_csr *B, dspg_semiring sr, const int32_t *rows,
                                        int64_t nrows, int64_t *rowptr, int32_t *col, void *val, int64_t capacity,
                                        int64_t *nnz_out, void *stream);

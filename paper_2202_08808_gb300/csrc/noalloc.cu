@@ -11,7 +11,7 @@
 // The working memory is na_scratch below: NA_CTAS slices, each a dense
 // accumulator of NA_MAX_COLS values plus a presence bitmap, and one status
 // word.  Every GPU that loads the library holds these NA_SCRATCH_BYTES
-// (about 4.2 MiB) until the process exits.  Host code must not pass the
+// (about 4.1 MiB) until the process exits.  Host code must not pass the
 // symbol itself to a kernel (in host code it names a host-side stand-in):
 // its device address is taken once per device with cudaGetSymbolAddress.
 //
@@ -20,7 +20,9 @@
 // slice, scatters the row's products into it (atomics), then reads the set
 // bits in column order.  A first pass counts each row's entries into the
 // caller's rowptr, one CTA scans them, and a second pass writes the rows.
+#include <atomic>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 
@@ -39,7 +41,10 @@ constexpr size_t NA_SCRATCH_BYTES = NA_STATUS_OFF + 256;
 static __device__ __align__(256) unsigned char na_scratch[NA_SCRATCH_BYTES];
 
 constexpr int NA_MAX_DEVICES = 64;
-unsigned char *g_na_ptr[NA_MAX_DEVICES] = {};
+// Device address of na_scratch per device, looked up once (under the mutex;
+// later calls read it without locking).
+std::atomic<unsigned char *> g_na_ptr[NA_MAX_DEVICES] = {};
+std::mutex g_na_mutex;
 
 template <int SR>
 struct NaSr;
@@ -227,20 +232,32 @@ extern "C" dspg_status dspg_multiply_rows_noalloc(const dspg_csr *A, const dspg_
     if (nrows == 0) return DSPG_OK;
 
     // set-up, once per device with that device current: the device address
-    // of the scratch array
+    // of the scratch array.  The stream must belong to that device, or the
+    // kernels would get another device's address.
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES)
         return fail_na(DSPG_ERR_CUDA, "cudaGetDevice failed");
-    if (!g_na_ptr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, na_scratch);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail_na(DSPG_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
-        }
-        g_na_ptr[dev] = (unsigned char *)p;
+    int sdev = dev;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_na(DSPG_ERR_INVALID, "the stream is not a valid stream");
     }
-    unsigned char *scratch = g_na_ptr[dev];
+    if (sdev != dev) return fail_na(DSPG_ERR_INVALID, "the stream belongs to another device than the current one");
+    unsigned char *scratch = g_na_ptr[dev].load(std::memory_order_acquire);
+    if (!scratch) {
+        std::lock_guard<std::mutex> lock(g_na_mutex);
+        scratch = g_na_ptr[dev].load(std::memory_order_relaxed);
+        if (!scratch) {
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, na_scratch);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail_na(DSPG_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
+            }
+            scratch = (unsigned char *)p;
+            g_na_ptr[dev].store(scratch, std::memory_order_release);
+        }
+    }
     unsigned *status = (unsigned *)(scratch + NA_STATUS_OFF);
 
     NaArgs g{A->rowptr, A->col, A->val, B->rowptr, B->col, B->val, A->nrows, B->nrows, B->ncols,

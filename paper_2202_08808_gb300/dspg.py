@@ -35,9 +35,10 @@ _lib = None
 
 
 class DspgError(RuntimeError):
-    def __init__(self, status: int, msg: str):
+    def __init__(self, status: int, msg: str, needed: int | None = None):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
         self.status = status
+        self.needed = needed  # the result size a call reported with its error, where it reports one
 
 
 class _Csr(C.Structure):
@@ -542,7 +543,8 @@ class Group:
             pass
 
 
-def multiply_rows_noalloc(A, B, rows, semiring: int | None = None, stream=None):
+def multiply_rows_noalloc(A, B, rows, semiring: int | None = None, stream=None, capacity: int | None = None,
+                          query_only: bool = False):
     """Rows `rows` of C = A B through dspg_multiply_rows_noalloc, for callers
     that cannot let the library allocate device memory (the call itself
     allocates nothing: its working memory is a fixed array in the library).
@@ -550,7 +552,9 @@ def multiply_rows_noalloc(A, B, rows, semiring: int | None = None, stream=None):
     A and B are objects with ``nrows, ncols, rowptr, col, val`` whose arrays
     are CUDA tensors; rows is a CUDA int32 tensor.  The output tensors are
     allocated here by torch, on the caller's side of the boundary.  Returns
-    (rowptr, col, val) as CUDA tensors."""
+    (rowptr, col, val) as CUDA tensors; with ``query_only`` the size query
+    alone, as (rowptr, nnz).  ``capacity`` sizes the output buffers of the
+    second call (default: the size the query returned)."""
     import torch
     lib = load()
     keep: list = []
@@ -574,13 +578,15 @@ def multiply_rows_noalloc(A, B, rows, semiring: int | None = None, stream=None):
                                         None, 0, C.byref(nnz), s)
     if st != 0:
         raise DspgError(st, lib.dspg_last_error(None).decode())
-    cap = max(nnz.value, 1)
-    col = torch.empty(cap, dtype=torch.int32, device=rows.device)
-    val = torch.empty(cap, dtype=torch.float64 if semiring == PLUS_TIMES_F64 else torch.int32, device=rows.device)
+    if query_only:
+        return rp, nnz.value
+    cap = max(nnz.value, 1) if capacity is None else int(capacity)
+    col = torch.empty(max(cap, 1), dtype=torch.int32, device=rows.device)
+    val = torch.empty(max(cap, 1), dtype=torch.float64 if semiring == PLUS_TIMES_F64 else torch.int32, device=rows.device)
     st = lib.dspg_multiply_rows_noalloc(C.byref(ca), C.byref(cb), semiring, rows.data_ptr(), n, rp.data_ptr(),
                                         col.data_ptr(), val.data_ptr(), cap, C.byref(nnz), s)
     if st != 0:
-        raise DspgError(st, lib.dspg_last_error(None).decode())
+        raise DspgError(st, lib.dspg_last_error(None).decode(), needed=nnz.value)
     return rp, col[: nnz.value], val[: nnz.value]
 
 

@@ -59,3 +59,43 @@ def test_noalloc_rejects_too_wide_b(dspg):
         dspg.multiply_rows_noalloc(_to_device(A), _to_device(B), torch.arange(10, dtype=torch.int32).cuda())
     assert e.value.status == 1
     assert "65536" in str(e.value)
+
+
+def test_noalloc_bad_row_index_is_reported(dspg):
+    """A row index outside A's rows is skipped by the kernel and reported by
+    the call as DSPG_ERR_INVALID with the index message."""
+    import torch
+    A = random_csr(50, 40, 5, 11, PLUS_TIMES_F64)
+    B = random_csr(40, 60, 5, 12, PLUS_TIMES_F64)
+    Ad, Bd = _to_device(A), _to_device(B)
+    for bad in (-1, A.nrows):
+        rows = torch.tensor([0, 3, bad, 7], dtype=torch.int32).cuda()
+        with pytest.raises(dspg.DspgError) as e:
+            dspg.multiply_rows_noalloc(Ad, Bd, rows)
+        assert e.value.status == 1 and "out of range" in str(e.value)
+    # the array is usable again right after the failed calls
+    rp, col, val = dspg.multiply_rows_noalloc(Ad, Bd, torch.tensor([0, 3, 7], dtype=torch.int32).cuda())
+    orp, ocol, _ = OMat.from_csr(A).multiply_rows(OMat.from_csr(B), np.array([0, 3, 7], np.int32))
+    assert np.array_equal(rp.cpu().numpy(), orp) and np.array_equal(col.cpu().numpy(), ocol)
+
+
+def test_noalloc_capacity_and_size_query(dspg):
+    """The size query (col = NULL) writes rowptr and the result size only;
+    a fill call with one entry less room than the result returns
+    DSPG_ERR_INVALID and reports the size it needs; the exact room works."""
+    import torch
+    A = random_csr(300, 200, 8, 21, MIN_PLUS_I32)
+    B = random_csr(200, 500, 8, 22, MIN_PLUS_I32)
+    Ad, Bd = _to_device(A), _to_device(B)
+    rows_np = np.arange(0, 300, 3, dtype=np.int32)
+    rows = torch.from_numpy(rows_np).cuda()
+    qrp, nnz = dspg.multiply_rows_noalloc(Ad, Bd, rows, query_only=True)
+    orp, ocol, oval = OMat.from_csr(A).multiply_rows(OMat.from_csr(B), rows_np)
+    assert nnz == int(orp[-1]) > 0
+    assert np.array_equal(qrp.cpu().numpy(), orp)
+    with pytest.raises(dspg.DspgError) as e:
+        dspg.multiply_rows_noalloc(Ad, Bd, rows, capacity=nnz - 1)
+    assert e.value.status == 1 and "capacity" in str(e.value) and e.value.needed == nnz
+    rp, col, val = dspg.multiply_rows_noalloc(Ad, Bd, rows, capacity=nnz)
+    assert np.array_equal(rp.cpu().numpy(), orp) and np.array_equal(col.cpu().numpy(), ocol)
+    assert np.array_equal(val.cpu().numpy(), oval)
