@@ -112,6 +112,7 @@ typedef struct {
     int64_t a_entries;      /* entries of A' rows read by the recompute */
     int64_t est_rows;       /* rows sized by the learned estimator */
     int64_t est_overflows;  /* of those, rows whose table was too small (counted exactly, recomputed) */
+    int64_t algebraic;      /* 1: the batch took the delta path of Eq. 1 (dspg_apply_batch_algebraic) */
 } dspg_batch_stats;
 
 /* Stages of apply_batch, in pipeline order, for dspg_stage_times. */
@@ -144,6 +145,28 @@ dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, 
  * Synchronises the stream once to return the status. */
 dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
                              dspg_batch_stats *stats, void *stream);
+
+/* Apply one batch as dspg_apply_batch does, by the delta path of Section 5's
+ * algebraic updates when the batch qualifies: C' = C (+) C* with
+ * C* = A* B' (+) A B* (Eq. 1; Section 5.1's local step), formed entry by
+ * entry from the update matrices instead of recomputing rows.  A batch
+ * qualifies when every entry that changes A or B writes an absent entry
+ * (an insertion: A' = A (+) A* with the semiring's addition; deletes of
+ * absent entries are ignored).  Any write to a present entry or delete of
+ * one makes the call apply the batch by the row path instead (general
+ * updates), with the same result as dspg_apply_batch; stats->algebraic says
+ * which path ran.  Each contribution a (x) b is folded into C'(i,j) where
+ * row i of C holds column j (an atomic (+) on the value, so in (+,.) the
+ * summation order varies, within the library's tolerance), and otherwise
+ * appended to row i (rows of C carry no column order); rows of C longer
+ * than 256 entries are recomputed by the row path instead of searched.
+ * After the call, C' = A' B' as after dspg_apply_batch; affected_rows and
+ * dspg_last_affected give the rows of C that took a contribution (a subset
+ * of the row path's R), products the contributions formed.  Runs eagerly
+ * (no captured graph) and synchronises the stream several times.  Errors
+ * as dspg_apply_batch. */
+dspg_status dspg_apply_batch_algebraic(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
+                                       dspg_batch_stats *stats, void *stream);
 
 /* Read C in canonical CSR (rows in order, columns ascending) into caller
  * buffers: rowptr[nrows+1], col[nnz], val[nnz], host or device per

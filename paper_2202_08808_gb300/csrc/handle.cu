@@ -225,6 +225,52 @@ struct FpWs {
     } hcnt;
 };
 
+// Working memory of the delta path (algebraic updates, Eq. 1): the list of
+// new entries of C, its sorted copy and sort buffers, the rows' plan, and the
+// bitmap of rows of C too long to take contributions in place.
+struct AlgWs {
+    int64_t ncap = 0;
+    DBuf<int32_t> nr, nc, srow, scol;
+    DBuf<char> nv, sval;
+    DBuf<uint8_t> nop, sop;
+    DBuf<uint64_t> k0, k1;
+    DBuf<uint32_t> i0, i1, counts;
+    DBuf<int64_t> scan_tmp, scan_out, dest;
+    DBuf<int32_t> cap;
+    DBuf<uint32_t> bm_long;
+    DBuf<InArgs> args;  // device: where the new-entry list is, for the sort
+    bool ensure(int64_t need, int64_t nrows, int vsize, cudaStream_t s) {
+        bool moved = false;
+        if (need > ncap) {
+            const int64_t c = std::max<int64_t>(need, 2 * ncap);
+            nr.reserve(c); nc.reserve(c); nv.reserve(c * vsize); nop.reserve(c);
+            srow.reserve(c); scol.reserve(c); sval.reserve(c * vsize); sop.reserve(c);
+            k0.reserve(c); k1.reserve(c); i0.reserve(c); i1.reserve(c);
+            int64_t cnt;
+            sort_tmp_sizes(c, &cnt);
+            counts.reserve(cnt);
+            scan_out.reserve(cnt + 1);
+            scan_tmp.reserve(scan_tmp_entries(cnt) + 1);
+            dest.reserve(c);
+            cap.reserve(c);
+            ncap = c;
+            moved = true;
+        }
+        if (bm_long.reserve(nrows / 32 + 2)) {
+            CK(cudaMemsetAsync(bm_long.p, 0, sizeof(uint32_t) * bm_long.n, s));
+            moved = true;
+        }
+        if (moved || !args.p) {
+            args.reserve(1);
+            const InArgs a{nr.p, nc.p, nv.p, nop.p};
+            CK(cudaMemcpyAsync(args.p, &a, sizeof(InArgs), cudaMemcpyHostToDevice, s));
+        }
+        return moved;
+    }
+    SortOut sort_out() { return SortOut{srow.p, scol.p, (void *)sval.p, sop.p}; }
+    SortTmp sort_tmp() { return SortTmp{k0.p, k1.p, i0.p, i1.p, counts.p, scan_tmp.p, scan_out.p, k0.n, counts.n}; }
+};
+
 struct BatchIn {
     const int32_t *row = nullptr, *col = nullptr;
     const void *val = nullptr;
@@ -311,6 +357,8 @@ struct dspg_handle {
     float est_margin = 0.25f;
     DBuf<uint16_t> est_w;                       // estimator weights (bfloat16 bits)
     FpWs fp;                                    // footprints (serving)
+    AlgWs alg;                                  // the delta path (algebraic updates)
+    bool last_alg = false;                      // the last batch took the delta path
     int64_t compactions = 0;
     std::string err;
 
@@ -1296,6 +1344,155 @@ void apply_one(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, d
     fill_stats(h, stats, compactions0);
 }
 
+// ------------------------------------------------- the delta path (Eq. 1)
+
+// Size and recompute the rows of R (ctl->n_affected of them) by the row
+// path, growing C's arena until they fit (rows of the delta path that are
+// too long to search, or every touched row when the new-entry list was full).
+void alg_recompute_rows(dspg_handle *h, cudaStream_t s) {
+    for (int iter = 0;; iter++) {
+        stage_size(h, s);
+        stage_numeric(h, s);
+        read_ctl(h, s);
+        const unsigned st = h->hctl->status & ~ST_ALG_FULL;
+        if ((st & ST_C_ARENA) && iter < 4) {
+            regrow(h, h->C, s);
+            CK(cudaMemsetAsync(h->ctl->bin_count, 0, sizeof(h->ctl->bin_count), s));
+            CK(cudaMemsetAsync(&h->ctl->status, 0, sizeof(unsigned), s));
+            continue;
+        }
+        if (st & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, overflow_message(h->hctl));
+        if (st) throw Err(DSPG_ERR_CUDA, "row recompute of the delta path failed, status " + std::to_string(st));
+        return;
+    }
+}
+
+// Collect a row bitmap into R (clearing it) with n_affected starting at 0.
+void alg_collect(dspg_handle *h, uint32_t *bm, cudaStream_t s) {
+    CK(cudaMemsetAsync(&h->ctl->n_affected, 0, sizeof(long long), s));
+    CK(cudaMemsetAsync(h->ctl->bin_count, 0, sizeof(h->ctl->bin_count), s));
+    run_collect_rows(bm, (h->A.nrows + 31) / 32, h->wc.R.p, h->wc.rchunk.p, h->ctl, 0u, s, h->num_sms);
+}
+
+// One batch by Eq. 1 when every effective change of it inserts an absent
+// entry (Section 5, algebraic updates): returns false, having changed
+// nothing, for any other batch (a write to a present entry or a delete),
+// which the caller then applies by the row path.  Runs eagerly on s and
+// reads the control block between its steps.
+bool apply_algebraic(dspg_handle *h, cudaStream_t s) {
+    const int64_t nA = h->inA.n, nB = h->b_is_a ? 0 : h->inB.n;
+    begin_batch(h->h_args_dev, h->d_args, h->ctl, s);
+    stage_sort(h, s);
+    if (nA > 0)
+        run_classify(h->wA.job(nA), h->A.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, DetectBufs{},
+                     false, false, s, h->num_sms);
+    if (nB > 0)
+        run_classify(h->wB.job(nB), h->B.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, DetectBufs{},
+                     false, false, s, h->num_sms);
+    CK(cudaGetLastError());
+    read_ctl(h, s);
+    {
+        const Ctl &c = *h->hctl;
+        if (c.status & ST_INVALID) throw Err(DSPG_ERR_INVALID, "batch entry out of range or with an invalid value/op");
+        if (c.status || c.u[0].upd || c.u[0].del || c.u[1].upd || c.u[1].del) return false;
+    }
+    // A' (and B'): the merge and the commit of the row path
+    stage_merge(h, s, -1);
+    stage_commit_ab(h, s);
+    // the contributions read the transposed pattern before this batch
+    const int64_t need = std::max<int64_t>(int64_t(1) << 20, 64 * (nA + nB));
+    if (h->alg.ensure(need, h->A.nrows, h->vsize, s)) h->epoch++;
+    AlgJob J{};
+    const UpdJob ja = h->wA.job(nA);
+    const UpdJob jb = h->b_is_a ? ja : h->wB.job(nB);
+    J.xr = ja.row; J.xc = ja.col; J.xv = ja.val; J.xk = ja.kind; J.xn = nA;
+    J.yr = jb.row; J.yc = jb.col; J.yv = jb.val; J.yk = jb.kind; J.yn = h->b_is_a ? nA : nB;
+    if (!h->has_at) J.yn = 0;  // no B batch reaches C without the pattern (B is never updated then)
+    J.nr = h->alg.nr.p; J.nc = h->alg.nc.p; J.nv = h->alg.nv.p; J.nop = h->alg.nop.p; J.ncap = h->alg.ncap;
+    J.bm_touch = h->wc.bmR.p;
+    J.bm_long = h->alg.bm_long.p;
+    const bool side_on = h->has_at && nA > 0;
+    for (int iter = 0;; iter++) {
+        run_alg_contrib(h->sr, J, h->A.view(), h->Bm().view(), h->AT.view(), h->C.view(), h->ctl, M_AB, s,
+                        h->num_sms);
+        if (side_on) {
+            transpose_front(h, s);
+            transpose_commit(h, s);
+        }
+        CK(cudaGetLastError());
+        read_ctl(h, s);
+        const unsigned st = h->hctl->status;
+        if (!(st & ST_AB_ARENA) || iter >= 4) break;
+        // A's arena ran out in the commit: nothing after it ran; grow it and
+        // commit again (the staged rows are still in place)
+        regrow(h, h->A, s);
+        if (nB > 0) regrow(h, h->B, s);
+        for (int k = 0; k < 2; k++) {
+            reset_range(h, &h->ctl->u[k].n_cchunk, sizeof(long long), s);
+            reset_range(h, &h->ctl->u[k].reloc, sizeof(long long), s);
+        }
+        reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
+        reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+        stage_commit_ab(h, s);
+    }
+    // the transposed pattern's staging or arena: grow and redo its update
+    for (int iter = 0; iter < 8 && (h->hctl->status & (ST_AT_STAGE | ST_AT_ARENA)); iter++) {
+        const unsigned st = h->hctl->status;
+        if ((st & ST_AT_STAGE) && h->wAT.grow_stage(h->hctl->u[2].stage_top + 1024)) h->epoch++;
+        if (st & ST_AT_ARENA) regrow(h, h->AT, s);
+        reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+        reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
+        transpose_front(h, s);
+        transpose_commit(h, s);
+        read_ctl(h, s);
+    }
+    if (h->hctl->status & ~ST_ALG_FULL)
+        throw Err(DSPG_ERR_CUDA, "delta path update failed, status " + std::to_string(h->hctl->status));
+    const long long n_new = h->hctl->alg_new, n_con = h->hctl->alg_contrib;
+    const bool full = h->hctl->status & ST_ALG_FULL;
+    CK(cudaMemsetAsync(&h->ctl->status, 0, sizeof(unsigned), s));
+    long long long_rows = 0;
+    if (full) {
+        // too many new entries: every touched row is recomputed from A', B'
+        // instead (exact whatever contributions it took)
+        CK(cudaMemsetAsync(h->alg.bm_long.p, 0, sizeof(uint32_t) * h->alg.bm_long.n, s));
+        alg_collect(h, h->wc.bmR.p, s);
+        read_ctl(h, s);
+        long_rows = h->hctl->n_affected;
+        alg_recompute_rows(h, s);
+    } else {
+        if (n_new > 0) {
+            sort_updates(h->alg.args.p, n_new, h->C.nrows, h->C.ncols, h->sr, false, h->alg.sort_out(),
+                         h->alg.sort_tmp(), h->ctl, 0u, s);
+            const AlgNew N{h->alg.srow.p, h->alg.scol.p, h->alg.sval.p, n_new, h->alg.dest.p, h->alg.cap.p};
+            for (int iter = 0;; iter++) {
+                run_alg_append(h->sr, N, h->C.view(), h->ctl, 0u, 0u, h->opt.slack_min, h->opt.slack_div, true, s,
+                               h->num_sms);
+                read_ctl(h, s);
+                if (!(h->hctl->status & ST_C_ARENA) || iter >= 4) break;
+                regrow(h, h->C, s);  // the plan wrote nothing but places: plan again in the new arena
+                CK(cudaMemsetAsync(&h->ctl->status, 0, sizeof(unsigned), s));
+            }
+            if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "delta path: C's arena cannot take the new entries");
+            run_alg_append(h->sr, N, h->C.view(), h->ctl, 0u, 0u, h->opt.slack_min, h->opt.slack_div, false, s,
+                           h->num_sms);
+        }
+        // rows too long to search: recomputed by the row path
+        alg_collect(h, h->alg.bm_long.p, s);
+        read_ctl(h, s);
+        long_rows = h->hctl->n_affected;
+        if (long_rows > 0) alg_recompute_rows(h, s);
+        // the touched rows, for the statistics and dspg_last_affected
+        alg_collect(h, h->wc.bmR.p, s);
+    }
+    read_ctl(h, s);
+    h->hctl->products += n_con;
+    h->hctl->alg_new = n_new;
+    h->hctl->alg_contrib = n_con;
+    (void)long_rows;
+    return true;
+}
+
 // Captures what body() enqueues on cs into an executable graph; the number
 // of kernels it launched goes to *nk.  The capture is closed on errors.
 template <typename F>
@@ -1429,6 +1626,28 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
     if (!h) return DSPG_ERR_INVALID;
     try {
         apply_one(h, dA, dB, stats, (cudaStream_t)stream);
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_apply_batch_algebraic(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
+                                       dspg_batch_stats *stats, void *stream) {
+    if (!h) return DSPG_ERR_INVALID;
+    try {
+        const cudaStream_t s = (cudaStream_t)stream;
+        prepare_batch(h, dA, dB, s);
+        const int64_t compactions0 = h->compactions;
+        h->last_alg = apply_algebraic(h, s);
+        if (!h->last_alg) {  // general updates: the row path
+            run_first(h, s);
+            if (h->prof) stage_times_from_events(h);
+            recover(h, s);
+        }
+        est_fallback(h, s);
+        fill_stats(h, stats, compactions0);
+        if (stats) stats->algebraic = h->last_alg ? 1 : 0;
         return DSPG_OK;
     } catch (const Err &e) {
         return fail(h, e);

@@ -130,6 +130,40 @@ void run_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t words, uns
 void run_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words, const unsigned long long *cnt, int or_anyway,
                    cudaStream_t s, int num_sms);
 
+// algebraic.cu: the delta path of Eq. 1 (batches that only insert)
+constexpr int ALG_SCAN = 256;  // rows of C up to this length take contributions in place
+struct AlgJob {
+    // X = A* B': the sorted A batch (entries of kind K_INS are A*)
+    const int32_t *xr, *xc;
+    const void *xv;
+    const uint8_t *xk;
+    int64_t xn;
+    // Y = A B*: the sorted B batch (the A batch when B is A)
+    const int32_t *yr, *yc;
+    const void *yv;
+    const uint8_t *yk;
+    int64_t yn;
+    // new entries of C (columns not yet in their row): room for ncap
+    int32_t *nr, *nc;
+    void *nv;
+    uint8_t *nop;
+    int64_t ncap;
+    uint32_t *bm_touch;  // rows of C that take a contribution
+    uint32_t *bm_long;   // rows longer than ALG_SCAN: recomputed by the row path
+};
+// The sorted new entries of C (equal keys adjacent) and their rows' plan.
+struct AlgNew {
+    const int32_t *row, *col;
+    const void *val;
+    int64_t n;
+    int64_t *dest;  // per row-run head: where the row goes
+    int32_t *cap;   // per row-run head: its capacity there
+};
+void run_alg_contrib(int sr, const AlgJob &J, const MatView &A, const MatView &B, const MatView &AT, const MatView &C,
+                     Ctl *ctl, unsigned mask, cudaStream_t s, int num_sms);
+void run_alg_append(int sr, const AlgNew &N, const MatView &C, Ctl *ctl, unsigned plan_mask, unsigned copy_mask,
+                    int slack_min, int slack_div, bool plan, cudaStream_t s, int num_sms);
+
 // spgemm.cu
 constexpr int64_t DENSE_M_MAX = 1024;  // C columns up to this use dense accumulators
 void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const CJob &J, int64_t max_rows, Ctl *ctl,

@@ -59,7 +59,8 @@ class _Opt(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "n_updates", "n_unique", "n_insert", "n_update", "n_delete", "n_noop", "touched_rows", "affected_rows",
-        "products", "nnz_written", "relocations", "compactions", "a_entries", "est_rows", "est_overflows")]
+        "products", "nnz_written", "relocations", "compactions", "a_entries", "est_rows", "est_overflows",
+        "algebraic")]
 
 
 class _Tuning(C.Structure):
@@ -83,6 +84,8 @@ def load():
         lib.dspg_build.argtypes = [C.POINTER(p), C.POINTER(_Csr), C.POINTER(_Csr), i32, C.POINTER(_Opt), p]
         lib.dspg_apply_batch.restype = i32
         lib.dspg_apply_batch.argtypes = [p, C.POINTER(_Upd), C.POINTER(_Upd), C.POINTER(_Stats), p]
+        lib.dspg_apply_batch_algebraic.restype = i32
+        lib.dspg_apply_batch_algebraic.argtypes = [p, C.POINTER(_Upd), C.POINTER(_Upd), C.POINTER(_Stats), p]
         for name in ("dspg_read_C", "dspg_read_A"):
             f = getattr(lib, name)
             f.restype = i32
@@ -149,7 +152,7 @@ def load():
         return lib
 
 
-EXPORTED = ["dspg_build", "dspg_apply_batch", "dspg_read_C", "dspg_read_A", "dspg_read_rows_C",
+EXPORTED = ["dspg_build", "dspg_apply_batch", "dspg_apply_batch_algebraic", "dspg_read_C", "dspg_read_A", "dspg_read_rows_C",
             "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_set_profiling", "dspg_stage_times",
             "dspg_kernel_launches", "dspg_multiply_rows_noalloc", "dspg_set_tuning", "dspg_get_tuning",
             "dspg_tuning_candidate", "dspg_autotune", "dspg_group_create", "dspg_group_apply", "dspg_group_destroy",
@@ -292,13 +295,17 @@ class DynamicSpGEMM:
         op, _ = _ptr(_as_int(b.op, np.uint8), keep)
         return _Upd(len(b.row), row, col, val, op, dev)
 
-    def apply_batch(self, dA=None, dB=None, stream=None) -> dict:
+    def apply_batch(self, dA=None, dB=None, stream=None, algebraic: bool = False) -> dict:
+        """Apply a batch (dspg_apply_batch); with ``algebraic`` through
+        dspg_apply_batch_algebraic (the delta path of Eq. 1 for batches that
+        only insert, the row path otherwise)."""
         keep: list = []
         ua = self._upd(dA, keep) if dA is not None else None
         ub = self._upd(dB, keep) if dB is not None else None
         stats = _Stats()
-        st = self._lib.dspg_apply_batch(self._h, C.byref(ua) if ua is not None else None,
-                                        C.byref(ub) if ub is not None else None, C.byref(stats), _stream(stream))
+        fn = self._lib.dspg_apply_batch_algebraic if algebraic else self._lib.dspg_apply_batch
+        st = fn(self._h, C.byref(ua) if ua is not None else None, C.byref(ub) if ub is not None else None,
+                C.byref(stats), _stream(stream))
         self._check(st)
         return {name: getattr(stats, name) for name, _ in _Stats._fields_}
 
