@@ -47,6 +47,13 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# DRAM bytes (read + write) of the numeric stage's kernels in one step of a
+# workload, from the ncu capture summarised in
+# profiles/numeric_stage_dram_stencil128.md (valid while those kernels are
+# unchanged); None where no capture exists.
+NUMERIC_TRAFFIC = {"stencil": 87991808}
+
+
 def dist_env():
     return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -296,7 +303,10 @@ def gpu_arm(args):
     a_ent = sum(s["a_entries"] for s in stats_acc)
     prods = sum(s["products"] for s in stats_acc)
     nnzw = sum(s["nnz_written"] for s in stats_acc)
-    alg_bytes = 12 * R + (s_entry + 12) * a_ent + s_entry * prods + s_entry * nnzw
+    # gather model: an 8 B row header per row of R and per B row read (the
+    # row's place and length), the A' entries, every product's B entry, and
+    # the entries of C written
+    alg_bytes = 8 * R + (s_entry + 8) * a_ent + s_entry * prods + s_entry * nnzw
     numeric_ms = stage_acc["numeric"]
     peak, peak_kind = peaks()
     achieved = alg_bytes / (numeric_ms * 1e-3) / 1e9 if numeric_ms > 0 else 0.0
@@ -373,6 +383,46 @@ def gpu_arm(args):
                           "latency_ms": round(med, 4),
                           "speedup_vs_static": round(static_med / med, 2), "affected_rows": st["affected_rows"]})
 
+    # the delta path of Eq. 1 beside the row path, on insert-only batches of
+    # the same sizes (positions two grid hops away, never inserted before),
+    # the two paths alternating on the same handle
+    delta = []
+    if not args.no_sweep and W.name == "stencil":
+        from workloads import stencil_insert_batch
+        taken: set = set()
+        Ag = g.read_A()  # positions present now (earlier batches inserted some two hops away)
+        present = np.repeat(np.arange(Ag.nrows, dtype=np.int64), np.diff(Ag.rowptr)) * Ag.ncols + Ag.col
+
+        def timed(b, algebraic):
+            db = type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(),
+                         torch.from_numpy(b.val).cuda(), torch.from_numpy(b.op).cuda())
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = g.apply_batch(db, algebraic=algebraic)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1), st
+
+        for nupd in (1000, 10000, 100000):
+            t_alg, t_row, alg_ok, rows_alg, rows_row = [], [], True, 0, 0
+            for r in range(4):
+                ta, sa = timed(stencil_insert_batch(GRID, GRID, GRID, nupd, 8000 + 10 * r + nupd, taken, present), True)
+                tr, sr_ = timed(stencil_insert_batch(GRID, GRID, GRID, nupd, 8005 + 10 * r + nupd, taken, present),
+                                False)
+                if r == 0:
+                    continue  # the first of each size warms the path (buffers, graph capture)
+                t_alg.append(ta)
+                t_row.append(tr)
+                alg_ok &= sa["algebraic"] == 1
+                rows_alg, rows_row = sa["affected_rows"], sr_["affected_rows"]
+            ma, mr = statistics.median(t_alg), statistics.median(t_row)
+            delta.append({"batch": nupd, "delta_path_ms": round(ma, 4), "row_path_ms": round(mr, 4),
+                          "delta_speedup_vs_row": round(mr / ma, 2), "delta_speedup_vs_static": round(static_med / ma, 2),
+                          "rows_touched_delta": rows_alg, "rows_recomputed_row": rows_row, "all_delta": bool(alg_ok)})
+
     out = None
     if rank == 0:
         cpu = None if args.no_cpu else cpu_baseline(args, W, budget_s=args.cpu_budget)
@@ -406,7 +456,11 @@ def gpu_arm(args):
             "roofline": {"bound": "hbm", "kernel": "numeric recompute (all bins) of the affected rows",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                         "alg_bytes_per_step": int(alg_bytes / max(n_prof, 1)), "traffic": None},
+                         "alg_bytes_per_step": int(alg_bytes / max(n_prof, 1)),
+                         "traffic": NUMERIC_TRAFFIC.get(W.name),
+                         "traffic_note": ("DRAM bytes of the numeric kernels in one step (ncu, "
+                                          "profiles/numeric_stage_dram_stencil128.md)"
+                                          if W.name in NUMERIC_TRAFFIC else None)},
             "e2e": {"value": round(1e3 / e2e_mean, 3), "unit": W.unit,
                     "latency_ms": round(e2e_mean, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
@@ -414,6 +468,7 @@ def gpu_arm(args):
             "clocks": clk,
             "wall_s_timed": round(wall, 3),
             "batch_sweep": sweep,
+            "delta_path_insert_only": delta,
             "cpu_baseline": cpu,
         }
     if dist is not None:
@@ -901,10 +956,12 @@ def learned_cpu_baseline(A, held, budget_s, n_batches=None, edges=100, unit="bat
 
 # ------------------------------------------------------------ CPU oracle
 
-def cpu_baseline(args, W, budget_s=20.0, steps=None, warmup=0):
+def cpu_baseline(args, W, budget_s=20.0, steps=None, warmup=0, single=True):
     """The oracle's row-dynamic route (apply, affected rows, recompute of R)
     on a bounded sample of the same workload: consecutive batches until the
-    time budget is used; single-threaded C."""
+    time budget is used, first single-threaded, then with its row loops on
+    all host cores (os.cpu_count() threads; the same results).  value and
+    cores are the all-cores figures; single_core holds the other."""
     import oracle
     from oracle import OMat
     A, B = W.operands()
@@ -916,23 +973,41 @@ def cpu_baseline(args, W, budget_s=20.0, steps=None, warmup=0):
     Co = Ao.multiply(Bo if Bo is not None else Ao)
     for w in range(warmup):  # untimed
         oracle.row_dynamic(Ao, Co, W.batches(1, 60000 + w)[0], Bo)
-    times = []
+    ncores = os.cpu_count() or 1
     k = 0
-    while True:
-        b = W.batches(1, 70000 + k)[0]
-        t0 = time.perf_counter()
-        oracle.row_dynamic(Ao, Co, b, Bo)
-        times.append(time.perf_counter() - t0)
-        k += 1
-        if steps is not None and k >= steps:
-            break
-        if steps is None and (sum(times) > budget_s or k >= 200):
-            break
-    mean = statistics.mean(times)
-    return {"value": round(1.0 / mean, 4), "unit": W.unit, "cores": 1,
-            "kind": "oracle", "latency_ms": round(mean * 1e3, 3),
-            "sample": f"{k} consecutive batches of the workload ({W.describe}): apply + affected rows + row recompute",
-            "times_ms": [round(t * 1e3, 2) for t in times[:20]]}
+
+    def run(threads, budget):
+        nonlocal k
+        oracle.set_threads(threads)
+        times = []
+        try:
+            while True:
+                b = W.batches(1, 70000 + k)[0]
+                t0 = time.perf_counter()
+                oracle.row_dynamic(Ao, Co, b, Bo)
+                times.append(time.perf_counter() - t0)
+                k += 1
+                if steps is not None and len(times) >= steps:
+                    break
+                if steps is None and (sum(times) > budget or len(times) >= 200):
+                    break
+        finally:
+            oracle.set_threads(1)
+        return times
+
+    one = run(1, budget_s / 2) if single else None
+    many = run(ncores, budget_s / 2)
+    mean = statistics.mean(many)
+    out = {"value": round(1.0 / mean, 4), "unit": W.unit, "cores": ncores,
+           "kind": "oracle", "latency_ms": round(mean * 1e3, 3),
+           "sample": f"{len(many)} consecutive batches of the workload ({W.describe}): apply + affected rows + "
+                     f"row recompute, the row loops on {ncores} threads",
+           "times_ms": [round(t * 1e3, 2) for t in many[:20]]}
+    if one is not None:
+        m1 = statistics.mean(one)
+        out["single_core"] = {"value": round(1.0 / m1, 4), "cores": 1, "latency_ms": round(m1 * 1e3, 3),
+                              "sample": f"{len(one)} consecutive batches, single-threaded"}
+    return out
 
 
 def reference_arm(args):
@@ -940,13 +1015,13 @@ def reference_arm(args):
     if rank != 0:
         return
     W = WORKLOADS[args.workload if args.workload in WORKLOADS else "stencil"]()
-    res = cpu_baseline(args, W, steps=args.steps, warmup=args.warmup)
+    res = cpu_baseline(args, W, steps=args.steps, warmup=args.warmup, single=False)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": res["value"], "unit": res["unit"], "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["latency_ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": W.dtype, "data": "synthetic",
         "config": {"workload": W.describe, "batch": W.batch},
-        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": res["sample"], "value": res["value"]},
+        "cpu_baseline": {"kind": "oracle", "cores": res["cores"], "sample": res["sample"], "value": res["value"]},
         "e2e": {"value": res["value"], "unit": res["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 

@@ -1,6 +1,7 @@
 """CPU oracle for batch-dynamic SpGEMM -- TEST INFRASTRUCTURE ONLY.
 
-A plain, slow, single-threaded C restatement (``dspg_oracle.c``) of what the
+A plain, slow C restatement (single-threaded unless ``set_threads`` asks
+for the all-cores timing of its row loops) (``dspg_oracle.c``) of what the
 library computes, wrapped with ctypes. Only ``tests/``, the smoke check in
 ``__graft_entry__`` and the CPU-baseline leg of ``bench.py`` may import it;
 the library itself never does, and the oracle imports nothing from the
@@ -22,5 +23,6 @@ from .oracle import (  # noqa: F401
     build_oracle,
     oracle_lib,
     row_dynamic,
+    set_threads,
 )
 from . import mlp  # noqa: F401,E402

@@ -33,6 +33,14 @@
  *
  * Every function taking an update list validates it completely before any
  * mutation; an invalid list returns ORC_ERR_INVALID and changes nothing.
+ *
+ * Threads: single-threaded unless orc_set_threads(n > 1) is called (the CPU
+ * baseline's all-cores timing only).  Then the two row loops of the
+ * row-dynamic route -- the scan of A' for the affected rows and the
+ * recompute of those rows -- are split over n OpenMP threads.  Each row is
+ * still computed by one thread in the same order with its own accumulator,
+ * so every result is identical to the single-threaded one.  Updates are
+ * always applied one by one in array order.
  */
 #include <math.h>
 #include <stdint.h>
@@ -51,6 +59,11 @@
 #define ORC_OP_SET 2
 
 #define ORC_MINPLUS_LIMIT (1 << 30)
+
+/* threads of the row loops (see the header comment); 1 = single-threaded */
+static int g_threads = 1;
+void orc_set_threads(int n) { g_threads = n > 1 ? n : 1; }
+int orc_threads(void) { return g_threads; }
 
 typedef struct {
     int32_t len, cap;
@@ -394,6 +407,7 @@ int64_t orc_affected_rows(const orc_mat *a_new,
         for (int64_t t = 0; t < nb; t++)
             if (bpre[t] || bpost[t]) brows[brow[t]] = 1;
     }
+#pragma omp parallel for num_threads(g_threads) schedule(static, 4096) if (g_threads > 1)
     for (int64_t i = 0; i < a_new->nrows; i++) {
         const orc_row *r = &a_new->rows[i];
         for (int32_t p = 0; p < r->len && !in_r[i]; p++)
@@ -411,14 +425,23 @@ int64_t orc_affected_rows(const orc_mat *a_new,
  * row of C is left as it is (the row-dynamic route). */
 int orc_replace_rows(orc_mat *C, const orc_mat *A, const orc_mat *B, const int32_t *rows, int64_t nr) {
     if (A->ncols != B->nrows || A->sr != B->sr || C->nrows != A->nrows || C->ncols != B->ncols) return ORC_ERR_INVALID;
-    orc_spa s;
-    if (spa_init(&s, B->ncols) != ORC_OK) { spa_free(&s); return ORC_ERR_OOM; }
-    for (int64_t t = 0; t < nr; t++) {
-        if (rows[t] < 0 || rows[t] >= A->nrows) { spa_free(&s); return ORC_ERR_INVALID; }
-        if (gustavson_row(A, B, rows[t], &s, &C->rows[rows[t]], 0) != ORC_OK) { spa_free(&s); return ORC_ERR_OOM; }
+    for (int64_t t = 0; t < nr; t++)
+        if (rows[t] < 0 || rows[t] >= A->nrows) return ORC_ERR_INVALID;
+    int err = ORC_OK;
+#pragma omp parallel num_threads(g_threads) if (g_threads > 1)
+    {
+        orc_spa s;  /* one accumulator per thread */
+        int mine = spa_init(&s, B->ncols);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t t = 0; t < nr; t++)
+            if (mine == ORC_OK) mine = gustavson_row(A, B, rows[t], &s, &C->rows[rows[t]], 0);
+        spa_free(&s);
+        if (mine != ORC_OK) {
+#pragma omp critical
+            err = mine;
+        }
     }
-    spa_free(&s);
-    return ORC_OK;
+    return err;
 }
 
 /* Row accessors for sampled comparisons. */

@@ -550,3 +550,24 @@ def test_affected_rows_separate_b_worked_example():
     assert Cn.rowptr.tolist() == [0, 2, 3, 4]
     assert Cn.col.tolist() == [0, 1, 2, 0]
     assert Cn.val.tolist() == [8.0, 5.0, 12.0, 28.0]
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_all_cores_route_is_identical(sr):
+    """The all-cores timing of the oracle (its row loops over threads) gives
+    bit for bit the single-threaded result: R, C' and A'."""
+    A = random_csr(3000, 3000, 9, 91, sr)
+    b = random_batch(3000, 3000, 2500, 92, sr, A=A)
+    out = []
+    for threads in (1, 4):
+        oracle.set_threads(threads)
+        try:
+            M = OMat.from_csr(A)
+            C = M.multiply(M)
+            R = oracle.row_dynamic(M, C, b)
+            out.append((R, C.to_csr(), M.to_csr()))
+        finally:
+            oracle.set_threads(1)
+    (R1, C1, A1), (R4, C4, A4) = out
+    assert np.array_equal(R1, R4) and csr_equal(C1, C4) and csr_equal(A1, A4)
+    assert np.array_equal(C1.val, C4.val)

@@ -36,7 +36,9 @@ def _worker(rank, world, port, local_ms, out):
 def test_slowest_rank_and_sharding_with_two_gloo_ranks():
     world = 2
     local_ms = [12.5, 40.25]
-    with mp.Manager() as m:
+    # spawn, not fork: the test process may already run threads (the
+    # oracle's OpenMP pool), which a forked child must not inherit
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, _free_port(), local_ms, out), nprocs=world, join=True)
         res = dict(out)

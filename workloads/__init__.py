@@ -20,6 +20,7 @@ from .gen import (  # noqa: F401
     bernoulli_sparse,
     er_batch,
     stencil_batch,
+    stencil_insert_batch,
     rmat_edge_batch,
     random_batch,
     random_csr,

@@ -283,6 +283,47 @@ def stencil_batch(nx: int, ny: int, nz: int, nupd: int, seed: int) -> Batch:
     return Batch(rows.astype(np.int32), cols.astype(np.int32), val, op)
 
 
+_HOP2_ONLY = [o for o in _HOP2 if abs(o[0]) + abs(o[1]) + abs(o[2]) == 2]
+
+
+def stencil_insert_batch(nx: int, ny: int, nz: int, nupd: int, seed: int, taken: set,
+                         present: np.ndarray | None = None) -> Batch:
+    """Insertions only, for the algebraic (Eq. 1) comparison: nupd distinct
+    positions (i, j) with j at L1 distance exactly 2 of i on the grid (18
+    offsets; absent from the 7-point pattern), i uniform, none of them in
+    ``taken`` (positions inserted before, which the call adds to) nor in
+    ``present`` (sorted keys i * n + j of a matrix's entries); values
+    -1 + U(-0.1, 0.1)."""
+    rng = np.random.default_rng(seed)
+    offs = np.array(_HOP2_ONLY, dtype=np.int64)
+    n = nx * ny * nz
+    keys = []
+    fresh = set()
+    while len(keys) < nupd:
+        m = (nupd - len(keys)) * 2 + 16
+        i = rng.integers(0, n, size=m)
+        o = offs[rng.integers(0, offs.shape[0], size=m)]
+        x = i % nx + o[:, 0]
+        y = (i // nx) % ny + o[:, 1]
+        z = i // (nx * ny) + o[:, 2]
+        ok = (x >= 0) & (x < nx) & (y >= 0) & (y < ny) & (z >= 0) & (z < nz)
+        kk = i[ok] * n + _stencil_index(x[ok], y[ok], z[ok], nx, ny)
+        if present is not None and present.shape[0] > 0:
+            p = np.minimum(np.searchsorted(present, kk), present.shape[0] - 1)
+            kk = kk[present[p] != kk]
+        for k in kk.tolist():
+            if k not in taken and k not in fresh:
+                fresh.add(k)
+                keys.append(k)
+                if len(keys) == nupd:
+                    break
+    taken |= fresh
+    keys = np.array(keys, np.int64)
+    val = -1.0 + rng.uniform(-0.1, 0.1, size=nupd)
+    return Batch((keys // n).astype(np.int32), (keys % n).astype(np.int32), val,
+                 np.full(nupd, OP_INSERT, np.uint8))
+
+
 def rmat_edge_batch(A: CSR, held, n_edges: int, seed: int) -> Batch:
     """Undirected-edge batch for a symmetric A: half INSERTs of edges drawn
     without replacement from the held-out pool ``held`` = (u, v, w), half
