@@ -113,6 +113,8 @@ typedef struct {
     int64_t est_rows;       /* rows sized by the learned estimator */
     int64_t est_overflows;  /* of those, rows whose table was too small (counted exactly, recomputed) */
     int64_t algebraic;      /* 1: the batch took the delta path of Eq. 1 (dspg_apply_batch_algebraic) */
+    int64_t table_slots;    /* accumulator slots of the recompute's rows (hash-table or dense-row size per
+                               row, summed; what the sizing decides, the learned estimator's gain) */
 } dspg_batch_stats;
 
 /* Stages of apply_batch, in pipeline order, for dspg_stage_times. */
@@ -137,6 +139,34 @@ typedef struct dspg_handle dspg_handle;
  * Returns DSPG_ERR_INVALID for a non-canonical or out-of-range input. */
 dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, dspg_semiring sr,
                        const dspg_options *opt, void *stream);
+
+/* The general product form of Section 3: C = alpha op(A) op(B) (+) beta X,
+ * where op is the identity or the transpose (Section 5.3, handling
+ * transposition).  In (+,.): alpha (x) p = alpha p and (+) = +; in (min,+):
+ * alpha (x) p = alpha + p and (+) = min.
+ *   trans_a, trans_b: 1 = the product uses A^T (B^T).  The operand is stored
+ *     transposed (built on the device); batches of A and B and dspg_read_A
+ *     stay in the caller's coordinates (an update (i, j) of A is applied as
+ *     (j, i) to A^T).  With B == NULL (B is A) and trans_a != trans_b (for
+ *     instance A^T A), the library keeps A and A^T and every batch of A
+ *     updates both.
+ *   alpha, beta (+,.) or alpha_i, beta_i ((min,+), |.| < 2^29): the scalars.
+ *   X: NULL, or a canonical CSR with the shape of op(A) op(B); borrowed for
+ *     the call (copied), fixed afterwards.
+ * The handle keeps P = op(A) op(B) up to date; alpha, beta and X are applied
+ * when rows are read (dspg_read_C, dspg_read_rows_C): the rows of C a batch
+ * can change are the rows of P it recomputes (dspg_last_affected).  A form
+ * with alpha = 1 (alpha_i = 0) and no X reads P itself.  dspg_footprint
+ * rejects handles with a transposed operand.  Returns DSPG_ERR_INVALID for
+ * mismatched shapes, an X of the wrong shape, or out-of-range scalars. */
+typedef struct {
+    int32_t trans_a, trans_b;
+    double alpha, beta;
+    int32_t alpha_i, beta_i;
+    const dspg_csr *X;
+} dspg_form;
+dspg_status dspg_build_form(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, dspg_semiring sr,
+                            const dspg_form *form, const dspg_options *opt, void *stream);
 
 /* Apply one batch to A (dA) and to B (dB; must be NULL or empty when B is
  * A) and bring C up to date: C' = A' B' (Section 5, general updates).

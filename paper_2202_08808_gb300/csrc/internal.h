@@ -164,6 +164,19 @@ void run_alg_contrib(int sr, const AlgJob &J, const MatView &A, const MatView &B
 void run_alg_append(int sr, const AlgNew &N, const MatView &C, Ctl *ctl, unsigned plan_mask, unsigned copy_mask,
                     int slack_min, int slack_div, bool plan, cudaStream_t s, int num_sms);
 
+// form.cu: C = alpha op(A) op(B) (+) beta X (Section 3), transposed operands
+struct FormScalars {
+    double alpha, beta;       // (+,.)
+    int32_t alpha_i, beta_i;  // (min,+): added to the products / to X
+};
+void permute_entries(const uint32_t *idx, const uint32_t *row_of, const void *val, int64_t nnz, int32_t *out_col,
+                     void *out_val, int vsize, cudaStream_t s, int num_sms);
+void form_count(const int32_t *rows, int64_t n, const MatView &P, const int64_t *xrp, const int32_t *xcol,
+                int64_t *cnt, cudaStream_t s, int num_sms);
+void form_merge(int sr, const int32_t *rows, int64_t n, const int64_t *prp, const int32_t *pcol, const void *pval,
+                const int64_t *xrp, const int32_t *xcol, const void *xval, const int64_t *orp, int32_t *ocol,
+                void *oval, const FormScalars &f, cudaStream_t s, int num_sms);
+
 // spgemm.cu
 constexpr int64_t DENSE_M_MAX = 1024;  // C columns up to this use dense accumulators
 void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const CJob &J, int64_t max_rows, Ctl *ctl,
@@ -171,6 +184,9 @@ void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const C
 void run_numeric(int sr, const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,
                  const cudaStream_t *ss, int ns, int num_sms);
 void init_dense_scratch(int sr, void *acc, uint32_t *mask, int64_t entries, int64_t words, cudaStream_t s);
+// Accumulator slots a row of bin `bin` gets (hash table or dense row of m
+// columns; 0 for the thread-merge bins, which keep no table).
+int64_t bin_table_slots(int bin, int64_t m);
 
 // Message for dspg_last_error(NULL) on the calling thread (handle.cu).
 void set_thread_error(const char *msg);

@@ -1719,6 +1719,27 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
     launch_k(k_num_gdense<SR>, grid_for(J.gd_ctas, J.rows_hint, 1), 512, 0, next(), A, B, C, J, ctl, mask, (int)BIN_GD);
 }
 
+int64_t bin_table_slots(int bin, int64_t m) {
+    switch (bin) {
+        case BIN_G8: return 32;
+        case BIN_G16: return 64;
+        case BIN_W128: return 128;
+        case BIN_W256: return 256;
+        case BIN_W512: return 512;
+        case BIN_W1024: return 1024;
+        case BIN_C2048: return 2048;
+        case BIN_C4096: return 4096;
+        case BIN_C8192: return 8192;
+        case BIN_C16384: return 16384;
+        case BIN_K2: return 2 * 8192;
+        case BIN_K4: return 4 * 8192;
+        case BIN_K8: return 8 * 8192;
+        case BIN_K8L: return 8 * 16384;
+        case BIN_GD: case BIN_WDENSE: case BIN_CDENSE: case BIN_DSPLIT: return m;
+        default: return 0;  // the thread-merge bins stage the row's products, no table
+    }
+}
+
 void run_numeric(int sr, const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,
                  const cudaStream_t *ss, int ns, int num_sms) {
     if (sr == SR_PT) run_numeric_t<SR_PT>(A, B, C, J, ctl, mask, ss, ns, num_sms);

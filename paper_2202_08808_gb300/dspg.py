@@ -56,11 +56,16 @@ class _Opt(C.Structure):
                 ("keep_transpose", C.c_int32), ("exact_static", C.c_int32)]
 
 
+class _Form(C.Structure):
+    _fields_ = [("trans_a", C.c_int32), ("trans_b", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double),
+                ("alpha_i", C.c_int32), ("beta_i", C.c_int32), ("X", C.POINTER(_Csr))]
+
+
 class _Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "n_updates", "n_unique", "n_insert", "n_update", "n_delete", "n_noop", "touched_rows", "affected_rows",
         "products", "nnz_written", "relocations", "compactions", "a_entries", "est_rows", "est_overflows",
-        "algebraic")]
+        "algebraic", "table_slots")]
 
 
 class _Tuning(C.Structure):
@@ -82,6 +87,9 @@ def load():
         p, i64, i32 = C.c_void_p, C.c_int64, C.c_int
         lib.dspg_build.restype = i32
         lib.dspg_build.argtypes = [C.POINTER(p), C.POINTER(_Csr), C.POINTER(_Csr), i32, C.POINTER(_Opt), p]
+        lib.dspg_build_form.restype = i32
+        lib.dspg_build_form.argtypes = [C.POINTER(p), C.POINTER(_Csr), C.POINTER(_Csr), i32, C.POINTER(_Form),
+                                        C.POINTER(_Opt), p]
         lib.dspg_apply_batch.restype = i32
         lib.dspg_apply_batch.argtypes = [p, C.POINTER(_Upd), C.POINTER(_Upd), C.POINTER(_Stats), p]
         lib.dspg_apply_batch_algebraic.restype = i32
@@ -152,7 +160,7 @@ def load():
         return lib
 
 
-EXPORTED = ["dspg_build", "dspg_apply_batch", "dspg_apply_batch_algebraic", "dspg_read_C", "dspg_read_A", "dspg_read_rows_C",
+EXPORTED = ["dspg_build", "dspg_build_form", "dspg_apply_batch", "dspg_apply_batch_algebraic", "dspg_read_C", "dspg_read_A", "dspg_read_rows_C",
             "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_set_profiling", "dspg_stage_times",
             "dspg_kernel_launches", "dspg_multiply_rows_noalloc", "dspg_set_tuning", "dspg_get_tuning",
             "dspg_tuning_candidate", "dspg_autotune", "dspg_group_create", "dspg_group_apply", "dspg_group_destroy",
@@ -247,10 +255,16 @@ class DynamicSpGEMM:
 
     ``A`` (and ``B``) are objects with ``nrows, ncols, rowptr, col, val``
     (e.g. ``workloads.CSR``; arrays may be numpy or torch). ``B=None`` means
-    C = A A with one batch updating both operands."""
+    C = A A with one batch updating both operands.
+
+    The general form C = alpha op(A) op(B) (+) beta X (dspg_build_form):
+    ``trans_a``/``trans_b`` multiply by the transposes, ``alpha``/``beta``
+    scale (multiply in (+,.), add in (min,+)) and ``X`` is a fixed matrix of
+    C's shape; batches stay in the caller's coordinates."""
 
     def __init__(self, A, B=None, semiring: int | None = None, slack_min: int = 4, slack_div: int = 4,
-                 arena_headroom: float = 1.5, keep_transpose: int = -1, exact_static: int = 0, stream=None):
+                 arena_headroom: float = 1.5, keep_transpose: int = -1, exact_static: int = 0, stream=None,
+                 trans_a: bool = False, trans_b: bool = False, alpha=None, beta=None, X=None):
         self._lib = load()
         self._h = C.c_void_p()
         if semiring is None:
@@ -260,8 +274,21 @@ class DynamicSpGEMM:
         ca = self._csr(A, keep)
         cb = self._csr(B, keep) if B is not None else None
         opt = _Opt(slack_min, slack_div, arena_headroom, keep_transpose, exact_static)
-        st = self._lib.dspg_build(C.byref(self._h), C.byref(ca), C.byref(cb) if cb is not None else None,
-                                  semiring, C.byref(opt), _stream(stream))
+        if trans_a or trans_b or alpha is not None or beta is not None or X is not None:
+            cx = self._csr(X, keep) if X is not None else None
+            pt = semiring == PLUS_TIMES_F64
+            form = _Form(int(trans_a), int(trans_b),
+                         float(alpha if alpha is not None else 1.0) if pt else 0.0,
+                         float(beta if beta is not None else 1.0) if pt else 0.0,
+                         0 if pt else int(alpha if alpha is not None else 0),
+                         0 if pt else int(beta if beta is not None else 0),
+                         C.pointer(cx) if cx is not None else None)
+            keep.append(cx)
+            st = self._lib.dspg_build_form(C.byref(self._h), C.byref(ca), C.byref(cb) if cb is not None else None,
+                                           semiring, C.byref(form), C.byref(opt), _stream(stream))
+        else:
+            st = self._lib.dspg_build(C.byref(self._h), C.byref(ca), C.byref(cb) if cb is not None else None,
+                                      semiring, C.byref(opt), _stream(stream))
         if st != 0:
             raise DspgError(st, self._lib.dspg_last_error(None).decode())
         self.b_is_a = B is None

@@ -158,3 +158,41 @@ def test_learned_sizing_inside_a_group(dspg):
             oracle.row_dynamic(Aos[t], Cos[t], bs[t])
             C_o, S_o = oracle_product(Aos[t], Aos[t])
             assert_matches(gs[t].read_C(), C_o, S_o, what=f"rep {rep} member {t}")
+
+
+def test_learned_sizing_gain_over_the_bound(dspg):
+    """What the trained network buys over sizing without it, measured in
+    memory the recompute reserves (not time): on the same R-MAT stream, the
+    learned tables of the rows it sizes, plus the second tables of the rows
+    whose prediction was too small, take fewer accumulator slots than tables
+    sized by the product bound (the method without the network); and unlike
+    exact sizing it needs no count-only pass over every product first.  C'
+    is the oracle's in all three."""
+    est, _, _ = _trained_estimator(dspg)
+    A, held = rmat_symmetric(13, 8, G500, seed=131, kind=PLUS_TIMES_F64, holdout=8000)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    batches = [rmat_edge_batch(A, held, 1000, seed=132 + k) for k in range(3)]
+    slots, ovf, rows_est = {}, 0, 0
+    for mode in ("bound", "exact", "learned"):
+        g = dspg.DynamicSpGEMM(A)
+        if mode == "exact":
+            g.set_sizing(dspg.SIZE_EXACT)
+        elif mode == "learned":
+            g.set_sizing(dspg.SIZE_LEARNED, est, est_min=0, margin=0.25)
+        Am, Cm = Ao.copy(), Co.copy()
+        total = 0
+        for k, b in enumerate(batches):
+            st = g.apply_batch(b)
+            oracle.row_dynamic(Am, Cm, b)
+            C_o, S_o = oracle_product(Am, Am)
+            assert_matches(g.read_C(), C_o, S_o, what=f"{mode} batch {k}")
+            total += st["table_slots"]
+            if mode == "learned":
+                ovf += st["est_overflows"]
+                rows_est += st["est_rows"]
+        slots[mode] = total
+        g.close()
+    print("table slots", slots, "estimated rows", rows_est, "overflows", ovf)
+    assert rows_est > 0 and ovf <= 0.05 * rows_est
+    assert slots["exact"] <= slots["learned"] < 0.8 * slots["bound"], slots
