@@ -198,7 +198,8 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
 dspg_status dspg_apply_batch_algebraic(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
                                        dspg_batch_stats *stats, void *stream);
 
-/* Read C in canonical CSR (rows in order, columns ascending) into caller
+/* Read C (with dspg_build_form: alpha op(A) op(B) (+) beta X) in canonical
+ * CSR (rows in order, columns ascending) into caller
  * buffers: rowptr[nrows+1], col[nnz], val[nnz], host or device per
  * on_device (host buffers may be pageable or page-locked; page-locked ones
  * are copied to at full speed).  Two-call convention: with rowptr == NULL
@@ -208,7 +209,9 @@ dspg_status dspg_apply_batch_algebraic(dspg_handle *h, const dspg_updates *dA, c
 dspg_status dspg_read_C(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32_t *col, void *val,
                         int on_device, void *stream);
 
-/* Read A' (the updated left operand) in canonical CSR; same convention. */
+/* Read A' (the updated left operand) in canonical CSR; same convention.
+ * A' is in the caller's coordinates: rowptr has A->nrows + 1 entries of the
+ * A given to dspg_build (dspg_build_form turns a stored transpose back). */
 dspg_status dspg_read_A(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32_t *col, void *val,
                         int on_device, void *stream);
 

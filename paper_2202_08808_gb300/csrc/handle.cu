@@ -17,6 +17,7 @@
 // from the failed one.  Nothing is mutated before the stage that overflowed
 // has succeeded, so the handle always stays consistent.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -359,6 +360,16 @@ struct dspg_handle {
     FpWs fp;                                    // footprints (serving)
     AlgWs alg;                                  // the delta path (algebraic updates)
     bool last_alg = false;                      // the last batch took the delta path
+    // the product form (Section 3): C = alpha op(A) op(B) (+) beta X
+    bool trans_a = false, trans_b = false;      // op = transpose: the operand is stored transposed
+    bool b_alias = false;                       // the caller's B is A, stored apart (one side transposed)
+    bool form = false;                          // reads apply alpha, beta and X
+    FormScalars fs{1.0, 1.0, 0, 0};
+    bool has_x = false;
+    DBuf<int64_t> xrp;                          // X (canonical CSR, library-owned)
+    DBuf<int32_t> xcol;
+    DBuf<char> xval;
+    int64_t extra_slots = 0;                    // table slots of the last batch's overflow recompute
     int64_t compactions = 0;
     std::string err;
 
@@ -937,18 +948,21 @@ void reset_c_counters(dspg_handle *h, cudaStream_t s) {
 
 // Host batches are copied to the device; device batches are read where
 // they are.  Either way the pointers go to the argument block slot k.
-void upload(dspg_handle *h, UpdWs &w, const dspg_updates *u, BatchIn &in, int k, cudaStream_t s) {
+// A transposed operand takes the caller's (i, j) as (j, i): the row and
+// column arrays trade places (swap).
+void upload(dspg_handle *h, UpdWs &w, const dspg_updates *u, BatchIn &in, int k, cudaStream_t s, bool swap = false) {
     in.n = u ? u->n : 0;
     h->h_args[k] = InArgs{nullptr, nullptr, nullptr, nullptr};
     if (in.n <= 0) return;
+    const int32_t *ur = swap ? u->col : u->row, *uc = swap ? u->row : u->col;
     if (u->on_device) {
-        in.row = u->row;
-        in.col = u->col;
+        in.row = ur;
+        in.col = uc;
         in.val = u->val;
         in.op = u->op;
     } else {
-        CK(cudaMemcpyAsync(w.in_row.p, u->row, sizeof(int32_t) * in.n, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(w.in_col.p, u->col, sizeof(int32_t) * in.n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w.in_row.p, ur, sizeof(int32_t) * in.n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w.in_col.p, uc, sizeof(int32_t) * in.n, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(w.in_val.p, u->val, (size_t)h->vsize * in.n, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(w.in_op.p, u->op, sizeof(uint8_t) * in.n, cudaMemcpyHostToDevice, s));
         in.row = w.in_row.p;
@@ -1076,6 +1090,67 @@ void init_slack_from_csr(dspg_handle *h, DevMat &M, const dspg_csr *m, cudaStrea
     make_slack(h, M, m->nrows, m->ncols, h->vsize, rp_d, len.p, col_d, val_d, s);
 }
 
+// Transpose of a canonical CSR on the device (nrows x ncols, nnz entries):
+// the entries are sorted by column with a stable radix sort of their
+// indices, which keeps each column's rows ascending, then gathered with
+// their row and value.  Outputs: trp (ncols + 1 row pointers), tlen (ncols
+// row lengths), tcol, tval.
+void transpose_device(dspg_handle *h, int64_t nrows, int64_t ncols, int64_t nnz, const int64_t *rp, const int32_t *col,
+                      const void *val, int vsize, DBuf<int64_t> &trp, DBuf<int32_t> &tlen, DBuf<int32_t> &tcol,
+                      DBuf<char> &tval, cudaStream_t s) {
+    trp.reserve(ncols + 1);
+    tlen.reserve(std::max<int64_t>(ncols, 1));
+    tcol.reserve(std::max<int64_t>(nnz, 1));
+    tval.reserve(std::max<int64_t>(nnz, 1) * std::max(vsize, 1));
+    CK(cudaMemsetAsync(tlen.p, 0, sizeof(int32_t) * tlen.n, s));
+    if (nnz > 0) {
+        if (nnz >= (int64_t(1) << 32)) throw Err(DSPG_ERR_INVALID, "too many entries to transpose");
+        DBuf<uint64_t> k0, k1;
+        DBuf<uint32_t> i0, i1, counts, row_of;
+        DBuf<int64_t> scan_tmp, scan_out;
+        k0.reserve(nnz); k1.reserve(nnz); i0.reserve(nnz); i1.reserve(nnz); row_of.reserve(nnz);
+        int64_t cnt;
+        sort_tmp_sizes(nnz, &cnt);
+        counts.reserve(cnt);
+        scan_out.reserve(cnt + 1);
+        scan_tmp.reserve(scan_tmp_entries(cnt) + 1);
+        keys_from_cols(col, nnz, k0.p, s);
+        fill_iota((int32_t *)i0.p, nnz, s);
+        bool alt = false;
+        radix_sort_pairs(k0.p, i0.p, k1.p, i1.p, nnz, bits_for(std::max<int64_t>(ncols, 2)), counts.p, scan_tmp.p,
+                         scan_out.p, s, &alt);
+        rows_of_entries(rp, nrows, row_of.p, s, h->num_sms);
+        permute_entries(alt ? i1.p : i0.p, row_of.p, val, nnz, tcol.p, vsize ? (void *)tval.p : nullptr, vsize, s,
+                        h->num_sms);
+        hist_cols(col, nnz, tlen.p, s);
+    }
+    DBuf<int64_t> tmp;
+    tmp.reserve(scan_tmp_entries(ncols) + 1);
+    scan_i32_to_i64(tlen.p, trp.p, ncols, tmp.p, s);
+    CK(cudaStreamSynchronize(s));  // the temporaries are freed on return
+}
+
+// An operand of the product from the caller's CSR: as given, or stored
+// transposed when the product uses its transpose.
+void load_operand(dspg_handle *h, DevMat &M, const dspg_csr *m, bool trans, cudaStream_t s) {
+    if (!trans) {
+        init_slack_from_csr(h, M, m, s);
+        return;
+    }
+    DBuf<int64_t> rp;
+    DBuf<int32_t> col;
+    DBuf<char> val;
+    const int64_t *rp_d;
+    const int32_t *col_d;
+    const void *val_d;
+    load_csr(h, m, rp, col, val, &rp_d, &col_d, &val_d, s);
+    DBuf<int64_t> trp;
+    DBuf<int32_t> tlen, tcol;
+    DBuf<char> tval;
+    transpose_device(h, m->nrows, m->ncols, m->nnz, rp_d, col_d, val_d, h->vsize, trp, tlen, tcol, tval, s);
+    make_slack(h, M, m->ncols, m->nrows, h->vsize, trp.p, tlen.p, tcol.p, tval.p, s);
+}
+
 int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, int64_t *rowptr, int32_t *col,
                  void *val, int on_device, cudaStream_t s) {
     DBuf<int32_t> rows_l;
@@ -1193,22 +1268,116 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
     return nnz;
 }
 
+// Rows of C = alpha P (+) beta X, where P = op(A) op(B) is what the handle
+// keeps (all rows when rows_in is NULL): sized by form_count, then P's rows
+// are read canonically into scratch and merged with X's rows.
+int64_t read_form(dspg_handle *h, const int32_t *rows_in, int64_t nr, int64_t *rowptr, int32_t *col, void *val,
+                  int on_device, cudaStream_t s) {
+    const int64_t n = rows_in ? nr : h->C.nrows;
+    DBuf<int32_t> rows_d;
+    const int32_t *rows = nullptr;
+    if (rows_in) {
+        if (on_device) rows = rows_in;
+        else {
+            rows_d.reserve(std::max<int64_t>(n, 1));
+            if (n > 0) CK(cudaMemcpyAsync(rows_d.p, rows_in, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+            rows = rows_d.p;
+        }
+    }
+    DBuf<int64_t> cnt, orp, tmp;
+    cnt.reserve(std::max<int64_t>(n, 1));
+    orp.reserve(n + 1);
+    tmp.reserve(scan_tmp_entries(n) + 1);
+    const int64_t *xrp = h->has_x ? h->xrp.p : nullptr;
+    DBuf<int64_t> zrp;  // no X: empty rows
+    if (!xrp) {
+        zrp.reserve(h->C.nrows + 1);
+        CK(cudaMemsetAsync(zrp.p, 0, sizeof(int64_t) * (h->C.nrows + 1), s));
+        xrp = zrp.p;
+    }
+    form_count(rows, n, h->C.view(), xrp, h->xcol.p, cnt.p, s, h->num_sms);
+    scan_i64(cnt.p, orp.p, n, tmp.p, s);
+    const int64_t nnz = read_i64(orp.p + n, s);
+    if (!rowptr) return nnz;
+    // P's rows, canonical, into scratch
+    DBuf<int64_t> prp;
+    DBuf<int32_t> pcol;
+    DBuf<char> pval;
+    prp.reserve(n + 1);
+    const int64_t pn = read_mat(h, h->C, rows, rows ? n : 0, nullptr, nullptr, nullptr, 1, s);
+    pcol.reserve(std::max<int64_t>(pn, 1));
+    pval.reserve(std::max<int64_t>(pn, 1) * h->vsize);
+    read_mat(h, h->C, rows, rows ? n : 0, prp.p, pcol.p, pval.p, 1, s);
+    DBuf<int32_t> ocol_l;
+    DBuf<char> oval_l;
+    int32_t *ocol = col;
+    void *oval = val;
+    if (!on_device) {
+        ocol_l.reserve(std::max<int64_t>(nnz, 1));
+        oval_l.reserve(std::max<int64_t>(nnz, 1) * h->vsize);
+        ocol = ocol_l.p;
+        oval = oval_l.p;
+    }
+    form_merge(h->sr, rows, n, prp.p, pcol.p, pval.p, xrp, h->xcol.p, h->xval.p, orp.p, ocol, oval, h->fs, s,
+               h->num_sms);
+    if (on_device) {
+        CK(cudaMemcpyAsync(rowptr, orp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
+    } else {
+        CK(cudaMemcpyAsync(rowptr, orp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+        if (nnz > 0) {
+            if (col) CK(cudaMemcpyAsync(col, ocol, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s));
+            if (val) CK(cudaMemcpyAsync(val, oval, (size_t)h->vsize * nnz, cudaMemcpyDeviceToHost, s));
+        }
+    }
+    CK(cudaStreamSynchronize(s));
+    return nnz;
+}
+
+// A as the caller gave it (its stored transpose turned back when the
+// product uses A^T).
+int64_t read_operand_a(dspg_handle *h, int64_t *rowptr, int32_t *col, void *val, int on_device, cudaStream_t s) {
+    if (!h->trans_a) return read_mat(h, h->A, nullptr, 0, rowptr, col, val, on_device, s);
+    const int64_t nnz = read_mat(h, h->A, nullptr, 0, nullptr, nullptr, nullptr, 1, s);
+    if (!rowptr) return nnz;
+    DBuf<int64_t> srp;
+    DBuf<int32_t> scol;
+    DBuf<char> sval;
+    srp.reserve(h->A.nrows + 1);
+    scol.reserve(std::max<int64_t>(nnz, 1));
+    sval.reserve(std::max<int64_t>(nnz, 1) * h->vsize);
+    read_mat(h, h->A, nullptr, 0, srp.p, scol.p, sval.p, 1, s);
+    DBuf<int64_t> trp;
+    DBuf<int32_t> tlen, tcol;
+    DBuf<char> tval;
+    transpose_device(h, h->A.nrows, h->A.ncols, nnz, srp.p, scol.p, sval.p, h->vsize, trp, tlen, tcol, tval, s);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(rowptr, trp.p, sizeof(int64_t) * (h->A.ncols + 1), k, s));
+    if (nnz > 0) {
+        if (col) CK(cudaMemcpyAsync(col, tcol.p, sizeof(int32_t) * nnz, k, s));
+        if (val) CK(cudaMemcpyAsync(val, tval.p, (size_t)h->vsize * nnz, k, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return nnz;
+}
+
 // Checks one batch pair and gets the handle's buffers and inputs ready.
 void prepare_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, cudaStream_t s) {
     h->c_serial++;
+    h->extra_slots = 0;
+    if ((h->b_is_a || h->b_alias) && dB && dB->n > 0) throw Err(DSPG_ERR_INVALID, "B is A: pass the batch as dA only");
+    if (h->b_alias) dB = dA;  // the caller's B is A: its stored copy takes the same batch
     const int64_t nA = dA ? dA->n : 0, nB = dB ? dB->n : 0;
     if (nA < 0 || nB < 0) throw Err(DSPG_ERR_INVALID, "negative batch size");
     if (nA > INT32_MAX / 2 || nB > INT32_MAX / 2) throw Err(DSPG_ERR_INVALID, "batch too large");
     if (nA > 0 && (!dA->row || !dA->col || !dA->val || !dA->op)) throw Err(DSPG_ERR_INVALID, "NULL array in dA");
     if (nB > 0 && (!dB->row || !dB->col || !dB->val || !dB->op)) throw Err(DSPG_ERR_INVALID, "NULL array in dB");
-    if (h->b_is_a && nB > 0) throw Err(DSPG_ERR_INVALID, "B is A: pass the batch as dA only");
     if (!h->b_is_a && nB > 0 && !h->has_at) build_transpose(h, s);
     ensure_c_ws(h, s);
     if (h->wA.ensure(nA, h->A.arena_cap)) h->epoch++;
     if (!h->b_is_a && h->wB.ensure(nB, h->B.arena_cap)) h->epoch++;
     if (h->has_at && h->wAT.ensure(nA, h->AT.arena_cap)) h->epoch++;
-    upload(h, h->wA, dA, h->inA, 0, s);
-    upload(h, h->wB, dB, h->inB, 1, s);
+    upload(h, h->wA, dA, h->inA, 0, s, h->trans_a);
+    upload(h, h->wB, dB, h->inB, 1, s, h->trans_b);
     if (h->b_is_a) {
         h->inB = BatchIn{};
         h->h_args[1] = InArgs{nullptr, nullptr, nullptr, nullptr};
@@ -1301,6 +1470,9 @@ void fill_stats(dspg_handle *h, dspg_batch_stats *stats, int64_t compactions0) {
         stats->a_entries = c.a_entries;
         stats->est_rows = c.n_est;
         stats->est_overflows = c.n_ovf;
+        const int64_t m = h->Bm().ncols;
+        for (int b = 0; b < NBINS; b++) stats->table_slots += c.bin_count[b] * bin_table_slots(b, m);
+        stats->table_slots += h->extra_slots;
     }
 }
 
@@ -1328,6 +1500,8 @@ void est_fallback(dspg_handle *h, cudaStream_t s) {
     CK(cudaMemcpyAsync(&h->ctl->n_affected, &main.n_affected, sizeof(long long), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     const long long reloc = h->hctl->c_reloc;
+    // the overflow rows' second tables count too (the estimator's cost)
+    for (int b = 0; b < NBINS; b++) h->extra_slots += h->hctl->bin_count[b] * bin_table_slots(b, h->Bm().ncols);
     *h->hctl = main;
     h->hctl->c_reloc += reloc;
 }
@@ -1556,20 +1730,37 @@ cudaGraphExec_t capture_recompute(dspg_handle *h) {
 
 extern "C" {
 
-dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, dspg_semiring sr,
-                       const dspg_options *opt, void *stream) {
+dspg_status dspg_build_form(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, dspg_semiring sr,
+                            const dspg_form *form, const dspg_options *opt, void *stream) {
     dspg_handle *h = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     try {
         if (!out) throw Err(DSPG_ERR_INVALID, "out is NULL");
         *out = nullptr;
         if (sr != DSPG_PLUS_TIMES_F64 && sr != DSPG_MIN_PLUS_I32) throw Err(DSPG_ERR_INVALID, "unknown semiring");
+        const bool ta = form && form->trans_a, tb = form && form->trans_b;
         check_csr_arg(A, "A");
+        const int64_t a_rows = ta ? A->ncols : A->nrows, a_cols = ta ? A->nrows : A->ncols;
+        int64_t b_rows, b_cols;
         if (B) {
             check_csr_arg(B, "B");
-            if (A->ncols != B->nrows) throw Err(DSPG_ERR_INVALID, "A.ncols != B.nrows");
-        } else if (A->nrows != A->ncols) {
-            throw Err(DSPG_ERR_INVALID, "B == NULL (B is A) needs a square A");
+            b_rows = tb ? B->ncols : B->nrows;
+            b_cols = tb ? B->nrows : B->ncols;
+        } else {
+            b_rows = tb ? A->ncols : A->nrows;
+            b_cols = tb ? A->nrows : A->ncols;
+        }
+        if (a_cols != b_rows) throw Err(DSPG_ERR_INVALID, "the inner dimensions of op(A) op(B) differ");
+        if (form && sr == DSPG_MIN_PLUS_I32 &&
+            (form->alpha_i <= -MP_LIMIT / 2 || form->alpha_i >= MP_LIMIT / 2 || form->beta_i <= -MP_LIMIT / 2 ||
+             form->beta_i >= MP_LIMIT / 2))
+            throw Err(DSPG_ERR_INVALID, "(min,+) alpha and beta must be below 2^29 in magnitude");
+        if (form && sr == DSPG_PLUS_TIMES_F64 && (!std::isfinite(form->alpha) || !std::isfinite(form->beta)))
+            throw Err(DSPG_ERR_INVALID, "alpha and beta must be finite");
+        if (form && form->X) {
+            check_csr_arg(form->X, "X");
+            if (form->X->nrows != a_rows || form->X->ncols != b_cols)
+                throw Err(DSPG_ERR_INVALID, "X must have the shape of op(A) op(B)");
         }
         h = new dspg_handle();
         set_defaults(&h->opt);
@@ -1582,6 +1773,13 @@ dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, 
         }
         h->sr = sr;
         h->vsize = sr == DSPG_PLUS_TIMES_F64 ? 8 : 4;
+        h->trans_a = ta;
+        h->trans_b = tb;
+        if (form) {
+            h->fs = FormScalars{form->alpha, form->beta, form->alpha_i, form->beta_i};
+            const bool unit = sr == DSPG_PLUS_TIMES_F64 ? form->alpha == 1.0 : form->alpha_i == 0;
+            h->form = !unit || form->X != nullptr;
+        }
         CK(cudaGetDevice(&h->dev));
         CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev));
         CK(cudaMalloc((void **)&h->ctl, sizeof(Ctl)));
@@ -1604,11 +1802,37 @@ dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, 
         h->wA.which = 0; h->wA.vsize = h->vsize;
         h->wB.which = 1; h->wB.vsize = h->vsize;
         h->wAT.which = 2; h->wAT.vsize = 0;
-        init_slack_from_csr(h, h->A, A, s);
-        h->b_is_a = (B == nullptr);
-        if (!h->b_is_a) init_slack_from_csr(h, h->B, B, s);
-        // C = A A needs the transposed pattern for every batch; otherwise it is built on the first B batch
-        const bool keep_t = h->b_is_a || h->opt.keep_transpose > 0;
+        load_operand(h, h->A, A, ta, s);
+        // B is A: one stored operand when both sides are (or neither is)
+        // transposed; otherwise a stored copy of A, transposed as its side
+        // asks, that every batch of A updates too
+        h->b_is_a = (B == nullptr) && ta == tb;
+        h->b_alias = (B == nullptr) && ta != tb;
+        if (B) load_operand(h, h->B, B, tb, s);
+        else if (h->b_alias) load_operand(h, h->B, A, tb, s);
+        if (form && form->X) {
+            DBuf<int64_t> rp;
+            DBuf<int32_t> col;
+            DBuf<char> val;
+            const int64_t *rp_d;
+            const int32_t *col_d;
+            const void *val_d;
+            load_csr(h, form->X, rp, col, val, &rp_d, &col_d, &val_d, s);
+            const int64_t nx = form->X->nnz;
+            h->xrp.reserve(form->X->nrows + 1);
+            h->xcol.reserve(std::max<int64_t>(nx, 1));
+            h->xval.reserve(std::max<int64_t>(nx, 1) * h->vsize);
+            CK(cudaMemcpyAsync(h->xrp.p, rp_d, sizeof(int64_t) * (form->X->nrows + 1), cudaMemcpyDeviceToDevice, s));
+            if (nx > 0) {
+                CK(cudaMemcpyAsync(h->xcol.p, col_d, sizeof(int32_t) * nx, cudaMemcpyDeviceToDevice, s));
+                CK(cudaMemcpyAsync(h->xval.p, val_d, (size_t)h->vsize * nx, cudaMemcpyDeviceToDevice, s));
+            }
+            CK(cudaStreamSynchronize(s));
+            h->has_x = true;
+        }
+        // C = A A (and a stored copy of A as B) needs the transposed pattern
+        // for every batch; otherwise it is built on the first B batch
+        const bool keep_t = h->b_is_a || h->b_alias || h->opt.keep_transpose > 0;
         if (keep_t) build_transpose(h, s);
         static_recompute(h, s);
         *out = h;
@@ -1619,6 +1843,11 @@ dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, 
         if (out) *out = nullptr;
         return e.st;
     }
+}
+
+dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, dspg_semiring sr,
+                       const dspg_options *opt, void *stream) {
+    return dspg_build_form(out, A, B, sr, nullptr, opt, stream);
 }
 
 dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
@@ -1658,7 +1887,8 @@ dspg_status dspg_read_C(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32
                         void *stream) {
     if (!h || !nnz_out) return DSPG_ERR_INVALID;
     try {
-        *nnz_out = read_mat(h, h->C, nullptr, 0, rowptr, col, val, on_device, (cudaStream_t)stream);
+        *nnz_out = h->form ? read_form(h, nullptr, 0, rowptr, col, val, on_device, (cudaStream_t)stream)
+                           : read_mat(h, h->C, nullptr, 0, rowptr, col, val, on_device, (cudaStream_t)stream);
         return DSPG_OK;
     } catch (const Err &e) {
         return fail(h, e);
@@ -1669,7 +1899,7 @@ dspg_status dspg_read_A(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32
                         void *stream) {
     if (!h || !nnz_out) return DSPG_ERR_INVALID;
     try {
-        *nnz_out = read_mat(h, h->A, nullptr, 0, rowptr, col, val, on_device, (cudaStream_t)stream);
+        *nnz_out = read_operand_a(h, rowptr, col, val, on_device, (cudaStream_t)stream);
         return DSPG_OK;
     } catch (const Err &e) {
         return fail(h, e);
@@ -1684,8 +1914,9 @@ dspg_status dspg_read_rows_C(dspg_handle *h, const int32_t *rows, int64_t nrows,
             for (int64_t i = 0; i < nrows; i++)
                 if (rows[i] < 0 || rows[i] >= h->C.nrows) throw Err(DSPG_ERR_INVALID, "row index out of range");
         }
-        *nnz_out = read_mat(h, h->C, rows ? rows : (const int32_t *)h->wc.iota.p, nrows, rowptr, col, val, on_device,
-                            (cudaStream_t)stream);
+        const int32_t *rr = rows ? rows : (const int32_t *)h->wc.iota.p;
+        *nnz_out = h->form ? read_form(h, rr, nrows, rowptr, col, val, on_device, (cudaStream_t)stream)
+                           : read_mat(h, h->C, rr, nrows, rowptr, col, val, on_device, (cudaStream_t)stream);
         return DSPG_OK;
     } catch (const Err &e) {
         return fail(h, e);
@@ -1767,7 +1998,8 @@ dspg_status dspg_info(dspg_handle *h, int64_t *n, int64_t *k, int64_t *m, int64_
         if (k) *k = h->A.ncols;
         if (m) *m = h->Bm().ncols;
         if (nnz_a) *nnz_a = read_mat(h, h->A, nullptr, 0, nullptr, nullptr, nullptr, 0, 0);
-        if (nnz_c) *nnz_c = read_mat(h, h->C, nullptr, 0, nullptr, nullptr, nullptr, 0, 0);
+        if (nnz_c) *nnz_c = h->form ? read_form(h, nullptr, 0, nullptr, nullptr, nullptr, 0, 0)
+                                    : read_mat(h, h->C, nullptr, 0, nullptr, nullptr, nullptr, 0, 0);
         return DSPG_OK;
     } catch (const Err &e) {
         return fail(h, e);
@@ -1930,6 +2162,8 @@ dspg_status dspg_footprint(dspg_handle *h, const dspg_updates *dA, uint32_t *f, 
     cudaStream_t s = (cudaStream_t)stream;
     try {
         if (!dA || !f) throw Err(DSPG_ERR_INVALID, "dA and f must not be NULL");
+        if (h->trans_a || h->trans_b || h->b_alias)
+            throw Err(DSPG_ERR_INVALID, "footprints are not available for a product with transposed operands");
         if (u && !admitted) throw Err(DSPG_ERR_INVALID, "admitted must not be NULL when u is given");
         const int64_t n = dA->n;
         if (n < 0 || (n > 0 && (!dA->row || !dA->col))) throw Err(DSPG_ERR_INVALID, "bad batch");

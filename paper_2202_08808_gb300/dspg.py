@@ -292,6 +292,7 @@ class DynamicSpGEMM:
         if st != 0:
             raise DspgError(st, self._lib.dspg_last_error(None).decode())
         self.b_is_a = B is None
+        self.a_shape = (int(A.nrows), int(A.ncols))  # the caller's A (read_A's shape)
 
     def _csr(self, M, keep) -> _Csr:
         rp, dev = _ptr(_as_int(M.rowptr, np.int64), keep)
@@ -336,11 +337,11 @@ class DynamicSpGEMM:
         self._check(st)
         return {name: getattr(stats, name) for name, _ in _Stats._fields_}
 
-    def _read(self, fn, ncols: int, stream=None) -> "CsrArrays":
+    def _read(self, fn, ncols: int, stream=None, nrows: int | None = None) -> "CsrArrays":
         s = _stream(stream)
         nnz = C.c_int64()
         self._check(fn(self._h, C.byref(nnz), None, None, None, 0, s))
-        n = self.info()["n"]
+        n = self.info()["n"] if nrows is None else nrows
         rp = _host_empty(n + 1, np.int64)
         col = _host_empty(nnz.value, np.int32)
         val = _host_empty(nnz.value, _vdtype(self.sr))
@@ -352,8 +353,8 @@ class DynamicSpGEMM:
         return self._read(self._lib.dspg_read_C, self.info()["m"], stream)
 
     def read_A(self, stream=None) -> "CsrArrays":
-        """A' in canonical CSR (host numpy arrays)."""
-        return self._read(self._lib.dspg_read_A, self.info()["k"], stream)
+        """A' in canonical CSR (host numpy arrays), in the caller's coordinates."""
+        return self._read(self._lib.dspg_read_A, self.a_shape[1], stream, nrows=self.a_shape[0])
 
     def read_C_device(self, stream=None):
         """C as torch device tensors (rowptr, col, val)."""

@@ -68,6 +68,7 @@ def test_binding_structs_mirror_the_header():
     assert [f for f, _ in b._Csr._fields_] == _struct_fields("dspg_csr")
     assert [f for f, _ in b._Upd._fields_] == _struct_fields("dspg_updates")
     assert [f for f, _ in b._Tuning._fields_] == _struct_fields("dspg_tuning")
+    assert [f for f, _ in b._Form._fields_] == _struct_fields("dspg_form")
 
 
 def test_tuning_candidates_start_with_the_defaults_and_stay_in_range():
