@@ -90,6 +90,7 @@ __device__ __forceinline__ void alg_apply(const MatView &C, const AlgJob &J, Ctl
 // contributions, those of the B batch (the A batch again when B is A) Y's.
 template <int SR>
 __global__ void k_alg_contrib(AlgJob J, MatView A, MatView B, MatView AT, MatView C, Ctl *ctl, unsigned mask) {
+    pdl_begin();
     using T = typename AlgSr<SR>::T;
     if (__any_sync(0xffffffffu, failed(ctl, mask))) return;  // a warp leaves as a whole
     const int lane = threadIdx.x & 31;
@@ -146,6 +147,7 @@ __global__ void k_alg_contrib(AlgJob J, MatView A, MatView B, MatView AT, MatVie
 // first entry of each row's run plans where the row goes (its own place if
 // the combined new entries fit its capacity, else the arena tail).
 __global__ void k_alg_plan(AlgNew N, MatView C, Ctl *ctl, unsigned mask, int slack_min, int slack_div) {
+    pdl_begin();
     if (failed(ctl, mask)) return;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N.n; s += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = N.row[s];
@@ -171,6 +173,7 @@ __global__ void k_alg_plan(AlgNew N, MatView C, Ctl *ctl, unsigned mask, int sla
 // the combined new entries after them.
 template <int SR>
 __global__ void k_alg_copy(AlgNew N, MatView C, Ctl *ctl, unsigned mask) {
+    pdl_begin();
     using T = typename AlgSr<SR>::T;
     if (failed(ctl, mask)) return;
     T *Cv = (T *)C.val;

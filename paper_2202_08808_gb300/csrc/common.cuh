@@ -111,6 +111,18 @@ __host__ __device__ inline int bits_for(int64_t x) {  // bits to hold values in 
 
 #ifdef __CUDACC__
 
+// Programmatic dependent launch: every kernel is launched so that it may
+// start while the kernel before it on the stream is finishing (launch_k).
+// Its first step waits until that kernel has completed and its writes are
+// visible (griddepcontrol.wait, a no-op without such a predecessor), then
+// lets its own successor start launching (launch_dependents), which will in
+// turn wait for this kernel's completion before reading anything.  So every
+// kernel calls pdl_begin() before its first access to global memory.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" :::);
+}
+
 __device__ __forceinline__ bool failed(const Ctl *ctl, unsigned mask) {
     return (*(volatile const unsigned *)&ctl->status & mask) != 0u;
 }
@@ -199,9 +211,27 @@ __device__ __forceinline__ int64_t run_end_dev(const T *a, int64_t s, int64_t n,
 unsigned long long &launch_counter();
 
 #ifdef __CUDACC__
+// The launch attribute that lets a kernel start before its predecessor on
+// the stream has finished (it waits in pdl_begin); in a captured graph it
+// becomes a programmatic dependency between the two kernel nodes.
+inline cudaLaunchAttribute pdl_attribute() {
+    cudaLaunchAttribute a;
+    a.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    a.val.programmaticStreamSerializationAllowed = 1;
+    return a;
+}
+
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
-    kern<<<grid, block, smem, s>>>(args...);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1] = {pdl_attribute()};
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);  // errors surface through cudaGetLastError
     __atomic_fetch_add(&launch_counter(), 1ull, __ATOMIC_RELAXED);
 }
 #endif

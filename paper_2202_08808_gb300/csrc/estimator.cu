@@ -54,6 +54,7 @@ __device__ __forceinline__ void load_weights(float *W, const uint16_t *w) {
 __global__ void __launch_bounds__(EST_NT)
 k_est_fwd(const uint16_t *w, const float *X, const float *y, int64_t n, float *H1, float *H2, float *O, float *D,
           double *loss) {
+    pdl_begin();
     extern __shared__ __align__(16) float W[];
     load_weights(W, w);
     double part = 0.0;
@@ -85,6 +86,7 @@ k_est_fwd(const uint16_t *w, const float *X, const float *y, int64_t n, float *H
 __global__ void __launch_bounds__(EST_NT)
 k_est_bwd_rows(const uint16_t *w, int64_t n, const float *H1, const float *H2, const float *D, float *DZ1,
                float *DZ2) {
+    pdl_begin();
     extern __shared__ __align__(16) float W[];
     load_weights(W, w);
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
@@ -105,6 +107,7 @@ k_est_bwd_rows(const uint16_t *w, int64_t n, const float *H1, const float *H2, c
 // One thread per parameter, each summing its term over the rows in order.
 __global__ void k_est_grad(const float *X, int64_t n, const float *H1, const float *H2, const float *D,
                            const float *DZ1, const float *DZ2, float *grad) {
+    pdl_begin();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= EST_PARAMS) return;
     float g = 0.0f;
@@ -130,6 +133,7 @@ __global__ void k_est_grad(const float *X, int64_t n, const float *H1, const flo
 }
 
 __global__ void k_est_sgd(float *master, const float *grad, float lr, uint16_t *w) {
+    pdl_begin();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= EST_PARAMS) return;
     const float v = master[p] - lr * grad[p];
@@ -138,6 +142,7 @@ __global__ void k_est_sgd(float *master, const float *grad, float lr, uint16_t *
 }
 
 __global__ void k_est_round(const float *master, uint16_t *w) {
+    pdl_begin();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < EST_PARAMS) w[p] = __bfloat16_as_ushort(__float2bfloat16_rn(master[p]));
 }
@@ -147,6 +152,7 @@ __global__ void k_est_round(const float *master, uint16_t *w) {
 // gets zeros.
 __global__ void k_row_features(MatView A, MatView B, MatView C, const int32_t *rows, int64_t n, float *X, float *y,
                                unsigned *bad) {
+    pdl_begin();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = rows ? rows[t] : (int32_t)t;
         if (i < 0 || i >= A.nrows) {

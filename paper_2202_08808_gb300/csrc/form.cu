@@ -25,6 +25,7 @@ namespace {
 // by column (idx from a stable sort) become the rows of its transpose.
 __global__ void k_permute_entries(const uint32_t *idx, const uint32_t *row_of, const char *val, int64_t nnz,
                                   int32_t *out_col, char *out_val, int vsize) {
+    pdl_begin();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t e = idx[t];
         out_col[t] = (int32_t)row_of[e];
@@ -36,6 +37,7 @@ __global__ void k_permute_entries(const uint32_t *idx, const uint32_t *row_of, c
 // A warp per output row: |P_i u X_i| = len(P_i) + len(X_i) - |P_i n X_i|.
 __global__ void k_form_count(const int32_t *rows, int64_t n, MatView P, const int64_t *xrp, const int32_t *xcol,
                              int64_t *cnt) {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n; t += nw) {
@@ -75,6 +77,7 @@ template <int SR>
 __global__ void k_form_merge(const int32_t *rows, int64_t n, const int64_t *prp, const int32_t *pcol, const void *pval,
                              const int64_t *xrp, const int32_t *xcol, const void *xval, const int64_t *orp,
                              int32_t *ocol, void *oval, FormScalars f) {
+    pdl_begin();
     using T = typename FormSr<SR>::T;
     const T a = SR == SR_PT ? (T)f.alpha : (T)f.alpha_i;
     const T b = SR == SR_PT ? (T)f.beta : (T)f.beta_i;

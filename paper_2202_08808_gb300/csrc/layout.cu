@@ -17,6 +17,7 @@ static unsigned blocks_for(int64_t n, int nt, int64_t cap = 1 << 20) {
 }
 
 __global__ void k_iota(int32_t *a, int64_t n) {
+    pdl_begin();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
         a[x] = (int32_t)x;
 }
@@ -30,6 +31,7 @@ constexpr int CTL_WORDS = (int)(sizeof(Ctl) / sizeof(unsigned long long));
 constexpr int ARG_WORDS = (int)(3 * sizeof(InArgs) / sizeof(unsigned long long));
 
 __global__ void k_begin_batch(const InArgs *host_args, InArgs *dev_args, Ctl *ctl) {
+    pdl_begin();
     unsigned long long *c = (unsigned long long *)ctl;
     for (int k = threadIdx.x; k < CTL_WORDS; k += blockDim.x) c[k] = 0ull;
     if (threadIdx.x < ARG_WORDS)
@@ -37,6 +39,7 @@ __global__ void k_begin_batch(const InArgs *host_args, InArgs *dev_args, Ctl *ct
 }
 
 __global__ void k_end_batch(const Ctl *ctl, Ctl *host_ctl) {
+    pdl_begin();
     const unsigned long long *c = (const unsigned long long *)ctl;
     for (int k = threadIdx.x; k < CTL_WORDS; k += blockDim.x) ((unsigned long long *)host_ctl)[k] = c[k];
     __threadfence_system();
@@ -53,6 +56,7 @@ void fill_iota(int32_t *a, int64_t n, cudaStream_t s) {
 }
 
 __global__ void k_caps(const int32_t *len, int32_t *cap, int64_t n, int smin, int sdiv) {
+    pdl_begin();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
         cap[x] = slack_cap(len[x], smin, sdiv);
 }
@@ -61,6 +65,7 @@ void caps_from_lens(const int32_t *len, int32_t *cap, int64_t n, int smin, int s
 }
 
 __global__ void k_lens_rowptr(const int64_t *rowptr, int32_t *len, int64_t n) {
+    pdl_begin();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
         len[x] = (int32_t)(rowptr[x + 1] - rowptr[x]);
 }
@@ -69,6 +74,7 @@ void lens_from_rowptr(const int64_t *rowptr, int32_t *len, int64_t n, cudaStream
 }
 
 __global__ void k_lens_of_rows(const int32_t *rows, int64_t n, const int32_t *len, int32_t *out) {
+    pdl_begin();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
         out[x] = len[rows[x]];
 }
@@ -80,6 +86,7 @@ template <typename T>
 __global__ void k_copy_rows(const int32_t *rows, int64_t n, const int64_t *src_off, const int32_t *len,
                             const int32_t *src_col, const T *src_val, const int64_t *dst_off, int32_t *dst_col,
                             T *dst_val) {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += nwarps) {
@@ -109,6 +116,7 @@ void copy_rows(const int32_t *rows, int64_t n, const int64_t *src_off, const int
 template <typename T>
 __global__ void k_gather_out(const int32_t *rows, int64_t n, MatView M, const int64_t *out_rowptr, int32_t *out_col,
                              T *out_val) {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const T *mv = (const T *)M.val;
@@ -141,6 +149,7 @@ constexpr int SORT_MAX = 16384;    // longer rows are listed and sorted together
 
 template <typename T>
 __global__ void k_sort_short_rows(const int64_t *rowptr, int64_t n, int32_t *col, T *val) {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += nwarps) {
@@ -176,6 +185,7 @@ __global__ void k_sort_short_rows(const int64_t *rowptr, int64_t n, int32_t *col
 template <typename T>
 __global__ void __launch_bounds__(512) k_sort_long_rows(const int64_t *rowptr, int64_t n, int32_t *col, T *val,
                                                         unsigned *n_listed, int64_t *listed, int64_t list_cap) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smem[];
     T *sv = (T *)smem;
     int32_t *sk = (int32_t *)(sv + SORT_MAX);
@@ -266,6 +276,7 @@ __device__ __forceinline__ int list_of(const int64_t *pre, int nl, int64_t q) {
 
 __global__ void k_listed_keys(const int64_t *rowptr, const int64_t *listed, const int64_t *pre, int nl, int cb,
                               const int32_t *col, uint64_t *keys, uint32_t *idx) {
+    pdl_begin();
     const int64_t E = pre[nl];
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E; q += (int64_t)gridDim.x * blockDim.x) {
         const int k = list_of(pre, nl, q);
@@ -278,6 +289,7 @@ __global__ void k_listed_keys(const int64_t *rowptr, const int64_t *listed, cons
 template <typename T>
 __global__ void k_listed_gather(const int64_t *rowptr, const int64_t *listed, const int64_t *pre, int nl,
                                 const uint32_t *idx, const int32_t *col, const T *val, int32_t *tcol, T *tval) {
+    pdl_begin();
     const int64_t E = pre[nl];
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t src = idx[q];  // the same row as q: the keys sort by list index first
@@ -291,6 +303,7 @@ __global__ void k_listed_gather(const int64_t *rowptr, const int64_t *listed, co
 template <typename T>
 __global__ void k_listed_back(const int64_t *rowptr, const int64_t *listed, const int64_t *pre, int nl,
                               const int32_t *tcol, const T *tval, int32_t *col, T *val) {
+    pdl_begin();
     const int64_t E = pre[nl];
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E; q += (int64_t)gridDim.x * blockDim.x) {
         const int k = list_of(pre, nl, q);
@@ -325,6 +338,7 @@ void sort_listed_rows(const int64_t *rowptr, const int64_t *listed, const int64_
 // columns in range and strictly ascending per row, values valid for the
 // semiring.  Sets *bad = 1 on the first violation seen.
 __global__ void k_validate_rows(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t *rowptr, unsigned *bad) {
+    pdl_begin();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= nrows;
          r += (int64_t)gridDim.x * blockDim.x) {
         if (r == 0 && rowptr[0] != 0) atomicOr(bad, 1u);
@@ -335,6 +349,7 @@ __global__ void k_validate_rows(int64_t nrows, int64_t ncols, int64_t nnz, const
 
 __global__ void k_validate_entries(int64_t nrows, int64_t ncols, const int64_t *rowptr, const int32_t *col,
                                    const void *val, int sr, unsigned *bad) {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nwarps) {
@@ -365,6 +380,7 @@ void validate_rowptr(int64_t nrows, int64_t nnz, const int64_t *rowptr, unsigned
 }
 
 __global__ void k_hist_cols(const int32_t *col, int64_t nnz, int32_t *counts) {
+    pdl_begin();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nnz; x += (int64_t)gridDim.x * blockDim.x)
         atomicAdd(&counts[col[x]], 1);
 }
@@ -373,6 +389,7 @@ void hist_cols(const int32_t *col, int64_t nnz, int32_t *counts, cudaStream_t s)
 }
 
 __global__ void k_rows_of_entries(const int64_t *rowptr, int64_t nrows, uint32_t *rows_out) {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nwarps)
@@ -384,6 +401,7 @@ void rows_of_entries(const int64_t *rowptr, int64_t nrows, uint32_t *rows_out, c
 }
 
 __global__ void k_keys_from_cols(const int32_t *col, int64_t nnz, uint64_t *keys) {
+    pdl_begin();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nnz; x += (int64_t)gridDim.x * blockDim.x)
         keys[x] = (uint64_t)(uint32_t)col[x];
 }
@@ -392,12 +410,14 @@ void keys_from_cols(const int32_t *col, int64_t nnz, uint64_t *keys, cudaStream_
 }
 
 __global__ void k_keys_from_i32(const int32_t *a, int64_t n, uint64_t *keys, uint32_t *idx) {
+    pdl_begin();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
         keys[x] = (uint64_t)(uint32_t)a[x];
         idx[x] = (uint32_t)x;
     }
 }
 __global__ void k_keys_to_i32(const uint64_t *keys, int64_t n, int32_t *a) {
+    pdl_begin();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
         a[x] = (int32_t)keys[x];
 }

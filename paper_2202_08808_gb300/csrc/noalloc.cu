@@ -83,6 +83,7 @@ struct NaArgs {
 // skipped.
 template <int SR>
 __global__ void __launch_bounds__(NA_NT) k_na_rows(NaArgs g, unsigned char *scratch, int mode) {
+    pdl_begin();
     using T = typename NaSr<SR>::T;
     __shared__ int s_incl[NA_NT];
     __shared__ int s_wsum[NA_NT / 32];
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(NA_NT) k_na_rows(NaArgs g, unsigned char *scra
 
 // rowptr[0] = 0 and rowptr[1..nr] = running sums of the counts (one CTA).
 __global__ void __launch_bounds__(1024) k_na_scan(int64_t *rowptr, int64_t nr) {
+    pdl_begin();
     __shared__ int64_t s_w[32];
     __shared__ int64_t s_carry;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;

@@ -30,6 +30,7 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *total) {
 
 template <typename T>
 __global__ void k_scan_reduce(const T *in, int64_t n, int64_t *partial) {
+    pdl_begin();
     int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
     int64_t s = 0;
     for (int j = 0; j < SCAN_IPT; j++) {
@@ -48,6 +49,7 @@ __global__ void k_scan_reduce(const T *in, int64_t n, int64_t *partial) {
 }
 
 __global__ void k_scan_partials(int64_t *partial, int64_t nb) {
+    pdl_begin();
     __shared__ int64_t carry;
     __shared__ int64_t tot;
     if (threadIdx.x == 0) carry = 0;
@@ -66,6 +68,7 @@ __global__ void k_scan_partials(int64_t *partial, int64_t nb) {
 
 template <typename T>
 __global__ void k_scan_final(const T *in, int64_t n, const int64_t *partial, int64_t *out) {
+    pdl_begin();
     __shared__ int64_t tot;
     int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
     // blocked arrangement: thread t owns SCAN_IPT consecutive elements

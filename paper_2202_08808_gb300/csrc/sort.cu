@@ -162,6 +162,7 @@ template <int NT>
 __global__ void __launch_bounds__(NT)
 k_cluster_sort(const InArgs *in, int n, int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out,
                Ctl *ctl, unsigned skip_mask, int cb, int ib) {
+    pdl_begin();
     constexpr int TILE = NT * CS_EPT;
     extern __shared__ uint64_t tiles[];  // slot u: the sorted tile of CTA u
     cg::cluster_group cl = cg::this_cluster();
@@ -261,6 +262,7 @@ void sort_tmp_sizes(int64_t n, int64_t *count_entries) {
 
 __global__ void k_make_keys(const InArgs *in, int64_t n, int64_t nrows, int64_t ncols, int sr, bool check_values,
                             Ctl *ctl, unsigned skip_mask, int cb, uint64_t *k, uint32_t *v) {
+    pdl_begin();
     if (failed(ctl, skip_mask)) return;
     const int32_t *row = in->row, *col = in->col;
     const void *val = in->val;
@@ -276,6 +278,7 @@ __global__ void k_make_keys(const InArgs *in, int64_t n, int64_t nrows, int64_t 
 
 __global__ void __launch_bounds__(MS_NT)
 k_hist(const uint64_t *k, int64_t n, int shift, uint32_t *counts, int64_t nb) {
+    pdl_begin();
     __shared__ uint32_t h[256];
     for (int j = threadIdx.x; j < 256; j += MS_NT) h[j] = 0;
     __syncthreads();
@@ -291,6 +294,7 @@ k_hist(const uint64_t *k, int64_t n, int shift, uint32_t *counts, int64_t nb) {
 __global__ void __launch_bounds__(MS_NT)
 k_scatter(const uint64_t *k, const uint32_t *v, int64_t n, int shift, const int64_t *offs, int64_t nb,
           uint64_t *k_out, uint32_t *v_out) {
+    pdl_begin();
     __shared__ uint32_t wc[MS_NW * 256];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     for (int j = tid; j < MS_NW * 256; j += MS_NT) wc[j] = 0;
@@ -338,6 +342,7 @@ k_scatter(const uint64_t *k, const uint32_t *v, int64_t n, int shift, const int6
 
 __global__ void k_finalize(const uint64_t *k, const uint32_t *v, int64_t n, int cb, const InArgs *in, int sr,
                            SortOut out, const Ctl *ctl, unsigned skip_mask) {
+    pdl_begin();
     if (failed(ctl, skip_mask)) return;
     const void *val = in->val;
     const uint8_t *op = in->op;
@@ -401,13 +406,14 @@ void sort_updates(const InArgs *in, int64_t n, int64_t nrows, int64_t ncols, int
         cfg.blockDim = dim3(small ? 512 : 1024);
         cfg.dynamicSmemBytes = (size_t)tiles * tile * sizeof(uint64_t);
         cfg.stream = s;
-        cudaLaunchAttribute at[1];
+        cudaLaunchAttribute at[2];
         at[0].id = cudaLaunchAttributeClusterDimension;
         at[0].val.clusterDim.x = (unsigned)tiles;
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
+        at[1] = pdl_attribute();
         cfg.attrs = at;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = 2;
         // a failed launch stays in the runtime's last error, which the caller checks
         if (small)
             cudaLaunchKernelEx(&cfg, k_cluster_sort<512>, in, (int)n, nrows, ncols, sr, check_values, out, ctl, skip_mask,

@@ -264,6 +264,7 @@ __device__ __forceinline__ void size_long_row(const MatView &A, const MatView &B
 // C.len (an exact count from a count_only pass); with SIZE_LEARNED rows
 // whose bound exceeds est_min go to the estimate list instead of a bin.
 __global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask) {
+    pdl_begin();
     __shared__ long long s_long[256];  // this block's rows (indices into R) with long A rows
     __shared__ long long s_sum[8], s_max[8];
     __shared__ int s_nlong;
@@ -365,6 +366,7 @@ __global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView
 // network (weights as floats in shared memory), sizes the row's table by the
 // prediction times (1 + margin), clamped to [max len(B_k), bound], and bins it.
 __global__ void __launch_bounds__(128) k_est_bins(CJob J, Ctl *ctl, unsigned mask) {
+    pdl_begin();
     extern __shared__ __align__(16) float W[];
     if (failed(ctl, mask)) return;
     for (int k = threadIdx.x; k < EST_PARAMS; k += blockDim.x) W[k] = bf16_bits_to_float(J.est_w[k]);
@@ -692,6 +694,7 @@ __device__ __forceinline__ int merge_rows_smem(const int32_t *scol, const typena
 template <int SR, int K>
 __global__ void __launch_bounds__(TM_NT)
 k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin, int UB) {
+    pdl_begin();
     using T = typename Sr<SR>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     if (failed(ctl, mask)) return;
@@ -765,6 +768,7 @@ k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned m
 template <int SR, int LOG_TS, int G, int NW>
 __global__ void __launch_bounds__(NW * 32)
 k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
+    pdl_begin();
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
     // rows of tables up to 64 slots are compacted and ranked (column order,
@@ -891,6 +895,7 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
 template <int SR, int LOG_TS, int NT>
 __global__ void __launch_bounds__(NT)
 k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
+    pdl_begin();
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -996,6 +1001,7 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
 template <int SR, int LOG_TS, int CL, int NT>
 __global__ void __launch_bounds__(NT, LOG_TS == 13 ? 2 : 1)  // two 8192-slot tables fit an SM
 k_num_cluster_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned early_mask, int bin) {
+    pdl_begin();
     using T = typename Sr<SR>::T;
     constexpr int TS = 1 << LOG_TS;
     constexpr int LOG_CL = CL == 2 ? 1 : (CL == 4 ? 2 : 3);
@@ -1116,6 +1122,7 @@ constexpr int GD_DIRECT = 16384;
 template <int SR>
 __global__ void __launch_bounds__(512)
 k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
+    pdl_begin();
     using T = typename Sr<SR>::T;
     __shared__ int64_t p_boff[512];
     __shared__ T p_av[512];
@@ -1250,6 +1257,7 @@ k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
 template <int SR, int NW>
 __global__ void __launch_bounds__(NW * 32)
 k_num_warp_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin, int mp) {
+    pdl_begin();
     using T = typename Sr<SR>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     if (failed(ctl, mask)) return;
@@ -1302,6 +1310,7 @@ k_num_warp_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
 template <int SR>
 __global__ void __launch_bounds__(512)
 k_num_cta_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin, int mp) {
+    pdl_begin();
     using T = typename Sr<SR>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     if (failed(ctl, mask)) return;
@@ -1359,6 +1368,7 @@ k_num_cta_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask
 
 template <typename T>
 __global__ void k_fill(T *p, int64_t n, T v) {
+    pdl_begin();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
         p[x] = v;
 }
@@ -1402,6 +1412,7 @@ void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const C
 // folds a row's last chunk (a per-row counter) writes the row into C in
 // column order and resets the accumulator for the next launch.
 __global__ void __launch_bounds__(1024) k_split_prep(MatView A, CJob J, Ctl *ctl, unsigned mask) {
+    pdl_begin();
     __shared__ int incl[1024], wsum[32];
     if (failed(ctl, mask)) return;
     long long cnt = ctl->bin_count[BIN_DSPLIT];
@@ -1425,6 +1436,7 @@ __global__ void __launch_bounds__(1024) k_split_prep(MatView A, CJob J, Ctl *ctl
 template <int SR>
 __global__ void __launch_bounds__(512)
 k_num_dsplit(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int mp) {
+    pdl_begin();
     using T = typename Sr<SR>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_last;
@@ -1629,13 +1641,14 @@ static void launch_cluster_hash(const MatView &A, const MatView &B, const MatVie
     cfg.blockDim = dim3(NT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = CL;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1] = pdl_attribute();
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     // every CTA must reach the kernel's cluster barriers, so it tests only the
     // status bits of the stages before the recompute (see the split kernel)
     const unsigned early = mask & (ST_INVALID | ST_AB_STAGE | ST_AB_ARENA);

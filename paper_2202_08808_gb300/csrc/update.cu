@@ -74,6 +74,7 @@ __device__ __forceinline__ void mark_warp(uint32_t *bm, bool want, int32_t i, in
 template <typename T>
 __global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigned stage_bit, DetectBufs D,
                            int mark_rows, int mark_cols) {
+    pdl_begin();
     if (failed(ctl, mask)) return;
     UpdCtl *u = &ctl->u[J.which];
     const int64_t n = J.n;
@@ -288,6 +289,7 @@ __device__ __forceinline__ void merge_copy_blocks(const UpdJob &J, const MatView
 
 template <typename T>
 __global__ void k_merge_copy(UpdJob J, MatView M, const Ctl *ctl, unsigned mask) {
+    pdl_begin();
     if (failed(ctl, mask)) return;
     merge_copy_blocks<T>(J, M, ctl, blockIdx.x, gridDim.x);
 }
@@ -333,6 +335,7 @@ __device__ __forceinline__ void commit_plan_blocks(const CommitJob &J, const Mat
 }
 
 __global__ void k_commit_plan(CommitJob J, MatView M, Ctl *ctl, unsigned mask, int slack_min, int slack_div) {
+    pdl_begin();
     if (failed(ctl, mask)) return;
     commit_plan_blocks(J, M, ctl, slack_min, slack_div, blockIdx.x, gridDim.x);
 }
@@ -366,6 +369,7 @@ __device__ __forceinline__ void commit_copy_blocks(const CommitJob &J, const Mat
 
 template <typename T>
 __global__ void k_commit_copy(CommitJob J, MatView M, const Ctl *ctl, unsigned mask) {
+    pdl_begin();
     if (failed(ctl, mask)) return;
     commit_copy_blocks<T>(J, M, blockIdx.x, gridDim.x);
 }
@@ -390,6 +394,7 @@ __device__ __forceinline__ void detect_cols_blocks(const MatView &AT, const Dete
 }
 
 __global__ void k_detect_cols(MatView AT, DetectBufs D, Ctl *ctl, unsigned mask) {
+    pdl_begin();
     if (failed(ctl, mask)) return;
     detect_cols_blocks(AT, D, ctl, blockIdx.x, gridDim.x);
 }
@@ -400,6 +405,7 @@ __global__ void k_detect_cols(MatView AT, DetectBufs D, Ctl *ctl, unsigned mask)
 template <typename T>
 __global__ void k_detect_merge(MatView AT, DetectBufs D, long long detect_blocks, UpdJob J, MatView M, Ctl *ctl,
                                unsigned mask) {
+    pdl_begin();
     if (failed(ctl, mask)) return;
     if (blockIdx.x < detect_blocks) detect_cols_blocks(AT, D, ctl, blockIdx.x, detect_blocks);
     else merge_copy_blocks<T>(J, M, ctl, blockIdx.x - detect_blocks, gridDim.x - detect_blocks);
@@ -453,6 +459,7 @@ __device__ __forceinline__ void collect_blocks(uint32_t *bm, int64_t words, int3
 
 __global__ void __launch_bounds__(256) k_collect_rows(uint32_t *bm, int64_t words, int32_t *R, long long *chunk,
                                                       Ctl *ctl, unsigned mask) {
+    pdl_begin();
     if (failed(ctl, mask)) return;
     collect_blocks(bm, words, R, ctl, blockIdx.x, gridDim.x, chunk);
 }
@@ -467,6 +474,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_detect_merge_plan(MatView AT, DetectBufs D, long long nd, UpdJob J, MatView M, CommitJob CJ, long long nm, Ctl *ctl,
                     unsigned mask, int slack_min, int slack_div) {
+    pdl_begin();
     if (failed(ctl, mask)) return;
     if (blockIdx.x < nd) detect_cols_blocks(AT, D, ctl, blockIdx.x, nd);
     else if (blockIdx.x < nd + nm) merge_copy_blocks<T>(J, M, ctl, blockIdx.x - nd, nm);
@@ -480,6 +488,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_collect_copy(uint32_t *bm, int64_t words, int32_t *R, long long *chunk, long long nc, CommitJob CJ, MatView M,
                Ctl *ctl, unsigned collect_mask, unsigned copy_mask) {
+    pdl_begin();
     if (blockIdx.x < nc) {
         if (failed(ctl, collect_mask)) return;
         collect_blocks(bm, words, R, ctl, blockIdx.x, nc, chunk);
@@ -530,6 +539,7 @@ void run_collect_rows(uint32_t *bm, int64_t words, int32_t *R, long long *chunk,
 __global__ void k_transpose_feed(const int32_t *srow, const int32_t *scol, const uint8_t *kind, int64_t n,
                                  int32_t pad_row, int32_t *trow, int32_t *tcol, uint8_t *top, const Ctl *ctl,
                                  unsigned mask) {
+    pdl_begin();
     if (failed(ctl, mask)) return;
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -613,6 +623,7 @@ void run_transpose_feed(const UpdJob &J, int32_t pad_row, int32_t *trow, int32_t
 // current pattern).  A warp per batch entry walks the transposed pattern.
 __global__ void k_footprint(const int32_t *row, const int32_t *col, int64_t n, int64_t nrows, int64_t ncols,
                             int b_is_a, MatView AT, uint32_t *bm, unsigned *bad) {
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -639,6 +650,7 @@ __global__ void k_footprint(const int32_t *row, const int32_t *col, int64_t n, i
 // cnt[0] = number of words where f and u share a bit (u may be null),
 // cnt[1] = number of bits set in f.
 __global__ void k_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t words, unsigned long long *cnt) {
+    pdl_begin();
     unsigned long long c = 0, b = 0;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < words; x += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t w = f[x];
@@ -656,6 +668,7 @@ __global__ void k_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t w
 // u |= f when nothing overlapped (cnt[0] == 0) or always (or_anyway).
 __global__ void k_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words, const unsigned long long *cnt,
                             int or_anyway) {
+    pdl_begin();
     if (!or_anyway && *(volatile const unsigned long long *)cnt != 0ull) return;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < words; x += (int64_t)gridDim.x * blockDim.x)
         u[x] |= f[x];
