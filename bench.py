@@ -906,17 +906,22 @@ def serving_on_stencil(args, log):
         return out
 
     res = {}
-    for name, mw in (("queue", 1), ("waves", args.max_wave)):
-        Server(g, max_wave=mw, read_results=True).serve(requests(20, None, 600000 + mw))  # warm graphs
-        srv = Server(g, max_wave=mw, read_results=True)
+    # a plain queue (one request at a time, nothing overlapped), waves one
+    # after another, and pipelined waves (the next wave runs on the GPU while
+    # the previous one's rows are read back)
+    for name, mw, pipe in (("queue", 1, False), ("waves", args.max_wave, False),
+                           ("pipelined", args.max_wave, True)):
+        Server(g, max_wave=mw, read_results=True, pipelined=pipe).serve(requests(20, None, 600000 + mw))  # warm graphs
+        srv = Server(g, max_wave=mw, read_results=True, pipelined=pipe)
         reqs = requests(args.requests, None, 700000 + 1000 * mw)
         t0 = time.perf_counter()
         out = srv.serve(reqs)
         wall = time.perf_counter() - t0
-        res[f"saturated_{name}"] = dict(latency_summary(out, wall), waves=srv.waves, conflicts=srv.conflicts)
-    mu = res["saturated_waves"]["throughput_req_s"]
+        res[f"saturated_{name}"] = dict(latency_summary(out, wall), waves=srv.waves, conflicts=srv.conflicts,
+                                        overlapped_reads=srv.overlaps() if pipe else 0)
+    mu = res["saturated_pipelined"]["throughput_req_s"]
     for f in (0.5, 1.0, 2.0):
-        srv = Server(g, max_wave=args.max_wave, read_results=True)
+        srv = Server(g, max_wave=args.max_wave, read_results=True, pipelined=True)
         reqs = requests(args.requests, f * mu, 800000 + int(10 * f))
         t0 = time.perf_counter()
         out = srv.serve(reqs)

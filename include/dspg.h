@@ -176,6 +176,20 @@ dspg_status dspg_build_form(dspg_handle **out, const dspg_csr *A, const dspg_csr
 dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
                              dspg_batch_stats *stats, void *stream);
 
+/* dspg_apply_batch in two halves, so that other work can run while the batch
+ * is on the GPU.  dspg_apply_batch_async checks the batch, uploads it and
+ * enqueues the whole pipeline on `stream`, then returns; the batch arrays
+ * (host or device) must stay unchanged until dspg_apply_batch_wait returns.
+ * dspg_apply_batch_wait waits for it, grows buffers and re-runs failed
+ * stages as dspg_apply_batch would, fills stats, and returns the status.
+ * In between, the handle takes no other call but dspg_read_C and
+ * dspg_read_rows_C (others return DSPG_ERR_STATE); those reads are
+ * consistent only for rows the batch cannot change (outside its
+ * footprint, dspg_footprint), which a serving loop uses to read one wave's
+ * rows while the next wave runs.  The reads may use another stream. */
+dspg_status dspg_apply_batch_async(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, void *stream);
+dspg_status dspg_apply_batch_wait(dspg_handle *h, dspg_batch_stats *stats, void *stream);
+
 /* Apply one batch as dspg_apply_batch does, by the delta path of Section 5's
  * algebraic updates when the batch qualifies: C' = C (+) C* with
  * C* = A* B' (+) A B* (Eq. 1; Section 5.1's local step), formed entry by
@@ -408,6 +422,22 @@ dspg_status dspg_set_sizing(dspg_handle *h, int mode, const dspg_estimator *e, i
  * synchronisation.  DSPG_ERR_INVALID for an entry out of range. */
 dspg_status dspg_footprint(dspg_handle *h, const dspg_updates *dA, uint32_t *f, uint32_t *u, int or_anyway,
                            int *admitted, int64_t *rows, void *stream);
+
+/* Footprints of k batches and their admission in one call (one
+ * synchronisation), as k calls of dspg_footprint in a row would give:
+ * f[j * words .. ) receives batch j's footprint (words = (rows of C + 31)
+ * / 32, device), and the footprints are tested against u and added to it in
+ * order.  admitted[j] = 1 when batch j met no footprint before it: with
+ * or_anyway = 0 the first batch that meets one ends the run (it and every
+ * later batch are not admitted, and u takes only the admitted footprints);
+ * with or_anyway = 1 a batch that meets one is passed over but its
+ * footprint still joins u (so a later batch overtakes only batches it
+ * commutes with).  rows (may be NULL): rows set in each footprint.
+ * Borrowed batches are read during the call.  DSPG_ERR_INVALID for an entry
+ * out of range, DSPG_ERR_STATE while an asynchronous batch is in flight.
+ * Not part of the paper; the serving loop's admission. */
+dspg_status dspg_footprint_batch(dspg_handle *h, const dspg_updates *batches, int64_t k, uint32_t *f, uint32_t *u,
+                                 int or_anyway, int *admitted, int64_t *rows, void *stream);
 
 /* Free the group (not its handles). */
 void dspg_group_destroy(dspg_group *g);

@@ -360,6 +360,8 @@ struct dspg_handle {
     FpWs fp;                                    // footprints (serving)
     AlgWs alg;                                  // the delta path (algebraic updates)
     bool last_alg = false;                      // the last batch took the delta path
+    bool pending = false;                       // an asynchronous apply is in flight (dspg_apply_batch_async)
+    int64_t pending_comp0 = 0;
     // the product form (Section 3): C = alpha op(A) op(B) (+) beta X
     bool trans_a = false, trans_b = false;      // op = transpose: the operand is stored transposed
     bool b_alias = false;                       // the caller's B is A, stored apart (one side transposed)
@@ -977,7 +979,9 @@ void upload(dspg_handle *h, UpdWs &w, const dspg_updates *u, BatchIn &in, int k,
 // A and B batches) seen before with unchanged buffers runs as a captured
 // CUDA graph on the handle's own stream (ordered after s); the first time a
 // shape is seen it runs eagerly on s, the second time it is captured.
-void run_first(dspg_handle *h, cudaStream_t s) {
+// With sync false the call returns once the work is enqueued (s is ordered
+// after it); the control block reaches h->hctl when s completes.
+void run_first(dspg_handle *h, cudaStream_t s, bool sync = true) {
     const int64_t nA = h->inA.n, nB = h->inB.n;
     if (h->use_graphs) {
         for (auto &g : h->graphs) {
@@ -988,7 +992,7 @@ void run_first(dspg_handle *h, cudaStream_t s) {
                 __atomic_fetch_add(&launch_counter(), g.kernels, __ATOMIC_RELAXED);
                 CK(cudaEventRecord(h->evIn, h->gs));
                 CK(cudaStreamWaitEvent(s, h->evIn, 0));
-                CK(cudaStreamSynchronize(h->gs));
+                if (sync) CK(cudaStreamSynchronize(h->gs));
                 return;
             }
         }
@@ -1017,7 +1021,7 @@ void run_first(dspg_handle *h, cudaStream_t s) {
             CK(cudaGraphLaunch(exec, h->gs));
             CK(cudaEventRecord(h->evIn, h->gs));
             CK(cudaStreamWaitEvent(s, h->evIn, 0));
-            CK(cudaStreamSynchronize(h->gs));
+            if (sync) CK(cudaStreamSynchronize(h->gs));
             return;
         }
         if (h->seen.size() >= 16) h->seen.erase(h->seen.begin());
@@ -1026,7 +1030,8 @@ void run_first(dspg_handle *h, cudaStream_t s) {
     begin_batch(h->h_args_dev, h->d_args, h->ctl, s);
     pipeline(h, s, h->prof, false);
     CK(cudaGetLastError());
-    read_ctl(h, s);
+    if (sync) read_ctl(h, s);
+    else CK(cudaMemcpyAsync(h->hctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
 }
 
 dspg_status fail(dspg_handle *h, const Err &e) {
@@ -1853,8 +1858,41 @@ dspg_status dspg_build(dspg_handle **out, const dspg_csr *A, const dspg_csr *B, 
 dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
                              dspg_batch_stats *stats, void *stream) {
     if (!h) return DSPG_ERR_INVALID;
+    if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
     try {
         apply_one(h, dA, dB, stats, (cudaStream_t)stream);
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_apply_batch_async(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, void *stream) {
+    if (!h) return DSPG_ERR_INVALID;
+    if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is already in flight"));
+    try {
+        const cudaStream_t s = (cudaStream_t)stream;
+        prepare_batch(h, dA, dB, s);
+        h->pending_comp0 = h->compactions;
+        run_first(h, s, false);
+        h->pending = true;
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_apply_batch_wait(dspg_handle *h, dspg_batch_stats *stats, void *stream) {
+    if (!h) return DSPG_ERR_INVALID;
+    if (!h->pending) return fail(h, Err(DSPG_ERR_STATE, "no asynchronous batch in flight"));
+    try {
+        const cudaStream_t s = (cudaStream_t)stream;
+        h->pending = false;
+        CK(cudaStreamSynchronize(s));
+        if (h->prof) stage_times_from_events(h);
+        recover(h, s);
+        est_fallback(h, s);
+        fill_stats(h, stats, h->pending_comp0);
         return DSPG_OK;
     } catch (const Err &e) {
         return fail(h, e);
@@ -1864,6 +1902,7 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
 dspg_status dspg_apply_batch_algebraic(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
                                        dspg_batch_stats *stats, void *stream) {
     if (!h) return DSPG_ERR_INVALID;
+    if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
     try {
         const cudaStream_t s = (cudaStream_t)stream;
         prepare_batch(h, dA, dB, s);
@@ -1925,6 +1964,7 @@ dspg_status dspg_read_rows_C(dspg_handle *h, const int32_t *rows, int64_t nrows,
 
 dspg_status dspg_last_affected(dspg_handle *h, int64_t *count, int32_t *rows, int on_device, void *stream) {
     if (!h || !count) return DSPG_ERR_INVALID;
+    if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
     cudaStream_t s = (cudaStream_t)stream;
     try {
         const int64_t n = h->last_nR;
@@ -1983,6 +2023,7 @@ dspg_status dspg_last_affected(dspg_handle *h, int64_t *count, int32_t *rows, in
 
 dspg_status dspg_recompute_all(dspg_handle *h, void *stream) {
     if (!h) return DSPG_ERR_INVALID;
+    if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
     try {
         static_recompute(h, (cudaStream_t)stream);
         return DSPG_OK;
@@ -2034,6 +2075,7 @@ dspg_status dspg_tuning_candidate(int k, dspg_tuning *t) {
 
 dspg_status dspg_set_tuning(dspg_handle *h, const dspg_tuning *t) {
     if (!h) return DSPG_ERR_INVALID;
+    if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
     try {
         const dspg_tuning v = t ? *t : kCandidates[0];
         check_tuning(v);
@@ -2054,6 +2096,7 @@ dspg_status dspg_get_tuning(dspg_handle *h, dspg_tuning *t) {
 dspg_status dspg_autotune(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, int64_t nbatches,
                           dspg_tuning *best, float *ms, int n_ms, int *n_cand, void *stream) {
     if (!h) return DSPG_ERR_INVALID;
+    if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<cudaGraphExec_t> execs(kNumCandidates, nullptr);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -2116,6 +2159,7 @@ dspg_status dspg_autotune(dspg_handle *h, const dspg_updates *dA, const dspg_upd
 
 dspg_status dspg_set_sizing(dspg_handle *h, int mode, const dspg_estimator *e, int32_t est_min, float margin) {
     if (!h) return DSPG_ERR_INVALID;
+    if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
     try {
         if (mode != DSPG_SIZE_BOUND && mode != DSPG_SIZE_EXACT && mode != DSPG_SIZE_LEARNED)
             throw Err(DSPG_ERR_INVALID, "unknown sizing mode");
@@ -2161,6 +2205,7 @@ dspg_status dspg_footprint(dspg_handle *h, const dspg_updates *dA, uint32_t *f, 
     if (!h) return DSPG_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     try {
+        if (h->pending) throw Err(DSPG_ERR_STATE, "an asynchronous batch is in flight");
         if (!dA || !f) throw Err(DSPG_ERR_INVALID, "dA and f must not be NULL");
         if (h->trans_a || h->trans_b || h->b_alias)
             throw Err(DSPG_ERR_INVALID, "footprints are not available for a product with transposed operands");
@@ -2192,6 +2237,67 @@ dspg_status dspg_footprint(dspg_handle *h, const dspg_updates *dA, uint32_t *f, 
         if ((unsigned)w.hcnt.p[0]) throw Err(DSPG_ERR_INVALID, "batch entry out of range");
         if (u) *admitted = w.hcnt.p[1] == 0 ? 1 : 0;
         if (rows) *rows = (int64_t)w.hcnt.p[2];
+        return DSPG_OK;
+    } catch (const Err &x) {
+        return fail(h, x);
+    }
+}
+
+dspg_status dspg_footprint_batch(dspg_handle *h, const dspg_updates *batches, int64_t k, uint32_t *f, uint32_t *u,
+                                 int or_anyway, int *admitted, int64_t *rows, void *stream) {
+    if (!h) return DSPG_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        if (h->pending) throw Err(DSPG_ERR_STATE, "an asynchronous batch is in flight");
+        if (k < 0 || (k > 0 && (!batches || !f || !u || !admitted))) throw Err(DSPG_ERR_INVALID, "NULL argument");
+        if (h->trans_a || h->trans_b || h->b_alias)
+            throw Err(DSPG_ERR_INVALID, "footprints are not available for a product with transposed operands");
+        if (k == 0) return DSPG_OK;
+        const int64_t words = (h->A.nrows + 31) / 32;
+        int64_t host_entries = 0;
+        for (int64_t j = 0; j < k; j++) {
+            const int64_t n = batches[j].n;
+            if (n < 0 || (n > 0 && (!batches[j].row || !batches[j].col))) throw Err(DSPG_ERR_INVALID, "bad batch");
+            if (!batches[j].on_device) host_entries += n;
+        }
+        FpWs &w = h->fp;
+        // [0] an entry out of range, [1] the stop flag, then per footprint:
+        // overlapping words and bits set
+        w.cnt.reserve(2 + 2 * k);
+        w.hcnt.reserve_host(2 + 2 * k);
+        w.row.reserve(std::max<int64_t>(host_entries, 1));
+        w.col.reserve(std::max<int64_t>(host_entries, 1));
+        CK(cudaMemsetAsync(f, 0, sizeof(uint32_t) * words * k, s));
+        CK(cudaMemsetAsync(w.cnt.p, 0, (2 + 2 * k) * sizeof(unsigned long long), s));
+        int64_t at = 0;
+        for (int64_t j = 0; j < k; j++) {
+            const dspg_updates &b = batches[j];
+            const int32_t *rp = b.row, *cp = b.col;
+            if (b.n > 0 && !b.on_device) {
+                CK(cudaMemcpyAsync(w.row.p + at, b.row, sizeof(int32_t) * b.n, cudaMemcpyHostToDevice, s));
+                CK(cudaMemcpyAsync(w.col.p + at, b.col, sizeof(int32_t) * b.n, cudaMemcpyHostToDevice, s));
+                rp = w.row.p + at;
+                cp = w.col.p + at;
+                at += b.n;
+            }
+            uint32_t *fj = f + words * j;
+            unsigned long long *cj = w.cnt.p + 2 + 2 * j;
+            if (b.n > 0)
+                run_footprint(rp, cp, b.n, h->A.nrows, h->A.ncols, h->b_is_a, h->AT.view(), fj, (unsigned *)w.cnt.p, s,
+                              h->num_sms);
+            run_bitmap_overlap(fj, u, words, cj, s, h->num_sms);
+            run_bitmap_or(fj, u, words, cj, or_anyway, s, h->num_sms, (unsigned *)(w.cnt.p + 1));
+        }
+        CK(cudaMemcpyAsync(w.hcnt.p, w.cnt.p, (2 + 2 * k) * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if ((unsigned)w.hcnt.p[0]) throw Err(DSPG_ERR_INVALID, "batch entry out of range");
+        bool stop = false;
+        for (int64_t j = 0; j < k; j++) {
+            const bool hit = w.hcnt.p[2 + 2 * j] != 0;
+            admitted[j] = (!stop && !hit) ? 1 : 0;
+            if (hit && !or_anyway) stop = true;
+            if (rows) rows[j] = (int64_t)w.hcnt.p[3 + 2 * j];
+        }
         return DSPG_OK;
     } catch (const Err &x) {
         return fail(h, x);
@@ -2238,6 +2344,7 @@ dspg_status dspg_group_apply(dspg_group *g, const dspg_updates *dA, const dspg_u
         for (size_t t = 0; t < n; t++) {
             dspg_handle *h = g->hs[t];
             try {
+                if (h->pending) throw Err(DSPG_ERR_STATE, "an asynchronous batch is in flight");
                 prepare_batch(h, dA + t, dB ? dB + t : nullptr, s);
             } catch (const Err &e) {
                 h->err = e.what();

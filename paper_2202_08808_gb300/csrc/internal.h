@@ -128,7 +128,7 @@ void run_footprint(const int32_t *row, const int32_t *col, int64_t n, int64_t nr
 void run_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t words, unsigned long long *cnt, cudaStream_t s,
                         int num_sms);
 void run_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words, const unsigned long long *cnt, int or_anyway,
-                   cudaStream_t s, int num_sms);
+                   cudaStream_t s, int num_sms, unsigned *stopped = nullptr);
 
 // algebraic.cu: the delta path of Eq. 1 (batches that only insert)
 constexpr int ALG_SCAN = 256;  // rows of C up to this length take contributions in place

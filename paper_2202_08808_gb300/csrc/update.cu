@@ -665,11 +665,20 @@ __global__ void k_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t w
     }
 }
 
-// u |= f when nothing overlapped (cnt[0] == 0) or always (or_anyway).
+// u |= f when nothing overlapped (cnt[0] == 0) or always (or_anyway).  With
+// `stopped` (a run of admissions in one stream): nothing once an earlier
+// footprint overlapped without or_anyway, and such an overlap sets it.  The
+// blocks of one launch agree: the flag changes only when cnt says overlap,
+// and then every block leaves without writing.
 __global__ void k_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words, const unsigned long long *cnt,
-                            int or_anyway) {
+                            int or_anyway, unsigned *stopped) {
     pdl_begin();
-    if (!or_anyway && *(volatile const unsigned long long *)cnt != 0ull) return;
+    if (stopped && *(volatile unsigned *)stopped) return;
+    const bool hit = *(volatile const unsigned long long *)cnt != 0ull;
+    if (hit && !or_anyway) {
+        if (stopped && blockIdx.x == 0 && threadIdx.x == 0) *stopped = 1u;
+        return;
+    }
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < words; x += (int64_t)gridDim.x * blockDim.x)
         u[x] |= f[x];
 }
@@ -691,11 +700,11 @@ void run_bitmap_overlap(const uint32_t *f, const uint32_t *u, int64_t words, uns
 }
 
 void run_bitmap_or(const uint32_t *f, uint32_t *u, int64_t words, const unsigned long long *cnt, int or_anyway,
-                   cudaStream_t s, int num_sms) {
+                   cudaStream_t s, int num_sms, unsigned *stopped) {
     int64_t g = (words + 255) / 256;
     if (g > num_sms * 8) g = num_sms * 8;
     if (g < 1) g = 1;
-    launch_k(k_bitmap_or, (unsigned)g, 256, 0, s, f, u, words, cnt, or_anyway);
+    launch_k(k_bitmap_or, (unsigned)g, 256, 0, s, f, u, words, cnt, or_anyway, stopped);
 }
 
 }  // namespace dspg

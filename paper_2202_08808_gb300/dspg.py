@@ -152,6 +152,12 @@ def load():
         lib.dspg_set_sizing.argtypes = [p, i32, p, i32, C.c_float]
         lib.dspg_footprint.restype = i32
         lib.dspg_footprint.argtypes = [p, C.POINTER(_Upd), p, p, i32, C.POINTER(i32), C.POINTER(i64), p]
+        lib.dspg_footprint_batch.restype = i32
+        lib.dspg_footprint_batch.argtypes = [p, C.POINTER(_Upd), i64, p, p, i32, C.POINTER(i32), C.POINTER(i64), p]
+        lib.dspg_apply_batch_async.restype = i32
+        lib.dspg_apply_batch_async.argtypes = [p, C.POINTER(_Upd), C.POINTER(_Upd), p]
+        lib.dspg_apply_batch_wait.restype = i32
+        lib.dspg_apply_batch_wait.argtypes = [p, C.POINTER(_Stats), p]
         lib.dspg_destroy.restype = None
         lib.dspg_destroy.argtypes = [p]
         lib.dspg_last_error.restype = C.c_char_p
@@ -166,7 +172,8 @@ EXPORTED = ["dspg_build", "dspg_build_form", "dspg_apply_batch", "dspg_apply_bat
             "dspg_tuning_candidate", "dspg_autotune", "dspg_group_create", "dspg_group_apply", "dspg_group_destroy",
             "dspg_group_last_error", "dspg_estimator_create", "dspg_estimator_params", "dspg_estimator_grad",
             "dspg_estimator_train", "dspg_estimator_predict", "dspg_estimator_last_error", "dspg_estimator_destroy",
-            "dspg_row_features", "dspg_set_sizing", "dspg_footprint", "dspg_destroy",
+            "dspg_row_features", "dspg_set_sizing", "dspg_footprint", "dspg_footprint_batch",
+            "dspg_apply_batch_async", "dspg_apply_batch_wait", "dspg_destroy",
             "dspg_last_error"]
 
 TUNING_FIELDS = [n for n, _ in _Tuning._fields_]
@@ -459,6 +466,39 @@ class DynamicSpGEMM:
         self._check(self._lib.dspg_footprint(self._h, C.byref(ub), f.data_ptr(), u.data_ptr() if u is not None else None,
                                              int(or_anyway), C.byref(adm), C.byref(rows), _stream(stream)))
         return int(rows.value), (bool(adm.value) if u is not None else None)
+
+    def footprint_batch(self, batches, f, u, or_anyway: bool = False, stream=None):
+        """Footprints of k batches into the rows of f (torch int32, k x
+        ceil(n/32)) and their admission against the wave bitmap u, in one
+        call (dspg_footprint_batch).  Returns (admitted, rows) lists."""
+        k = len(batches)
+        if k == 0:
+            return [], []
+        keep: list = []
+        arr = (_Upd * k)(*[self._upd(b, keep) for b in batches])
+        adm = (C.c_int * k)()
+        rows = (C.c_int64 * k)()
+        self._check(self._lib.dspg_footprint_batch(self._h, arr, k, f.data_ptr(), u.data_ptr(), int(or_anyway), adm,
+                                                   rows, _stream(stream)))
+        return [bool(x) for x in adm], [int(x) for x in rows]
+
+    def apply_batch_async(self, dA=None, dB=None, stream=None):
+        """Enqueue a batch and return (dspg_apply_batch_async); the arrays must
+        stay alive until apply_batch_wait."""
+        self._async_keep: list = []
+        ua = self._upd(dA, self._async_keep) if dA is not None else None
+        ub = self._upd(dB, self._async_keep) if dB is not None else None
+        self._async_keep.extend([ua, ub, dA, dB])
+        self._check(self._lib.dspg_apply_batch_async(self._h, C.byref(ua) if ua is not None else None,
+                                                     C.byref(ub) if ub is not None else None, _stream(stream)))
+
+    def apply_batch_wait(self, stream=None) -> dict:
+        stats = _Stats()
+        try:
+            self._check(self._lib.dspg_apply_batch_wait(self._h, C.byref(stats), _stream(stream)))
+        finally:
+            self._async_keep = []
+        return {name: getattr(stats, name) for name, _ in _Stats._fields_}
 
     def recompute_all(self, stream=None) -> None:
         self._check(self._lib.dspg_recompute_all(self._h, _stream(stream)))

@@ -7,25 +7,34 @@ admits as many as it can into one *wave*, applied as a single batch (the
 requests concatenated in arrival order, so the last write of an entry wins
 exactly as if they ran one by one):
 
-- a request joins only if its footprint (``dspg_footprint``: the rows of C
-  it can touch, and the rows its entries could connect) shares no row with
-  the footprints already in the wave; by default the first request that
-  conflicts ends the wave.  With ``overtake`` a conflicting request is passed
-  over instead and its footprint still counts, so a later request joins only
-  if it meets none of the footprints examined before it: it overtakes only
-  requests it commutes with, and conflicting requests stay in arrival order;
+- a request joins only if its footprint (the rows of C it can touch, and
+  the rows its entries could connect) shares no row with the footprints
+  already in the wave, nor with the wave still being read back (below); by
+  default the first request that conflicts ends the wave.  With
+  ``overtake`` a conflicting request is passed over instead and its
+  footprint still counts, so a later request joins only if it meets none of
+  the footprints examined before it: it overtakes only requests it commutes
+  with, and conflicting requests stay in arrival order;
 - at most ``max_wave`` requests and ``max_wave_entries`` update entries per
   wave (the slots);
 - and only while the wave's estimated device memory (its batch and working
   buffers, and the C rows it will read back) fits in the free HBM reported
   by the driver, minus ``hbm_reserve`` bytes.
 
-Requests that arrive while a wave runs on the GPU wait for the next turn.
-The result of a request is its affected rows of C (the rows of the wave's
-affected set inside its footprint) right after its wave commits, which, by
-the disjointness, is the result it would have had alone in arrival order:
-see ``tests/test_gpu_serving.py``.  All computation is in the library's
-kernels; this module only schedules and moves data.
+Waves are pipelined on the GPU (``pipelined``, the default with a GPU): a
+turn admits the next wave from everything that has arrived by then -- while
+the previous wave's rows have not been read back yet -- with one batched
+footprint call (``dspg_footprint_batch``), starts it without waiting
+(``dspg_apply_batch_async``), reads the previous wave's rows on a second
+stream while it runs, and only then waits for it.  The previous wave's rows
+lie outside the running wave's footprint, so reading them meanwhile is
+exact.  A request that conflicts with the wave being read waits until that
+read is done.  The result of a request is its affected rows of C (the rows
+of its wave's affected set inside its footprint) right after its wave
+commits, which, by the disjointness, is the result it would have had alone
+in arrival order: see ``tests/test_gpu_serving.py``.  All computation is in
+the library's kernels; this module schedules, moves data, and sorts each
+wave's affected rows to its requests.
 """
 
 from __future__ import annotations
@@ -85,7 +94,7 @@ class Server:
 
     def __init__(self, g, max_wave: int = 32, max_wave_entries: int = 1 << 21, hbm_reserve: int = 4 << 30,
                  read_results: bool = True, hbm_free=None, overtake: bool = False, scan: int | None = None,
-                 bitmap_device: str = "cuda"):
+                 bitmap_device: str = "cuda", pipelined: bool | None = None):
         """bitmap_device: where the footprint bitmaps live.  The library
         writes them on the GPU ("cuda"); "cpu" is for driving the scheduling
         alone with a stand-in for the handle (the host-logic tests)."""
@@ -109,6 +118,12 @@ class Server:
         self.waves = 0
         self.conflicts = 0
         self.memory_stops = 0
+        self.pipelined = (bitmap_device != "cpu") if pipelined is None else pipelined
+        self.trace = []  # pipelined: (wave, "apply" or "read", start event, end event)
+        self._base = None
+        if self.pipelined:
+            self._fstack = torch.zeros((self.scan, self.words), dtype=torch.int32, device=bitmap_device)
+            self._wave_union = torch.zeros(self.words, dtype=torch.int32, device=bitmap_device)
 
     def _stage(self, b: UpdateBatch) -> UpdateBatch:
         """The wave's batch in pinned host memory (buffers kept and grown), so
@@ -137,6 +152,150 @@ class Server:
         return 64.0 * entries + 2.0 * fp_rows * self.c_row_bytes
 
     def serve(self, requests: list[Request], clock=time.perf_counter) -> list[Result]:
+        """Serve the requests; pipelined waves unless ``pipelined`` is off."""
+        if self.pipelined:
+            return self._serve_pipelined(requests, clock)
+        return self._serve_waves(requests, clock)
+
+    def _admit(self, queue, stream):
+        """The next wave: candidates from the head of the queue (slots and
+        entries), footprints and admission in one call against the union
+        already in self._union, then the memory budget.  Returns (wave as
+        (request, footprint row) pairs, queue positions taken)."""
+        cands, entries = [], 0
+        for req in queue[: self.scan]:
+            if len(cands) >= self.max_wave:
+                break
+            if cands and entries + len(req.batch) > self.max_wave_entries:
+                break
+            cands.append(req)
+            entries += len(req.batch)
+        if self.max_wave == 1 and not cands:
+            return [], []
+        admitted, rows = self.g.footprint_batch([r.batch for r in cands], self._fstack[: len(cands)], self._union,
+                                                or_anyway=self.overtake, stream=stream)
+        budget = self._free() - self.hbm_reserve
+        wave, taken, fp_rows, entries = [], [], 0, 0
+        for j, (req, ok) in enumerate(zip(cands, admitted)):
+            if not ok:
+                self.conflicts += 1
+                if self.overtake:
+                    continue
+                break
+            if wave and self._wave_bytes(entries + len(req.batch), fp_rows + rows[j]) > budget:
+                self.memory_stops += 1
+                break
+            wave.append((req, j))
+            taken.append(j)
+            fp_rows += rows[j]
+            entries += len(req.batch)
+        return wave, taken
+
+    def _finish(self, w, results, clock, t0, stream):
+        """Read a committed wave's rows (on `stream`) and hand each request
+        the rows of the wave's affected set inside its own footprint."""
+        import torch
+        R, labels = w["R"], w["labels"]
+        if self.read_results:
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            rp, col, val = self.g.read_rows_C(R, stream=stream)
+            ev1.record(stream)
+            self.trace.append((w["wave"], "read", ev0, ev1))
+        done = clock() - t0
+        for slot, req in enumerate(w["reqs"]):
+            pos = np.nonzero(labels == slot)[0] if len(w["reqs"]) > 1 else np.arange(R.shape[0])
+            res = Result(req.rid, req.arrival, w["start"], done, w["wave"], len(w["reqs"]), R[pos])
+            if self.read_results:
+                lens = rp[pos + 1] - rp[pos]
+                res.rowptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+                idx = np.repeat(rp[pos], lens) + (np.arange(int(lens.sum())) - np.repeat(res.rowptr[:-1], lens))
+                res.col, res.val = col[idx], val[idx]
+            results.append(res)
+
+    def _serve_pipelined(self, requests: list[Request], clock=time.perf_counter) -> list[Result]:
+        import torch
+        order = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        results: list[Result] = []
+        queue: list[Request] = []
+        nxt = 0
+        run_stream = torch.cuda.Stream()
+        read_stream = torch.cuda.Stream()
+        self._base = torch.cuda.Event(enable_timing=True)
+        self._base.record(run_stream)
+        inflight = None  # the committed wave whose rows are still to be read
+        t0 = clock()
+        while nxt < len(order) or queue or inflight is not None:
+            now = clock() - t0
+            while nxt < len(order) and order[nxt].arrival <= now:
+                queue.append(order[nxt])
+                nxt += 1
+            if not queue and inflight is None:
+                time.sleep(max(0.0, min(order[nxt].arrival - now, 0.01)))
+                continue
+            wave, taken = [], []
+            if queue:
+                # the wave being read back keeps its rows: admissions avoid them
+                if inflight is not None:
+                    self._union.copy_(self._wave_union)
+                else:
+                    self._union.zero_()
+                wave, taken = self._admit(queue, run_stream)
+                if not wave and inflight is None and queue:
+                    raise RuntimeError("no request admitted against an empty wave")
+            if wave:
+                keep = set(taken)
+                cand = queue[: max(taken) + 1]
+                queue = [r for k, r in enumerate(cand) if k not in keep] + queue[len(cand):]
+                start = clock() - t0
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(run_stream)
+                self.g.apply_batch_async(self._stage(concat([r.batch for r, _ in wave])), stream=run_stream)
+                ev1.record(run_stream)
+                self.trace.append((self.waves, "apply", ev0, ev1))
+            if inflight is not None:  # meanwhile: the previous wave's rows
+                self._finish(inflight, results, clock, t0, read_stream)
+                inflight = None
+            if wave:
+                self.g.apply_batch_wait(stream=run_stream)
+                R = self.g.last_affected(stream=run_stream)
+                labels = None
+                if len(wave) > 1 and R.shape[0]:
+                    Rt = torch.from_numpy(R.astype(np.int64)).to(self._fstack.device)
+                    word, bit = Rt >> 5, (Rt & 31).to(torch.int32)
+                    lab = torch.full((R.shape[0],), -1, dtype=torch.int32, device=Rt.device)
+                    for slot, (_, j) in enumerate(wave):
+                        hit = ((self._fstack[j][word] >> bit) & 1).bool()
+                        lab[hit] = slot
+                    labels = lab.cpu().numpy()
+                self._wave_union.zero_()
+                for _, j in wave:
+                    self._wave_union |= self._fstack[j]
+                inflight = {"reqs": [r for r, _ in wave], "R": R, "labels": labels, "start": start,
+                            "wave": self.waves}
+                self.waves += 1
+        torch.cuda.synchronize()
+        return results
+
+    def overlaps(self) -> int:
+        """Pipelined runs: how many wave reads ran while the next wave's
+        apply was on the GPU (their event intervals intersect)."""
+        if self._base is None:
+            return 0
+        span = {}
+        for w, kind, e0, e1 in self.trace:
+            span[(w, kind)] = (self._base.elapsed_time(e0), self._base.elapsed_time(e1))
+        n = 0
+        for (w, kind), (r0, r1) in span.items():
+            if kind != "read" or (w + 1, "apply") not in span:
+                continue
+            a0, a1 = span[(w + 1, "apply")]
+            n += max(r0, a0) < min(r1, a1)
+        return n
+
+    def _serve_waves(self, requests: list[Request], clock=time.perf_counter) -> list[Result]:
         import torch
 
         order = sorted(requests, key=lambda r: (r.arrival, r.rid))

@@ -134,3 +134,70 @@ def test_footprint_is_the_rows_a_batch_can_reach(dspg):
     assert adm2 == (not (brute(b1) & brute(b2)))
     n3, adm3 = g.footprint(b1, f1)  # no wave bitmap: no admission
     assert adm3 is None and n3 == n1
+
+
+def test_pipelined_waves_overlap_on_the_device(dspg):
+    """Pipelined serving: the next wave's pipeline runs while the previous
+    wave's rows are read on another stream (their CUDA event intervals
+    intersect), and every result is still the one it has alone."""
+    from paper_2202_08808_gb300.serving import Server
+    A = er_matrix(1 << 16, 6, seed=201, kind=PLUS_TIMES_F64)
+    reqs = _requests(A, 48, 202)
+    srv = Server(dspg.DynamicSpGEMM(A), max_wave=6)
+    assert srv.pipelined
+    results = srv.serve(reqs)
+    assert len(results) == len(reqs) and srv.waves > 2
+    assert srv.overlaps() > 0, "no wave's read ran beside the next wave's apply"
+    _alone_and_oracle(dspg, A, reqs, results)
+
+
+@pytest.mark.parametrize("overtake", [False, True])
+def test_footprint_batch_equals_calls_in_a_row(dspg, overtake):
+    """One dspg_footprint_batch call admits exactly what the same batches
+    given one by one to dspg_footprint admit, and leaves the same wave bitmap
+    (first conflict ends the run, or with overtake is passed over)."""
+    import torch
+    A = er_matrix(4096, 4, seed=211, kind=PLUS_TIMES_F64)
+    g = dspg.DynamicSpGEMM(A)
+    words = (A.nrows + 31) // 32
+    bs = [random_batch(A.nrows, A.ncols, 3, seed=212 + k, kind=PLUS_TIMES_F64, A=A, dup_frac=0.0) for k in range(20)]
+    f = torch.zeros((len(bs), words), dtype=torch.int32, device="cuda")
+    u = torch.zeros(words, dtype=torch.int32, device="cuda")
+    adm, rows = g.footprint_batch(bs, f, u, or_anyway=overtake)
+    u1 = torch.zeros(words, dtype=torch.int32, device="cuda")
+    f1 = torch.zeros(words, dtype=torch.int32, device="cuda")
+    want, stopped = [], False
+    for k, b in enumerate(bs):
+        if stopped:
+            want.append(False)
+            continue
+        n, ok = g.footprint(b, f1, u1, or_anyway=overtake)
+        assert torch.equal(f1, f[k]) and n == rows[k]
+        want.append(ok)
+        if not ok and not overtake:
+            stopped = True
+    assert adm == want and any(adm) and not all(adm)
+    assert torch.equal(u, u1)
+
+
+def test_async_apply_equals_apply_and_guards_the_handle(dspg):
+    """dspg_apply_batch_async + dspg_apply_batch_wait give what
+    dspg_apply_batch gives; in between, other calls are refused
+    (DSPG_ERR_STATE) except reads."""
+    A = er_matrix(4096, 8, seed=221, kind=MIN_PLUS_I32)
+    g1, g2 = dspg.DynamicSpGEMM(A), dspg.DynamicSpGEMM(A)
+    for t in range(3):  # eager, captured, replayed
+        b = random_batch(A.nrows, A.ncols, 300, seed=222 + t, kind=MIN_PLUS_I32, A=A)
+        s1 = g1.apply_batch(b)
+        g2.apply_batch_async(b)
+        with pytest.raises(dspg.DspgError) as e:
+            g2.apply_batch(b)
+        assert e.value.status == 5
+        g2.read_rows_C(np.array([0, 1], np.int32))  # reads are allowed meanwhile
+        s2 = g2.apply_batch_wait()
+        assert s1 == s2
+        assert np.array_equal(g1.last_affected(), g2.last_affected())
+    c1, c2 = g1.read_C(), g2.read_C()
+    assert np.array_equal(c1.rowptr, c2.rowptr) and np.array_equal(c1.col, c2.col) and np.array_equal(c1.val, c2.val)
+    with pytest.raises(dspg.DspgError):
+        g2.apply_batch_wait()  # nothing in flight
