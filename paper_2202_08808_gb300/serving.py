@@ -157,13 +157,14 @@ class Server:
             return self._serve_pipelined(requests, clock)
         return self._serve_waves(requests, clock)
 
-    def _admit(self, queue, stream):
-        """The next wave: candidates from the head of the queue (slots and
-        entries), footprints and admission in one call against the union
-        already in self._union, then the memory budget.  Returns (wave as
-        (request, footprint row) pairs, queue positions taken)."""
+    def _admit(self, queue, stream, limit):
+        """The next wave: at most `limit` candidates from the head of the
+        queue (slots and entries), footprints and admission in one call
+        against the union already in self._union, then the memory budget.
+        Returns (wave as (request, footprint row) pairs, queue positions
+        taken)."""
         cands, entries = [], 0
-        for req in queue[: self.scan]:
+        for req in queue[: min(self.scan, limit)]:
             if len(cands) >= self.max_wave:
                 break
             if cands and entries + len(req.batch) > self.max_wave_entries:
@@ -225,6 +226,11 @@ class Server:
         self._base = torch.cuda.Event(enable_timing=True)
         self._base.record(run_stream)
         inflight = None  # the committed wave whose rows are still to be read
+        # running averages: requests per wave (how many candidates a turn
+        # examines) and how often the wave being read blocked the next one
+        # (then the loop reads first and admits after, instead of admitting
+        # twice)
+        avg_wave, blocked = 1.0, 0.0
         t0 = clock()
         while nxt < len(order) or queue or inflight is not None:
             now = clock() - t0
@@ -235,15 +241,23 @@ class Server:
                 time.sleep(max(0.0, min(order[nxt].arrival - now, 0.01)))
                 continue
             wave, taken = [], []
+            if queue and inflight is not None and blocked > 0.5:
+                self._finish(inflight, results, clock, t0, read_stream)
+                inflight = None
             if queue:
                 # the wave being read back keeps its rows: admissions avoid them
                 if inflight is not None:
                     self._union.copy_(self._wave_union)
                 else:
                     self._union.zero_()
-                wave, taken = self._admit(queue, run_stream)
+                limit = max(2, int(2 * avg_wave + 1))
+                wave, taken = self._admit(queue, run_stream, limit)
+                if inflight is not None:
+                    blocked = 0.8 * blocked + 0.2 * (0.0 if wave else 1.0)
                 if not wave and inflight is None and queue:
                     raise RuntimeError("no request admitted against an empty wave")
+                if wave:
+                    avg_wave = 0.8 * avg_wave + 0.2 * len(wave)
             if wave:
                 keep = set(taken)
                 cand = queue[: max(taken) + 1]
