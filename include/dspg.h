@@ -259,6 +259,13 @@ dspg_status dspg_stage_times(dspg_handle *h, float *ms, int n);
  * handles), for auditing how many launches a call makes. */
 unsigned long long dspg_kernel_launches(void);
 
+/* How the handle's batches have run so far (the row path, alone or in a
+ * group): replaying a captured pipeline, capturing one, or eagerly.  A
+ * captured pipeline serves every later batch of the same launch sizes (the
+ * batch length rounded up to a multiple of 1024 up to 16384, to a power of
+ * two beyond) while no buffer moves.  Not part of the paper. */
+dspg_status dspg_run_counts(const dspg_handle *h, int64_t *replayed, int64_t *captured, int64_t *eager);
+
 /* Row bins of the recompute.  Section 6.1 fixes only that each row is formed
  * in a sparse accumulator; which accumulator serves which row is this
  * library's choice.  A row of R is binned by its product bound ub (the sum of

@@ -248,7 +248,20 @@ struct InArgs {
     const int32_t *col;
     const void *val;
     const uint8_t *op;
+    int64_t n;  // entries; launches are sized for a bucket of at least n, kernels stop at n
 };
+
+// Launch size of a batch of n entries: n rounded up to a multiple of 1024
+// (the batch sort's tile) up to 16384, the next power of two beyond (0 for
+// an empty batch).  One captured pipeline serves every batch of the same
+// launch size: its kernels read the true length from the argument block.
+inline int64_t batch_bucket(int64_t n) {
+    if (n <= 0) return 0;
+    if (n <= 16384) return (n + 1023) / 1024 * 1024;
+    int64_t b = 32768;
+    while (b < n) b <<= 1;
+    return b;
+}
 
 // Sort a batch of updates by (row, col), keep the last write of each key:
 // see sort.cu.
@@ -268,7 +281,8 @@ struct SortTmp {
 };
 int64_t sort_small_max();
 void sort_tmp_sizes(int64_t n, int64_t *count_entries);
-// Validate + sort + dedupe n updates of a matrix with the given shape.
+// Validate + sort + dedupe the in->n updates of a matrix with the given shape;
+// n is the launch size (at least in->n, e.g. batch_bucket(in->n)).
 // Sets ST_INVALID in ctl on a bad entry.
 // Kernels return at entry when a bit of skip_mask is set in ctl->status.
 void sort_updates(const InArgs *in, int64_t n, int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out,

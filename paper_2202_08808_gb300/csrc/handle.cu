@@ -105,6 +105,7 @@ struct DevMat {
 struct UpdWs {
     int which = 0;
     int vsize = 0;
+    const int64_t *n_dev = nullptr;  // the batch's length in the device argument block
     int64_t ncap = 0;
     DBuf<int32_t> in_row, in_col;
     DBuf<char> in_val;
@@ -159,10 +160,11 @@ struct UpdWs {
     SortTmp sort_tmp() {
         return SortTmp{k0.p, k1.p, i0.p, i1.p, counts.p, scan_tmp.p, scan_out.p, k0.n, counts.n};
     }
-    UpdJob job(int64_t n) {
+    UpdJob job(int64_t n) {  // n: the launch size (at least the batch's length)
         UpdJob J{};
         J.which = which;
         J.n = n;
+        J.n_dev = n_dev;
         J.row = row.p; J.col = col.p; J.val = vsize ? (void *)val.p : nullptr; J.op = op.p;
         J.kind = kind.p; J.pos = pos.p; J.insx = insx.p; J.delx = delx.p;
         J.m_row = m_row.p; J.m_lo = m_lo.p; J.m_hi = m_hi.p; J.m_len = m_len.p; J.m_nins = m_nins.p; J.m_ndel = m_ndel.p;
@@ -277,6 +279,7 @@ struct BatchIn {
     const void *val = nullptr;
     const uint8_t *op = nullptr;
     int64_t n = 0;
+    int64_t cap = 0;  // launch size: batch_bucket(n)
 };
 
 thread_local std::string g_err;
@@ -360,6 +363,7 @@ struct dspg_handle {
     FpWs fp;                                    // footprints (serving)
     AlgWs alg;                                  // the delta path (algebraic updates)
     bool last_alg = false;                      // the last batch took the delta path
+    int64_t runs_replayed = 0, runs_captured = 0, runs_eager = 0;  // how batches ran (dspg_run_counts)
     bool pending = false;                       // an asynchronous apply is in flight (dspg_apply_batch_async)
     int64_t pending_comp0 = 0;
     // the product form (Section 3): C = alpha op(A) op(B) (+) beta X
@@ -748,10 +752,10 @@ void build_transpose(dspg_handle *h, cudaStream_t s) {
 
 void stage_sort(dspg_handle *h, cudaStream_t s) {
     if (h->inA.n > 0)
-        sort_updates(h->d_args + 0, h->inA.n, h->A.nrows, h->A.ncols, h->sr, true, h->wA.sort_out(), h->wA.sort_tmp(),
+        sort_updates(h->d_args + 0, h->inA.cap, h->A.nrows, h->A.ncols, h->sr, true, h->wA.sort_out(), h->wA.sort_tmp(),
                      h->ctl, 0u, s);
     if (!h->b_is_a && h->inB.n > 0)
-        sort_updates(h->d_args + 1, h->inB.n, h->B.nrows, h->B.ncols, h->sr, true, h->wB.sort_out(), h->wB.sort_tmp(),
+        sort_updates(h->d_args + 1, h->inB.cap, h->B.nrows, h->B.ncols, h->sr, true, h->wB.sort_out(), h->wB.sort_tmp(),
                      h->ctl, 0u, s);
 }
 
@@ -768,12 +772,12 @@ DetectBufs detect_bufs(dspg_handle *h) {
 void stage_classify(dspg_handle *h, cudaStream_t s) {
     const DetectBufs D = detect_bufs(h);
     if (h->inA.n > 0) {
-        UpdJob J = h->wA.job(h->inA.n);
+        UpdJob J = h->wA.job(h->inA.cap);
         run_classify(J, h->A.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, D, true,
                      h->b_is_a && h->has_at, s, h->num_sms);
     }
     if (!h->b_is_a && h->inB.n > 0) {
-        UpdJob J = h->wB.job(h->inB.n);
+        UpdJob J = h->wB.job(h->inB.cap);
         run_classify(J, h->B.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, D, false, true, s,
                      h->num_sms);
     }
@@ -788,27 +792,27 @@ int stage_detect(dspg_handle *h, cudaStream_t s) {
     const bool any_cols = h->has_at && (h->b_is_a ? h->inA.n > 0 : h->inB.n > 0);
     if (!any_cols) return -1;
     if (h->b_is_a) {
-        run_detect_merge(h->AT.view(), D, h->wA.job(h->inA.n), h->A.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
+        run_detect_merge(h->AT.view(), D, h->wA.job(h->inA.cap), h->A.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
         return 0;
     }
-    run_detect_merge(h->AT.view(), D, h->wB.job(h->inB.n), h->B.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
+    run_detect_merge(h->AT.view(), D, h->wB.job(h->inB.cap), h->B.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
     return 1;
 }
 
 // The merge copies not done with the detection.
 void stage_merge(dspg_handle *h, cudaStream_t s, int merged) {
     if (h->inA.n > 0 && merged != 0)
-        run_merge_copy(h->wA.job(h->inA.n), h->A.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
+        run_merge_copy(h->wA.job(h->inA.cap), h->A.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
     if (!h->b_is_a && h->inB.n > 0 && merged != 1)
-        run_merge_copy(h->wB.job(h->inB.n), h->B.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
+        run_merge_copy(h->wB.job(h->inB.cap), h->B.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
 }
 
 void stage_commit_ab(dspg_handle *h, cudaStream_t s) {
     if (h->inA.n > 0)
-        run_commit(upd_commit_job(h, h->wA, ST_AB_ARENA, ST_AB_STAGE), h->A.view(), h->vsize, h->inA.n, h->ctl,
+        run_commit(upd_commit_job(h, h->wA, ST_AB_ARENA, ST_AB_STAGE), h->A.view(), h->vsize, h->inA.cap, h->ctl,
                    M_AB & ~ST_AB_ARENA, M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
     if (!h->b_is_a && h->inB.n > 0)
-        run_commit(upd_commit_job(h, h->wB, ST_AB_ARENA, ST_AB_STAGE), h->B.view(), h->vsize, h->inB.n, h->ctl,
+        run_commit(upd_commit_job(h, h->wB, ST_AB_ARENA, ST_AB_STAGE), h->B.view(), h->vsize, h->inB.cap, h->ctl,
                    M_AB & ~ST_AB_ARENA, M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
 }
 
@@ -816,7 +820,7 @@ void stage_commit_ab(dspg_handle *h, cudaStream_t s) {
 // the A batch, sort them by (column, row) and rebuild the changed rows in
 // staging.  These only read the transposed pattern.
 void transpose_front(dspg_handle *h, cudaStream_t s) {
-    const int64_t n = h->inA.n;
+    const int64_t n = h->inA.cap;
     UpdWs &w = h->wAT;
     run_transpose_feed(h->wA.job(n), (int32_t)h->AT.nrows, w.in_row.p, w.in_col.p, w.in_op.p, h->ctl, M_AB, s);
     sort_updates(h->d_args + 2, n, h->AT.nrows + 1, h->AT.ncols, h->sr, false, w.sort_out(), w.sort_tmp(), h->ctl, M_AT,
@@ -830,7 +834,7 @@ void transpose_front(dspg_handle *h, cudaStream_t s) {
 // Second part: write the rebuilt rows into the transposed pattern (only
 // after the affected-row detection has finished reading it).
 void transpose_commit(dspg_handle *h, cudaStream_t s) {
-    run_commit(upd_commit_job(h, h->wAT, ST_AT_ARENA, ST_AT_STAGE), h->AT.view(), 0, h->inA.n, h->ctl,
+    run_commit(upd_commit_job(h, h->wAT, ST_AT_ARENA, ST_AT_STAGE), h->AT.view(), 0, h->inA.cap, h->ctl,
                M_AT & ~ST_AT_ARENA, M_AT, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
 }
 
@@ -895,8 +899,8 @@ void pipeline(dspg_handle *h, cudaStream_t s, bool timed, bool capturing) {
     const CommitJob cjA = upd_commit_job(h, h->wA, ST_AB_ARENA, ST_AB_STAGE);
     int merged = -1;
     if (fused)
-        run_detect_merge_plan(h->AT.view(), detect_bufs(h), h->wA.job(h->inA.n), h->A.view(), cjA, h->vsize, h->ctl,
-                              M_AB & ~ST_AB_ARENA, h->opt.slack_min, h->opt.slack_div, h->inA.n, s, h->num_sms);
+        run_detect_merge_plan(h->AT.view(), detect_bufs(h), h->wA.job(h->inA.cap), h->A.view(), cjA, h->vsize, h->ctl,
+                              M_AB & ~ST_AB_ARENA, h->opt.slack_min, h->opt.slack_div, h->inA.cap, s, h->num_sms);
     else
         merged = stage_detect(h, s);
     if (side_on) {
@@ -954,7 +958,8 @@ void reset_c_counters(dspg_handle *h, cudaStream_t s) {
 // column arrays trade places (swap).
 void upload(dspg_handle *h, UpdWs &w, const dspg_updates *u, BatchIn &in, int k, cudaStream_t s, bool swap = false) {
     in.n = u ? u->n : 0;
-    h->h_args[k] = InArgs{nullptr, nullptr, nullptr, nullptr};
+    in.cap = batch_bucket(in.n);
+    h->h_args[k] = InArgs{nullptr, nullptr, nullptr, nullptr, 0};
     if (in.n <= 0) return;
     const int32_t *ur = swap ? u->col : u->row, *uc = swap ? u->row : u->col;
     if (u->on_device) {
@@ -972,7 +977,7 @@ void upload(dspg_handle *h, UpdWs &w, const dspg_updates *u, BatchIn &in, int k,
         in.val = w.in_val.p;
         in.op = w.in_op.p;
     }
-    h->h_args[k] = InArgs{in.row, in.col, in.val, in.op};
+    h->h_args[k] = InArgs{in.row, in.col, in.val, in.op, in.n};
 }
 
 // Runs the pipeline once and reads the status.  A batch shape (sizes of the
@@ -982,7 +987,8 @@ void upload(dspg_handle *h, UpdWs &w, const dspg_updates *u, BatchIn &in, int k,
 // With sync false the call returns once the work is enqueued (s is ordered
 // after it); the control block reaches h->hctl when s completes.
 void run_first(dspg_handle *h, cudaStream_t s, bool sync = true) {
-    const int64_t nA = h->inA.n, nB = h->inB.n;
+    // a captured pipeline serves every batch of the same launch sizes
+    const int64_t nA = h->inA.cap, nB = h->inB.cap;
     if (h->use_graphs) {
         for (auto &g : h->graphs) {
             if (g.nA == nA && g.nB == nB && g.epoch == h->epoch && g.prof == h->prof) {
@@ -990,6 +996,7 @@ void run_first(dspg_handle *h, cudaStream_t s, bool sync = true) {
                 CK(cudaStreamWaitEvent(h->gs, h->evIn, 0));
                 CK(cudaGraphLaunch(g.exec, h->gs));
                 __atomic_fetch_add(&launch_counter(), g.kernels, __ATOMIC_RELAXED);
+                h->runs_replayed++;
                 CK(cudaEventRecord(h->evIn, h->gs));
                 CK(cudaStreamWaitEvent(s, h->evIn, 0));
                 if (sync) CK(cudaStreamSynchronize(h->gs));
@@ -1012,12 +1019,13 @@ void run_first(dspg_handle *h, cudaStream_t s, bool sync = true) {
             const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
             CK(e);
-            if (h->graphs.size() >= 4) {
+            if (h->graphs.size() >= 8) {
                 cudaGraphExecDestroy(h->graphs.front().exec);
                 h->graphs.erase(h->graphs.begin());
             }
             const unsigned long long nk = launch_counter() - k0;
             h->graphs.push_back(dspg_handle::Graph{nA, nB, h->epoch, h->prof, exec, nk});
+            h->runs_captured++;
             CK(cudaGraphLaunch(exec, h->gs));
             CK(cudaEventRecord(h->evIn, h->gs));
             CK(cudaStreamWaitEvent(s, h->evIn, 0));
@@ -1027,6 +1035,7 @@ void run_first(dspg_handle *h, cudaStream_t s, bool sync = true) {
         if (h->seen.size() >= 16) h->seen.erase(h->seen.begin());
         h->seen.push_back(dspg_handle::Graph{nA, nB, h->epoch, h->prof, nullptr, 0});
     }
+    h->runs_eager++;
     begin_batch(h->h_args_dev, h->d_args, h->ctl, s);
     pipeline(h, s, h->prof, false);
     CK(cudaGetLastError());
@@ -1378,16 +1387,16 @@ void prepare_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *d
     if (nB > 0 && (!dB->row || !dB->col || !dB->val || !dB->op)) throw Err(DSPG_ERR_INVALID, "NULL array in dB");
     if (!h->b_is_a && nB > 0 && !h->has_at) build_transpose(h, s);
     ensure_c_ws(h, s);
-    if (h->wA.ensure(nA, h->A.arena_cap)) h->epoch++;
-    if (!h->b_is_a && h->wB.ensure(nB, h->B.arena_cap)) h->epoch++;
-    if (h->has_at && h->wAT.ensure(nA, h->AT.arena_cap)) h->epoch++;
+    if (h->wA.ensure(batch_bucket(nA), h->A.arena_cap)) h->epoch++;
+    if (!h->b_is_a && h->wB.ensure(batch_bucket(nB), h->B.arena_cap)) h->epoch++;
+    if (h->has_at && h->wAT.ensure(batch_bucket(nA), h->AT.arena_cap)) h->epoch++;
     upload(h, h->wA, dA, h->inA, 0, s, h->trans_a);
     upload(h, h->wB, dB, h->inB, 1, s, h->trans_b);
     if (h->b_is_a) {
         h->inB = BatchIn{};
-        h->h_args[1] = InArgs{nullptr, nullptr, nullptr, nullptr};
+        h->h_args[1] = InArgs{nullptr, nullptr, nullptr, nullptr, 0};
     }
-    h->h_args[2] = InArgs{h->wAT.in_row.p, h->wAT.in_col.p, nullptr, h->wAT.in_op.p};
+    h->h_args[2] = InArgs{h->wAT.in_row.p, h->wAT.in_col.p, nullptr, h->wAT.in_op.p, h->inA.n};
 }
 
 // After a run: grow what overflowed and re-run the failed stages (eagerly,
@@ -1641,6 +1650,9 @@ bool apply_algebraic(dspg_handle *h, cudaStream_t s) {
         alg_recompute_rows(h, s);
     } else {
         if (n_new > 0) {
+            const InArgs na{h->alg.nr.p, h->alg.nc.p, h->alg.nv.p, h->alg.nop.p, n_new};
+            CK(cudaMemcpyAsync(h->alg.args.p, &na, sizeof(InArgs), cudaMemcpyHostToDevice, s));
+            CK(cudaStreamSynchronize(s));  // na leaves scope
             sort_updates(h->alg.args.p, n_new, h->C.nrows, h->C.ncols, h->sr, false, h->alg.sort_out(),
                          h->alg.sort_tmp(), h->ctl, 0u, s);
             const AlgNew N{h->alg.srow.p, h->alg.scol.p, h->alg.sval.p, n_new, h->alg.dest.p, h->alg.cap.p};
@@ -1804,9 +1816,9 @@ dspg_status dspg_build_form(dspg_handle **out, const dspg_csr *A, const dspg_csr
         CK(cudaHostGetDevicePointer((void **)&h->h_args_dev, h->h_args, 0));
         std::memset(h->h_args, 0, 3 * sizeof(InArgs));
         std::memset(h->hctl, 0, sizeof(Ctl));
-        h->wA.which = 0; h->wA.vsize = h->vsize;
-        h->wB.which = 1; h->wB.vsize = h->vsize;
-        h->wAT.which = 2; h->wAT.vsize = 0;
+        h->wA.which = 0; h->wA.vsize = h->vsize; h->wA.n_dev = &h->d_args[0].n;
+        h->wB.which = 1; h->wB.vsize = h->vsize; h->wB.n_dev = &h->d_args[1].n;
+        h->wAT.which = 2; h->wAT.vsize = 0; h->wAT.n_dev = &h->d_args[2].n;
         load_operand(h, h->A, A, ta, s);
         // B is A: one stored operand when both sides are (or neither is)
         // transposed; otherwise a stored copy of A, transposed as its side
@@ -2066,6 +2078,14 @@ dspg_status dspg_stage_times(dspg_handle *h, float *ms, int n) {
 }
 
 unsigned long long dspg_kernel_launches(void) { return __atomic_load_n(&launch_counter(), __ATOMIC_RELAXED); }
+
+dspg_status dspg_run_counts(const dspg_handle *h, int64_t *replayed, int64_t *captured, int64_t *eager) {
+    if (!h) return DSPG_ERR_INVALID;
+    if (replayed) *replayed = h->runs_replayed;
+    if (captured) *captured = h->runs_captured;
+    if (eager) *eager = h->runs_eager;
+    return DSPG_OK;
+}
 
 dspg_status dspg_tuning_candidate(int k, dspg_tuning *t) {
     if (k < 0 || k >= kNumCandidates || !t) return DSPG_ERR_INVALID;
@@ -2351,8 +2371,8 @@ dspg_status dspg_group_apply(dspg_group *g, const dspg_updates *dA, const dspg_u
                 throw Err(e.st, "member " + std::to_string(t) + ": " + e.what());
             }
             comp0[t] = h->compactions;
-            key.push_back(h->inA.n);
-            key.push_back(h->inB.n);
+            key.push_back(h->inA.cap);
+            key.push_back(h->inB.cap);
             key.push_back((int64_t)h->epoch);
         }
         const bool use_graphs = n > 0 && g->hs[0]->use_graphs;
@@ -2384,6 +2404,7 @@ dspg_status dspg_group_apply(dspg_group *g, const dspg_updates *dA, const dspg_u
             hit = &g->graphs.back();
         }
         if (hit) {
+            for (dspg_handle *h : g->hs) h->runs_replayed++;
             CK(cudaEventRecord(g->evIn, s));
             CK(cudaStreamWaitEvent(g->gs, g->evIn, 0));
             CK(cudaGraphLaunch(hit->exec, g->gs));
@@ -2398,6 +2419,7 @@ dspg_status dspg_group_apply(dspg_group *g, const dspg_updates *dA, const dspg_u
             }
             CK(cudaEventRecord(g->evFork, s));
             for (dspg_handle *h : g->hs) {
+                h->runs_eager++;
                 CK(cudaStreamWaitEvent(h->gs, g->evFork, 0));
                 begin_batch(h->h_args_dev, h->d_args, h->ctl, h->gs);
                 pipeline(h, h->gs, false, false);

@@ -13,7 +13,8 @@ namespace dspg {
 // have n entries too (at most one item per entry).
 struct UpdJob {
     int which;  // index into Ctl::u
-    int64_t n;  // sorted entries
+    int64_t n;  // launch size: at least the sorted entries (batch_bucket)
+    const int64_t *n_dev;  // the sorted entries (the argument block's n, on the device)
     // sorted batch (output of sort_updates)
     int32_t *row, *col;
     void *val;  // nullptr for a pattern

@@ -160,9 +160,10 @@ __device__ __forceinline__ void bitonic_sort_tile(uint64_t (&x)[CS_EPT], uint64_
 
 template <int NT>
 __global__ void __launch_bounds__(NT)
-k_cluster_sort(const InArgs *in, int n, int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out,
-               Ctl *ctl, unsigned skip_mask, int cb, int ib) {
+k_cluster_sort(const InArgs *in, int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out, Ctl *ctl,
+               unsigned skip_mask, int cb, int ib) {
     pdl_begin();
+    const int n = (int)in->n;  // the launch covers a bucket of at least n words
     constexpr int TILE = NT * CS_EPT;
     extern __shared__ uint64_t tiles[];  // slot u: the sorted tile of CTA u
     cg::cluster_group cl = cg::this_cluster();
@@ -269,6 +270,11 @@ __global__ void k_make_keys(const InArgs *in, int64_t n, int64_t nrows, int64_t 
     const uint8_t *op = in->op;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (i >= in->n) {  // padding up to the launch size: sorts after every entry
+        k[i] = ~uint64_t(0);
+        v[i] = (uint32_t)i;
+        return;
+    }
     int32_t r = row[i], c = col[i];
     bool ok = entry_ok(r, c, op[i], val, i, nrows, ncols, sr, check_values);
     if (!ok) set_status(ctl, ST_INVALID);
@@ -346,6 +352,7 @@ __global__ void k_finalize(const uint64_t *k, const uint32_t *v, int64_t n, int 
     if (failed(ctl, skip_mask)) return;
     const void *val = in->val;
     const uint8_t *op = in->op;
+    n = in->n;  // the entries; the sort covered padding after them
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint64_t key = k[s];
@@ -416,11 +423,11 @@ void sort_updates(const InArgs *in, int64_t n, int64_t nrows, int64_t ncols, int
         cfg.numAttrs = 2;
         // a failed launch stays in the runtime's last error, which the caller checks
         if (small)
-            cudaLaunchKernelEx(&cfg, k_cluster_sort<512>, in, (int)n, nrows, ncols, sr, check_values, out, ctl, skip_mask,
-                               cb, ib);
+            cudaLaunchKernelEx(&cfg, k_cluster_sort<512>, in, nrows, ncols, sr, check_values, out, ctl, skip_mask, cb,
+                               ib);
         else
-            cudaLaunchKernelEx(&cfg, k_cluster_sort<1024>, in, (int)n, nrows, ncols, sr, check_values, out, ctl,
-                               skip_mask, cb, ib);
+            cudaLaunchKernelEx(&cfg, k_cluster_sort<1024>, in, nrows, ncols, sr, check_values, out, ctl, skip_mask, cb,
+                               ib);
         __atomic_fetch_add(&launch_counter(), 1ull, __ATOMIC_RELAXED);
         return;
     }

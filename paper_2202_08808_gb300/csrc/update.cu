@@ -77,7 +77,7 @@ __global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigne
     pdl_begin();
     if (failed(ctl, mask)) return;
     UpdCtl *u = &ctl->u[J.which];
-    const int64_t n = J.n;
+    const int64_t n = *J.n_dev;  // the launch covers a bucket of at least n entries
     const int lane = threadIdx.x & 31;
     const T *bval = (const T *)J.val;
     T *sval = (T *)J.st_val;
@@ -536,13 +536,13 @@ void run_collect_rows(uint32_t *bm, int64_t words, int32_t *R, long long *chunk,
 // inserts (k,i), DEL (i,k) deletes (k,i).  Other entries become padding in a
 // row past the end (dropped by k_segments), so the forwarded batch keeps the
 // host-known length of the A batch.
-__global__ void k_transpose_feed(const int32_t *srow, const int32_t *scol, const uint8_t *kind, int64_t n,
+__global__ void k_transpose_feed(const int32_t *srow, const int32_t *scol, const uint8_t *kind, const int64_t *n_dev,
                                  int32_t pad_row, int32_t *trow, int32_t *tcol, uint8_t *top, const Ctl *ctl,
                                  unsigned mask) {
     pdl_begin();
     if (failed(ctl, mask)) return;
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
+    if (s >= *n_dev) return;
     const uint8_t k = kind[s];
     if (k == K_INS || k == K_DEL) {
         trow[s] = scol[s];
@@ -611,8 +611,8 @@ void run_detect_cols(const MatView &AT, const DetectBufs &D, Ctl *ctl, unsigned 
 void run_transpose_feed(const UpdJob &J, int32_t pad_row, int32_t *trow, int32_t *tcol, uint8_t *top, Ctl *ctl,
                         unsigned mask, cudaStream_t s) {
     if (J.n <= 0) return;
-    launch_k(k_transpose_feed, (unsigned)((J.n + 255) / 256), 256, 0, s, J.row, J.col, J.kind, J.n, pad_row, trow, tcol,
-                                                                  top, ctl, mask);
+    launch_k(k_transpose_feed, (unsigned)((J.n + 255) / 256), 256, 0, s, J.row, J.col, J.kind, J.n_dev, pad_row, trow,
+             tcol, top, ctl, mask);
 }
 
 // ------------------------------------------------------------ footprints

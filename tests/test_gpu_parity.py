@@ -549,3 +549,30 @@ def test_row_reads_between_batches(dspg):
         _sampled_rows(g, Ao, Ao, other, f"batch {t}: other rows")
         g.read_C()
         _sampled_rows(g, Ao, Ao, R, f"batch {t}: R after a read of C")
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_captured_pipeline_serves_uneven_sizes(dspg, sr):
+    """Batches of different sizes within one launch size (a multiple of 1024
+    up to 16384, powers of two beyond): after the first two, every batch
+    replays the same captured pipeline (no new kernels are captured), which
+    reads each batch's own length on the device; every result matches the
+    oracle.  Sizes cross the cluster sort's limit too (LSD path)."""
+    n = 3000
+    A = random_csr(n, n, 10, 311, sr)
+    # room in the arenas, so that no buffer moves (which would retire the
+    # captured pipeline) during the sequence
+    g = dspg.DynamicSpGEMM(A, arena_headroom=4.0)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    for sizes in ([700, 900, 1000, 13, 333, 1024, 1], [20000, 17000, 30000, 16385]):
+        r0 = g.run_counts()
+        for k, m in enumerate(sizes):
+            b = random_batch(n, n, m, 312 + 17 * k + m, sr, A=Ao.to_csr(), dup_frac=0.2)
+            _apply_both(g, Ao, Co, b)
+            _check_state(g, Ao, None, f"size {m}")
+        r1 = g.run_counts()
+        # one launch size: run eagerly once, captured once, then replayed
+        # (a buffer that still has to grow once costs one more of each)
+        assert r1["eager"] - r0["eager"] <= 2 and r1["captured"] - r0["captured"] <= 2, (r0, r1)
+        assert r1["replayed"] - r0["replayed"] >= len(sizes) - 4, (r0, r1)
