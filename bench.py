@@ -503,12 +503,16 @@ def batched_instances(count, seed=4):
     return out
 
 
-def batched_batches(insts, step, device=True):
+def batched_batches(insts, step, device=True, uneven=False):
+    """One batch per instance: of the instance's own size, or (uneven) of a
+    size drawn afresh for every step, log-uniform in 10..10^4 edges."""
     import torch
     from workloads import rmat_edge_batch
     bs = []
+    rng = np.random.default_rng(31 * step + 7) if uneven else None
     for t, it in enumerate(insts):
-        b = rmat_edge_batch(it["A"], it["held"], it["size"], seed=7919 * (step + 1) + t)
+        size = int(10 ** rng.uniform(1, 4)) if uneven else it["size"]
+        b = rmat_edge_batch(it["A"], it["held"], size, seed=7919 * (step + 1) + t)
         if device:
             b = type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(), torch.from_numpy(b.val).cuda(),
                         torch.from_numpy(b.op).cuda())
@@ -540,15 +544,15 @@ def batched_arm(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     step_no = [0]
 
-    def next_batches(device=True):
+    def next_batches(device=True, uneven=False):
         step_no[0] += 1
-        return batched_batches(insts, step_no[0], device)
+        return batched_batches(insts, step_no[0], device, uneven)
 
-    def time_group(grp, steps, warmup, collect=None):
+    def time_group(grp, steps, warmup, collect=None, uneven=False):
         for _ in range(warmup):
-            grp.apply(next_batches())
+            grp.apply(next_batches(uneven=uneven))
         torch.cuda.synchronize()
-        pre = [next_batches() for _ in range(steps)]
+        pre = [next_batches(uneven=uneven) for _ in range(steps)]
         ms = []
         k0 = pkg.kernel_launches()
         for k in range(steps):
@@ -602,6 +606,38 @@ def batched_arm(args):
         torch.cuda.synchronize()
         sep_ms.append(e0.elapsed_time(e1))
 
+    # fresh uneven sizes every step (log-uniform 10..10^4 edges per instance):
+    # with every member's launch sizes reserved for the largest batch, the
+    # group replays one captured pipeline whatever the sizes; separate calls
+    # take the same batches
+    def runs():
+        c = [h.run_counts() for h in hs]
+        return {k: sum(x[k] for x in c) for k in ("replayed", "captured", "eager")}
+    for h in hs:  # launch sizes for the largest batch of the distribution: 10^4 edges, both directions
+        h.reserve(2 * 10 ** 4)
+    for _ in range(2):  # eager, captured
+        grp.apply(next_batches(uneven=True))
+    r0 = runs()
+    uneven_ms, _ = time_group(grp, args.steps, 0, uneven=True)
+    r1 = runs()
+    uneven_sep = []
+    for k in range(args.steps):
+        bs = next_batches(uneven=True)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for h, b in zip(hs, bs):
+            h.apply_batch(b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        uneven_sep.append(e0.elapsed_time(e1))
+    member_runs = sum(r1[k] - r0[k] for k in r1)
+    uneven = {"group_ms": round(statistics.median(uneven_ms), 4),
+              "separate_calls_ms": round(statistics.median(uneven_sep), 4),
+              "speedup_group_vs_separate": round(statistics.median(uneven_sep) / statistics.median(uneven_ms), 2),
+              "member_runs_replayed": round((r1["replayed"] - r0["replayed"]) / max(member_runs, 1), 3),
+              "member_runs": int(member_runs)}
+
     # end to end with pinned host batches through the group call
     e2e_ms, h2d = [], 0
     for k in range(max(3, min(args.steps, 5))):
@@ -651,6 +687,7 @@ def batched_arm(args):
         "group_tuned_ms": round(med, 4),
         "separate_calls_ms": round(statistics.median(sep_ms), 4),
         "speedup_group_vs_separate": round(statistics.median(sep_ms) / med, 2),
+        "uneven_sizes_every_step": uneven,
         "autotune": {"seconds": round(tune_s, 2), "chosen": {str(cands.index(k)): v for k, v in chosen.items()}},
         "affected_rows_per_step": int(R),
         "roofline": {"bound": "hbm", "kernel": "whole group step (every stage of every instance)",

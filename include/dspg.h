@@ -266,6 +266,15 @@ unsigned long long dspg_kernel_launches(void);
  * two beyond) while no buffer moves.  Not part of the paper. */
 dspg_status dspg_run_counts(const dspg_handle *h, int64_t *replayed, int64_t *captured, int64_t *eager);
 
+/* Reserve launch sizes for batches of up to nA (and nB) entries when the
+ * handle runs inside a group (dspg_group_apply): the member then launches
+ * its pipeline at those sizes whatever its batch's length (a shorter batch
+ * runs as a zero-padded one, an empty batch as a zero-length one), so one
+ * captured group pipeline serves every combination of the members' batch
+ * sizes up to their reservations; a larger batch raises the member's
+ * reservation.  Buffers are grown now.  Not part of the paper. */
+dspg_status dspg_reserve(dspg_handle *h, int64_t nA, int64_t nB, void *stream);
+
 /* Row bins of the recompute.  Section 6.1 fixes only that each row is formed
  * in a sparse accumulator; which accumulator serves which row is this
  * library's choice.  A row of R is binned by its product bound ub (the sum of

@@ -363,6 +363,7 @@ struct dspg_handle {
     FpWs fp;                                    // footprints (serving)
     AlgWs alg;                                  // the delta path (algebraic updates)
     bool last_alg = false;                      // the last batch took the delta path
+    int64_t grp_cap_a = 0, grp_cap_b = 0;       // in a group: launch sizes reserved so far (grow-only)
     int64_t runs_replayed = 0, runs_captured = 0, runs_eager = 0;  // how batches ran (dspg_run_counts)
     bool pending = false;                       // an asynchronous apply is in flight (dspg_apply_batch_async)
     int64_t pending_comp0 = 0;
@@ -751,10 +752,10 @@ void build_transpose(dspg_handle *h, cudaStream_t s) {
 // ------------------------------------------------------------ pipeline
 
 void stage_sort(dspg_handle *h, cudaStream_t s) {
-    if (h->inA.n > 0)
+    if (h->inA.cap > 0)
         sort_updates(h->d_args + 0, h->inA.cap, h->A.nrows, h->A.ncols, h->sr, true, h->wA.sort_out(), h->wA.sort_tmp(),
                      h->ctl, 0u, s);
-    if (!h->b_is_a && h->inB.n > 0)
+    if (!h->b_is_a && h->inB.cap > 0)
         sort_updates(h->d_args + 1, h->inB.cap, h->B.nrows, h->B.ncols, h->sr, true, h->wB.sort_out(), h->wB.sort_tmp(),
                      h->ctl, 0u, s);
 }
@@ -771,12 +772,12 @@ DetectBufs detect_bufs(dspg_handle *h) {
 // followed next).
 void stage_classify(dspg_handle *h, cudaStream_t s) {
     const DetectBufs D = detect_bufs(h);
-    if (h->inA.n > 0) {
+    if (h->inA.cap > 0) {
         UpdJob J = h->wA.job(h->inA.cap);
         run_classify(J, h->A.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, D, true,
                      h->b_is_a && h->has_at, s, h->num_sms);
     }
-    if (!h->b_is_a && h->inB.n > 0) {
+    if (!h->b_is_a && h->inB.cap > 0) {
         UpdJob J = h->wB.job(h->inB.cap);
         run_classify(J, h->B.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, D, false, true, s,
                      h->num_sms);
@@ -789,7 +790,7 @@ void stage_classify(dspg_handle *h, cudaStream_t s) {
 // is A); returns which (0: A, 1: B, -1: none).
 int stage_detect(dspg_handle *h, cudaStream_t s) {
     const DetectBufs D = detect_bufs(h);
-    const bool any_cols = h->has_at && (h->b_is_a ? h->inA.n > 0 : h->inB.n > 0);
+    const bool any_cols = h->has_at && (h->b_is_a ? h->inA.cap > 0 : h->inB.cap > 0);
     if (!any_cols) return -1;
     if (h->b_is_a) {
         run_detect_merge(h->AT.view(), D, h->wA.job(h->inA.cap), h->A.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
@@ -801,17 +802,17 @@ int stage_detect(dspg_handle *h, cudaStream_t s) {
 
 // The merge copies not done with the detection.
 void stage_merge(dspg_handle *h, cudaStream_t s, int merged) {
-    if (h->inA.n > 0 && merged != 0)
+    if (h->inA.cap > 0 && merged != 0)
         run_merge_copy(h->wA.job(h->inA.cap), h->A.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
-    if (!h->b_is_a && h->inB.n > 0 && merged != 1)
+    if (!h->b_is_a && h->inB.cap > 0 && merged != 1)
         run_merge_copy(h->wB.job(h->inB.cap), h->B.view(), h->vsize, h->ctl, M_AB, s, h->num_sms);
 }
 
 void stage_commit_ab(dspg_handle *h, cudaStream_t s) {
-    if (h->inA.n > 0)
+    if (h->inA.cap > 0)
         run_commit(upd_commit_job(h, h->wA, ST_AB_ARENA, ST_AB_STAGE), h->A.view(), h->vsize, h->inA.cap, h->ctl,
                    M_AB & ~ST_AB_ARENA, M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
-    if (!h->b_is_a && h->inB.n > 0)
+    if (!h->b_is_a && h->inB.cap > 0)
         run_commit(upd_commit_job(h, h->wB, ST_AB_ARENA, ST_AB_STAGE), h->B.view(), h->vsize, h->inB.cap, h->ctl,
                    M_AB & ~ST_AB_ARENA, M_AB, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
 }
@@ -883,7 +884,7 @@ void pipeline(dspg_handle *h, cudaStream_t s, bool timed, bool capturing) {
     stage_sort(h, s);
     mark(1, s);
     stage_classify(h, s);
-    const bool side_on = h->has_at && h->inA.n > 0;
+    const bool side_on = h->has_at && h->inA.cap > 0;
     if (side_on) {
         CK(cudaEventRecord(h->evFork, s));
         CK(cudaStreamWaitEvent(h->side, h->evFork, 0));
@@ -894,7 +895,7 @@ void pipeline(dspg_handle *h, cudaStream_t s, bool timed, bool capturing) {
     // when B is A: the detection's column step, A's merge copy and commit
     // plan share one launch, the collection of R and the commit copy the
     // next (the merge and commit stage times are then part of the detection's)
-    const bool fused = h->b_is_a && h->has_at && h->inA.n > 0;
+    const bool fused = h->b_is_a && h->has_at && h->inA.cap > 0;
     const int64_t words = (h->A.nrows + 31) / 32;
     const CommitJob cjA = upd_commit_job(h, h->wA, ST_AB_ARENA, ST_AB_STAGE);
     int merged = -1;
@@ -934,7 +935,7 @@ void pipeline(dspg_handle *h, cudaStream_t s, bool timed, bool capturing) {
 void stage_times_from_events(dspg_handle *h) {
     const int a[DSPG_NSTAGES] = {0, 1, 2, 3, 4, 8, 5, 6};
     const int b[DSPG_NSTAGES] = {1, 2, 3, 4, 5, 9, 6, 7};
-    const bool side_on = h->has_at && h->inA.n > 0;
+    const bool side_on = h->has_at && h->inA.cap > 0;
     for (int k = 0; k < DSPG_NSTAGES; k++) {
         h->stage_ms[k] = 0.f;
         if (k == DSPG_STAGE_TRANSPOSE && !side_on) continue;
@@ -1402,7 +1403,7 @@ void prepare_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *d
 // After a run: grow what overflowed and re-run the failed stages (eagerly,
 // on s) until the status is clean; errors become exceptions.
 void recover(dspg_handle *h, cudaStream_t s) {
-    const int64_t nA = h->inA.n, nB = h->inB.n;
+    const int64_t nA = h->inA.cap, nB = h->inB.cap;  // the stages that ran
     for (int iter = 0; iter < 8 && h->hctl->status; iter++) {
         const unsigned st = h->hctl->status;
         if (st & ST_INVALID) throw Err(DSPG_ERR_INVALID, "batch entry out of range or with an invalid value/op");
@@ -2079,6 +2080,25 @@ dspg_status dspg_stage_times(dspg_handle *h, float *ms, int n) {
 
 unsigned long long dspg_kernel_launches(void) { return __atomic_load_n(&launch_counter(), __ATOMIC_RELAXED); }
 
+dspg_status dspg_reserve(dspg_handle *h, int64_t nA, int64_t nB, void *stream) {
+    if (!h) return DSPG_ERR_INVALID;
+    if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
+    try {
+        if (nA < 0 || nB < 0 || nA > INT32_MAX / 2 || nB > INT32_MAX / 2) throw Err(DSPG_ERR_INVALID, "bad size");
+        if ((h->b_is_a || h->b_alias) && nB > 0) throw Err(DSPG_ERR_INVALID, "B is A: reserve through nA");
+        h->grp_cap_a = std::max(h->grp_cap_a, batch_bucket(nA));
+        h->grp_cap_b = std::max(h->grp_cap_b, batch_bucket(h->b_alias ? nA : nB));
+        cudaStream_t s = (cudaStream_t)stream;
+        if (h->wA.ensure(h->grp_cap_a, h->A.arena_cap)) h->epoch++;
+        if (!h->b_is_a && h->wB.ensure(h->grp_cap_b, h->B.arena_cap)) h->epoch++;
+        if (h->has_at && h->wAT.ensure(h->grp_cap_a, h->AT.arena_cap)) h->epoch++;
+        CK(cudaStreamSynchronize(s));
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
 dspg_status dspg_run_counts(const dspg_handle *h, int64_t *replayed, int64_t *captured, int64_t *eager) {
     if (!h) return DSPG_ERR_INVALID;
     if (replayed) *replayed = h->runs_replayed;
@@ -2366,6 +2386,17 @@ dspg_status dspg_group_apply(dspg_group *g, const dspg_updates *dA, const dspg_u
             try {
                 if (h->pending) throw Err(DSPG_ERR_STATE, "an asynchronous batch is in flight");
                 prepare_batch(h, dA + t, dB ? dB + t : nullptr, s);
+                // a member launches at the largest size it has seen (an
+                // empty batch runs as a zero-length one), so that one
+                // captured group pipeline serves every later combination of
+                // batch sizes up to those
+                h->grp_cap_a = std::max(h->grp_cap_a, h->inA.cap);
+                h->grp_cap_b = std::max(h->grp_cap_b, h->inB.cap);
+                h->inA.cap = h->grp_cap_a;
+                h->inB.cap = h->b_is_a ? 0 : h->grp_cap_b;
+                if (h->wA.ensure(h->inA.cap, h->A.arena_cap)) h->epoch++;
+                if (!h->b_is_a && h->wB.ensure(h->inB.cap, h->B.arena_cap)) h->epoch++;
+                if (h->has_at && h->wAT.ensure(h->inA.cap, h->AT.arena_cap)) h->epoch++;
             } catch (const Err &e) {
                 h->err = e.what();
                 throw Err(e.st, "member " + std::to_string(t) + ": " + e.what());

@@ -112,6 +112,8 @@ def load():
         lib.dspg_stage_times.argtypes = [p, C.POINTER(C.c_float), i32]
         lib.dspg_kernel_launches.restype = C.c_ulonglong
         lib.dspg_kernel_launches.argtypes = []
+        lib.dspg_reserve.restype = i32
+        lib.dspg_reserve.argtypes = [p, i64, i64, p]
         lib.dspg_run_counts.restype = i32
         lib.dspg_run_counts.argtypes = [p, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
         lib.dspg_multiply_rows_noalloc.restype = i32
@@ -170,7 +172,7 @@ def load():
 
 EXPORTED = ["dspg_build", "dspg_build_form", "dspg_apply_batch", "dspg_apply_batch_algebraic", "dspg_read_C", "dspg_read_A", "dspg_read_rows_C",
             "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_set_profiling", "dspg_stage_times",
-            "dspg_kernel_launches", "dspg_run_counts", "dspg_multiply_rows_noalloc", "dspg_set_tuning", "dspg_get_tuning",
+            "dspg_kernel_launches", "dspg_run_counts", "dspg_reserve", "dspg_multiply_rows_noalloc", "dspg_set_tuning", "dspg_get_tuning",
             "dspg_tuning_candidate", "dspg_autotune", "dspg_group_create", "dspg_group_apply", "dspg_group_destroy",
             "dspg_group_last_error", "dspg_estimator_create", "dspg_estimator_params", "dspg_estimator_grad",
             "dspg_estimator_train", "dspg_estimator_predict", "dspg_estimator_last_error", "dspg_estimator_destroy",
@@ -501,6 +503,11 @@ class DynamicSpGEMM:
         finally:
             self._async_keep = []
         return {name: getattr(stats, name) for name, _ in _Stats._fields_}
+
+    def reserve(self, nA: int, nB: int = 0, stream=None) -> None:
+        """Launch sizes for batches up to nA (nB) entries inside a group
+        (dspg_reserve)."""
+        self._check(self._lib.dspg_reserve(self._h, int(nA), int(nB), _stream(stream)))
 
     def run_counts(self) -> dict:
         """How this handle's batches ran: graph replays, captures, eager runs."""

@@ -153,3 +153,38 @@ def test_group_rejects_repeated_member(dspg):
     g = dspg.DynamicSpGEMM(A)
     with pytest.raises(dspg.DspgError):
         dspg.Group([g, g])
+
+
+def test_reserved_group_replays_any_sizes(dspg):
+    """Members reserved for batches up to 3000 entries: after the eager and
+    the capturing apply, the group replays one captured pipeline for fresh
+    uneven sizes every step (empty batches included), and every member
+    matches the oracle."""
+    insts = _instances(6, 17)
+    # room in the arenas: a buffer that moves retires the captured pipeline
+    gs = [dspg.DynamicSpGEMM(A, arena_headroom=3.0) for A, _, _ in insts]
+    for g in gs:
+        g.reserve(3000)
+    Aos = [OMat.from_csr(A) for A, _, _ in insts]
+    Cos = [Ao.multiply(Ao) for Ao in Aos]
+    grp = dspg.Group(gs)
+    rng = np.random.default_rng(18)
+    for rep in range(6):
+        bs = []
+        for t, (A, held, _) in enumerate(insts):
+            size = int(rng.integers(0, 1500))
+            bs.append(rmat_edge_batch(Aos[t].to_csr(), held, size, seed=400 * rep + t) if size else None)
+        r0 = [g.run_counts() for g in gs]
+        stats, status = grp.apply(bs)
+        assert status == [0] * len(gs)
+        r1 = [g.run_counts() for g in gs]
+        if rep >= 2:
+            assert all(b["replayed"] - a["replayed"] == 1 for a, b in zip(r0, r1)), f"rep {rep}: not replayed"
+        for t, (g, Ao, Co) in enumerate(zip(gs, Aos, Cos)):
+            if bs[t] is None:
+                assert stats[t]["affected_rows"] == 0
+                continue
+            R = oracle.row_dynamic(Ao, Co, bs[t])
+            assert np.array_equal(g.last_affected(), R), f"rep {rep} member {t}: R"
+            _check(g, Ao, f"rep {rep} member {t}")
+    grp.close()
