@@ -279,7 +279,10 @@ dspg_status dspg_reserve(dspg_handle *h, int64_t nA, int64_t nB, void *stream);
  * in a sparse accumulator; which accumulator serves which row is this
  * library's choice.  A row of R is binned by its product bound ub (the sum of
  * the lengths of the B rows it reads, capped at the column count):
- *  - thread merge: A rows with at most merge_k entries (0..8; 0 turns the
+ *  - group sort: rows with an uncapped bound ub <= sort_max (0..256; 0 turns
+ *    it off), whose products a group of 8, 16 or 32 lanes (for ub up to 64,
+ *    128, 256) holds in registers, sorts by column and folds;
+ *  - thread merge (the rows the group sort leaves): A rows with at most merge_k entries (0..8; 0 turns the
  *    merge off) and an uncapped bound ub <= 64, in two kernels: ub <=
  *    merge_ub (0..64) in one whose threads stage merge_ub entries in shared
  *    memory, so that a lower bound lets more threads run at once (at 49,
@@ -301,9 +304,10 @@ typedef struct {
     int32_t table_shift;
     int32_t warp_max;
     int32_t cta_max;
+    int32_t sort_max;
 } dspg_tuning;
 
-/* Set (t == NULL: restore the defaults {8, 64, 8, 0, 1024, 16384}) or read
+/* Set (t == NULL: restore the defaults {8, 64, 8, 0, 1024, 16384, 64}) or read
  * the tuning of h.  Out-of-range fields return DSPG_ERR_INVALID. */
 dspg_status dspg_set_tuning(dspg_handle *h, const dspg_tuning *t);
 dspg_status dspg_get_tuning(dspg_handle *h, dspg_tuning *t);

@@ -355,7 +355,7 @@ struct dspg_handle {
     std::vector<Graph> seen;  // keys run once eagerly (exec unused)
     uint64_t epoch = 1;       // bumped whenever a persistent buffer moves
     bool use_graphs = true;
-    dspg_tuning tune{8, 64, 8, 0, 1024, 16384};  // row bins of the recompute
+    dspg_tuning tune{8, 64, 8, 0, 1024, 16384, 64};  // row bins of the recompute
     int sizing = DSPG_SIZE_BOUND;               // how the recompute's tables are sized
     int est_min = 128;
     float est_margin = 0.25f;
@@ -596,6 +596,7 @@ CJob c_job(dspg_handle *h, const int32_t *R, bool static_mode) {
     J.table_shift = h->tune.table_shift;
     J.warp_max = h->tune.warp_max;
     J.cta_max = h->tune.cta_max;
+    J.sort_max = h->tune.sort_max;
     J.sizing = (!static_mode && h->sizing == DSPG_SIZE_LEARNED) ? SIZE_LEARNED : SIZE_BOUND;
     J.est_min = h->est_min;
     J.est_margin = h->est_margin;
@@ -1717,16 +1718,19 @@ void check_tuning(const dspg_tuning &t) {
     if (t.table_shift < 0 || t.table_shift > 1) throw Err(DSPG_ERR_INVALID, "tuning: table_shift must be 0 or 1");
     if (t.warp_max < 0 || t.warp_max > 1024 || t.cta_max < 0 || t.cta_max > 16384)
         throw Err(DSPG_ERR_INVALID, "tuning: warp_max must be in 0..1024 and cta_max in 0..16384");
+    if (t.sort_max < 0 || t.sort_max > 256) throw Err(DSPG_ERR_INVALID, "tuning: sort_max must be in 0..256");
 }
 
 // The autotuner's candidates: the defaults first, then one or two changes
-// each (thread-merge reach, lanes per short row, table oversizing, the
-// warp/CTA and CTA/global crossovers).
+// each (group-sort reach, thread-merge reach, lanes per short row, table
+// oversizing, the warp/CTA and CTA/global crossovers).
 const dspg_tuning kCandidates[] = {
-    {8, 64, 8, 0, 1024, 16384}, {0, 0, 8, 0, 1024, 16384},   {4, 32, 8, 0, 1024, 16384}, {8, 49, 8, 0, 1024, 16384},
-    {8, 64, 16, 0, 1024, 16384}, {8, 64, 32, 0, 1024, 16384}, {8, 64, 8, 1, 1024, 16384}, {8, 64, 8, 0, 512, 16384},
-    {8, 64, 8, 0, 1024, 4096},  {8, 64, 8, 0, 1024, 8192},    {8, 64, 8, 1, 1024, 8192},  {8, 64, 32, 0, 1024, 8192},
-    {0, 0, 16, 1, 1024, 16384},
+    {8, 64, 8, 0, 1024, 16384, 64},  {8, 64, 8, 0, 1024, 16384, 0},   {8, 64, 8, 0, 1024, 16384, 128},
+    {8, 64, 8, 0, 1024, 16384, 256}, {0, 0, 8, 0, 1024, 16384, 0},    {4, 32, 8, 0, 1024, 16384, 0},
+    {8, 49, 8, 0, 1024, 16384, 0},   {8, 64, 16, 0, 1024, 16384, 64}, {8, 64, 32, 0, 1024, 16384, 64},
+    {8, 64, 8, 1, 1024, 16384, 64},  {8, 64, 8, 0, 512, 16384, 64},   {8, 64, 8, 0, 1024, 4096, 64},
+    {8, 64, 8, 0, 1024, 8192, 64},   {8, 64, 8, 1, 1024, 8192, 64},   {8, 64, 32, 0, 1024, 8192, 256},
+    {0, 0, 16, 1, 1024, 16384, 0},
 };
 constexpr int kNumCandidates = (int)(sizeof(kCandidates) / sizeof(kCandidates[0]));
 

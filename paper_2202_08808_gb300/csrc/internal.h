@@ -84,6 +84,7 @@ struct CJob {
     // row-bin thresholds (dspg_tuning): thread-merge limits, smallest hash
     // executor, table oversizing, warp/CTA and CTA/global crossovers
     int tm_k, tm_ub, lanes_min, table_shift, warp_max, cta_max;
+    int sort_max;             // rows of at most this many products: group sort
     // sizing of the hash tables: SIZE_BOUND by the product bound; SIZE_COUNT
     // by C.len (an exact count written by a count_only pass); SIZE_LEARNED by
     // the estimator for rows with bound above est_min (tables may then

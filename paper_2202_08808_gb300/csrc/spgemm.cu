@@ -71,6 +71,7 @@ enum {
     BIN_WDENSE, BIN_CDENSE, BIN_DSPLIT,
     BIN_T64,  // thread merge, rows whose bound is above the tuned staging bound (up to MERGE_UB)
     BIN_K2, BIN_K4, BIN_K8, BIN_K8L,  // cluster tables: 2, 4, 8 CTAs x 8192 slots, 8 x 16384
+    BIN_S64, BIN_S128, BIN_S256,      // group sort: 8, 16, 32 lanes, up to 64, 128, 256 products
     BIN_COUNT
 };
 static_assert(BIN_COUNT <= NBINS, "bin counters");
@@ -144,8 +145,21 @@ __device__ __forceinline__ bool merge_row(int alen, long long ub, const CJob &J)
     return alen <= J.tm_k && ub <= MERGE_UB;
 }
 
+// Rows sorted in registers by a group of lanes: at most sort_max products
+// (the uncapped bound, which is what the group holds), in the smallest of
+// the three group sizes that holds them.
+// The group sort packs a column with a product index (up to 8 bits) into 32.
+__device__ __forceinline__ bool sort_cols_ok(long long m) { return m < (1LL << 24) - 1; }
+__device__ __forceinline__ bool sort_row(long long ub, const CJob &J) { return ub <= J.sort_max && sort_cols_ok(J.m); }
+
+// Rows whose kernel holds all their products (no table to size).
+__device__ __forceinline__ bool small_row(int alen, long long ub, const CJob &J) {
+    return sort_row(ub, J) || merge_row(alen, ub, J);
+}
+
 __device__ __forceinline__ int pick_bin(long long ubc, int alen, const CJob &J, long long table_need,
                                         long long ub) {
+    if (sort_row(ub, J)) return ub <= 64 ? BIN_S64 : (ub <= 128 ? BIN_S128 : BIN_S256);
     if (merge_row(alen, ub, J)) return ub <= J.tm_ub ? BIN_T8 : BIN_T64;
     if (J.dense_mode) return (alen <= DENSE_WARP_A && ub <= 4096) ? BIN_WDENSE : BIN_CDENSE;
     return pick_table_bin(table_need, J, ub);
@@ -239,7 +253,7 @@ __device__ __forceinline__ void size_long_row(const MatView &A, const MatView &B
         } else if (J.sizing != SIZE_COUNT) {
             if (ub == 0) C.len[i] = 0;
         }
-        const bool t8 = merge_row(alen, ub, J);
+        const bool t8 = small_row(alen, ub, J);
         if (wants_est(J, ub, ubc, t8)) {
             push_est(J, ctl, i, alen, bmax, ub);
         } else if (ub > 0) {
@@ -335,7 +349,7 @@ __global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView
         } else if (valid && J.sizing != SIZE_COUNT) {
             if (ub == 0) C.len[i] = 0;  // no products: the row becomes empty
         }
-        const bool t8 = merge_row(alen, ub, J);
+        const bool t8 = small_row(alen, ub, J);
         const bool to_est = valid && wants_est(J, ub, ubc, t8);
         long long need = ubc;
         if (J.sizing == SIZE_COUNT && valid) need = C.len[i];
@@ -760,6 +774,234 @@ k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned m
     }
     nnz_acc = warp_sum<long long>(nnz_acc);
     if ((threadIdx.x & 31) == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
+}
+
+// ---------------------------------------------------- group sort kernel
+
+// G lanes per row (32 / G rows per warp) for rows of at most N = G * GS_EPL
+// products.  Product p of the row (A entries in order, each B row in order)
+// has slot p of the group's shared memory, filled by lane p % G: its B
+// column and value arrive by asynchronous copies (all of the row's copies
+// in flight at once, lane after lane along each B row), its A value by a
+// store.  The lane then holds the word (column << log2 N | p) as its
+// register p / G.  The group sorts its N words with a bitonic network of
+// integer min/max (partners inside a lane's registers for the short
+// strides, in another lane of the group, by shuffles, for the long ones; a
+// run that descends is sorted ascending on complemented words), folds each
+// run of equal columns (inside a lane, then across lanes with a segmented
+// scan), multiplying out the slots that the sorted words name, and writes
+// the row in column order.  The words are distinct, so the sort needs no
+// tie rule, and it has no data-dependent branches.  Columns must leave room
+// for the slot bits (sort_cols_ok).
+constexpr int GS_EPL = 8;
+constexpr int GS_NT = 256;
+
+template <int SR, int G>
+__global__ void __launch_bounds__(GS_NT, 4)
+k_num_group_sort(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int bin) {
+    pdl_begin();
+    using T = typename Sr<SR>::T;
+    constexpr int N = G * GS_EPL;
+    constexpr int LOGN = G == 8 ? 6 : (G == 16 ? 7 : 8);
+    static_assert((1 << LOGN) == N, "words per group");
+    constexpr uint32_t PAD = 0xffffffffu;  // empty word: sorts last, never written
+    // the group's N product slots: B column, A value, B value
+    __shared__ int32_t s_col[GS_NT / G * N];
+    __shared__ T s_a[GS_NT / G * N];
+    __shared__ T s_b[GS_NT / G * N];
+    if (__any_sync(0xffffffffu, failed(ctl, mask))) return;  // a warp leaves as a whole
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1), gw = lane / G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (gw * G));
+    int32_t *scol = s_col + (threadIdx.x / G) * N;
+    T *sa = s_a + (threadIdx.x / G) * N;
+    T *sb = s_b + (threadIdx.x / G) * N;
+    const long long ngroups = ((long long)gridDim.x * GS_NT) / G;
+    const T *Av = (const T *)A.val;
+    const T *Bv = (const T *)B.val;
+    T *Cv = (T *)C.val;
+    long long nnz_acc = 0;
+    const long long cnt = ctl->bin_count[bin];
+    for (long long it = ((long long)blockIdx.x * GS_NT + threadIdx.x) / G; it < cnt; it += ngroups) {
+        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        const int64_t aoff = A.off[i];
+        const int alen = A.len[i];
+        int base = 0;  // products placed so far (the same on every lane of the group)
+        bool over = false;
+        for (int a0 = 0; a0 < alen; a0 += G) {
+            const int ai = a0 + gl;
+            int blen = 0;
+            int64_t boff = 0;
+            T av = T(0);
+            if (ai < alen) {
+                const int32_t k = A.col[aoff + ai];
+                av = Av[aoff + ai];
+                boff = B.off[k];
+                blen = B.len[k];
+            }
+            int incl = blen;
+#pragma unroll
+            for (int d = 1; d < G; d <<= 1) {
+                const int o = __shfl_up_sync(gmask, incl, d, G);
+                if (gl >= d) incl += o;
+            }
+            const int total = __shfl_sync(gmask, incl, G - 1, G);
+            if (base + total > N) {  // the bin's bound rules this out; guard the slots anyway
+                over = true;
+                break;
+            }
+#pragma unroll
+            for (int e = 0; e < GS_EPL; e++) {
+                // the same on every lane of the group: whether word e takes
+                // a product of this chunk
+                if ((e + 1) * G > base && e * G < base + total) {
+                    const int p = e * G + gl - base;
+                    const bool in = p >= 0 && p < total;
+                    const int pc = in ? p : 0;
+                    int s = 0;  // the A entry whose B row holds product pc of the chunk
+#pragma unroll
+                    for (int step = G / 2; step > 0; step >>= 1) {
+                        const int v = __shfl_sync(gmask, incl, s + step - 1, G);
+                        if (v <= pc) s += step;
+                    }
+                    const int64_t bo = __shfl_sync(gmask, boff, s, G);
+                    const T as = __shfl_sync(gmask, av, s, G);
+                    const int ex = __shfl_sync(gmask, incl, s, G) - __shfl_sync(gmask, blen, s, G);
+                    if (in) {
+                        // the B entry straight into the slot (no register
+                        // waits for it): every copy of the row is in flight
+                        const int slot = e * G + gl;
+                        const int64_t q = bo + (pc - ex);
+                        cp_async_4(&scol[slot], B.col + q);
+                        if (sizeof(T) == 8) cp_async_8(&sb[slot], Bv + q);
+                        else cp_async_4(&sb[slot], Bv + q);
+                        sa[slot] = as;
+                    }
+                }
+            }
+            base += total;
+        }
+        cp_async_wait_all();  // this lane's copies (it reads only its own slots here)
+        if (over) {
+            if (gl == 0) report_overflow(ctl, bin, i, A, B);
+            __syncwarp(gmask);
+            continue;
+        }
+        uint32_t x[GS_EPL];
+#pragma unroll
+        for (int e = 0; e < GS_EPL; e++) {
+            const int slot = e * G + gl;
+            x[e] = slot < base ? ((uint32_t)scol[slot] << LOGN) | (uint32_t)slot : PAD;
+        }
+        // bitonic sort of the N words; word e of lane gl is position
+        // gl * GS_EPL + e.  Merges of up to GS_EPL / 2 words lie inside a
+        // lane with a direction fixed by e; a merge of size >= GS_EPL runs
+        // one direction per lane, taken as ascending on complemented words.
+        uint32_t flip = 0;
+#pragma unroll
+        for (int size = 2; size <= N; size <<= 1) {
+            if (size >= GS_EPL) {
+                const uint32_t f = ((gl * GS_EPL) & size) ? PAD : 0u;
+#pragma unroll
+                for (int e = 0; e < GS_EPL; e++) x[e] ^= f ^ flip;
+                flip = f;
+            }
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                if (stride >= GS_EPL) {
+                    const int lm = stride / GS_EPL;
+                    const bool lower = (gl & lm) == 0;
+#pragma unroll
+                    for (int e = 0; e < GS_EPL; e++) {
+                        const uint32_t y = __shfl_xor_sync(gmask, x[e], lm, G);
+                        const uint32_t lo = min(x[e], y), hi = max(x[e], y);
+                        x[e] = lower ? lo : hi;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < GS_EPL; e++)
+                        if ((e & stride) == 0) {
+                            const uint32_t lo = min(x[e], x[e | stride]), hi = max(x[e], x[e | stride]);
+                            const bool up = size >= GS_EPL || (e & size) == 0;
+                            x[e] = up ? lo : hi;
+                            x[e | stride] = up ? hi : lo;
+                        }
+                }
+            }
+        }
+        __syncwarp(gmask);  // the slots, filled by the group's lanes
+        // fold runs of equal columns: inside the lane, each word's value
+        // becomes the fold of its run up to itself
+        int32_t col[GS_EPL];
+        T v[GS_EPL];
+#pragma unroll
+        for (int e = 0; e < GS_EPL; e++) {
+            const int slot = (int)(x[e] & (N - 1));
+            col[e] = x[e] == PAD ? -1 : (int32_t)(x[e] >> LOGN);
+            v[e] = x[e] == PAD ? Sr<SR>::zero() : Sr<SR>::mul(sa[slot], sb[slot]);
+        }
+#pragma unroll
+        for (int e = 1; e < GS_EPL; e++)
+            if (col[e] == col[e - 1]) v[e] = Sr<SR>::add(v[e - 1], v[e]);
+        // across lanes: a lane's first run continues the previous lane's
+        // last one when their columns agree; a segmented scan over the lanes
+        // gives each lane the fold of the run that ends at its last word
+        const int32_t first = col[0], last = col[GS_EPL - 1];
+        const int32_t prev_last = __shfl_up_sync(gmask, last, 1, G);
+        const bool link = gl > 0 && prev_last == first;
+        T run = v[GS_EPL - 1];
+        int head = !(link && first == last);  // the run ending here starts in this lane
+#pragma unroll
+        for (int d = 1; d < G; d <<= 1) {
+            const T pr = __shfl_up_sync(gmask, run, d, G);
+            const int ph = __shfl_up_sync(gmask, head, d, G);
+            if (gl >= d && !head) {
+                run = Sr<SR>::add(pr, run);
+                head = ph;
+            }
+        }
+        const T carry = __shfl_up_sync(gmask, run, 1, G);
+        if (link)
+#pragma unroll
+            for (int e = 0; e < GS_EPL; e++)
+                if (col[e] == first) v[e] = Sr<SR>::add(carry, v[e]);
+        // the last word of each run holds the entry; its rank among the
+        // row's runs is its place in the output
+        const int32_t next_first = __shfl_down_sync(gmask, first, 1, G);
+        int nl = 0;
+#pragma unroll
+        for (int e = 0; e < GS_EPL; e++) {
+            const int32_t nk = e + 1 < GS_EPL ? col[e + 1] : (gl + 1 < G ? next_first : -1);
+            nl += col[e] >= 0 && nk != col[e];
+        }
+        int w = nl;
+#pragma unroll
+        for (int d = 1; d < G; d <<= 1) {
+            const int o = __shfl_up_sync(gmask, w, d, G);
+            if (gl >= d) w += o;
+        }
+        const int n = __shfl_sync(gmask, w, G - 1, G);
+        w -= nl;
+        int64_t dest = 0;
+        if (gl == 0) dest = c_row_dest(C, J, ctl, i, n);
+        dest = __shfl_sync(gmask, dest, 0, G);
+        if (dest >= 0) {
+#pragma unroll
+            for (int e = 0; e < GS_EPL; e++) {
+                const int32_t nk = e + 1 < GS_EPL ? col[e + 1] : (gl + 1 < G ? next_first : -1);
+                if (col[e] >= 0 && nk != col[e]) {
+                    C.col[dest + w] = col[e];
+                    Cv[dest + w] = v[e];
+                    w++;
+                }
+            }
+            if (gl == 0) C.len[i] = n;
+        }
+        if (gl == 0) nnz_acc += n;
+        __syncwarp(gmask);  // every lane has read the slots before the next row fills them
+    }
+    nnz_acc = warp_sum<long long>(nnz_acc);
+    if (lane == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
 }
 
 // ---------------------------------------------------- group hash kernel
@@ -1586,6 +1828,14 @@ static void launch_group_hash(const MatView &A, const MatView &B, const MatView 
              C, J, ctl, mask, bin);
 }
 
+template <int SR, int G>
+static void launch_group_sort(const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl,
+                              unsigned mask, int bin, cudaStream_t s, int num_sms) {
+    static const int per_sm = resident_per_sm(k_num_group_sort<SR, G>, GS_NT, 0);
+    launch_k(k_num_group_sort<SR, G>, grid_for(num_sms * per_sm, J.rows_hint, GS_NT / G), GS_NT, 0, s, A, B, C, J,
+             ctl, mask, bin);
+}
+
 template <int SR, int LOG_TS>
 static void launch_cta_hash(const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl,
                             unsigned mask, int bin, cudaStream_t s, int num_sms) {
@@ -1670,6 +1920,11 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
         const int j = k++;
         return (j == 0 || ns == 1) ? ss[0] : ss[1 + (j - 1) % (ns - 1)];
     };
+    // with the group sort on, its first bin takes the rows of sparse
+    // products and the first stream
+    if (J.sort_max > 0) launch_group_sort<SR, 8>(A, B, C, J, ctl, mask, BIN_S64, next(), num_sms);
+    if (J.sort_max > 64) launch_group_sort<SR, 16>(A, B, C, J, ctl, mask, BIN_S128, next(), num_sms);
+    if (J.sort_max > 128) launch_group_sort<SR, 32>(A, B, C, J, ctl, mask, BIN_S256, next(), num_sms);
     {
         // shared memory for the bin's bound only: at a bound of 49 three
         // blocks of 128 threads fit an SM with double values (two at 64),
@@ -1687,8 +1942,11 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
             launch_k(k_num_thread_merge<SR, MERGE_K>, grid_for(num_sms * per_sm, J.rows_hint, TM_NT), TM_NT, smem_m,
                      next(), A, B, C, J, ctl, mask, bin, ub);
         };
-        launch_merge((int)BIN_T8, std::max(J.tm_ub, 1));
-        if (J.tm_k > 0 && J.tm_ub < MERGE_UB) launch_merge((int)BIN_T64, MERGE_UB);
+        // rows the group sort takes leave the merge bins empty
+        if (J.tm_k > 0 && J.sort_max < MERGE_UB) {
+            launch_merge((int)BIN_T8, std::max(J.tm_ub, 1));
+            if (J.tm_ub < MERGE_UB) launch_merge((int)BIN_T64, MERGE_UB);
+        }
     }
     if (J.dense_mode) {
         const int mp = (int)((J.m + 31) / 32 * 32);

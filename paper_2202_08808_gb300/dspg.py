@@ -69,7 +69,8 @@ class _Stats(C.Structure):
 
 
 class _Tuning(C.Structure):
-    _fields_ = [(n, C.c_int32) for n in ("merge_k", "merge_ub", "lanes_min", "table_shift", "warp_max", "cta_max")]
+    _fields_ = [(n, C.c_int32) for n in ("merge_k", "merge_ub", "lanes_min", "table_shift", "warp_max", "cta_max",
+                                         "sort_max")]
 
 
 def library_path() -> str:

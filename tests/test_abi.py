@@ -78,11 +78,13 @@ def test_tuning_candidates_start_with_the_defaults_and_stay_in_range():
     import paper_2202_08808_gb300 as pkg
     cands = pkg.tuning_candidates()
     assert len(cands) >= 8
-    assert cands[0] == dict(merge_k=8, merge_ub=64, lanes_min=8, table_shift=0, warp_max=1024, cta_max=16384)
+    assert cands[0] == dict(merge_k=8, merge_ub=64, lanes_min=8, table_shift=0, warp_max=1024, cta_max=16384,
+                            sort_max=64)
     for c in cands:
         assert 0 <= c["merge_k"] <= 8 and 0 <= c["merge_ub"] <= 64
         assert c["lanes_min"] in (8, 16, 32) and c["table_shift"] in (0, 1)
         assert 0 <= c["warp_max"] <= 1024 and 0 <= c["cta_max"] <= 16384
+        assert 0 <= c["sort_max"] <= 256
     assert len({tuple(sorted(c.items())) for c in cands}) == len(cands)
 
 
