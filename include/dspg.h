@@ -92,6 +92,10 @@ typedef struct {
     int32_t exact_static;   /* static product: 1 = count rows exactly before laying C out (two passes);
                                0 = auto (exact only when the bound-sized layout would take over a quarter
                                of the free device memory) */
+    int32_t bloom;          /* 1: keep the Bloom filter F of C (Section 5.2: a 64-bit word per entry of C,
+                               bit (k mod 64) set when A(i,k) B(k,j) contributes to C(i,j)) and apply every
+                               batch by the entry-level masked recompute of Algorithm 2 (general updates);
+                               0 (default): the row path.  See dspg_apply_batch. */
 } dspg_options;
 
 /* What one apply_batch did.  Counts of the unique, last-writer-wins batch
@@ -115,6 +119,10 @@ typedef struct {
     int64_t algebraic;      /* 1: the batch took the delta path of Eq. 1 (dspg_apply_batch_algebraic) */
     int64_t table_slots;    /* accumulator slots of the recompute's rows (hash-table or dense-row size per
                                row, summed; what the sizing decides, the learned estimator's gain) */
+    int64_t masked_entries; /* handles with the Bloom filter: entries of C* (Algorithm 2's mask), the
+                               entries of C the batch may change; affected_rows then counts C*'s rows,
+                               a_entries the entries of A' the filter kept (A^R) and products the
+                               products of the masked multiplication */
 } dspg_batch_stats;
 
 /* Stages of apply_batch, in pipeline order, for dspg_stage_times. */
@@ -172,7 +180,18 @@ dspg_status dspg_build_form(dspg_handle **out, const dspg_csr *A, const dspg_csr
  * A) and bring C up to date: C' = A' B' (Section 5, general updates).
  * Rows of C outside the affected set R = rows(A*) u {i : A(i,k) != 0,
  * k in rows(B*)} are left bit-for-bit as they were.  stats may be NULL.
- * Synchronises the stream once to return the status. */
+ * Synchronises the stream once to return the status.
+ *
+ * A handle built with options.bloom = 1 applies the batch entry by entry
+ * instead (Section 5.2, Algorithm 2): the pattern of C* = A* B' + A B*
+ * with its Bloom words F*, E = F | F* at C*'s entries and its OR per row
+ * R_i, the entries of A' that R_i's bits keep (A^R), their products masked
+ * at C*, and the merge of the results into C and F.  Entries of C outside
+ * C* are left bit-for-bit as they were, the rows of C* are what
+ * dspg_last_affected lists, and masked_entries in stats counts C*.  It
+ * runs eagerly with several stream synchronisations (no graph); such a
+ * handle rejects dspg_apply_batch_algebraic, dspg_apply_batch_async,
+ * dspg_autotune and groups (DSPG_ERR_STATE). */
 dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
                              dspg_batch_stats *stats, void *stream);
 
@@ -222,6 +241,13 @@ dspg_status dspg_apply_batch_algebraic(dspg_handle *h, const dspg_updates *dA, c
  * frees its scratch within the call. */
 dspg_status dspg_read_C(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32_t *col, void *val,
                         int on_device, void *stream);
+
+/* The Bloom filter F of C (handles with options.bloom = 1; Section 5.2):
+ * the same two-call protocol and canonical order as dspg_read_C, with the
+ * 64-bit word of each entry in words (bit (k mod 64) set when A(i,k) B(k,j)
+ * contributes to C(i,j)).  DSPG_ERR_STATE for a handle without F. */
+dspg_status dspg_read_bloom(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32_t *col, uint64_t *words,
+                            int on_device, void *stream);
 
 /* Read A' (the updated left operand) in canonical CSR; same convention.
  * A' is in the caller's coordinates: rowptr has A->nrows + 1 entries of the

@@ -22,6 +22,7 @@
  *    compute C' = A' B'.  For general updates C' can only differ from C where
  *    C* = A* B' + A B* (Eq. 1) has a non-zero; the row set of C* is the set
  *    of rows this oracle recomputes in its row-dynamic route.
+ *  - Section 5.2: the Bloom filter F of C (orc_bloom), by its definition.
  *  - Section 6.1: the local product is Gustavson's row-wise algorithm with a
  *    sparse accumulator.  Here the accumulator is a dense value array plus a
  *    presence flag per column and a list of touched columns, the plainest
@@ -372,6 +373,49 @@ int orc_multiply_rows(const orc_mat *A, const orc_mat *B, const int32_t *rows, i
     }
     free(tmp.col); free(tmp.fv); free(tmp.iv);
     spa_free(&s);
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------- the Bloom filter F */
+
+/* Section 5.2: the Bloom filter of C = A B is a matrix F with C's pattern
+ * whose entry F(i,j) is an l-bit field (l = 64 here, as in the paper) with
+ * bit (k mod l) set iff the term A(i,k) B(k,j) contributes to C(i,j), i.e.
+ * iff both A(i,k) and B(k,j) are non-zeros.  Computed by definition, row by
+ * row like the product: for each A(i,k), each B(k,j), OR the bit into the
+ * word of column j.  Two calls: with col == NULL only rowptr (nrows+1
+ * entries) is filled. */
+int orc_bloom(const orc_mat *A, const orc_mat *B, int64_t *rowptr, int32_t *col, uint64_t *words) {
+    if (A->ncols != B->nrows) return ORC_ERR_INVALID;
+    int64_t m = B->ncols;
+    uint8_t *present = (uint8_t *)calloc((size_t)(m > 0 ? m : 1), 1);
+    uint64_t *acc = (uint64_t *)calloc((size_t)(m > 0 ? m : 1), sizeof(uint64_t));
+    int32_t *touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    if (!present || !acc || !touched) { free(present); free(acc); free(touched); return ORC_ERR_OOM; }
+    rowptr[0] = 0;
+    for (int64_t i = 0; i < A->nrows; i++) {
+        const orc_row *ar = &A->rows[i];
+        int32_t nt = 0;
+        for (int32_t p = 0; p < ar->len; p++) {
+            int32_t k = ar->col[p];
+            uint64_t bit = (uint64_t)1 << (k % 64);
+            const orc_row *br = &B->rows[k];
+            for (int32_t q = 0; q < br->len; q++) {
+                int32_t j = br->col[q];
+                if (!present[j]) { present[j] = 1; acc[j] = 0; touched[nt++] = j; }
+                acc[j] |= bit;
+            }
+        }
+        qsort(touched, (size_t)nt, sizeof(int32_t), cmp_i32);
+        int64_t o = rowptr[i];
+        for (int32_t t = 0; t < nt; t++) {
+            int32_t j = touched[t];
+            if (col) { col[o + t] = j; words[o + t] = acc[j]; }
+            present[j] = 0;
+        }
+        rowptr[i + 1] = o + nt;
+    }
+    free(present); free(acc); free(touched);
     return ORC_OK;
 }
 

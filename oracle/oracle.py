@@ -66,6 +66,8 @@ def oracle_lib():
             lib.orc_multiply_rows.argtypes = [p, p, p, i64, i32, p, p, p]
             lib.orc_affected_rows.restype = i64
             lib.orc_affected_rows.argtypes = [p, i64, p, p, p, i64, p, p, p, i64, i32, p]
+            lib.orc_bloom.restype = i32
+            lib.orc_bloom.argtypes = [p, p, p, p, p]
             lib.orc_replace_rows.restype = i32
             lib.orc_replace_rows.argtypes = [p, p, p, p, i64]
             lib.orc_row_len.restype = C.c_int32
@@ -177,6 +179,21 @@ class OMat:
         if st != 0:
             raise OracleError(f"orc_multiply_rows status {st}")
         return rp, col, val
+
+    def bloom(self, B: "OMat"):
+        """The Bloom filter F of self * B (Section 5.2, l = 64), by its
+        definition: (rowptr, col, words) with words uint64."""
+        n = self._shape[0]
+        rp = np.empty(n + 1, np.int64)
+        st = self._lib.orc_bloom(self._h, B._h, _ptr(rp), None, None)
+        if st != 0:
+            raise OracleError(f"orc_bloom status {st}")
+        col = np.empty(int(rp[-1]), np.int32)
+        words = np.empty(int(rp[-1]), np.uint64)
+        st = self._lib.orc_bloom(self._h, B._h, _ptr(rp), _ptr(col), _ptr(words))
+        if st != 0:
+            raise OracleError(f"orc_bloom status {st}")
+        return rp, col, words
 
     def replace_rows(self, A: "OMat", B: "OMat", rows) -> None:
         rows = np.ascontiguousarray(rows, np.int32)

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdspg.so")
 
-SOURCES = ["scan.cu", "sort.cu", "update.cu", "spgemm.cu", "layout.cu", "handle.cu", "noalloc.cu", "estimator.cu", "algebraic.cu", "form.cu"]
+SOURCES = ["scan.cu", "sort.cu", "update.cu", "spgemm.cu", "layout.cu", "handle.cu", "noalloc.cu", "estimator.cu", "algebraic.cu", "form.cu", "masked.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

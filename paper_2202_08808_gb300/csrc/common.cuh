@@ -29,6 +29,7 @@ enum : unsigned {
     ST_C_SCRATCH = 1u << 7,   // accumulator scratch too small
     ST_TIMEOUT = 1u << 8,     // a bounded probe loop gave up
     ST_ALG_FULL = 1u << 9,    // the delta path's list of new C entries is full: recompute the touched rows
+    ST_MASK_FULL = 1u << 10,  // the masked path's contribution or kept-entry list is full: grow it, run again
 };
 constexpr unsigned M_AB = ST_INVALID | ST_AB_STAGE | ST_AB_ARENA | ST_TIMEOUT;
 constexpr unsigned M_AT = M_AB | ST_AT_STAGE | ST_AT_ARENA;
@@ -77,6 +78,8 @@ struct Ctl {
     long long timeout_ub;      // that row's product bound, summed again when it happened
     long long alg_new;         // delta path: new entries of C listed
     long long alg_contrib;     // delta path: contributions formed (products of Eq. 1's two terms)
+    long long mask_n;          // masked path: contributions to the pattern of C* formed
+    long long mask_kept;       // masked path: entries of A' kept by the Bloom filter (A^R)
     long long pad[1];
 };
 

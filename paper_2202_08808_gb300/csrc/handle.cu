@@ -94,6 +94,7 @@ struct DevMat {
     DBuf<int64_t> off;
     DBuf<int32_t> len, cap, col;
     DBuf<char> val;
+    DBuf<unsigned long long> fb;  // C with its Bloom filter: a word per arena entry (else empty)
     DBuf<long long> top;
     int64_t arena_cap = 0;
     MatView view() {
@@ -294,6 +295,59 @@ void dspg::set_thread_error(const char *msg) { g_err = msg; }
 // launches share queues and wait on each other: three side streams.
 constexpr int NUM_SIDE = 3;
 
+// The masked path's work buffers (Algorithm 2), grown to each batch's
+// counts: contributions to C*, their sort, C* itself with its runs, the
+// kept entries of A', and the Bloom build's long-row list and place maps.
+struct MaskWs {
+    int64_t ccap = 0;  // contributions
+    DBuf<uint64_t> key, key_alt, bits;
+    DBuf<uint32_t> idx, idx_alt, counts;
+    DBuf<int64_t> scan_tmp, scan_out, ex;
+    DBuf<int32_t> flag;
+    int64_t ucap = 0;  // entries of C*
+    DBuf<int32_t> urow, ucol, rflag, upos, run_row, dcap;
+    DBuf<unsigned long long> ufs, ue, rbits, h;
+    DBuf<int64_t> rex, run_start, dest, uscan;
+    DBuf<char> z;
+    DBuf<uint8_t> hit;
+    int64_t kcap = 0;  // kept entries of A'
+    DBuf<int32_t> kept_run;
+    DBuf<int64_t> kept_a;
+    DBuf<int32_t> rows_long, posmap;
+    DBuf<long long> n_long;
+    int64_t posmap_ctas = 0, posmap_m = 0;
+
+    void ensure_contrib(int64_t n) {
+        if (n <= ccap) return;
+        const int64_t c = std::max<int64_t>(n, 2 * ccap);
+        key.reserve(c); key_alt.reserve(c); bits.reserve(c);
+        idx.reserve(c); idx_alt.reserve(c);
+        flag.reserve(c); ex.reserve(c + 1);
+        int64_t cnt = 0;
+        sort_tmp_sizes(c, &cnt);
+        counts.reserve(cnt);
+        scan_out.reserve(cnt + 1);
+        scan_tmp.reserve(scan_tmp_entries(std::max(cnt, c)) + 1);
+        ccap = c;
+    }
+    void ensure_unique(int64_t nu, int vsize) {
+        if (nu <= ucap) return;
+        const int64_t c = std::max<int64_t>(nu, 2 * ucap);
+        urow.reserve(c); ucol.reserve(c); rflag.reserve(c); upos.reserve(c); run_row.reserve(c); dcap.reserve(c);
+        ufs.reserve(c); ue.reserve(c); rbits.reserve(c); h.reserve(c);
+        rex.reserve(c + 1); run_start.reserve(c + 1); dest.reserve(c);
+        uscan.reserve(scan_tmp_entries(c) + 1);
+        z.reserve(c * vsize); hit.reserve(c);
+        ucap = c;
+    }
+    void ensure_kept(int64_t n) {
+        if (n <= kcap) return;
+        const int64_t c = std::max<int64_t>(n, 2 * kcap);
+        kept_run.reserve(c); kept_a.reserve(c);
+        kcap = c;
+    }
+};
+
 struct dspg_handle {
     int sr = 0, vsize = 8, num_sms = 148, dev = 0;
     dspg_options opt{};
@@ -377,6 +431,9 @@ struct dspg_handle {
     DBuf<int32_t> xcol;
     DBuf<char> xval;
     int64_t extra_slots = 0;                    // table slots of the last batch's overflow recompute
+    bool bloom = false;                         // C keeps its Bloom filter; batches take Algorithm 2
+    MaskWs mw;                                  // the masked path's buffers
+    int64_t last_masked = 0;                    // entries of C* of the last batch
     int64_t compactions = 0;
     std::string err;
 
@@ -406,6 +463,7 @@ void set_defaults(dspg_options *o) {
     o->arena_headroom = 1.5;
     o->keep_transpose = -1;
     o->exact_static = 0;
+    o->bloom = 0;
 }
 
 std::string overflow_message(const Ctl *c) {
@@ -477,6 +535,12 @@ void regrow(dspg_handle *h, DevMat &M, cudaStream_t s) {
     if (M.vsize) nval.reserve(cap * M.vsize);
     copy_rows(nullptr, M.nrows, M.off.p, M.len.p, M.col.p, M.vsize ? (void *)M.val.p : nullptr, noff.p, ncol.p,
               M.vsize ? (void *)nval.p : nullptr, M.vsize, s, h->num_sms);
+    DBuf<unsigned long long> nfb;
+    if (M.fb.n > 0) {  // the Bloom words move with their entries (bit patterns copied as 8-byte values)
+        nfb.reserve(cap);
+        copy_rows(nullptr, M.nrows, M.off.p, M.len.p, M.col.p, (const void *)M.fb.p, noff.p, ncol.p, (void *)nfb.p,
+                  8, s, h->num_sms);
+    }
     long long t = total;
     CK(cudaMemcpyAsync(M.top.p, &t, sizeof(long long), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
@@ -484,6 +548,7 @@ void regrow(dspg_handle *h, DevMat &M, cudaStream_t s) {
     M.cap.swap(ncap);
     M.col.swap(ncol);
     M.val.swap(nval);
+    if (M.fb.n > 0) M.fb.swap(nfb);
     M.arena_cap = cap;
     h->compactions++;
     h->epoch++;
@@ -651,6 +716,8 @@ void numeric_branches(dspg_handle *h, cudaStream_t s, const CJob &J) {
 // as in squares of skewed graphs), an exact pass first counts every row and
 // C is laid out from the counts instead.  The arena is reused when large
 // enough.
+void bloom_build(dspg_handle *h, cudaStream_t s);
+
 void static_recompute(dspg_handle *h, cudaStream_t s) {
     h->c_serial++;
     ensure_c_ws(h, s);
@@ -712,6 +779,7 @@ void static_recompute(dspg_handle *h, cudaStream_t s) {
     read_ctl(h, s);
     if (h->hctl->status & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, overflow_message(h->hctl));
     if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "static recompute failed with status " + std::to_string(h->hctl->status));
+    if (h->bloom) bloom_build(h, s);
     h->epoch++;
 }
 
@@ -1168,7 +1236,14 @@ void load_operand(dspg_handle *h, DevMat &M, const dspg_csr *m, bool trans, cuda
 }
 
 int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, int64_t *rowptr, int32_t *col,
-                 void *val, int on_device, cudaStream_t s) {
+                 void *val, int on_device, cudaStream_t s, bool bloom = false) {
+    // with bloom the values read are C's Bloom words (8 bytes each) instead
+    MatView V = M.view();
+    int vs = M.vsize;
+    if (bloom) {
+        V.val = (void *)M.fb.p;
+        vs = 8;
+    }
     DBuf<int32_t> rows_l;
     const int32_t *rows = nullptr;
     int64_t n = M.nrows;
@@ -1214,7 +1289,7 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
     int64_t *listed = read_scratch(h->rd.listed, listed_l, list_cap);
     CK(cudaMemsetAsync(n_listed, 0, sizeof(unsigned), s));
     auto sort_out = [&](int32_t *oc, void *ov) {
-        sort_rows(rp, n, oc, ov, M.vsize, n_listed, listed, list_cap, s, h->num_sms);
+        sort_rows(rp, n, oc, ov, vs, n_listed, listed, list_cap, s, h->num_sms);
         unsigned nl = 0;
         CK(cudaMemcpyAsync(&nl, n_listed, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1254,30 +1329,30 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
             scan_out.reserve(cnt + 1);
             scan_tmp.reserve(scan_tmp_entries(cnt) + 1);
             tcol.reserve(total);
-            tval.reserve(total * std::max(M.vsize, 1));
+            tval.reserve(total * std::max(vs, 1));
             CK(cudaMemcpyAsync(d_pre.p, pre.data(), sizeof(int64_t) * (nk + 1), cudaMemcpyHostToDevice, s));
             CK(cudaMemcpyAsync(d_list.p, lh.data() + k0, sizeof(int64_t) * nk, cudaMemcpyHostToDevice, s));
             SortScratch w{kk0.p, kk1.p, ii0.p, ii1.p, counts.p, scan_tmp.p, scan_out.p, tcol.p, (void *)tval.p};
-            sort_listed_rows(rp, d_list.p, d_pre.p, nk, total, cb, oc, ov, M.vsize, w, s, h->num_sms);
+            sort_listed_rows(rp, d_list.p, d_pre.p, nk, total, cb, oc, ov, vs, w, s, h->num_sms);
             CK(cudaStreamSynchronize(s));
             k0 = k1;
         }
     };
     if (on_device) {
         CK(cudaMemcpyAsync(rowptr, rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
-        gather_rows_out(rows, n, M.view(), rp, col, val, M.vsize, s, h->num_sms);
+        gather_rows_out(rows, n, V, rp, col, val, vs, s, h->num_sms);
         sort_out(col, val);
     } else {
         DBuf<int32_t> c_l;
         DBuf<char> v_l;
         int32_t *c = read_scratch(h->rd.c, c_l, nnz);
-        char *v = read_scratch(h->rd.v, v_l, nnz * std::max(M.vsize, 1));
-        gather_rows_out(rows, n, M.view(), rp, c, v, M.vsize, s, h->num_sms);
-        sort_out(c, M.vsize ? (void *)v : nullptr);
+        char *v = read_scratch(h->rd.v, v_l, nnz * std::max(vs, 1));
+        gather_rows_out(rows, n, V, rp, c, v, vs, s, h->num_sms);
+        sort_out(c, vs ? (void *)v : nullptr);
         CK(cudaMemcpyAsync(rowptr, rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
         if (nnz > 0) {
             if (col) CK(cudaMemcpyAsync(col, c, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s));
-            if (val) CK(cudaMemcpyAsync(val, v, (size_t)M.vsize * nnz, cudaMemcpyDeviceToHost, s));
+            if (val) CK(cudaMemcpyAsync(val, v, (size_t)vs * nnz, cudaMemcpyDeviceToHost, s));
         }
         CK(cudaStreamSynchronize(s));
     }
@@ -1465,6 +1540,7 @@ void recover(dspg_handle *h, cudaStream_t s) {
 void fill_stats(dspg_handle *h, dspg_batch_stats *stats, int64_t compactions0) {
     const int64_t nA = h->inA.n, nB = h->inB.n;
     h->last_nR = h->hctl->n_affected;
+    if (!h->bloom) h->last_masked = 0;
     if (stats) {
         const Ctl &c = *h->hctl;
         std::memset(stats, 0, sizeof(*stats));
@@ -1489,6 +1565,7 @@ void fill_stats(dspg_handle *h, dspg_batch_stats *stats, int64_t compactions0) {
         const int64_t m = h->Bm().ncols;
         for (int b = 0; b < NBINS; b++) stats->table_slots += c.bin_count[b] * bin_table_slots(b, m);
         stats->table_slots += h->extra_slots;
+        stats->masked_entries = h->last_masked;
     }
 }
 
@@ -1523,10 +1600,17 @@ void est_fallback(dspg_handle *h, cudaStream_t s) {
 }
 
 // One batch on one handle, as dspg_apply_batch (errors as exceptions).
+void masked_apply(dspg_handle *h, cudaStream_t s);
+
 void apply_one(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, dspg_batch_stats *stats,
                cudaStream_t s) {
     prepare_batch(h, dA, dB, s);
     const int64_t compactions0 = h->compactions;
+    if (h->bloom) {
+        masked_apply(h, s);
+        fill_stats(h, stats, compactions0);
+        return;
+    }
     run_first(h, s);
     if (h->prof) stage_times_from_events(h);
     recover(h, s);
@@ -1686,6 +1770,213 @@ bool apply_algebraic(dspg_handle *h, cudaStream_t s) {
     return true;
 }
 
+// ------------------------------------- general updates by Algorithm 2
+
+// F for every entry of C from A and B (after a static recompute): rows up
+// to 512 entries by the warp kernel, which lists the longer ones for the
+// CTA kernel and its per-CTA column-to-place maps (m entries each, at most
+// about 1 GiB of them).
+void bloom_build(dspg_handle *h, cudaStream_t s) {
+    DevMat &C = h->C;
+    MaskWs &w = h->mw;
+    if (C.fb.n < C.arena_cap) {
+        C.fb.release();
+        C.fb.reserve(std::max<int64_t>(C.arena_cap, 1));
+    }
+    const int64_t n = C.nrows;
+    const long long cap_long = std::max<int64_t>(n, 1);
+    w.rows_long.reserve(cap_long);
+    w.n_long.reserve(1);
+    CK(cudaMemsetAsync(w.n_long.p, 0, sizeof(long long), s));
+    bloom_rows(h->A.view(), h->Bm().view(), C.view(), C.fb.p, w.rows_long.p, w.n_long.p, cap_long, s, h->num_sms);
+    long long nl = 0;
+    CK(cudaMemcpyAsync(&nl, w.n_long.p, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (nl > 0) {
+        const int64_t m = std::max<int64_t>(C.ncols, 1);
+        int64_t ctas = std::min<int64_t>(2 * h->num_sms, std::max<int64_t>(1, (int64_t(1) << 28) / m));
+        ctas = std::min<int64_t>(ctas, nl);
+        if (w.posmap_ctas < ctas || w.posmap_m != m) {
+            w.posmap.release();
+            w.posmap.reserve(ctas * m);
+            CK(cudaMemsetAsync(w.posmap.p, 0xff, sizeof(int32_t) * ctas * m, s));  // -1: no place
+            w.posmap_ctas = ctas;
+            w.posmap_m = m;
+        }
+        bloom_long_rows(h->A.view(), h->Bm().view(), C.view(), C.fb.p, w.rows_long.p, w.n_long.p, cap_long,
+                        w.posmap.p, (int)ctas, s);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+}
+
+// One batch of general updates by Algorithm 2 (the handle keeps F): the
+// merge of A' and B' as on the row path, then computePattern, E and R,
+// A^R, the masked product and the merge into C and F.  Runs eagerly on s
+// and reads the control block between its steps, growing what overflowed.
+void masked_apply(dspg_handle *h, cudaStream_t s) {
+    const int64_t nA = h->inA.n, nB = h->b_is_a ? 0 : h->inB.n;
+    MaskWs &w = h->mw;
+    for (int iter = 0;; iter++) {
+        begin_batch(h->h_args_dev, h->d_args, h->ctl, s);
+        stage_sort(h, s);
+        if (nA > 0)
+            run_classify(h->wA.job(nA), h->A.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE,
+                         DetectBufs{}, false, false, s, h->num_sms);
+        if (nB > 0)
+            run_classify(h->wB.job(nB), h->B.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE,
+                         DetectBufs{}, false, false, s, h->num_sms);
+        CK(cudaGetLastError());
+        read_ctl(h, s);
+        const unsigned st = h->hctl->status;
+        if (st & ST_INVALID) throw Err(DSPG_ERR_INVALID, "batch entry out of range or with an invalid value/op");
+        if ((st & ST_AB_STAGE) && iter < 4) {
+            if (h->wA.grow_stage(h->hctl->u[0].stage_top + 1024)) h->epoch++;
+            if (h->wB.grow_stage(h->hctl->u[1].stage_top + 1024)) h->epoch++;
+            continue;
+        }
+        if (st) throw Err(DSPG_ERR_CUDA, "masked path: classification failed, status " + std::to_string(st));
+        break;
+    }
+    stage_merge(h, s, -1);
+    stage_commit_ab(h, s);
+    // computePattern reads B' and the transposed pattern of A before this batch
+    const UpdJob ja = h->wA.job(nA);
+    const UpdJob jb = h->b_is_a ? ja : h->wB.job(nB);
+    const int cb = bits_for(std::max<int64_t>(h->C.ncols, 2));
+    const int rb = bits_for(std::max<int64_t>(h->C.nrows, 2));
+    w.ensure_contrib(std::max<int64_t>(int64_t(1) << 16, 16 * (nA + nB)));
+    const bool side_on = h->has_at && nA > 0;
+    for (int iter = 0;; iter++) {
+        PatJob J{};
+        J.xr = ja.row; J.xc = ja.col; J.xk = ja.kind; J.xn = nA;
+        J.yr = jb.row; J.yc = jb.col; J.yk = jb.kind; J.yn = h->b_is_a ? nA : nB;
+        if (!h->has_at) J.yn = 0;  // B is never updated without the pattern
+        J.key = w.key.p; J.bits = w.bits.p; J.cap = w.ccap; J.cb = cb;
+        reset_range(h, &h->ctl->mask_n, sizeof(long long), s);
+        pat_contrib(J, h->Bm().view(), h->AT.view(), h->ctl, M_AB, s, h->num_sms);
+        CK(cudaGetLastError());
+        read_ctl(h, s);
+        const unsigned st = h->hctl->status;
+        if ((st & ST_AB_ARENA) && iter < 4) {
+            // A's arena ran out in the commit: nothing after it ran; grow it
+            // and commit again (the staged rows are still in place)
+            regrow(h, h->A, s);
+            if (nB > 0) regrow(h, h->B, s);
+            for (int k = 0; k < 2; k++) {
+                reset_range(h, &h->ctl->u[k].n_cchunk, sizeof(long long), s);
+                reset_range(h, &h->ctl->u[k].reloc, sizeof(long long), s);
+            }
+            reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+            stage_commit_ab(h, s);
+            continue;
+        }
+        if ((st & ST_MASK_FULL) && iter < 6) {
+            w.ensure_contrib(h->hctl->mask_n);
+            reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+            continue;
+        }
+        if (st) throw Err(DSPG_ERR_CUDA, "masked path: computePattern failed, status " + std::to_string(st));
+        break;
+    }
+    const int64_t n = h->hctl->mask_n;
+    if (side_on) {
+        transpose_front(h, s);
+        transpose_commit(h, s);
+        read_ctl(h, s);
+    }
+    for (int iter = 0; iter < 8 && (h->hctl->status & (ST_AT_STAGE | ST_AT_ARENA)); iter++) {
+        const unsigned st = h->hctl->status;
+        if ((st & ST_AT_STAGE) && h->wAT.grow_stage(h->hctl->u[2].stage_top + 1024)) h->epoch++;
+        if (st & ST_AT_ARENA) regrow(h, h->AT, s);
+        reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+        reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
+        transpose_front(h, s);
+        transpose_commit(h, s);
+        read_ctl(h, s);
+    }
+    if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "masked path: update failed, status " + std::to_string(h->hctl->status));
+    // C* sorted by (i, j), equal keys merged, in runs of one row
+    int64_t nu = 0, nruns = 0;
+    MaskJob M{};
+    auto job = [&]() {
+        M.urow = w.urow.p; M.ucol = w.ucol.p; M.ufs = w.ufs.p;
+        M.run_start = w.run_start.p; M.run_row = w.run_row.p; M.nruns = nruns;
+        M.upos = w.upos.p; M.ue = w.ue.p; M.rbits = w.rbits.p;
+        M.kept_run = w.kept_run.p; M.kept_a = w.kept_a.p; M.kcap = w.kcap; M.nkept = 0;
+        M.z = (void *)w.z.p; M.h = w.h.p; M.hit = w.hit.p; M.dest = w.dest.p; M.dcap = w.dcap.p;
+    };
+    if (n > 0) {
+        iota_u32(w.idx.p, n, s, h->num_sms);
+        bool alt = false;
+        radix_sort_pairs(w.key.p, w.idx.p, w.key_alt.p, w.idx_alt.p, n, rb + cb, w.counts.p, w.scan_tmp.p,
+                         w.scan_out.p, s, &alt);
+        const uint64_t *K = alt ? w.key_alt.p : w.key.p;
+        const uint32_t *I = alt ? w.idx_alt.p : w.idx.p;
+        pat_heads(K, n, w.flag.p, s, h->num_sms);
+        scan_i32_to_i64(w.flag.p, w.ex.p, n, w.scan_tmp.p, s);
+        nu = read_i64(w.ex.p + n, s);
+        w.ensure_unique(nu, h->vsize);
+        job();
+        pat_unique(K, I, w.bits.p, n, w.ex.p, cb, M, w.rflag.p, s, h->num_sms);
+        scan_i32_to_i64(w.rflag.p, w.rex.p, nu, w.uscan.p, s);
+        nruns = read_i64(w.rex.p + nu, s);
+        job();
+        CK(cudaMemsetAsync(h->wc.bmR.p, 0, sizeof(uint32_t) * h->wc.bmR.n, s));
+        pat_runs(M, w.rflag.p, w.rex.p, nu, h->wc.bmR.p, s, h->num_sms);
+        CK(cudaMemcpyAsync(w.run_start.p + nruns, &nu, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        // E and R
+        CK(cudaMemsetAsync(w.upos.p, 0xff, sizeof(int32_t) * nu, s));
+        CK(cudaMemsetAsync(w.ue.p, 0, sizeof(unsigned long long) * nu, s));
+        mask_scan(M, h->C.view(), h->C.fb.p, s, h->num_sms);
+        // A^R
+        w.ensure_kept(std::max<int64_t>(int64_t(1) << 16, 4 * nu));
+        for (int iter = 0;; iter++) {
+            job();
+            reset_range(h, &h->ctl->mask_kept, sizeof(long long), s);
+            mask_keep(M, h->A.view(), h->ctl, s, h->num_sms);
+            CK(cudaGetLastError());
+            read_ctl(h, s);
+            if ((h->hctl->status & ST_MASK_FULL) && iter < 6) {
+                w.ensure_kept(h->hctl->mask_kept);
+                reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+                continue;
+            }
+            break;
+        }
+        if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "masked path: A^R failed, status " + std::to_string(h->hctl->status));
+        job();
+        M.nkept = h->hctl->mask_kept;
+        // the masked product
+        mask_init_acc(h->sr, M, nu, s, h->num_sms);
+        CK(cudaMemsetAsync(w.h.p, 0, sizeof(unsigned long long) * nu, s));
+        CK(cudaMemsetAsync(w.hit.p, 0, nu, s));
+        mask_product(h->sr, M, h->A.view(), h->Bm().view(), h->ctl, s, h->num_sms);
+        // the merge into C and F, growing C's arena until the moved rows fit
+        for (int iter = 0;; iter++) {
+            mask_plan(M, h->C.view(), h->ctl, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
+            CK(cudaGetLastError());
+            read_ctl(h, s);
+            if ((h->hctl->status & ST_C_ARENA) && iter < 4) {
+                regrow(h, h->C, s);  // the plan wrote nothing but places: plan again in the new arena
+                reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+                reset_range(h, &h->ctl->c_reloc, sizeof(long long), s);
+                continue;
+            }
+            break;
+        }
+        if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "masked path: C's arena cannot take the merge");
+        mask_splice(h->sr, M, h->C.view(), h->C.fb.p, h->ctl, M_C, s, h->num_sms);
+    }
+    // the rows of C*, for the statistics and dspg_last_affected
+    alg_collect(h, h->wc.bmR.p, s);
+    CK(cudaGetLastError());
+    read_ctl(h, s);
+    if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "masked path: merge failed, status " + std::to_string(h->hctl->status));
+    h->hctl->a_entries = M.nkept;
+    h->last_masked = nu;
+}
+
 // Captures what body() enqueues on cs into an executable graph; the number
 // of kernels it launched goes to *nk.  The capture is closed on errors.
 template <typename F>
@@ -1792,7 +2083,10 @@ dspg_status dspg_build_form(dspg_handle **out, const dspg_csr *A, const dspg_csr
             if (opt->arena_headroom >= 1.0) h->opt.arena_headroom = opt->arena_headroom;
             h->opt.keep_transpose = opt->keep_transpose;
             h->opt.exact_static = opt->exact_static;
+            if (opt->bloom != 0 && opt->bloom != 1) throw Err(DSPG_ERR_INVALID, "options: bloom must be 0 or 1");
+            h->opt.bloom = opt->bloom;
         }
+        h->bloom = h->opt.bloom == 1;
         h->sr = sr;
         h->vsize = sr == DSPG_PLUS_TIMES_F64 ? 8 : 4;
         h->trans_a = ta;
@@ -1854,7 +2148,7 @@ dspg_status dspg_build_form(dspg_handle **out, const dspg_csr *A, const dspg_csr
         }
         // C = A A (and a stored copy of A as B) needs the transposed pattern
         // for every batch; otherwise it is built on the first B batch
-        const bool keep_t = h->b_is_a || h->b_alias || h->opt.keep_transpose > 0;
+        const bool keep_t = h->b_is_a || h->b_alias || h->opt.keep_transpose > 0 || h->bloom;
         if (keep_t) build_transpose(h, s);
         static_recompute(h, s);
         *out = h;
@@ -1887,6 +2181,7 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
 dspg_status dspg_apply_batch_async(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, void *stream) {
     if (!h) return DSPG_ERR_INVALID;
     if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is already in flight"));
+    if (h->bloom) return fail(h, Err(DSPG_ERR_STATE, "a handle with the Bloom filter applies batches synchronously"));
     try {
         const cudaStream_t s = (cudaStream_t)stream;
         prepare_batch(h, dA, dB, s);
@@ -1920,6 +2215,7 @@ dspg_status dspg_apply_batch_algebraic(dspg_handle *h, const dspg_updates *dA, c
                                        dspg_batch_stats *stats, void *stream) {
     if (!h) return DSPG_ERR_INVALID;
     if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
+    if (h->bloom) return fail(h, Err(DSPG_ERR_STATE, "a handle with the Bloom filter takes dspg_apply_batch"));
     try {
         const cudaStream_t s = (cudaStream_t)stream;
         prepare_batch(h, dA, dB, s);
@@ -1945,6 +2241,19 @@ dspg_status dspg_read_C(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32
     try {
         *nnz_out = h->form ? read_form(h, nullptr, 0, rowptr, col, val, on_device, (cudaStream_t)stream)
                            : read_mat(h, h->C, nullptr, 0, rowptr, col, val, on_device, (cudaStream_t)stream);
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_read_bloom(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32_t *col, uint64_t *words,
+                            int on_device, void *stream) {
+    if (!h || !nnz_out) return DSPG_ERR_INVALID;
+    if (!h->bloom) return fail(h, Err(DSPG_ERR_STATE, "the handle keeps no Bloom filter (options.bloom = 0)"));
+    if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
+    try {
+        *nnz_out = read_mat(h, h->C, nullptr, 0, rowptr, col, (void *)words, on_device, (cudaStream_t)stream, true);
         return DSPG_OK;
     } catch (const Err &e) {
         return fail(h, e);
@@ -2141,6 +2450,7 @@ dspg_status dspg_autotune(dspg_handle *h, const dspg_updates *dA, const dspg_upd
                           dspg_tuning *best, float *ms, int n_ms, int *n_cand, void *stream) {
     if (!h) return DSPG_ERR_INVALID;
     if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
+    if (h->bloom) return fail(h, Err(DSPG_ERR_STATE, "the autotuner replays the row path, which a handle with the Bloom filter does not take"));
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<cudaGraphExec_t> execs(kNumCandidates, nullptr);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -2357,6 +2667,7 @@ dspg_status dspg_group_create(dspg_group **out, dspg_handle *const *handles, int
         std::vector<dspg_handle *> hs(handles, handles + n);
         for (int64_t t = 0; t < n; t++) {
             if (!hs[t]) throw Err(DSPG_ERR_INVALID, "group member " + std::to_string(t) + " is NULL");
+            if (hs[t]->bloom) throw Err(DSPG_ERR_STATE, "group member " + std::to_string(t) + " keeps a Bloom filter");
             for (int64_t u = 0; u < t; u++)
                 if (hs[u] == hs[t]) throw Err(DSPG_ERR_INVALID, "group member " + std::to_string(t) + " repeats member " + std::to_string(u));
         }

@@ -106,6 +106,64 @@ struct CJob {
 };
 enum { SIZE_BOUND = 0, SIZE_COUNT = 1, SIZE_LEARNED = 2 };
 
+// The masked path (masked.cu): the contributions to the pattern of C*.
+struct PatJob {
+    const int32_t *xr, *xc;  // the sorted A batch and its kinds
+    const uint8_t *xk;
+    int64_t xn;
+    const int32_t *yr, *yc;  // the sorted B batch (the A batch when B is A)
+    const uint8_t *yk;
+    int64_t yn;
+    uint64_t *key;           // (i << cb | j) of each contribution
+    uint64_t *bits;          // its bit (k mod 64)
+    int64_t cap;
+    int cb;
+};
+
+// C* as sorted entries (row, column, F*) in runs of one row each, and the
+// masked product's working arrays, one entry per entry of C*.
+struct MaskJob {
+    int32_t *urow, *ucol;
+    unsigned long long *ufs;  // F*
+    int64_t *run_start;       // nruns + 1
+    int32_t *run_row;
+    int64_t nruns;
+    int32_t *upos;            // place of the entry in its row of C, -1 if C has none
+    unsigned long long *ue;   // F there (0 if none)
+    unsigned long long *rbits;  // R_i per run
+    int32_t *kept_run;        // A^R: run and A' entry of each kept entry
+    int64_t *kept_a;
+    int64_t kcap, nkept;
+    void *z;                  // Z: the masked product's values
+    unsigned long long *h;    // H: its Bloom words
+    uint8_t *hit;             // 1 where some product reached the entry
+    int64_t *dest;            // per run: the row's new place (-1: in place)
+    int32_t *dcap;
+};
+
+void bloom_rows(const MatView &A, const MatView &B, const MatView &C, unsigned long long *F, int32_t *rows_long,
+                long long *n_long, long long cap_long, cudaStream_t s, int num_sms);
+void bloom_long_rows(const MatView &A, const MatView &B, const MatView &C, unsigned long long *F,
+                     const int32_t *rows_long, const long long *n_long, long long cap_long, int32_t *posmap,
+                     int ctas, cudaStream_t s);
+void pat_contrib(const PatJob &J, const MatView &B, const MatView &AT, Ctl *ctl, unsigned mask, cudaStream_t s,
+                 int num_sms);
+void iota_u32(uint32_t *v, int64_t n, cudaStream_t s, int num_sms);
+void pat_heads(const uint64_t *K, int64_t n, int32_t *flag, cudaStream_t s, int num_sms);
+void pat_unique(const uint64_t *K, const uint32_t *I, const uint64_t *bits, int64_t n, const int64_t *ex, int cb,
+                const MaskJob &M, int32_t *rflag, cudaStream_t s, int num_sms);
+void pat_runs(const MaskJob &M, const int32_t *rflag, const int64_t *rex, int64_t nu, uint32_t *bm, cudaStream_t s,
+              int num_sms);
+void mask_scan(const MaskJob &M, const MatView &C, const unsigned long long *F, cudaStream_t s, int num_sms);
+void mask_keep(const MaskJob &M, const MatView &A, Ctl *ctl, cudaStream_t s, int num_sms);
+void mask_init_acc(int sr, const MaskJob &M, int64_t nu, cudaStream_t s, int num_sms);
+void mask_product(int sr, const MaskJob &M, const MatView &A, const MatView &B, Ctl *ctl, cudaStream_t s,
+                  int num_sms);
+void mask_plan(const MaskJob &M, const MatView &C, Ctl *ctl, int slack_min, int slack_div, cudaStream_t s,
+               int num_sms);
+void mask_splice(int sr, const MaskJob &M, const MatView &C, unsigned long long *F, Ctl *ctl, unsigned mask,
+                 cudaStream_t s, int num_sms);
+
 // update.cu
 void run_classify(const UpdJob &J, const MatView &M, int vsize, Ctl *ctl, unsigned mask, unsigned stage_bit,
                   const DetectBufs &D, bool mark_rows, bool mark_cols, cudaStream_t s, int num_sms);

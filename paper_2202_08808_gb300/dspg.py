@@ -53,7 +53,7 @@ class _Upd(C.Structure):
 
 class _Opt(C.Structure):
     _fields_ = [("slack_min", C.c_int32), ("slack_div", C.c_int32), ("arena_headroom", C.c_double),
-                ("keep_transpose", C.c_int32), ("exact_static", C.c_int32)]
+                ("keep_transpose", C.c_int32), ("exact_static", C.c_int32), ("bloom", C.c_int32)]
 
 
 class _Form(C.Structure):
@@ -65,7 +65,7 @@ class _Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "n_updates", "n_unique", "n_insert", "n_update", "n_delete", "n_noop", "touched_rows", "affected_rows",
         "products", "nnz_written", "relocations", "compactions", "a_entries", "est_rows", "est_overflows",
-        "algebraic", "table_slots")]
+        "algebraic", "table_slots", "masked_entries")]
 
 
 class _Tuning(C.Structure):
@@ -95,7 +95,7 @@ def load():
         lib.dspg_apply_batch.argtypes = [p, C.POINTER(_Upd), C.POINTER(_Upd), C.POINTER(_Stats), p]
         lib.dspg_apply_batch_algebraic.restype = i32
         lib.dspg_apply_batch_algebraic.argtypes = [p, C.POINTER(_Upd), C.POINTER(_Upd), C.POINTER(_Stats), p]
-        for name in ("dspg_read_C", "dspg_read_A"):
+        for name in ("dspg_read_C", "dspg_read_A", "dspg_read_bloom"):
             f = getattr(lib, name)
             f.restype = i32
             f.argtypes = [p, C.POINTER(i64), p, p, p, i32, p]
@@ -171,7 +171,8 @@ def load():
         return lib
 
 
-EXPORTED = ["dspg_build", "dspg_build_form", "dspg_apply_batch", "dspg_apply_batch_algebraic", "dspg_read_C", "dspg_read_A", "dspg_read_rows_C",
+EXPORTED = ["dspg_build", "dspg_build_form", "dspg_apply_batch", "dspg_apply_batch_algebraic", "dspg_read_C", "dspg_read_A",
+            "dspg_read_bloom", "dspg_read_rows_C",
             "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_set_profiling", "dspg_stage_times",
             "dspg_kernel_launches", "dspg_run_counts", "dspg_reserve", "dspg_multiply_rows_noalloc", "dspg_set_tuning", "dspg_get_tuning",
             "dspg_tuning_candidate", "dspg_autotune", "dspg_group_create", "dspg_group_apply", "dspg_group_destroy",
@@ -272,11 +273,14 @@ class DynamicSpGEMM:
     The general form C = alpha op(A) op(B) (+) beta X (dspg_build_form):
     ``trans_a``/``trans_b`` multiply by the transposes, ``alpha``/``beta``
     scale (multiply in (+,.), add in (min,+)) and ``X`` is a fixed matrix of
-    C's shape; batches stay in the caller's coordinates."""
+    C's shape; batches stay in the caller's coordinates.
+
+    ``bloom=True`` keeps C's Bloom filter F and applies every batch by the
+    entry-level masked recompute of Algorithm 2 (``read_bloom`` reads F)."""
 
     def __init__(self, A, B=None, semiring: int | None = None, slack_min: int = 4, slack_div: int = 4,
                  arena_headroom: float = 1.5, keep_transpose: int = -1, exact_static: int = 0, stream=None,
-                 trans_a: bool = False, trans_b: bool = False, alpha=None, beta=None, X=None):
+                 trans_a: bool = False, trans_b: bool = False, alpha=None, beta=None, X=None, bloom: bool = False):
         self._lib = load()
         self._h = C.c_void_p()
         if semiring is None:
@@ -285,7 +289,7 @@ class DynamicSpGEMM:
         keep: list = []
         ca = self._csr(A, keep)
         cb = self._csr(B, keep) if B is not None else None
-        opt = _Opt(slack_min, slack_div, arena_headroom, keep_transpose, exact_static)
+        opt = _Opt(slack_min, slack_div, arena_headroom, keep_transpose, exact_static, int(bool(bloom)))
         if trans_a or trans_b or alpha is not None or beta is not None or X is not None:
             cx = self._csr(X, keep) if X is not None else None
             pt = semiring == PLUS_TIMES_F64
@@ -363,6 +367,20 @@ class DynamicSpGEMM:
     def read_C(self, stream=None) -> "CsrArrays":
         """C' in canonical CSR (host numpy arrays)."""
         return self._read(self._lib.dspg_read_C, self.info()["m"], stream)
+
+    def read_bloom(self, stream=None) -> "CsrArrays":
+        """C's Bloom filter F (handles built with ``bloom=True``) in canonical
+        CSR: the pattern of C with one uint64 word per entry as ``val``."""
+        s = _stream(stream)
+        nnz = C.c_int64()
+        self._check(self._lib.dspg_read_bloom(self._h, C.byref(nnz), None, None, None, 0, s))
+        n = self.info()["n"]
+        rp = _host_empty(n + 1, np.int64)
+        col = _host_empty(nnz.value, np.int32)
+        words = _host_empty(nnz.value, np.int64).view(np.uint64)
+        self._check(self._lib.dspg_read_bloom(self._h, C.byref(nnz), rp.ctypes.data, col.ctypes.data,
+                                              words.ctypes.data, 0, s))
+        return CsrArrays(n, self.info()["m"], rp, col, words)
 
     def read_A(self, stream=None) -> "CsrArrays":
         """A' in canonical CSR (host numpy arrays), in the caller's coordinates."""
