@@ -423,6 +423,8 @@ def gpu_arm(args):
                           "delta_speedup_vs_row": round(mr / ma, 2), "delta_speedup_vs_static": round(static_med / ma, 2),
                           "rows_touched_delta": rows_alg, "rows_recomputed_row": rows_row, "all_delta": bool(alg_ok)})
 
+    masked = masked_leg(args, flush, stream) if (not args.no_masked and W.name == "stencil") else None
+
     out = None
     if rank == 0:
         cpu = None if args.no_cpu else cpu_baseline(args, W, budget_s=args.cpu_budget)
@@ -469,6 +471,7 @@ def gpu_arm(args):
             "wall_s_timed": round(wall, 3),
             "batch_sweep": sweep,
             "delta_path_insert_only": delta,
+            "masked_general_updates": masked,
             "cpu_baseline": cpu,
         }
     if dist is not None:
@@ -476,6 +479,66 @@ def gpu_arm(args):
         dist.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
+
+
+def masked_leg(args, flush, stream, scale=20):
+    """The entry-level masked recompute (Algorithm 2) beside the row path,
+    on R-MAT scale 20 (edge factor 8, (0.45,0.15,0.15,0.25), symmetrised,
+    C = A A in (+,.) f64): the same edge batches (half insertions of
+    held-out edges, half deletions) applied to a row-path handle and to a
+    handle with the Bloom filter, each apply timed on the device with L2
+    flushed before it; then sampled rows of the two C's compared."""
+    import torch
+    import paper_2202_08808_gb300 as pkg
+    W = Rmat21Workload(scale)
+    A, _ = W.operands()
+    g_row = pkg.DynamicSpGEMM(A)
+    g_msk = pkg.DynamicSpGEMM(A, bloom=True)
+    res = []
+
+    def timed(g, db):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = g.apply_batch(db)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), st
+
+    for n_edges in (100, 1000, 10000):
+        bs = W.batches(5, 600 + n_edges, n_edges)
+        t_row, t_msk, s_row, s_msk = [], [], None, None
+        for k, b in enumerate(bs):
+            db = type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(), torch.from_numpy(b.val).cuda(),
+                         torch.from_numpy(b.op).cuda())
+            tr, s_row = timed(g_row, db)
+            tm, s_msk = timed(g_msk, db)
+            if k > 0:  # the first of each size warms the paths (buffers, graph capture)
+                t_row.append(tr)
+                t_msk.append(tm)
+        mr, mm = statistics.median(t_row), statistics.median(t_msk)
+        res.append({"edges": n_edges, "row_path_ms": round(mr, 4), "masked_path_ms": round(mm, 4),
+                    "masked_speedup_vs_row": round(mr / mm, 2),
+                    "row_path": {"affected_rows": s_row["affected_rows"], "products": s_row["products"],
+                                 "nnz_written": s_row["nnz_written"]},
+                    "masked_path": {"rows_of_c_star": s_msk["affected_rows"], "c_star_entries": s_msk["masked_entries"],
+                                    "kept_a_entries": s_msk["a_entries"], "products": s_msk["products"],
+                                    "nnz_written": s_msk["nnz_written"]}})
+    rows = np.unique(g_row.last_affected())[:2000]
+    ra, rb = g_row.read_rows_C(rows), g_msk.read_rows_C(rows)
+    same = bool(np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1]))
+    scale_v = np.maximum(np.abs(ra[2]), 1e-300) if same else None
+    rel = float(np.max(np.abs(ra[2] - rb[2]) / scale_v)) if same and ra[2].size else None
+    info = g_row.info()
+    out = {"workload": f"R-MAT scale {scale} ef 8 (0.45,0.15,0.15,0.25) symmetrised, C = A A (+,.) f64",
+           "n": info["n"], "nnz_a": info["nnz_a"], "nnz_c": info["nnz_c"],
+           "l2": "flushed before every timed apply", "batches": res,
+           "same_rows_sampled": int(rows.shape[0]), "same_pattern": same, "max_rel_diff": rel}
+    g_row.close()
+    g_msk.close()
+    return out
 
 
 # ------------------------------------------------- batched instances (group)
@@ -1111,6 +1174,8 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-masked", action="store_true",
+                    help="skip the masked-path leg (Algorithm 2 beside the row path on R-MAT scale 20)")
     ap.add_argument("--profile", choices=["step", "static"], default=None,
                     help="run one NVTX-marked step or static recompute for ncu, then exit")
     ap.add_argument("--batch", type=int, default=BATCH)

@@ -80,6 +80,7 @@ struct Ctl {
     long long alg_contrib;     // delta path: contributions formed (products of Eq. 1's two terms)
     long long mask_n;          // masked path: contributions to the pattern of C* formed
     long long mask_kept;       // masked path: entries of A' kept by the Bloom filter (A^R)
+    long long mask_u;          // masked path: entries of C*
     long long pad[1];
 };
 

@@ -1817,48 +1817,48 @@ void bloom_build(dspg_handle *h, cudaStream_t s) {
 void masked_apply(dspg_handle *h, cudaStream_t s) {
     const int64_t nA = h->inA.n, nB = h->b_is_a ? 0 : h->inB.n;
     MaskWs &w = h->mw;
-    for (int iter = 0;; iter++) {
-        begin_batch(h->h_args_dev, h->d_args, h->ctl, s);
-        stage_sort(h, s);
-        if (nA > 0)
-            run_classify(h->wA.job(nA), h->A.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE,
-                         DetectBufs{}, false, false, s, h->num_sms);
-        if (nB > 0)
-            run_classify(h->wB.job(nB), h->B.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE,
-                         DetectBufs{}, false, false, s, h->num_sms);
-        CK(cudaGetLastError());
-        read_ctl(h, s);
-        const unsigned st = h->hctl->status;
-        if (st & ST_INVALID) throw Err(DSPG_ERR_INVALID, "batch entry out of range or with an invalid value/op");
-        if ((st & ST_AB_STAGE) && iter < 4) {
-            if (h->wA.grow_stage(h->hctl->u[0].stage_top + 1024)) h->epoch++;
-            if (h->wB.grow_stage(h->hctl->u[1].stage_top + 1024)) h->epoch++;
-            continue;
-        }
-        if (st) throw Err(DSPG_ERR_CUDA, "masked path: classification failed, status " + std::to_string(st));
-        break;
-    }
-    stage_merge(h, s, -1);
-    stage_commit_ab(h, s);
-    // computePattern reads B' and the transposed pattern of A before this batch
-    const UpdJob ja = h->wA.job(nA);
-    const UpdJob jb = h->b_is_a ? ja : h->wB.job(nB);
     const int cb = bits_for(std::max<int64_t>(h->C.ncols, 2));
     const int rb = bits_for(std::max<int64_t>(h->C.nrows, 2));
     w.ensure_contrib(std::max<int64_t>(int64_t(1) << 16, 16 * (nA + nB)));
-    const bool side_on = h->has_at && nA > 0;
+    // sort, classify, merge and commit A' (and B'), then computePattern,
+    // which reads B' and the transposed pattern of A before this batch; one
+    // read of the control block after it (the later kernels skip on the
+    // status bits, so a failed step is redone from where it stopped)
+    bool restart = true;
     for (int iter = 0;; iter++) {
+        // the jobs point at the staging, which a grown stage moves: built afresh each pass
+        const UpdJob ja = h->wA.job(nA);
+        const UpdJob jb = h->b_is_a ? ja : h->wB.job(nB);
+        if (restart) {
+            begin_batch(h->h_args_dev, h->d_args, h->ctl, s);
+            stage_sort(h, s);
+            if (nA > 0)
+                run_classify(ja, h->A.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, DetectBufs{}, false,
+                             false, s, h->num_sms);
+            if (nB > 0)
+                run_classify(jb, h->B.view(), h->vsize, h->ctl, M_AB & ~ST_AB_STAGE, ST_AB_STAGE, DetectBufs{}, false,
+                             false, s, h->num_sms);
+            stage_merge(h, s, -1);
+            stage_commit_ab(h, s);
+            restart = false;
+        }
         PatJob J{};
         J.xr = ja.row; J.xc = ja.col; J.xk = ja.kind; J.xn = nA;
         J.yr = jb.row; J.yc = jb.col; J.yk = jb.kind; J.yn = h->b_is_a ? nA : nB;
         if (!h->has_at) J.yn = 0;  // B is never updated without the pattern
         J.key = w.key.p; J.bits = w.bits.p; J.cap = w.ccap; J.cb = cb;
-        reset_range(h, &h->ctl->mask_n, sizeof(long long), s);
         pat_contrib(J, h->Bm().view(), h->AT.view(), h->ctl, M_AB, s, h->num_sms);
         CK(cudaGetLastError());
         read_ctl(h, s);
         const unsigned st = h->hctl->status;
-        if ((st & ST_AB_ARENA) && iter < 4) {
+        if (st & ST_INVALID) throw Err(DSPG_ERR_INVALID, "batch entry out of range or with an invalid value/op");
+        if ((st & ST_AB_STAGE) && iter < 6) {
+            if (h->wA.grow_stage(h->hctl->u[0].stage_top + 1024)) h->epoch++;
+            if (h->wB.grow_stage(h->hctl->u[1].stage_top + 1024)) h->epoch++;
+            restart = true;
+            continue;
+        }
+        if ((st & ST_AB_ARENA) && iter < 6) {
             // A's arena ran out in the commit: nothing after it ran; grow it
             // and commit again (the staged rows are still in place)
             regrow(h, h->A, s);
@@ -1868,45 +1868,47 @@ void masked_apply(dspg_handle *h, cudaStream_t s) {
                 reset_range(h, &h->ctl->u[k].reloc, sizeof(long long), s);
             }
             reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+            reset_range(h, &h->ctl->mask_n, sizeof(long long), s);
             stage_commit_ab(h, s);
             continue;
         }
         if ((st & ST_MASK_FULL) && iter < 6) {
             w.ensure_contrib(h->hctl->mask_n);
             reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+            reset_range(h, &h->ctl->mask_n, sizeof(long long), s);
             continue;
         }
         if (st) throw Err(DSPG_ERR_CUDA, "masked path: computePattern failed, status " + std::to_string(st));
         break;
     }
     const int64_t n = h->hctl->mask_n;
-    if (side_on) {
+    if (h->has_at && nA > 0) {
         transpose_front(h, s);
         transpose_commit(h, s);
-        read_ctl(h, s);
     }
-    for (int iter = 0; iter < 8 && (h->hctl->status & (ST_AT_STAGE | ST_AT_ARENA)); iter++) {
-        const unsigned st = h->hctl->status;
-        if ((st & ST_AT_STAGE) && h->wAT.grow_stage(h->hctl->u[2].stage_top + 1024)) h->epoch++;
-        if (st & ST_AT_ARENA) regrow(h, h->AT, s);
-        reset_range(h, &h->ctl->status, sizeof(unsigned), s);
-        reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
-        transpose_front(h, s);
-        transpose_commit(h, s);
-        read_ctl(h, s);
-    }
-    if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "masked path: update failed, status " + std::to_string(h->hctl->status));
-    // C* sorted by (i, j), equal keys merged, in runs of one row
-    int64_t nu = 0, nruns = 0;
+    // C* sorted by (i, j), equal keys merged, in runs of one row; its
+    // counts stay on the device (bounded by n for the grids and buffers)
     MaskJob M{};
     auto job = [&]() {
         M.urow = w.urow.p; M.ucol = w.ucol.p; M.ufs = w.ufs.p;
-        M.run_start = w.run_start.p; M.run_row = w.run_row.p; M.nruns = nruns;
+        M.nu_dev = w.ex.p + n;
+        M.run_start = w.run_start.p; M.run_row = w.run_row.p;
+        M.nruns_dev = w.rex.p + n; M.max_runs = n;
         M.upos = w.upos.p; M.ue = w.ue.p; M.rbits = w.rbits.p;
-        M.kept_run = w.kept_run.p; M.kept_a = w.kept_a.p; M.kcap = w.kcap; M.nkept = 0;
+        M.kept_run = w.kept_run.p; M.kept_a = w.kept_a.p; M.kcap = w.kcap; M.nkept_dev = &h->ctl->mask_kept;
         M.z = (void *)w.z.p; M.h = w.h.p; M.hit = w.hit.p; M.dest = w.dest.p; M.dcap = w.dcap.p;
     };
+    auto product_and_merge = [&]() {
+        job();
+        mask_init_acc(h->sr, M, n, s, h->num_sms);
+        CK(cudaMemsetAsync(w.h.p, 0, sizeof(unsigned long long) * n, s));
+        CK(cudaMemsetAsync(w.hit.p, 0, n, s));
+        mask_product(h->sr, M, h->A.view(), h->Bm().view(), h->ctl, ST_MASK_FULL, s, h->num_sms);
+        mask_plan(M, h->C.view(), h->ctl, ST_MASK_FULL, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
+        mask_splice(h->sr, M, h->C.view(), h->C.fb.p, h->ctl, M_C | ST_MASK_FULL, s, h->num_sms);
+    };
     if (n > 0) {
+        w.ensure_unique(n, h->vsize);
         iota_u32(w.idx.p, n, s, h->num_sms);
         bool alt = false;
         radix_sort_pairs(w.key.p, w.idx.p, w.key_alt.p, w.idx_alt.p, n, rb + cb, w.counts.p, w.scan_tmp.p,
@@ -1915,66 +1917,62 @@ void masked_apply(dspg_handle *h, cudaStream_t s) {
         const uint32_t *I = alt ? w.idx_alt.p : w.idx.p;
         pat_heads(K, n, w.flag.p, s, h->num_sms);
         scan_i32_to_i64(w.flag.p, w.ex.p, n, w.scan_tmp.p, s);
-        nu = read_i64(w.ex.p + n, s);
-        w.ensure_unique(nu, h->vsize);
         job();
+        CK(cudaMemsetAsync(w.rflag.p, 0, sizeof(int32_t) * n, s));
         pat_unique(K, I, w.bits.p, n, w.ex.p, cb, M, w.rflag.p, s, h->num_sms);
-        scan_i32_to_i64(w.rflag.p, w.rex.p, nu, w.uscan.p, s);
-        nruns = read_i64(w.rex.p + nu, s);
-        job();
+        scan_i32_to_i64(w.rflag.p, w.rex.p, n, w.uscan.p, s);
         CK(cudaMemsetAsync(h->wc.bmR.p, 0, sizeof(uint32_t) * h->wc.bmR.n, s));
-        pat_runs(M, w.rflag.p, w.rex.p, nu, h->wc.bmR.p, s, h->num_sms);
-        CK(cudaMemcpyAsync(w.run_start.p + nruns, &nu, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        pat_runs(M, w.rflag.p, w.rex.p, n, h->wc.bmR.p, s, h->num_sms);
         // E and R
-        CK(cudaMemsetAsync(w.upos.p, 0xff, sizeof(int32_t) * nu, s));
-        CK(cudaMemsetAsync(w.ue.p, 0, sizeof(unsigned long long) * nu, s));
+        CK(cudaMemsetAsync(w.upos.p, 0xff, sizeof(int32_t) * n, s));
+        CK(cudaMemsetAsync(w.ue.p, 0, sizeof(unsigned long long) * n, s));
         mask_scan(M, h->C.view(), h->C.fb.p, s, h->num_sms);
-        // A^R
-        w.ensure_kept(std::max<int64_t>(int64_t(1) << 16, 4 * nu));
-        for (int iter = 0;; iter++) {
-            job();
-            reset_range(h, &h->ctl->mask_kept, sizeof(long long), s);
-            mask_keep(M, h->A.view(), h->ctl, s, h->num_sms);
-            CK(cudaGetLastError());
-            read_ctl(h, s);
-            if ((h->hctl->status & ST_MASK_FULL) && iter < 6) {
-                w.ensure_kept(h->hctl->mask_kept);
-                reset_range(h, &h->ctl->status, sizeof(unsigned), s);
-                continue;
-            }
-            break;
-        }
-        if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "masked path: A^R failed, status " + std::to_string(h->hctl->status));
+        // A^R, the masked product, the merge into C and F
+        w.ensure_kept(std::max<int64_t>(int64_t(1) << 16, 4 * n));
         job();
-        M.nkept = h->hctl->mask_kept;
-        // the masked product
-        mask_init_acc(h->sr, M, nu, s, h->num_sms);
-        CK(cudaMemsetAsync(w.h.p, 0, sizeof(unsigned long long) * nu, s));
-        CK(cudaMemsetAsync(w.hit.p, 0, nu, s));
-        mask_product(h->sr, M, h->A.view(), h->Bm().view(), h->ctl, s, h->num_sms);
-        // the merge into C and F, growing C's arena until the moved rows fit
-        for (int iter = 0;; iter++) {
-            mask_plan(M, h->C.view(), h->ctl, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
-            CK(cudaGetLastError());
-            read_ctl(h, s);
-            if ((h->hctl->status & ST_C_ARENA) && iter < 4) {
-                regrow(h, h->C, s);  // the plan wrote nothing but places: plan again in the new arena
-                reset_range(h, &h->ctl->status, sizeof(unsigned), s);
-                reset_range(h, &h->ctl->c_reloc, sizeof(long long), s);
-                continue;
-            }
-            break;
-        }
-        if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "masked path: C's arena cannot take the merge");
-        mask_splice(h->sr, M, h->C.view(), h->C.fb.p, h->ctl, M_C, s, h->num_sms);
+        mask_keep(M, h->A.view(), h->ctl, s, h->num_sms);
+        product_and_merge();
     }
     // the rows of C*, for the statistics and dspg_last_affected
+    if (n > 0) CK(cudaMemcpyAsync(&h->ctl->mask_u, w.ex.p + n, sizeof(long long), cudaMemcpyDeviceToDevice, s));
     alg_collect(h, h->wc.bmR.p, s);
     CK(cudaGetLastError());
     read_ctl(h, s);
-    if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "masked path: merge failed, status " + std::to_string(h->hctl->status));
-    h->hctl->a_entries = M.nkept;
-    h->last_masked = nu;
+    // what overflowed: the kept list (nothing after it ran), C's arena (the
+    // plan wrote places only), the transposed pattern's staging or arena
+    for (int iter = 0; iter < 8 && h->hctl->status; iter++) {
+        const unsigned st = h->hctl->status;
+        if (st & ST_MASK_FULL) {
+            w.ensure_kept(h->hctl->mask_kept);
+            reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+            reset_range(h, &h->ctl->mask_kept, sizeof(long long), s);
+            reset_range(h, &h->ctl->c_reloc, sizeof(long long), s);
+            job();
+            mask_keep(M, h->A.view(), h->ctl, s, h->num_sms);
+            product_and_merge();
+        } else if (st & ST_C_ARENA) {
+            regrow(h, h->C, s);  // the plan wrote nothing but places: plan again in the new arena
+            reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+            reset_range(h, &h->ctl->c_reloc, sizeof(long long), s);
+            job();
+            mask_plan(M, h->C.view(), h->ctl, ST_MASK_FULL, h->opt.slack_min, h->opt.slack_div, s, h->num_sms);
+            mask_splice(h->sr, M, h->C.view(), h->C.fb.p, h->ctl, M_C | ST_MASK_FULL, s, h->num_sms);
+        } else if (st & (ST_AT_STAGE | ST_AT_ARENA)) {
+            if ((st & ST_AT_STAGE) && h->wAT.grow_stage(h->hctl->u[2].stage_top + 1024)) h->epoch++;
+            if (st & ST_AT_ARENA) regrow(h, h->AT, s);
+            reset_range(h, &h->ctl->status, sizeof(unsigned), s);
+            reset_range(h, &h->ctl->u[2], sizeof(UpdCtl), s);
+            transpose_front(h, s);
+            transpose_commit(h, s);
+        } else {
+            break;
+        }
+        CK(cudaGetLastError());
+        read_ctl(h, s);
+    }
+    if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "masked path: update failed, status " + std::to_string(h->hctl->status));
+    h->hctl->a_entries = h->hctl->mask_kept;
+    h->last_masked = h->hctl->mask_u;
 }
 
 // Captures what body() enqueues on cs into an executable graph; the number

@@ -125,15 +125,18 @@ struct PatJob {
 struct MaskJob {
     int32_t *urow, *ucol;
     unsigned long long *ufs;  // F*
-    int64_t *run_start;       // nruns + 1
+    const int64_t *nu_dev;    // |C*| (device)
+    int64_t *run_start;       // runs + 1
     int32_t *run_row;
-    int64_t nruns;
+    const int64_t *nruns_dev; // runs (device)
+    int64_t max_runs;         // a bound on the runs (grid sizes)
     int32_t *upos;            // place of the entry in its row of C, -1 if C has none
     unsigned long long *ue;   // F there (0 if none)
     unsigned long long *rbits;  // R_i per run
     int32_t *kept_run;        // A^R: run and A' entry of each kept entry
     int64_t *kept_a;
-    int64_t kcap, nkept;
+    int64_t kcap;
+    const long long *nkept_dev;  // entries kept (device; beyond kcap the list overflowed)
     void *z;                  // Z: the masked product's values
     unsigned long long *h;    // H: its Bloom words
     uint8_t *hit;             // 1 where some product reached the entry
@@ -152,15 +155,15 @@ void iota_u32(uint32_t *v, int64_t n, cudaStream_t s, int num_sms);
 void pat_heads(const uint64_t *K, int64_t n, int32_t *flag, cudaStream_t s, int num_sms);
 void pat_unique(const uint64_t *K, const uint32_t *I, const uint64_t *bits, int64_t n, const int64_t *ex, int cb,
                 const MaskJob &M, int32_t *rflag, cudaStream_t s, int num_sms);
-void pat_runs(const MaskJob &M, const int32_t *rflag, const int64_t *rex, int64_t nu, uint32_t *bm, cudaStream_t s,
+void pat_runs(const MaskJob &M, const int32_t *rflag, const int64_t *rex, int64_t max_u, uint32_t *bm, cudaStream_t s,
               int num_sms);
 void mask_scan(const MaskJob &M, const MatView &C, const unsigned long long *F, cudaStream_t s, int num_sms);
 void mask_keep(const MaskJob &M, const MatView &A, Ctl *ctl, cudaStream_t s, int num_sms);
 void mask_init_acc(int sr, const MaskJob &M, int64_t nu, cudaStream_t s, int num_sms);
-void mask_product(int sr, const MaskJob &M, const MatView &A, const MatView &B, Ctl *ctl, cudaStream_t s,
-                  int num_sms);
-void mask_plan(const MaskJob &M, const MatView &C, Ctl *ctl, int slack_min, int slack_div, cudaStream_t s,
-               int num_sms);
+void mask_product(int sr, const MaskJob &M, const MatView &A, const MatView &B, Ctl *ctl, unsigned mask,
+                  cudaStream_t s, int num_sms);
+void mask_plan(const MaskJob &M, const MatView &C, Ctl *ctl, unsigned mask, int slack_min, int slack_div,
+               cudaStream_t s, int num_sms);
 void mask_splice(int sr, const MaskJob &M, const MatView &C, unsigned long long *F, Ctl *ctl, unsigned mask,
                  cudaStream_t s, int num_sms);
 

@@ -243,9 +243,12 @@ __global__ void k_pat_unique(const uint64_t *K, const uint32_t *I, const uint64_
     }
 }
 
-// Runs of C* per row: start and row of run r = rex[u]; the row's bit in bm.
-__global__ void k_pat_runs(MaskJob M, const int32_t *rflag, const int64_t *rex, int64_t nu, uint32_t *bm) {
+// Runs of C* per row: start and row of run r = rex[u]; the row's bit in
+// bm; and the end of the last run.
+__global__ void k_pat_runs(MaskJob M, const int32_t *rflag, const int64_t *rex, uint32_t *bm) {
     pdl_begin();
+    const int64_t nu = *M.nu_dev;
+    if (blockIdx.x == 0 && threadIdx.x == 0) M.run_start[*M.nruns_dev] = nu;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
         if (!rflag[u]) continue;
         const int64_t r = rex[u];
@@ -265,7 +268,8 @@ __global__ void k_mask_scan(MaskJob M, MatView C, const unsigned long long *F) {
     pdl_begin();
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < M.nruns; r += nwarps) {
+    const long long nr = *M.nruns_dev;
+    for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nr; r += nwarps) {
         const int64_t u0 = M.run_start[r], u1 = M.run_start[r + 1];
         const int32_t i = M.run_row[r];
         const int64_t coff = C.off[i];
@@ -292,7 +296,8 @@ __global__ void k_mask_keep(MaskJob M, MatView A, Ctl *ctl) {
     pdl_begin();
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < M.nruns; r += nwarps) {
+    const long long nr = *M.nruns_dev;
+    for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nr; r += nwarps) {
         const int32_t i = M.run_row[r];
         const unsigned long long rb = M.rbits[r];
         const int64_t aoff = A.off[i];
@@ -333,16 +338,18 @@ struct MSr<SR_MP> {
 // A warp per kept entry (i, k, a): the products with row k of B' whose
 // column is in row i's run of C*.
 template <int SR>
-__global__ void k_mask_product(MaskJob M, MatView A, MatView B, Ctl *ctl) {
+__global__ void k_mask_product(MaskJob M, MatView A, MatView B, Ctl *ctl, unsigned mask) {
     pdl_begin();
     using T = typename MSr<SR>::T;
+    if (failed(ctl, mask)) return;  // no barrier or shuffle below
     const int lane = threadIdx.x & 31;
+    const long long nk = *M.nkept_dev < M.kcap ? *M.nkept_dev : M.kcap;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const T *Av = (const T *)A.val;
     const T *Bv = (const T *)B.val;
     T *z = (T *)M.z;
     long long prods = 0;
-    for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < M.nkept; t += nwarps) {
+    for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nk; t += nwarps) {
         const int32_t r = M.kept_run[t];
         const int64_t ae = M.kept_a[t];
         const int32_t k = A.col[ae];
@@ -370,11 +377,13 @@ __global__ void k_mask_product(MaskJob M, MatView A, MatView B, Ctl *ctl) {
 // A warp per run: the row's length after the merge (deleted entries out,
 // new entries in); a row that outgrows its capacity gets a place at the
 // arena tail (nothing is written when the arena is exhausted).
-__global__ void k_mask_plan(MaskJob M, MatView C, Ctl *ctl, int slack_min, int slack_div) {
+__global__ void k_mask_plan(MaskJob M, MatView C, Ctl *ctl, unsigned mask, int slack_min, int slack_div) {
     pdl_begin();
+    if (__any_sync(0xffffffffu, failed(ctl, mask))) return;  // a warp leaves as a whole
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < M.nruns; r += nwarps) {
+    const long long nr = *M.nruns_dev;
+    for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nr; r += nwarps) {
         const int64_t u0 = M.run_start[r], u1 = M.run_start[r + 1];
         int ndel = 0, nins = 0;
         for (int64_t u = u0 + lane; u < u1; u += 32) {
@@ -415,7 +424,8 @@ __global__ void k_mask_splice(MaskJob M, MatView C, unsigned long long *F, Ctl *
     T *Cv = (T *)C.val;
     const T *z = (const T *)M.z;
     long long written = 0;
-    for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < M.nruns; r += nwarps) {
+    const long long nr = *M.nruns_dev;
+    for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nr; r += nwarps) {
         const int64_t u0 = M.run_start[r], u1 = M.run_start[r + 1];
         const int32_t i = M.run_row[r];
         const int L = C.len[i];
@@ -551,27 +561,29 @@ void pat_unique(const uint64_t *K, const uint32_t *I, const uint64_t *bits, int6
     launch_k(k_pat_unique, grid_of(n, 256, num_sms), 256, 0, s, K, I, bits, n, ex, cb, M, rflag);
 }
 
-void pat_runs(const MaskJob &M, const int32_t *rflag, const int64_t *rex, int64_t nu, uint32_t *bm, cudaStream_t s,
+void pat_runs(const MaskJob &M, const int32_t *rflag, const int64_t *rex, int64_t max_u, uint32_t *bm, cudaStream_t s,
               int num_sms) {
-    if (nu <= 0) return;
-    launch_k(k_pat_runs, grid_of(nu, 256, num_sms), 256, 0, s, M, rflag, rex, nu, bm);
+    if (max_u <= 0) return;
+    launch_k(k_pat_runs, grid_of(max_u, 256, num_sms), 256, 0, s, M, rflag, rex, bm);
 }
 
 void mask_scan(const MaskJob &M, const MatView &C, const unsigned long long *F, cudaStream_t s, int num_sms) {
-    if (M.nruns <= 0) return;
-    launch_k(k_mask_scan, grid_of(M.nruns, 8, num_sms), 256, 0, s, M, C, F);
+    if (M.max_runs <= 0) return;
+    launch_k(k_mask_scan, grid_of(M.max_runs, 8, num_sms), 256, 0, s, M, C, F);
 }
 
 void mask_keep(const MaskJob &M, const MatView &A, Ctl *ctl, cudaStream_t s, int num_sms) {
-    if (M.nruns <= 0) return;
-    launch_k(k_mask_keep, grid_of(M.nruns, 8, num_sms), 256, 0, s, M, A, ctl);
+    if (M.max_runs <= 0) return;
+    launch_k(k_mask_keep, grid_of(M.max_runs, 8, num_sms), 256, 0, s, M, A, ctl);
 }
 
-void mask_product(int sr, const MaskJob &M, const MatView &A, const MatView &B, Ctl *ctl, cudaStream_t s,
-                  int num_sms) {
-    if (M.nkept <= 0) return;
-    if (sr == SR_PT) launch_k(k_mask_product<SR_PT>, grid_of(M.nkept, 8, num_sms), 256, 0, s, M, A, B, ctl);
-    else launch_k(k_mask_product<SR_MP>, grid_of(M.nkept, 8, num_sms), 256, 0, s, M, A, B, ctl);
+void mask_product(int sr, const MaskJob &M, const MatView &A, const MatView &B, Ctl *ctl, unsigned mask,
+                  cudaStream_t s, int num_sms) {
+    if (M.kcap <= 0) return;
+    if (sr == SR_PT)
+        launch_k(k_mask_product<SR_PT>, grid_of(M.kcap, 8, num_sms), 256, 0, s, M, A, B, ctl, mask);
+    else
+        launch_k(k_mask_product<SR_MP>, grid_of(M.kcap, 8, num_sms), 256, 0, s, M, A, B, ctl, mask);
 }
 
 void mask_init_acc(int sr, const MaskJob &M, int64_t nu, cudaStream_t s, int num_sms) {
@@ -580,17 +592,17 @@ void mask_init_acc(int sr, const MaskJob &M, int64_t nu, cudaStream_t s, int num
     else launch_k(k_fill_val<int32_t>, grid_of(nu, 256, num_sms), 256, 0, s, (int32_t *)M.z, nu, MP_INF);
 }
 
-void mask_plan(const MaskJob &M, const MatView &C, Ctl *ctl, int slack_min, int slack_div, cudaStream_t s,
-               int num_sms) {
-    if (M.nruns <= 0) return;
-    launch_k(k_mask_plan, grid_of(M.nruns, 8, num_sms), 256, 0, s, M, C, ctl, slack_min, slack_div);
+void mask_plan(const MaskJob &M, const MatView &C, Ctl *ctl, unsigned mask, int slack_min, int slack_div,
+               cudaStream_t s, int num_sms) {
+    if (M.max_runs <= 0) return;
+    launch_k(k_mask_plan, grid_of(M.max_runs, 8, num_sms), 256, 0, s, M, C, ctl, mask, slack_min, slack_div);
 }
 
 void mask_splice(int sr, const MaskJob &M, const MatView &C, unsigned long long *F, Ctl *ctl, unsigned mask,
                  cudaStream_t s, int num_sms) {
-    if (M.nruns <= 0) return;
-    if (sr == SR_PT) launch_k(k_mask_splice<SR_PT>, grid_of(M.nruns, 8, num_sms), 256, 0, s, M, C, F, ctl, mask);
-    else launch_k(k_mask_splice<SR_MP>, grid_of(M.nruns, 8, num_sms), 256, 0, s, M, C, F, ctl, mask);
+    if (M.max_runs <= 0) return;
+    if (sr == SR_PT) launch_k(k_mask_splice<SR_PT>, grid_of(M.max_runs, 8, num_sms), 256, 0, s, M, C, F, ctl, mask);
+    else launch_k(k_mask_splice<SR_MP>, grid_of(M.max_runs, 8, num_sms), 256, 0, s, M, C, F, ctl, mask);
 }
 
 }  // namespace dspg

@@ -210,3 +210,26 @@ def test_masked_handle_refuses_the_row_path_calls(dspg):
     _bloom_matches(g, Ao, Ao, "after refusals")
     g.close()
     plain.close()
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_masked_staging_growth(dspg, sr):
+    """A batch whose rebuilt rows of A need more staging than a batch of its
+    size starts with (100 rows of 1,500 entries each): the merge is redone
+    with grown staging, and the result matches as before."""
+    rng = np.random.default_rng(61)
+    from workloads import CSR
+    rows = []
+    for i in range(200):
+        k = 1500 if i < 100 else 5
+        rows.append({int(c): (float(rng.random()) if sr == PLUS_TIMES_F64 else int(rng.integers(1, 101)))
+                     for c in rng.choice(3000, size=k, replace=False)})
+    A = _csr_from_rows(rows, 3000, sr)
+    B = random_csr(3000, 50, 3, 62, sr, empty_frac=0.0)
+    g = dspg.DynamicSpGEMM(A, B, bloom=True)
+    n = 300
+    ops = rng.integers(0, 3, n).astype(np.uint8)
+    vals = rng.random(n) if sr == PLUS_TIMES_F64 else rng.integers(1, 101, n).astype(np.int32)
+    b = Batch(rng.integers(0, 100, n).astype(np.int32), rng.integers(0, 3000, n).astype(np.int32), vals, ops)
+    _run_sequence(dspg, g, om.rows_of(A), om.rows_of(B), [b], [None], sr, False, 200, 50)
+    g.close()
