@@ -341,9 +341,10 @@ def gpu_arm(args):
     # the batch, apply, read back the affected row set and its rows of C
     e2e_ms, h2d, d2h = [], 0, 0
     pinned = []
-    # (the first, untimed, is the warm-up: it also fills the pinned host
+    # (the first W, untimed, are the warm-up: they also fill the pinned host
     # allocator that the read-back arrays come from)
-    for b in W.batches(max(3, min(args.steps, 10)) + 1, 5000 * (rank + 1)):
+    n_warm = max(3, args.warmup)
+    for b in W.batches(max(3, min(args.steps, 10)) + n_warm, 5000 * (rank + 1)):
         pinned.append(type(b)(torch.from_numpy(b.row).pin_memory(), torch.from_numpy(b.col).pin_memory(),
                               torch.from_numpy(b.val).pin_memory(), torch.from_numpy(b.op).pin_memory()))
     for k, b in enumerate(pinned):
@@ -351,10 +352,9 @@ def gpu_arm(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g.apply_batch(b)
-        rows = g.last_affected()
-        rp, col, val = g.read_rows_C(rows)
+        rows, rp, col, val = g.read_affected()  # R and its rows of C' in one call
         t1 = time.perf_counter()
-        if k > 0:
+        if k >= n_warm:
             e2e_ms.append((t1 - t0) * 1e3)
         h2d = len(b.row) * (4 + 4 + vsize + 1)
         d2h = rows.nbytes + rp.nbytes + col.nbytes + val.nbytes + 13 * 8

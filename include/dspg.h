@@ -262,6 +262,19 @@ dspg_status dspg_read_A(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32
 dspg_status dspg_read_rows_C(dspg_handle *h, const int32_t *rows, int64_t nrows, int64_t *nnz_out,
                              int64_t *rowptr, int32_t *col, void *val, int on_device, void *stream);
 
+/* The rows of C the last batch affected (the set dspg_last_affected lists)
+ * and their entries, in one call: R ascending into rows, and the rows of C'
+ * in canonical CSR (rowptr n+1 entries, columns ascending per row) into
+ * rowptr, col and val, host or device memory per on_device.  *nrows_out and
+ * *nnz_out receive the sizes; with rows == NULL nothing else is written.
+ * Buffers smaller than rows_cap < n or nnz_cap < nnz: DSPG_ERR_INVALID with
+ * the sizes written (the caller grows and calls again).  Synchronises the
+ * stream twice.  Not for handles with alpha, beta or X (DSPG_ERR_STATE).
+ * Not part of the paper: the read a server makes after each batch. */
+dspg_status dspg_read_affected_C(dspg_handle *h, int64_t rows_cap, int64_t nnz_cap, int64_t *nrows_out,
+                                 int64_t *nnz_out, int32_t *rows, int64_t *rowptr, int32_t *col, void *val,
+                                 int on_device, void *stream);
+
 /* The affected row set R of the last apply_batch, ascending, into rows
  * (room for *count rows; with rows == NULL only *count is written). */
 dspg_status dspg_last_affected(dspg_handle *h, int64_t *count, int32_t *rows, int on_device, void *stream);

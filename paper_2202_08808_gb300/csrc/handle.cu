@@ -365,7 +365,7 @@ struct dspg_handle {
     // buffer allocates for the call instead of holding that memory
     struct ReadWs {
         DBuf<int32_t> rows, lens, c, r;
-        DBuf<int64_t> rp, scan, listed, st, so;
+        DBuf<int64_t> rp, scan, listed, st, so, chunk_cnt, chunk_ex, chunk_tmp;
         DBuf<unsigned> n_listed;
         DBuf<char> v;
         DBuf<uint64_t> k0, k1;
@@ -1235,52 +1235,11 @@ void load_operand(dspg_handle *h, DevMat &M, const dspg_csr *m, bool trans, cuda
     make_slack(h, M, m->ncols, m->nrows, h->vsize, trp.p, tlen.p, tcol.p, tval.p, s);
 }
 
-int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, int64_t *rowptr, int32_t *col,
-                 void *val, int on_device, cudaStream_t s, bool bloom = false) {
-    // with bloom the values read are C's Bloom words (8 bytes each) instead
-    MatView V = M.view();
-    int vs = M.vsize;
-    if (bloom) {
-        V.val = (void *)M.fb.p;
-        vs = 8;
-    }
-    DBuf<int32_t> rows_l;
-    const int32_t *rows = nullptr;
-    int64_t n = M.nrows;
-    if (rows_in) n = nr;
-    // host rows of C that the last read of this generation of C listed too:
-    // their row pointers are still in the kept buffer
-    dspg_handle::ReadKey &key = h->rd_key;
-    const bool keyed = rows_in && !on_device && &M == &h->C;
-    const bool hit = keyed && key.valid && key.serial == h->c_serial && (int64_t)key.rows.size() == n &&
-                     (n == 0 || std::memcmp(key.rows.data(), rows_in, sizeof(int32_t) * (size_t)n) == 0);
-    key.valid = false;  // the kept row list and row pointers are rewritten below unless this is a hit
-    DBuf<int64_t> rp_l;
-    int64_t *rp;
-    int64_t nnz;
-    if (hit) {
-        rows = h->rd.rows.p;
-        rp = h->rd.rp.p;
-        nnz = key.nnz;
-    } else {
-        if (rows_in) {
-            if (on_device) rows = rows_in;
-            else {
-                int32_t *rows_d = read_scratch(h->rd.rows, rows_l, n);
-                if (n > 0) CK(cudaMemcpyAsync(rows_d, rows_in, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-                rows = rows_d;
-            }
-        }
-        rp = read_scratch(h->rd.rp, rp_l, n + 1);
-        nnz = mat_rowptr(h, M, rows, n, rp, s);
-    }
-    if (keyed && rows == h->rd.rows.p && rp == h->rd.rp.p) {
-        if (!hit) key.rows.assign(rows_in, rows_in + n);
-        key.serial = h->c_serial;
-        key.nnz = nnz;
-        key.valid = true;
-    }
-    if (!rowptr) return nnz;
+// The fill of a read: rows (device, n of them; NULL = all) of M whose
+// row pointers rp (device, n + 1) and total nnz are known, gathered, sorted
+// by column and copied out (V, vs: the view and value size read).
+void fill_rows_out(dspg_handle *h, DevMat &M, const MatView &V, int vs, const int32_t *rows, int64_t n, int64_t *rp,
+                   int64_t nnz, int64_t *rowptr, int32_t *col, void *val, int on_device, cudaStream_t s) {
     // rows too long to sort in shared memory are listed, then sorted together
     const int64_t list_cap = nnz / 16385 + 1;
     DBuf<int64_t> listed_l;
@@ -1356,6 +1315,55 @@ int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, 
         }
         CK(cudaStreamSynchronize(s));
     }
+}
+
+int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, int64_t *rowptr, int32_t *col,
+                 void *val, int on_device, cudaStream_t s, bool bloom = false) {
+    // with bloom the values read are C's Bloom words (8 bytes each) instead
+    MatView V = M.view();
+    int vs = M.vsize;
+    if (bloom) {
+        V.val = (void *)M.fb.p;
+        vs = 8;
+    }
+    DBuf<int32_t> rows_l;
+    const int32_t *rows = nullptr;
+    int64_t n = M.nrows;
+    if (rows_in) n = nr;
+    // host rows of C that the last read of this generation of C listed too:
+    // their row pointers are still in the kept buffer
+    dspg_handle::ReadKey &key = h->rd_key;
+    const bool keyed = rows_in && !on_device && &M == &h->C;
+    const bool hit = keyed && key.valid && key.serial == h->c_serial && (int64_t)key.rows.size() == n &&
+                     (n == 0 || std::memcmp(key.rows.data(), rows_in, sizeof(int32_t) * (size_t)n) == 0);
+    key.valid = false;  // the kept row list and row pointers are rewritten below unless this is a hit
+    DBuf<int64_t> rp_l;
+    int64_t *rp;
+    int64_t nnz;
+    if (hit) {
+        rows = h->rd.rows.p;
+        rp = h->rd.rp.p;
+        nnz = key.nnz;
+    } else {
+        if (rows_in) {
+            if (on_device) rows = rows_in;
+            else {
+                int32_t *rows_d = read_scratch(h->rd.rows, rows_l, n);
+                if (n > 0) CK(cudaMemcpyAsync(rows_d, rows_in, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+                rows = rows_d;
+            }
+        }
+        rp = read_scratch(h->rd.rp, rp_l, n + 1);
+        nnz = mat_rowptr(h, M, rows, n, rp, s);
+    }
+    if (keyed && rows == h->rd.rows.p && rp == h->rd.rp.p) {
+        if (!hit) key.rows.assign(rows_in, rows_in + n);
+        key.serial = h->c_serial;
+        key.nnz = nnz;
+        key.valid = true;
+    }
+    if (!rowptr) return nnz;
+    fill_rows_out(h, M, V, vs, rows, n, rp, nnz, rowptr, col, val, on_device, s);
     return nnz;
 }
 
@@ -2280,6 +2288,66 @@ dspg_status dspg_read_rows_C(dspg_handle *h, const int32_t *rows, int64_t nrows,
         const int32_t *rr = rows ? rows : (const int32_t *)h->wc.iota.p;
         *nnz_out = h->form ? read_form(h, rr, nrows, rowptr, col, val, on_device, (cudaStream_t)stream)
                            : read_mat(h, h->C, rr, nrows, rowptr, col, val, on_device, (cudaStream_t)stream);
+        return DSPG_OK;
+    } catch (const Err &e) {
+        return fail(h, e);
+    }
+}
+
+dspg_status dspg_read_affected_C(dspg_handle *h, int64_t rows_cap, int64_t nnz_cap, int64_t *nrows_out,
+                                 int64_t *nnz_out, int32_t *rows, int64_t *rowptr, int32_t *col, void *val,
+                                 int on_device, void *stream) {
+    if (!h || !nrows_out || !nnz_out) return DSPG_ERR_INVALID;
+    if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
+    if (h->form) return fail(h, Err(DSPG_ERR_STATE, "a handle with alpha, beta or X reads its rows by dspg_read_rows_C"));
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        const int64_t n = h->last_nR;
+        dspg_handle::ReadWs &w = h->rd;
+        w.r.reserve(std::max<int64_t>(n, 1));
+        DBuf<int64_t> rp_l;
+        int64_t *rp = read_scratch(w.rp, rp_l, n + 1);
+        // R in row order on the device, from the chunk table of its collection
+        const int64_t nch = ((h->A.nrows + 31) / 32 + 255) / 256;
+        w.chunk_cnt.reserve(nch + 1);
+        w.chunk_ex.reserve(nch + 1);
+        w.chunk_tmp.reserve(scan_tmp_entries(nch + 1) + 1);
+        rows_in_order(h->wc.R.p, h->wc.rchunk.p, nch, n, w.chunk_cnt.p, w.chunk_ex.p, w.chunk_tmp.p, w.r.p, s);
+        DBuf<int64_t> scan_l;
+        int64_t *lens_scan = read_scratch(w.scan, scan_l, scan_tmp_entries(n) + 1);
+        DBuf<int32_t> lens_l;
+        int32_t *lens = read_scratch(w.lens, lens_l, n);
+        lens_of_rows(w.r.p, n, h->C.len.p, lens, s);
+        scan_i32_to_i64(lens, rp, n, lens_scan, s);
+        int64_t tot[2] = {0, 0};
+        CK(cudaMemcpyAsync(&tot[0], w.chunk_ex.p + nch, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&tot[1], rp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (tot[0] != n) {
+            // R not from one collection: sort it on the device, size it again
+            CK(cudaMemcpyAsync(w.r.p, h->wc.R.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+            w.k0.reserve(n); w.k1.reserve(n); w.i0.reserve(n); w.i1.reserve(n);
+            int64_t cnt;
+            sort_tmp_sizes(n, &cnt);
+            w.counts.reserve(cnt);
+            w.so.reserve(cnt + 1);
+            w.st.reserve(scan_tmp_entries(cnt) + 1);
+            sort_i32_values(w.r.p, n, bits_for(h->A.nrows), w.k0.p, w.k1.p, w.i0.p, w.i1.p, w.counts.p, w.st.p,
+                            w.so.p, s);
+            tot[1] = mat_rowptr(h, h->C, w.r.p, n, rp, s);
+        }
+        const int64_t nnz = tot[1];
+        *nrows_out = n;
+        *nnz_out = nnz;
+        if (!rows) return DSPG_OK;
+        if (rows_cap < n || nnz_cap < nnz)
+            throw Err(DSPG_ERR_INVALID, "read_affected_C: buffers too small (need " + std::to_string(n) + " rows, " +
+                                            std::to_string(nnz) + " entries)");
+        if (n > 0)
+            CK(cudaMemcpyAsync(rows, w.r.p, sizeof(int32_t) * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               s));
+        fill_rows_out(h, h->C, h->C.view(), h->vsize, w.r.p, n, rp, nnz, rowptr, col, val, on_device, s);
+        if (on_device) CK(cudaStreamSynchronize(s));
         return DSPG_OK;
     } catch (const Err &e) {
         return fail(h, e);

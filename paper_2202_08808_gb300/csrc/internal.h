@@ -289,6 +289,12 @@ struct SortScratch {  // for `total` entries: keys, indices (two each), radix co
 void sort_listed_rows(const int64_t *rowptr, const int64_t *listed, const int64_t *pre, int nl, int64_t total,
                       int cb, int32_t *col, void *val, int vsize, const SortScratch &w, cudaStream_t s, int num_sms);
 void lens_of_rows(const int32_t *rows, int64_t n, const int32_t *len, int32_t *out, cudaStream_t s);
+// R (n rows, as collected: ascending within each 8192-row chunk, chunk c's
+// rows at chunk[2c] with chunk[2c+1] of them) into out in row order; cnt and
+// ex (nch + 1) and tmp (scan_tmp_entries(nch) + 1) are scratch, and ex[nch]
+// is the number of rows placed (n when R came from one collection).
+void rows_in_order(const int32_t *R, const long long *chunk, int64_t nch, int64_t n, int64_t *cnt, int64_t *ex,
+                   int64_t *tmp, int32_t *out, cudaStream_t s);
 void validate_rowptr(int64_t nrows, int64_t nnz, const int64_t *rowptr, unsigned *bad, cudaStream_t s);
 void validate_csr_entries(int64_t nrows, int64_t ncols, const int64_t *rowptr, const int32_t *col, const void *val,
                           int sr, unsigned *bad, cudaStream_t s);

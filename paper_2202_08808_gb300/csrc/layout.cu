@@ -82,6 +82,35 @@ void lens_of_rows(const int32_t *rows, int64_t n, const int32_t *len, int32_t *o
     if (n > 0) launch_k(k_lens_of_rows, blocks_for(n, 256, 8192), 256, 0, s, rows, n, len, out);
 }
 
+// R in row order from its collection: each chunk of 8192 rows wrote its
+// (ascending) rows at chunk[2c] in R, chunk[2c+1] of them, so laying the
+// chunks end to end in chunk order sorts R.  k_chunk_counts lists the
+// counts for a scan, k_chunk_copy moves each chunk (a block per chunk).
+__global__ void k_chunk_counts(const long long *chunk, int64_t nch, int64_t *cnt) {
+    pdl_begin();
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += (int64_t)gridDim.x * blockDim.x)
+        cnt[c] = chunk[2 * c + 1];
+}
+
+__global__ void k_chunk_copy(const int32_t *R, const long long *chunk, int64_t nch, const int64_t *ex, int64_t n,
+                             int32_t *out) {
+    pdl_begin();
+    for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        const long long b = chunk[2 * c], k = chunk[2 * c + 1];
+        const int64_t o = ex[c];
+        if (k <= 0 || b < 0 || b + k > n || o + k > n) continue;  // not one collection: the caller checks ex[nch]
+        for (long long t = threadIdx.x; t < k; t += blockDim.x) out[o + t] = R[b + t];
+    }
+}
+
+void rows_in_order(const int32_t *R, const long long *chunk, int64_t nch, int64_t n, int64_t *cnt, int64_t *ex,
+                   int64_t *tmp, int32_t *out, cudaStream_t s) {
+    if (nch <= 0) return;
+    launch_k(k_chunk_counts, blocks_for(nch, 256, 1024), 256, 0, s, chunk, nch, cnt);
+    scan_i64(cnt, ex, nch, tmp, s);
+    launch_k(k_chunk_copy, (unsigned)std::min<int64_t>(nch, 8192), 256, 0, s, R, chunk, nch, ex, n, out);
+}
+
 template <typename T>
 __global__ void k_copy_rows(const int32_t *rows, int64_t n, const int64_t *src_off, const int32_t *len,
                             const int32_t *src_col, const T *src_val, const int64_t *dst_off, int32_t *dst_col,

@@ -101,6 +101,8 @@ def load():
             f.argtypes = [p, C.POINTER(i64), p, p, p, i32, p]
         lib.dspg_read_rows_C.restype = i32
         lib.dspg_read_rows_C.argtypes = [p, p, i64, C.POINTER(i64), p, p, p, i32, p]
+        lib.dspg_read_affected_C.restype = i32
+        lib.dspg_read_affected_C.argtypes = [p, i64, i64, C.POINTER(i64), C.POINTER(i64), p, p, p, p, i32, p]
         lib.dspg_last_affected.restype = i32
         lib.dspg_last_affected.argtypes = [p, C.POINTER(i64), p, i32, p]
         lib.dspg_recompute_all.restype = i32
@@ -172,7 +174,7 @@ def load():
 
 
 EXPORTED = ["dspg_build", "dspg_build_form", "dspg_apply_batch", "dspg_apply_batch_algebraic", "dspg_read_C", "dspg_read_A",
-            "dspg_read_bloom", "dspg_read_rows_C",
+            "dspg_read_bloom", "dspg_read_rows_C", "dspg_read_affected_C",
             "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_set_profiling", "dspg_stage_times",
             "dspg_kernel_launches", "dspg_run_counts", "dspg_reserve", "dspg_multiply_rows_noalloc", "dspg_set_tuning", "dspg_get_tuning",
             "dspg_tuning_candidate", "dspg_autotune", "dspg_group_create", "dspg_group_apply", "dspg_group_destroy",
@@ -399,6 +401,34 @@ class DynamicSpGEMM:
                           device="cuda")
         self._check(self._lib.dspg_read_C(self._h, C.byref(nnz), rp.data_ptr(), col.data_ptr(), val.data_ptr(), 1, s))
         return rp, col[: nnz.value], val[: nnz.value]
+
+    def read_affected(self, stream=None):
+        """(rows, rowptr, col, val) of the last batch's affected rows of C', in
+        one call (dspg_read_affected_C): R ascending and its rows canonical,
+        in page-locked host arrays kept at the largest size seen."""
+        s = _stream(stream)
+        n = C.c_int64()
+        nnz = C.c_int64()
+        cap = getattr(self, "_aff_cap", (0, 0))
+        for _ in range(2):
+            if cap[0] == 0:  # sizes first
+                self._check(self._lib.dspg_read_affected_C(self._h, 0, 0, C.byref(n), C.byref(nnz), None, None, None,
+                                                           None, 0, s))
+                cap = (n.value + n.value // 4 + 1, nnz.value + nnz.value // 4 + 1)  # room for the next batches
+            rows = _host_empty(cap[0], np.int32)
+            rp = _host_empty(cap[0] + 1, np.int64)
+            col = _host_empty(cap[1], np.int32)
+            val = _host_empty(cap[1], _vdtype(self.sr))
+            st = self._lib.dspg_read_affected_C(self._h, cap[0], cap[1], C.byref(n), C.byref(nnz), rows.ctypes.data,
+                                                rp.ctypes.data, col.ctypes.data, val.ctypes.data, 0, s)
+            if st == 1 and (n.value > cap[0] or nnz.value > cap[1]):
+                cap = (max(n.value, cap[0]) + n.value // 4 + 1, max(nnz.value, cap[1]) + nnz.value // 4 + 1)
+                continue
+            self._check(st)
+            self._aff_cap = (max(cap[0], n.value), max(cap[1], nnz.value))
+            k, e = n.value, nnz.value
+            return rows[:k], rp[:k + 1], col[:e], val[:e]
+        raise DspgError(1, "read_affected: sizes kept changing")
 
     def read_rows_C(self, rows, stream=None):
         rows = np.ascontiguousarray(rows, np.int32)

@@ -551,6 +551,57 @@ def test_row_reads_between_batches(dspg):
         _sampled_rows(g, Ao, Ao, R, f"batch {t}: R after a read of C")
 
 
+@pytest.mark.parametrize("bloom", [False, True])
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_read_affected_in_one_call(dspg, sr, bloom):
+    """dspg_read_affected_C returns R ascending and its rows of C' in one
+    call: the same as dspg_last_affected and a read of those rows, against
+    the oracle (row path, masked path, the delta path's batches, an empty
+    batch, and buffers that start too small)."""
+    n = 3000
+    A = er_matrix(n, 6, seed=81, kind=sr)
+    g = dspg.DynamicSpGEMM(A, bloom=bloom)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    g._aff_cap = (4, 4)  # too small: the binding grows them and calls again
+    empty = Batch(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, A.val.dtype), np.zeros(0, np.uint8))
+    batches = [random_batch(n, n, 300 + 200 * t, 82 + t, sr, A=A) for t in range(3)] + [empty]
+    for t, b in enumerate(batches):
+        if bloom:
+            g.apply_batch(b)
+            Ao.apply(b)
+        else:
+            _apply_both(g, Ao, Co, b)
+        rows, rp, col, val = g.read_affected()
+        R = g.last_affected()
+        assert np.array_equal(rows, R), f"batch {t}: rows"
+        assert np.all(np.diff(rows) > 0)
+        orp, ocol, oval = Ao.multiply_rows(Ao, rows)
+        assert np.array_equal(rp, orp) and np.array_equal(col, ocol), f"batch {t}: pattern"
+        if sr == MIN_PLUS_I32:
+            assert np.array_equal(val, oval)
+        else:
+            _, _, sabs = Ao.multiply_rows(Ao, rows, absval=True)
+            assert np.all(np.abs(val - oval) <= 1e-12 * sabs), f"batch {t}: values"
+    if not bloom:
+        # an insert-only batch through the delta path, then the read
+        Ag = g.read_A()
+        rng = np.random.default_rng(90)
+        present = set(zip(np.repeat(np.arange(n), np.diff(Ag.rowptr)).tolist(), Ag.col.tolist()))
+        ins = [(int(i), int(j)) for i, j in zip(rng.integers(0, n, 400), rng.integers(0, n, 400)) if (i, j) not in present]
+        ins = list(dict.fromkeys(ins))
+        vals = rng.random(len(ins)) if sr == PLUS_TIMES_F64 else rng.integers(1, 101, len(ins)).astype(np.int32)
+        b = Batch(np.array([i for i, _ in ins], np.int32), np.array([j for _, j in ins], np.int32), vals,
+                  np.zeros(len(ins), np.uint8))
+        g.apply_batch(b, algebraic=True)
+        Ao.apply(b)
+        rows, rp, col, val = g.read_affected()
+        assert np.array_equal(rows, g.last_affected())
+        orp, ocol, _ = Ao.multiply_rows(Ao, rows)
+        assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    g.close()
+
+
 @pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
 def test_captured_pipeline_serves_uneven_sizes(dspg, sr):
     """Batches of different sizes within one launch size (a multiple of 1024
