@@ -262,6 +262,19 @@ dspg_status dspg_read_A(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32
 dspg_status dspg_read_rows_C(dspg_handle *h, const int32_t *rows, int64_t nrows, int64_t *nnz_out,
                              int64_t *rowptr, int32_t *col, void *val, int on_device, void *stream);
 
+/* Host-side fault injection, a testing aid with no counterpart in the
+ * paper.  spec: NULL or "" (off), or "site@N" items separated by commas:
+ * alloc@N fails the N-th device allocation from now on (DSPG_ERR_OOM),
+ * validate@N fails the N-th batch check (DSPG_ERR_INVALID).  Counted per
+ * process; each fires once.  The environment variable DSPG_FAULT sets the
+ * same at the first use of the library.  A batch that fails in its checks
+ * or while its buffers grow (before A, B or C change) leaves the handle as
+ * it was; a failure after that (an exhausted arena that cannot grow, a
+ * probe limit, a CUDA error) leaves the handle's matrices undefined, and
+ * every later call on it returns DSPG_ERR_STATE.  Returns
+ * DSPG_ERR_INVALID for a malformed spec. */
+dspg_status dspg_fault_inject(const char *spec);
+
 /* The rows of C the last batch affected (the set dspg_last_affected lists)
  * and their entries, in one call: R ascending into rows, and the rows of C'
  * in canonical CSR (rowptr n+1 entries, columns ascending per row) into

@@ -25,6 +25,7 @@ from .dspg import (  # noqa: F401
     SIZE_EXACT,
     SIZE_LEARNED,
     TUNING_FIELDS,
+    fault_inject,
     kernel_launches,
     library_path,
     multiply_rows_noalloc,

@@ -17,6 +17,7 @@
 // from the failed one.  Nothing is mutated before the stage that overflowed
 // has succeeded, so the handle always stays consistent.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -24,6 +25,8 @@
 #include <stdexcept>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "estimator.cuh"
 #include "internal.h"
@@ -48,8 +51,67 @@ struct Err : std::runtime_error {
         if (e_ != cudaSuccess) throw Err(DSPG_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// Host-side fault injection (testing aid; DSPG_FAULT in the environment or
+// dspg_fault_inject): "alloc@N" makes the N-th device allocation from then
+// on fail as out of memory, "validate@N" the N-th batch check fail as an
+// invalid batch.  Counted process-wide.
+struct FaultPlan {
+    std::atomic<long long> alloc_at{0}, alloc_seen{0}, validate_at{0}, validate_seen{0};
+};
+FaultPlan &faults() {
+    static FaultPlan f;
+    return f;
+}
+bool parse_faults(const char *spec, long long *alloc_at, long long *validate_at) {
+    *alloc_at = 0;
+    *validate_at = 0;
+    if (!spec) return true;
+    std::string s(spec);
+    size_t p = 0;
+    while (p < s.size()) {
+        size_t q = s.find(',', p);
+        if (q == std::string::npos) q = s.size();
+        const std::string item = s.substr(p, q - p);
+        const size_t at = item.find('@');
+        if (!item.empty()) {
+            if (at == std::string::npos) return false;
+            const std::string site = item.substr(0, at);
+            char *end = nullptr;
+            const long long n = strtoll(item.c_str() + at + 1, &end, 10);
+            if (!end || *end != '\0' || n < 1) return false;
+            if (site == "alloc") *alloc_at = n;
+            else if (site == "validate") *validate_at = n;
+            else return false;
+        }
+        p = q + 1;
+    }
+    return true;
+}
+void arm_faults(long long alloc_at, long long validate_at) {
+    FaultPlan &f = faults();
+    f.alloc_seen = 0;
+    f.validate_seen = 0;
+    f.alloc_at = alloc_at;
+    f.validate_at = validate_at;
+}
+void faults_from_env() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    long long a = 0, v = 0;
+    if (const char *env = getenv("DSPG_FAULT"))
+        if (parse_faults(env, &a, &v)) arm_faults(a, v);
+}
+bool fault_fires(std::atomic<long long> &at, std::atomic<long long> &seen) {
+    faults_from_env();
+    if (at.load() <= 0) return false;
+    return ++seen == at.load();
+}
+
 void *dmalloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
+    if (fault_fires(faults().alloc_at, faults().alloc_seen))
+        throw Err(DSPG_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected fault)");
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
@@ -432,6 +494,7 @@ struct dspg_handle {
     DBuf<char> xval;
     int64_t extra_slots = 0;                    // table slots of the last batch's overflow recompute
     bool bloom = false;                         // C keeps its Bloom filter; batches take Algorithm 2
+    bool broken = false;                        // a batch failed after A, B or C began to change
     MaskWs mw;                                  // the masked path's buffers
     int64_t last_masked = 0;                    // entries of C* of the last batch
     int64_t compactions = 0;
@@ -456,6 +519,19 @@ struct dspg_group {
 };
 
 namespace {
+
+// An NVTX range over a host call (shown by profilers that record NVTX; a
+// push and a pop of a string otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// DSPG_TRACE=<file>: one JSON line per applied batch (its statistics, the
+// stage times when profiling is on), appended to the file.
+void trace_batch(const dspg_handle *h, const dspg_batch_stats &st, const char *path_kind);
 
 void set_defaults(dspg_options *o) {
     o->slack_min = 4;
@@ -719,6 +795,7 @@ void numeric_branches(dspg_handle *h, cudaStream_t s, const CJob &J) {
 void bloom_build(dspg_handle *h, cudaStream_t s);
 
 void static_recompute(dspg_handle *h, cudaStream_t s) {
+    NvtxRange r("dspg/static_recompute");
     h->c_serial++;
     ensure_c_ws(h, s);
     DevMat &C = h->C;
@@ -1319,6 +1396,7 @@ void fill_rows_out(dspg_handle *h, DevMat &M, const MatView &V, int vs, const in
 
 int64_t read_mat(dspg_handle *h, DevMat &M, const int32_t *rows_in, int64_t nr, int64_t *rowptr, int32_t *col,
                  void *val, int on_device, cudaStream_t s, bool bloom = false) {
+    NvtxRange nr_("dspg/read");
     // with bloom the values read are C's Bloom words (8 bytes each) instead
     MatView V = M.view();
     int vs = M.vsize;
@@ -1460,7 +1538,23 @@ int64_t read_operand_a(dspg_handle *h, int64_t *rowptr, int32_t *col, void *val,
 }
 
 // Checks one batch pair and gets the handle's buffers and inputs ready.
+void prepare_batch_impl(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, cudaStream_t s);
+
+// The host checks and the growth of the batch's buffers, before anything of
+// A, B or C changes: a failure here leaves the handle as it was (buffers that
+// moved before it bump the epoch, so no captured graph keeps their old places).
 void prepare_batch(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, cudaStream_t s) {
+    try {
+        if (fault_fires(faults().validate_at, faults().validate_seen))
+            throw Err(DSPG_ERR_INVALID, "batch check failed (injected fault)");
+        prepare_batch_impl(h, dA, dB, s);
+    } catch (...) {
+        h->epoch++;
+        throw;
+    }
+}
+
+void prepare_batch_impl(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, cudaStream_t s) {
     h->c_serial++;
     h->extra_slots = 0;
     if ((h->b_is_a || h->b_alias) && dB && dB->n > 0) throw Err(DSPG_ERR_INVALID, "B is A: pass the batch as dA only");
@@ -1577,6 +1671,33 @@ void fill_stats(dspg_handle *h, dspg_batch_stats *stats, int64_t compactions0) {
     }
 }
 
+void trace_batch(const dspg_handle *h, const dspg_batch_stats &st, const char *path_kind) {
+    const char *path = getenv("DSPG_TRACE");
+    if (!path || !path[0]) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;  // tracing never fails a batch
+    static const char *stage_names[DSPG_NSTAGES] = {"sort", "classify", "detect", "merge",
+                                                    "commit", "transpose", "size", "numeric"};
+    fprintf(f,
+            "{\"handle\": \"%p\", \"path\": \"%s\", \"n_updates\": %lld, \"n_unique\": %lld, \"n_insert\": %lld, "
+            "\"n_update\": %lld, \"n_delete\": %lld, \"n_noop\": %lld, \"touched_rows\": %lld, \"affected_rows\": %lld, "
+            "\"products\": %lld, \"nnz_written\": %lld, \"relocations\": %lld, \"compactions\": %lld, "
+            "\"a_entries\": %lld, \"est_rows\": %lld, \"est_overflows\": %lld, \"table_slots\": %lld, "
+            "\"masked_entries\": %lld",
+            (const void *)h, path_kind, (long long)st.n_updates, (long long)st.n_unique, (long long)st.n_insert,
+            (long long)st.n_update, (long long)st.n_delete, (long long)st.n_noop, (long long)st.touched_rows,
+            (long long)st.affected_rows, (long long)st.products, (long long)st.nnz_written,
+            (long long)st.relocations, (long long)st.compactions, (long long)st.a_entries, (long long)st.est_rows,
+            (long long)st.est_overflows, (long long)st.table_slots, (long long)st.masked_entries);
+    if (h->prof && !h->bloom) {
+        fprintf(f, ", \"stage_ms\": {");
+        for (int k = 0; k < DSPG_NSTAGES; k++) fprintf(f, "%s\"%s\": %.5f", k ? ", " : "", stage_names[k], h->stage_ms[k]);
+        fprintf(f, "}");
+    }
+    fprintf(f, "}\n");
+    fclose(f);
+}
+
 
 // Rows whose learned table overflowed were left as they were; they are
 // counted exactly and recomputed here (eagerly; only when there are any).
@@ -1612,18 +1733,37 @@ void masked_apply(dspg_handle *h, cudaStream_t s);
 
 void apply_one(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB, dspg_batch_stats *stats,
                cudaStream_t s) {
+    NvtxRange r(h->bloom ? "dspg/apply_batch (Algorithm 2)" : "dspg/apply_batch");
+    dspg_batch_stats local;
+    if (!stats) stats = &local;
     prepare_batch(h, dA, dB, s);
     const int64_t compactions0 = h->compactions;
-    if (h->bloom) {
-        masked_apply(h, s);
+    try {
+        if (h->bloom) {
+            masked_apply(h, s);
+            fill_stats(h, stats, compactions0);
+            trace_batch(h, *stats, "masked");
+            return;
+        }
+        run_first(h, s);
+        if (h->prof) stage_times_from_events(h);
+        recover(h, s);
+        est_fallback(h, s);
         fill_stats(h, stats, compactions0);
-        return;
+        trace_batch(h, *stats, "rows");
+    } catch (const Err &e) {
+        // an invalid batch is found before anything changes (every stage
+        // after the check skips on its status bit); any other failure may
+        // have left A', B' and C part-way
+        if (e.st != DSPG_ERR_INVALID) h->broken = true;
+        throw;
     }
-    run_first(h, s);
-    if (h->prof) stage_times_from_events(h);
-    recover(h, s);
-    est_fallback(h, s);
-    fill_stats(h, stats, compactions0);
+}
+
+// Calls on a handle whose earlier batch failed part-way are refused.
+void check_usable(const dspg_handle *h) {
+    if (h->broken)
+        throw Err(DSPG_ERR_STATE, "an earlier batch failed part-way; the handle's matrices are undefined: rebuild it");
 }
 
 // ------------------------------------------------- the delta path (Eq. 1)
@@ -1662,6 +1802,7 @@ void alg_collect(dspg_handle *h, uint32_t *bm, cudaStream_t s) {
 // which the caller then applies by the row path.  Runs eagerly on s and
 // reads the control block between its steps.
 bool apply_algebraic(dspg_handle *h, cudaStream_t s) {
+    NvtxRange r("dspg/apply_batch_algebraic");
     const int64_t nA = h->inA.n, nB = h->b_is_a ? 0 : h->inB.n;
     begin_batch(h->h_args_dev, h->d_args, h->ctl, s);
     stage_sort(h, s);
@@ -2054,6 +2195,7 @@ dspg_status dspg_build_form(dspg_handle **out, const dspg_csr *A, const dspg_csr
     dspg_handle *h = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     try {
+        NvtxRange nvtx_build("dspg/build");
         if (!out) throw Err(DSPG_ERR_INVALID, "out is NULL");
         *out = nullptr;
         if (sr != DSPG_PLUS_TIMES_F64 && sr != DSPG_MIN_PLUS_I32) throw Err(DSPG_ERR_INVALID, "unknown semiring");
@@ -2177,6 +2319,7 @@ dspg_status dspg_apply_batch(dspg_handle *h, const dspg_updates *dA, const dspg_
     if (!h) return DSPG_ERR_INVALID;
     if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
     try {
+        check_usable(h);
         apply_one(h, dA, dB, stats, (cudaStream_t)stream);
         return DSPG_OK;
     } catch (const Err &e) {
@@ -2189,6 +2332,7 @@ dspg_status dspg_apply_batch_async(dspg_handle *h, const dspg_updates *dA, const
     if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is already in flight"));
     if (h->bloom) return fail(h, Err(DSPG_ERR_STATE, "a handle with the Bloom filter applies batches synchronously"));
     try {
+        check_usable(h);
         const cudaStream_t s = (cudaStream_t)stream;
         prepare_batch(h, dA, dB, s);
         h->pending_comp0 = h->compactions;
@@ -2206,10 +2350,15 @@ dspg_status dspg_apply_batch_wait(dspg_handle *h, dspg_batch_stats *stats, void 
     try {
         const cudaStream_t s = (cudaStream_t)stream;
         h->pending = false;
-        CK(cudaStreamSynchronize(s));
-        if (h->prof) stage_times_from_events(h);
-        recover(h, s);
-        est_fallback(h, s);
+        try {
+            CK(cudaStreamSynchronize(s));
+            if (h->prof) stage_times_from_events(h);
+            recover(h, s);
+            est_fallback(h, s);
+        } catch (const Err &e) {
+            if (e.st != DSPG_ERR_INVALID) h->broken = true;
+            throw;
+        }
         fill_stats(h, stats, h->pending_comp0);
         return DSPG_OK;
     } catch (const Err &e) {
@@ -2223,18 +2372,27 @@ dspg_status dspg_apply_batch_algebraic(dspg_handle *h, const dspg_updates *dA, c
     if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
     if (h->bloom) return fail(h, Err(DSPG_ERR_STATE, "a handle with the Bloom filter takes dspg_apply_batch"));
     try {
+        check_usable(h);
         const cudaStream_t s = (cudaStream_t)stream;
         prepare_batch(h, dA, dB, s);
         const int64_t compactions0 = h->compactions;
-        h->last_alg = apply_algebraic(h, s);
-        if (!h->last_alg) {  // general updates: the row path
-            run_first(h, s);
-            if (h->prof) stage_times_from_events(h);
-            recover(h, s);
+        try {
+            h->last_alg = apply_algebraic(h, s);
+            if (!h->last_alg) {  // general updates: the row path
+                run_first(h, s);
+                if (h->prof) stage_times_from_events(h);
+                recover(h, s);
+            }
+            est_fallback(h, s);
+        } catch (const Err &e) {
+            if (e.st != DSPG_ERR_INVALID) h->broken = true;
+            throw;
         }
-        est_fallback(h, s);
+        dspg_batch_stats local;
+        if (!stats) stats = &local;
         fill_stats(h, stats, compactions0);
-        if (stats) stats->algebraic = h->last_alg ? 1 : 0;
+        stats->algebraic = h->last_alg ? 1 : 0;
+        trace_batch(h, *stats, h->last_alg ? "delta" : "rows");
         return DSPG_OK;
     } catch (const Err &e) {
         return fail(h, e);
@@ -2245,6 +2403,7 @@ dspg_status dspg_read_C(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32
                         void *stream) {
     if (!h || !nnz_out) return DSPG_ERR_INVALID;
     try {
+        check_usable(h);
         *nnz_out = h->form ? read_form(h, nullptr, 0, rowptr, col, val, on_device, (cudaStream_t)stream)
                            : read_mat(h, h->C, nullptr, 0, rowptr, col, val, on_device, (cudaStream_t)stream);
         return DSPG_OK;
@@ -2259,6 +2418,7 @@ dspg_status dspg_read_bloom(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, i
     if (!h->bloom) return fail(h, Err(DSPG_ERR_STATE, "the handle keeps no Bloom filter (options.bloom = 0)"));
     if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
     try {
+        check_usable(h);
         *nnz_out = read_mat(h, h->C, nullptr, 0, rowptr, col, (void *)words, on_device, (cudaStream_t)stream, true);
         return DSPG_OK;
     } catch (const Err &e) {
@@ -2270,6 +2430,7 @@ dspg_status dspg_read_A(dspg_handle *h, int64_t *nnz_out, int64_t *rowptr, int32
                         void *stream) {
     if (!h || !nnz_out) return DSPG_ERR_INVALID;
     try {
+        check_usable(h);
         *nnz_out = read_operand_a(h, rowptr, col, val, on_device, (cudaStream_t)stream);
         return DSPG_OK;
     } catch (const Err &e) {
@@ -2281,6 +2442,7 @@ dspg_status dspg_read_rows_C(dspg_handle *h, const int32_t *rows, int64_t nrows,
                              int32_t *col, void *val, int on_device, void *stream) {
     if (!h || !nnz_out || nrows < 0 || (nrows > 0 && !rows)) return DSPG_ERR_INVALID;
     try {
+        check_usable(h);
         if (!on_device) {
             for (int64_t i = 0; i < nrows; i++)
                 if (rows[i] < 0 || rows[i] >= h->C.nrows) throw Err(DSPG_ERR_INVALID, "row index out of range");
@@ -2294,6 +2456,16 @@ dspg_status dspg_read_rows_C(dspg_handle *h, const int32_t *rows, int64_t nrows,
     }
 }
 
+dspg_status dspg_fault_inject(const char *spec) {
+    long long a = 0, v = 0;
+    if (!parse_faults(spec, &a, &v)) {
+        set_thread_error("fault spec must be NULL, empty, or site@N[,site@N] with site alloc or validate, N >= 1");
+        return DSPG_ERR_INVALID;
+    }
+    arm_faults(a, v);
+    return DSPG_OK;
+}
+
 dspg_status dspg_read_affected_C(dspg_handle *h, int64_t rows_cap, int64_t nnz_cap, int64_t *nrows_out,
                                  int64_t *nnz_out, int32_t *rows, int64_t *rowptr, int32_t *col, void *val,
                                  int on_device, void *stream) {
@@ -2302,6 +2474,8 @@ dspg_status dspg_read_affected_C(dspg_handle *h, int64_t rows_cap, int64_t nnz_c
     if (h->form) return fail(h, Err(DSPG_ERR_STATE, "a handle with alpha, beta or X reads its rows by dspg_read_rows_C"));
     cudaStream_t s = (cudaStream_t)stream;
     try {
+        check_usable(h);
+        NvtxRange r("dspg/read_affected_C");
         const int64_t n = h->last_nR;
         dspg_handle::ReadWs &w = h->rd;
         w.r.reserve(std::max<int64_t>(n, 1));
@@ -2359,6 +2533,7 @@ dspg_status dspg_last_affected(dspg_handle *h, int64_t *count, int32_t *rows, in
     if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
     cudaStream_t s = (cudaStream_t)stream;
     try {
+        check_usable(h);
         const int64_t n = h->last_nR;
         if (!rows) {
             *count = n;
@@ -2417,6 +2592,7 @@ dspg_status dspg_recompute_all(dspg_handle *h, void *stream) {
     if (!h) return DSPG_ERR_INVALID;
     if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
     try {
+        check_usable(h);
         static_recompute(h, (cudaStream_t)stream);
         return DSPG_OK;
     } catch (const Err &e) {

@@ -101,6 +101,8 @@ def load():
             f.argtypes = [p, C.POINTER(i64), p, p, p, i32, p]
         lib.dspg_read_rows_C.restype = i32
         lib.dspg_read_rows_C.argtypes = [p, p, i64, C.POINTER(i64), p, p, p, i32, p]
+        lib.dspg_fault_inject.restype = i32
+        lib.dspg_fault_inject.argtypes = [C.c_char_p]
         lib.dspg_read_affected_C.restype = i32
         lib.dspg_read_affected_C.argtypes = [p, i64, i64, C.POINTER(i64), C.POINTER(i64), p, p, p, p, i32, p]
         lib.dspg_last_affected.restype = i32
@@ -174,7 +176,7 @@ def load():
 
 
 EXPORTED = ["dspg_build", "dspg_build_form", "dspg_apply_batch", "dspg_apply_batch_algebraic", "dspg_read_C", "dspg_read_A",
-            "dspg_read_bloom", "dspg_read_rows_C", "dspg_read_affected_C",
+            "dspg_read_bloom", "dspg_read_rows_C", "dspg_read_affected_C", "dspg_fault_inject",
             "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_set_profiling", "dspg_stage_times",
             "dspg_kernel_launches", "dspg_run_counts", "dspg_reserve", "dspg_multiply_rows_noalloc", "dspg_set_tuning", "dspg_get_tuning",
             "dspg_tuning_candidate", "dspg_autotune", "dspg_group_create", "dspg_group_apply", "dspg_group_destroy",
@@ -263,6 +265,16 @@ def _stream(stream):
     except Exception:
         pass
     return None
+
+
+def fault_inject(spec: str | None) -> None:
+    """Arm host-side fault injection (dspg_fault_inject): "alloc@N" fails the
+    N-th device allocation, "validate@N" the N-th batch check; None or ""
+    disarms."""
+    lib = load()
+    st = lib.dspg_fault_inject(spec.encode() if spec else None)
+    if st != 0:
+        raise DspgError(st, lib.dspg_last_error(None).decode())
 
 
 class DynamicSpGEMM:
