@@ -275,6 +275,11 @@ dspg_status dspg_read_rows_C(dspg_handle *h, const int32_t *rows, int64_t nrows,
  * DSPG_ERR_INVALID for a malformed spec. */
 dspg_status dspg_fault_inject(const char *spec);
 
+/* 1 for the debug build (compiled with DSPG_DEBUG=1: kernels check indices
+ * and room before their accesses, and a failed check fails the batch with
+ * DSPG_ERR_CUDA naming the check), else 0. */
+int dspg_debug_build(void);
+
 /* The rows of C the last batch affected (the set dspg_last_affected lists)
  * and their entries, in one call: R ascending into rows, and the rows of C'
  * in canonical CSR (rowptr n+1 entries, columns ascending per row) into

@@ -30,6 +30,7 @@ enum : unsigned {
     ST_TIMEOUT = 1u << 8,     // a bounded probe loop gave up
     ST_ALG_FULL = 1u << 9,    // the delta path's list of new C entries is full: recompute the touched rows
     ST_MASK_FULL = 1u << 10,  // the masked path's contribution or kept-entry list is full: grow it, run again
+    ST_DEBUG = 1u << 11,      // a check of the debug build failed (code and index in the control block)
 };
 constexpr unsigned M_AB = ST_INVALID | ST_AB_STAGE | ST_AB_ARENA | ST_TIMEOUT;
 constexpr unsigned M_AT = M_AB | ST_AT_STAGE | ST_AT_ARENA;
@@ -81,6 +82,8 @@ struct Ctl {
     long long mask_n;          // masked path: contributions to the pattern of C* formed
     long long mask_kept;       // masked path: entries of A' kept by the Bloom filter (A^R)
     long long mask_u;          // masked path: entries of C*
+    long long dbg_code;        // debug build: the first failed check's code (0: none) and index
+    long long dbg_idx;
     long long pad[1];
 };
 
@@ -132,6 +135,35 @@ __device__ __forceinline__ bool failed(const Ctl *ctl, unsigned mask) {
 }
 
 __device__ __forceinline__ void set_status(Ctl *ctl, unsigned bit) { atomicOr(&ctl->status, bit); }
+
+// The debug build (DSPG_DEBUG=1) checks indices and room before its
+// accesses: a failed check records its code and the offending index (the
+// first one only), sets ST_DEBUG, and returns false so that the caller
+// skips the access; the batch then fails with the code in its message.
+// Without DSPG_DEBUG the checks compile to nothing (always true).
+#ifndef DSPG_DEBUG
+#define DSPG_DEBUG 0
+#endif
+enum : int {
+    DBG_B_ROW = 1,      // a column of A is not a row of B
+    DBG_C_ROOM = 2,     // a row of C written past its capacity or the arena
+    DBG_BIN_SLOT = 3,   // a bin list written past its capacity
+    DBG_STAGE = 4,      // merge staging written past its capacity
+    DBG_ARENA = 5,      // a committed row of A, B or the pattern past its arena
+    DBG_MASK_ROOM = 6,  // the masked merge wrote a row of C past its room
+};
+__device__ __forceinline__ bool dcheck(Ctl *ctl, bool ok, int code, long long idx) {
+#if DSPG_DEBUG
+    if (!ok) {
+        if (atomicCAS((unsigned long long *)&ctl->dbg_code, 0ull, (unsigned long long)code) == 0ull) ctl->dbg_idx = idx;
+        set_status(ctl, ST_DEBUG);
+    }
+    return ok;
+#else
+    (void)ctl; (void)code; (void)idx;
+    return ok || true;
+#endif
+}
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;

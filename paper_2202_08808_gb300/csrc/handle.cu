@@ -542,6 +542,13 @@ void set_defaults(dspg_options *o) {
     o->bloom = 0;
 }
 
+// A failed check of the debug build (ST_DEBUG) as an error.
+void check_debug(const Ctl *c) {
+    if (c->status & ST_DEBUG)
+        throw Err(DSPG_ERR_CUDA, "debug build: check " + std::to_string(c->dbg_code) + " failed at index " +
+                                     std::to_string(c->dbg_idx));
+}
+
 std::string overflow_message(const Ctl *c) {
     return "accumulator probe limit reached (bin " + std::to_string(c->timeout_bin - 1) + ", row " +
            std::to_string(c->timeout_row) + ", product bound " + std::to_string(c->timeout_ub) + ")";
@@ -854,6 +861,7 @@ void static_recompute(dspg_handle *h, cudaStream_t s) {
     CK(cudaMemcpyAsync(h->ctl->bin_count, h->hctl->bin_count, sizeof(h->hctl->bin_count), cudaMemcpyHostToDevice, s));
     numeric_branches(h, s, c_job(h, h->wc.iota.p, true));
     read_ctl(h, s);
+    check_debug(h->hctl);
     if (h->hctl->status & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, overflow_message(h->hctl));
     if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "static recompute failed with status " + std::to_string(h->hctl->status));
     if (h->bloom) bloom_build(h, s);
@@ -1584,6 +1592,7 @@ void recover(dspg_handle *h, cudaStream_t s) {
     const int64_t nA = h->inA.cap, nB = h->inB.cap;  // the stages that ran
     for (int iter = 0; iter < 8 && h->hctl->status; iter++) {
         const unsigned st = h->hctl->status;
+        check_debug(h->hctl);
         if (st & ST_INVALID) throw Err(DSPG_ERR_INVALID, "batch entry out of range or with an invalid value/op");
         if (st & ST_TIMEOUT) throw Err(DSPG_ERR_TIMEOUT, overflow_message(h->hctl));
         if (st & ST_AB_STAGE) {
@@ -1869,6 +1878,7 @@ bool apply_algebraic(dspg_handle *h, cudaStream_t s) {
         transpose_commit(h, s);
         read_ctl(h, s);
     }
+    check_debug(h->hctl);
     if (h->hctl->status & ~ST_ALG_FULL)
         throw Err(DSPG_ERR_CUDA, "delta path update failed, status " + std::to_string(h->hctl->status));
     const long long n_new = h->hctl->alg_new, n_con = h->hctl->alg_contrib;
@@ -2119,6 +2129,7 @@ void masked_apply(dspg_handle *h, cudaStream_t s) {
         CK(cudaGetLastError());
         read_ctl(h, s);
     }
+    check_debug(h->hctl);
     if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "masked path: update failed, status " + std::to_string(h->hctl->status));
     h->hctl->a_entries = h->hctl->mask_kept;
     h->last_masked = h->hctl->mask_u;
@@ -2455,6 +2466,8 @@ dspg_status dspg_read_rows_C(dspg_handle *h, const int32_t *rows, int64_t nrows,
         return fail(h, e);
     }
 }
+
+int dspg_debug_build(void) { return DSPG_DEBUG ? 1 : 0; }
 
 dspg_status dspg_fault_inject(const char *spec) {
     long long a = 0, v = 0;

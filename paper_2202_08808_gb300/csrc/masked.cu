@@ -498,6 +498,7 @@ __global__ void k_mask_splice(MaskJob M, MatView C, unsigned long long *F, Ctl *
         }
         __syncwarp();
         if (lane == 0) {
+            dcheck(ctl, base + len <= C.arena_cap && len <= (dest >= 0 ? M.dcap[r] : C.cap[i]), DBG_MASK_ROOM, i);
             C.len[i] = len;
             if (dest >= 0) {
                 C.off[i] = dest;

@@ -174,7 +174,8 @@ __device__ __forceinline__ void append_bins(const CJob &J, Ctl *ctl, int b, int3
     long long bb = 0;
     if (b >= 0 && lane == leader) bb = atomic_add_ll2(&ctl->bin_count[b], __popc(peers));
     bb = __shfl_sync(0xffffffffu, bb, leader);
-    if (b >= 0) J.bins[(int64_t)b * J.bin_cap + bb + __popc(peers & lanemask_lt())] = i;
+    const long long slot = bb + __popc(peers & lanemask_lt());
+    if (b >= 0 && dcheck(ctl, slot < J.bin_cap, DBG_BIN_SLOT, i)) J.bins[(int64_t)b * J.bin_cap + slot] = i;
 }
 
 constexpr int SIZE_SHORT = 64;   // A rows up to this length are sized by one thread,
@@ -420,7 +421,11 @@ __device__ __forceinline__ int64_t c_row_dest(const MatView &C, const CJob &J, C
         return -1;
     }
     const int32_t cap = C.cap[i];
-    if (J.static_mode || n <= cap) return C.off[i];
+    if (J.static_mode || n <= cap) {
+        const int64_t o = C.off[i];
+        if (!dcheck(ctl, o >= 0 && o + n <= C.arena_cap && (J.static_mode || n <= cap), DBG_C_ROOM, i)) return -1;
+        return o;
+    }
     const int32_t c = slack_cap(n, J.slack_min, J.slack_div);
     const long long d = atomic_add_ll2(C.top, c);
     if (d + c > C.arena_cap) {
@@ -736,9 +741,11 @@ k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned m
             blen[s] = 0;
             if (s < alen) {
                 const int32_t k = A.col[aoff + s];
-                av[s] = Av[aoff + s];
-                boff[s] = B.off[k];
-                blen[s] = B.len[k];
+                if (dcheck(ctl, k >= 0 && k < B.nrows, DBG_B_ROW, aoff + s)) {
+                    av[s] = Av[aoff + s];
+                    boff[s] = B.off[k];
+                    blen[s] = B.len[k];
+                }
             }
         }
         int tot = 0;
@@ -835,9 +842,11 @@ k_num_group_sort(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
             T av = T(0);
             if (ai < alen) {
                 const int32_t k = A.col[aoff + ai];
-                av = Av[aoff + ai];
-                boff = B.off[k];
-                blen = B.len[k];
+                if (dcheck(ctl, k >= 0 && k < B.nrows, DBG_B_ROW, aoff + ai)) {
+                    av = Av[aoff + ai];
+                    boff = B.off[k];
+                    blen = B.len[k];
+                }
             }
             int incl = blen;
 #pragma unroll

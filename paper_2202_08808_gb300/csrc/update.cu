@@ -342,7 +342,7 @@ __global__ void k_commit_plan(CommitJob J, MatView M, Ctl *ctl, unsigned mask, i
 
 template <typename T>
 __device__ __forceinline__ void commit_copy_blocks(const CommitJob &J, const MatView &M, long long blk,
-                                                   long long nblk) {
+                                                   long long nblk, Ctl *ctl) {
     const long long n = *J.cc_count;
     const int lane = threadIdx.x & 31;
     const long long nwarps = (nblk * blockDim.x) >> 5;
@@ -355,6 +355,7 @@ __device__ __forceinline__ void commit_copy_blocks(const CommitJob &J, const Mat
         const int64_t d = J.dest[m];
         const int64_t so = J.soff[m];
         const int e1 = min(nl, (part + 1) * CH);
+        if (!dcheck(ctl, d >= 0 && d + nl <= M.arena_cap, DBG_ARENA, r)) continue;
         for (int e = part * CH + lane; e < e1; e += 32) {
             M.col[d + e] = J.st_col[so + e];
             if (mv) mv[d + e] = sv[so + e];
@@ -371,7 +372,7 @@ template <typename T>
 __global__ void k_commit_copy(CommitJob J, MatView M, const Ctl *ctl, unsigned mask) {
     pdl_begin();
     if (failed(ctl, mask)) return;
-    commit_copy_blocks<T>(J, M, blockIdx.x, gridDim.x);
+    commit_copy_blocks<T>(J, M, blockIdx.x, gridDim.x, const_cast<Ctl *>(ctl));
 }
 
 // ---------------------------------------------------------- detection
@@ -494,7 +495,7 @@ k_collect_copy(uint32_t *bm, int64_t words, int32_t *R, long long *chunk, long l
         collect_blocks(bm, words, R, ctl, blockIdx.x, nc, chunk);
     } else {
         if (failed(ctl, copy_mask)) return;
-        commit_copy_blocks<T>(CJ, M, blockIdx.x - nc, gridDim.x - nc);
+        commit_copy_blocks<T>(CJ, M, blockIdx.x - nc, gridDim.x - nc, const_cast<Ctl *>(ctl));
     }
 }
 

@@ -73,17 +73,23 @@ class _Tuning(C.Structure):
                                          "sort_max")]
 
 
+def _debug() -> bool:
+    return os.environ.get("DSPG_DEBUG", "") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if _debug() else _build.LIB
 
 
 def load():
-    """Load libdspg.so (compiling it first if it is missing or stale)."""
+    """Load libdspg.so (compiling it first if it is missing or stale); with
+    DSPG_DEBUG=1 in the environment, the debug build libdspg_debug.so, whose
+    kernels check indices and room before their accesses."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build()
+        path = _build.build(debug=_debug())
         lib = C.CDLL(path)
         p, i64, i32 = C.c_void_p, C.c_int64, C.c_int
         lib.dspg_build.restype = i32
@@ -101,6 +107,8 @@ def load():
             f.argtypes = [p, C.POINTER(i64), p, p, p, i32, p]
         lib.dspg_read_rows_C.restype = i32
         lib.dspg_read_rows_C.argtypes = [p, p, i64, C.POINTER(i64), p, p, p, i32, p]
+        lib.dspg_debug_build.restype = i32
+        lib.dspg_debug_build.argtypes = []
         lib.dspg_fault_inject.restype = i32
         lib.dspg_fault_inject.argtypes = [C.c_char_p]
         lib.dspg_read_affected_C.restype = i32
@@ -176,7 +184,7 @@ def load():
 
 
 EXPORTED = ["dspg_build", "dspg_build_form", "dspg_apply_batch", "dspg_apply_batch_algebraic", "dspg_read_C", "dspg_read_A",
-            "dspg_read_bloom", "dspg_read_rows_C", "dspg_read_affected_C", "dspg_fault_inject",
+            "dspg_read_bloom", "dspg_read_rows_C", "dspg_read_affected_C", "dspg_fault_inject", "dspg_debug_build",
             "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_set_profiling", "dspg_stage_times",
             "dspg_kernel_launches", "dspg_run_counts", "dspg_reserve", "dspg_multiply_rows_noalloc", "dspg_set_tuning", "dspg_get_tuning",
             "dspg_tuning_candidate", "dspg_autotune", "dspg_group_create", "dspg_group_apply", "dspg_group_destroy",
