@@ -940,18 +940,21 @@ k_num_group_sort(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
         }
         __syncwarp(gmask);  // the slots, filled by the group's lanes
         // fold runs of equal columns: inside the lane, each word's value
-        // becomes the fold of its run up to itself
+        // becomes the fold of its run up to itself, one multiply-add per
+        // product (c (+) a (x) b, with c the run so far or the neutral
+        // element where a run starts; the double-precision pipe is the
+        // scarce one on this GPU)
         int32_t col[GS_EPL];
         T v[GS_EPL];
 #pragma unroll
         for (int e = 0; e < GS_EPL; e++) {
             const int slot = (int)(x[e] & (N - 1));
-            col[e] = x[e] == PAD ? -1 : (int32_t)(x[e] >> LOGN);
-            v[e] = x[e] == PAD ? Sr<SR>::zero() : Sr<SR>::mul(sa[slot], sb[slot]);
+            const bool pad = x[e] == PAD;
+            col[e] = pad ? -1 : (int32_t)(x[e] >> LOGN);
+            const T a = pad ? T(0) : sa[slot], b = pad ? T(0) : sb[slot];
+            const bool same = e > 0 && col[e] == col[e - 1];
+            v[e] = Sr<SR>::fma(a, b, same ? v[e > 0 ? e - 1 : 0] : Sr<SR>::zero());
         }
-#pragma unroll
-        for (int e = 1; e < GS_EPL; e++)
-            if (col[e] == col[e - 1]) v[e] = Sr<SR>::add(v[e - 1], v[e]);
         // across lanes: a lane's first run continues the previous lane's
         // last one when their columns agree; a segmented scan over the lanes
         // gives each lane the fold of the run that ends at its last word
@@ -969,11 +972,14 @@ k_num_group_sort(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
                 head = ph;
             }
         }
+        // the carry of a linked lane joins its first run, whose last word is
+        // the only one of that run an output can come from
         const T carry = __shfl_up_sync(gmask, run, 1, G);
-        if (link)
+        T first_end = v[0];
 #pragma unroll
-            for (int e = 0; e < GS_EPL; e++)
-                if (col[e] == first) v[e] = Sr<SR>::add(carry, v[e]);
+        for (int e = 1; e < GS_EPL; e++)
+            if (col[e] == first) first_end = v[e];
+        first_end = link ? Sr<SR>::add(carry, first_end) : first_end;
         // the last word of each run holds the entry; its rank among the
         // row's runs is its place in the output
         const int32_t next_first = __shfl_down_sync(gmask, first, 1, G);
@@ -1000,7 +1006,7 @@ k_num_group_sort(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
                 const int32_t nk = e + 1 < GS_EPL ? col[e + 1] : (gl + 1 < G ? next_first : -1);
                 if (col[e] >= 0 && nk != col[e]) {
                     C.col[dest + w] = col[e];
-                    Cv[dest + w] = v[e];
+                    Cv[dest + w] = col[e] == first ? first_end : v[e];
                     w++;
                 }
             }
