@@ -51,7 +51,7 @@ def peaks():
 # workload, from the ncu capture summarised in
 # profiles/numeric_stage_dram_stencil128.md (valid while those kernels are
 # unchanged); None where no capture exists.
-NUMERIC_TRAFFIC = {"stencil": 87991808}
+NUMERIC_TRAFFIC = {"stencil": 85725952}
 
 
 def dist_env():
@@ -333,6 +333,7 @@ def gpu_arm(args):
         static_runs[f"candidate_{ci}"] = time_static()
     g.set_tuning(keep_tuning)
     static_med = min(static_runs.values())
+    cusparse = cusparse_static(A, B, flush, stream) if (W.name == "stencil" and not args.no_cusparse) else None
     for b in W.batches(2, 7000 * (rank + 1)):  # re-capture the pipeline under the restored bins
         g.apply_batch(type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(),
                               torch.from_numpy(b.val).cuda(), torch.from_numpy(b.op).cuda()))
@@ -454,6 +455,7 @@ def gpu_arm(args):
             "static_recompute_ms": round(static_med, 3),
             "static_runs_ms": {k: round(v, 3) for k, v in static_runs.items()},
             "static_best": min(static_runs, key=static_runs.get),
+            "cusparse_static": cusparse,
             "tuning": tuned,
             "speedup_vs_static": round(static_med / statistics.median(lat), 2),
             "stages_ms": {s: round(v / max(n_prof, 1), 4) for s, v in stage_acc.items()},
@@ -482,6 +484,39 @@ def gpu_arm(args):
         dist.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
+
+
+def cusparse_static(A, B, flush, stream):
+    """An external sanity reference for the static (+,.) product: cuSPARSE's
+    SpGEMM (torch's CSR x CSR product on the device) on the same A', timed
+    like the static recompute (median of three, L2 flushed before each);
+    not on the library's path."""
+    import torch
+    try:
+        def dev(M):
+            return torch.sparse_csr_tensor(torch.from_numpy(np.asarray(M.rowptr, np.int64)).cuda(),
+                                           torch.from_numpy(np.asarray(M.col, np.int64)).cuda(),
+                                           torch.from_numpy(np.asarray(M.val, np.float64)).cuda(),
+                                           size=(M.nrows, M.ncols))
+        a = dev(A)
+        b = a if B is None else dev(B)
+        ts, nnz = [], None
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c = a @ b
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            nnz = int(c._nnz())
+            del c
+        return {"ms": round(statistics.median(ts), 3), "nnz_c": nnz,
+                "what": "torch CSR @ CSR on the device (cuSPARSE SpGEMM), f64, the build's A"}
+    except Exception as e:  # a comparator only: report why it did not run
+        return {"unavailable": str(e).splitlines()[0][:200]}
 
 
 def masked_leg(args, flush, stream, scale=20):
@@ -1177,6 +1212,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cusparse", action="store_true", help="skip the cuSPARSE static-product comparator")
     ap.add_argument("--no-masked", action="store_true",
                     help="skip the masked-path leg (Algorithm 2 beside the row path on R-MAT scale 20)")
     ap.add_argument("--profile", choices=["step", "static"], default=None,

@@ -975,11 +975,11 @@ k_num_group_sort(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
         // the carry of a linked lane joins its first run, whose last word is
         // the only one of that run an output can come from
         const T carry = __shfl_up_sync(gmask, run, 1, G);
-        T first_end = v[0];
+        if (link)
 #pragma unroll
-        for (int e = 1; e < GS_EPL; e++)
-            if (col[e] == first) first_end = v[e];
-        first_end = link ? Sr<SR>::add(carry, first_end) : first_end;
+            for (int e = 0; e < GS_EPL; e++)
+                if (col[e] == first && (e + 1 == GS_EPL || col[e + 1 < GS_EPL ? e + 1 : e] != first))
+                    v[e] = Sr<SR>::add(carry, v[e]);
         // the last word of each run holds the entry; its rank among the
         // row's runs is its place in the output
         const int32_t next_first = __shfl_down_sync(gmask, first, 1, G);
@@ -1006,7 +1006,7 @@ k_num_group_sort(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
                 const int32_t nk = e + 1 < GS_EPL ? col[e + 1] : (gl + 1 < G ? next_first : -1);
                 if (col[e] >= 0 && nk != col[e]) {
                     C.col[dest + w] = col[e];
-                    Cv[dest + w] = col[e] == first ? first_end : v[e];
+                    Cv[dest + w] = v[e];
                     w++;
                 }
             }
