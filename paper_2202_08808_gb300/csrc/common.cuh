@@ -84,7 +84,7 @@ struct Ctl {
     long long mask_u;          // masked path: entries of C*
     long long dbg_code;        // debug build: the first failed check's code (0: none) and index
     long long dbg_idx;
-    long long pad[1];
+    unsigned long long bins_wanted;  // bins (bit b) whose rows went to the global dense bin instead
 };
 
 // A row-slack CSR ("slack-CSR") on the device: row i occupies

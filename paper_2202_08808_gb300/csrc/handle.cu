@@ -471,6 +471,11 @@ struct dspg_handle {
     std::vector<Graph> seen;  // keys run once eagerly (exec unused)
     uint64_t epoch = 1;       // bumped whenever a persistent buffer moves
     bool use_graphs = true;
+    // recompute bins launched (bit b); a row of a bin that is off goes to the
+    // global dense bin and turns the bin on for the next batch (learn_bins)
+    unsigned long long bin_on = ~0ull;
+    bool bins_narrowed = false;  // bin_on has been cut to the bins batches used
+    bool gate_bins = true;       // DSPG_ALL_BINS=1: every bin, always
     dspg_tuning tune{8, 64, 8, 0, 1024, 16384, 64};  // row bins of the recompute
     int sizing = DSPG_SIZE_BOUND;               // how the recompute's tables are sized
     int est_min = 128;
@@ -745,6 +750,7 @@ CJob c_job(dspg_handle *h, const int32_t *R, bool static_mode) {
     J.warp_max = h->tune.warp_max;
     J.cta_max = h->tune.cta_max;
     J.sort_max = h->tune.sort_max;
+    J.bin_on = (J.dense_mode || static_mode || !h->gate_bins) ? ~0ull : h->bin_on;
     J.sizing = (!static_mode && h->sizing == DSPG_SIZE_LEARNED) ? SIZE_LEARNED : SIZE_BOUND;
     J.est_min = h->est_min;
     J.est_margin = h->est_margin;
@@ -1648,8 +1654,33 @@ void recover(dspg_handle *h, cudaStream_t s) {
     if (h->hctl->status) throw Err(DSPG_ERR_CUDA, "apply_batch did not converge, status " + std::to_string(h->hctl->status));
 }
 
+// After a row-path batch: the bins the recompute launches from now on (the
+// bins that got rows, and those a row was redirected from to the global
+// dense bin).  A change bumps the epoch, so the next batch is captured anew.
+void learn_bins(dspg_handle *h) {
+    if (!h->gate_bins || h->bloom) return;
+    const Ctl &c = *h->hctl;
+    bool any = c.bins_wanted != 0;
+    for (int b = 0; b < NBINS; b++) any |= c.bin_count[b] > 0;
+    if (!any) return;  // nothing was binned (no affected rows, or the delta path)
+    const unsigned long long next = next_bin_mask(c, h->bin_on, h->bins_narrowed);
+    h->bins_narrowed = true;
+    if (next != h->bin_on) {
+        h->bin_on = next;
+        h->epoch++;
+    }
+}
+
+// Every bin on again (the thresholds or the sizing changed which bins rows take).
+void reset_bins(dspg_handle *h) {
+    h->bin_on = ~0ull;
+    h->bins_narrowed = false;
+    h->epoch++;
+}
+
 void fill_stats(dspg_handle *h, dspg_batch_stats *stats, int64_t compactions0) {
     const int64_t nA = h->inA.n, nB = h->inB.n;
+    learn_bins(h);
     h->last_nR = h->hctl->n_affected;
     if (!h->bloom) h->last_masked = 0;
     if (stats) {
@@ -2260,6 +2291,7 @@ dspg_status dspg_build_form(dspg_handle **out, const dspg_csr *A, const dspg_csr
         CK(cudaMalloc((void **)&h->ctl, sizeof(Ctl)));
         CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        if (const char *env = getenv("DSPG_ALL_BINS")) h->gate_bins = env[0] == '0';
         for (int k = 0; k < NUM_SIDE; k++) {
             CK(cudaStreamCreateWithFlags(&h->nstr[k], cudaStreamNonBlocking));
             CK(cudaEventCreateWithFlags(&h->evNum[k], cudaEventDisableTiming));
@@ -2688,7 +2720,7 @@ dspg_status dspg_set_tuning(dspg_handle *h, const dspg_tuning *t) {
         const dspg_tuning v = t ? *t : kCandidates[0];
         check_tuning(v);
         h->tune = v;
-        h->epoch++;  // captured pipelines carry the old bins
+        reset_bins(h);  // captured pipelines carry the old bins
         return DSPG_OK;
     } catch (const Err &e) {
         return fail(h, e);
@@ -2710,6 +2742,7 @@ dspg_status dspg_autotune(dspg_handle *h, const dspg_updates *dA, const dspg_upd
     std::vector<cudaGraphExec_t> execs(kNumCandidates, nullptr);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const dspg_tuning keep = h->tune;
+    const bool gate0 = h->gate_bins;
     auto cleanup = [&] {
         for (auto &x : execs)
             if (x) cudaGraphExecDestroy(x);
@@ -2722,6 +2755,8 @@ dspg_status dspg_autotune(dspg_handle *h, const dspg_updates *dA, const dspg_upd
         CK(cudaEventCreate(&e1));
         std::vector<double> tot(kNumCandidates, 0.0);
         std::vector<uint64_t> epochs(kNumCandidates, 0);
+        reset_bins(h);
+        h->gate_bins = false;  // every candidate runs with all its bins
         for (int64_t b = 0; b < nbatches; b++) {
             h->tune = keep;
             apply_one(h, dA + b, dB ? dB + b : nullptr, nullptr, s);
@@ -2752,7 +2787,8 @@ dspg_status dspg_autotune(dspg_handle *h, const dspg_updates *dA, const dspg_upd
         for (int c = 1; c < kNumCandidates; c++)
             if (tot[c] < tot[bi]) bi = c;
         h->tune = kCandidates[bi];
-        h->epoch++;
+        h->gate_bins = gate0;
+        reset_bins(h);
         if (best) *best = h->tune;
         for (int c = 0; c < kNumCandidates && ms && c < n_ms; c++) ms[c] = (float)tot[c];
         if (n_cand) *n_cand = kNumCandidates;
@@ -2760,7 +2796,8 @@ dspg_status dspg_autotune(dspg_handle *h, const dspg_updates *dA, const dspg_upd
         return DSPG_OK;
     } catch (const Err &e) {
         h->tune = keep;
-        h->epoch++;
+        h->gate_bins = gate0;
+        reset_bins(h);
         cleanup();
         return fail(h, e);
     }
@@ -2781,7 +2818,7 @@ dspg_status dspg_set_sizing(dspg_handle *h, int mode, const dspg_estimator *e, i
             h->est_margin = margin;
         }
         h->sizing = mode;
-        h->epoch++;  // captured pipelines carry the old sizing
+        reset_bins(h);  // captured pipelines carry the old sizing
         return DSPG_OK;
     } catch (const Err &x) {
         return fail(h, x);

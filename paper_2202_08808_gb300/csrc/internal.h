@@ -85,6 +85,10 @@ struct CJob {
     // executor, table oversizing, warp/CTA and CTA/global crossovers
     int tm_k, tm_ub, lanes_min, table_shift, warp_max, cta_max;
     int sort_max;             // rows of at most this many products: group sort
+    // bins (bit b) whose kernels the recompute launches; a row whose bin is
+    // off goes to the global dense bin (any row fits it), and the bin is
+    // recorded in Ctl::bins_wanted.  All bits set in dense mode.
+    unsigned long long bin_on;
     // sizing of the hash tables: SIZE_BOUND by the product bound; SIZE_COUNT
     // by C.len (an exact count written by a count_only pass); SIZE_LEARNED by
     // the estimator for rows with bound above est_min (tables may then
@@ -246,6 +250,11 @@ void run_size_bins(const MatView &A, const MatView &B, const MatView &C, const C
                    unsigned mask, cudaStream_t s, int num_sms);
 void run_numeric(int sr, const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,
                  const cudaStream_t *ss, int ns, int num_sms);
+// The bins a handle launches after a batch whose control block is c, given
+// the bins it launched (on) and whether it has narrowed them before: the
+// first time, the bins that got rows; then those plus every bin a row was
+// redirected from.  The global dense bin is always on.
+unsigned long long next_bin_mask(const Ctl &c, unsigned long long on, bool narrowed);
 void init_dense_scratch(int sr, void *acc, uint32_t *mask, int64_t entries, int64_t words, cudaStream_t s);
 // Accumulator slots a row of bin `bin` gets (hash table or dense row of m
 // columns; 0 for the thread-merge bins, which keep no table).

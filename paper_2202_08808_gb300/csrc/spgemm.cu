@@ -165,6 +165,15 @@ __device__ __forceinline__ int pick_bin(long long ubc, int alen, const CJob &J, 
     return pick_table_bin(table_need, J, ub);
 }
 
+// A row whose bin b is not launched by this pipeline goes to the global
+// dense bin, which takes rows of any size and width; b is recorded so that
+// the host launches it from the next captured pipeline on.
+__device__ __forceinline__ int gate_bin(const CJob &J, Ctl *ctl, int b) {
+    if (b < 0 || ((J.bin_on >> b) & 1ull)) return b;
+    atomicOr(&ctl->bins_wanted, 1ull << b);
+    return BIN_GD;
+}
+
 // Append the calling lanes' rows i (of C) to their bins b (b < 0: none), one
 // atomic per distinct bin in the warp.
 __device__ __forceinline__ void append_bins(const CJob &J, Ctl *ctl, int b, int32_t i) {
@@ -259,7 +268,7 @@ __device__ __forceinline__ void size_long_row(const MatView &A, const MatView &B
             push_est(J, ctl, i, alen, bmax, ub);
         } else if (ub > 0) {
             const long long need = J.sizing == SIZE_COUNT ? (long long)C.len[i] : ubc;
-            const int b = pick_bin(ubc, alen, J, need, ub);
+            const int b = gate_bin(J, ctl, pick_bin(ubc, alen, J, need, ub));
             if (!(b == BIN_CDENSE && (ub > SPLIT_MIN || alen > SPLIT_A) && claim_split(J, ctl, i)))
                 J.bins[(int64_t)b * J.bin_cap + atomic_add_ll2(&ctl->bin_count[b], 1)] = i;
         }
@@ -354,7 +363,7 @@ __global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView
         const bool to_est = valid && wants_est(J, ub, ubc, t8);
         long long need = ubc;
         if (J.sizing == SIZE_COUNT && valid) need = C.len[i];
-        int b = (valid && ub > 0 && !to_est && !direct) ? pick_bin(ubc, alen, J, need, ub) : -1;
+        int b = (valid && ub > 0 && !to_est && !direct) ? gate_bin(J, ctl, pick_bin(ubc, alen, J, need, ub)) : -1;
         if (b == BIN_CDENSE && (ub > SPLIT_MIN || alen > SPLIT_A) && claim_split(J, ctl, i)) b = -1;
         append_bins(J, ctl, b, i);
         if (to_est) push_est(J, ctl, i, alen, bmax, ub);
@@ -403,7 +412,7 @@ __global__ void __launch_bounds__(128) k_est_bins(CJob J, Ctl *ctl, unsigned mas
             if (need > ubc) need = ubc;
             if (need < e.z) need = e.z;
             if (need < 1) need = 1;
-            b = pick_table_bin(need, J, (long long)e.w);
+            b = gate_bin(J, ctl, pick_table_bin(need, J, (long long)e.w));
         }
         append_bins(J, ctl, b, i);
     }
@@ -1931,15 +1940,16 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
     // streams in turn, so that a small bin never waits behind a large one
     // of a stream it shares unless there are more bins than streams
     int k = 0;
+    auto on = [&](int b) { return ((J.bin_on >> b) & 1ull) != 0; };
     auto next = [&]() {
         const int j = k++;
         return (j == 0 || ns == 1) ? ss[0] : ss[1 + (j - 1) % (ns - 1)];
     };
     // with the group sort on, its first bin takes the rows of sparse
     // products and the first stream
-    if (J.sort_max > 0) launch_group_sort<SR, 8>(A, B, C, J, ctl, mask, BIN_S64, next(), num_sms);
-    if (J.sort_max > 64) launch_group_sort<SR, 16>(A, B, C, J, ctl, mask, BIN_S128, next(), num_sms);
-    if (J.sort_max > 128) launch_group_sort<SR, 32>(A, B, C, J, ctl, mask, BIN_S256, next(), num_sms);
+    if (J.sort_max > 0 && on(BIN_S64)) launch_group_sort<SR, 8>(A, B, C, J, ctl, mask, BIN_S64, next(), num_sms);
+    if (J.sort_max > 64 && on(BIN_S128)) launch_group_sort<SR, 16>(A, B, C, J, ctl, mask, BIN_S128, next(), num_sms);
+    if (J.sort_max > 128 && on(BIN_S256)) launch_group_sort<SR, 32>(A, B, C, J, ctl, mask, BIN_S256, next(), num_sms);
     {
         // shared memory for the bin's bound only: at a bound of 49 three
         // blocks of 128 threads fit an SM with double values (two at 64),
@@ -1959,8 +1969,8 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
         };
         // rows the group sort takes leave the merge bins empty
         if (J.tm_k > 0 && J.sort_max < MERGE_UB) {
-            launch_merge((int)BIN_T8, std::max(J.tm_ub, 1));
-            if (J.tm_ub < MERGE_UB) launch_merge((int)BIN_T64, MERGE_UB);
+            if (on(BIN_T8)) launch_merge((int)BIN_T8, std::max(J.tm_ub, 1));
+            if (J.tm_ub < MERGE_UB && on(BIN_T64)) launch_merge((int)BIN_T64, MERGE_UB);
         }
     }
     if (J.dense_mode) {
@@ -1988,20 +1998,21 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
         }
         return;
     }
-    launch_group_hash<SR, 6, 16, 8>(A, B, C, J, ctl, mask, BIN_G16, next(), num_sms);
-    launch_group_hash<SR, 5, 8, 8>(A, B, C, J, ctl, mask, BIN_G8, next(), num_sms);
-    launch_group_hash<SR, 7, 32, 8>(A, B, C, J, ctl, mask, BIN_W128, next(), num_sms);
-    launch_group_hash<SR, 8, 32, 8>(A, B, C, J, ctl, mask, BIN_W256, next(), num_sms);
-    launch_group_hash<SR, 9, 32, 4>(A, B, C, J, ctl, mask, BIN_W512, next(), num_sms);
-    launch_group_hash<SR, 10, 32, 4>(A, B, C, J, ctl, mask, BIN_W1024, next(), num_sms);
-    launch_cta_hash<SR, 11>(A, B, C, J, ctl, mask, BIN_C2048, next(), num_sms);
-    launch_cta_hash<SR, 12>(A, B, C, J, ctl, mask, BIN_C4096, next(), num_sms);
-    launch_cta_hash<SR, 13>(A, B, C, J, ctl, mask, BIN_C8192, next(), num_sms);
-    launch_cta_hash<SR, 14>(A, B, C, J, ctl, mask, BIN_C16384, next(), num_sms);
-    launch_cluster_hash<SR, 13, 2>(A, B, C, J, ctl, mask, BIN_K2, next(), num_sms);
-    launch_cluster_hash<SR, 13, 4>(A, B, C, J, ctl, mask, BIN_K4, next(), num_sms);
-    launch_cluster_hash<SR, 13, 8>(A, B, C, J, ctl, mask, BIN_K8, next(), num_sms);
-    launch_cluster_hash<SR, 14, 8>(A, B, C, J, ctl, mask, BIN_K8L, next(), num_sms);
+    if (on(BIN_G16)) launch_group_hash<SR, 6, 16, 8>(A, B, C, J, ctl, mask, BIN_G16, next(), num_sms);
+    if (on(BIN_G8)) launch_group_hash<SR, 5, 8, 8>(A, B, C, J, ctl, mask, BIN_G8, next(), num_sms);
+    if (on(BIN_W128)) launch_group_hash<SR, 7, 32, 8>(A, B, C, J, ctl, mask, BIN_W128, next(), num_sms);
+    if (on(BIN_W256)) launch_group_hash<SR, 8, 32, 8>(A, B, C, J, ctl, mask, BIN_W256, next(), num_sms);
+    if (on(BIN_W512)) launch_group_hash<SR, 9, 32, 4>(A, B, C, J, ctl, mask, BIN_W512, next(), num_sms);
+    if (on(BIN_W1024)) launch_group_hash<SR, 10, 32, 4>(A, B, C, J, ctl, mask, BIN_W1024, next(), num_sms);
+    if (on(BIN_C2048)) launch_cta_hash<SR, 11>(A, B, C, J, ctl, mask, BIN_C2048, next(), num_sms);
+    if (on(BIN_C4096)) launch_cta_hash<SR, 12>(A, B, C, J, ctl, mask, BIN_C4096, next(), num_sms);
+    if (on(BIN_C8192)) launch_cta_hash<SR, 13>(A, B, C, J, ctl, mask, BIN_C8192, next(), num_sms);
+    if (on(BIN_C16384)) launch_cta_hash<SR, 14>(A, B, C, J, ctl, mask, BIN_C16384, next(), num_sms);
+    if (on(BIN_K2)) launch_cluster_hash<SR, 13, 2>(A, B, C, J, ctl, mask, BIN_K2, next(), num_sms);
+    if (on(BIN_K4)) launch_cluster_hash<SR, 13, 4>(A, B, C, J, ctl, mask, BIN_K4, next(), num_sms);
+    if (on(BIN_K8)) launch_cluster_hash<SR, 13, 8>(A, B, C, J, ctl, mask, BIN_K8, next(), num_sms);
+    if (on(BIN_K8L)) launch_cluster_hash<SR, 14, 8>(A, B, C, J, ctl, mask, BIN_K8L, next(), num_sms);
+    // the global dense bin is always launched: rows of bins that are off go there
     launch_k(k_num_gdense<SR>, grid_for(J.gd_ctas, J.rows_hint, 1), 512, 0, next(), A, B, C, J, ctl, mask, (int)BIN_GD);
 }
 
@@ -2024,6 +2035,13 @@ int64_t bin_table_slots(int bin, int64_t m) {
         case BIN_GD: case BIN_WDENSE: case BIN_CDENSE: case BIN_DSPLIT: return m;
         default: return 0;  // the thread-merge bins stage the row's products, no table
     }
+}
+
+unsigned long long next_bin_mask(const Ctl &c, unsigned long long on, bool narrowed) {
+    unsigned long long used = c.bins_wanted | (1ull << BIN_GD);
+    for (int b = 0; b < BIN_COUNT; b++)
+        if (c.bin_count[b] > 0) used |= 1ull << b;
+    return narrowed ? (on | used) : used;
 }
 
 void run_numeric(int sr, const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,

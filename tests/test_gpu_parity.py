@@ -603,17 +603,21 @@ def test_read_affected_in_one_call(dspg, sr, bloom):
 
 
 @pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
-def test_captured_pipeline_serves_uneven_sizes(dspg, sr):
+def test_captured_pipeline_serves_uneven_sizes(dspg, sr, monkeypatch):
     """Batches of different sizes within one launch size (a multiple of 1024
     up to 16384, powers of two beyond): after the first two, every batch
     replays the same captured pipeline (no new kernels are captured), which
     reads each batch's own length on the device; every result matches the
-    oracle.  Sizes cross the cluster sort's limit too (LSD path)."""
+    oracle.  Sizes cross the cluster sort's limit too (LSD path).  Every
+    recompute bin is launched here (a batch whose rows first reach a bin
+    that is off is captured anew: test_bins_off_go_to_global_dense)."""
     n = 3000
     A = random_csr(n, n, 10, 311, sr)
     # room in the arenas, so that no buffer moves (which would retire the
     # captured pipeline) during the sequence
+    monkeypatch.setenv("DSPG_ALL_BINS", "1")
     g = dspg.DynamicSpGEMM(A, arena_headroom=4.0)
+    monkeypatch.delenv("DSPG_ALL_BINS")
     Ao = OMat.from_csr(A)
     Co = Ao.multiply(Ao)
     for sizes in ([700, 900, 1000, 13, 333, 1024, 1], [20000, 17000, 30000, 16385]):
@@ -627,3 +631,52 @@ def test_captured_pipeline_serves_uneven_sizes(dspg, sr):
         # (a buffer that still has to grow once costs one more of each)
         assert r1["eager"] - r0["eager"] <= 2 and r1["captured"] - r0["captured"] <= 2, (r0, r1)
         assert r1["replayed"] - r0["replayed"] >= len(sizes) - 4, (r0, r1)
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_bins_off_go_to_global_dense(dspg, sr, monkeypatch):
+    """After its first batch a handle launches only the recompute bins that
+    batch used (plus the global dense bin).  A first batch confined to a
+    low-degree corner of an R-MAT square leaves most bins off; the next,
+    spread over the hubs, sends the rows of the bins that are off to the
+    global dense bin (seen in its larger tables against a handle that
+    launches every bin), and turns those bins on.  C' and R match the oracle
+    after every batch on both handles."""
+    A, _ = rmat_symmetric(12, 16, (0.57, 0.19, 0.19, 0.05), seed=9, kind=sr)
+    g = dspg.DynamicSpGEMM(A)
+    monkeypatch.setenv("DSPG_ALL_BINS", "1")
+    g_all = dspg.DynamicSpGEMM(A)
+    monkeypatch.delenv("DSPG_ALL_BINS")
+    Ao = OMat.from_csr(A)
+    deg = np.diff(A.rowptr)
+    # an entry (i, j) with both ends of degree 1 or 2: few affected rows, few products
+    rows = np.repeat(np.arange(A.nrows), deg)
+    pick = np.flatnonzero((deg[rows] <= 2) & (deg[A.col] <= 2))
+    assert pick.size > 0
+    p = pick[0]
+    val = A.val[p:p + 1].copy()
+    first = Batch(np.array([rows[p]], np.int32), np.array([A.col[p]], np.int32), val + 1,
+                  np.array([OP_SET], np.uint8))
+    batches = [first] + [random_batch(A.nrows, A.ncols, 600, 40 + k, sr, A=None, dup_frac=0.2) for k in range(3)]
+    slots = []
+    for k, b in enumerate(batches):
+        Co = Ao.multiply(Ao)
+        st = _apply_both(g, Ao, Co, b)
+        st_all = g_all.apply_batch(b)
+        assert st_all["affected_rows"] == st["affected_rows"]
+        Ao.apply(b)
+        _check_state(g, Ao, None, f"gated batch {k}")
+        _check_state(g_all, Ao, None, f"all-bins batch {k}")
+        slots.append((st["table_slots"], st_all["table_slots"]))
+    # the second batch's hub rows went to the global dense bin (m slots each)
+    assert slots[1][0] > slots[1][1], slots
+    # once the bins the batches need are on, batches of one launch size replay
+    r0 = g.run_counts()
+    for k in range(4):
+        b = random_batch(A.nrows, A.ncols, 600, 60 + k, sr, A=None, dup_frac=0.2)
+        Co = Ao.multiply(Ao)
+        _apply_both(g, Ao, Co, b)
+        Ao.apply(b)
+    _check_state(g, Ao, None, "gated, bins learned")
+    r1 = g.run_counts()
+    assert r1["replayed"] - r0["replayed"] >= 2, (r0, r1)
