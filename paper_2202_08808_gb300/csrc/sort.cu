@@ -248,6 +248,176 @@ k_cluster_sort(const InArgs *in, int64_t nrows, int64_t ncols, int sr, bool chec
         if (e < nv) write_sorted(out, rank[e], x[e] >> ib, x[e] & imask, dead[e], cb, val, op, sr);
 }
 
+// ------------------------------------------------- cluster radix path
+//
+// Batches of more than 8192 entries (up to 16384) where clusters of 16 CTAs
+// are allowed: the same one-launch contract as k_cluster_sort, but an LSD
+// radix sort across the cluster instead of the bitonic network and the
+// cross-tile rank searches, whose work grows with the number of tiles.  The
+// words start in arrival order (word p of the batch in slot p mod 1024 of
+// CTA p / 1024) and go through passes over the key's digits (at most 8 bits
+// each, as few passes as the key's width needs).  Each pass:
+//  * every warp ranks its 2 x 32 slots by digit: the lanes holding the same
+//    digit are found with one ballot per digit bit, and a per-warp
+//    shared-memory counter per digit carries ranks from the first 32 slots
+//    to the next, which keeps slot order among equal digits;
+//  * the CTA turns the warps' counts into per-warp offsets and its digit
+//    totals, which the other CTAs read through distributed shared memory
+//    (one cluster barrier);
+//  * each CTA derives, per digit, the words of smaller digits in the whole
+//    cluster plus those of the same digit in lower CTAs, and every word is
+//    stored straight into the slot of its new position, in the CTA that
+//    owns it (distributed shared memory; a second barrier).
+// The sort is stable, so equal keys keep arrival order; a word is dead when
+// the word after it (in the next CTA for a tile's last slot) has its key.
+// The output is written at the words' final positions, consecutive across a
+// warp's lanes.  On GB300 it takes a 10^4-entry batch in about 26 us against
+// 31 us for k_cluster_sort (16384 entries: 29 against 43 us), and is slower
+// below about 8192 entries.
+
+constexpr int CS_DIG = 256;  // digit counters (at most 8-bit digits)
+constexpr int CS_MAXC = 16;  // CTAs of the radix path's cluster
+
+// dynamic shared memory of k_cluster_radix<NT>: the tile, the per-warp digit
+// counters, the CTA's digit totals, the digit bases and the scan's warp sums
+static size_t cluster_radix_smem(int nt) {
+    return (size_t)nt * CS_EPT * sizeof(uint64_t) + ((size_t)(nt / 32) * CS_DIG + 2 * CS_DIG + 32) * sizeof(uint32_t);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_cluster_radix(const InArgs *in, int64_t nrows, int64_t ncols, int sr, bool check_values, SortOut out, Ctl *ctl,
+                unsigned skip_mask, int cb, int ib, int kb) {
+    pdl_begin();
+    constexpr int TILE = NT * CS_EPT;
+    constexpr int NW = NT / 32;
+    extern __shared__ uint64_t cr_smem[];
+    uint64_t *tile = cr_smem;                          // TILE words: this CTA's slots
+    uint32_t *wc = (uint32_t *)(cr_smem + TILE);      // NW x CS_DIG per-warp counts, then offsets
+    uint32_t *tot = wc + NW * CS_DIG;                  // this CTA's count per digit (read by the cluster)
+    uint32_t *base = tot + CS_DIG;                     // first position of each digit's words of this CTA
+    uint32_t *wsum = base + CS_DIG;                    // warp sums of the digit scan
+    cg::cluster_group cl = cg::this_cluster();
+    // no early return: every CTA of the cluster must reach every cluster barrier
+    const bool skip = failed(ctl, skip_mask);
+    const int n = (int)in->n;  // the launch covers a bucket of at least n words
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int me = blockIdx.x, nt = gridDim.x;
+    // slot of word e of this thread: w * 64 + e * 32 + lane
+    uint64_t x[CS_EPT];
+#pragma unroll
+    for (int e = 0; e < CS_EPT; e++) {
+        const int gi = me * TILE + w * 32 * CS_EPT + e * 32 + lane;
+        uint64_t word = ~uint64_t(0);  // padding sorts last
+        if (!skip && gi < n) {
+            const int32_t r = in->row[gi], c = in->col[gi];
+            const uint8_t o = in->op[gi];
+            const bool ok = entry_ok(r, c, o, in->val, gi, nrows, ncols, sr, check_values);
+            if (!ok) set_status(ctl, ST_INVALID);
+            const uint64_t key = ok ? (((uint64_t)(uint32_t)r << cb) | (uint32_t)c) : 0;
+            word = (key << ib) | (uint64_t)gi;
+        }
+        x[e] = word;
+    }
+    const int passes = (kb + 7) / 8;
+    const int width = passes > 0 ? (kb + passes - 1) / passes : 0;
+    const int nd = 1 << width;
+    uint32_t *mine = wc + w * CS_DIG;
+    for (int p = 0; p < passes; p++) {
+        const int shift = ib + p * width;
+        for (int d = lane; d < nd; d += 32) mine[d] = 0;
+        __syncwarp();
+        unsigned dg[CS_EPT];
+        uint32_t lr[CS_EPT];
+#pragma unroll
+        for (int e = 0; e < CS_EPT; e++) {
+            dg[e] = (unsigned)(x[e] >> shift) & (unsigned)(nd - 1);
+            unsigned peers = 0xffffffffu;
+#pragma unroll
+            for (int b = 0; b < 8; b++)
+                if (b < width) {
+                    const bool bit = (dg[e] >> b) & 1u;
+                    const unsigned bal = __ballot_sync(0xffffffffu, bit);
+                    peers &= bit ? bal : ~bal;
+                }
+            const uint32_t before = mine[dg[e]];
+            __syncwarp();  // every lane has read the counter before the group's last lane bumps it
+            lr[e] = before + __popc(peers & lanemask_lt());
+            if (lane == 31 - __clz(peers)) mine[dg[e]] = before + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int d = tid; d < nd; d += NT) {  // per-warp offsets inside the CTA, warp order
+            uint32_t c[NW];
+#pragma unroll
+            for (int ww = 0; ww < NW; ww++) c[ww] = wc[ww * CS_DIG + d];
+            uint32_t run = 0;
+#pragma unroll
+            for (int ww = 0; ww < NW; ww++) {
+                wc[ww * CS_DIG + d] = run;
+                run += c[ww];
+            }
+            tot[d] = run;
+        }
+        cl.sync();  // every CTA's totals are complete
+        if (tid < CS_DIG) {  // warps 0..7: the digit bases (an exclusive scan over digits)
+            const int d = tid;
+            uint32_t t[CS_MAXC];  // the other CTAs' counts, loaded together
+#pragma unroll
+            for (int u = 0; u < CS_MAXC; u++) t[u] = (d < nd && u < nt) ? *cl.map_shared_rank(tot + d, u) : 0u;
+            uint32_t all = 0, lower = 0;
+#pragma unroll
+            for (int u = 0; u < CS_MAXC; u++) {
+                all += t[u];
+                lower += u < me ? t[u] : 0u;
+            }
+            uint32_t inc = all;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) wsum[w] = inc;
+            asm volatile("bar.sync 1, %0;" ::"r"(CS_DIG));  // the scanning warps only
+            uint32_t off = 0;
+            for (int ww = 0; ww < w; ww++) off += wsum[ww];
+            base[d] = off + inc - all + lower;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < CS_EPT; e++) {
+            const uint32_t pos = base[dg[e]] + mine[dg[e]] + lr[e];
+            *cl.map_shared_rank(tile + (pos % TILE), (int)(pos / TILE)) = x[e];
+        }
+        cl.sync();  // every word is in its new slot
+#pragma unroll
+        for (int e = 0; e < CS_EPT; e++) x[e] = tile[w * 32 * CS_EPT + e * 32 + lane];
+    }
+    if (passes == 0) {  // one key: the slots still hold arrival order
+#pragma unroll
+        for (int e = 0; e < CS_EPT; e++) tile[w * 32 * CS_EPT + e * 32 + lane] = x[e];
+        cl.sync();
+    }
+    // a word is dead when the next position holds its key
+    bool dead[CS_EPT];
+#pragma unroll
+    for (int e = 0; e < CS_EPT; e++) {
+        const int slot = w * 32 * CS_EPT + e * 32 + lane;
+        const int pos = me * TILE + slot;
+        uint64_t nx = ~uint64_t(0);
+        if (pos + 1 < n) nx = slot + 1 < TILE ? tile[slot + 1] : *cl.map_shared_rank(tile, me + 1);
+        dead[e] = pos + 1 < n && (nx >> ib) == (x[e] >> ib);
+    }
+    cl.sync();  // no CTA leaves while another still reads its first slot
+    if (skip) return;
+    const uint64_t imask = (uint64_t(1) << ib) - 1;
+#pragma unroll
+    for (int e = 0; e < CS_EPT; e++) {
+        const int pos = me * TILE + w * 32 * CS_EPT + e * 32 + lane;
+        if (pos < n) write_sorted(out, pos, x[e] >> ib, x[e] & imask, dead[e], cb, in->val, in->op, sr);
+    }
+}
+
 // ------------------------------------------------------- multi-CTA path
 
 constexpr int MS_NT = 512;
@@ -404,6 +574,44 @@ void sort_updates(const InArgs *in, int64_t n, int64_t nrows, int64_t ncols, int
                     small_tiles_max = 16;
             }
             cudaGetLastError();  // the queries' errors are not the pipeline's
+        }
+        static int radix_ok = -1;  // clusters of 16 CTAs of the radix kernel allowed
+        if (radix_ok < 0) {
+            radix_ok = 0;
+            if (small_tiles_max == 16 &&
+                cudaFuncSetAttribute(k_cluster_radix<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)cluster_radix_smem(512)) == cudaSuccess &&
+                cudaFuncSetAttribute(k_cluster_radix<512>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                    cudaSuccess) {
+                cudaLaunchConfig_t q = {};
+                q.gridDim = dim3(CS_MAXC);
+                q.blockDim = dim3(512);
+                q.dynamicSmemBytes = cluster_radix_smem(512);
+                int cs = 0;
+                if (cudaOccupancyMaxPotentialClusterSize(&cs, k_cluster_radix<512>, &q) == cudaSuccess && cs >= CS_MAXC)
+                    radix_ok = 1;
+            }
+            cudaGetLastError();
+        }
+        if (radix_ok && n > 8192) {
+            const int tiles = (int)((n + 1023) / 1024);
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)tiles);
+            cfg.blockDim = dim3(512);
+            cfg.dynamicSmemBytes = cluster_radix_smem(512);
+            cfg.stream = s;
+            cudaLaunchAttribute at[2];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = (unsigned)tiles;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            at[1] = pdl_attribute();
+            cfg.attrs = at;
+            cfg.numAttrs = 2;
+            cudaLaunchKernelEx(&cfg, k_cluster_radix<512>, in, nrows, ncols, sr, check_values, out, ctl, skip_mask, cb,
+                               ib, kb);
+            __atomic_fetch_add(&launch_counter(), 1ull, __ATOMIC_RELAXED);
+            return;
         }
         const bool small = n <= (int64_t)1024 * small_tiles_max;
         const int tile = small ? 1024 : 2048;

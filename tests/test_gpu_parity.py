@@ -248,13 +248,17 @@ def test_growth_paths_tight_arena(dspg):
     assert total > 0
 
 
-@pytest.mark.parametrize("nupd", [1023, 1024, 1025, 2049, 6000, 8192, 8193, 10000, 16384, 16385])
-def test_batch_sizes_at_the_sort_tile_bounds(dspg, nupd):
+@pytest.mark.parametrize("nupd,sr", [(1023, PLUS_TIMES_F64), (1024, PLUS_TIMES_F64), (1025, PLUS_TIMES_F64),
+                                     (2049, PLUS_TIMES_F64), (6000, PLUS_TIMES_F64), (8192, PLUS_TIMES_F64),
+                                     (8193, PLUS_TIMES_F64), (10000, PLUS_TIMES_F64), (10000, MIN_PLUS_I32),
+                                     (15000, MIN_PLUS_I32), (16384, PLUS_TIMES_F64), (16385, PLUS_TIMES_F64)])
+def test_batch_sizes_at_the_sort_tile_bounds(dspg, nupd, sr):
     """Batch sizes around the sort's tiles (1024 words per CTA, up to 16 CTAs
     in one cluster where the device allows it, else 2048 words in up to 8;
-    16385 takes the radix path), half of the entries repeating keys, so that
-    a key's last write and its dead copies sit in different tiles."""
-    sr = PLUS_TIMES_F64
+    above 8192 entries the cluster's radix sort where clusters of 16 are
+    allowed; 16385 takes the multi-pass radix path), half of the entries
+    repeating keys, so that a key's last write and its dead copies sit in
+    different tiles."""
     A = er_matrix(3000, 6, seed=43, kind=sr)
     g = dspg.DynamicSpGEMM(A)
     Ao = OMat.from_csr(A)
