@@ -250,7 +250,8 @@ def gpu_arm(args):
                                    torch.from_numpy(b.val).cuda(), torch.from_numpy(b.op).cuda()))
     torch.cuda.synchronize()
 
-    for k in range(args.warmup):  # eager, captured, replayed
+    for k in range(args.warmup):  # eager, captured, replayed; like the timed steps
+        flush.zero_()
         g.apply_batch(dev_batches[k])
     tuned = None
     if args.autotune > 0:
@@ -269,6 +270,7 @@ def gpu_arm(args):
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     launches0 = pkg.kernel_launches()
+    runs0 = g.run_counts()
     barrier()
     wall0 = time.perf_counter()
     for k in range(args.steps):
@@ -277,6 +279,7 @@ def gpu_arm(args):
         g.apply_batch(dev_batches[args.warmup + k])
         ev1[k].record(stream)
     launches = pkg.kernel_launches() - launches0
+    runs1 = g.run_counts()
     barrier()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
@@ -317,7 +320,6 @@ def gpu_arm(args):
         ts = []
         for k in range(3):
             flush.zero_()
-            torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -368,12 +370,14 @@ def gpu_arm(args):
             # a new launch size runs eagerly once and is captured on its
             # second batch: the median is over the three replays after those
             bs = W.batches(5, 9000 + nupd, nupd)
+            dbs = [type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(),
+                           torch.from_numpy(b.val).cuda(), torch.from_numpy(b.op).cuda()) for b in bs]
+            torch.cuda.synchronize()
             ts = []
-            for kb, b in enumerate(bs):
-                db = type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(),
-                             torch.from_numpy(b.val).cuda(), torch.from_numpy(b.op).cuda())
+            for kb, db in enumerate(dbs):
+                # as in the timed steps: the flush is enqueued before the
+                # start event, without a host synchronisation in between
                 flush.zero_()
-                torch.cuda.synchronize()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -401,7 +405,6 @@ def gpu_arm(args):
             db = type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(),
                          torch.from_numpy(b.val).cuda(), torch.from_numpy(b.op).cuda())
             flush.zero_()
-            torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -451,7 +454,8 @@ def gpu_arm(args):
                        "batch_entries": len(host_batches[0]),
                        "l2": "flushed before every timed step (256 MiB write)", "parallelism": f"replicas x{world}"},
             "latency_ms": {"mean": round(statistics.mean(lat), 4), "p50": round(statistics.median(lat), 4),
-                           "p99": round(float(np.percentile(lat, 99)), 4)},
+                           "p99": round(float(np.percentile(lat, 99)), 4), "max": round(max(lat), 4)},
+            "graph_runs_timed": {k: runs1[k] - runs0[k] for k in runs0},
             "static_recompute_ms": round(static_med, 3),
             "static_runs_ms": {k: round(v, 3) for k, v in static_runs.items()},
             "static_best": min(static_runs, key=static_runs.get),
@@ -503,7 +507,6 @@ def cusparse_static(A, B, flush, stream):
         ts, nnz = [], None
         for _ in range(3):
             flush.zero_()
-            torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -536,7 +539,6 @@ def masked_leg(args, flush, stream, scale=20):
 
     def timed(g, db):
         flush.zero_()
-        torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)

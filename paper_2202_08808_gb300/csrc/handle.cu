@@ -427,7 +427,8 @@ struct dspg_handle {
     // buffer allocates for the call instead of holding that memory
     struct ReadWs {
         DBuf<int32_t> rows, lens, c, r;
-        DBuf<int64_t> rp, scan, listed, st, so, chunk_cnt, chunk_ex, chunk_tmp;
+        DBuf<int64_t> rp, scan, listed, st, so, chunk_cnt, chunk_ex, chunk_tmp, long_l, huge_l;
+        DBuf<ReadOut> res;
         DBuf<unsigned> n_listed;
         DBuf<char> v;
         DBuf<uint64_t> k0, k1;
@@ -476,6 +477,7 @@ struct dspg_handle {
     unsigned long long bin_on = ~0ull;
     bool bins_narrowed = false;  // bin_on has been cut to the bins batches used
     bool gate_bins = true;       // DSPG_ALL_BINS=1: every bin, always
+    bool direct_read = true;     // DSPG_NO_DIRECT_READ=1: reads always stage on the device and copy
     dspg_tuning tune{8, 64, 8, 0, 1024, 16384, 64};  // row bins of the recompute
     int sizing = DSPG_SIZE_BOUND;               // how the recompute's tables are sized
     int est_min = 128;
@@ -1329,6 +1331,64 @@ void load_operand(dspg_handle *h, DevMat &M, const dspg_csr *m, bool trans, cuda
 // The fill of a read: rows (device, n of them; NULL = all) of M whose
 // row pointers rp (device, n + 1) and total nnz are known, gathered, sorted
 // by column and copied out (V, vs: the view and value size read).
+// The device address of page-locked host memory the GPU can reach (over the
+// C2C link on this system), or null for any other pointer.
+void *device_view(void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// The listed rows (lh: indices into the row list, rph: its row pointers on
+// the host) of oc/ov, sorted by column on the device with the LSD radix sort,
+// in groups of at most 2^28 entries (the radix sort's indices are 32-bit).
+void sort_listed_host(dspg_handle *h, const DevMat &M, const int64_t *rp, const std::vector<int64_t> &lh,
+                      const int64_t *rph, int32_t *oc, void *ov, int vs, cudaStream_t s) {
+    const size_t nl = lh.size();
+    std::vector<int64_t> lo(nl), hi(nl);
+    for (size_t k = 0; k < nl; k++) {
+        lo[k] = rph[lh[k]];
+        hi[k] = rph[lh[k] + 1];
+    }
+    const int cb = bits_for(std::max<int64_t>(M.ncols, 2));
+    size_t k0 = 0;
+    while (k0 < nl) {
+        std::vector<int64_t> pre(1, 0);
+        size_t k1 = k0;
+        while (k1 < nl && (k1 == k0 || pre.back() + (hi[k1] - lo[k1]) <= (int64_t(1) << 28))) {
+            pre.push_back(pre.back() + (hi[k1] - lo[k1]));
+            k1++;
+        }
+        const int nk = (int)(k1 - k0);
+        const int64_t total = pre.back();
+        DBuf<int64_t> d_pre, d_list, scan_tmp, scan_out;
+        DBuf<uint64_t> kk0, kk1;
+        DBuf<uint32_t> ii0, ii1, counts;
+        DBuf<int32_t> tcol;
+        DBuf<char> tval;
+        d_pre.reserve(nk + 1);
+        d_list.reserve(nk);
+        kk0.reserve(total); kk1.reserve(total); ii0.reserve(total); ii1.reserve(total);
+        int64_t cnt;
+        sort_tmp_sizes(total, &cnt);
+        counts.reserve(cnt);
+        scan_out.reserve(cnt + 1);
+        scan_tmp.reserve(scan_tmp_entries(cnt) + 1);
+        tcol.reserve(total);
+        tval.reserve(total * std::max(vs, 1));
+        CK(cudaMemcpyAsync(d_pre.p, pre.data(), sizeof(int64_t) * (nk + 1), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_list.p, lh.data() + k0, sizeof(int64_t) * nk, cudaMemcpyHostToDevice, s));
+        SortScratch w{kk0.p, kk1.p, ii0.p, ii1.p, counts.p, scan_tmp.p, scan_out.p, tcol.p, (void *)tval.p};
+        sort_listed_rows(rp, d_list.p, d_pre.p, nk, total, cb, oc, ov, vs, w, s, h->num_sms);
+        CK(cudaStreamSynchronize(s));
+        k0 = k1;
+    }
+}
+
 void fill_rows_out(dspg_handle *h, DevMat &M, const MatView &V, int vs, const int32_t *rows, int64_t n, int64_t *rp,
                    int64_t nnz, int64_t *rowptr, int32_t *col, void *val, int on_device, cudaStream_t s) {
     // rows too long to sort in shared memory are listed, then sorted together
@@ -1345,48 +1405,11 @@ void fill_rows_out(dspg_handle *h, DevMat &M, const MatView &V, int vs, const in
         CK(cudaStreamSynchronize(s));
         if (nl == 0) return;
         if ((int64_t)nl > list_cap) throw Err(DSPG_ERR_CUDA, "more long rows than the read can hold");
-        std::vector<int64_t> lh(nl), lo(nl), hi(nl), rph(n + 1);
+        std::vector<int64_t> lh(nl), rph(n + 1);
         CK(cudaMemcpyAsync(lh.data(), listed, sizeof(int64_t) * nl, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(rph.data(), rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        for (unsigned k = 0; k < nl; k++) {
-            lo[k] = rph[lh[k]];
-            hi[k] = rph[lh[k] + 1];
-        }
-        // groups of rows of at most 2^28 entries (the radix sort's indices are 32-bit)
-        const int cb = bits_for(std::max<int64_t>(M.ncols, 2));
-        unsigned k0 = 0;
-        while (k0 < nl) {
-            std::vector<int64_t> pre(1, 0);
-            unsigned k1 = k0;
-            while (k1 < nl && (k1 == k0 || pre.back() + (hi[k1] - lo[k1]) <= (int64_t(1) << 28))) {
-                pre.push_back(pre.back() + (hi[k1] - lo[k1]));
-                k1++;
-            }
-            const int nk = (int)(k1 - k0);
-            const int64_t total = pre.back();
-            DBuf<int64_t> d_pre, d_list, scan_tmp, scan_out;
-            DBuf<uint64_t> kk0, kk1;
-            DBuf<uint32_t> ii0, ii1, counts;
-            DBuf<int32_t> tcol;
-            DBuf<char> tval;
-            d_pre.reserve(nk + 1);
-            d_list.reserve(nk);
-            kk0.reserve(total); kk1.reserve(total); ii0.reserve(total); ii1.reserve(total);
-            int64_t cnt;
-            sort_tmp_sizes(total, &cnt);
-            counts.reserve(cnt);
-            scan_out.reserve(cnt + 1);
-            scan_tmp.reserve(scan_tmp_entries(cnt) + 1);
-            tcol.reserve(total);
-            tval.reserve(total * std::max(vs, 1));
-            CK(cudaMemcpyAsync(d_pre.p, pre.data(), sizeof(int64_t) * (nk + 1), cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(d_list.p, lh.data() + k0, sizeof(int64_t) * nk, cudaMemcpyHostToDevice, s));
-            SortScratch w{kk0.p, kk1.p, ii0.p, ii1.p, counts.p, scan_tmp.p, scan_out.p, tcol.p, (void *)tval.p};
-            sort_listed_rows(rp, d_list.p, d_pre.p, nk, total, cb, oc, ov, vs, w, s, h->num_sms);
-            CK(cudaStreamSynchronize(s));
-            k0 = k1;
-        }
+        sort_listed_host(h, M, rp, lh, rph.data(), oc, ov, vs, s);
     };
     if (on_device) {
         CK(cudaMemcpyAsync(rowptr, rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
@@ -1656,7 +1679,11 @@ void recover(dspg_handle *h, cudaStream_t s) {
 
 // After a row-path batch: the bins the recompute launches from now on (the
 // bins that got rows, and those a row was redirected from to the global
-// dense bin).  A change bumps the epoch, so the next batch is captured anew.
+// dense bin).  A captured pipeline is right under any mask (its sizing pass
+// and its launches share the mask it was captured with), so the first
+// narrowing keeps the captured pipelines (later captures take the narrower
+// mask); turning a bin on bumps the epoch, so that the next batch is
+// captured anew and its rows leave the global dense bin.
 void learn_bins(dspg_handle *h) {
     if (!h->gate_bins || h->bloom) return;
     const Ctl &c = *h->hctl;
@@ -1664,11 +1691,10 @@ void learn_bins(dspg_handle *h) {
     for (int b = 0; b < NBINS; b++) any |= c.bin_count[b] > 0;
     if (!any) return;  // nothing was binned (no affected rows, or the delta path)
     const unsigned long long next = next_bin_mask(c, h->bin_on, h->bins_narrowed);
+    const bool widened = h->bins_narrowed && next != h->bin_on;
     h->bins_narrowed = true;
-    if (next != h->bin_on) {
-        h->bin_on = next;
-        h->epoch++;
-    }
+    h->bin_on = next;
+    if (widened) h->epoch++;
 }
 
 // Every bin on again (the thresholds or the sizing changed which bins rows take).
@@ -2292,6 +2318,7 @@ dspg_status dspg_build_form(dspg_handle **out, const dspg_csr *A, const dspg_csr
         CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
         if (const char *env = getenv("DSPG_ALL_BINS")) h->gate_bins = env[0] == '0';
+        if (const char *env = getenv("DSPG_NO_DIRECT_READ")) h->direct_read = env[0] == '0';
         for (int k = 0; k < NUM_SIDE; k++) {
             CK(cudaStreamCreateWithFlags(&h->nstr[k], cudaStreamNonBlocking));
             CK(cudaEventCreateWithFlags(&h->evNum[k], cudaEventDisableTiming));
@@ -2538,6 +2565,49 @@ dspg_status dspg_read_affected_C(dspg_handle *h, int64_t rows_cap, int64_t nnz_c
         int32_t *lens = read_scratch(w.lens, lens_l, n);
         lens_of_rows(w.r.p, n, h->C.len.p, lens, s);
         scan_i32_to_i64(lens, rp, n, lens_scan, s);
+        // page-locked host buffers: the rows go straight into them, in column
+        // order, with one synchronisation (unless R was not collected in
+        // order, which the read finds on the device and leaves to the path below)
+        int32_t *dcol = rows && !on_device && h->direct_read && rows_cap >= n ? (int32_t *)device_view(col) : nullptr;
+        void *dval = (dcol && val && h->vsize) ? device_view(val) : nullptr;
+        if (dcol && (!val || !h->vsize || dval)) {
+            w.res.reserve(1);
+            w.long_l.reserve(std::max<int64_t>(n, 1));
+            w.huge_l.reserve(std::max<int64_t>(n, 1));
+            w.c.reserve(std::max<int64_t>(nnz_cap, 1));
+            w.v.reserve(std::max<int64_t>(nnz_cap, 1) * std::max(h->vsize, 1));
+            CK(cudaMemsetAsync(w.res.p, 0, sizeof(ReadOut), s));
+            read_rows_direct(w.r.p, n, h->C.view(), h->vsize, rp, w.chunk_ex.p + nch, nnz_cap, dcol, dval, w.c.p,
+                             (void *)w.v.p, w.long_l.p, w.huge_l.p, w.res.p, s, h->num_sms);
+            ReadOut ro{};
+            CK(cudaMemcpyAsync(&ro, w.res.p, sizeof(ReadOut), cudaMemcpyDeviceToHost, s));
+            if (n > 0) CK(cudaMemcpyAsync(rows, w.r.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(rowptr, rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (!(ro.flags & READ_UNORDERED)) {
+                *nrows_out = n;
+                *nnz_out = ro.nnz;
+                if (ro.flags & READ_TOO_SMALL)
+                    throw Err(DSPG_ERR_INVALID, "read_affected_C: buffers too small (need " + std::to_string(n) +
+                                                    " rows, " + std::to_string(ro.nnz) + " entries)");
+                if (ro.n_huge > 0) {  // rows over 16384 entries out of order: sorted in the scratch, then copied
+                    std::vector<int64_t> lh(ro.n_huge);
+                    CK(cudaMemcpyAsync(lh.data(), w.huge_l.p, sizeof(int64_t) * ro.n_huge, cudaMemcpyDeviceToHost, s));
+                    CK(cudaStreamSynchronize(s));
+                    std::sort(lh.begin(), lh.end());
+                    sort_listed_host(h, h->C, rp, lh, rowptr, w.c.p, (void *)w.v.p, h->vsize, s);
+                    for (int64_t x : lh) {
+                        const int64_t lo = rowptr[x], len = rowptr[x + 1] - rowptr[x];
+                        CK(cudaMemcpyAsync(col + lo, w.c.p + lo, sizeof(int32_t) * len, cudaMemcpyDeviceToHost, s));
+                        if (val && h->vsize)
+                            CK(cudaMemcpyAsync((char *)val + lo * h->vsize, w.v.p + lo * h->vsize, (size_t)h->vsize * len,
+                                               cudaMemcpyDeviceToHost, s));
+                    }
+                    CK(cudaStreamSynchronize(s));
+                }
+                return DSPG_OK;
+            }
+        }
         int64_t tot[2] = {0, 0};
         CK(cudaMemcpyAsync(&tot[0], w.chunk_ex.p + nch, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(&tot[1], rp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));

@@ -298,6 +298,25 @@ struct SortScratch {  // for `total` entries: keys, indices (two each), radix co
 void sort_listed_rows(const int64_t *rowptr, const int64_t *listed, const int64_t *pre, int nl, int64_t total,
                       int cb, int32_t *col, void *val, int vsize, const SortScratch &w, cudaStream_t s, int num_sms);
 void lens_of_rows(const int32_t *rows, int64_t n, const int32_t *len, int32_t *out, cudaStream_t s);
+// A read of rows of C straight into page-locked host buffers (layout.cu):
+// what it found, for the one host synchronisation after it.
+struct ReadOut {
+    long long nnz;   // entries of the rows (rp[n])
+    unsigned n_long; // rows of more than 64 entries (listed)
+    unsigned n_huge; // of those, rows over 16384 entries that are out of order (left in the scratch)
+    unsigned flags;  // READ_TOO_SMALL, READ_UNORDERED: nothing was written
+    unsigned pad;
+};
+enum : unsigned { READ_TOO_SMALL = 1u, READ_UNORDERED = 2u };
+// rows[0..n) (ascending, R from its collection when r_total is given: its
+// chunk total must equal n), their row pointers rp (device, rp[n] = entries)
+// -> out_col/out_val (device addresses of page-locked host memory, at least
+// nnz_cap entries; out_val may be null).  Scratch: nnz_cap entries; lists:
+// n entries each; res zeroed by the caller.
+void read_rows_direct(const int32_t *rows, int64_t n, const MatView &M, int vsize, const int64_t *rp,
+                      const int64_t *r_total, int64_t nnz_cap, int32_t *out_col, void *out_val, int32_t *scr_col,
+                      void *scr_val, int64_t *long_list, int64_t *huge_list, ReadOut *res, cudaStream_t s,
+                      int num_sms);
 // R (n rows, as collected: ascending within each 8192-row chunk, chunk c's
 // rows at chunk[2c] with chunk[2c+1] of them) into out in row order; cnt and
 // ex (nch + 1) and tmp (scan_tmp_entries(nch) + 1) are scratch, and ex[nch]

@@ -211,6 +211,32 @@ __global__ void k_sort_short_rows(const int64_t *rowptr, int64_t n, int32_t *col
     }
 }
 
+// Bitonic sort by column of the N (a power of two) keys in sk, with their
+// values in sv when hv, in the block's shared memory (padding keys INT32_MAX).
+template <typename T>
+__device__ __forceinline__ void block_sort_row(int32_t *sk, T *sv, int N, bool hv) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int size = 2; size <= N; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int q = tid; q < N / 2; q += nt) {
+                const int a = 2 * q - (q & (stride - 1)), b = a + stride;
+                const bool up = (a & size) == 0;
+                const int32_t ka = sk[a], kb = sk[b];
+                if ((ka > kb) == up) {
+                    sk[a] = kb;
+                    sk[b] = ka;
+                    if (hv) {
+                        const T t = sv[a];
+                        sv[a] = sv[b];
+                        sv[b] = t;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(512) k_sort_long_rows(const int64_t *rowptr, int64_t n, int32_t *col, T *val,
                                                         unsigned *n_listed, int64_t *listed, int64_t list_cap) {
@@ -240,31 +266,162 @@ __global__ void __launch_bounds__(512) k_sort_long_rows(const int64_t *rowptr, i
             if (val && e < len) sv[e] = val[lo + e];
         }
         __syncthreads();
-        for (int size = 2; size <= N; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int q = tid; q < N / 2; q += nt) {
-                    const int a = 2 * q - (q & (stride - 1)), b = a + stride;
-                    const bool up = (a & size) == 0;
-                    const int32_t ka = sk[a], kb = sk[b];
-                    if ((ka > kb) == up) {
-                        sk[a] = kb;
-                        sk[b] = ka;
-                        if (val) {
-                            const T t = sv[a];
-                            sv[a] = sv[b];
-                            sv[b] = t;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
+        block_sort_row<T>(sk, sv, N, val != nullptr);
         for (int e = tid; e < len; e += nt) {
             col[lo + e] = sk[e];
             if (val) val[lo + e] = sv[e];
         }
         __syncthreads();
     }
+}
+
+// ------------------------------------------- direct read into host memory
+//
+// Rows of C read straight into the caller's page-locked host buffers, which
+// the GPU reaches over the C2C link (out_col, out_val: their device
+// addresses), with one host synchronisation for the whole read.  Each warp
+// takes a row: a row of up to SORT_SHORT entries is put in column order in
+// registers (ranked by shuffles unless it is in order already) and written
+// out; a longer row is copied to device scratch at its place and listed for
+// k_long_rows_out.  Nothing is written when R is not the ordered list of its
+// collection (r_total != n) or the entries do not fit the caller's buffers;
+// the flags say which, and the caller takes the general path.
+template <typename T>
+__global__ void k_gather_sort_out(const int32_t *rows, int64_t n, MatView M, const int64_t *rp,
+                                  const int64_t *r_total, int64_t nnz_cap, int32_t *out_col, T *out_val,
+                                  int32_t *scr_col, T *scr_val, int64_t *long_list, ReadOut *res) {
+    pdl_begin();
+    const int64_t nnz = rp[n];
+    const unsigned bad = (r_total && *r_total != n ? READ_UNORDERED : 0u) | (nnz > nnz_cap ? READ_TOO_SMALL : 0u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        res->nnz = nnz;
+        if (bad) atomicOr(&res->flags, bad);
+    }
+    if (bad) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const T *mv = (const T *)M.val;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += nwarps) {
+        const int64_t r = rows[x];
+        const int64_t so = M.off[r], d = rp[x];
+        const int L = M.len[r];
+        if (L <= SORT_SHORT) {
+            const int32_t k0 = lane < L ? M.col[so + lane] : INT32_MAX;
+            const int32_t k1 = lane + 32 < L ? M.col[so + lane + 32] : INT32_MAX;
+            T v0 = T(0), v1 = T(0);
+            if (out_val) {
+                if (lane < L) v0 = mv[so + lane];
+                if (lane + 32 < L) v1 = mv[so + lane + 32];
+            }
+            // entry e + 1 after entry e: the next lane's, across the halves at lane 31
+            const int32_t up0 = __shfl_down_sync(0xffffffffu, k0, 1);
+            const int32_t lo1 = __shfl_sync(0xffffffffu, k1, 0);
+            const int32_t up1 = __shfl_down_sync(0xffffffffu, k1, 1);
+            const int32_t n0 = lane == 31 ? lo1 : up0;
+            const bool out_of_order = (lane + 1 < L && k0 > n0) || (lane + 33 < L && k1 > up1);
+            int r0 = lane, r1 = lane + 32;
+            if (__any_sync(0xffffffffu, out_of_order)) {  // rank among the row's (distinct) columns
+                r0 = 0;
+                r1 = 0;
+                for (int j = 0; j < 32; j++) {
+                    const int32_t a = __shfl_sync(0xffffffffu, k0, j), b = __shfl_sync(0xffffffffu, k1, j);
+                    r0 += (a < k0) + (b < k0);
+                    r1 += (a < k1) + (b < k1);
+                }
+            }
+            if (lane < L) {
+                out_col[d + r0] = k0;
+                if (out_val) out_val[d + r0] = v0;
+            }
+            if (lane + 32 < L) {
+                out_col[d + r1] = k1;
+                if (out_val) out_val[d + r1] = v1;
+            }
+        } else {
+            for (int e = lane; e < L; e += 32) {
+                scr_col[d + e] = M.col[so + e];
+                if (out_val) scr_val[d + e] = mv[so + e];
+            }
+            if (lane == 0) long_list[atomicAdd(&res->n_long, 1u)] = x;
+        }
+    }
+}
+
+// The listed rows of more than SORT_SHORT entries, a block each: put in
+// column order in shared memory (unless in order already) and written from
+// the scratch to the caller's buffers; rows over SORT_MAX entries are listed
+// again (huge_list) and left for the host's radix sort of the scratch.
+template <typename T>
+__global__ void __launch_bounds__(512) k_long_rows_out(const int64_t *rp, const int64_t *long_list, const int32_t *scr_col,
+                                                       const T *scr_val, int32_t *out_col, T *out_val,
+                                                       int64_t *huge_list, ReadOut *res) {
+    pdl_begin();
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *sv = (T *)smem;
+    int32_t *sk = (int32_t *)(sv + SORT_MAX);
+    if (res->flags) return;
+    const unsigned nl = res->n_long;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (unsigned j = blockIdx.x; j < nl; j += gridDim.x) {
+        const int64_t x = long_list[j];
+        const int64_t lo = rp[x];
+        const int64_t len = rp[x + 1] - lo;
+        int unsorted = 0;
+        for (int64_t e = tid; e + 1 < len; e += nt) unsorted |= scr_col[lo + e] > scr_col[lo + e + 1];
+        if (!__syncthreads_or(unsorted)) {
+            for (int64_t e = tid; e < len; e += nt) {
+                out_col[lo + e] = scr_col[lo + e];
+                if (out_val) out_val[lo + e] = scr_val[lo + e];
+            }
+            continue;
+        }
+        if (len > SORT_MAX) {
+            if (tid == 0) huge_list[atomicAdd(&res->n_huge, 1u)] = x;
+            continue;
+        }
+        int N = 128;
+        while (N < len) N <<= 1;
+        for (int e = tid; e < N; e += nt) {
+            sk[e] = e < len ? scr_col[lo + e] : INT32_MAX;
+            if (out_val && e < len) sv[e] = scr_val[lo + e];
+        }
+        __syncthreads();
+        block_sort_row<T>(sk, sv, N, out_val != nullptr);
+        for (int e = tid; e < len; e += nt) {
+            out_col[lo + e] = sk[e];
+            if (out_val) out_val[lo + e] = sv[e];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+static void read_rows_direct_t(const int32_t *rows, int64_t n, const MatView &M, const int64_t *rp,
+                               const int64_t *r_total, int64_t nnz_cap, int32_t *out_col, T *out_val, int32_t *scr_col,
+                               T *scr_val, int64_t *long_list, int64_t *huge_list, ReadOut *res, cudaStream_t s,
+                               int num_sms) {
+    launch_k(k_gather_sort_out<T>, blocks_for(std::max<int64_t>(n, 1) * 32, 256, (int64_t)num_sms * 16), 256, 0, s, rows,
+             n, M, rp, r_total, nnz_cap, out_col, out_val, scr_col, scr_val, long_list, res);
+    const size_t smem = (size_t)SORT_MAX * (sizeof(T) + sizeof(int32_t));
+    static bool set = false;
+    if (!set) {
+        cudaFuncSetAttribute(k_long_rows_out<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        set = true;
+    }
+    launch_k(k_long_rows_out<T>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)num_sms * 2)), 512, smem,
+             s, rp, long_list, scr_col, scr_val, out_col, out_val, huge_list, res);
+}
+
+void read_rows_direct(const int32_t *rows, int64_t n, const MatView &M, int vsize, const int64_t *rp,
+                      const int64_t *r_total, int64_t nnz_cap, int32_t *out_col, void *out_val, int32_t *scr_col,
+                      void *scr_val, int64_t *long_list, int64_t *huge_list, ReadOut *res, cudaStream_t s,
+                      int num_sms) {
+    if (vsize == 8)
+        read_rows_direct_t<double>(rows, n, M, rp, r_total, nnz_cap, out_col, (double *)out_val, scr_col,
+                                   (double *)scr_val, long_list, huge_list, res, s, num_sms);
+    else
+        read_rows_direct_t<int32_t>(rows, n, M, rp, r_total, nnz_cap, out_col, (int32_t *)out_val, scr_col,
+                                    (int32_t *)scr_val, long_list, huge_list, res, s, num_sms);
 }
 
 template <typename T>

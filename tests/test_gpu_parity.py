@@ -12,7 +12,7 @@ import pytest
 import oracle
 from oracle import OMat
 from parity import assert_matches, assert_same_pattern, oracle_product
-from workloads import (MIN_PLUS_I32, OP_DELETE, OP_SET, PLUS_TIMES_F64, Batch, bernoulli_sparse, er_batch,
+from workloads import (CSR, MIN_PLUS_I32, OP_DELETE, OP_SET, PLUS_TIMES_F64, Batch, bernoulli_sparse, er_batch,
                        er_matrix, random_batch, random_csr, rmat_edge_batch, rmat_symmetric, stencil7,
                        stencil_batch)
 
@@ -684,3 +684,63 @@ def test_bins_off_go_to_global_dense(dspg, sr, monkeypatch):
     _check_state(g, Ao, None, "gated, bins learned")
     r1 = g.run_counts()
     assert r1["replayed"] - r0["replayed"] >= 2, (r0, r1)
+
+
+def _csr_of_rows(cols_per_row, ncols, sr, rng):
+    rp = np.zeros(len(cols_per_row) + 1, np.int64)
+    rp[1:] = np.cumsum([len(c) for c in cols_per_row])
+    col = np.concatenate([np.sort(np.asarray(c, np.int64)) for c in cols_per_row]).astype(np.int32)
+    nnz = col.shape[0]
+    val = rng.random(nnz) + 0.5 if sr == PLUS_TIMES_F64 else rng.integers(1, 101, nnz).astype(np.int32)
+    return CSR(len(cols_per_row), ncols, rp, col, val)
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_read_affected_rows_of_every_length(dspg, sr, monkeypatch):
+    """The one-call read writes the rows of C' straight into page-locked host
+    arrays: rows of up to 64 entries put in column order in registers (the
+    group sort's rows arrive in order; rows of colliding products from the
+    hash tables do not), longer ones in shared memory, and rows of more than
+    16384 entries out of order (hub rows of A over B rows of ~20 entries,
+    from the cluster tables) by the radix sort.  R and every row equal the
+    oracle's, and the read that stages the rows on the device first."""
+    rng = np.random.default_rng(93)
+    n, k, m = 1200, 4000, 400000
+    bcols = [rng.choice(m, size=int(rng.integers(0, 41)), replace=False) for _ in range(k)]
+    shared = rng.choice(m, size=30, replace=False)
+    for q in range(10):  # B rows 0..9 share their 30 columns: rows of A over them collide
+        bcols[q] = shared
+    B = _csr_of_rows(bcols, m, sr, rng)
+    acols = [rng.choice(np.arange(10, k), size=int(rng.choice([0, 1, 2, 3, 6, 12])), replace=False) for _ in range(n)]
+    for i in range(100, 120):
+        acols[i] = np.arange(10)
+    for i in (5, 600, 1111):
+        acols[i] = rng.choice(np.arange(10, k), size=1000, replace=False)  # hubs
+    A = _csr_of_rows(acols, k, sr, rng)
+    g = dspg.DynamicSpGEMM(A, B)
+    monkeypatch.setenv("DSPG_NO_DIRECT_READ", "1")
+    g_staged = dspg.DynamicSpGEMM(A, B)
+    monkeypatch.delenv("DSPG_NO_DIRECT_READ")
+    Ao, Bo = OMat.from_csr(A), OMat.from_csr(B)
+    for t in range(2):
+        b = random_batch(n, k, 600, 95 + t, sr, A=Ao.to_csr(), dup_frac=0.1)
+        b.row[:23] = np.array([5, 600, 1111] + list(range(100, 120)), np.int32)  # hubs and colliding rows in R
+        b.col[:23] = np.array([10 + t] * 3 + [0] * 20, np.int32)
+        b.op[:23] = OP_SET
+        b.val[:23] = b.val[:23] * 0 + 2
+        g.apply_batch(b)
+        g_staged.apply_batch(b)
+        Ao.apply(b)
+        rows, rp_g, col, val = g.read_affected()
+        rows_s, rp_s, col_s, val_s = g_staged.read_affected()
+        assert np.array_equal(rows, g.last_affected()) and np.array_equal(rows, rows_s)
+        lens_c = np.diff(rp_g)
+        assert lens_c.max() > 16384 and ((lens_c > 64) & (lens_c <= 16384)).any() and (lens_c <= 64).any()
+        orp, ocol, oval = Ao.multiply_rows(Bo, rows)
+        assert np.array_equal(rp_g, orp) and np.array_equal(col, ocol), f"batch {t}: pattern"
+        assert np.array_equal(rp_s, rp_g) and np.array_equal(col_s, col) and np.array_equal(val_s, val)
+        if sr == MIN_PLUS_I32:
+            assert np.array_equal(val, oval)
+        else:
+            _, _, sabs = Ao.multiply_rows(Bo, rows, absval=True)
+            assert np.all(np.abs(val - oval) <= 1e-12 * sabs), f"batch {t}: values"
