@@ -313,6 +313,9 @@ def test_config2_stencil_full_size(dspg):
     S_o = Ao.multiply(Ao, absval=True).to_csr()
     err = np.abs(Cg.val - C_o.val)
     assert np.all(err <= 1e-12 * S_o.val)
+    # and relative to the entry itself (no entry of this C cancels: S / |C| <= 3.4 here)
+    nz = C_o.val != 0
+    assert (err[nz] / np.abs(C_o.val[nz])).max() <= 1e-12
 
 
 def test_config3_rmat_minplus_full_size(dspg):

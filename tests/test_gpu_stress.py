@@ -33,6 +33,9 @@ def _rows_against_oracle(g, Ao, rows, what):
     orp, ocol, oval = Ao.multiply_rows(Ao, rows)
     _, _, sabs = Ao.multiply_rows(Ao, rows, absval=True)
     assert_rows_match(rp, col, val, orp, ocol, oval, sabs, what=what)
+    # relative to the entry itself where the entry does not cancel much (|C| >= S / 100)
+    keep = np.abs(oval) * 100 >= sabs
+    assert (np.abs(val - oval)[keep] / np.abs(oval[keep])).max(initial=0.0) <= 1e-12, what
 
 
 def test_rmat18_consecutive_1e4_edge_batches(dspg):
