@@ -280,27 +280,39 @@ __device__ __forceinline__ void size_long_row(const MatView &A, const MatView &B
     __syncthreads();
 }
 
-// One thread per row of R sums the B-row lengths of its A entries (rows
-// longer than SIZE_SHORT are summed by the whole warp afterwards, rows
-// longer than SIZE_LONG by the whole block at the end of its round); then the warp hands out
-// bin slots (and, for the static product, the row's place in a fresh C)
-// with one atomic per counter.  With SIZE_COUNT the tables are sized by
-// C.len (an exact count from a count_only pass); with SIZE_LEARNED rows
-// whose bound exceeds est_min go to the estimate list instead of a bin.
+// One thread per row of R sums the B-row lengths of its A entries; rows
+// longer than SIZE_SHORT are listed and summed by a whole warp each (the
+// block's warps share the list), rows longer than SIZE_LONG by the whole
+// block at the end of its round; then the warp hands out bin slots (and,
+// for the static product, the row's place in a fresh C) with one atomic per
+// counter.  A block takes CH rows a round, CH (32..256) chosen so that R
+// covers the grid: a small R of long rows (the hubs a skewed graph's batch
+// touches) spreads over as many SMs as it can instead of queueing in a few
+// warps.  With SIZE_COUNT the tables are sized by C.len (an exact count from
+// a count_only pass); with SIZE_LEARNED rows whose bound exceeds est_min go
+// to the estimate list instead of a bin.
 __global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask) {
     pdl_begin();
     __shared__ long long s_long[256];  // this block's rows (indices into R) with long A rows
     __shared__ long long s_sum[8], s_max[8];
-    __shared__ int s_nlong;
+    __shared__ int s_nlong, s_nmid;
+    __shared__ int s_mid[256];          // this round's rows (thread index) of more than SIZE_SHORT A entries
+    __shared__ long long s_moff[256], s_mub[256], s_mmax[256];
+    __shared__ int s_mlen[256];
     if (failed(ctl, mask)) return;
     const long long nR = ctl->n_affected;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long per = (nR + gridDim.x - 1) / gridDim.x;
+    const int CH = per >= 256 ? 256 : (per <= 32 ? 32 : (int)((per + 31) & ~31LL));
     long long prod_acc = 0, a_acc = 0;
-    if (threadIdx.x == 0) s_nlong = 0;
+    if (threadIdx.x == 0) {
+        s_nlong = 0;
+        s_nmid = 0;
+    }
     __syncthreads();
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < nR; base += (long long)gridDim.x * blockDim.x) {
+    for (long long base = (long long)blockIdx.x * CH; base < nR; base += (long long)gridDim.x * CH) {
         const long long t = base + threadIdx.x;
-        bool valid = t < nR;
+        bool valid = (int)threadIdx.x < CH && t < nR;
         // the row structure was just rewritten by the commit: read through L2
         // (ld.global.cg), not a possibly stale L1 line
         const int32_t i = valid ? __ldcg(J.R + t) : 0;
@@ -323,28 +335,40 @@ __global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView
                 ub += l;
                 bmax = l > bmax ? l : bmax;
             }
-        unsigned lm = __ballot_sync(0xffffffffu, valid && lng);
-        while (lm) {
-            const int src = __ffs(lm) - 1;
-            lm &= lm - 1;
-            const int64_t o = __shfl_sync(0xffffffffu, aoff, src);
-            const int l = __shfl_sync(0xffffffffu, alen, src);
-            long long s = 0, mx = 0;
+        if (valid && lng) {
+            const int k = atomicAdd(&s_nmid, 1);
+            s_mid[k] = (int)threadIdx.x;
+            s_moff[threadIdx.x] = aoff;
+            s_mlen[threadIdx.x] = alen;
+        }
+        // the listed rows, a warp each, all of the block's warps at once (a
+        // round without such rows skips the pass and its second barrier)
+        const int nmid = __syncthreads_or(valid && lng) ? s_nmid : 0;
+        for (int k = warp; k < nmid; k += (int)(blockDim.x >> 5)) {
+            const int r = s_mid[k];
+            const int64_t o = s_moff[r];
+            const int l = s_mlen[r];
+            long long sm = 0, mx = 0;
             for (int a = lane; a < l; a += 32) {
                 const long long x = __ldcg(B.len + __ldcg(A.col + o + a));
-                s += x;
+                sm += x;
                 mx = x > mx ? x : mx;
             }
-            s = warp_sum<long long>(s);
+            sm = warp_sum<long long>(sm);
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) {
                 const long long y = __shfl_xor_sync(0xffffffffu, mx, d);
                 mx = y > mx ? y : mx;
             }
-            if (lane == src) {
-                ub = s;
-                bmax = mx;
+            if (lane == 0) {
+                s_mub[r] = sm;
+                s_mmax[r] = mx;
             }
+        }
+        if (nmid > 0) __syncthreads();
+        if (valid && lng) {
+            ub = s_mub[threadIdx.x];
+            bmax = s_mmax[threadIdx.x];
         }
         const long long ubc = ub < J.m ? ub : J.m;
         if (J.static_mode) {
@@ -375,7 +399,10 @@ __global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView
         const int nl = s_nlong;
         for (int k = 0; k < nl; k++) size_long_row(A, B, C, J, ctl, s_long[k], s_sum, s_max);
         __syncthreads();
-        if (threadIdx.x == 0) s_nlong = 0;
+        if (threadIdx.x == 0) {
+            s_nlong = 0;
+            s_nmid = 0;
+        }
         __syncthreads();
     }
     prod_acc = warp_sum<long long>(prod_acc);
