@@ -151,6 +151,7 @@ enum : int {
     DBG_STAGE = 4,      // merge staging written past its capacity
     DBG_ARENA = 5,      // a committed row of A, B or the pattern past its arena
     DBG_MASK_ROOM = 6,  // the masked merge wrote a row of C past its room
+    DBG_R_ROW = 7,      // a row of R is not a row of A, or its entries lie outside A's arena
 };
 __device__ __forceinline__ bool dcheck(Ctl *ctl, bool ok, int code, long long idx) {
 #if DSPG_DEBUG

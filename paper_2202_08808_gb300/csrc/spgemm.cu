@@ -227,7 +227,8 @@ __device__ __forceinline__ void size_long_row(const MatView &A, const MatView &B
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const int a = a0 + u * (int)blockDim.x + tid;
-            l[u] = a < alen ? (long long)__ldcg(B.len + __ldcg(A.col + aoff + a)) : 0;
+            const int32_t k = a < alen ? __ldcg(A.col + aoff + a) : 0;
+            l[u] = a < alen && dcheck(ctl, k >= 0 && k < B.nrows, DBG_B_ROW, aoff + a) ? (long long)__ldcg(B.len + k) : 0;
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
@@ -315,9 +316,18 @@ __global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView
         bool valid = (int)threadIdx.x < CH && t < nR;
         // the row structure was just rewritten by the commit: read through L2
         // (ld.global.cg), not a possibly stale L1 line
-        const int32_t i = valid ? __ldcg(J.R + t) : 0;
-        const int64_t aoff = valid ? __ldcg(A.off + i) : 0;
-        const int alen = valid ? __ldcg(A.len + i) : 0;
+        int32_t i = valid ? __ldcg(J.R + t) : 0;
+        if (valid && !dcheck(ctl, i >= 0 && i < A.nrows, DBG_R_ROW, t)) {
+            valid = false;
+            i = 0;
+        }
+        int64_t aoff = valid ? __ldcg(A.off + i) : 0;
+        int alen = valid ? __ldcg(A.len + i) : 0;
+        if (valid && !dcheck(ctl, aoff >= 0 && alen >= 0 && aoff + alen <= A.arena_cap, DBG_R_ROW, i)) {
+            valid = false;
+            aoff = 0;
+            alen = 0;
+        }
         // dense accumulators: a row with more than SPLIT_A A entries is split,
         // whatever its product count, so it needs no sum (its products are
         // counted by the split kernel); its bound for the static layout is m
@@ -331,7 +341,8 @@ __global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView
         if (valid && !lng && !direct)
 #pragma unroll 8
             for (int a = 0; a < alen; a++) {
-                const long long l = __ldcg(B.len + __ldcg(A.col + aoff + a));
+                const int32_t k = __ldcg(A.col + aoff + a);
+                const long long l = dcheck(ctl, k >= 0 && k < B.nrows, DBG_B_ROW, aoff + a) ? __ldcg(B.len + k) : 0;
                 ub += l;
                 bmax = l > bmax ? l : bmax;
             }
@@ -350,7 +361,8 @@ __global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView
             const int l = s_mlen[r];
             long long sm = 0, mx = 0;
             for (int a = lane; a < l; a += 32) {
-                const long long x = __ldcg(B.len + __ldcg(A.col + o + a));
+                const int32_t k = __ldcg(A.col + o + a);
+                const long long x = dcheck(ctl, k >= 0 && k < B.nrows, DBG_B_ROW, o + a) ? __ldcg(B.len + k) : 0;
                 sm += x;
                 mx = x > mx ? x : mx;
             }
@@ -762,7 +774,8 @@ k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned m
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = (long long)blockIdx.x * TM_NT + threadIdx.x; it < cnt; it += (long long)gridDim.x * TM_NT) {
-        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        if (!dcheck(ctl, i >= 0 && i < A.nrows, DBG_R_ROW, it)) i = 0;  // debug build: a bad list entry fails the batch
         const int64_t aoff = A.off[i];
         const int alen = A.len[i];
         const int64_t off = C.off[i];  // independent of the A and B loads: issued with them
@@ -866,7 +879,8 @@ k_num_group_sort(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = ((long long)blockIdx.x * GS_NT + threadIdx.x) / G; it < cnt; it += ngroups) {
-        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        if (!dcheck(ctl, i >= 0 && i < A.nrows, DBG_R_ROW, it)) i = 0;  // debug build: a bad list entry fails the batch
         const int64_t aoff = A.off[i];
         const int alen = A.len[i];
         int base = 0;  // products placed so far (the same on every lane of the group)
@@ -1094,7 +1108,8 @@ k_num_group_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
     }
     __syncwarp(gmask);
     for (long long it = (long long)blockIdx.x * NG + g; it < cnt; it += (long long)gridDim.x * NG) {
-        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        if (!dcheck(ctl, i >= 0 && i < A.nrows, DBG_R_ROW, it)) i = 0;  // debug build: a bad list entry fails the batch
         bool ok = true;
         unsigned fresh = 0;  // slots this lane claimed: the row's length, summed over the group
         group_products<SR, G>(A, B, i, gmask, [&](int32_t j, T v) {
@@ -1214,7 +1229,8 @@ k_num_cta_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask,
     if (tid == 0) s_n = 0;
     __syncthreads();
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
-        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        if (!dcheck(ctl, i >= 0 && i < A.nrows, DBG_R_ROW, it)) i = 0;  // debug build: a bad list entry fails the batch
         bool ok = true;
         int fresh = 0;  // slots this thread claimed; their sum is the row's length
         block_products<SR>(A, B, i, ps, [&](int32_t j, T v) {
@@ -1332,7 +1348,8 @@ k_num_cluster_hash(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned e
     cl.sync();
     long long nnz_acc = 0;
     for (long long it = blockIdx.x / CL; it < cnt; it += nclusters) {
-        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        if (!dcheck(ctl, i >= 0 && i < A.nrows, DBG_R_ROW, it)) i = 0;  // debug build: a bad list entry fails the batch
         if (tid == 0) s_pos = 0;
         bool ok = true;
         // every CTA goes through all of the row's products and keeps those
@@ -1435,7 +1452,8 @@ k_num_gdense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
-        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        if (!dcheck(ctl, i >= 0 && i < A.nrows, DBG_R_ROW, it)) i = 0;  // debug build: a bad list entry fails the batch
         if (tid == 0) s_n = 0;
         __syncthreads();
         block_products<SR>(A, B, i, ps, [&](int32_t j, T v) {
@@ -1566,7 +1584,8 @@ k_num_warp_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
     __syncwarp();
     long long nnz_acc = 0;
     for (long long it = (long long)blockIdx.x * NW + w; it < cnt; it += (long long)gridDim.x * NW) {
-        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        if (!dcheck(ctl, i >= 0 && i < A.nrows, DBG_R_ROW, it)) i = 0;  // debug build: a bad list entry fails the batch
         group_products<SR, 32>(A, B, i, 0xffffffffu, [&](int32_t j, T v) {
             atomicOr(&msk[j >> 5], 1u << (j & 31));
             Sr<SR>::acc(&acc[j], v);
@@ -1619,7 +1638,8 @@ k_num_cta_dense(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask
     __syncthreads();
     long long nnz_acc = 0;
     for (long long it = blockIdx.x; it < cnt; it += gridDim.x) {
-        const int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
+        if (!dcheck(ctl, i >= 0 && i < A.nrows, DBG_R_ROW, it)) i = 0;  // debug build: a bad list entry fails the batch
         group_products<SR, 32>(A, B, i, 0xffffffffu, [&](int32_t j, T v) {
             atomicOr(&msk[j >> 5], 1u << (j & 31));
             Sr<SR>::acc(&acc[j], v);
