@@ -192,6 +192,7 @@ constexpr int SIZE_LONG = 512;   // up to this by a warp, longer ones by the who
 constexpr long long SPLIT_MIN = 8192;  // dense mode: rows with more products, or with more than
 constexpr int SPLIT_A = 256;           // SPLIT_A A entries, are split in chunks (k_num_dsplit)
 constexpr int SPLIT_CHUNK = 2048;      // A entries per work item of a split row
+constexpr int DS_NT = 256;             // threads of a split-kernel block
 
 // Dense mode: claim a split slot for a row with very many products; false
 // when all slots are taken (the row then goes to the CTA dense bin).
@@ -1746,8 +1747,8 @@ __global__ void __launch_bounds__(1024) k_split_prep(MatView A, CJob J, Ctl *ctl
     if (threadIdx.x == 0) J.sp_pre[cnt] = carry;
 }
 
-template <int SR>
-__global__ void __launch_bounds__(512)
+template <int SR, int NT>
+__global__ void __launch_bounds__(NT)
 k_num_dsplit(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, int mp) {
     pdl_begin();
     using T = typename Sr<SR>::T;
@@ -1761,7 +1762,7 @@ k_num_dsplit(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
     T *acc = (T *)smem;
     uint32_t *msk = (uint32_t *)(acc + mp);
     T *Cv = (T *)C.val;
-    for (int s = tid; s < mp; s += 512) acc[s] = Sr<SR>::zero();
+    for (int s = tid; s < mp; s += NT) acc[s] = Sr<SR>::zero();
     if (tid < 32) msk[tid] = 0u;
     __syncthreads();
     long long cnt = ctl->bin_count[BIN_DSPLIT];
@@ -1797,7 +1798,7 @@ k_num_dsplit(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
             atomicOr(&msk[j >> 5], 1u << (j & 31));
             Sr<SR>::acc(&acc[j], v);
             prods++;
-        }, a_lo + (tid >> 5) * 32, a_hi, 512);
+        }, a_lo + (tid >> 5) * 32, a_hi, NT);
         pending++;
         if (c + 1 < nch && w + 1 < w1) continue;  // the next item is this row's next chunk: keep accumulating
         __syncthreads();
@@ -1805,7 +1806,7 @@ k_num_dsplit(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
         uint32_t *gmsk = J.sp_mask + slot * nw;
         // fold: each present column into the global row, each mask word once;
         // then one barrier, the mask reset and the row's chunk counter
-        for (int j = tid; j < mp; j += 512) {
+        for (int j = tid; j < mp; j += NT) {
             const uint32_t word = msk[j >> 5];
             if ((j & 31) == 0 && word) atomicOr(&gmsk[j >> 5], word);
             if (word & (1u << (j & 31))) {
@@ -1848,7 +1849,7 @@ k_num_dsplit(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask, i
                 }
             }
             __syncthreads();
-            for (int j = tid; j < mp; j += 512) gacc[j] = Sr<SR>::zero();
+            for (int j = tid; j < mp; j += NT) gacc[j] = Sr<SR>::zero();
             if (tid < nw) gmsk[tid] = 0u;
             if (tid == 0) {
                 if (s_dest >= 0) C.len[i] = s_n;
@@ -2041,7 +2042,9 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
             const cudaStream_t ss = next();
             const unsigned early = mask & (ST_INVALID | ST_AB_STAGE | ST_AB_ARENA);
             launch_k(k_split_prep, 1, 1024, 0, ss, A, J, ctl, early);
-            launch_k(k_num_dsplit<SR>, (unsigned)(2 * num_sms), 512, smem_c, ss, A, B, C, J, ctl, early, mp);
+            // blocks of DS_NT threads, 1024 threads an SM: a row's fold waits for fewer warps
+            launch_k(k_num_dsplit<SR, DS_NT>, (unsigned)((1024 / DS_NT) * num_sms), DS_NT, smem_c, ss, A, B, C, J,
+                     ctl, early, mp);
         }
         return;
     }

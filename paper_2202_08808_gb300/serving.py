@@ -231,6 +231,7 @@ class Server:
         # (then the loop reads first and admits after, instead of admitting
         # twice)
         avg_wave, blocked = 1.0, 0.0
+        turn = 0
         t0 = clock()
         while nxt < len(order) or queue or inflight is not None:
             now = clock() - t0
@@ -250,7 +251,13 @@ class Server:
                     self._union.copy_(self._wave_union)
                 else:
                     self._union.zero_()
-                limit = max(2, int(2 * avg_wave + 1))
+                # a footprint costs about a detection pass, and the ones of
+                # candidates left in the queue are computed again next turn
+                # (A changes in between): while waves hold one request, a turn
+                # examines the head only, and every fourth turn a few more,
+                # so that waves can grow again
+                turn += 1
+                limit = 1 if (avg_wave < 1.2 and turn % 4) else max(2, int(2 * avg_wave + 1))
                 wave, taken = self._admit(queue, run_stream, limit)
                 if inflight is not None:
                     blocked = 0.8 * blocked + 0.2 * (0.0 if wave else 1.0)
