@@ -1983,19 +1983,31 @@ template <int SR>
 static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, const CJob &J, Ctl *ctl, unsigned mask,
                           const cudaStream_t *ss, int ns, int num_sms) {
     using T = typename Sr<SR>::T;
-    // the first kernel (the thread-merge bin, the bulk of the rows of
-    // sparse products) has ss[0] to itself; the others take the remaining
-    // streams in turn, so that a small bin never waits behind a large one
-    // of a stream it shares unless there are more bins than streams
+    // the first kernel (the bin of the bulk of the rows of sparse products)
+    // has ss[0] to itself; the others take the remaining streams in turn,
+    // so that a small bin never waits behind a large one of a stream it
+    // shares unless there are more bins than streams
     int k = 0;
     auto on = [&](int b) { return ((J.bin_on >> b) & 1ull) != 0; };
     auto next = [&]() {
         const int j = k++;
         return (j == 0 || ns == 1) ? ss[0] : ss[1 + (j - 1) % (ns - 1)];
     };
-    // with the group sort on, its first bin takes the rows of sparse
-    // products and the first stream
-    if (J.sort_max > 0 && on(BIN_S64)) launch_group_sort<SR, 8>(A, B, C, J, ctl, mask, BIN_S64, next(), num_sms);
+    // with the group sort on, its 64-product bin takes the rows of sparse
+    // products and the first stream.  Its grid is one resident wave that
+    // fills every SM, so kernels launched after it wait for it: with dense
+    // accumulators it is launched last, so that the split kernel of the
+    // long rows (the longest kernel there) starts first (the R-MAT 20
+    // step: 0.329 to 0.311 ms); on the hash path first, as the empty grids
+    // of the small bins would otherwise be dispatched ahead of it (a
+    // one-update stencil step: 0.070 to 0.075 ms)
+    const bool s64 = J.sort_max > 0 && on(BIN_S64);
+    const bool s64_last = s64 && J.dense_mode;
+    if (s64_last) k = 1;
+    auto launch_s64 = [&]() {
+        if (s64_last) launch_group_sort<SR, 8>(A, B, C, J, ctl, mask, BIN_S64, ss[0], num_sms);
+    };
+    if (s64 && !s64_last) launch_group_sort<SR, 8>(A, B, C, J, ctl, mask, BIN_S64, next(), num_sms);
     if (J.sort_max > 64 && on(BIN_S128)) launch_group_sort<SR, 16>(A, B, C, J, ctl, mask, BIN_S128, next(), num_sms);
     if (J.sort_max > 128 && on(BIN_S256)) launch_group_sort<SR, 32>(A, B, C, J, ctl, mask, BIN_S256, next(), num_sms);
     {
@@ -2046,6 +2058,7 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
             launch_k(k_num_dsplit<SR, DS_NT>, (unsigned)((1024 / DS_NT) * num_sms), DS_NT, smem_c, ss, A, B, C, J,
                      ctl, early, mp);
         }
+        launch_s64();
         return;
     }
     if (on(BIN_G16)) launch_group_hash<SR, 6, 16, 8>(A, B, C, J, ctl, mask, BIN_G16, next(), num_sms);
@@ -2064,6 +2077,7 @@ static void run_numeric_t(const MatView &A, const MatView &B, const MatView &C, 
     if (on(BIN_K8L)) launch_cluster_hash<SR, 14, 8>(A, B, C, J, ctl, mask, BIN_K8L, next(), num_sms);
     // the global dense bin is always launched: rows of bins that are off go there
     launch_k(k_num_gdense<SR>, grid_for(J.gd_ctas, J.rows_hint, 1), 512, 0, next(), A, B, C, J, ctl, mask, (int)BIN_GD);
+    launch_s64();
 }
 
 int64_t bin_table_slots(int bin, int64_t m) {

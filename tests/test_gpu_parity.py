@@ -741,9 +741,14 @@ def test_read_affected_rows_of_every_length(dspg, sr, monkeypatch):
         assert lens_c.max() > 16384 and ((lens_c > 64) & (lens_c <= 16384)).any() and (lens_c <= 64).any()
         orp, ocol, oval = Ao.multiply_rows(Bo, rows)
         assert np.array_equal(rp_g, orp) and np.array_equal(col, ocol), f"batch {t}: pattern"
-        assert np.array_equal(rp_s, rp_g) and np.array_equal(col_s, col) and np.array_equal(val_s, val)
+        assert np.array_equal(rp_s, rp_g) and np.array_equal(col_s, col)
         if sr == MIN_PLUS_I32:
+            # (min,+) is order-free; (+,.) sums of the hash bins depend on the
+            # order of their shared-memory atomics, so the two handles' values
+            # are each checked against the oracle below instead
+            assert np.array_equal(val_s, val)
             assert np.array_equal(val, oval)
         else:
             _, _, sabs = Ao.multiply_rows(Bo, rows, absval=True)
             assert np.all(np.abs(val - oval) <= 1e-12 * sabs), f"batch {t}: values"
+            assert np.all(np.abs(val_s - oval) <= 1e-12 * sabs), f"batch {t}: staged values"
