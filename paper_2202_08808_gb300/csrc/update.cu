@@ -256,7 +256,11 @@ __global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigne
 
 // The work of the merge copy for block `blk` of `nblk` (a kernel of its own,
 // or a share of the grid of k_detect_merge).
-template <typename T>
+// BATCHED: a row of at most 32 updates takes them a lane each and loads
+// its chunk before any store (rows of thousands of entries and few updates,
+// the hubs of skewed graphs); the fused kernels, whose registers the
+// detection shares, keep a search per entry.
+template <typename T, bool BATCHED>
 __device__ __forceinline__ void merge_copy_blocks(const UpdJob &J, const MatView &M, const Ctl *ctl, long long blk,
                                                   long long nblk) {
     const long long nch = ctl->u[J.which].n_chunk;
@@ -272,8 +276,52 @@ __device__ __forceinline__ void merge_copy_blocks(const UpdJob &J, const MatView
         const int L = M.len[r];
         const int64_t soff = J.m_soff[m];
         const int tins = J.m_nins[m], tdel = J.m_ndel[m];
-        const int p1 = min(L, (part + 1) * CH);
-        for (int p = part * CH + lane; p < p1; p += 32) {
+        const int p0 = part * CH;
+        const int p1 = min(L, p0 + CH);
+        const int nu = hi - lo;  // the row's updates (warp-uniform)
+        if (BATCHED && nu <= 32) {
+            // the row's updates a lane each (position, kind, the deletions
+            // and insertions before it), the chunk's entries loaded together
+            // first; each entry's place then comes from shuffles over the
+            // updates instead of a search in global memory per entry
+            const int upos = lane < nu ? J.pos[lo + lane] : 0;
+            const uint8_t ukind = lane < nu ? J.kind[lo + lane] : (uint8_t)K_NOP;
+            const int udel = lane < nu ? J.delx[lo + lane] : 0;
+            const int uins = lane < nu ? J.insx[lo + lane] : 0;
+            constexpr int PER = CH / 32;
+            const int nit = (p1 - p0 + 31) >> 5;  // rounds of 32 entries in this chunk (warp-uniform)
+            int32_t cc[PER];
+            T vv[PER];
+#pragma unroll
+            for (int u = 0; u < PER; u++) {
+                const int p = p0 + u * 32 + lane;
+                cc[u] = p < p1 ? M.col[base + p] : 0;
+                vv[u] = (sval && p < p1) ? mval[base + p] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < PER; u++) {
+                if (u >= nit) break;
+                const int p = p0 + u * 32 + lane;
+                int lt = 0, le = 0;  // updates at positions below p, and at or below p
+                for (int j = 0; j < nu; j++) {
+                    const int pj = __shfl_sync(0xffffffffu, upos, j);
+                    lt += pj < p;
+                    le += pj <= p;
+                }
+                const uint8_t klast = (uint8_t)__shfl_sync(0xffffffffu, (int)ukind, le > 0 ? le - 1 : 0);
+                const int dsh = __shfl_sync(0xffffffffu, udel, lt < 32 ? lt : 31);
+                const int ish = __shfl_sync(0xffffffffu, uins, le < 32 ? le : 31);
+                const bool hit = le > lt && (klast == K_UPD || klast == K_DEL);
+                if (p >= p1 || hit) continue;  // past the row, deleted, or rewritten by the classify kernel
+                const int dbefore = lt < nu ? dsh : tdel;
+                const int ibefore = le < nu ? ish : tins;
+                const int o = p - dbefore + ibefore;
+                J.st_col[soff + o] = cc[u];
+                if (sval) sval[soff + o] = vv[u];
+            }
+            continue;
+        }
+        for (int p = p0 + lane; p < p1; p += 32) {
             const int q = (int)lower_bound_dev<int32_t>(J.pos, lo, hi, p);
             const int q2 = (int)upper_bound_dev<int32_t>(J.pos, q, hi, p);
             const bool hit = q2 > q && (J.kind[q2 - 1] == K_UPD || J.kind[q2 - 1] == K_DEL);
@@ -291,7 +339,7 @@ template <typename T>
 __global__ void k_merge_copy(UpdJob J, MatView M, const Ctl *ctl, unsigned mask) {
     pdl_begin();
     if (failed(ctl, mask)) return;
-    merge_copy_blocks<T>(J, M, ctl, blockIdx.x, gridDim.x);
+    merge_copy_blocks<T, true>(J, M, ctl, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------- commit
@@ -354,11 +402,26 @@ __device__ __forceinline__ void commit_copy_blocks(const CommitJob &J, const Mat
         const int32_t nl = J.lens[m];
         const int64_t d = J.dest[m];
         const int64_t so = J.soff[m];
-        const int e1 = min(nl, (part + 1) * CH);
+        const int e0 = part * CH;
+        const int e1 = min(nl, e0 + CH);
         if (!dcheck(ctl, d >= 0 && d + nl <= M.arena_cap, DBG_ARENA, r)) continue;
-        for (int e = part * CH + lane; e < e1; e += 32) {
-            M.col[d + e] = J.st_col[so + e];
-            if (mv) mv[d + e] = sv[so + e];
+        // the chunk's entries loaded together, then stored
+        constexpr int PER = CH / 32;
+        int32_t cc[PER];
+        T vv[PER];
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const int e = e0 + u * 32 + lane;
+            cc[u] = e < e1 ? J.st_col[so + e] : 0;
+            vv[u] = (mv && e < e1) ? sv[so + e] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const int e = e0 + u * 32 + lane;
+            if (e < e1) {
+                M.col[d + e] = cc[u];
+                if (mv) mv[d + e] = vv[u];
+            }
         }
         if (part == 0 && lane == 0) {
             M.off[r] = d;
@@ -409,7 +472,7 @@ __global__ void k_detect_merge(MatView AT, DetectBufs D, long long detect_blocks
     pdl_begin();
     if (failed(ctl, mask)) return;
     if (blockIdx.x < detect_blocks) detect_cols_blocks(AT, D, ctl, blockIdx.x, detect_blocks);
-    else merge_copy_blocks<T>(J, M, ctl, blockIdx.x - detect_blocks, gridDim.x - detect_blocks);
+    else merge_copy_blocks<T, false>(J, M, ctl, blockIdx.x - detect_blocks, gridDim.x - detect_blocks);
 }
 
 // The affected rows R from their bitmap: a thread per bitmap word, a block
@@ -478,7 +541,7 @@ k_detect_merge_plan(MatView AT, DetectBufs D, long long nd, UpdJob J, MatView M,
     pdl_begin();
     if (failed(ctl, mask)) return;
     if (blockIdx.x < nd) detect_cols_blocks(AT, D, ctl, blockIdx.x, nd);
-    else if (blockIdx.x < nd + nm) merge_copy_blocks<T>(J, M, ctl, blockIdx.x - nd, nm);
+    else if (blockIdx.x < nd + nm) merge_copy_blocks<T, false>(J, M, ctl, blockIdx.x - nd, nm);
     else commit_plan_blocks(CJ, M, ctl, slack_min, slack_div, blockIdx.x - nd - nm, gridDim.x - nd - nm);
 }
 
