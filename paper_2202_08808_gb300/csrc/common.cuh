@@ -214,6 +214,32 @@ __device__ __forceinline__ int64_t lower_bound_dev(const T *a, int64_t lo, int64
     return lo;
 }
 
+// lower_bound_dev with fewer loads in a row: while more than eight entries
+// remain, seven pivots loaded together split the range into eight; the last
+// eight at most are loaded together and counted.  A search in a row of
+// thousands of entries then waits for about four loads one after another
+// instead of a dozen.
+template <typename T>
+__device__ __forceinline__ int64_t lower_bound_wide(const T *a, int64_t lo, int64_t hi, T x) {
+    while (hi - lo > 8) {
+        const int64_t len = hi - lo;
+        T v[7];  // pivot j at lo + len (j + 1) / 8
+#pragma unroll
+        for (int j = 0; j < 7; j++) v[j] = a[lo + (len * (j + 1)) / 8];
+        int c = 0;  // pivots below x: a prefix of them, a being ascending
+#pragma unroll
+        for (int j = 0; j < 7; j++) c += v[j] < x;
+        const int64_t nlo = c == 0 ? lo : lo + (len * c) / 8 + 1;
+        const int64_t nhi = c == 7 ? hi : lo + (len * (c + 1)) / 8;
+        lo = nlo;
+        hi = nhi;
+    }
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) c += (lo + j < hi) && (a[lo + j] < x);
+    return lo + c;
+}
+
 // First index in [lo, hi) with a[idx] > x.
 template <typename T>
 __device__ __forceinline__ int64_t upper_bound_dev(const T *a, int64_t lo, int64_t hi, T x) {

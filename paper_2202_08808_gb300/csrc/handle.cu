@@ -476,7 +476,6 @@ struct dspg_handle {
     // global dense bin and turns the bin on for the next batch (learn_bins)
     unsigned long long bin_on = ~0ull;
     bool bins_narrowed = false;  // bin_on has been cut to the bins the first batch used
-    bool bins_settled = false;   // a later batch needed a bin that was off: every bin stays on
     bool gate_bins = true;       // DSPG_ALL_BINS=1: every bin, always
     bool direct_read = true;     // DSPG_NO_DIRECT_READ=1: reads always stage on the device and copy
     dspg_tuning tune{8, 64, 8, 0, 1024, 16384, 64};  // row bins of the recompute
@@ -1680,29 +1679,25 @@ void recover(dspg_handle *h, cudaStream_t s) {
 
 // After a row-path batch: which bins the recompute launches from now on.
 // After the first batch that bins rows, only the bins it used (and the
-// global dense bin).  That is a bet on batches alike, as in a stream of
-// batches of one workload: the first time a later batch needs a bin that is
-// off (its rows went to the global dense bin), every bin is turned on for
-// good, so that handles whose batches vary widely (serving requests of many
-// sizes) do not keep narrowing and widening.  A captured pipeline is right
-// under any mask (its sizing pass and its launches share the mask it was
-// captured with), so the narrowing keeps the captured pipelines (later
-// captures take the narrower mask); turning the bins back on bumps the
-// epoch, so that the next batch is captured anew with every bin.
+// global dense bin, which takes rows of any size); later, also every bin
+// whose rows a batch sent to the global dense bin instead.  A captured
+// pipeline is right under any mask (its sizing pass and its launches share
+// the mask it was captured with), so the narrowing keeps the captured
+// pipelines (later captures take the narrower mask); turning a bin on bumps
+// the epoch, so that the next batch is captured anew with it.  The mask
+// only grows after the narrowing, so a handle is captured anew at most once
+// per bin.
 void learn_bins(dspg_handle *h) {
-    if (!h->gate_bins || h->bloom || h->bins_settled) return;
+    if (!h->gate_bins || h->bloom) return;
     const Ctl &c = *h->hctl;
     bool any = c.bins_wanted != 0;
     for (int b = 0; b < NBINS; b++) any |= c.bin_count[b] > 0;
     if (!any) return;  // nothing was binned (no affected rows, or the delta path)
-    if (!h->bins_narrowed) {
-        h->bin_on = next_bin_mask(c, h->bin_on, false);
-        h->bins_narrowed = true;
-    } else if (c.bins_wanted != 0) {
-        h->bin_on = ~0ull;
-        h->bins_settled = true;
-        h->epoch++;
-    }
+    const unsigned long long next = next_bin_mask(c, h->bin_on, h->bins_narrowed);
+    const bool widened = h->bins_narrowed && next != h->bin_on;
+    h->bins_narrowed = true;
+    h->bin_on = next;
+    if (widened) h->epoch++;
 }
 
 // Every bin on again (the thresholds or the sizing changed which bins rows
@@ -1710,7 +1705,6 @@ void learn_bins(dspg_handle *h) {
 void reset_bins(dspg_handle *h) {
     h->bin_on = ~0ull;
     h->bins_narrowed = false;
-    h->bins_settled = false;
     h->epoch++;
 }
 

@@ -287,10 +287,11 @@ __device__ __forceinline__ void size_long_row(const MatView &A, const MatView &B
 // block's warps share the list), rows longer than SIZE_LONG by the whole
 // block at the end of its round; then the warp hands out bin slots (and,
 // for the static product, the row's place in a fresh C) with one atomic per
-// counter.  A block takes CH rows a round, CH (32..256) chosen so that R
-// covers the grid: a small R of long rows (the hubs a skewed graph's batch
-// touches) spreads over as many SMs as it can instead of queueing in a few
-// warps.  With SIZE_COUNT the tables are sized by C.len (an exact count from
+// counter.  A block takes 256 rows a round, or 32 when R has fewer than 32
+// rows a block: a small R of long rows (the hubs a skewed graph's batch
+// touches) then spreads over as many SMs as it can instead of queueing in a
+// few warps (with 64 rows a block the 52 k rows of a stencil step took 21
+// instead of 13 us: four times the blocks, each mostly idle).  With SIZE_COUNT the tables are sized by C.len (an exact count from
 // a count_only pass); with SIZE_LEARNED rows whose bound exceeds est_min go
 // to the estimate list instead of a bin.
 __global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mask) {
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView
     const long long nR = ctl->n_affected;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long per = (nR + gridDim.x - 1) / gridDim.x;
-    const int CH = per >= 256 ? 256 : (per <= 32 ? 32 : (int)((per + 31) & ~31LL));
+    const int CH = per >= 32 ? 256 : 32;  // 32 rows a block only when R is small against the grid
     long long prod_acc = 0, a_acc = 0;
     if (threadIdx.x == 0) {
         s_nlong = 0;

@@ -103,7 +103,7 @@ __global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigne
             for (int x = (int)s; x < hi; x++) {
                 const int32_t c = J.col[x];
                 const uint8_t op = J.op[x];
-                const int p = (int)lower_bound_dev<int32_t>(rc, 0, L, c);
+                const int p = (int)lower_bound_wide<int32_t>(rc, 0, L, c);
                 const uint8_t k = kind_of(op, p < L && rc[p] == c);
                 J.kind[x] = k;
                 J.pos[x] = p;
@@ -172,7 +172,7 @@ __global__ void k_classify(UpdJob J, MatView M, Ctl *ctl, unsigned mask, unsigne
                 if (x < hi2) {
                     const int32_t c = J.col[x];
                     const uint8_t op = J.op[x];
-                    const int p = (int)lower_bound_dev<int32_t>(rc, 0, L2, c);
+                    const int p = (int)lower_bound_wide<int32_t>(rc, 0, L2, c);
                     const uint8_t k = kind_of(op, p < L2 && rc[p] == c);
                     J.kind[x] = k;
                     J.pos[x] = p;

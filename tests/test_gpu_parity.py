@@ -647,8 +647,8 @@ def test_bins_off_go_to_global_dense(dspg, sr, monkeypatch):
     low-degree corner of an R-MAT square leaves most bins off; the next,
     spread over the hubs, sends the rows of the bins that are off to the
     global dense bin (seen in its larger tables against a handle that
-    launches every bin), and turns every bin on for good.  C' and R match
-    the oracle after every batch on both handles."""
+    launches every bin), and turns those bins on.  C' and R match the oracle
+    after every batch on both handles."""
     A, _ = rmat_symmetric(12, 16, (0.57, 0.19, 0.19, 0.05), seed=9, kind=sr)
     g = dspg.DynamicSpGEMM(A)
     monkeypatch.setenv("DSPG_ALL_BINS", "1")
