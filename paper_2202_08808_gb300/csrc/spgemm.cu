@@ -362,6 +362,7 @@ __global__ void __launch_bounds__(256) k_size_bins(MatView A, MatView B, MatView
             const int64_t o = s_moff[r];
             const int l = s_mlen[r];
             long long sm = 0, mx = 0;
+#pragma unroll 4
             for (int a = lane; a < l; a += 32) {
                 const int32_t k = __ldcg(A.col + o + a);
                 const long long x = dcheck(ctl, k >= 0 && k < B.nrows, DBG_B_ROW, o + a) ? __ldcg(B.len + k) : 0;
