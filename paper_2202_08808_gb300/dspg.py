@@ -422,14 +422,33 @@ class DynamicSpGEMM:
         self._check(self._lib.dspg_read_C(self._h, C.byref(nnz), rp.data_ptr(), col.data_ptr(), val.data_ptr(), 1, s))
         return rp, col[: nnz.value], val[: nnz.value]
 
-    def read_affected(self, stream=None):
+    def read_affected(self, stream=None, out=None):
         """(rows, rowptr, col, val) of the last batch's affected rows of C', in
         one call (dspg_read_affected_C): R ascending and its rows canonical,
-        in page-locked host arrays kept at the largest size seen."""
+        in page-locked host arrays sized with room for the next batches.
+        out: caller-owned host arrays (rows int32, rowptr int64 with one more
+        entry than rows, col int32, val of the semiring's type), reused when
+        they hold the result (a loop that reads every batch keeps one set);
+        the result is then views of them."""
         s = _stream(stream)
         n = C.c_int64()
         nnz = C.c_int64()
         cap = getattr(self, "_aff_cap", (0, 0))
+        if out is not None:
+            o_rows, o_rp, o_col, o_val = out
+            if (o_rows.dtype != np.int32 or o_rp.dtype != np.int64 or o_col.dtype != np.int32
+                    or o_val.dtype != _vdtype(self.sr) or o_rp.shape[0] < o_rows.shape[0] + 1
+                    or o_val.shape[0] < o_col.shape[0]):
+                raise ValueError("read_affected: out arrays of the wrong types or sizes")
+            st = self._lib.dspg_read_affected_C(self._h, o_rows.shape[0], o_col.shape[0], C.byref(n), C.byref(nnz),
+                                                o_rows.ctypes.data, o_rp.ctypes.data, o_col.ctypes.data,
+                                                o_val.ctypes.data, 0, s)
+            if st == 0:
+                k, e = n.value, nnz.value
+                return o_rows[:k], o_rp[:k + 1], o_col[:e], o_val[:e]
+            if not (st == 1 and (n.value > o_rows.shape[0] or nnz.value > o_col.shape[0])):
+                self._check(st)
+            cap = (n.value + n.value // 4 + 1, nnz.value + nnz.value // 4 + 1)  # too small: arrays of our own
         for _ in range(2):
             if cap[0] == 0:  # sizes first
                 self._check(self._lib.dspg_read_affected_C(self._h, 0, 0, C.byref(n), C.byref(nnz), None, None, None,

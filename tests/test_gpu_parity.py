@@ -752,3 +752,39 @@ def test_read_affected_rows_of_every_length(dspg, sr, monkeypatch):
             _, _, sabs = Ao.multiply_rows(Bo, rows, absval=True)
             assert np.all(np.abs(val - oval) <= 1e-12 * sabs), f"batch {t}: values"
             assert np.all(np.abs(val_s - oval) <= 1e-12 * sabs), f"batch {t}: staged values"
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_read_affected_into_caller_arrays(dspg, sr):
+    """read_affected(out=...) fills caller-owned arrays: page-locked ones
+    (written from the device directly), pageable ones (staged and copied),
+    and arrays too small for the result (the binding then returns arrays of
+    its own); every result equals the default read and the oracle's rows."""
+    import torch
+    n = 3000
+    A = er_matrix(n, 6, seed=97, kind=sr)
+    g = dspg.DynamicSpGEMM(A)
+    Ao = OMat.from_csr(A)
+    vt = torch.float64 if sr == PLUS_TIMES_F64 else torch.int32
+    vn = np.float64 if sr == PLUS_TIMES_F64 else np.int32
+    pinned = tuple(torch.empty(m, dtype=dt, pin_memory=True).numpy()
+                   for m, dt in ((n, torch.int32), (n + 1, torch.int64), (200000, torch.int32), (200000, vt)))
+    pageable = (np.empty(n, np.int32), np.empty(n + 1, np.int64), np.empty(200000, np.int32), np.empty(200000, vn))
+    small = (np.empty(4, np.int32), np.empty(5, np.int64), np.empty(4, np.int32), np.empty(4, vn))
+    for t, out in enumerate((pinned, pageable, small, pinned)):
+        b = random_batch(n, n, 400, 98 + t, sr, A=Ao.to_csr())
+        g.apply_batch(b)
+        Ao.apply(b)
+        rows, rp, col, val = g.read_affected(out=out)
+        if out is not small:
+            assert rows.base is not None and np.shares_memory(rows, out[0]), "out arrays not used"
+        r2, rp2, c2, v2 = g.read_affected()
+        assert np.array_equal(rows, r2) and np.array_equal(rp, rp2) and np.array_equal(col, c2)
+        assert np.array_equal(val, v2)
+        orp, ocol, oval = Ao.multiply_rows(Ao, rows)
+        assert np.array_equal(rp, orp) and np.array_equal(col, ocol), f"read {t}: pattern"
+        if sr == MIN_PLUS_I32:
+            assert np.array_equal(val, oval)
+        else:
+            _, _, sabs = Ao.multiply_rows(Ao, rows, absval=True)
+            assert np.all(np.abs(val - oval) <= 1e-12 * sabs), f"read {t}: values"
