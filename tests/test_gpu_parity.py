@@ -788,3 +788,25 @@ def test_read_affected_into_caller_arrays(dspg, sr):
         else:
             _, _, sabs = Ao.multiply_rows(Ao, rows, absval=True)
             assert np.all(np.abs(val - oval) <= 1e-12 * sabs), f"read {t}: values"
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_host_batches_page_locked_pageable_and_device(dspg, sr):
+    """The same batches given as page-locked host arrays, pageable host
+    arrays (both copied to the device first) and device arrays (read where
+    they are) leave the same A' and C' as the oracle's, in sizes on both
+    sides of the cluster sort's limits (one CTA, radix cluster, multi-pass)."""
+    import torch
+    n = 3000
+    A = er_matrix(n, 6, seed=103, kind=sr)
+    handles = [dspg.DynamicSpGEMM(A) for _ in range(3)]
+    Ao = OMat.from_csr(A)
+    for t, m in enumerate((500, 9000, 20000)):
+        b = random_batch(n, n, m, 104 + t, sr, A=Ao.to_csr(), dup_frac=0.2)
+        pinned = Batch(*(torch.from_numpy(x).pin_memory().numpy() for x in (b.row, b.col, b.val, b.op)))
+        dev = Batch(*(torch.from_numpy(x).cuda() for x in (b.row, b.col, b.val, b.op)))
+        for g, bb in zip(handles, (pinned, b, dev)):
+            g.apply_batch(bb)
+        Ao.apply(b)
+        for g, what in zip(handles, ("page-locked", "pageable", "device")):
+            _check_state(g, Ao, None, f"batch {t} {what}")
