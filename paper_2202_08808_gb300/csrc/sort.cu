@@ -115,9 +115,12 @@ __device__ __forceinline__ void bitonic_in_thread(uint64_t (&x)[CS_EPT], bool as
 // Bitonic sort of the tile, word e of thread tid at position tid * CS_EPT + e.
 // Merges up to CS_EPT words run inside the thread (unrolled); the larger ones
 // are loops whose steps reach the partner by shuffle (within a warp's span)
-// or through shared memory, so the code stays small.
+// or through shared memory, so the code stays small.  Only the first `span`
+// positions (a power of two, the same across the CTA) hold words: the rest
+// is padding, which sorts last and is already in place, so the merges stop
+// at size span (a one-entry batch then skips the network).
 template <int TILE>
-__device__ __forceinline__ void bitonic_sort_tile(uint64_t (&x)[CS_EPT], uint64_t *own, int tid) {
+__device__ __forceinline__ void bitonic_sort_tile(uint64_t (&x)[CS_EPT], uint64_t *own, int tid, int span) {
 #pragma unroll
     for (int size = 2; size <= CS_EPT; size <<= 1)
 #pragma unroll
@@ -132,7 +135,7 @@ __device__ __forceinline__ void bitonic_sort_tile(uint64_t (&x)[CS_EPT], uint64_
                     x[e | stride] = asc ? umax64(a, b) : umin64(a, b);
                 }
 #pragma unroll 1
-    for (int size = 2 * CS_EPT; size <= TILE; size <<= 1) {
+    for (int size = 2 * CS_EPT; size <= span; size <<= 1) {
 #pragma unroll 1
         for (int stride = size >> 1; stride >= CS_EPT; stride >>= 1) {
             if (stride >= CS_EPT * 32) {  // partner in another warp
@@ -198,8 +201,11 @@ k_cluster_sort(const InArgs *in, int64_t nrows, int64_t ncols, int sr, bool chec
 #pragma unroll
         for (int e = 0; e < CS_EPT; e++) x[e] = ~uint64_t(0);
     }
-    // bitonic sort of the tile: position of x[e] is tid * CS_EPT + e
-    bitonic_sort_tile<TILE>(x, own, tid);
+    // bitonic sort of the tile: position of x[e] is tid * CS_EPT + e; the
+    // merges cover the smallest power of two that holds the tile's words
+    int span = CS_EPT;
+    while (span < cnt) span <<= 1;
+    bitonic_sort_tile<TILE>(x, own, tid, span);
 #pragma unroll
     for (int e = 0; e < CS_EPT; e++) own[tid * CS_EPT + e] = x[e];
     cl.sync();
