@@ -80,7 +80,7 @@ class StencilWorkload:
     grid hops (inserts / deletes / value changes, a third each)."""
     name = "stencil"
     batch = BATCH
-    sweep = (1000, 10000, 100000, 1000000)
+    sweep = (1, 100, 1000, 10000, 100000, 1000000)
     vsize, dtype = 8, "f64"
 
     def __init__(self):
@@ -369,13 +369,14 @@ def gpu_arm(args):
         d2h = rows.nbytes + rp.nbytes + col.nbytes + val.nbytes + 13 * 8
     e2e_mean = statistics.mean(e2e_ms)
 
-    # batch-size sweep (latency and speedup at 10^3 .. 10^6)
+    # batch-size sweep (latency and speedup from one update to 10^6)
     sweep = []
     if not args.no_sweep:
         for nupd in W.sweep:
             # a new launch size runs eagerly once and is captured on its
-            # second batch: the median is over the three replays after those
-            bs = W.batches(5, 9000 + nupd, nupd)
+            # second batch: the median is over the replays after those (ten
+            # up to 10^4 updates, where a step is well under a millisecond)
+            bs = W.batches(12 if nupd <= 10000 else 5, 9000 + nupd, nupd)
             dbs = [type(b)(torch.from_numpy(b.row).cuda(), torch.from_numpy(b.col).cuda(),
                            torch.from_numpy(b.val).cuda(), torch.from_numpy(b.op).cuda()) for b in bs]
             torch.cuda.synchronize()
