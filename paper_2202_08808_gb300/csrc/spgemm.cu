@@ -489,30 +489,6 @@ __device__ __forceinline__ int64_t c_row_dest(const MatView &C, const CJob &J, C
     return d;
 }
 
-// c_row_dest with the row's C.cap and C.off already loaded (the group sort
-// fetches them while the row's products arrive).
-__device__ __forceinline__ int64_t c_row_dest_pre(const MatView &C, const CJob &J, Ctl *ctl, int32_t i, int n,
-                                                  int32_t cap, int64_t o) {
-    if (J.count_only) {
-        C.len[i] = n;
-        return -1;
-    }
-    if (J.static_mode || n <= cap) {
-        if (!dcheck(ctl, o >= 0 && o + n <= C.arena_cap && (J.static_mode || n <= cap), DBG_C_ROOM, i)) return -1;
-        return o;
-    }
-    const int32_t c = slack_cap(n, J.slack_min, J.slack_div);
-    const long long d = atomic_add_ll2(C.top, c);
-    if (d + c > C.arena_cap) {
-        set_status(ctl, ST_C_ARENA);
-        return -1;
-    }
-    C.off[i] = d;
-    C.cap[i] = c;
-    atomic_add_ll2(&ctl->c_reloc, 1);
-    return d;
-}
-
 // --------------------------------------------------- product generators
 
 constexpr int PU = 4;  // products per lane whose B loads are issued together
@@ -876,21 +852,8 @@ k_num_thread_merge(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned m
 // the row in column order.  The words are distinct, so the sort needs no
 // tie rule, and it has no data-dependent branches.  Columns must leave room
 // for the slot bits (sort_cols_ok).
-// The loads that only feed later steps travel as asynchronous copies beside
-// the products' (the group's first lane issues them): the row's C.off and
-// C.cap, wanted only by the write, and the next row's list entry, then its
-// A.off and A.len, wanted only by the next row.  A row then waits on three
-// dependent loads (A entries, B headers, B entries) instead of seven.
 constexpr int GS_EPL = 8;
 constexpr int GS_NT = 256;
-struct GsHdr {          // per group, in shared memory
-    int64_t coff;       // C.off of the current row
-    int64_t naoff;      // A.off of the next row
-    int32_t ccap;       // C.cap of the current row
-    int32_t ni;         // the next row
-    int32_t nalen;      // A.len of the next row
-    int32_t pad;
-};
 
 template <int SR, int G>
 __global__ void __launch_bounds__(GS_NT, 4)
@@ -905,7 +868,6 @@ k_num_group_sort(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
     __shared__ int32_t s_col[GS_NT / G * N];
     __shared__ T s_a[GS_NT / G * N];
     __shared__ T s_b[GS_NT / G * N];
-    __shared__ GsHdr s_hdr[GS_NT / G];
     if (__any_sync(0xffffffffu, failed(ctl, mask))) return;  // a warp leaves as a whole
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1), gw = lane / G;
@@ -913,33 +875,17 @@ k_num_group_sort(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
     int32_t *scol = s_col + (threadIdx.x / G) * N;
     T *sa = s_a + (threadIdx.x / G) * N;
     T *sb = s_b + (threadIdx.x / G) * N;
-    GsHdr *hdr = s_hdr + threadIdx.x / G;
     const long long ngroups = ((long long)gridDim.x * GS_NT) / G;
     const T *Av = (const T *)A.val;
     const T *Bv = (const T *)B.val;
     T *Cv = (T *)C.val;
-    const int32_t *list = J.bins + (int64_t)bin * J.bin_cap;
     long long nnz_acc = 0;
     const long long cnt = ctl->bin_count[bin];
-    long long it = ((long long)blockIdx.x * GS_NT + threadIdx.x) / G;
-    int32_t i = 0;
-    int64_t aoff = 0;
-    int alen = 0;
-    if (it < cnt) {
-        i = list[it];
+    for (long long it = ((long long)blockIdx.x * GS_NT + threadIdx.x) / G; it < cnt; it += ngroups) {
+        int32_t i = J.bins[(int64_t)bin * J.bin_cap + it];
         if (!dcheck(ctl, i >= 0 && i < A.nrows, DBG_R_ROW, it)) i = 0;  // debug build: a bad list entry fails the batch
-        aoff = A.off[i];
-        alen = A.len[i];
-    }
-    for (; it < cnt; it += ngroups) {
-        const long long itn = it + ngroups;
-        if (gl == 0) {
-            if (!J.count_only) {
-                cp_async_8(&hdr->coff, C.off + i);
-                cp_async_4(&hdr->ccap, C.cap + i);
-            }
-            if (itn < cnt) cp_async_4(&hdr->ni, list + itn);
-        }
+        const int64_t aoff = A.off[i];
+        const int alen = A.len[i];
         int base = 0;  // products placed so far (the same on every lane of the group)
         bool over = false;
         for (int a0 = 0; a0 < alen; a0 += G) {
@@ -998,16 +944,11 @@ k_num_group_sort(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
             base += total;
         }
         cp_async_wait_all();  // this lane's copies (it reads only its own slots here)
-        if (gl == 0 && itn < cnt) {  // the next row's A header, in flight while this row is sorted
-            int32_t ni = hdr->ni;
-            if (!dcheck(ctl, ni >= 0 && ni < A.nrows, DBG_R_ROW, itn)) ni = 0;
-            hdr->ni = ni;
-            cp_async_8(&hdr->naoff, A.off + ni);
-            cp_async_4(&hdr->nalen, A.len + ni);
-        }
         if (over) {
             if (gl == 0) report_overflow(ctl, bin, i, A, B);
-        } else {
+            __syncwarp(gmask);
+            continue;
+        }
         uint32_t x[GS_EPL];
 #pragma unroll
         for (int e = 0; e < GS_EPL; e++) {
@@ -1110,7 +1051,7 @@ k_num_group_sort(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
         const int n = __shfl_sync(gmask, w, G - 1, G);
         w -= nl;
         int64_t dest = 0;
-        if (gl == 0) dest = c_row_dest_pre(C, J, ctl, i, n, hdr->ccap, hdr->coff);
+        if (gl == 0) dest = c_row_dest(C, J, ctl, i, n);
         dest = __shfl_sync(gmask, dest, 0, G);
         if (dest >= 0) {
 #pragma unroll
@@ -1125,17 +1066,7 @@ k_num_group_sort(MatView A, MatView B, MatView C, CJob J, Ctl *ctl, unsigned mas
             if (gl == 0) C.len[i] = n;
         }
         if (gl == 0) nnz_acc += n;
-        }
-        // the next row: its header reaches the group's lanes through shared
-        // memory once the first lane's copies have landed
-        if (gl == 0) cp_async_wait_all();
         __syncwarp(gmask);  // every lane has read the slots before the next row fills them
-        if (itn < cnt) {
-            i = hdr->ni;
-            aoff = hdr->naoff;
-            alen = hdr->nalen;
-        }
-        __syncwarp(gmask);  // read before the first lane's next copies overwrite them
     }
     nnz_acc = warp_sum<long long>(nnz_acc);
     if (lane == 0 && nnz_acc) atomic_add_ll2(&ctl->nnz_written, nnz_acc);
