@@ -2561,32 +2561,45 @@ dspg_status dspg_read_affected_C(dspg_handle *h, int64_t rows_cap, int64_t nnz_c
         const int64_t nch = ((h->A.nrows + 31) / 32 + 255) / 256;
         w.chunk_cnt.reserve(nch + 1);
         w.chunk_ex.reserve(nch + 1);
-        w.chunk_tmp.reserve(scan_tmp_entries(nch + 1) + 1);
-        rows_in_order(h->wc.R.p, h->wc.rchunk.p, nch, n, w.chunk_cnt.p, w.chunk_ex.p, w.chunk_tmp.p, w.r.p, s);
-        DBuf<int64_t> scan_l;
-        int64_t *lens_scan = read_scratch(w.scan, scan_l, scan_tmp_entries(n) + 1);
         DBuf<int32_t> lens_l;
         int32_t *lens = read_scratch(w.lens, lens_l, n);
-        lens_of_rows(w.r.p, n, h->C.len.p, lens, s);
-        scan_i32_to_i64(lens, rp, n, lens_scan, s);
         // page-locked host buffers: the rows go straight into them, in column
         // order, with one synchronisation (unless R was not collected in
         // order, which the read finds on the device and leaves to the path below)
         int32_t *dcol = rows && !on_device && h->direct_read && rows_cap >= n ? (int32_t *)device_view(col) : nullptr;
         void *dval = (dcol && val && h->vsize) ? device_view(val) : nullptr;
-        if (dcol && (!val || !h->vsize || dval)) {
-            w.res.reserve(1);
+        const bool direct = dcol && (!val || !h->vsize || dval);
+        if (direct) w.res.reserve(1);
+        // R in row order and its row pointers: two launches (each block scans
+        // the chunk table), written into the caller's page-locked rows and
+        // rowptr as well on the direct path; with a larger chunk table, the
+        // chunk scan, a gather of the lengths and their scan
+        const bool two = nch <= read_nch_max();
+        int32_t *drows = direct && two ? (int32_t *)device_view(rows) : nullptr;
+        int64_t *drp = direct && two ? (int64_t *)device_view(rowptr) : nullptr;
+        if (two) {
+            read_order_rowptr(h->wc.R.p, h->wc.rchunk.p, nch, n, h->C.len.p, w.r.p, lens, w.chunk_cnt.p,
+                              w.chunk_ex.p + nch, rp, drows, drp, direct ? w.res.p : nullptr, s, h->num_sms);
+        } else {
+            w.chunk_tmp.reserve(scan_tmp_entries(nch + 1) + 1);
+            rows_in_order(h->wc.R.p, h->wc.rchunk.p, nch, n, w.chunk_cnt.p, w.chunk_ex.p, w.chunk_tmp.p, w.r.p, s);
+            DBuf<int64_t> scan_l;
+            int64_t *lens_scan = read_scratch(w.scan, scan_l, scan_tmp_entries(n) + 1);
+            lens_of_rows(w.r.p, n, h->C.len.p, lens, s);
+            scan_i32_to_i64(lens, rp, n, lens_scan, s);
+            if (direct) CK(cudaMemsetAsync(w.res.p, 0, sizeof(ReadOut), s));
+        }
+        if (direct) {
             w.long_l.reserve(std::max<int64_t>(n, 1));
             w.huge_l.reserve(std::max<int64_t>(n, 1));
             w.c.reserve(std::max<int64_t>(nnz_cap, 1));
             w.v.reserve(std::max<int64_t>(nnz_cap, 1) * std::max(h->vsize, 1));
-            CK(cudaMemsetAsync(w.res.p, 0, sizeof(ReadOut), s));
             read_rows_direct(w.r.p, n, h->C.view(), h->vsize, rp, w.chunk_ex.p + nch, nnz_cap, dcol, dval, w.c.p,
                              (void *)w.v.p, w.long_l.p, w.huge_l.p, w.res.p, s, h->num_sms);
             ReadOut ro{};
             CK(cudaMemcpyAsync(&ro, w.res.p, sizeof(ReadOut), cudaMemcpyDeviceToHost, s));
-            if (n > 0) CK(cudaMemcpyAsync(rows, w.r.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
-            CK(cudaMemcpyAsync(rowptr, rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+            if (n > 0 && !drows) CK(cudaMemcpyAsync(rows, w.r.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+            if (!drp) CK(cudaMemcpyAsync(rowptr, rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (!(ro.flags & READ_UNORDERED)) {
                 *nrows_out = n;

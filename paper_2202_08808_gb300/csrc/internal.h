@@ -323,6 +323,16 @@ void read_rows_direct(const int32_t *rows, int64_t n, const MatView &M, int vsiz
 // is the number of rows placed (n when R came from one collection).
 void rows_in_order(const int32_t *R, const long long *chunk, int64_t nch, int64_t n, int64_t *cnt, int64_t *ex,
                    int64_t *tmp, int32_t *out, cudaStream_t s);
+// The same in two launches, with R's row pointers: out (n) gets R in row
+// order, lens (n) its rows' lengths in C (len), S (nch) the lengths summed per
+// chunk, rp (n + 1) the row pointers, *r_total the rows placed; h_rows and
+// h_rp (device addresses of page-locked host arrays of at least n and n + 1
+// entries, or null) get copies of out and rp, and res (or null) is zeroed.
+// For nch <= read_nch_max(); nothing but *r_total is written when it is not n.
+int64_t read_nch_max();
+void read_order_rowptr(const int32_t *R, const long long *chunk, int64_t nch, int64_t n, const int32_t *len,
+                       int32_t *out, int32_t *lens, int64_t *S, int64_t *r_total, int64_t *rp, int32_t *h_rows,
+                       int64_t *h_rp, ReadOut *res, cudaStream_t s, int num_sms);
 void validate_rowptr(int64_t nrows, int64_t nnz, const int64_t *rowptr, unsigned *bad, cudaStream_t s);
 void validate_csr_entries(int64_t nrows, int64_t ncols, const int64_t *rowptr, const int32_t *col, const void *val,
                           int sr, unsigned *bad, cudaStream_t s);

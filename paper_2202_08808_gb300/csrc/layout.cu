@@ -111,6 +111,159 @@ void rows_in_order(const int32_t *R, const long long *chunk, int64_t nch, int64_
     launch_k(k_chunk_copy, (unsigned)std::min<int64_t>(nch, 8192), 256, 0, s, R, chunk, nch, ex, n, out);
 }
 
+// R in row order and its row pointers for a read, in two launches while
+// the chunk table is small enough for one block to scan (READ_NCH_MAX
+// chunks): every block scans the chunk counts itself, so no scan launches
+// come between.  k_read_order lays each chunk's rows at the scan of the
+// counts, looks up their lengths in C and sums them per chunk;
+// k_read_rowptr scans the sums and each chunk's lengths into the rows' first
+// entries.  Both also write the caller's page-locked arrays when given
+// (h_rows, h_rp: device addresses), and both leave everything untouched when
+// the counts do not add up to n (R was not collected in one pass; the caller
+// sees *r_total != n).
+constexpr int RD_NT = 1024;
+constexpr int RD_IPT = 2;
+
+int64_t read_nch_max() { return (int64_t)RD_NT * RD_IPT; }
+
+// Exclusive scan of the m <= RD_NT * RD_IPT values load(0..m) into s_ex;
+// returns their total.  Every thread of the block calls it.
+template <class F>
+__device__ __forceinline__ int64_t rd_scan_table(F load, int m, int64_t *s_ex, int64_t *s_w) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int64_t v[RD_IPT];
+    int64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < RD_IPT; j++) {
+        const int c = tid * RD_IPT + j;
+        v[j] = c < m ? load(c) : 0;
+        sum += v[j];
+    }
+    const int64_t incl = warp_incl_scan<int64_t>(sum);
+    if (lane == 31) s_w[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int64_t t = s_w[lane];
+        const int64_t ti = warp_incl_scan<int64_t>(t);
+        s_w[lane] = ti - t;
+        if (lane == 31) s_w[32] = ti;
+    }
+    __syncthreads();
+    int64_t e = s_w[w] + incl - sum;
+#pragma unroll
+    for (int j = 0; j < RD_IPT; j++) {
+        const int c = tid * RD_IPT + j;
+        if (c < m) s_ex[c] = e;
+        e += v[j];
+    }
+    const int64_t total = s_w[32];
+    __syncthreads();
+    return total;
+}
+
+// Exclusive scan of one value per thread; *total gets the block's sum.
+__device__ __forceinline__ int64_t rd_block_scan(int64_t v, int64_t *s_w, int64_t *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t incl = warp_incl_scan<int64_t>(v);
+    if (lane == 31) s_w[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int64_t t = s_w[lane];
+        const int64_t ti = warp_incl_scan<int64_t>(t);
+        s_w[lane] = ti - t;
+        if (lane == 31) s_w[32] = ti;
+    }
+    __syncthreads();
+    const int64_t r = s_w[w] + incl - v;
+    *total = s_w[32];
+    __syncthreads();
+    return r;
+}
+
+// chunk c of R holds k = chunk[2c+1] rows at chunk[2c]; they go to o = ex[c]
+__device__ __forceinline__ bool rd_chunk_ok(long long b, long long k, int64_t o, int64_t n) {
+    return k > 0 && b >= 0 && b + k <= n && o + k <= n;
+}
+
+__global__ void __launch_bounds__(RD_NT)
+k_read_order(const int32_t *R, const long long *chunk, int nch, int64_t n, const int32_t *len, int32_t *out,
+             int32_t *lens, int64_t *S, int64_t *r_total, int32_t *h_rows, ReadOut *res) {
+    pdl_begin();
+    __shared__ int64_t s_ex[RD_NT * RD_IPT];
+    __shared__ int64_t s_w[33];
+    const int64_t tot = rd_scan_table([&](int c) { return (int64_t)chunk[2 * c + 1]; }, nch, s_ex, s_w);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *r_total = tot;
+        if (res) *res = ReadOut{};
+    }
+    if (tot != n) return;
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        const long long b = chunk[2 * c], k = chunk[2 * c + 1];
+        const int64_t o = s_ex[c];
+        int64_t sum = 0;
+        if (rd_chunk_ok(b, k, o, n))
+            for (long long t = threadIdx.x; t < k; t += RD_NT) {
+                const int32_t r = R[b + t];
+                out[o + t] = r;
+                if (h_rows) h_rows[o + t] = r;
+                const int32_t L = len[r];
+                lens[o + t] = L;
+                sum += L;
+            }
+        sum = warp_sum<int64_t>(sum);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int64_t t = s_w[threadIdx.x];
+            t = warp_sum<int64_t>(t);
+            if (threadIdx.x == 0) S[c] = t;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(RD_NT)
+k_read_rowptr(const long long *chunk, int nch, int64_t n, const int32_t *lens, const int64_t *S,
+              const int64_t *r_total, int64_t *rp, int64_t *h_rp) {
+    pdl_begin();
+    __shared__ int64_t s_ex[RD_NT * RD_IPT];
+    __shared__ int64_t s_base[RD_NT * RD_IPT];
+    __shared__ int64_t s_w[33];
+    if (*r_total != n) return;
+    rd_scan_table([&](int c) { return (int64_t)chunk[2 * c + 1]; }, nch, s_ex, s_w);
+    const int64_t nnz = rd_scan_table([&](int c) { return S[c]; }, nch, s_base, s_w);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        rp[n] = nnz;
+        if (h_rp) h_rp[n] = nnz;
+    }
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        const long long b = chunk[2 * c], k = chunk[2 * c + 1];
+        const int64_t o = s_ex[c];
+        if (!rd_chunk_ok(b, k, o, n)) continue;  // the same for the whole block
+        int64_t carry = s_base[c];
+        for (long long t0 = 0; t0 < k; t0 += RD_NT) {
+            const long long t = t0 + threadIdx.x;
+            const int64_t L = t < k ? lens[o + t] : 0;
+            int64_t round = 0;
+            const int64_t e = rd_block_scan(L, s_w, &round);
+            if (t < k) {
+                rp[o + t] = carry + e;
+                if (h_rp) h_rp[o + t] = carry + e;
+            }
+            carry += round;
+        }
+    }
+}
+
+void read_order_rowptr(const int32_t *R, const long long *chunk, int64_t nch, int64_t n, const int32_t *len,
+                       int32_t *out, int32_t *lens, int64_t *S, int64_t *r_total, int64_t *rp, int32_t *h_rows,
+                       int64_t *h_rp, ReadOut *res, cudaStream_t s, int num_sms) {
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nch, (int64_t)num_sms * 2));
+    launch_k(k_read_order, g, RD_NT, 0, s, R, chunk, (int)nch, n, len, out, lens, S, r_total, h_rows, res);
+    launch_k(k_read_rowptr, g, RD_NT, 0, s, chunk, (int)nch, n, (const int32_t *)lens, (const int64_t *)S,
+             (const int64_t *)r_total, rp, h_rp);
+}
+
 template <typename T>
 __global__ void k_copy_rows(const int32_t *rows, int64_t n, const int64_t *src_off, const int32_t *len,
                             const int32_t *src_col, const T *src_val, const int64_t *dst_off, int32_t *dst_col,
