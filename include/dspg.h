@@ -287,11 +287,32 @@ int dspg_debug_build(void);
  * *nnz_out receive the sizes; with rows == NULL nothing else is written.
  * Buffers smaller than rows_cap < n or nnz_cap < nnz: DSPG_ERR_INVALID with
  * the sizes written (the caller grows and calls again).  Synchronises the
- * stream twice.  Not for handles with alpha, beta or X (DSPG_ERR_STATE).
+ * stream once when col and val are page-locked host memory, twice
+ * otherwise.  Not for handles with alpha, beta or X (DSPG_ERR_STATE).
  * Not part of the paper: the read a server makes after each batch. */
 dspg_status dspg_read_affected_C(dspg_handle *h, int64_t rows_cap, int64_t nnz_cap, int64_t *nrows_out,
                                  int64_t *nnz_out, int32_t *rows, int64_t *rowptr, int32_t *col, void *val,
                                  int on_device, void *stream);
+
+/* dspg_apply_batch followed by dspg_read_affected_C (host memory,
+ * on_device = 0), with the same arguments and results, in one call.  When
+ * rows, rowptr, col and val are all page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister), rows_cap >= 0 and the handle keeps no Bloom filter, the
+ * read is enqueued behind the batch and the stream is synchronised once:
+ * the read's kernels take R's size from the device, check it against
+ * rows_cap, and write R, its row pointers and its rows of C' into the
+ * caller's arrays.  When the batch needed a second pass (a buffer grew, a
+ * learned table overflowed) or the arrays are too small, the enqueued read
+ * is discarded and the read runs again on its own after the batch
+ * (DSPG_ERR_INVALID with the sizes written, as dspg_read_affected_C, for
+ * arrays that are too small).  Any other host memory: the two calls one
+ * after the other.  A batch that fails returns its error with nothing read.
+ * Not part of the paper: the step of a server that returns every batch's
+ * affected rows. */
+dspg_status dspg_apply_read_affected(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
+                                     int64_t rows_cap, int64_t nnz_cap, int64_t *nrows_out, int64_t *nnz_out,
+                                     int32_t *rows, int64_t *rowptr, int32_t *col, void *val,
+                                     dspg_batch_stats *stats, void *stream);
 
 /* The affected row set R of the last apply_batch, ascending, into rows
  * (room for *count rows; with rows == NULL only *count is written). */

@@ -2578,8 +2578,9 @@ dspg_status dspg_read_affected_C(dspg_handle *h, int64_t rows_cap, int64_t nnz_c
         int32_t *drows = direct && two ? (int32_t *)device_view(rows) : nullptr;
         int64_t *drp = direct && two ? (int64_t *)device_view(rowptr) : nullptr;
         if (two) {
-            read_order_rowptr(h->wc.R.p, h->wc.rchunk.p, nch, n, h->C.len.p, w.r.p, lens, w.chunk_cnt.p,
-                              w.chunk_ex.p + nch, rp, drows, drp, direct ? w.res.p : nullptr, s, h->num_sms);
+            read_order_rowptr(h->wc.R.p, h->wc.rchunk.p, nch, n, nullptr, n, nullptr, h->C.len.p, w.r.p, lens,
+                              w.chunk_cnt.p, w.chunk_ex.p + nch, rp, drows, drp, direct ? w.res.p : nullptr, s,
+                              h->num_sms);
         } else {
             w.chunk_tmp.reserve(scan_tmp_entries(nch + 1) + 1);
             rows_in_order(h->wc.R.p, h->wc.rchunk.p, nch, n, w.chunk_cnt.p, w.chunk_ex.p, w.chunk_tmp.p, w.r.p, s);
@@ -2594,8 +2595,8 @@ dspg_status dspg_read_affected_C(dspg_handle *h, int64_t rows_cap, int64_t nnz_c
             w.huge_l.reserve(std::max<int64_t>(n, 1));
             w.c.reserve(std::max<int64_t>(nnz_cap, 1));
             w.v.reserve(std::max<int64_t>(nnz_cap, 1) * std::max(h->vsize, 1));
-            read_rows_direct(w.r.p, n, h->C.view(), h->vsize, rp, w.chunk_ex.p + nch, nnz_cap, dcol, dval, w.c.p,
-                             (void *)w.v.p, w.long_l.p, w.huge_l.p, w.res.p, s, h->num_sms);
+            read_rows_direct(w.r.p, n, nullptr, h->C.view(), h->vsize, rp, w.chunk_ex.p + nch, nnz_cap, dcol, dval,
+                             w.c.p, (void *)w.v.p, w.long_l.p, w.huge_l.p, w.res.p, s, h->num_sms);
             ReadOut ro{};
             CK(cudaMemcpyAsync(&ro, w.res.p, sizeof(ReadOut), cudaMemcpyDeviceToHost, s));
             if (n > 0 && !drows) CK(cudaMemcpyAsync(rows, w.r.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
@@ -2658,6 +2659,89 @@ dspg_status dspg_read_affected_C(dspg_handle *h, int64_t rows_cap, int64_t nnz_c
     } catch (const Err &e) {
         return fail(h, e);
     }
+}
+
+dspg_status dspg_apply_read_affected(dspg_handle *h, const dspg_updates *dA, const dspg_updates *dB,
+                                     int64_t rows_cap, int64_t nnz_cap, int64_t *nrows_out, int64_t *nnz_out,
+                                     int32_t *rows, int64_t *rowptr, int32_t *col, void *val,
+                                     dspg_batch_stats *stats, void *stream) {
+    if (!h || !nrows_out || !nnz_out) return DSPG_ERR_INVALID;
+    if (h->pending) return fail(h, Err(DSPG_ERR_STATE, "an asynchronous batch is in flight"));
+    if (h->form) return fail(h, Err(DSPG_ERR_STATE, "a handle with alpha, beta or X reads its rows by dspg_read_rows_C"));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nch = ((h->A.nrows + 31) / 32 + 255) / 256;
+    int32_t *drows = nullptr, *dcol = nullptr;
+    int64_t *drp = nullptr;
+    void *dval = nullptr;
+    bool one = !h->bloom && h->direct_read && rows && rowptr && col && rows_cap >= 0 && nnz_cap >= 0 &&
+               nch <= read_nch_max();
+    if (one) {
+        drows = (int32_t *)device_view(rows);
+        drp = (int64_t *)device_view(rowptr);
+        dcol = (int32_t *)device_view(col);
+        dval = (val && h->vsize) ? device_view(val) : nullptr;
+        one = drows && drp && dcol && (!val || !h->vsize || dval);
+    }
+    if (one) {
+        try {
+            check_usable(h);
+            NvtxRange r("dspg/apply_read_affected");
+            // the read's buffers first, so that nothing is allocated while the batch runs
+            dspg_handle::ReadWs &w = h->rd;
+            const int64_t cap = std::min<int64_t>(rows_cap, h->A.nrows);  // R never has more rows than A
+            const int64_t rc = std::max<int64_t>(cap, 1);
+            w.r.reserve(rc);
+            w.lens.reserve(rc);
+            w.rp.reserve(rc + 1);
+            w.chunk_cnt.reserve(nch + 1);
+            w.chunk_ex.reserve(nch + 1);
+            w.res.reserve(1);
+            w.long_l.reserve(rc);
+            w.huge_l.reserve(rc);
+            w.c.reserve(std::max<int64_t>(nnz_cap, 1));
+            w.v.reserve(std::max<int64_t>(nnz_cap, 1) * std::max(h->vsize, 1));
+            dspg_batch_stats local;
+            if (!stats) stats = &local;
+            prepare_batch(h, dA, dB, s);
+            const int64_t compactions0 = h->compactions;
+            bool clean = false;
+            ReadOut ro{};
+            try {
+                run_first(h, s, false);
+                // behind the batch: R's size from the device, bounded by cap
+                const long long *n_dev = &h->ctl->n_affected;
+                read_order_rowptr(h->wc.R.p, h->wc.rchunk.p, nch, rc, n_dev, cap, &h->ctl->status, h->C.len.p, w.r.p,
+                                  w.lens.p, w.chunk_cnt.p, w.chunk_ex.p + nch, w.rp.p, drows, drp, w.res.p, s,
+                                  h->num_sms);
+                read_rows_direct(w.r.p, rc, n_dev, h->C.view(), h->vsize, w.rp.p, w.chunk_ex.p + nch, nnz_cap, dcol,
+                                 dval, w.c.p, (void *)w.v.p, w.long_l.p, w.huge_l.p, w.res.p, s, h->num_sms);
+                CK(cudaMemcpyAsync(&ro, w.res.p, sizeof(ReadOut), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                // a batch that needs a second pass changes C after the read
+                clean = h->hctl->status == 0 && h->hctl->n_ovf <= 0;
+                if (h->prof) stage_times_from_events(h);
+                recover(h, s);
+                est_fallback(h, s);
+            } catch (const Err &e) {
+                if (e.st != DSPG_ERR_INVALID) h->broken = true;
+                throw;
+            }
+            fill_stats(h, stats, compactions0);
+            trace_batch(h, *stats, "rows");
+            if (clean && ro.flags == 0 && ro.n_huge == 0 && ro.nr == h->last_nR) {
+                *nrows_out = ro.nr;
+                *nnz_out = ro.nnz;
+                return DSPG_OK;
+            }
+        } catch (const Err &e) {
+            return fail(h, e);
+        }
+    } else {
+        const dspg_status st = dspg_apply_batch(h, dA, dB, stats, stream);
+        if (st != DSPG_OK) return st;
+    }
+    // the read on its own, after the batch
+    return dspg_read_affected_C(h, rows_cap, nnz_cap, nrows_out, nnz_out, rows, rowptr, col, val, 0, stream);
 }
 
 dspg_status dspg_last_affected(dspg_handle *h, int64_t *count, int32_t *rows, int on_device, void *stream) {

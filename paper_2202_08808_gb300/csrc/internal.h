@@ -306,6 +306,7 @@ struct ReadOut {
     unsigned n_huge; // of those, rows over 16384 entries that are out of order (left in the scratch)
     unsigned flags;  // READ_TOO_SMALL, READ_UNORDERED: nothing was written
     unsigned pad;
+    long long nr;    // the rows of R (n, as read on the device)
 };
 enum : unsigned { READ_TOO_SMALL = 1u, READ_UNORDERED = 2u };
 // rows[0..n) (ascending, R from its collection when r_total is given: its
@@ -313,10 +314,11 @@ enum : unsigned { READ_TOO_SMALL = 1u, READ_UNORDERED = 2u };
 // -> out_col/out_val (device addresses of page-locked host memory, at least
 // nnz_cap entries; out_val may be null).  Scratch: nnz_cap entries; lists:
 // n entries each; res zeroed by the caller.
-void read_rows_direct(const int32_t *rows, int64_t n, const MatView &M, int vsize, const int64_t *rp,
-                      const int64_t *r_total, int64_t nnz_cap, int32_t *out_col, void *out_val, int32_t *scr_col,
-                      void *scr_val, int64_t *long_list, int64_t *huge_list, ReadOut *res, cudaStream_t s,
-                      int num_sms);
+// n_dev (or null): n read on the device, n then bounding it (grid sizes).
+void read_rows_direct(const int32_t *rows, int64_t n, const long long *n_dev, const MatView &M, int vsize,
+                      const int64_t *rp, const int64_t *r_total, int64_t nnz_cap, int32_t *out_col, void *out_val,
+                      int32_t *scr_col, void *scr_val, int64_t *long_list, int64_t *huge_list, ReadOut *res,
+                      cudaStream_t s, int num_sms);
 // R (n rows, as collected: ascending within each 8192-row chunk, chunk c's
 // rows at chunk[2c] with chunk[2c+1] of them) into out in row order; cnt and
 // ex (nch + 1) and tmp (scan_tmp_entries(nch) + 1) are scratch, and ex[nch]
@@ -327,12 +329,17 @@ void rows_in_order(const int32_t *R, const long long *chunk, int64_t nch, int64_
 // order, lens (n) its rows' lengths in C (len), S (nch) the lengths summed per
 // chunk, rp (n + 1) the row pointers, *r_total the rows placed; h_rows and
 // h_rp (device addresses of page-locked host arrays of at least n and n + 1
-// entries, or null) get copies of out and rp, and res (or null) is zeroed.
-// For nch <= read_nch_max(); nothing but *r_total is written when it is not n.
+// entries, or null) get copies of out and rp, and res (or null) is zeroed
+// with its nr set.  For nch <= read_nch_max(); nothing but *r_total is
+// written when it is not n.  With n_dev, n is read on the device (behind a
+// batch still on the stream): rows_cap bounds it (the arrays are sized for
+// rows_cap), and a nonzero *status (a failed batch) or a larger n makes
+// *r_total -1, so that nothing is read.
 int64_t read_nch_max();
-void read_order_rowptr(const int32_t *R, const long long *chunk, int64_t nch, int64_t n, const int32_t *len,
-                       int32_t *out, int32_t *lens, int64_t *S, int64_t *r_total, int64_t *rp, int32_t *h_rows,
-                       int64_t *h_rp, ReadOut *res, cudaStream_t s, int num_sms);
+void read_order_rowptr(const int32_t *R, const long long *chunk, int64_t nch, int64_t n, const long long *n_dev,
+                       int64_t rows_cap, const unsigned *status, const int32_t *len, int32_t *out, int32_t *lens,
+                       int64_t *S, int64_t *r_total, int64_t *rp, int32_t *h_rows, int64_t *h_rp, ReadOut *res,
+                       cudaStream_t s, int num_sms);
 void validate_rowptr(int64_t nrows, int64_t nnz, const int64_t *rowptr, unsigned *bad, cudaStream_t s);
 void validate_csr_entries(int64_t nrows, int64_t ncols, const int64_t *rowptr, const int32_t *col, const void *val,
                           int sr, unsigned *bad, cudaStream_t s);

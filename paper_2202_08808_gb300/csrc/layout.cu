@@ -186,17 +186,26 @@ __device__ __forceinline__ bool rd_chunk_ok(long long b, long long k, int64_t o,
 }
 
 __global__ void __launch_bounds__(RD_NT)
-k_read_order(const int32_t *R, const long long *chunk, int nch, int64_t n, const int32_t *len, int32_t *out,
-             int32_t *lens, int64_t *S, int64_t *r_total, int32_t *h_rows, ReadOut *res) {
+k_read_order(const int32_t *R, const long long *chunk, int nch, int64_t n_arg, const long long *n_dev, int64_t rows_cap,
+             const unsigned *status, const int32_t *len, int32_t *out, int32_t *lens, int64_t *S, int64_t *r_total,
+             int32_t *h_rows, ReadOut *res) {
     pdl_begin();
     __shared__ int64_t s_ex[RD_NT * RD_IPT];
     __shared__ int64_t s_w[33];
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_arg;
+    // enqueued behind an apply (n on the device): nothing is read after a
+    // failed batch or when R would not fit the buffers sized for it
+    const bool skip = (status && *status) || n < 0 || n > rows_cap;
     const int64_t tot = rd_scan_table([&](int c) { return (int64_t)chunk[2 * c + 1]; }, nch, s_ex, s_w);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *r_total = tot;
-        if (res) *res = ReadOut{};
+        *r_total = skip ? -1 : tot;
+        if (res) {
+            ReadOut z{};
+            z.nr = n;
+            *res = z;
+        }
     }
-    if (tot != n) return;
+    if (skip || tot != n) return;
     for (int c = blockIdx.x; c < nch; c += gridDim.x) {
         const long long b = chunk[2 * c], k = chunk[2 * c + 1];
         const int64_t o = s_ex[c];
@@ -223,12 +232,13 @@ k_read_order(const int32_t *R, const long long *chunk, int nch, int64_t n, const
 }
 
 __global__ void __launch_bounds__(RD_NT)
-k_read_rowptr(const long long *chunk, int nch, int64_t n, const int32_t *lens, const int64_t *S,
-              const int64_t *r_total, int64_t *rp, int64_t *h_rp) {
+k_read_rowptr(const long long *chunk, int nch, int64_t n_arg, const long long *n_dev, const int32_t *lens,
+              const int64_t *S, const int64_t *r_total, int64_t *rp, int64_t *h_rp) {
     pdl_begin();
     __shared__ int64_t s_ex[RD_NT * RD_IPT];
     __shared__ int64_t s_base[RD_NT * RD_IPT];
     __shared__ int64_t s_w[33];
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_arg;
     if (*r_total != n) return;
     rd_scan_table([&](int c) { return (int64_t)chunk[2 * c + 1]; }, nch, s_ex, s_w);
     const int64_t nnz = rd_scan_table([&](int c) { return S[c]; }, nch, s_base, s_w);
@@ -255,12 +265,14 @@ k_read_rowptr(const long long *chunk, int nch, int64_t n, const int32_t *lens, c
     }
 }
 
-void read_order_rowptr(const int32_t *R, const long long *chunk, int64_t nch, int64_t n, const int32_t *len,
-                       int32_t *out, int32_t *lens, int64_t *S, int64_t *r_total, int64_t *rp, int32_t *h_rows,
-                       int64_t *h_rp, ReadOut *res, cudaStream_t s, int num_sms) {
+void read_order_rowptr(const int32_t *R, const long long *chunk, int64_t nch, int64_t n, const long long *n_dev,
+                       int64_t rows_cap, const unsigned *status, const int32_t *len, int32_t *out, int32_t *lens,
+                       int64_t *S, int64_t *r_total, int64_t *rp, int32_t *h_rows, int64_t *h_rp, ReadOut *res,
+                       cudaStream_t s, int num_sms) {
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nch, (int64_t)num_sms * 2));
-    launch_k(k_read_order, g, RD_NT, 0, s, R, chunk, (int)nch, n, len, out, lens, S, r_total, h_rows, res);
-    launch_k(k_read_rowptr, g, RD_NT, 0, s, chunk, (int)nch, n, (const int32_t *)lens, (const int64_t *)S,
+    launch_k(k_read_order, g, RD_NT, 0, s, R, chunk, (int)nch, n, n_dev, rows_cap, status, len, out, lens, S, r_total,
+             h_rows, res);
+    launch_k(k_read_rowptr, g, RD_NT, 0, s, chunk, (int)nch, n, n_dev, (const int32_t *)lens, (const int64_t *)S,
              (const int64_t *)r_total, rp, h_rp);
 }
 
@@ -440,12 +452,15 @@ __global__ void __launch_bounds__(512) k_sort_long_rows(const int64_t *rowptr, i
 // collection (r_total != n) or the entries do not fit the caller's buffers;
 // the flags say which, and the caller takes the general path.
 template <typename T>
-__global__ void k_gather_sort_out(const int32_t *rows, int64_t n, MatView M, const int64_t *rp,
-                                  const int64_t *r_total, int64_t nnz_cap, int32_t *out_col, T *out_val,
-                                  int32_t *scr_col, T *scr_val, int64_t *long_list, ReadOut *res) {
+__global__ void k_gather_sort_out(const int32_t *rows, int64_t n_arg, const long long *n_dev, MatView M,
+                                  const int64_t *rp, const int64_t *r_total, int64_t nnz_cap, int32_t *out_col,
+                                  T *out_val, int32_t *scr_col, T *scr_val, int64_t *long_list, ReadOut *res) {
     pdl_begin();
-    const int64_t nnz = rp[n];
-    const unsigned bad = (r_total && *r_total != n ? READ_UNORDERED : 0u) | (nnz > nnz_cap ? READ_TOO_SMALL : 0u);
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_arg;
+    // rp[n] exists only when R was placed (r_total == n)
+    const bool unordered = r_total && *r_total != n;
+    const int64_t nnz = unordered ? 0 : rp[n];
+    const unsigned bad = (unordered ? READ_UNORDERED : 0u) | (nnz > nnz_cap ? READ_TOO_SMALL : 0u);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         res->nnz = nnz;
         if (bad) atomicOr(&res->flags, bad);
@@ -549,12 +564,13 @@ __global__ void __launch_bounds__(512) k_long_rows_out(const int64_t *rp, const 
 }
 
 template <typename T>
-static void read_rows_direct_t(const int32_t *rows, int64_t n, const MatView &M, const int64_t *rp,
-                               const int64_t *r_total, int64_t nnz_cap, int32_t *out_col, T *out_val, int32_t *scr_col,
-                               T *scr_val, int64_t *long_list, int64_t *huge_list, ReadOut *res, cudaStream_t s,
-                               int num_sms) {
+static void read_rows_direct_t(const int32_t *rows, int64_t n, const long long *n_dev, const MatView &M,
+                               const int64_t *rp, const int64_t *r_total, int64_t nnz_cap, int32_t *out_col, T *out_val,
+                               int32_t *scr_col, T *scr_val, int64_t *long_list, int64_t *huge_list, ReadOut *res,
+                               cudaStream_t s, int num_sms) {
+    // n on the device: n is the host's bound on it, which sizes the grids
     launch_k(k_gather_sort_out<T>, blocks_for(std::max<int64_t>(n, 1) * 32, 256, (int64_t)num_sms * 16), 256, 0, s, rows,
-             n, M, rp, r_total, nnz_cap, out_col, out_val, scr_col, scr_val, long_list, res);
+             n, n_dev, M, rp, r_total, nnz_cap, out_col, out_val, scr_col, scr_val, long_list, res);
     const size_t smem = (size_t)SORT_MAX * (sizeof(T) + sizeof(int32_t));
     static bool set = false;
     if (!set) {
@@ -565,15 +581,15 @@ static void read_rows_direct_t(const int32_t *rows, int64_t n, const MatView &M,
              s, rp, long_list, scr_col, scr_val, out_col, out_val, huge_list, res);
 }
 
-void read_rows_direct(const int32_t *rows, int64_t n, const MatView &M, int vsize, const int64_t *rp,
-                      const int64_t *r_total, int64_t nnz_cap, int32_t *out_col, void *out_val, int32_t *scr_col,
-                      void *scr_val, int64_t *long_list, int64_t *huge_list, ReadOut *res, cudaStream_t s,
-                      int num_sms) {
+void read_rows_direct(const int32_t *rows, int64_t n, const long long *n_dev, const MatView &M, int vsize,
+                      const int64_t *rp, const int64_t *r_total, int64_t nnz_cap, int32_t *out_col, void *out_val,
+                      int32_t *scr_col, void *scr_val, int64_t *long_list, int64_t *huge_list, ReadOut *res,
+                      cudaStream_t s, int num_sms) {
     if (vsize == 8)
-        read_rows_direct_t<double>(rows, n, M, rp, r_total, nnz_cap, out_col, (double *)out_val, scr_col,
+        read_rows_direct_t<double>(rows, n, n_dev, M, rp, r_total, nnz_cap, out_col, (double *)out_val, scr_col,
                                    (double *)scr_val, long_list, huge_list, res, s, num_sms);
     else
-        read_rows_direct_t<int32_t>(rows, n, M, rp, r_total, nnz_cap, out_col, (int32_t *)out_val, scr_col,
+        read_rows_direct_t<int32_t>(rows, n, n_dev, M, rp, r_total, nnz_cap, out_col, (int32_t *)out_val, scr_col,
                                     (int32_t *)scr_val, long_list, huge_list, res, s, num_sms);
 }
 

@@ -113,6 +113,9 @@ def load():
         lib.dspg_fault_inject.argtypes = [C.c_char_p]
         lib.dspg_read_affected_C.restype = i32
         lib.dspg_read_affected_C.argtypes = [p, i64, i64, C.POINTER(i64), C.POINTER(i64), p, p, p, p, i32, p]
+        lib.dspg_apply_read_affected.restype = i32
+        lib.dspg_apply_read_affected.argtypes = [p, C.POINTER(_Upd), C.POINTER(_Upd), i64, i64, C.POINTER(i64),
+                                                 C.POINTER(i64), p, p, p, p, C.POINTER(_Stats), p]
         lib.dspg_last_affected.restype = i32
         lib.dspg_last_affected.argtypes = [p, C.POINTER(i64), p, i32, p]
         lib.dspg_recompute_all.restype = i32
@@ -184,7 +187,8 @@ def load():
 
 
 EXPORTED = ["dspg_build", "dspg_build_form", "dspg_apply_batch", "dspg_apply_batch_algebraic", "dspg_read_C", "dspg_read_A",
-            "dspg_read_bloom", "dspg_read_rows_C", "dspg_read_affected_C", "dspg_fault_inject", "dspg_debug_build",
+            "dspg_read_bloom", "dspg_read_rows_C", "dspg_read_affected_C", "dspg_apply_read_affected",
+            "dspg_fault_inject", "dspg_debug_build",
             "dspg_last_affected", "dspg_recompute_all", "dspg_info", "dspg_set_profiling", "dspg_stage_times",
             "dspg_kernel_launches", "dspg_run_counts", "dspg_reserve", "dspg_multiply_rows_noalloc", "dspg_set_tuning", "dspg_get_tuning",
             "dspg_tuning_candidate", "dspg_autotune", "dspg_group_create", "dspg_group_apply", "dspg_group_destroy",
@@ -468,6 +472,39 @@ class DynamicSpGEMM:
             k, e = n.value, nnz.value
             return rows[:k], rp[:k + 1], col[:e], val[:e]
         raise DspgError(1, "read_affected: sizes kept changing")
+
+    def apply_read_affected(self, dA=None, dB=None, stream=None, out=None):
+        """apply_batch and then read_affected in one call
+        (dspg_apply_read_affected): returns (stats, (rows, rowptr, col,
+        val)).  With out (caller-owned page-locked arrays, as read_affected
+        takes them) the read is enqueued behind the batch and the stream is
+        synchronised once; without, the two calls run one after the other."""
+        if out is None:
+            stats = self.apply_batch(dA, dB, stream)
+            return stats, self.read_affected(stream)
+        o_rows, o_rp, o_col, o_val = out
+        if (o_rows.dtype != np.int32 or o_rp.dtype != np.int64 or o_col.dtype != np.int32
+                or o_val.dtype != _vdtype(self.sr) or o_rp.shape[0] < o_rows.shape[0] + 1
+                or o_val.shape[0] < o_col.shape[0]):
+            raise ValueError("apply_read_affected: out arrays of the wrong types or sizes")
+        keep: list = []
+        ua = self._upd(dA, keep) if dA is not None else None
+        ub = self._upd(dB, keep) if dB is not None else None
+        stats = _Stats()
+        n = C.c_int64()
+        nnz = C.c_int64()
+        st = self._lib.dspg_apply_read_affected(self._h, C.byref(ua) if ua is not None else None,
+                                                C.byref(ub) if ub is not None else None, o_rows.shape[0],
+                                                o_col.shape[0], C.byref(n), C.byref(nnz), o_rows.ctypes.data,
+                                                o_rp.ctypes.data, o_col.ctypes.data, o_val.ctypes.data,
+                                                C.byref(stats), _stream(stream))
+        sd = {name: getattr(stats, name) for name, _ in _Stats._fields_}
+        if st == 0:
+            k, e = n.value, nnz.value
+            return sd, (o_rows[:k], o_rp[:k + 1], o_col[:e], o_val[:e])
+        if st == 1 and (n.value > o_rows.shape[0] or nnz.value > o_col.shape[0]):
+            return sd, self.read_affected(stream)  # applied; the arrays were too small for the read
+        self._check(st)
 
     def read_rows_C(self, rows, stream=None):
         rows = np.ascontiguousarray(rows, np.int32)

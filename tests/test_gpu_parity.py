@@ -790,6 +790,69 @@ def test_read_affected_into_caller_arrays(dspg, sr):
             assert np.all(np.abs(val - oval) <= 1e-12 * sabs), f"read {t}: values"
 
 
+def _check_rows_of_c(Ao, rows, rp, col, val, sr, what):
+    orp, ocol, oval = Ao.multiply_rows(Ao, rows)
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol), f"{what}: pattern"
+    if sr == MIN_PLUS_I32:
+        assert np.array_equal(val, oval), f"{what}: values"
+    else:
+        _, _, sabs = Ao.multiply_rows(Ao, rows, absval=True)
+        assert np.all(np.abs(val - oval) <= 1e-12 * sabs), f"{what}: values"
+
+
+@pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
+def test_apply_read_affected_one_call(dspg, sr):
+    """apply_read_affected: a batch and the read of its affected rows in one
+    call.  With page-locked arrays the read is enqueued behind the batch and
+    takes R's size from the device (one synchronisation); pageable arrays,
+    arrays too small for the result and batches that need a second pass (a
+    tight arena rebuilt mid-batch) take the read on its own after the batch.
+    Every result is the oracle's R and rows of C', and A' the oracle's."""
+    import torch
+    vt = torch.float64 if sr == PLUS_TIMES_F64 else torch.int32
+    vn = np.float64 if sr == PLUS_TIMES_F64 else np.int32
+
+    def page_locked(nr, ne):
+        return tuple(torch.empty(m, dtype=dt, pin_memory=True).numpy()
+                     for m, dt in ((nr, torch.int32), (nr + 1, torch.int64), (ne, torch.int32), (ne, vt)))
+
+    n = 3000
+    A = er_matrix(n, 6, seed=111, kind=sr)
+    g = dspg.DynamicSpGEMM(A)
+    Ao = OMat.from_csr(A)
+    Co = Ao.multiply(Ao)
+    pinned = page_locked(n, 200000)
+    pageable = (np.empty(n, np.int32), np.empty(n + 1, np.int64), np.empty(200000, np.int32), np.empty(200000, vn))
+    small = page_locked(4, 4)
+    for t, out in enumerate((pinned, pinned, pageable, small, pinned)):
+        b = random_batch(n, n, 400 + 300 * t, 112 + t, sr, A=Ao.to_csr())
+        st, (rows, rp, col, val) = g.apply_read_affected(b, out=out)
+        R = oracle.row_dynamic(Ao, Co, b, None, None)  # A' and C' of the oracle, and its R
+        if out is not small:
+            assert np.shares_memory(rows, out[0]) and np.shares_memory(col, out[2]), "out arrays not used"
+        assert st["affected_rows"] == rows.shape[0]
+        assert np.array_equal(rows, R), f"batch {t}: affected rows"
+        _check_rows_of_c(Ao, rows, rp, col, val, sr, f"batch {t}")
+        _check_state(g, Ao, None, f"batch {t}")
+    # arenas without room: every batch is applied in two passes, and the read
+    # enqueued behind the first is replaced by one after the second
+    A2 = random_csr(400, 400, 10, 31, sr)
+    g2 = dspg.DynamicSpGEMM(A2, slack_min=0, slack_div=1 << 20, arena_headroom=1.0)
+    Ao2 = OMat.from_csr(A2)
+    Co2 = Ao2.multiply(Ao2)
+    out2 = page_locked(400, 160000)
+    grown = 0
+    for k in range(3):
+        b = random_batch(400, 400, 3000, 60 + k, sr, A=Ao2.to_csr(), hit_frac=0.1)
+        st, (rows, rp, col, val) = g2.apply_read_affected(b, out=out2)
+        R = oracle.row_dynamic(Ao2, Co2, b, None, None)
+        grown += st["compactions"]
+        assert np.array_equal(rows, R), f"tight {k}: affected rows"
+        _check_rows_of_c(Ao2, rows, rp, col, val, sr, f"tight {k}")
+        _check_state(g2, Ao2, None, f"tight {k}")
+    assert grown > 0
+
+
 @pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
 def test_host_batches_page_locked_pageable_and_device(dspg, sr):
     """The same batches given as page-locked host arrays, pageable host
