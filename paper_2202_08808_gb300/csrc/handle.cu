@@ -2542,6 +2542,28 @@ dspg_status dspg_fault_inject(const char *spec) {
     return DSPG_OK;
 }
 
+// The end of a direct read whose rows over 16384 entries were out of order
+// (ro.n_huge of them, listed in the read's scratch): each is sorted in the
+// scratch on the device and copied into the caller's col and val (rp: the
+// device row pointers, rowptr: the same on the host).
+void read_huge_rows(dspg_handle *h, const ReadOut &ro, const int64_t *rp, const int64_t *rowptr, int32_t *col,
+                    void *val, cudaStream_t s) {
+    dspg_handle::ReadWs &w = h->rd;
+    std::vector<int64_t> lh(ro.n_huge);
+    CK(cudaMemcpyAsync(lh.data(), w.huge_l.p, sizeof(int64_t) * ro.n_huge, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::sort(lh.begin(), lh.end());
+    sort_listed_host(h, h->C, rp, lh, rowptr, w.c.p, (void *)w.v.p, h->vsize, s);
+    for (int64_t x : lh) {
+        const int64_t lo = rowptr[x], len = rowptr[x + 1] - rowptr[x];
+        CK(cudaMemcpyAsync(col + lo, w.c.p + lo, sizeof(int32_t) * len, cudaMemcpyDeviceToHost, s));
+        if (val && h->vsize)
+            CK(cudaMemcpyAsync((char *)val + lo * h->vsize, w.v.p + lo * h->vsize, (size_t)h->vsize * len,
+                               cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+}
+
 dspg_status dspg_read_affected_C(dspg_handle *h, int64_t rows_cap, int64_t nnz_cap, int64_t *nrows_out,
                                  int64_t *nnz_out, int32_t *rows, int64_t *rowptr, int32_t *col, void *val,
                                  int on_device, void *stream) {
@@ -2608,21 +2630,7 @@ dspg_status dspg_read_affected_C(dspg_handle *h, int64_t rows_cap, int64_t nnz_c
                 if (ro.flags & READ_TOO_SMALL)
                     throw Err(DSPG_ERR_INVALID, "read_affected_C: buffers too small (need " + std::to_string(n) +
                                                     " rows, " + std::to_string(ro.nnz) + " entries)");
-                if (ro.n_huge > 0) {  // rows over 16384 entries out of order: sorted in the scratch, then copied
-                    std::vector<int64_t> lh(ro.n_huge);
-                    CK(cudaMemcpyAsync(lh.data(), w.huge_l.p, sizeof(int64_t) * ro.n_huge, cudaMemcpyDeviceToHost, s));
-                    CK(cudaStreamSynchronize(s));
-                    std::sort(lh.begin(), lh.end());
-                    sort_listed_host(h, h->C, rp, lh, rowptr, w.c.p, (void *)w.v.p, h->vsize, s);
-                    for (int64_t x : lh) {
-                        const int64_t lo = rowptr[x], len = rowptr[x + 1] - rowptr[x];
-                        CK(cudaMemcpyAsync(col + lo, w.c.p + lo, sizeof(int32_t) * len, cudaMemcpyDeviceToHost, s));
-                        if (val && h->vsize)
-                            CK(cudaMemcpyAsync((char *)val + lo * h->vsize, w.v.p + lo * h->vsize, (size_t)h->vsize * len,
-                                               cudaMemcpyDeviceToHost, s));
-                    }
-                    CK(cudaStreamSynchronize(s));
-                }
+                if (ro.n_huge > 0) read_huge_rows(h, ro, rp, rowptr, col, val, s);
                 return DSPG_OK;
             }
         }
@@ -2728,9 +2736,10 @@ dspg_status dspg_apply_read_affected(dspg_handle *h, const dspg_updates *dA, con
             }
             fill_stats(h, stats, compactions0);
             trace_batch(h, *stats, "rows");
-            if (clean && ro.flags == 0 && ro.n_huge == 0 && ro.nr == h->last_nR) {
+            if (clean && ro.flags == 0 && ro.nr == h->last_nR) {
                 *nrows_out = ro.nr;
                 *nnz_out = ro.nnz;
+                if (ro.n_huge > 0) read_huge_rows(h, ro, w.rp.p, rowptr, col, val, s);
                 return DSPG_OK;
             }
         } catch (const Err &e) {

@@ -706,7 +706,10 @@ def test_read_affected_rows_of_every_length(dspg, sr, monkeypatch):
     hash tables do not), longer ones in shared memory, and rows of more than
     16384 entries out of order (hub rows of A over B rows of ~20 entries,
     from the cluster tables) by the radix sort.  R and every row equal the
-    oracle's, and the read that stages the rows on the device first."""
+    oracle's, and the read that stages the rows on the device first; so do
+    those of apply_read_affected into page-locked arrays (the read enqueued
+    behind the batch)."""
+    import torch
     rng = np.random.default_rng(93)
     n, k, m = 1200, 4000, 400000
     bcols = [rng.choice(m, size=int(rng.integers(0, 41)), replace=False) for _ in range(k)]
@@ -724,6 +727,10 @@ def test_read_affected_rows_of_every_length(dspg, sr, monkeypatch):
     monkeypatch.setenv("DSPG_NO_DIRECT_READ", "1")
     g_staged = dspg.DynamicSpGEMM(A, B)
     monkeypatch.delenv("DSPG_NO_DIRECT_READ")
+    g_one = dspg.DynamicSpGEMM(A, B)
+    vt = torch.float64 if sr == PLUS_TIMES_F64 else torch.int32
+    out = tuple(torch.empty(q, dtype=dt, pin_memory=True).numpy()
+                for q, dt in ((n, torch.int32), (n + 1, torch.int64), (2000000, torch.int32), (2000000, vt)))
     Ao, Bo = OMat.from_csr(A), OMat.from_csr(B)
     for t in range(2):
         b = random_batch(n, k, 600, 95 + t, sr, A=Ao.to_csr(), dup_frac=0.1)
@@ -733,9 +740,12 @@ def test_read_affected_rows_of_every_length(dspg, sr, monkeypatch):
         b.val[:23] = b.val[:23] * 0 + 2
         g.apply_batch(b)
         g_staged.apply_batch(b)
+        _, (rows_1, rp_1, col_1, val_1) = g_one.apply_read_affected(b, out=out)
         Ao.apply(b)
         rows, rp_g, col, val = g.read_affected()
         rows_s, rp_s, col_s, val_s = g_staged.read_affected()
+        assert np.shares_memory(col_1, out[2]), "out arrays not used"
+        assert np.array_equal(rows_1, rows) and np.array_equal(rp_1, rp_g) and np.array_equal(col_1, col)
         assert np.array_equal(rows, g.last_affected()) and np.array_equal(rows, rows_s)
         lens_c = np.diff(rp_g)
         assert lens_c.max() > 16384 and ((lens_c > 64) & (lens_c <= 16384)).any() and (lens_c <= 64).any()
@@ -746,12 +756,13 @@ def test_read_affected_rows_of_every_length(dspg, sr, monkeypatch):
             # (min,+) is order-free; (+,.) sums of the hash bins depend on the
             # order of their shared-memory atomics, so the two handles' values
             # are each checked against the oracle below instead
-            assert np.array_equal(val_s, val)
+            assert np.array_equal(val_s, val) and np.array_equal(val_1, val)
             assert np.array_equal(val, oval)
         else:
             _, _, sabs = Ao.multiply_rows(Bo, rows, absval=True)
             assert np.all(np.abs(val - oval) <= 1e-12 * sabs), f"batch {t}: values"
             assert np.all(np.abs(val_s - oval) <= 1e-12 * sabs), f"batch {t}: staged values"
+            assert np.all(np.abs(val_1 - oval) <= 1e-12 * sabs), f"batch {t}: one-call values"
 
 
 @pytest.mark.parametrize("sr", [PLUS_TIMES_F64, MIN_PLUS_I32])
