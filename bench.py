@@ -1211,6 +1211,17 @@ def profile_arm(args):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     print("step profiled", st)
+    if args.profile == "read":  # R and its rows of C' into page-locked arrays (sized by a first read)
+        rows, rp, col, val = g.read_affected()
+        out = tuple(torch.empty(x.shape[0], dtype=dt, pin_memory=True).numpy() for x, dt in
+                    ((rows, torch.int32), (rp, torch.int64), (col, torch.int32),
+                     (val, torch.float64 if val.dtype == np.float64 else torch.int32)))
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("read")
+        g.read_affected(out=out)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print("read profiled", rows.shape[0], col.shape[0])
 
 
 def main():
@@ -1225,8 +1236,9 @@ def main():
     ap.add_argument("--no-cusparse", action="store_true", help="skip the cuSPARSE static-product comparator")
     ap.add_argument("--no-masked", action="store_true",
                     help="skip the masked-path leg (Algorithm 2 beside the row path on R-MAT scale 20)")
-    ap.add_argument("--profile", choices=["step", "static"], default=None,
-                    help="run one NVTX-marked step or static recompute for ncu, then exit")
+    ap.add_argument("--profile", choices=["step", "static", "read"], default=None,
+                    help="run one NVTX-marked step, static recompute or read of a step's affected rows for ncu, "
+                         "then exit")
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--workload", choices=["stencil", "rmat20", "rmat21", "batched", "learned"], default="stencil",
                     help="stencil: the 128^3 stencil with 10^4-update batches; rmat20: R-MAT scale 20 (min,+) "
