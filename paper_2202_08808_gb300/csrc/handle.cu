@@ -2546,8 +2546,8 @@ dspg_status dspg_fault_inject(const char *spec) {
 // (ro.n_huge of them, listed in the read's scratch): each is sorted in the
 // scratch on the device and copied into the caller's col and val (rp: the
 // device row pointers, rowptr: the same on the host).
-void read_huge_rows(dspg_handle *h, const ReadOut &ro, const int64_t *rp, const int64_t *rowptr, int32_t *col,
-                    void *val, cudaStream_t s) {
+static void read_huge_rows(dspg_handle *h, const ReadOut &ro, const int64_t *rp, const int64_t *rowptr,
+                           int32_t *col, void *val, cudaStream_t s) {
     dspg_handle::ReadWs &w = h->rd;
     std::vector<int64_t> lh(ro.n_huge);
     CK(cudaMemcpyAsync(lh.data(), w.huge_l.p, sizeof(int64_t) * ro.n_huge, cudaMemcpyDeviceToHost, s));
